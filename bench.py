@@ -1,0 +1,299 @@
+#!/usr/bin/env python
+"""Benchmark of the NeFTY hot path on GB300: one step = the forward sweep plus
+the reverse adjoint sweep with the diffusivity gradient, on a synthetic
+256x256x48 grid over 1000 implicit-Euler steps (dt = 0.25, FP32 vectors and
+stencil, FP64 reductions).
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own replica
+of the workload (no data-path collective; weak scaling) and rank 0 reports the
+aggregate over the max-over-ranks time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+``--impl reference`` times the FP64 CPU oracle on the host cores, on a bounded
+sample of the same workload (the first few time steps of the same grid).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import signal
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# The oracle's OpenMP loops read this once, when the library loads.
+os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+
+import numpy as np  # noqa: E402
+
+METRIC = "fwd+adjoint Gcell-steps/s"
+UNIT = "Gcell-steps/s"
+# Algorithmic bytes of one fused Jacobi-PCG iteration per cell (FP32 path):
+# read + write of x, r, p (24 B) and a read of the three face values plus the
+# Jacobi diagonal (16 B); per time step one right-hand-side read and one
+# solution write (8 B).  FP64 doubles both.
+ALG_BYTES_ITER = {"fp32": 40, "fp64": 80}
+ALG_BYTES_STEP = {"fp32": 8, "fp64": 16}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--nx", type=int, default=256)
+    ap.add_argument("--ny", type=int, default=256)
+    ap.add_argument("--nz", type=int, default=48)
+    ap.add_argument("--nt", type=int, default=1000)
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--ckpt-every", type=int, default=0)
+    ap.add_argument("--cpu-sample-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2603_11045_gb300 import synthetic as S
+    w = S.neural_field_case(nx=args.nx, ny=args.ny, nz=args.nz, nt=args.nt, dt=0.25)
+    # candidate field for the inversion step: the smooth background without
+    # the inclusions (the target frames come from the field with inclusions)
+    g = S.rng(w.extra["seed"])
+    cand = g.uniform(0.8, 1.2, size=(w.nz, w.ny, w.nx))
+    return w, cand
+
+
+def config_dict(args, w):
+    return {"workload": f"inversion step, {w.nx}x{w.ny}x{w.nz} cells, {w.nt} implicit-Euler steps, dt={w.dt}",
+            "grid": [w.nx, w.ny, w.nz], "nt": w.nt, "dt": w.dt, "prec": args.prec,
+            "solver": "Jacobi-PCG, rtol 1e-9 (FP32) / 1e-13 (FP64)",
+            "bc": "zero-flux walls", "forcing": "Gaussian surface pulse, sigma 20 cells, 3 steps",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.send_signal(signal.SIGTERM)
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -------------------------------------------------------------- CPU oracle
+def oracle_sample(args, w, cand, steps):
+    """The FP64 oracle (as it stands) on the first `steps` time steps of the
+    same grid: forward + adjoint gradient.  Returns (Gcell-steps/s, seconds)."""
+    import oracle
+    p = oracle.from_workload(w, nt=steps, loss_scale=1.0 / (w.nt * w.nx * w.ny))
+    obs = oracle.forward(p, w.alpha, q_face=w.q_face, q_steps=w.q_steps)["frames"]
+    t = time.perf_counter()
+    oracle.adjoint_grad(p, cand, q_face=w.q_face, q_steps=w.q_steps, obs=obs)
+    dt = time.perf_counter() - t
+    return w.n_cells * steps / dt / 1e9, dt
+
+
+def cpu_cores():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w, cand = workload(args)
+    steps = max(1, args.cpu_sample_steps)
+    for _ in range(args.warmup):
+        oracle_sample(args, w, cand, steps)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        v, s = oracle_sample(args, w, cand, steps)
+        vals.append(v)
+        secs.append(s)
+    value = w.n_cells * steps * len(secs) / sum(secs) / 1e9
+    sample = f"first {steps} of {w.nt} steps of the same {w.nx}x{w.ny}x{w.nz} grid, forward + adjoint, per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(secs) / len(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(args, w),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ native
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2603_11045_gb300.solver import Problem, Solver
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    w, cand = workload(args)
+    prob = Problem.from_workload(w, prec=args.prec, ckpt_every=args.ckpt_every)
+    dt = prob.torch_dtype
+    solver = Solver(local)
+    q = torch.tensor(w.q_face, dtype=dt, device=dev)
+    # target frames from the field with inclusions (setup, not timed)
+    obs = solver.forward(prob, torch.tensor(w.alpha, dtype=dt, device=dev), q_face=q, q_steps=w.q_steps)["frames"]
+    alpha = torch.tensor(cand, dtype=dt, device=dev)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return solver.adjoint_grad(prob, alpha, obs, q_face=q, q_steps=w.q_steps)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        out = step()
+        ev[k][1].record(stream)
+        stats.append(out["stats"])
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    units = w.n_cells * w.nt * args.steps * world
+    value = units / (max_ms / 1000.0) / 1e9
+
+    # roofline of the fused CG kernel (forward + adjoint + recompute launches)
+    R = args.prec
+    cg_ms = sum(s["fwd_ms"] + s["adj_ms"] + s["recompute_ms"] for s in stats) / len(stats)
+    launches = stats[0]["kernel_launches"]
+    iters = sum(s["fwd_iters"] + s["adj_iters"] + s["recompute_iters"] for s in stats) / len(stats)
+    steps_solved = stats[0]["fwd_steps"] + stats[0]["adj_steps"] + stats[0]["recompute_steps"]
+    alg_bytes = w.n_cells * (iters * ALG_BYTES_ITER[R] + steps_solved * ALG_BYTES_STEP[R])
+    pk = peaks()
+    peak = pk["hbm_gbs"] if pk else 6800.0
+    achieved = alg_bytes / (cg_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "persistent fused Jacobi-PCG (forward_kernel + adjoint_kernel)",
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback",
+                "cg_ms_per_step": cg_ms, "alg_bytes_per_step": alg_bytes,
+                "mean_cg_iters_per_solve": iters / max(1, steps_solved)}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    e2e = None
+    if rank == 0 or world > 1:
+        a_h = alpha.cpu().pin_memory()
+        o_h = obs.cpu().pin_memory()
+        q_h = q.cpu().pin_memory()
+        solver.adjoint_grad(prob, a_h, o_h, q_face=q_h, q_steps=w.q_steps)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            out_h = solver.adjoint_grad(prob, a_h, o_h, q_face=q_h, q_steps=w.q_steps)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        h2d = a_h.numel() * a_h.element_size() + o_h.numel() * o_h.element_size() + q_h.numel() * q_h.element_size()
+        d2h = out_h["grad_alpha"].numel() * out_h["grad_alpha"].element_size() + 8
+        e2e = {"value": w.n_cells * w.nt * world / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        steps = max(1, args.cpu_sample_steps)
+        v, s = oracle_sample(args, w, cand, steps)
+        cpu = {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"first {steps} of {w.nt} steps of the same grid, forward + adjoint, FP64, {s:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if R == "fp32" else "f64",
+                "data": "synthetic", "config": config_dict(args, w), "parallelism": f"replicas x{world}",
+                "gpu_launches": launches * args.steps, "e2e": e2e, "roofline": roofline,
+                "cpu_baseline": cpu, "clocks": clk,
+                "solver_stats": {k: stats[-1][k] for k in ("fwd_iters", "adj_iters", "recompute_iters",
+                                                           "max_step_iters", "max_rel_residual",
+                                                           "ckpt_every", "grid_blocks", "workspace_bytes")}}
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,157 @@
+/*
+ * nefty.h — C ABI of libnefty, the GB300 (sm_103a) hot path of NeFTY
+ * (Neural Field Thermal Tomography): the differentiable 3D implicit-Euler
+ * heat solve, its discrete adjoint and the diffusivity gradient.
+ *
+ * Discretisation (Sec. 4.2 and App. D.2 of the paper):
+ *   grid of nx*ny*nz cells, layout [z][y][x] with x fastest, spacing dx,dy,dz;
+ *   face conductance a_pq = 2 alpha_p alpha_q / (alpha_p + alpha_q) / h_d^2
+ *   (harmonic mean, Prop. 1); L(alpha) the 7-point operator built from them;
+ *   A(alpha) = I - dt L(alpha); each step solves
+ *       A T^{n+1} = T^n + dt * q^n / dz * [k == 0]            (Eq. state_eq)
+ *   by Jacobi-preconditioned conjugate gradients, warm-started from T^n.
+ *   The surface flux q^n (a map on the z = 0 face) is spread over the k = 0
+ *   cell slab; the paper's state equation has no source term (its heat enters
+ *   through the initial condition), so q = 0 and T^0 != 0 reproduces it.
+ * Objective (Eq. nefty_obj):  J = loss_scale * sum_{n=1..nt} ||Pi T^n - obs^n||^2
+ *   with Pi the k = 0 plane (obs_face = 0) or the k = nz-1 plane (obs_face = 1).
+ * Adjoint (Eq. adjoint_eq): A^T mu^n = mu^{n+1} + 2 loss_scale Pi^T (Pi T^n - obs^n),
+ *   mu^{nt+1} = 0; A is symmetric so the same operator is used.
+ * Gradient (Eq. grad_assembly): dJ/dalpha = dt sum_n (d(L T^n)/dalpha)^T mu^n,
+ *   with d a_pq / d alpha_p = 2 alpha_q^2 / (alpha_p + alpha_q)^2 / h_d^2;
+ *   dJ/dT^0 = mu^1 (App. D.3, "Sensitivity to initial conditions").
+ *
+ * Conventions for every call below:
+ *   - Array arguments are plain pointers.  Each may point to device memory or
+ *     to host memory (pageable or pinned); host arrays are copied to the
+ *     device inside the call and host outputs are copied back before return.
+ *   - Element type: float when prec == NEFTY_FP32, double when NEFTY_FP64.
+ *   - The caller owns every array it passes.  The handle owns its workspace
+ *     (operator coefficients, CG vectors, checkpoints), allocated with
+ *     cudaMalloc on first use, reused by later calls, freed by nefty_destroy.
+ *   - Work is issued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream).  Every call returns after its work on `stream` has completed.
+ *   - A handle serves one call at a time; calls on one handle from several
+ *     threads must be serialised by the caller.
+ *   - Errors: argument errors are returned before any work is issued.  A
+ *     device-side failure (a grid barrier that timed out, a CUDA error) is
+ *     returned by the same call.  nefty_last_error() gives a message.
+ */
+#ifndef NEFTY_H
+#define NEFTY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NEFTY_OK = 0,
+    NEFTY_EINVAL = 1,      /* bad argument: sizes, spacing, null pointer, alpha <= 0 or not finite */
+    NEFTY_ENOMEM = 2,      /* workspace does not fit the handle's memory budget or the device */
+    NEFTY_ENOTCONV = 3,    /* some CG solve hit max_iter; outputs are written but less accurate */
+    NEFTY_ECUDA = 4,       /* a CUDA runtime error; see nefty_last_error */
+    NEFTY_ETIMEOUT = 5,    /* a device-side wait exceeded its time limit; outputs are invalid */
+    NEFTY_EBUSY = 6,       /* serving queue full */
+    NEFTY_ECANCELLED = 7,  /* serving job cancelled */
+    NEFTY_ENOTFOUND = 8    /* unknown serving job id */
+} nefty_status;
+
+typedef enum { NEFTY_FP32 = 0, NEFTY_FP64 = 1 } nefty_precision;
+
+typedef enum {
+    NEFTY_BC_NEUMANN = 0,     /* zero-flux walls on all six faces */
+    NEFTY_BC_PERIODIC_XY = 1  /* paper default (App. A.5): periodic in x and y, adiabatic in z */
+} nefty_bc;
+
+/* One heat-inversion problem.  Fields set to 0 take the stated default. */
+typedef struct {
+    int32_t nx, ny, nz;    /* cells, each >= 1, nx*ny*nz < 2^31 */
+    double dx, dy, dz;     /* cell spacing, > 0 */
+    double dt;             /* time step, > 0 */
+    int32_t nt;            /* implicit-Euler steps, >= 1 */
+    int32_t bc;            /* nefty_bc */
+    double robin_h;        /* Robin coefficient h on the k = nz-1 face (App. A.5); 0 = adiabatic */
+    int32_t obs_face;      /* 0: observe k = 0 (the heated face); 1: observe k = nz-1 */
+    int32_t prec;          /* nefty_precision: FP32 = float vectors and stencil, FP64 inner
+                              products and residual norms; FP64 = double throughout */
+    double rtol;           /* CG stop: ||b - A x||_2 <= rtol ||b||_2 (recursive residual);
+                              0 = 1e-9 (FP32) or 1e-13 (FP64) */
+    int32_t max_iter;      /* CG iteration cap per solve; 0 = 1000 */
+    int32_t ckpt_every;    /* adjoint: 0 = automatic (every state kept if it fits the budget,
+                              else a checkpoint every ceil(sqrt(nt)) steps), 1 = keep every
+                              state, K >= 2 = checkpoint every K steps and recompute */
+    double loss_scale;     /* 0 = 1/(nt*nx*ny), i.e. the surface mean-squared error */
+} nefty_problem;
+
+/* Solver statistics of one call. */
+typedef struct {
+    int64_t fwd_iters;          /* CG iterations summed over forward steps */
+    int64_t recompute_iters;    /* CG iterations of forward steps re-run from checkpoints */
+    int64_t adj_iters;          /* CG iterations summed over adjoint steps */
+    int32_t fwd_steps, recompute_steps, adj_steps;
+    int32_t max_step_iters;     /* largest CG iteration count of any solve */
+    int32_t not_converged;      /* solves that hit max_iter */
+    int32_t ckpt_every;         /* checkpoint stride used (1 = every state kept) */
+    int32_t n_checkpoints;      /* states held for the reverse sweep */
+    double max_rel_residual;    /* largest final ||r||/||b|| over all solves */
+    uint64_t workspace_bytes;   /* device workspace held by the handle */
+    int32_t grid_blocks;        /* persistent CTAs of the solver launch */
+    int32_t kernel_launches;    /* library kernels launched by the call */
+    double fwd_ms;              /* device time of the forward-sweep launches (CUDA events) */
+    double recompute_ms;        /* device time of the checkpoint-recompute launches */
+    double adj_ms;              /* device time of the adjoint-sweep launches */
+} nefty_stats;
+
+typedef struct nefty_handle nefty_handle;
+
+/* Create a handle on CUDA device `device`.  mem_budget_bytes caps the
+ * workspace (0 = 90% of the device's free memory at creation).
+ * Returns NEFTY_ECUDA when no usable device is present. */
+nefty_status nefty_create(nefty_handle **out, int device, uint64_t mem_budget_bytes);
+
+/* Free the handle and its workspace.  NULL is accepted. */
+nefty_status nefty_destroy(nefty_handle *h);
+
+/* Message of the last failed call on `h` (or of the calling thread when h is
+ * NULL, e.g. after nefty_create failed).  Never NULL; owned by the library. */
+const char *nefty_last_error(const nefty_handle *h);
+
+/* Static name of a status code. */
+const char *nefty_status_string(nefty_status s);
+
+/* Host-only validation of a problem (no device work): NEFTY_OK or NEFTY_EINVAL. */
+nefty_status nefty_problem_check(const nefty_problem *p);
+
+/* Forward sweep (Eq. state_eq).
+ *   alpha      [nz*ny*nx]  cell diffusivity, every value > 0 and finite.
+ *   T0         [nz*ny*nx]  initial temperature, or NULL for zero.
+ *   q_face     [ny*nx]     surface flux on z = 0 applied for steps n < q_steps, or NULL.
+ *   q_full     [nt*ny*nx]  per-step flux maps (overrides q_face), or NULL.
+ *   frames_out [nt*ny*nx]  Pi T^1 .. Pi T^nt, or NULL.
+ *   T_final    [nz*ny*nx]  T^nt, or NULL.
+ *   obs        [nt*ny*nx]  target frames; with loss_out non-NULL the objective is written.
+ *   loss_out   host double*, or NULL.
+ *   stats      host nefty_stats*, or NULL. */
+nefty_status nefty_forward(nefty_handle *h, const nefty_problem *p, const void *alpha,
+                           const void *T0, const void *q_face, int32_t q_steps, const void *q_full,
+                           void *frames_out, void *T_final, const void *obs, double *loss_out,
+                           nefty_stats *stats, void *stream);
+
+/* Forward sweep, then the reverse-time adjoint (Eq. adjoint_eq) and gradient
+ * assembly (Eq. grad_assembly).  Inputs as in nefty_forward; obs is required.
+ *   grad_alpha [nz*ny*nx]  dJ/dalpha, overwritten.
+ *   grad_T0    [nz*ny*nx]  dJ/dT^0 = mu^1, or NULL.
+ * States for the reverse sweep follow p->ckpt_every. */
+nefty_status nefty_adjoint_grad(nefty_handle *h, const nefty_problem *p, const void *alpha,
+                                const void *T0, const void *q_face, int32_t q_steps,
+                                const void *q_full, const void *obs, double *loss_out,
+                                void *grad_alpha, void *grad_T0, nefty_stats *stats, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NEFTY_H */

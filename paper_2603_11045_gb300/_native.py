@@ -1,0 +1,102 @@
+"""ctypes declarations of libnefty's C ABI (include/nefty.h).
+
+This module only marshals arguments.  The library is loaded from this package
+directory; if it is missing the import of any compute entry point fails with an
+error that says how to build it (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnefty.so")
+
+NEFTY_OK, NEFTY_EINVAL, NEFTY_ENOMEM, NEFTY_ENOTCONV = 0, 1, 2, 3
+NEFTY_ECUDA, NEFTY_ETIMEOUT, NEFTY_EBUSY, NEFTY_ECANCELLED, NEFTY_ENOTFOUND = 4, 5, 6, 7, 8
+NEFTY_FP32, NEFTY_FP64 = 0, 1
+NEFTY_BC_NEUMANN, NEFTY_BC_PERIODIC_XY = 0, 1
+
+
+class nefty_problem(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("dt", ctypes.c_double), ("nt", ctypes.c_int32), ("bc", ctypes.c_int32),
+                ("robin_h", ctypes.c_double), ("obs_face", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("ckpt_every", ctypes.c_int32),
+                ("loss_scale", ctypes.c_double)]
+
+
+class nefty_stats(ctypes.Structure):
+    _fields_ = [("fwd_iters", ctypes.c_int64), ("recompute_iters", ctypes.c_int64),
+                ("adj_iters", ctypes.c_int64), ("fwd_steps", ctypes.c_int32),
+                ("recompute_steps", ctypes.c_int32), ("adj_steps", ctypes.c_int32),
+                ("max_step_iters", ctypes.c_int32), ("not_converged", ctypes.c_int32),
+                ("ckpt_every", ctypes.c_int32), ("n_checkpoints", ctypes.c_int32),
+                ("max_rel_residual", ctypes.c_double), ("workspace_bytes", ctypes.c_uint64),
+                ("grid_blocks", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
+                ("fwd_ms", ctypes.c_double), ("recompute_ms", ctypes.c_double),
+                ("adj_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class NeftyError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{status_name(status)}: {message}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+_vp = ctypes.c_void_p
+_P = ctypes.POINTER(nefty_problem)
+_ST = ctypes.POINTER(nefty_stats)
+_SIGNATURES = {
+    "nefty_create": ([ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_uint64], ctypes.c_int),
+    "nefty_destroy": ([_vp], ctypes.c_int),
+    "nefty_last_error": ([_vp], ctypes.c_char_p),
+    "nefty_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "nefty_problem_check": ([_P], ctypes.c_int),
+    "nefty_forward": ([_vp, _P, _vp, _vp, _vp, ctypes.c_int32, _vp, _vp, _vp, _vp,
+                       ctypes.POINTER(ctypes.c_double), _ST, _vp], ctypes.c_int),
+    "nefty_adjoint_grad": ([_vp, _P, _vp, _vp, _vp, ctypes.c_int32, _vp, _vp,
+                            ctypes.POINTER(ctypes.c_double), _vp, _vp, _ST, _vp], ctypes.c_int),
+}
+
+
+def load():
+    """Load libnefty.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(
+                    f"libnefty.so not found at {LIB_PATH}; build it with "
+                    "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc, sm_103a)")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGNATURES.items():
+                fn = getattr(lib, name, None)
+                if fn is None:
+                    continue
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def status_name(status: int) -> str:
+    try:
+        return load().nefty_status_string(int(status)).decode()
+    except ImportError:
+        return f"status {status}"
+
+
+def check(status: int, handle=None, allow=()):
+    if status == NEFTY_OK or status in allow:
+        return status
+    msg = load().nefty_last_error(handle).decode(errors="replace")
+    raise NeftyError(status, msg)

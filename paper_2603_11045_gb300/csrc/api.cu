@@ -1,0 +1,719 @@
+// C-ABI of libnefty: argument checks, device workspace, host<->device staging,
+// the checkpoint/recompute schedule of the reverse sweep, and the launches of
+// the persistent solver kernels (solver.cu).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "nefty.h"
+
+using namespace nefty;
+
+struct nefty_handle {
+    int device = 0;
+    uint64_t budget = 0;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    int grid_max[2] = {0, 0};
+    std::string err;
+};
+
+static thread_local std::string t_err;
+
+namespace {
+
+nefty_status fail(nefty_handle* h, nefty_status s, const std::string& msg) {
+    if (h) h->err = msg;
+    t_err = msg;
+    return s;
+}
+
+nefty_status cuda_fail(nefty_handle* h, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(h, NEFTY_ECUDA, m);
+}
+
+#define NEFTY_CUDA(h, expr)                                       \
+    do {                                                          \
+        cudaError_t e_ = (expr);                                  \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #expr); \
+    } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Effective problem with defaults filled in.
+struct Prob {
+    int nx, ny, nz, nt, bc, obs_face, prec, max_iter, ckpt_every;
+    double dx, dy, dz, dt, robin_h, rtol, loss_scale;
+    unsigned N, S;
+};
+
+nefty_status check_problem(const nefty_problem* p, Prob* out, std::string* why) {
+    if (!p) { *why = "problem is NULL"; return NEFTY_EINVAL; }
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) { *why = "nx, ny, nz must be >= 1"; return NEFTY_EINVAL; }
+    const double cells = (double)p->nx * p->ny * p->nz;
+    if (cells >= 2147483647.0) { *why = "nx*ny*nz must be < 2^31"; return NEFTY_EINVAL; }
+    if (p->nt < 1) { *why = "nt must be >= 1"; return NEFTY_EINVAL; }
+    if (!(p->dx > 0) || !(p->dy > 0) || !(p->dz > 0) || !std::isfinite(p->dx) ||
+        !std::isfinite(p->dy) || !std::isfinite(p->dz)) {
+        *why = "dx, dy, dz must be positive and finite";
+        return NEFTY_EINVAL;
+    }
+    if (!(p->dt > 0) || !std::isfinite(p->dt)) { *why = "dt must be positive and finite"; return NEFTY_EINVAL; }
+    if (p->bc != NEFTY_BC_NEUMANN && p->bc != NEFTY_BC_PERIODIC_XY) { *why = "unknown bc"; return NEFTY_EINVAL; }
+    if (!(p->robin_h >= 0) || !std::isfinite(p->robin_h)) { *why = "robin_h must be >= 0"; return NEFTY_EINVAL; }
+    if (p->obs_face != 0 && p->obs_face != 1) { *why = "obs_face must be 0 or 1"; return NEFTY_EINVAL; }
+    if (p->prec != NEFTY_FP32 && p->prec != NEFTY_FP64) { *why = "unknown precision"; return NEFTY_EINVAL; }
+    if (p->rtol < 0 || !std::isfinite(p->rtol)) { *why = "rtol must be >= 0"; return NEFTY_EINVAL; }
+    if (p->max_iter < 0) { *why = "max_iter must be >= 0"; return NEFTY_EINVAL; }
+    if (p->ckpt_every < 0) { *why = "ckpt_every must be >= 0"; return NEFTY_EINVAL; }
+    if (p->loss_scale < 0 || !std::isfinite(p->loss_scale)) { *why = "loss_scale must be >= 0"; return NEFTY_EINVAL; }
+    if (out) {
+        out->nx = p->nx; out->ny = p->ny; out->nz = p->nz; out->nt = p->nt; out->bc = p->bc;
+        out->obs_face = p->obs_face; out->prec = p->prec;
+        out->max_iter = p->max_iter > 0 ? p->max_iter : 1000;
+        out->ckpt_every = p->ckpt_every;
+        out->dx = p->dx; out->dy = p->dy; out->dz = p->dz; out->dt = p->dt; out->robin_h = p->robin_h;
+        out->rtol = p->rtol > 0 ? p->rtol : (p->prec == NEFTY_FP32 ? 1e-9 : 1e-13);
+        out->loss_scale = p->loss_scale > 0 ? p->loss_scale : 1.0 / ((double)p->nt * p->nx * p->ny);
+        out->S = (unsigned)p->nx * (unsigned)p->ny;
+        out->N = out->S * (unsigned)p->nz;
+    }
+    return NEFTY_OK;
+}
+
+// Bump allocator over the handle's device workspace.  A first pass with
+// base == nullptr only measures.
+struct Arena {
+    char* base = nullptr;
+    size_t off = 0;
+    void* take(size_t bytes) {
+        off = (off + 255) & ~size_t(255);
+        void* p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    }
+};
+
+nefty_status ensure_workspace(nefty_handle* h, size_t bytes) {
+    if (bytes > h->budget) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "workspace of %zu bytes exceeds the memory budget of %llu bytes", bytes,
+                 (unsigned long long)h->budget);
+        return fail(h, NEFTY_ENOMEM, buf);
+    }
+    if (bytes <= h->ws_bytes) return NEFTY_OK;
+    if (h->ws) {
+        cudaFree(h->ws);
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&h->ws, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->ws = nullptr;
+        char buf[160];
+        snprintf(buf, sizeof buf, "cudaMalloc of %zu workspace bytes failed (%s)", bytes, cudaGetErrorName(e));
+        return fail(h, NEFTY_ENOMEM, buf);
+    }
+    h->ws_bytes = bytes;
+    return NEFTY_OK;
+}
+
+// Input arrays: used in place when on the device, staged into the workspace
+// when on the host.
+struct Input {
+    const void* user = nullptr;
+    size_t bytes = 0;
+    bool stage = false;
+    void* dev = nullptr;
+    void plan(const void* p, size_t b) {
+        user = p;
+        bytes = b;
+        stage = p && !is_device_ptr(p);
+    }
+    void place(Arena& a) {
+        if (!user) { dev = nullptr; return; }
+        if (stage) dev = a.take(bytes);
+        else { a.take(0); dev = const_cast<void*>(user); }
+    }
+};
+
+// Output arrays: written in place when on the device, staged and copied back
+// when on the host.
+struct Output {
+    void* user = nullptr;
+    size_t bytes = 0;
+    bool stage = false;
+    void* dev = nullptr;
+    void plan(void* p, size_t b) {
+        user = p;
+        bytes = b;
+        stage = p && !is_device_ptr(p);
+    }
+    void place(Arena& a) {
+        if (!user) { dev = nullptr; return; }
+        if (stage) dev = a.take(bytes);
+        else { a.take(0); dev = user; }
+    }
+};
+
+int grid_for(nefty_handle* h, int prec, unsigned N) {
+    if (h->grid_max[prec] == 0) h->grid_max[prec] = solver_grid_blocks(h->device, prec);
+    const int gmax = h->grid_max[prec];
+    // about four cells per thread; small grids use few CTAs so that the grid
+    // barriers of the CG loop stay cheap.
+    long want = ((long)N + (long)kThreads * 4 - 1) / ((long)kThreads * 4);
+    if (want < 1) want = 1;
+    return (int)std::min<long>(want, gmax);
+}
+
+template <typename Real>
+OperatorView<Real> make_view(const Prob& P, Real* coef) {
+    OperatorView<Real> v;
+    v.nx = P.nx; v.ny = P.ny; v.nz = P.nz;
+    v.px = P.bc == NEFTY_BC_PERIODIC_XY && P.nx > 1;
+    v.py = P.bc == NEFTY_BC_PERIODIC_XY && P.ny > 1;
+    v.N = P.N; v.S = P.S;
+    v.cx = coef;
+    v.cy = coef + P.N;
+    v.cz = coef + 2 * (size_t)P.N;
+    v.d = coef + 3 * (size_t)P.N;
+    v.dinv = coef + 4 * (size_t)P.N;
+    v.robin = (Real)(P.dt * P.robin_h / P.dz);
+    return v;
+}
+
+// Shared state of one forward / adjoint call.
+template <typename Real>
+struct Call {
+    nefty_handle* h;
+    Prob P;
+    cudaStream_t s;
+    int G;
+    // workspace regions
+    Real* coef = nullptr;
+    Real *r = nullptr, *p = nullptr, *q = nullptr;
+    DevCtl* ctl = nullptr;
+    double* partials = nullptr;
+    double* loss_partials = nullptr;
+    int* iters = nullptr;        // [3][nt]: forward, recompute, adjoint
+    double* resid = nullptr;     // [3][nt]
+    Real** tables = nullptr;
+    Input alpha, T0, qf, qfull, obs;
+    // CUDA events around every solver launch (kind 0 forward, 1 recompute, 2 adjoint)
+    bool timing = false;
+    struct Timed { cudaEvent_t a, b; int kind; };
+    std::vector<Timed> timed;
+    int launches = 0;
+
+    ~Call() {
+        for (auto& t : timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+    }
+
+    void place_common(Arena& a, size_t ntables) {
+        const size_t N = P.N;
+        coef = (Real*)a.take(5 * N * sizeof(Real));
+        r = (Real*)a.take(N * sizeof(Real));
+        p = (Real*)a.take(N * sizeof(Real));
+        q = (Real*)a.take(N * sizeof(Real));
+        ctl = (DevCtl*)a.take(sizeof(DevCtl));
+        partials = (double*)a.take(2 * kMaxRed * (size_t)G * sizeof(double));
+        loss_partials = (double*)a.take((size_t)G * sizeof(double));
+        iters = (int*)a.take(3 * (size_t)P.nt * sizeof(int));
+        resid = (double*)a.take(3 * (size_t)P.nt * sizeof(double));
+        tables = (Real**)a.take(ntables * sizeof(Real*));
+        alpha.place(a); T0.place(a); qf.place(a); qfull.place(a); obs.place(a);
+    }
+
+    nefty_status upload_inputs() {
+        for (Input* in : {&alpha, &T0, &qf, &qfull, &obs})
+            if (in->user && in->stage)
+                NEFTY_CUDA(h, cudaMemcpyAsync(in->dev, in->user, in->bytes, cudaMemcpyHostToDevice, s));
+        NEFTY_CUDA(h, cudaMemsetAsync(ctl, 0, sizeof(DevCtl), s));
+        return NEFTY_OK;
+    }
+
+    // Face values of A(alpha); rejects alpha <= 0 or non-finite.
+    nefty_status coefficients() {
+        Real* c = coef;
+        NEFTY_CUDA(h, launch_coefficients<Real>((const Real*)alpha.dev, P.nx, P.ny, P.nz, P.bc, P.dx,
+                                                P.dy, P.dz, P.dt, P.robin_h, c, c + P.N, c + 2 * (size_t)P.N,
+                                                c + 3 * (size_t)P.N, c + 4 * (size_t)P.N, ctl, s));
+        ++launches;
+        DevCtl hc;
+        NEFTY_CUDA(h, cudaMemcpyAsync(&hc, ctl, sizeof hc, cudaMemcpyDeviceToHost, s));
+        NEFTY_CUDA(h, cudaStreamSynchronize(s));
+        if (hc.err == kDevBadAlpha) return fail(h, NEFTY_EINVAL, "alpha must be > 0 and finite in every cell");
+        return NEFTY_OK;
+    }
+
+    FwdArgs<Real> fwd_args(int n0, int n1, Real* const* src, Real* const* dst, int* it, double* rs) {
+        FwdArgs<Real> a;
+        a.op = make_view<Real>(P, coef);
+        a.r = r; a.p = p; a.q = q;
+        a.n0 = n0; a.n1 = n1;
+        a.src = src; a.dst = dst;
+        a.q_face = (const Real*)qf.dev;
+        a.q_steps = qf.dev ? q_steps : 0;
+        a.q_full = (const Real*)qfull.dev;
+        a.src_scale = P.dt / P.dz;
+        a.obs_off = P.obs_face ? (unsigned)(P.nz - 1) * P.S : 0u;
+        a.obs = nullptr;
+        a.frames = nullptr;
+        a.tol2 = P.rtol * P.rtol;
+        a.max_iter = P.max_iter;
+        a.ctl = ctl;
+        a.partials = partials;
+        a.iters = it;
+        a.resid = rs;
+        a.loss_partials = nullptr;
+        return a;
+    }
+    int q_steps = 0;
+
+    nefty_status begin_timed(int kind, Timed* t) {
+        t->kind = kind;
+        t->a = t->b = nullptr;
+        if (!timing) return NEFTY_OK;
+        NEFTY_CUDA(h, cudaEventCreate(&t->a));
+        NEFTY_CUDA(h, cudaEventCreate(&t->b));
+        NEFTY_CUDA(h, cudaEventRecord(t->a, s));
+        return NEFTY_OK;
+    }
+    nefty_status end_timed(Timed& t) {
+        ++launches;
+        if (!timing) return NEFTY_OK;
+        NEFTY_CUDA(h, cudaEventRecord(t.b, s));
+        timed.push_back(t);
+        return NEFTY_OK;
+    }
+    nefty_status launch_fwd(const FwdArgs<Real>& a, int kind = 0) {
+        NEFTY_CUDA(h, cudaMemsetAsync(&ctl->bar, 0, sizeof(unsigned), s));
+        Timed t;
+        if (nefty_status e = begin_timed(kind, &t)) return e;
+        NEFTY_CUDA(h, launch_forward<Real>(a, G, s));
+        return end_timed(t);
+    }
+    nefty_status launch_adj(const AdjArgs<Real>& a) {
+        NEFTY_CUDA(h, cudaMemsetAsync(&ctl->bar, 0, sizeof(unsigned), s));
+        Timed t;
+        if (nefty_status e = begin_timed(2, &t)) return e;
+        NEFTY_CUDA(h, launch_adjoint<Real>(a, G, s));
+        return end_timed(t);
+    }
+
+    // Wait for the stream, then turn the device control word into a status.
+    nefty_status finish(double* loss_out, bool want_loss, nefty_stats* st, int fwd_steps,
+                        int rec_steps, int adj_steps, int K, int nck) {
+        NEFTY_CUDA(h, cudaStreamSynchronize(s));
+        DevCtl hc;
+        NEFTY_CUDA(h, cudaMemcpy(&hc, ctl, sizeof hc, cudaMemcpyDeviceToHost));
+        if (hc.err == kDevTimeout)
+            return fail(h, NEFTY_ETIMEOUT, "a grid barrier of the persistent solver timed out");
+        if (want_loss && loss_out) {
+            std::vector<double> lp(G);
+            NEFTY_CUDA(h, cudaMemcpy(lp.data(), loss_partials, G * sizeof(double), cudaMemcpyDeviceToHost));
+            double t = 0.0;
+            for (int b = 0; b < G; ++b) t += lp[b];
+            *loss_out = P.loss_scale * t;
+        }
+        if (st) {
+            std::memset(st, 0, sizeof *st);
+            const size_t nt = (size_t)P.nt;
+            std::vector<int> it(3 * nt);
+            std::vector<double> rs(3 * nt);
+            NEFTY_CUDA(h, cudaMemcpy(it.data(), iters, it.size() * sizeof(int), cudaMemcpyDeviceToHost));
+            NEFTY_CUDA(h, cudaMemcpy(rs.data(), resid, rs.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            const int counts[3] = {fwd_steps, rec_steps, adj_steps};
+            int64_t tot[3] = {0, 0, 0};
+            for (int k = 0; k < 3; ++k)
+                for (int i = 0; i < counts[k]; ++i) {
+                    tot[k] += it[k * nt + i];
+                    st->max_step_iters = std::max(st->max_step_iters, it[k * nt + i]);
+                    st->max_rel_residual = std::max(st->max_rel_residual, rs[k * nt + i]);
+                }
+            st->fwd_iters = tot[0]; st->recompute_iters = tot[1]; st->adj_iters = tot[2];
+            st->fwd_steps = fwd_steps; st->recompute_steps = rec_steps; st->adj_steps = adj_steps;
+            st->not_converged = hc.notconv;
+            st->ckpt_every = K;
+            st->n_checkpoints = nck;
+            st->workspace_bytes = h->ws_bytes;
+            st->grid_blocks = G;
+            st->kernel_launches = launches;
+            double ms[3] = {0.0, 0.0, 0.0};
+            for (auto& t : timed) {
+                float v = 0.f;
+                NEFTY_CUDA(h, cudaEventElapsedTime(&v, t.a, t.b));
+                ms[t.kind] += v;
+            }
+            st->fwd_ms = ms[0];
+            st->recompute_ms = ms[1];
+            st->adj_ms = ms[2];
+        }
+        if (hc.notconv > 0) {
+            char buf[128];
+            snprintf(buf, sizeof buf, "%d CG solve(s) reached max_iter = %d", hc.notconv, P.max_iter);
+            return fail(h, NEFTY_ENOTCONV, buf);
+        }
+        return NEFTY_OK;
+    }
+};
+
+template <typename Real>
+nefty_status run_forward(nefty_handle* h, const Prob& P, const void* alpha, const void* T0,
+                         const void* q_face, int q_steps, const void* q_full, void* frames_out,
+                         void* T_final, const void* obs, double* loss_out, nefty_stats* st,
+                         cudaStream_t s) {
+    const size_t N = P.N, S = P.S, nt = (size_t)P.nt, R = sizeof(Real);
+    Call<Real> C;
+    C.h = h; C.P = P; C.s = s; C.q_steps = q_steps;
+    C.timing = st != nullptr;
+    C.G = grid_for(h, P.prec, P.N);
+    if (C.G <= 0) return fail(h, NEFTY_ECUDA, "cannot size the persistent solver grid on this device");
+    C.alpha.plan(alpha, N * R);
+    C.T0.plan(T0, N * R);
+    C.qf.plan(q_face, S * R);
+    C.qfull.plan(q_full, nt * S * R);
+    C.obs.plan(loss_out ? obs : nullptr, nt * S * R);
+    Output fr, tf;
+    fr.plan(frames_out, nt * S * R);
+    tf.plan(T_final, N * R);
+    Real *work[2], *t0buf = nullptr;
+    auto layout = [&](Arena& a) {
+        C.place_common(a, 2 * nt);
+        work[0] = (Real*)a.take(N * R);
+        work[1] = (Real*)a.take(N * R);
+        t0buf = (Real*)a.take(C.T0.user ? 0 : N * R);
+        fr.place(a);
+        tf.place(a);
+    };
+    Arena probe;
+    layout(probe);
+    if (nefty_status e = ensure_workspace(h, probe.off)) return e;
+    Arena arena;
+    arena.base = (char*)h->ws;
+    layout(arena);
+    if (nefty_status e = C.upload_inputs()) return e;
+    if (nefty_status e = C.coefficients()) return e;
+    const Real* T0dev = C.T0.user ? (const Real*)C.T0.dev : t0buf;
+    if (!C.T0.user) NEFTY_CUDA(h, cudaMemsetAsync(t0buf, 0, N * R, s));
+    // step n reads src[n], writes dst[n]; states alternate between two buffers
+    std::vector<Real*> tab(2 * nt);
+    for (size_t n = 0; n < nt; ++n) {
+        tab[n] = n == 0 ? const_cast<Real*>(T0dev) : work[(n - 1) & 1];
+        tab[nt + n] = work[n & 1];
+    }
+    NEFTY_CUDA(h, cudaMemcpyAsync(C.tables, tab.data(), tab.size() * sizeof(Real*), cudaMemcpyHostToDevice, s));
+    FwdArgs<Real> a = C.fwd_args(0, P.nt, C.tables, C.tables + nt, C.iters, C.resid);
+    a.frames = (Real*)fr.dev;
+    a.obs = (const Real*)C.obs.dev;
+    a.loss_partials = C.loss_partials;
+    if (nefty_status e = C.launch_fwd(a)) return e;
+    if (tf.user) NEFTY_CUDA(h, cudaMemcpyAsync(tf.dev, work[(nt - 1) & 1], N * R, cudaMemcpyDeviceToDevice, s));
+    for (Output* o : {&fr, &tf})
+        if (o->user && o->stage)
+            NEFTY_CUDA(h, cudaMemcpyAsync(o->user, o->dev, o->bytes, cudaMemcpyDeviceToHost, s));
+    return C.finish(loss_out, true, st, P.nt, 0, 0, 1, 2);
+}
+
+// Checkpoint stride of the reverse sweep: 1 keeps every state.
+int choose_stride(const Prob& P, size_t fixed_bytes, uint64_t budget) {
+    if (P.ckpt_every >= 1) return std::min(P.ckpt_every, P.nt);
+    const size_t state = (size_t)P.N * (P.prec == NEFTY_FP32 ? 4 : 8);
+    const size_t all = (size_t)(P.nt + 1) * state + fixed_bytes;
+    if (all <= budget) return 1;
+    int K = (int)std::ceil(std::sqrt((double)P.nt));
+    return std::max(K, 2);
+}
+
+template <typename Real>
+nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, const void* T0,
+                         const void* q_face, int q_steps, const void* q_full, const void* obs,
+                         double* loss_out, void* grad_alpha, void* grad_T0, nefty_stats* st,
+                         cudaStream_t s) {
+    const size_t N = P.N, S = P.S, nt = (size_t)P.nt, R = sizeof(Real);
+    Call<Real> C;
+    C.h = h; C.P = P; C.s = s; C.q_steps = q_steps;
+    C.timing = st != nullptr;
+    C.G = grid_for(h, P.prec, P.N);
+    if (C.G <= 0) return fail(h, NEFTY_ECUDA, "cannot size the persistent solver grid on this device");
+    C.alpha.plan(alpha, N * R);
+    C.T0.plan(T0, N * R);
+    C.qf.plan(q_face, S * R);
+    C.qfull.plan(q_full, nt * S * R);
+    C.obs.plan(obs, nt * S * R);
+    Output ga, gt;
+    ga.plan(grad_alpha, N * R);
+    gt.plan(grad_T0, N * R);
+
+    // Fixed part of the workspace (everything except stored states).
+    size_t fixed = 0;
+    {
+        Arena a;
+        C.place_common(a, 6 * nt + 4);
+        a.take(2 * N * R);        // mu
+        a.take(N * sizeof(double));
+        ga.place(a);
+        gt.place(a);
+        fixed = a.off;
+    }
+    const int K = choose_stride(P, fixed, h->budget);
+    // every state kept: the reverse sweep is one segment [0, nt]
+    const int nseg = K == 1 ? 1 : (P.nt + K - 1) / K;
+    const int seg_len = K == 1 ? P.nt : K;
+    // K == 1: states[0..nt]; K >= 2: checkpoints at n = 0, K, 2K, ... (< nt),
+    // two forward work buffers, and a recompute buffer of K states.
+    const int nck = K == 1 ? P.nt + 1 : nseg;
+    const int nseg_buf = K == 1 ? 0 : K;
+    Real* mu[2];
+    double* grad = nullptr;
+    std::vector<Real*> ck(nck), segbuf(nseg_buf);
+    Real* work[2] = {nullptr, nullptr};
+    auto layout = [&](Arena& a) {
+        C.place_common(a, 6 * nt + 4);
+        mu[0] = (Real*)a.take(N * R);
+        mu[1] = (Real*)a.take(N * R);
+        grad = (double*)a.take(N * sizeof(double));
+        ga.place(a);
+        gt.place(a);
+        for (int i = 0; i < nck; ++i) ck[i] = (Real*)a.take(N * R);
+        for (int i = 0; i < nseg_buf; ++i) segbuf[i] = (Real*)a.take(N * R);
+        if (K > 1) {
+            work[0] = (Real*)a.take(N * R);
+            work[1] = (Real*)a.take(N * R);
+        }
+    };
+    Arena probe;
+    layout(probe);
+    if (nefty_status e = ensure_workspace(h, probe.off)) return e;
+    Arena arena;
+    arena.base = (char*)h->ws;
+    layout(arena);
+    if (nefty_status e = C.upload_inputs()) return e;
+    if (nefty_status e = C.coefficients()) return e;
+    if (C.T0.user) NEFTY_CUDA(h, cudaMemcpyAsync(ck[0], C.T0.dev, N * R, cudaMemcpyDeviceToDevice, s));
+    else NEFTY_CUDA(h, cudaMemsetAsync(ck[0], 0, N * R, s));
+    NEFTY_CUDA(h, cudaMemsetAsync(grad, 0, N * sizeof(double), s));
+
+    // Pointer tables: forward src/dst (2 nt), recompute src/dst (2 nt), adjoint T (nt + nseg).
+    std::vector<Real*> tab(6 * nt + 4, nullptr);
+    Real** F_src = tab.data();
+    Real** F_dst = tab.data() + nt;
+    Real** R_src = tab.data() + 2 * nt;
+    Real** R_dst = tab.data() + 3 * nt;
+    Real** A_T = tab.data() + 4 * nt;
+    auto state_fwd = [&](int n) -> Real* {   // where the first sweep keeps T^n
+        if (K == 1) return ck[n];
+        if (n % K == 0 && n / K < nseg) return ck[n / K];
+        return work[n & 1];
+    };
+    for (int n = 0; n < P.nt; ++n) {
+        F_src[n] = state_fwd(n);
+        F_dst[n] = state_fwd(n + 1);
+    }
+    // segment g covers steps [g K, min(g K + K, nt)]; its recomputed states
+    // T^{gK+j} go to segbuf[j-1], j = 1..len; T^{gK} is checkpoint g.
+    size_t aoff = 0;
+    std::vector<size_t> seg_aoff(nseg);
+    for (int g = 0; g < nseg; ++g) {
+        const int a0 = g * seg_len, a1 = std::min(a0 + seg_len, P.nt);
+        seg_aoff[g] = aoff;
+        for (int n = a0; n <= a1; ++n) {
+            Real* Tn = (K == 1) ? ck[n] : (n == a0 ? ck[g] : segbuf[n - a0 - 1]);
+            A_T[aoff + (n - a0)] = Tn;
+        }
+        aoff += (size_t)(a1 - a0 + 1);
+        if (K > 1)
+            for (int n = a0; n < a1; ++n) {
+                R_src[n] = n == a0 ? ck[g] : segbuf[n - a0 - 1];
+                R_dst[n] = segbuf[n - a0];
+            }
+    }
+    NEFTY_CUDA(h, cudaMemcpyAsync(C.tables, tab.data(), tab.size() * sizeof(Real*), cudaMemcpyHostToDevice, s));
+    Real** dF_src = C.tables;
+    Real** dF_dst = C.tables + nt;
+    Real** dR_src = C.tables + 2 * nt;
+    Real** dR_dst = C.tables + 3 * nt;
+    Real** dA_T = C.tables + 4 * nt;
+
+    // forward sweep with the loss
+    FwdArgs<Real> fa = C.fwd_args(0, P.nt, dF_src, dF_dst, C.iters, C.resid);
+    fa.obs = (const Real*)C.obs.dev;
+    fa.loss_partials = C.loss_partials;
+    if (nefty_status e = C.launch_fwd(fa)) return e;
+
+    // reverse sweep, one segment at a time
+    NEFTY_CUDA(h, cudaMemsetAsync(mu[(P.nt + 1) & 1], 0, N * R, s));
+    int rec_steps = 0, adj_steps = 0;
+    AdjArgs<Real> aa;
+    aa.op = make_view<Real>(P, C.coef);
+    aa.r = C.r; aa.p = C.p; aa.q = C.q;
+    aa.mu[0] = mu[0]; aa.mu[1] = mu[1];
+    aa.alpha = (const Real*)C.alpha.dev;
+    aa.wx = 2.0 * P.dt / (P.dx * P.dx);
+    aa.wy = 2.0 * P.dt / (P.dy * P.dy);
+    aa.wz = 2.0 * P.dt / (P.dz * P.dz);
+    aa.g_scale = 2.0 * P.loss_scale;
+    aa.obs_off = P.obs_face ? (unsigned)(P.nz - 1) * P.S : 0u;
+    aa.obs = (const Real*)C.obs.dev;
+    aa.grad = grad;
+    aa.tol2 = P.rtol * P.rtol;
+    aa.max_iter = P.max_iter;
+    aa.ctl = C.ctl;
+    aa.partials = C.partials;
+    for (int g = nseg - 1; g >= 0; --g) {
+        const int a0 = g * seg_len, a1 = std::min(a0 + seg_len, P.nt);
+        if (K > 1) {
+            FwdArgs<Real> ra = C.fwd_args(a0, a1, dR_src + a0, dR_dst + a0, C.iters + nt + rec_steps,
+                                          C.resid + nt + rec_steps);
+            if (nefty_status e = C.launch_fwd(ra, 1)) return e;
+            rec_steps += a1 - a0;
+        }
+        aa.n0 = a0;
+        aa.n1 = a1;
+        aa.T = dA_T + seg_aoff[g];
+        aa.iters = C.iters + 2 * nt + adj_steps;
+        aa.resid = C.resid + 2 * nt + adj_steps;
+        if (nefty_status e = C.launch_adj(aa)) return e;
+        adj_steps += a1 - a0;
+    }
+    NEFTY_CUDA(h, launch_cast<Real>(grad, (Real*)ga.dev, P.N, s));
+    ++C.launches;
+    if (gt.user) NEFTY_CUDA(h, cudaMemcpyAsync(gt.dev, mu[1], N * R, cudaMemcpyDeviceToDevice, s));
+    for (Output* o : {&ga, &gt})
+        if (o->user && o->stage)
+            NEFTY_CUDA(h, cudaMemcpyAsync(o->user, o->dev, o->bytes, cudaMemcpyDeviceToHost, s));
+    return C.finish(loss_out, true, st, P.nt, rec_steps, adj_steps, K, nck + nseg_buf);
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+const char* nefty_status_string(nefty_status s) {
+    switch (s) {
+        case NEFTY_OK: return "NEFTY_OK";
+        case NEFTY_EINVAL: return "NEFTY_EINVAL";
+        case NEFTY_ENOMEM: return "NEFTY_ENOMEM";
+        case NEFTY_ENOTCONV: return "NEFTY_ENOTCONV";
+        case NEFTY_ECUDA: return "NEFTY_ECUDA";
+        case NEFTY_ETIMEOUT: return "NEFTY_ETIMEOUT";
+        case NEFTY_EBUSY: return "NEFTY_EBUSY";
+        case NEFTY_ECANCELLED: return "NEFTY_ECANCELLED";
+        case NEFTY_ENOTFOUND: return "NEFTY_ENOTFOUND";
+    }
+    return "NEFTY_UNKNOWN";
+}
+
+const char* nefty_last_error(const nefty_handle* h) {
+    if (h) return h->err.c_str();
+    return t_err.c_str();
+}
+
+nefty_status nefty_problem_check(const nefty_problem* p) {
+    std::string why;
+    nefty_status s = check_problem(p, nullptr, &why);
+    if (s) t_err = why;
+    return s;
+}
+
+nefty_status nefty_create(nefty_handle** out, int device, uint64_t mem_budget_bytes) {
+    if (!out) return fail(nullptr, NEFTY_EINVAL, "out is NULL");
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        return fail(nullptr, NEFTY_ECUDA, std::string("no CUDA device: ") + cudaGetErrorName(e));
+    }
+    if (device < 0 || device >= count) return fail(nullptr, NEFTY_EINVAL, "device index out of range");
+    DeviceGuard guard(device);
+    size_t free_b = 0, total_b = 0;
+    e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaMemGetInfo");
+    nefty_handle* h = new nefty_handle();
+    h->device = device;
+    h->budget = mem_budget_bytes ? mem_budget_bytes : (uint64_t)(0.9 * (double)free_b);
+    *out = h;
+    return NEFTY_OK;
+}
+
+nefty_status nefty_destroy(nefty_handle* h) {
+    if (!h) return NEFTY_OK;
+    {
+        DeviceGuard guard(h->device);
+        if (h->ws) cudaFree(h->ws);
+    }
+    delete h;
+    return NEFTY_OK;
+}
+
+nefty_status nefty_forward(nefty_handle* h, const nefty_problem* p, const void* alpha, const void* T0,
+                           const void* q_face, int32_t q_steps, const void* q_full, void* frames_out,
+                           void* T_final, const void* obs, double* loss_out, nefty_stats* stats,
+                           void* stream) {
+    if (!h) return fail(nullptr, NEFTY_EINVAL, "handle is NULL");
+    Prob P;
+    std::string why;
+    if (check_problem(p, &P, &why)) return fail(h, NEFTY_EINVAL, why);
+    if (!alpha) return fail(h, NEFTY_EINVAL, "alpha is NULL");
+    if (loss_out && !obs) return fail(h, NEFTY_EINVAL, "loss_out needs obs");
+    if (q_steps < 0) return fail(h, NEFTY_EINVAL, "q_steps must be >= 0");
+    DeviceGuard guard(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (P.prec == NEFTY_FP32)
+        return run_forward<float>(h, P, alpha, T0, q_face, q_steps, q_full, frames_out, T_final, obs,
+                                  loss_out, stats, s);
+    return run_forward<double>(h, P, alpha, T0, q_face, q_steps, q_full, frames_out, T_final, obs,
+                               loss_out, stats, s);
+}
+
+nefty_status nefty_adjoint_grad(nefty_handle* h, const nefty_problem* p, const void* alpha,
+                                const void* T0, const void* q_face, int32_t q_steps,
+                                const void* q_full, const void* obs, double* loss_out,
+                                void* grad_alpha, void* grad_T0, nefty_stats* stats, void* stream) {
+    if (!h) return fail(nullptr, NEFTY_EINVAL, "handle is NULL");
+    Prob P;
+    std::string why;
+    if (check_problem(p, &P, &why)) return fail(h, NEFTY_EINVAL, why);
+    if (!alpha || !obs || !grad_alpha) return fail(h, NEFTY_EINVAL, "alpha, obs and grad_alpha are required");
+    if (q_steps < 0) return fail(h, NEFTY_EINVAL, "q_steps must be >= 0");
+    DeviceGuard guard(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (P.prec == NEFTY_FP32)
+        return run_adjoint<float>(h, P, alpha, T0, q_face, q_steps, q_full, obs, loss_out, grad_alpha,
+                                  grad_T0, stats, s);
+    return run_adjoint<double>(h, P, alpha, T0, q_face, q_steps, q_full, obs, loss_out, grad_alpha,
+                               grad_T0, stats, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+// Internal interface between the C-ABI layer (api.cu) and the solver kernels
+// (solver.cu).  Not installed; callers use include/nefty.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nefty {
+
+// Threads per CTA of the persistent solver kernels.
+constexpr int kThreads = 512;
+// Maximum number of values reduced together across the grid.
+constexpr int kMaxRed = 3;
+// Device-side wait limit of a grid barrier (nanoseconds of %globaltimer).
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;
+
+// Device error word values.
+enum DevError : int { kDevOk = 0, kDevTimeout = 1, kDevBadAlpha = 2 };
+
+// Shared control block of one persistent launch (device memory, zeroed by the
+// host before each launch except `err`, which persists over a call).
+struct DevCtl {
+    unsigned int bar;      // grid-barrier arrival counter
+    int err;               // DevError of the call
+    int notconv;           // number of solves that hit max_iter
+    int pad;
+};
+
+// Grid geometry and the precomputed operator of A(alpha) = I - dt L(alpha).
+template <typename Real>
+struct OperatorView {
+    int nx, ny, nz;
+    int px, py;            // lateral wrap active along x / y (periodic and extent > 1)
+    unsigned N, S;         // cells, cells per z-plane
+    const Real* cx;        // dt * a of the +x face of every cell (0 on a zero-flux wall)
+    const Real* cy;
+    const Real* cz;
+    const Real* d;         // diagonal of A: 1 + sum of the six face values (+ dt*h/dz)
+    const Real* dinv;      // 1 / d (Jacobi preconditioner)
+    Real robin;            // dt * h / dz on the k = nz-1 cells (0 without a Robin face)
+};
+
+// Arguments of the forward persistent kernel: steps n in [n0, n1).
+template <typename Real>
+struct FwdArgs {
+    OperatorView<Real> op;
+    Real* r; Real* p; Real* q;         // CG work vectors
+    int n0, n1;
+    Real* const* src;                  // src[n - n0] = T^n
+    Real* const* dst;                  // dst[n - n0] = T^{n+1} (written)
+    const Real* q_face; int q_steps;   // flux map applied for n < q_steps
+    const Real* q_full;                // per-step flux maps (overrides q_face)
+    double src_scale;                  // dt / dz
+    unsigned obs_off;                  // first cell of the observed plane
+    const Real* obs;                   // target frames [nt][S] or null
+    Real* frames;                      // Pi T^{n+1} -> frames[n] or null
+    double tol2;                       // rtol^2
+    int max_iter;
+    DevCtl* ctl;
+    double* partials;                  // [2][kMaxRed][G]
+    int* iters;                        // per-step CG iterations [n1 - n0]
+    double* resid;                     // per-step final ||r||/||b||
+    double* loss_partials;             // [G] per-CTA sum of squared frame errors
+};
+
+// Arguments of the adjoint persistent kernel: steps n = n1 down to n0 + 1.
+template <typename Real>
+struct AdjArgs {
+    OperatorView<Real> op;
+    Real* r; Real* p; Real* q;
+    int n0, n1;
+    Real* const* T;                    // T[n - n0] = T^n, n in [n0, n1]
+    Real* mu[2];                       // mu^n lives in mu[n & 1]
+    const Real* alpha;
+    double wx, wy, wz;                 // 2 dt / h_d^2 (harmonic-mean derivative weights)
+    double g_scale;                    // 2 * loss_scale
+    unsigned obs_off;
+    const Real* obs;                   // [nt][S]
+    double* grad;                      // dJ/dalpha accumulator (FP64)
+    double tol2;
+    int max_iter;
+    DevCtl* ctl;
+    double* partials;
+    int* iters;                        // per-step iterations, index n1 - n
+    double* resid;
+};
+
+// Launch helpers (solver.cu).  All are stream-ordered.
+int solver_grid_blocks(int device, int prec);
+template <typename Real>
+cudaError_t launch_coefficients(const Real* alpha, int nx, int ny, int nz, int bc, double dx,
+                                double dy, double dz, double dt, double robin_h, Real* cx,
+                                Real* cy, Real* cz, Real* d, Real* dinv, DevCtl* ctl,
+                                cudaStream_t s);
+template <typename Real>
+cudaError_t launch_forward(const FwdArgs<Real>& a, int grid, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_adjoint(const AdjArgs<Real>& a, int grid, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_cast(const double* in, Real* out, unsigned n, cudaStream_t s);
+
+}  // namespace nefty
