@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -21,6 +22,7 @@ struct nefty_handle {
     void* ws = nullptr;
     size_t ws_bytes = 0;
     int grid_max[2] = {0, 0};
+    int grid_tiled = 0;
     std::string err;
 };
 
@@ -195,6 +197,15 @@ int grid_for(nefty_handle* h, int prec, unsigned N) {
     return (int)std::min<long>(want, gmax);
 }
 
+int grid_for_tiled(nefty_handle* h, const Prob& P) {
+    if (h->grid_tiled == 0) h->grid_tiled = tiled_grid_blocks(h->device);
+    const long tiles = (long)((P.nx + tiled::TX - 1) / tiled::TX) * ((P.ny + tiled::TY - 1) / tiled::TY);
+    const long units = tiles * P.nz;
+    // at least two planes per CTA, so small grids keep their barriers cheap
+    long want = std::max(1L, units / 2);
+    return (int)std::min<long>(want, h->grid_tiled);
+}
+
 template <typename Real>
 OperatorView<Real> make_view(const Prob& P, Real* coef) {
     OperatorView<Real> v;
@@ -238,12 +249,27 @@ struct Call {
         for (auto& t : timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
     }
 
+    static constexpr bool kTiled = std::is_same<Real, float>::value;
+    tiled::Vecs tv{};
+    tiled::TmaMaps* tmaps = nullptr;   // device copy (TMA-staged iterations), or null
+
     void place_common(Arena& a, size_t ntables) {
         const size_t N = P.N;
         coef = (Real*)a.take(5 * N * sizeof(Real));
-        r = (Real*)a.take(N * sizeof(Real));
-        p = (Real*)a.take(N * sizeof(Real));
-        q = (Real*)a.take(N * sizeof(Real));
+        if (kTiled) {
+            for (int i = 0; i < 2; ++i) {
+                tv.u[i] = (float*)a.take(N * sizeof(float));
+                tv.ws[i] = (float*)a.take(N * sizeof(float));
+                tv.ss[i] = (float*)a.take(N * sizeof(float));
+            }
+            tv.p = (float*)a.take(N * sizeof(float));
+            tv.delta = (float*)a.take(N * sizeof(float));
+            tmaps = (tiled::TmaMaps*)a.take(sizeof(tiled::TmaMaps));
+        } else {
+            r = (Real*)a.take(N * sizeof(Real));
+            p = (Real*)a.take(N * sizeof(Real));
+            q = (Real*)a.take(N * sizeof(Real));
+        }
         ctl = (DevCtl*)a.take(sizeof(DevCtl));
         partials = (double*)a.take(2 * kMaxRed * (size_t)G * sizeof(double));
         loss_partials = (double*)a.take((size_t)G * sizeof(double));
@@ -258,6 +284,25 @@ struct Call {
             if (in->user && in->stage)
                 NEFTY_CUDA(h, cudaMemcpyAsync(in->dev, in->user, in->bytes, cudaMemcpyHostToDevice, s));
         NEFTY_CUDA(h, cudaMemsetAsync(ctl, 0, sizeof(DevCtl), s));
+        return NEFTY_OK;
+    }
+
+    // TMA-staged iterations serve zero-flux lateral walls with a 16-byte row
+    // pitch; other grids take the plain-load pass.
+    bool use_tma = false;
+    nefty_status prepare_tma() {
+        if constexpr (kTiled) {
+            if (P.bc != NEFTY_BC_NEUMANN || P.nx % 4 != 0) return NEFTY_OK;
+            tiled::TmaMaps host;
+            tiled::Geo g{};
+            g.nx = P.nx; g.ny = P.ny; g.nz = P.nz; g.S = P.S;
+            if (!tiled_encode_maps(&host, g, tv.u, tv.ws, tv.ss, tv.p, tv.delta, (const float*)coef,
+                                   (const float*)coef + P.N, (const float*)coef + 2 * (size_t)P.N))
+                return NEFTY_OK;
+            NEFTY_CUDA(h, cudaMemcpyAsync(tmaps, &host, sizeof host, cudaMemcpyHostToDevice, s));
+            NEFTY_CUDA(h, cudaStreamSynchronize(s));
+            use_tma = true;
+        }
         return NEFTY_OK;
     }
 
@@ -321,6 +366,67 @@ struct Call {
         if (nefty_status e = begin_timed(kind, &t)) return e;
         NEFTY_CUDA(h, launch_forward<Real>(a, G, s));
         return end_timed(t);
+    }
+    tiled::Common tiled_common(int* it, double* rs) {
+        tiled::Common c{};
+        c.g.nx = P.nx; c.g.ny = P.ny; c.g.nz = P.nz;
+        c.g.px = P.bc == NEFTY_BC_PERIODIC_XY && P.nx > 1;
+        c.g.py = P.bc == NEFTY_BC_PERIODIC_XY && P.ny > 1;
+        c.g.S = P.S;
+        c.g.tiles_x = (P.nx + tiled::TX - 1) / tiled::TX;
+        c.g.units = (unsigned)(c.g.tiles_x * ((P.ny + tiled::TY - 1) / tiled::TY)) * (unsigned)P.nz;
+        c.maps = use_tma ? tmaps : nullptr;
+        c.cx = (const float*)coef;
+        c.cy = (const float*)coef + P.N;
+        c.cz = (const float*)coef + 2 * (size_t)P.N;
+        c.robin = (float)(P.dt * P.robin_h / P.dz);
+        c.v = tv;
+        c.ctl = ctl;
+        c.partials = partials;
+        c.tol2 = P.rtol * P.rtol;
+        c.max_iter = P.max_iter;
+        c.iters = it;
+        c.resid = rs;
+        return c;
+    }
+    nefty_status launch_fwd_tiled(const tiled::FwdTiled& a, int kind) {
+        NEFTY_CUDA(h, cudaMemsetAsync(&ctl->bar, 0, sizeof(unsigned), s));
+        Timed t;
+        if (nefty_status e = begin_timed(kind, &t)) return e;
+        NEFTY_CUDA(h, launch_forward_tiled(a, G, s));
+        return end_timed(t);
+    }
+    nefty_status launch_adj_tiled(const tiled::AdjTiled& a) {
+        NEFTY_CUDA(h, cudaMemsetAsync(&ctl->bar, 0, sizeof(unsigned), s));
+        Timed t;
+        if (nefty_status e = begin_timed(2, &t)) return e;
+        NEFTY_CUDA(h, launch_adjoint_tiled(a, G, s));
+        return end_timed(t);
+    }
+    // forward launch over steps [n0, n1) with either kernel family
+    nefty_status forward_steps(int n0, int n1, Real* const* src, Real* const* dst, int* it, double* rs,
+                               Real* frames, const Real* obsp, double* lossp, int kind) {
+        if constexpr (kTiled) {
+            tiled::FwdTiled a{};
+            a.c = tiled_common(it, rs);
+            a.n0 = n0; a.n1 = n1;
+            a.src = src; a.dst = dst;
+            a.q_face = (const float*)qf.dev;
+            a.q_steps = qf.dev ? q_steps : 0;
+            a.q_full = (const float*)qfull.dev;
+            a.src_scale = (float)(P.dt / P.dz);
+            a.obs_off = P.obs_face ? (unsigned)(P.nz - 1) * P.S : 0u;
+            a.obs = obsp;
+            a.frames = frames;
+            a.loss_partials = lossp;
+            return launch_fwd_tiled(a, kind);
+        } else {
+            FwdArgs<Real> a = fwd_args(n0, n1, src, dst, it, rs);
+            a.frames = frames;
+            a.obs = obsp;
+            a.loss_partials = lossp;
+            return launch_fwd(a, kind);
+        }
     }
     nefty_status launch_adj(const AdjArgs<Real>& a) {
         NEFTY_CUDA(h, cudaMemsetAsync(&ctl->bar, 0, sizeof(unsigned), s));
@@ -396,7 +502,7 @@ nefty_status run_forward(nefty_handle* h, const Prob& P, const void* alpha, cons
     Call<Real> C;
     C.h = h; C.P = P; C.s = s; C.q_steps = q_steps;
     C.timing = st != nullptr;
-    C.G = grid_for(h, P.prec, P.N);
+    C.G = Call<Real>::kTiled ? grid_for_tiled(h, P) : grid_for(h, P.prec, P.N);
     if (C.G <= 0) return fail(h, NEFTY_ECUDA, "cannot size the persistent solver grid on this device");
     C.alpha.plan(alpha, N * R);
     C.T0.plan(T0, N * R);
@@ -423,6 +529,7 @@ nefty_status run_forward(nefty_handle* h, const Prob& P, const void* alpha, cons
     layout(arena);
     if (nefty_status e = C.upload_inputs()) return e;
     if (nefty_status e = C.coefficients()) return e;
+    if (nefty_status e = C.prepare_tma()) return e;
     const Real* T0dev = C.T0.user ? (const Real*)C.T0.dev : t0buf;
     if (!C.T0.user) NEFTY_CUDA(h, cudaMemsetAsync(t0buf, 0, N * R, s));
     // step n reads src[n], writes dst[n]; states alternate between two buffers
@@ -432,11 +539,9 @@ nefty_status run_forward(nefty_handle* h, const Prob& P, const void* alpha, cons
         tab[nt + n] = work[n & 1];
     }
     NEFTY_CUDA(h, cudaMemcpyAsync(C.tables, tab.data(), tab.size() * sizeof(Real*), cudaMemcpyHostToDevice, s));
-    FwdArgs<Real> a = C.fwd_args(0, P.nt, C.tables, C.tables + nt, C.iters, C.resid);
-    a.frames = (Real*)fr.dev;
-    a.obs = (const Real*)C.obs.dev;
-    a.loss_partials = C.loss_partials;
-    if (nefty_status e = C.launch_fwd(a)) return e;
+    if (nefty_status e = C.forward_steps(0, P.nt, C.tables, C.tables + nt, C.iters, C.resid, (Real*)fr.dev,
+                                         (const Real*)C.obs.dev, C.loss_partials, 0))
+        return e;
     if (tf.user) NEFTY_CUDA(h, cudaMemcpyAsync(tf.dev, work[(nt - 1) & 1], N * R, cudaMemcpyDeviceToDevice, s));
     for (Output* o : {&fr, &tf})
         if (o->user && o->stage)
@@ -463,7 +568,7 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
     Call<Real> C;
     C.h = h; C.P = P; C.s = s; C.q_steps = q_steps;
     C.timing = st != nullptr;
-    C.G = grid_for(h, P.prec, P.N);
+    C.G = Call<Real>::kTiled ? grid_for_tiled(h, P) : grid_for(h, P.prec, P.N);
     if (C.G <= 0) return fail(h, NEFTY_ECUDA, "cannot size the persistent solver grid on this device");
     C.alpha.plan(alpha, N * R);
     C.T0.plan(T0, N * R);
@@ -519,6 +624,7 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
     layout(arena);
     if (nefty_status e = C.upload_inputs()) return e;
     if (nefty_status e = C.coefficients()) return e;
+    if (nefty_status e = C.prepare_tma()) return e;
     if (C.T0.user) NEFTY_CUDA(h, cudaMemcpyAsync(ck[0], C.T0.dev, N * R, cudaMemcpyDeviceToDevice, s));
     else NEFTY_CUDA(h, cudaMemsetAsync(ck[0], 0, N * R, s));
     NEFTY_CUDA(h, cudaMemsetAsync(grad, 0, N * sizeof(double), s));
@@ -565,10 +671,9 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
     Real** dA_T = C.tables + 4 * nt;
 
     // forward sweep with the loss
-    FwdArgs<Real> fa = C.fwd_args(0, P.nt, dF_src, dF_dst, C.iters, C.resid);
-    fa.obs = (const Real*)C.obs.dev;
-    fa.loss_partials = C.loss_partials;
-    if (nefty_status e = C.launch_fwd(fa)) return e;
+    if (nefty_status e = C.forward_steps(0, P.nt, dF_src, dF_dst, C.iters, C.resid, nullptr,
+                                         (const Real*)C.obs.dev, C.loss_partials, 0))
+        return e;
 
     // reverse sweep, one segment at a time
     NEFTY_CUDA(h, cudaMemsetAsync(mu[(P.nt + 1) & 1], 0, N * R, s));
@@ -592,17 +697,34 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
     for (int g = nseg - 1; g >= 0; --g) {
         const int a0 = g * seg_len, a1 = std::min(a0 + seg_len, P.nt);
         if (K > 1) {
-            FwdArgs<Real> ra = C.fwd_args(a0, a1, dR_src + a0, dR_dst + a0, C.iters + nt + rec_steps,
-                                          C.resid + nt + rec_steps);
-            if (nefty_status e = C.launch_fwd(ra, 1)) return e;
+            if (nefty_status e = C.forward_steps(a0, a1, dR_src + a0, dR_dst + a0, C.iters + nt + rec_steps,
+                                                 C.resid + nt + rec_steps, nullptr, nullptr, nullptr, 1))
+                return e;
             rec_steps += a1 - a0;
         }
-        aa.n0 = a0;
-        aa.n1 = a1;
-        aa.T = dA_T + seg_aoff[g];
-        aa.iters = C.iters + 2 * nt + adj_steps;
-        aa.resid = C.resid + 2 * nt + adj_steps;
-        if (nefty_status e = C.launch_adj(aa)) return e;
+        if constexpr (Call<Real>::kTiled) {
+            tiled::AdjTiled ta{};
+            ta.c = C.tiled_common(C.iters + 2 * nt + adj_steps, C.resid + 2 * nt + adj_steps);
+            ta.n0 = a0;
+            ta.n1 = a1;
+            ta.T = (float* const*)(dA_T + seg_aoff[g]);
+            ta.mu[0] = mu[0];
+            ta.mu[1] = mu[1];
+            ta.alpha = (const float*)C.alpha.dev;
+            ta.wx = (float)aa.wx; ta.wy = (float)aa.wy; ta.wz = (float)aa.wz;
+            ta.g_scale = (float)aa.g_scale;
+            ta.obs_off = aa.obs_off;
+            ta.obs = (const float*)C.obs.dev;
+            ta.grad = grad;
+            if (nefty_status e = C.launch_adj_tiled(ta)) return e;
+        } else {
+            aa.n0 = a0;
+            aa.n1 = a1;
+            aa.T = dA_T + seg_aoff[g];
+            aa.iters = C.iters + 2 * nt + adj_steps;
+            aa.resid = C.resid + 2 * nt + adj_steps;
+            if (nefty_status e = C.launch_adj(aa)) return e;
+        }
         adj_steps += a1 - a0;
     }
     NEFTY_CUDA(h, launch_cast<Real>(grad, (Real*)ga.dev, P.N, s));

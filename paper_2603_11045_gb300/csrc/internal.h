@@ -2,6 +2,7 @@
 // (solver.cu).  Not installed; callers use include/nefty.h.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -98,5 +99,88 @@ template <typename Real>
 cudaError_t launch_adjoint(const AdjArgs<Real>& a, int grid, cudaStream_t s);
 template <typename Real>
 cudaError_t launch_cast(const double* in, Real* out, unsigned n, cudaStream_t s);
+
+// ------------------------------------------------- tiled FP32 solver (cg_tiled.cu)
+namespace tiled {
+
+constexpr int TX = 32, TY = 16, NT = TX * TY;   // CTA: 32 x 16 columns, one thread each
+
+struct Geo {
+    int nx, ny, nz;
+    int px, py;            // lateral wrap active
+    unsigned S;            // nx * ny
+    int tiles_x;           // ceil(nx / TX)
+    unsigned units;        // (tiles_x * tiles_y) * nz  (tile, plane) work units
+};
+
+// CG vectors of the single-reduction iteration (ping-pong pairs are read with
+// a halo in one pass and written in the next).
+struct Vecs {
+    float* u[2];           // M^{-1} r
+    float* ws[2];          // M^{-1} A u
+    float* ss[2];          // M^{-1} A p
+    float* p;
+    float* delta;          // increment of the current solve
+};
+
+// TMA descriptors of the arrays one CG iteration reads (tiled FP32 path).
+struct TmaMaps {
+    CUtensorMap u[2], ws[2], ss[2];   // box 40 x 18 at (x0-4, y0-1, k)
+    CUtensorMap p, delta, cz;         // box 32 x 16 at (x0, y0, k)
+    CUtensorMap cx;                   // box 40 x 16 at (x0-4, y0, k)
+    CUtensorMap cy;                   // box 32 x 17 at (x0, y0-1, k)
+};
+
+struct Common {
+    Geo g;
+    const TmaMaps* maps;   // device copy of the descriptors, or null (plain loads)
+    const float* cx; const float* cy; const float* cz;   // dt * a of the +x/+y/+z face
+    float robin;           // dt h / dz on k = nz-1
+    Vecs v;
+    DevCtl* ctl;
+    double* partials;      // [2][kMaxRed][G]
+    double tol2;
+    int max_iter;
+    int* iters;
+    double* resid;
+};
+
+struct FwdTiled {
+    Common c;
+    int n0, n1;
+    float* const* src;
+    float* const* dst;
+    const float* q_face; int q_steps; const float* q_full;
+    float src_scale;
+    unsigned obs_off;
+    const float* obs;
+    float* frames;
+    double* loss_partials;
+};
+
+struct AdjTiled {
+    Common c;
+    int n0, n1;
+    float* const* T;
+    float* mu[2];
+    const float* alpha;
+    float wx, wy, wz;      // 2 dt / h_d^2
+    float g_scale;         // 2 * loss_scale
+    unsigned obs_off;
+    const float* obs;
+    double* grad;
+};
+
+}  // namespace tiled
+
+int tiled_grid_blocks(int device);
+// Shared memory (bytes) the tiled kernels request dynamically.
+int tiled_dynamic_smem();
+// Fill `maps` for the given device buffers; false if the driver refused.
+bool tiled_encode_maps(tiled::TmaMaps* maps, const tiled::Geo& g, float* const u[2], float* const ws[2],
+                       float* const ss[2], float* p, float* delta, const float* cx, const float* cy,
+                       const float* cz);
+cudaError_t launch_forward_tiled(const tiled::FwdTiled& a, int grid, cudaStream_t s);
+cudaError_t launch_adjoint_tiled(const tiled::AdjTiled& a, int grid, cudaStream_t s);
 
 }  // namespace nefty
