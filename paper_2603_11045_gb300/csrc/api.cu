@@ -296,8 +296,7 @@ struct Call {
             tiled::TmaMaps host;
             tiled::Geo g{};
             g.nx = P.nx; g.ny = P.ny; g.nz = P.nz; g.S = P.S;
-            if (!tiled_encode_maps(&host, g, tv.u, tv.ws, tv.ss, tv.p, tv.delta, (const float*)coef,
-                                   (const float*)coef + P.N, (const float*)coef + 2 * (size_t)P.N))
+            if (!tiled_encode_maps(&host, g, tv.u, tv.ws, tv.ss, tv.p, tv.delta, (const float*)alpha.dev))
                 return NEFTY_OK;
             NEFTY_CUDA(h, cudaMemcpyAsync(tmaps, &host, sizeof host, cudaMemcpyHostToDevice, s));
             NEFTY_CUDA(h, cudaStreamSynchronize(s));
@@ -376,9 +375,10 @@ struct Call {
         c.g.tiles_x = (P.nx + tiled::TX - 1) / tiled::TX;
         c.g.units = (unsigned)(c.g.tiles_x * ((P.ny + tiled::TY - 1) / tiled::TY)) * (unsigned)P.nz;
         c.maps = use_tma ? tmaps : nullptr;
-        c.cx = (const float*)coef;
-        c.cy = (const float*)coef + P.N;
-        c.cz = (const float*)coef + 2 * (size_t)P.N;
+        c.alpha = (const float*)alpha.dev;
+        c.kx = (float)(P.dt / (P.dx * P.dx));
+        c.ky = (float)(P.dt / (P.dy * P.dy));
+        c.kz = (float)(P.dt / (P.dz * P.dz));
         c.robin = (float)(P.dt * P.robin_h / P.dz);
         c.v = tv;
         c.ctl = ctl;
@@ -513,11 +513,15 @@ nefty_status run_forward(nefty_handle* h, const Prob& P, const void* alpha, cons
     fr.plan(frames_out, nt * S * R);
     tf.plan(T_final, N * R);
     Real *work[2], *t0buf = nullptr;
+    // one state = N values; the FP32 path keeps it as a compensated (hi, lo)
+    // pair, so its state slots hold 2N floats
+    const size_t SB = (Call<Real>::kTiled ? 2 : 1) * N * R;
+    const bool own_t0 = Call<Real>::kTiled || !C.T0.user;
     auto layout = [&](Arena& a) {
         C.place_common(a, 2 * nt);
-        work[0] = (Real*)a.take(N * R);
-        work[1] = (Real*)a.take(N * R);
-        t0buf = (Real*)a.take(C.T0.user ? 0 : N * R);
+        work[0] = (Real*)a.take(SB);
+        work[1] = (Real*)a.take(SB);
+        t0buf = (Real*)a.take(own_t0 ? SB : 0);
         fr.place(a);
         tf.place(a);
     };
@@ -530,8 +534,11 @@ nefty_status run_forward(nefty_handle* h, const Prob& P, const void* alpha, cons
     if (nefty_status e = C.upload_inputs()) return e;
     if (nefty_status e = C.coefficients()) return e;
     if (nefty_status e = C.prepare_tma()) return e;
-    const Real* T0dev = C.T0.user ? (const Real*)C.T0.dev : t0buf;
-    if (!C.T0.user) NEFTY_CUDA(h, cudaMemsetAsync(t0buf, 0, N * R, s));
+    const Real* T0dev = own_t0 ? t0buf : (const Real*)C.T0.dev;
+    if (own_t0) {
+        NEFTY_CUDA(h, cudaMemsetAsync(t0buf, 0, SB, s));
+        if (C.T0.user) NEFTY_CUDA(h, cudaMemcpyAsync(t0buf, C.T0.dev, N * R, cudaMemcpyDeviceToDevice, s));
+    }
     // step n reads src[n], writes dst[n]; states alternate between two buffers
     std::vector<Real*> tab(2 * nt);
     for (size_t n = 0; n < nt; ++n) {
@@ -552,7 +559,7 @@ nefty_status run_forward(nefty_handle* h, const Prob& P, const void* alpha, cons
 // Checkpoint stride of the reverse sweep: 1 keeps every state.
 int choose_stride(const Prob& P, size_t fixed_bytes, uint64_t budget) {
     if (P.ckpt_every >= 1) return std::min(P.ckpt_every, P.nt);
-    const size_t state = (size_t)P.N * (P.prec == NEFTY_FP32 ? 4 : 8);
+    const size_t state = (size_t)P.N * 8;   // an FP32 compensated pair or an FP64 value
     const size_t all = (size_t)(P.nt + 1) * state + fixed_bytes;
     if (all <= budget) return 1;
     int K = (int)std::ceil(std::sqrt((double)P.nt));
@@ -602,18 +609,19 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
     double* grad = nullptr;
     std::vector<Real*> ck(nck), segbuf(nseg_buf);
     Real* work[2] = {nullptr, nullptr};
+    const size_t SB = (Call<Real>::kTiled ? 2 : 1) * N * R;   // one state slot (see run_forward)
     auto layout = [&](Arena& a) {
         C.place_common(a, 6 * nt + 4);
-        mu[0] = (Real*)a.take(N * R);
-        mu[1] = (Real*)a.take(N * R);
+        mu[0] = (Real*)a.take(SB);
+        mu[1] = (Real*)a.take(SB);
         grad = (double*)a.take(N * sizeof(double));
         ga.place(a);
         gt.place(a);
-        for (int i = 0; i < nck; ++i) ck[i] = (Real*)a.take(N * R);
-        for (int i = 0; i < nseg_buf; ++i) segbuf[i] = (Real*)a.take(N * R);
+        for (int i = 0; i < nck; ++i) ck[i] = (Real*)a.take(SB);
+        for (int i = 0; i < nseg_buf; ++i) segbuf[i] = (Real*)a.take(SB);
         if (K > 1) {
-            work[0] = (Real*)a.take(N * R);
-            work[1] = (Real*)a.take(N * R);
+            work[0] = (Real*)a.take(SB);
+            work[1] = (Real*)a.take(SB);
         }
     };
     Arena probe;
@@ -625,8 +633,8 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
     if (nefty_status e = C.upload_inputs()) return e;
     if (nefty_status e = C.coefficients()) return e;
     if (nefty_status e = C.prepare_tma()) return e;
+    NEFTY_CUDA(h, cudaMemsetAsync(ck[0], 0, SB, s));
     if (C.T0.user) NEFTY_CUDA(h, cudaMemcpyAsync(ck[0], C.T0.dev, N * R, cudaMemcpyDeviceToDevice, s));
-    else NEFTY_CUDA(h, cudaMemsetAsync(ck[0], 0, N * R, s));
     NEFTY_CUDA(h, cudaMemsetAsync(grad, 0, N * sizeof(double), s));
 
     // Pointer tables: forward src/dst (2 nt), recompute src/dst (2 nt), adjoint T (nt + nseg).
@@ -676,7 +684,7 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
         return e;
 
     // reverse sweep, one segment at a time
-    NEFTY_CUDA(h, cudaMemsetAsync(mu[(P.nt + 1) & 1], 0, N * R, s));
+    NEFTY_CUDA(h, cudaMemsetAsync(mu[(P.nt + 1) & 1], 0, SB, s));
     int rec_steps = 0, adj_steps = 0;
     AdjArgs<Real> aa;
     aa.op = make_view<Real>(P, C.coef);

@@ -95,44 +95,75 @@ __device__ bool barrier(Sync& g) {
     return s_ok != 0;
 }
 
-// Grid sum of NV values given per thread in FP32 (promoted to FP64 here).
+// Error-free transformation of a + b (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bv = s - a;
+    e = (a - (s - bv)) + (b - bv);
+}
+
+// (hi, lo) + d as a renormalised compensated pair.
+__device__ __forceinline__ void add_pair(float hi, float lo, float d, float& oh, float& ol) {
+    float s, e;
+    two_sum(hi, d, s, e);
+    two_sum(s, lo + e, oh, ol);
+}
+
+// Compensated warp sum of (hi, lo) pairs; lane 0 holds the result.
+__device__ __forceinline__ void warp_sum2(float& hi, float& lo) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+        float sh, e;
+        two_sum(hi, oh, sh, e);
+        lo = lo + ol + e;
+        two_sum(sh, lo, hi, lo);
+    }
+}
+
+// Grid sum of NV values given per thread in FP32.  The sums run on the FP32
+// pipes as compensated (hi, lo) pairs, which keeps about twice the FP32
+// precision: per thread over its cells, then TwoSum trees over the warp, the
+// CTA and the G CTA partials (fixed order, so every run gives the same bits).
+// GB300's FP64 rate is a small fraction of its FP32 rate, so no FP64 arithmetic
+// is done per thread.  On return thread 0 holds the totals as doubles
+// (hi + lo); the other threads' out[] is unspecified.
 template <int NV>
 __device__ bool grid_sum(Sync& g, const float (&in)[NV], double (&out)[NV]) {
-    __shared__ double s_w[NT / 32][kMaxRed];
-    __shared__ double s_t[kMaxRed];
+    __shared__ float s_h[NT / 32][kMaxRed], s_l[NT / 32][kMaxRed];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
-        double t = (double)in[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) s_w[warp][i] = t;
+        float hi = in[i], lo = 0.f;
+        warp_sum2(hi, lo);
+        if (lane == 0) { s_h[warp][i] = hi; s_l[warp][i] = lo; }
     }
     __syncthreads();
-    double* part = g.partials + (size_t)(g.red & 1u) * kMaxRed * g.G;
+    float2* part = reinterpret_cast<float2*>(g.partials) + (size_t)(g.red & 1u) * kMaxRed * g.G;
     if (warp == 0) {
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
-            double t = lane < NT / 32 ? s_w[lane][i] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0) part[(size_t)i * g.G + blockIdx.x] = t;
+            float hi = lane < NT / 32 ? s_h[lane][i] : 0.f, lo = lane < NT / 32 ? s_l[lane][i] : 0.f;
+            warp_sum2(hi, lo);
+            if (lane == 0) part[(size_t)i * g.G + blockIdx.x] = make_float2(hi, lo);
         }
     }
     if (!barrier(g)) return false;
     if (warp == 0) {
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
-            double t = 0.0;
-            for (unsigned b = lane; b < g.G; b += 32) t += part[(size_t)i * g.G + b];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0) s_t[i] = t;
+            float hi = 0.f, lo = 0.f;
+            for (unsigned b = lane; b < g.G; b += 32) {
+                const float2 v = part[(size_t)i * g.G + b];
+                float sh, e;
+                two_sum(hi, v.x, sh, e);
+                lo = lo + v.y + e;
+                two_sum(sh, lo, hi, lo);
+            }
+            warp_sum2(hi, lo);
+            out[i] = (double)hi + (double)lo;
         }
     }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < NV; ++i) out[i] = s_t[i];
     g.red += 1;
     return true;
 }
@@ -168,6 +199,15 @@ __device__ __forceinline__ int map_y(const Geo& g, int y) {
     return y;
 }
 
+// The halo ring's RING cells are spread over the high lanes of all warps
+// (slot r -> warp r % 16, lane 31 - r / 16), keeping thread 0 free to issue
+// copies and every warp's share of the ring equal.  Returns -1 for no slot.
+__device__ __forceinline__ int ring_slot() {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = (31 - lane) * (NT / 32) + warp;
+    return r < RING ? r : -1;
+}
+
 // Halo-ring slot t in [0, RING) -> (row, col) in the BY x BX shared tile.
 __device__ __forceinline__ void ring_pos(int t, int& hy, int& hx) {
     if (t < BX) { hy = 0; hx = t; }
@@ -176,16 +216,33 @@ __device__ __forceinline__ void ring_pos(int t, int& hy, int& hx) {
     else { hy = t - 2 * BX - TY + 1; hx = BX - 1; }
 }
 
-// Face values of the own cell (x, y, k): +x, -x, +y, -y from the stored +face
-// arrays (the -x face of a cell is the +x face of its -x neighbour).
+// Hardware reciprocal (rcp.approx, about 1 ulp).  Used for the face values and
+// the Jacobi diagonal: their rounding moves the solution far less than the
+// FP32 CG arithmetic does, and every pass evaluates them identically.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Harmonic-mean face value dt * a_f = k * 2 a b / (a + b), k = dt / h^2, of the
+// face between cells of diffusivity a and b (Prop. 1).  Both cells that share a
+// face evaluate the same products on the same two values, so A stays exactly
+// symmetric.  b = 0 (a cell beyond a zero-flux wall, as TMA fills it) gives 0.
+__device__ __forceinline__ float face(float a, float b, float k) {
+    return k * (2.f * a * b) * rcp_approx(a + b);
+}
+
+// Face values +x, -x, +y, -y of the own cell c = (x, y, k), from alpha.
 struct Faces { float xp, xm, yp, ym; };
-__device__ __forceinline__ Faces lateral_faces(const Geo& g, const float* __restrict__ cx,
-                                               const float* __restrict__ cy, unsigned c, int x, int y) {
+__device__ __forceinline__ Faces lateral_faces(const Geo& g, const float* __restrict__ al, unsigned c, int x,
+                                               int y, float ac, float kx, float ky) {
     Faces f;
-    f.xp = cx[c];
-    f.yp = cy[c];
-    f.xm = x > 0 ? cx[c - 1] : (g.px ? cx[c + g.nx - 1] : 0.f);
-    f.ym = y > 0 ? cy[c - g.nx] : (g.py ? cy[c + (unsigned)(g.ny - 1) * g.nx] : 0.f);
+    const unsigned wrap_y = (unsigned)(g.ny - 1) * g.nx;
+    f.xp = x + 1 < g.nx ? face(ac, al[c + 1], kx) : (g.px ? face(ac, al[c + 1 - g.nx], kx) : 0.f);
+    f.xm = x > 0 ? face(ac, al[c - 1], kx) : (g.px ? face(ac, al[c + g.nx - 1], kx) : 0.f);
+    f.yp = y + 1 < g.ny ? face(ac, al[c + g.nx], ky) : (g.py ? face(ac, al[c - wrap_y], ky) : 0.f);
+    f.ym = y > 0 ? face(ac, al[c - g.nx], ky) : (g.py ? face(ac, al[c + wrap_y], ky) : 0.f);
     return f;
 }
 
@@ -210,8 +267,9 @@ __device__ __forceinline__ void march(const Geo& g, int tile, int k0, int k1, fl
     int rhy = 0, rhx = 0;
     unsigned ring_col = 0;
     bool ring_mapped = false;
-    if (threadIdx.x < RING) {
-        ring_pos(threadIdx.x, rhy, rhx);
+    const int rslot = ring_slot();
+    if (rslot >= 0) {
+        ring_pos(rslot, rhy, rhx);
         const int gx = map_x(g, x0 - 1 + rhx), gy = map_y(g, y0 - 1 + rhy);
         ring_mapped = gx >= 0 && gy >= 0;
         ring_col = ring_mapped ? (unsigned)gy * g.nx + gx : 0u;
@@ -220,7 +278,7 @@ __device__ __forceinline__ void march(const Geo& g, int tile, int k0, int k1, fl
         float* buf = &sm[k % 3][0][0];
         const float v = own_mapped ? field(own_col + (unsigned)k * g.S, valid) : 0.f;
         buf[(ty + 1) * BX + tx + 1] = v;
-        if (threadIdx.x < RING) buf[rhy * BX + rhx] = ring_mapped ? field(ring_col + (unsigned)k * g.S, false) : 0.f;
+        if (rslot >= 0) buf[rhy * BX + rhx] = ring_mapped ? field(ring_col + (unsigned)k * g.S, false) : 0.f;
         return v;
     };
     float fzm = 0.f;
@@ -259,30 +317,26 @@ __device__ __forceinline__ void for_segments(const Geo& g, SegFn seg) {
 // ------------------------------------------------------------ TMA staging
 // The CG iteration pass can take its inputs through the Tensor Memory
 // Accelerator: for every plane a single thread issues bulk tensor copies of
-// the eight arrays the pass reads (u, ws, ss with a one-cell halo; p, delta,
-// cz, and the face arrays with the -x / -y neighbour row) into one stage of a
-// four-stage shared-memory ring, completing on that stage's mbarrier.  Copies
-// run two planes ahead of the plane being computed.  Cells outside the grid
+// the six arrays the pass reads (u, ws, ss and alpha with a one-cell halo; p
+// and delta) into one stage of a six-stage shared-memory ring, completing on
+// that stage's mbarrier.  Copies run four planes ahead of the plane being
+// computed.  Cells outside the grid
 // arrive as zeros, which is exactly a zero-flux wall (their face values are
 // zero), so this path serves grids with zero-flux lateral walls and nx % 4 == 0
 // (row pitch a multiple of 16 bytes).
-constexpr int NS = 4;                         // stages
+constexpr int NS = 6;                         // stages
 constexpr int HB = TX + 8, HR = TY + 2;       // halo box: x0-4 .. x0+35, y0-1 .. y0+16
 constexpr int SZ_H = HB * HR * 4;             // 2880
 constexpr int SZ_O = TX * TY * 4;             // 2048
-constexpr int SZ_CX = HB * TY * 4;            // 2560
-constexpr int SZ_CY = TX * (TY + 1) * 4;      // 2176
 constexpr int al128(int b) { return (b + 127) & ~127; }
 constexpr int OFF_U = 0;
 constexpr int OFF_W = OFF_U + al128(SZ_H);
 constexpr int OFF_S = OFF_W + al128(SZ_H);
-constexpr int OFF_P = OFF_S + al128(SZ_H);
+constexpr int OFF_A = OFF_S + al128(SZ_H);
+constexpr int OFF_P = OFF_A + al128(SZ_H);
 constexpr int OFF_D = OFF_P + al128(SZ_O);
-constexpr int OFF_CZ = OFF_D + al128(SZ_O);
-constexpr int OFF_CX = OFF_CZ + al128(SZ_O);
-constexpr int OFF_CY = OFF_CX + al128(SZ_CX);
-constexpr int STAGE_BYTES = al128(OFF_CY + SZ_CY);
-constexpr unsigned TX_BYTES = 3 * SZ_H + 3 * SZ_O + SZ_CX + SZ_CY;
+constexpr int STAGE_BYTES = al128(OFF_D + SZ_O);
+constexpr unsigned TX_BYTES = 4 * SZ_H + 2 * SZ_O;
 constexpr int DYN_SMEM = NS * STAGE_BYTES + 128;   // + alignment slack
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -331,11 +385,9 @@ __device__ __forceinline__ void issue_plane(TmaRing& R, const TmaMaps* M, int cu
     tma_load3(dst + OFF_U, &M->u[cur], x0 - 4, y0 - 1, k, bar);
     tma_load3(dst + OFF_W, &M->ws[cur], x0 - 4, y0 - 1, k, bar);
     tma_load3(dst + OFF_S, &M->ss[cur], x0 - 4, y0 - 1, k, bar);
+    tma_load3(dst + OFF_A, &M->alpha, x0 - 4, y0 - 1, k, bar);
     tma_load3(dst + OFF_P, &M->p, x0, y0, k, bar);
     tma_load3(dst + OFF_D, &M->delta, x0, y0, k, bar);
-    tma_load3(dst + OFF_CZ, &M->cz, x0, y0, k, bar);
-    tma_load3(dst + OFF_CX, &M->cx, x0 - 4, y0, k, bar);
-    tma_load3(dst + OFF_CY, &M->cy, x0, y0 - 1, k, bar);
     R.issued += 1;
 }
 
@@ -372,6 +424,7 @@ __device__ bool iter_pass_tma(const Common& C, TmaRing& R, float (*fr)[BY][BX], 
         } else {
             next = min(kh + 1, kl + NS);
         }
+        const int rslot = ring_slot();
         auto stage = [&](int k) -> const unsigned char* { return R.base + ((t0 + (unsigned)(k - kl)) % NS) * STAGE_BYTES; };
         auto wait_plane = [&](int k) -> bool {
             const unsigned t = t0 + (unsigned)(k - kl);
@@ -388,9 +441,9 @@ __device__ bool iter_pass_tma(const Common& C, TmaRing& R, float (*fr)[BY][BX], 
             int hb = (ty + 1) * HB + tx + 4;
             const float vo = U[hb] - a * (first ? W[hb] : W[hb] + bt * Sv[hb]);
             buf[(ty + 1) * BX + tx + 1] = vo;
-            if (threadIdx.x < RING) {
+            if (rslot >= 0) {
                 int hy, hx;
-                ring_pos(threadIdx.x, hy, hx);
+                ring_pos(rslot, hy, hx);
                 hb = hy * HB + hx + 3;
                 buf[hy * BX + hx] = U[hb] - a * (first ? W[hb] : W[hb] + bt * Sv[hb]);
             }
@@ -414,9 +467,12 @@ __device__ bool iter_pass_tma(const Common& C, TmaRing& R, float (*fr)[BY][BX], 
             const float* W = (const float*)(st + OFF_W);
             const float* Sv = (const float*)(st + OFF_S);
             fzm = U[hb] - a * (first ? W[hb] : W[hb] + bt * Sv[hb]);
-            czm = ((const float*)(st + OFF_CZ))[ty * TX + tx];
         }
         w_ok = w_ok && wait_plane(k0);
+        if (k0 > 0 && w_ok) {
+            const int hb = (ty + 1) * HB + tx + 4;
+            czm = face(((const float*)(stage(k0) + OFF_A))[hb], ((const float*)(stage(k0 - 1) + OFF_A))[hb], C.kz);
+        }
         float fc = w_ok ? fill(k0) : 0.f;
         if (abort_uniform(w_ok)) return;
         for (int k = k0; k < k1; ++k) {
@@ -436,16 +492,17 @@ __device__ bool iter_pass_tma(const Common& C, TmaRing& R, float (*fr)[BY][BX], 
                 const int b = (ty + 1) * BX + tx + 1;
                 const float fxm = buf[b - 1], fxp = buf[b + 1], fym = buf[b - BX], fyp = buf[b + BX];
                 const float fzmv = k > 0 ? fzm : fc;
-                const float* CXs = (const float*)(st + OFF_CX);
-                const float* CYs = (const float*)(st + OFF_CY);
-                const float cxp = CXs[ty * HB + tx + 4], cxm = CXs[ty * HB + tx + 3];
-                const float cyp = CYs[(ty + 1) * TX + tx], cym = CYs[ty * TX + tx];
-                const float czp = ((const float*)(st + OFF_CZ))[ty * TX + tx];
+                const float* As = (const float*)(st + OFF_A);
+                const int ha = (ty + 1) * HB + tx + 4;
+                const float ac = As[ha];
+                const float cxp = face(ac, As[ha + 1], C.kx), cxm = face(ac, As[ha - 1], C.kx);
+                const float cyp = face(ac, As[ha + HB], C.ky), cym = face(ac, As[ha - HB], C.ky);
+                const float czp = k + 1 < g.nz ? face(ac, ((const float*)(stage(k + 1) + OFF_A))[ha], C.kz) : 0.f;
                 const float rob = k + 1 == g.nz ? C.robin : 0.f;
                 const float d = 1.f + cxp + cxm + cyp + cym + czp + czm + rob;
                 const float Au = fc + cxp * (fc - fxp) + cxm * (fc - fxm) + cyp * (fc - fyp) + cym * (fc - fym) +
                                  czp * (fc - fzp) + czm * (fc - fzmv) + rob * fc;
-                const float wn = __frcp_rn(d) * Au;
+                const float wn = rcp_approx(d) * Au;
                 const int hb = (ty + 1) * HB + tx + 4;
                 const float uold = ((const float*)(st + OFF_U))[hb];
                 const float wold = ((const float*)(st + OFF_W))[hb];
@@ -479,14 +536,20 @@ __device__ __forceinline__ float diag(const Faces& f, float czp, float czm, floa
 
 // --------------------------------------------------------------- solve
 // One linear solve A (x0 + delta) = x0 + e, where e (the forcing of this
-// step) is given per own cell by Rhs(c, k) and x0 by X0 (read-only field).
-// On return delta holds the increment.  Returns false if a barrier failed.
+// step) is given per own cell by Rhs(c, k) and the state x0 = x0hi + x0lo is
+// a compensated pair (read-only).  The initial residual r0 = e - (A - I) x0 is
+// formed with error-free products and sums (TwoProd through fmaf, TwoSum), so
+// it is accurate relative to itself however small it is against x0; the CG
+// then runs in FP32 on the increment.  On return delta holds the increment.
+// Returns false if a barrier failed.
 template <class RhsFn>
 __device__ bool solve(const Common& C, Sync& sy, float (*sm)[BY][BX], TmaRing* ring,
-                      const float* __restrict__ x0, RhsFn rhs, int* it_out, double* rel_out) {
+                      const float* __restrict__ x0, const float* __restrict__ x0lo, RhsFn rhs, int* it_out,
+                      double* rel_out) {
     const Geo& g = C.g;
     // ---- init 1: r0 = e - (A - I) x0, u0 = M^{-1} r0 ; bb, (r0,u0), (r0,r0)
     float acc3[3] = {0.f, 0.f, 0.f};
+    const unsigned wrap_y = (unsigned)(g.ny - 1) * g.nx;
     for_segments(g, [&](int tile, int k0, int k1) {
         float czm = 0.f;
         march(g, tile, k0, k1, sm,
@@ -494,31 +557,65 @@ __device__ bool solve(const Common& C, Sync& sy, float (*sm)[BY][BX], TmaRing* r
               [&](int k, unsigned c, int x, int y, bool valid, float fc, float fxm, float fxp, float fym,
                   float fyp, float fzm, float fzp) {
                   if (!valid) return;
-                  if (k == k0 && k > 0) czm = C.cz[c - g.S];
-                  const Faces f = lateral_faces(g, C.cx, C.cy, c, x, y);
-                  const float czp = C.cz[c];
+                  const float ac = C.alpha[c];
+                  if (k == k0 && k > 0) czm = face(ac, C.alpha[c - g.S], C.kz);
+                  const Faces f = lateral_faces(g, C.alpha, c, x, y, ac, C.kx, C.ky);
+                  const float czp = k + 1 < g.nz ? face(ac, C.alpha[c + g.S], C.kz) : 0.f;
                   const float rob = k + 1 == g.nz ? C.robin : 0.f;
-                  const float lap = f.xp * (fc - fxp) + f.xm * (fc - fxm) + f.yp * (fc - fyp) +
-                                    f.ym * (fc - fym) + czp * (fc - fzp) + czm * (fc - fzm) + rob * fc;
+                  const float lc = x0lo[c];
+                  float sh = 0.f, sl = 0.f;
+                  // sh + sl += cf * ((fc + lc) - (hq + lq)), error-free up to the final rounding
+                  auto term = [&](float cf, float hq, unsigned q) {
+                      if (cf == 0.f) return;
+                      float dh, dhe;
+                      two_sum(fc, -hq, dh, dhe);
+                      const float dl = (lc - x0lo[q]) + dhe;
+                      const float pr = cf * dh;
+                      const float pe = fmaf(cf, dh, -pr) + cf * dl;
+                      float t, te;
+                      two_sum(sh, pr, t, te);
+                      sh = t;
+                      sl += te + pe;
+                  };
+                  term(f.xp, fxp, x + 1 < g.nx ? c + 1 : c + 1 - g.nx);
+                  term(f.xm, fxm, x > 0 ? c - 1 : c + g.nx - 1);
+                  term(f.yp, fyp, y + 1 < g.ny ? c + g.nx : c - wrap_y);
+                  term(f.ym, fym, y > 0 ? c - g.nx : c + wrap_y);
+                  term(czp, fzp, c + g.S);
+                  term(czm, fzm, c - g.S);
+                  if (rob != 0.f) {
+                      const float pr = rob * fc;
+                      const float pe = fmaf(rob, fc, -pr) + rob * lc;
+                      float t, te;
+                      two_sum(sh, pr, t, te);
+                      sh = t;
+                      sl += te + pe;
+                  }
                   const float e = rhs(c, k);
-                  const float r = e - lap;
-                  const float dinv = __frcp_rn(diag(f, czp, czm, rob));
+                  const float r = (e - sh) - sl;
+                  const float dinv = rcp_approx(diag(f, czp, czm, rob));
                   const float u = dinv * r;
                   C.v.u[0][c] = u;
                   C.v.delta[c] = 0.f;
-                  const float b = fc + e;
+                  const float b = (fc + lc) + e;
                   acc3[0] += b * b;
                   acc3[1] += r * u;
                   acc3[2] += r * r;
                   czm = czp;
               });
     });
-    double t3[3];
+    // CG scalars live in thread 0 (FP64); the FP32 step lengths and the stop
+    // decision reach the other threads through shared memory.
+    __shared__ float s_a, s_b;
+    __shared__ int s_go;
+    double t3[3] = {0.0, 0.0, 0.0};
     if (!grid_sum<3>(sy, acc3, t3)) return false;
     const double bb = t3[0], lim = C.tol2 * bb;
     double gam = t3[1], rho = t3[2];
     int it = 0;
-    if (rho > lim && C.max_iter > 0) {
+    if (threadIdx.x == 0) s_go = (rho > lim && C.max_iter > 0) ? 1 : 0;
+    __syncthreads();
+    if (s_go) {
         // ---- init 2: ws0 = M^{-1} A u0 ; (A u0, u0)
         float acc1[1] = {0.f};
         for_segments(g, [&](int tile, int k0, int k1) {
@@ -529,25 +626,32 @@ __device__ bool solve(const Common& C, Sync& sy, float (*sm)[BY][BX], TmaRing* r
                   [&](int k, unsigned c, int x, int y, bool valid, float fc, float fxm, float fxp, float fym,
                       float fyp, float fzm, float fzp) {
                       if (!valid) return;
-                      if (k == k0 && k > 0) czm = C.cz[c - g.S];
-                      const Faces f = lateral_faces(g, C.cx, C.cy, c, x, y);
-                      const float czp = C.cz[c];
+                      const float ac = C.alpha[c];
+                      if (k == k0 && k > 0) czm = face(ac, C.alpha[c - g.S], C.kz);
+                      const Faces f = lateral_faces(g, C.alpha, c, x, y, ac, C.kx, C.ky);
+                      const float czp = k + 1 < g.nz ? face(ac, C.alpha[c + g.S], C.kz) : 0.f;
                       const float rob = k + 1 == g.nz ? C.robin : 0.f;
                       const float Au = fc + f.xp * (fc - fxp) + f.xm * (fc - fxm) + f.yp * (fc - fyp) +
                                        f.ym * (fc - fym) + czp * (fc - fzp) + czm * (fc - fzm) + rob * fc;
-                      const float dinv = __frcp_rn(diag(f, czp, czm, rob));
+                      const float dinv = rcp_approx(diag(f, czp, czm, rob));
                       C.v.ws[0][c] = dinv * Au;
                       acc1[0] += Au * fc;
                       czm = czp;
                   });
         });
-        double t1[1];
+        double t1[1] = {0.0};
         if (!grid_sum<1>(sy, acc1, t1)) return false;
-        double alpha = gam / t1[0], beta = 0.0;
+        double alpha = 0.0, beta = 0.0;
+        if (threadIdx.x == 0) {
+            alpha = gam / t1[0];
+            s_a = (float)alpha;
+            s_b = 0.f;
+        }
+        __syncthreads();
         int cur = 0;
         // ---- iterations: one pass, one reduction each
         while (true) {
-            const float a = (float)alpha, bt = (float)beta;
+            const float a = s_a, bt = s_b;
             const bool first = it == 0;
             const float* __restrict__ ui = C.v.u[cur];
             const float* __restrict__ wi = C.v.ws[cur];
@@ -572,14 +676,15 @@ __device__ bool solve(const Common& C, Sync& sy, float (*sm)[BY][BX], TmaRing* r
                       [&](int k, unsigned c, int x, int y, bool valid, float fc, float fxm, float fxp,
                           float fym, float fyp, float fzm, float fzp) {
                           if (!valid) return;
-                          if (k == k0 && k > 0) czm = C.cz[c - g.S];
-                          const Faces f = lateral_faces(g, C.cx, C.cy, c, x, y);
-                          const float czp = C.cz[c];
+                          const float ac = C.alpha[c];
+                          if (k == k0 && k > 0) czm = face(ac, C.alpha[c - g.S], C.kz);
+                          const Faces f = lateral_faces(g, C.alpha, c, x, y, ac, C.kx, C.ky);
+                          const float czp = k + 1 < g.nz ? face(ac, C.alpha[c + g.S], C.kz) : 0.f;
                           const float rob = k + 1 == g.nz ? C.robin : 0.f;
                           const float d = diag(f, czp, czm, rob);
                           const float Au = fc + f.xp * (fc - fxp) + f.xm * (fc - fxm) + f.yp * (fc - fyp) +
                                            f.ym * (fc - fym) + czp * (fc - fzp) + czm * (fc - fzm) + rob * fc;
-                          const float wn = __frcp_rn(d) * Au;
+                          const float wn = rcp_approx(d) * Au;
                           const float uold = ui[c];
                           const float sn = first ? wi[c] : wi[c] + bt * si[c];
                           const float pn = first ? uold : uold + bt * C.v.p[c];
@@ -595,16 +700,25 @@ __device__ bool solve(const Common& C, Sync& sy, float (*sm)[BY][BX], TmaRing* r
                           czm = czp;
                       });
             });
-            double t[3];
+            double t[3] = {0.0, 0.0, 0.0};
             if (!grid_sum<3>(sy, acc, t)) return false;
             ++it;
             cur ^= 1;
-            rho = t[2];
-            if (rho <= lim || it >= C.max_iter) break;
-            const double gam_new = t[0];
-            beta = gam_new / gam;
-            alpha = gam_new / (t[1] - beta * gam_new / alpha);
-            gam = gam_new;
+            if (threadIdx.x == 0) {
+                rho = t[2];
+                const bool go = !(rho <= lim || it >= C.max_iter);
+                if (go) {
+                    const double gam_new = t[0];
+                    beta = gam_new / gam;
+                    alpha = gam_new / (t[1] - beta * gam_new / alpha);
+                    gam = gam_new;
+                    s_a = (float)alpha;
+                    s_b = (float)beta;
+                }
+                s_go = go ? 1 : 0;
+            }
+            __syncthreads();
+            if (!s_go) break;
         }
     }
     *it_out = it;
@@ -648,13 +762,14 @@ __global__ void __launch_bounds__(NT, 2) forward_tiled(FwdTiled a) {
     const unsigned c0 = blockIdx.x * NT + threadIdx.x;
     double loss = 0.0;
     for (int n = a.n0; n < a.n1; ++n) {
+        // states are compensated pairs: hi in [0, N), lo in [N, 2N)
         const float* __restrict__ Tn = a.src[n - a.n0];
         float* __restrict__ Tn1 = a.dst[n - a.n0];
         const float* qmap = a.q_full ? a.q_full + (size_t)n * S : (n < a.q_steps ? a.q_face : nullptr);
         const float sc = a.src_scale;
         int it = 0;
         double rel = 0.0;
-        bool ok = solve(a.c, sy, sm, &ring, Tn,
+        bool ok = solve(a.c, sy, sm, &ring, Tn, Tn + N,
                         [&](unsigned c, int k) { return (qmap && k == 0) ? sc * qmap[c] : 0.f; }, &it, &rel);
         if (!ok) return;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -662,15 +777,15 @@ __global__ void __launch_bounds__(NT, 2) forward_tiled(FwdTiled a) {
             a.c.resid[n - a.n0] = rel;
             if (it >= a.c.max_iter && rel * rel > a.c.tol2) atomicAdd(&a.c.ctl->notconv, 1);
         }
-        // T^{n+1} = T^n + delta (one rounding per step)
-        for (unsigned c = c0; c < N; c += stride) Tn1[c] = Tn[c] + a.c.v.delta[c];
+        // T^{n+1} = T^n + delta, kept as a compensated pair
+        for (unsigned c = c0; c < N; c += stride) add_pair(Tn[c], Tn[N + c], a.c.v.delta[c], Tn1[c], Tn1[N + c]);
         if (!barrier(sy)) return;
         if (a.frames || a.obs) {
             for (unsigned s = c0; s < S; s += stride) {
                 const float v = Tn1[a.obs_off + s];
                 if (a.frames) a.frames[(size_t)n * S + s] = v;
                 if (a.obs) {
-                    const double e = (double)v - (double)a.obs[(size_t)n * S + s];
+                    const double e = ((double)v - (double)a.obs[(size_t)n * S + s]) + (double)Tn1[N + a.obs_off + s];
                     loss += e * e;
                 }
             }
@@ -717,9 +832,10 @@ __global__ void __launch_bounds__(NT, 2) adjoint_tiled(AdjTiled a) {
         const float* ob = a.obs + (size_t)(n - 1) * S;
         int it = 0;
         double rel = 0.0;
-        bool ok = solve(a.c, sy, sm, &ring, mnext,
+        bool ok = solve(a.c, sy, sm, &ring, mnext, mnext + N,
                         [&](unsigned c, int) {
-                            return (c >= a.obs_off && c < a.obs_off + S) ? gs * (Tn[c] - ob[c - a.obs_off]) : 0.f;
+                            return (c >= a.obs_off && c < a.obs_off + S)
+                                       ? gs * ((Tn[c] - ob[c - a.obs_off]) + Tn[N + c]) : 0.f;
                         },
                         &it, &rel);
         if (!ok) return;
@@ -728,7 +844,7 @@ __global__ void __launch_bounds__(NT, 2) adjoint_tiled(AdjTiled a) {
             a.c.resid[a.n1 - n] = rel;
             if (it >= a.c.max_iter && rel * rel > a.c.tol2) atomicAdd(&a.c.ctl->notconv, 1);
         }
-        for (unsigned c = c0; c < N; c += stride) mu[c] = mnext[c] + a.c.v.delta[c];
+        for (unsigned c = c0; c < N; c += stride) add_pair(mnext[c], mnext[N + c], a.c.v.delta[c], mu[c], mu[N + c]);
         if (!barrier(sy)) return;
         // gradient of step n with mu^n and T^n (the next step writes only the
         // other mu buffer and the CG vectors, so no barrier is needed after it)
@@ -737,12 +853,14 @@ __global__ void __launch_bounds__(NT, 2) adjoint_tiled(AdjTiled a) {
             if (x >= g.nx || y >= g.ny) return;
             for (int k = k0; k < k1; ++k) {
                 const unsigned c = (unsigned)k * S + (unsigned)y * g.nx + x;
-                const float ac = a.alpha[c], mc = mu[c], tc = Tn[c];
+                const float ac = a.alpha[c], mc = mu[c], tc = Tn[c], mcl = mu[N + c], tcl = Tn[N + c];
                 float s = 0.f;
                 auto term = [&](unsigned q, float w) {
                     const float aq = a.alpha[q];
                     const float h = aq / (ac + aq);
-                    s += w * h * h * (mc - mu[q]) * (tc - Tn[q]);
+                    const float dm = (mc - mu[q]) + (mcl - mu[N + q]);
+                    const float dT = (tc - Tn[q]) + (tcl - Tn[N + q]);
+                    s += w * h * h * dm * dT;
                 };
                 if (x + 1 < g.nx) term(c + 1, a.wx); else if (g.px) term(c + 1 - g.nx, a.wx);
                 if (x > 0) term(c - 1, a.wx); else if (g.px) term(c + g.nx - 1, a.wx);
@@ -800,8 +918,7 @@ int tiled_grid_blocks(int device) {
 // Tensor maps of one iteration pass (see TmaMaps).  The encoder comes from the
 // driver through the runtime's entry-point query, so no libcuda link is needed.
 bool tiled_encode_maps(tiled::TmaMaps* M, const tiled::Geo& g, float* const u[2], float* const ws[2],
-                       float* const ss[2], float* p, float* delta, const float* cx, const float* cy,
-                       const float* cz) {
+                       float* const ss[2], float* p, float* delta, const float* alpha) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         void* fn = nullptr;
@@ -828,9 +945,8 @@ bool tiled_encode_maps(tiled::TmaMaps* M, const tiled::Geo& g, float* const u[2]
         ok = ok && make(&M->ws[i], ws[i], tiled::HB, tiled::HR);
         ok = ok && make(&M->ss[i], ss[i], tiled::HB, tiled::HR);
     }
-    ok = ok && make(&M->p, p, tiled::TX, tiled::TY) && make(&M->delta, delta, tiled::TX, tiled::TY) &&
-         make(&M->cz, cz, tiled::TX, tiled::TY) && make(&M->cx, cx, tiled::HB, tiled::TY) &&
-         make(&M->cy, cy, tiled::TX, tiled::TY + 1);
+    ok = ok && make(&M->alpha, alpha, tiled::HB, tiled::HR) && make(&M->p, p, tiled::TX, tiled::TY) &&
+         make(&M->delta, delta, tiled::TX, tiled::TY);
     return ok;
 }
 

@@ -126,15 +126,15 @@ struct Vecs {
 // TMA descriptors of the arrays one CG iteration reads (tiled FP32 path).
 struct TmaMaps {
     CUtensorMap u[2], ws[2], ss[2];   // box 40 x 18 at (x0-4, y0-1, k)
-    CUtensorMap p, delta, cz;         // box 32 x 16 at (x0, y0, k)
-    CUtensorMap cx;                   // box 40 x 16 at (x0-4, y0, k)
-    CUtensorMap cy;                   // box 32 x 17 at (x0, y0-1, k)
+    CUtensorMap alpha;                // box 40 x 18 at (x0-4, y0-1, k)
+    CUtensorMap p, delta;             // box 32 x 16 at (x0, y0, k)
 };
 
 struct Common {
     Geo g;
     const TmaMaps* maps;   // device copy of the descriptors, or null (plain loads)
-    const float* cx; const float* cy; const float* cz;   // dt * a of the +x/+y/+z face
+    const float* alpha;    // cell diffusivity; face values are recomputed from it
+    float kx, ky, kz;      // dt / h_d^2
     float robin;           // dt h / dz on k = nz-1
     Vecs v;
     DevCtl* ctl;
@@ -178,8 +178,7 @@ int tiled_grid_blocks(int device);
 int tiled_dynamic_smem();
 // Fill `maps` for the given device buffers; false if the driver refused.
 bool tiled_encode_maps(tiled::TmaMaps* maps, const tiled::Geo& g, float* const u[2], float* const ws[2],
-                       float* const ss[2], float* p, float* delta, const float* cx, const float* cy,
-                       const float* cz);
+                       float* const ss[2], float* p, float* delta, const float* alpha);
 cudaError_t launch_forward_tiled(const tiled::FwdTiled& a, int grid, cudaStream_t s);
 cudaError_t launch_adjoint_tiled(const tiled::AdjTiled& a, int grid, cudaStream_t s);
 
