@@ -150,6 +150,37 @@ nefty_status nefty_adjoint_grad(nefty_handle *h, const nefty_problem *p, const v
                                 const void *q_full, const void *obs, double *loss_out,
                                 void *grad_alpha, void *grad_T0, nefty_stats *stats, void *stream);
 
+/* Forward sweep that allocates no device memory.
+ *
+ * The paper has no counterpart; this is an integration entry point.  Some
+ * callers may not allocate device memory when they need a solve: code running
+ * while a stream is captured into a CUDA graph in global capture mode (where
+ * cudaMalloc is an illegal call), real-time or serving loops that reserve the
+ * whole device up front and cannot take the implicit synchronisation of
+ * cudaMalloc/cudaFree, and hosts that hand out memory only from their own
+ * pool.  This call needs no handle and calls no allocator: its scratch is one
+ * static device array of 48 MiB that every GPU loading the library holds until
+ * the process exits.
+ *
+ *   device      CUDA device to run on (made current for the call, then restored).
+ *   p           as for nefty_forward (FP32 or FP64; the FP64 kernel family of
+ *               nefty_forward runs in both precisions here).
+ *   alpha, T0, q_face, frames_out, T_final, obs: as for nefty_forward, but every
+ *               non-NULL array must be DEVICE memory (no host staging).
+ *   loss_out    host double*, or NULL; needs obs.
+ * Limits: the problem's scratch, 10 values per cell (40 B FP32, 80 B FP64) plus
+ * about 2 MiB of fixed tables, must fit the 48 MiB array (e.g. about 1.1 M cells
+ * FP32, 0.57 M cells FP64), and nt <= 65536; larger problems return NEFTY_EINVAL
+ * with a message, and so do host arrays.
+ * The first call on each device resolves the array's device address; make that
+ * first call before any stream capture.  All calls on a device share the array
+ * and it keeps the last call's contents (the call clears what must start at
+ * zero), so calls whose work overlaps on the GPU race and must be serialised by
+ * the caller.  Returns after the work on `stream` has completed. */
+nefty_status nefty_forward_static(int device, const nefty_problem *p, const void *alpha, const void *T0,
+                                  const void *q_face, int32_t q_steps, void *frames_out, void *T_final,
+                                  const void *obs, double *loss_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -65,6 +65,8 @@ _SIGNATURES = {
                        ctypes.POINTER(ctypes.c_double), _ST, _vp], ctypes.c_int),
     "nefty_adjoint_grad": ([_vp, _P, _vp, _vp, _vp, ctypes.c_int32, _vp, _vp,
                             ctypes.POINTER(ctypes.c_double), _vp, _vp, _ST, _vp], ctypes.c_int),
+    "nefty_forward_static": ([ctypes.c_int, _P, _vp, _vp, _vp, ctypes.c_int32, _vp, _vp, _vp,
+                              ctypes.POINTER(ctypes.c_double), _vp], ctypes.c_int),
 }
 
 

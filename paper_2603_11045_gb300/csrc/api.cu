@@ -28,6 +28,8 @@ struct nefty_handle {
 
 static thread_local std::string t_err;
 
+void nefty::set_thread_error(const char* msg) { t_err = msg; }
+
 namespace {
 
 nefty_status fail(nefty_handle* h, nefty_status s, const std::string& msg) {

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace nefty {
 
 // Threads per CTA of the persistent solver kernels.
@@ -85,6 +87,10 @@ struct AdjArgs {
     int* iters;                        // per-step iterations, index n1 - n
     double* resid;
 };
+
+// Message returned by nefty_last_error(NULL) on the calling thread (api.cu).
+void set_thread_error(const char* msg);
+inline void set_thread_error(const std::string& msg) { set_thread_error(msg.c_str()); }
 
 // Launch helpers (solver.cu).  All are stream-ordered.
 int solver_grid_blocks(int device, int prec);
