@@ -39,6 +39,12 @@ UNIT = "Gcell-steps/s"
 # solution write (8 B).  FP64 doubles both.
 ALG_BYTES_ITER = {"fp32": 40, "fp64": 80}
 ALG_BYTES_STEP = {"fp32": 8, "fp64": 16}
+# DRAM bytes per cell per solver pass of the FP32 CG kernels, from the ncu
+# capture summarised in profiles/forward_tiled_256x256x48_nt20_ncu.md (28.9 GB
+# over 378 passes of 3,145,728 cells), scaled to the timed launches by their
+# pass count (CG iterations plus the init/finalise/gradient passes of each
+# solve).  None = no capture of the current kernels.
+DRAM_BYTES_PER_CELL_PASS = {"fp32": 24.3, "fp64": None}
 
 
 def parse():
@@ -241,8 +247,12 @@ def run_native(args):
     pk = peaks()
     peak = pk["hbm_gbs"] if pk else 6800.0
     achieved = alg_bytes / (cg_ms / 1000.0) / 1e9
+    st0 = stats[0]
+    passes = (iters + 3 * (st0["fwd_steps"] + st0["recompute_steps"]) + 4 * st0["adj_steps"])
+    bpp = DRAM_BYTES_PER_CELL_PASS[R]
+    traffic = None if bpp is None else bpp * w.n_cells * passes
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "persistent fused Jacobi-PCG (forward_kernel + adjoint_kernel)",
+                "traffic": traffic, "traffic_note": "DRAM bytes per step, ncu capture scaled by solver passes", "kernel": "persistent fused Jacobi-PCG (forward_kernel + adjoint_kernel)",
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback",
                 "cg_ms_per_step": cg_ms, "alg_bytes_per_step": alg_bytes,
                 "mean_cg_iters_per_solve": iters / max(1, steps_solved)}
