@@ -150,6 +150,58 @@ nefty_status nefty_adjoint_grad(nefty_handle *h, const nefty_problem *p, const v
                                 const void *q_full, const void *obs, double *loss_out,
                                 void *grad_alpha, void *grad_T0, nefty_stats *stats, void *stream);
 
+/* Neural diffusivity field (Sec. 4.1, App. D.1).  Cell centres x_d = 2(i+1/2)/N_d - 1
+ * are encoded with n_freq log-spaced bands per axis, w_b = freq_lo (freq_hi/freq_lo)^(b/(n_freq-1)):
+ * features d*2F + 2b, d*2F + 2b + 1 = band_weights[b] * (sin(w_b x_d), cos(w_b x_d)) (band
+ * weights: the frequency-annealing weights of Eq. fa_schedule, NULL = 1).  Then `depth` hidden
+ * ReLU layers of `width` units and a linear output f; alpha = alpha_min + (alpha_max - alpha_min)
+ * * sigmoid(f) (Eq. bracket).  Dense layers run in BF16 on the tensor cores with FP32
+ * accumulation; features, head, biases and gradients are FP32.
+ * Parameter vector (FP32, packed): W_0 [width x 6 n_freq], b_0 [width], then W_l [width x width],
+ * b_l [width] for l = 1 .. depth-1, then w_out [width], b_out [1]; weights row-major [out][in].
+ * Constraints: n_freq a multiple of 32, width a multiple of 128, 1 <= depth <= 15,
+ * 0 < freq_lo <= freq_hi, 0 < alpha_min < alpha_max. */
+typedef struct {
+    int32_t nx, ny, nz;     /* grid; the field is evaluated at every cell centre */
+    int32_t n_freq;         /* bands per axis */
+    int32_t width;          /* hidden width */
+    int32_t depth;          /* hidden layers */
+    double freq_lo, freq_hi;
+    double alpha_min, alpha_max;
+} nefty_field_desc;
+
+/* Number of FP32 parameters of the packed vector for `d` (0 if d is invalid). */
+uint64_t nefty_field_param_count(const nefty_field_desc *d);
+
+/* alpha_out [nz*ny*nx] (float) = field(theta) at every cell centre.
+ * theta [param_count] FP32; band_weights [n_freq] FP32 or NULL. */
+nefty_status nefty_field_eval(nefty_handle *h, const nefty_field_desc *d, const float *theta,
+                              const float *band_weights, float *alpha_out, void *stream);
+
+/* grad_theta [param_count] (overwritten) = (d alpha / d theta)^T grad_alpha, with
+ * grad_alpha [nz*ny*nx] FP32 (e.g. dJ/dalpha from nefty_adjoint_grad plus the TV term). */
+nefty_status nefty_field_backward(nefty_handle *h, const nefty_field_desc *d, const float *theta,
+                                  const float *band_weights, const float *grad_alpha, float *grad_theta,
+                                  void *stream);
+
+/* The field's tensor-core GEMM on its own: C[M x N] (FP32, row-major, ld N) =
+ * A[M x K] B[N x K]^T with A, B BF16 row-major (lda, ldb in elements, multiples of 8)
+ * and K a multiple of 64.  Device pointers only. */
+nefty_status nefty_gemm_bf16(nefty_handle *h, const void *A, int32_t lda, const void *B, int32_t ldb, int32_t M,
+                             int32_t N, int32_t K, float *C, void *stream);
+
+/* Total-variation regulariser (Eq. tv_discrete) and its gradient:
+ *   lam * R(alpha),  R = dx dy dz * sum_cells sqrt((d_x a/dx)^2 + (d_y a/dy)^2 + (d_z a/dz)^2 + eps^2)
+ * with forward differences; the lateral ones wrap when p->bc is periodic and
+ * vanish on the last column/row with zero-flux walls; the z difference
+ * vanishes on the last slice.
+ *   alpha             [nz*ny*nx] (float for FP32, double for FP64).
+ *   tv_out            host double*: lam * R, or NULL.
+ *   grad_alpha_accum  [nz*ny*nx]: lam * dR/dalpha is ADDED to it, or NULL.
+ * lam, eps >= 0 and finite. */
+nefty_status nefty_tv(nefty_handle *h, const nefty_problem *p, const void *alpha, double lam, double eps,
+                      double *tv_out, void *grad_alpha_accum, void *stream);
+
 /* Forward sweep that allocates no device memory.
  *
  * The paper has no counterpart; this is an integration entry point.  Some

@@ -28,6 +28,13 @@ class nefty_problem(ctypes.Structure):
                 ("loss_scale", ctypes.c_double)]
 
 
+class nefty_field_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("n_freq", ctypes.c_int32), ("width", ctypes.c_int32), ("depth", ctypes.c_int32),
+                ("freq_lo", ctypes.c_double), ("freq_hi", ctypes.c_double),
+                ("alpha_min", ctypes.c_double), ("alpha_max", ctypes.c_double)]
+
+
 class nefty_stats(ctypes.Structure):
     _fields_ = [("fwd_iters", ctypes.c_int64), ("recompute_iters", ctypes.c_int64),
                 ("adj_iters", ctypes.c_int64), ("fwd_steps", ctypes.c_int32),
@@ -65,6 +72,13 @@ _SIGNATURES = {
                        ctypes.POINTER(ctypes.c_double), _ST, _vp], ctypes.c_int),
     "nefty_adjoint_grad": ([_vp, _P, _vp, _vp, _vp, ctypes.c_int32, _vp, _vp,
                             ctypes.POINTER(ctypes.c_double), _vp, _vp, _ST, _vp], ctypes.c_int),
+    "nefty_field_param_count": ([ctypes.c_void_p], ctypes.c_uint64),
+    "nefty_field_eval": ([_vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "nefty_field_backward": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "nefty_gemm_bf16": ([_vp, _vp, ctypes.c_int32, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                         ctypes.c_int32, _vp, _vp], ctypes.c_int),
+    "nefty_tv": ([_vp, _P, _vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _vp, _vp],
+                 ctypes.c_int),
     "nefty_forward_static": ([ctypes.c_int, _P, _vp, _vp, _vp, ctypes.c_int32, _vp, _vp, _vp,
                               ctypes.POINTER(ctypes.c_double), _vp], ctypes.c_int),
 }

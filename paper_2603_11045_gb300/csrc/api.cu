@@ -849,3 +849,172 @@ nefty_status nefty_adjoint_grad(nefty_handle* h, const nefty_problem* p, const v
 }
 
 }  // extern "C"
+
+namespace {
+
+bool field_dims(const nefty_field_desc* d, FieldDims* out, std::string* why) {
+    if (!d) { *why = "field descriptor is NULL"; return false; }
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1) { *why = "field grid must be >= 1 in each direction"; return false; }
+    const double cells = (double)d->nx * d->ny * d->nz;
+    if (cells >= 2147483647.0 - 128) { *why = "field grid too large"; return false; }
+    if (d->n_freq < 32 || d->n_freq % 32 != 0) { *why = "n_freq must be a positive multiple of 32"; return false; }
+    if (d->width < 128 || d->width % 128 != 0) { *why = "width must be a positive multiple of 128"; return false; }
+    if (d->depth < 1 || d->depth > 15) { *why = "depth must be in 1..15"; return false; }
+    if (!(d->freq_lo > 0) || !(d->freq_hi >= d->freq_lo) || !std::isfinite(d->freq_hi)) {
+        *why = "need 0 < freq_lo <= freq_hi";
+        return false;
+    }
+    if (!(d->alpha_min > 0) || !(d->alpha_max > d->alpha_min) || !std::isfinite(d->alpha_max)) {
+        *why = "need 0 < alpha_min < alpha_max";
+        return false;
+    }
+    if (out) {
+        out->nx = d->nx; out->ny = d->ny; out->nz = d->nz;
+        out->M = (unsigned)cells;
+        out->Mp = (out->M + 127u) / 128u * 128u;
+        out->F = d->n_freq; out->W = d->width; out->depth = d->depth;
+        out->freq_lo = d->freq_lo; out->freq_hi = d->freq_hi;
+        out->alpha_min = d->alpha_min; out->alpha_max = d->alpha_max;
+        // split-K so the weight-gradient GEMMs cover about two waves of CTAs
+        const int kblocks = (int)(out->Mp / 64);
+        const int tiles = (out->W / 128) * ((6 * out->F > out->W ? 6 * out->F : out->W) / 128);
+        int sp = std::max(1, 304 / std::max(1, tiles));
+        out->splits = std::min(sp, kblocks);
+        out->colsum_blocks = (int)std::min<unsigned>(1024u, std::max(1u, out->Mp / 256u));
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t nefty_field_param_count(const nefty_field_desc* d) {
+    FieldDims fd;
+    std::string why;
+    if (!field_dims(d, &fd, &why)) return 0;
+    return field_param_count(fd.F, fd.W, fd.depth);
+}
+
+static nefty_status field_call(nefty_handle* h, const nefty_field_desc* d, const float* theta,
+                               const float* band_weights, const float* grad_alpha, float* out, bool backward,
+                               void* stream) {
+    if (!h) return fail(nullptr, NEFTY_EINVAL, "handle is NULL");
+    FieldDims fd;
+    std::string why;
+    if (!field_dims(d, &fd, &why)) return fail(h, NEFTY_EINVAL, why);
+    if (!theta || !out || (backward && !grad_alpha)) return fail(h, NEFTY_EINVAL, "missing array argument");
+    DeviceGuard guard(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t P = field_param_count(fd.F, fd.W, fd.depth);
+    Input th, bw, ga;
+    th.plan(theta, P * 4);
+    bw.plan(band_weights, (size_t)fd.F * 4);
+    ga.plan(backward ? grad_alpha : nullptr, (size_t)fd.M * 4);
+    Output o;
+    o.plan(out, (backward ? P : (size_t)fd.M) * 4);
+    char* fws = nullptr;
+    const size_t fbytes = field_workspace_bytes(fd, backward);
+    auto layout = [&](Arena& a) {
+        th.place(a); bw.place(a); ga.place(a); o.place(a);
+        fws = (char*)a.take(fbytes);
+    };
+    Arena probe;
+    layout(probe);
+    if (nefty_status e = ensure_workspace(h, probe.off)) return e;
+    Arena arena;
+    arena.base = (char*)h->ws;
+    layout(arena);
+    for (Input* in : {&th, &bw, &ga})
+        if (in->user && in->stage) NEFTY_CUDA(h, cudaMemcpyAsync(in->dev, in->user, in->bytes, cudaMemcpyHostToDevice, s));
+    if (backward)
+        NEFTY_CUDA(h, field_backward(fd, (const float*)th.dev, (const float*)bw.dev, (const float*)ga.dev,
+                                     (float*)o.dev, fws, s));
+    else
+        NEFTY_CUDA(h, field_eval(fd, (const float*)th.dev, (const float*)bw.dev, (float*)o.dev, fws, s));
+    if (o.stage) NEFTY_CUDA(h, cudaMemcpyAsync(o.user, o.dev, o.bytes, cudaMemcpyDeviceToHost, s));
+    const int err = field_error(fd, fws, s, backward);
+    if (err < 0) return fail(h, NEFTY_ECUDA, "field: stream synchronisation failed");
+    if (err > 0) return fail(h, NEFTY_ETIMEOUT, "field: a tensor-core pipeline wait timed out");
+    return NEFTY_OK;
+}
+
+nefty_status nefty_field_eval(nefty_handle* h, const nefty_field_desc* d, const float* theta,
+                              const float* band_weights, float* alpha_out, void* stream) {
+    return field_call(h, d, theta, band_weights, nullptr, alpha_out, false, stream);
+}
+
+nefty_status nefty_field_backward(nefty_handle* h, const nefty_field_desc* d, const float* theta,
+                                  const float* band_weights, const float* grad_alpha, float* grad_theta,
+                                  void* stream) {
+    return field_call(h, d, theta, band_weights, grad_alpha, grad_theta, true, stream);
+}
+
+nefty_status nefty_gemm_bf16(nefty_handle* h, const void* A, int32_t lda, const void* B, int32_t ldb, int32_t M,
+                             int32_t N, int32_t K, float* C, void* stream) {
+    if (!h) return fail(nullptr, NEFTY_EINVAL, "handle is NULL");
+    if (!A || !B || !C || M < 1 || N < 1 || K < 64 || K % 64 || lda % 8 || ldb % 8 || lda < K || ldb < K)
+        return fail(h, NEFTY_EINVAL, "gemm: bad arguments");
+    if (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(C)) return fail(h, NEFTY_EINVAL, "gemm: device pointers only");
+    DeviceGuard guard(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (nefty_status e = ensure_workspace(h, 256)) return e;
+    int* err = (int*)h->ws;
+    NEFTY_CUDA(h, cudaMemsetAsync(err, 0, sizeof(int), s));
+    NEFTY_CUDA(h, umma_gemm((const __nv_bfloat16*)A, lda, (const __nv_bfloat16*)B, ldb, M, N, K, 2, nullptr, nullptr,
+                            nullptr, C, N, 1, err, s));
+    int herr = 0;
+    NEFTY_CUDA(h, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NEFTY_CUDA(h, cudaStreamSynchronize(s));
+    if (herr) return fail(h, NEFTY_ETIMEOUT, "gemm: a tensor-core pipeline wait timed out");
+    return NEFTY_OK;
+}
+
+nefty_status nefty_tv(nefty_handle* h, const nefty_problem* p, const void* alpha, double lam, double eps,
+                      double* tv_out, void* grad_alpha_accum, void* stream) {
+    if (!h) return fail(nullptr, NEFTY_EINVAL, "handle is NULL");
+    Prob P;
+    std::string why;
+    if (check_problem(p, &P, &why)) return fail(h, NEFTY_EINVAL, why);
+    if (!alpha) return fail(h, NEFTY_EINVAL, "alpha is NULL");
+    if (!(lam >= 0) || !std::isfinite(lam) || !(eps >= 0) || !std::isfinite(eps))
+        return fail(h, NEFTY_EINVAL, "lam and eps must be finite and >= 0");
+    DeviceGuard guard(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t R = P.prec == NEFTY_FP32 ? 4 : 8, N = P.N;
+    const int blocks = tv_blocks(P.N);
+    Input a;
+    a.plan(alpha, N * R);
+    Output g;
+    g.plan(grad_alpha_accum, N * R);
+    double* partials = nullptr;
+    auto layout = [&](Arena& ar) {
+        partials = (double*)ar.take((size_t)blocks * sizeof(double));
+        a.place(ar);
+        g.place(ar);
+    };
+    Arena probe;
+    layout(probe);
+    if (nefty_status e = ensure_workspace(h, probe.off)) return e;
+    Arena arena;
+    arena.base = (char*)h->ws;
+    layout(arena);
+    if (a.stage) NEFTY_CUDA(h, cudaMemcpyAsync(a.dev, a.user, a.bytes, cudaMemcpyHostToDevice, s));
+    if (g.user && g.stage) NEFTY_CUDA(h, cudaMemcpyAsync(g.dev, g.user, g.bytes, cudaMemcpyHostToDevice, s));
+    if (P.prec == NEFTY_FP32)
+        NEFTY_CUDA(h, launch_tv<float>((const float*)a.dev, P.nx, P.ny, P.nz, P.bc, P.dx, P.dy, P.dz, lam, eps,
+                                       (float*)g.dev, partials, blocks, s));
+    else
+        NEFTY_CUDA(h, launch_tv<double>((const double*)a.dev, P.nx, P.ny, P.nz, P.bc, P.dx, P.dy, P.dz, lam, eps,
+                                        (double*)g.dev, partials, blocks, s));
+    if (g.user && g.stage) NEFTY_CUDA(h, cudaMemcpyAsync(g.user, g.dev, g.bytes, cudaMemcpyDeviceToHost, s));
+    std::vector<double> part(blocks);
+    NEFTY_CUDA(h, cudaMemcpyAsync(part.data(), partials, blocks * sizeof(double), cudaMemcpyDeviceToHost, s));
+    NEFTY_CUDA(h, cudaStreamSynchronize(s));
+    double t = 0.0;
+    for (double v : part) t += v;
+    if (tv_out) *tv_out = lam * P.dx * P.dy * P.dz * t;
+    return NEFTY_OK;
+}
+
+}  // extern "C"

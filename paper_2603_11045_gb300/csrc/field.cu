@@ -1,0 +1,372 @@
+// Neural diffusivity field (Sec. 4.1, App. D.1): Fourier features of the cell
+// centres -> ReLU MLP -> bounded output, evaluated at every cell, and its
+// backward pass to the parameters.  Dense layers run on tcgen05 (umma_gemm.cu)
+// in BF16 with FP32 accumulation; everything else is FP32.
+//
+// Encoding: centre coordinates x_d = 2 (i + 1/2) / N_d - 1 in (-1, 1); F bands
+// per axis with log-spaced frequencies w_b = freq_lo * (freq_hi/freq_lo)^(b/(F-1));
+// band b of axis d contributes (wt_b sin(w_b x_d), wt_b cos(w_b x_d)) at feature
+// indices d*2F + 2b and d*2F + 2b + 1, wt_b being the band's annealing weight
+// (Eq. fa_schedule; 1 when none is given).  The encoding is separable, so it is
+// tabulated per axis once and assembled per cell.
+//
+// Network: h_0 = gamma(x) (6F), h_{l+1} = relu(W_l h_l + b_l) for l < depth
+// (width W), f = w_out . h_depth + b_out, alpha = alpha_min +
+// (alpha_max - alpha_min) * sigmoid(f) (Eq. bracket).
+//
+// Parameter vector theta (FP32, packed): W_0 [W x 6F], b_0 [W], then for
+// l = 1 .. depth-1: W_l [W x W], b_l [W]; then w_out [W], b_out [1].  Weights are
+// row-major [out][in].
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace nefty {
+namespace {
+
+constexpr int kT = 256;
+
+__global__ void axis_table_kernel(float* tab, int n, int F, float lo, float ratio_log, const float* band_w) {
+    // tab[i][2b + {0,1}] for cell index i along one axis
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * F; e += gridDim.x * blockDim.x) {
+        const int i = e / F, b = e % F;
+        const float x = 2.f * ((float)i + 0.5f) / (float)n - 1.f;
+        const float w = F > 1 ? lo * expf(ratio_log * (float)b / (float)(F - 1)) : lo;
+        const float wt = band_w ? band_w[b] : 1.f;
+        tab[(size_t)i * 2 * F + 2 * b] = wt * sinf(w * x);
+        tab[(size_t)i * 2 * F + 2 * b + 1] = wt * cosf(w * x);
+    }
+}
+
+// h0[c][d*2F + j] = tab_d[index_d(c)][j], as BF16, rows padded to Mp (zeros).
+__global__ void features_kernel(__nv_bfloat16* h0, unsigned M, unsigned Mp, int nx, int ny, int F,
+                                const float* tx, const float* ty, const float* tz) {
+    const int D = 6 * F;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)Mp * D;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const unsigned c = (unsigned)(e / D);
+        const int f = (int)(e % D);
+        float v = 0.f;
+        if (c < M) {
+            const unsigned i = c % nx, j = (c / nx) % ny, k = c / ((unsigned)nx * ny);
+            const int d = f / (2 * F), r = f % (2 * F);
+            v = d == 0 ? tx[(size_t)i * 2 * F + r] : (d == 1 ? ty[(size_t)j * 2 * F + r] : tz[(size_t)k * 2 * F + r]);
+        }
+        h0[e] = __float2bfloat16_rn(v);
+    }
+}
+
+__global__ void to_bf16_kernel(const float* src, __nv_bfloat16* dst, size_t n) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        dst[e] = __float2bfloat16_rn(src[e]);
+}
+
+// dst[c][r] = bf16(src[r][c]) : transpose of a [R x C] FP32 matrix to BF16.
+__global__ void transpose_f32_bf16_kernel(const float* src, __nv_bfloat16* dst, int R, int C) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)R * C;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / R), r = (int)(e % R);
+        dst[e] = __float2bfloat16_rn(src[(size_t)r * C + c]);
+    }
+}
+
+// dst[c][r] = src[r][c] for a BF16 [R x C] matrix (R rows = points), tiled.
+__global__ void transpose_bf16_kernel(const __nv_bfloat16* src, __nv_bfloat16* dst, unsigned R, int C) {
+    __shared__ __nv_bfloat16 t[32][33];
+    const unsigned r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        const unsigned r = r0 + yy, c = c0 + threadIdx.x;
+        t[yy][threadIdx.x] = (r < R && c < (unsigned)C) ? src[(size_t)r * C + c] : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        const unsigned c = c0 + yy, r = r0 + threadIdx.x;
+        if (c < (unsigned)C && r < R) dst[(size_t)c * R + r] = t[threadIdx.x][yy];
+    }
+}
+
+// Output head: f = w_out . h + b_out, alpha = lo + (hi - lo) sigmoid(f).
+__global__ void head_kernel(const __nv_bfloat16* h, int W, const float* w_out, const float* b_out, unsigned M,
+                            float a_lo, float a_hi, float* alpha) {
+    const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (unsigned m = warp; m < M; m += nwarps) {
+        float s = 0.f;
+        for (int j = lane; j < W; j += 32) s += __bfloat162float(h[(size_t)m * W + j]) * w_out[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            const float f = s + b_out[0];
+            alpha[m] = a_lo + (a_hi - a_lo) / (1.f + expf(-f));
+        }
+    }
+}
+
+// Backward of the head: g_f = g_alpha (hi - lo) sig (1 - sig);
+// delta[m][j] = bf16(g_f w_out[j] [h[m][j] > 0]); gf[m] kept for dw_out, db_out.
+__global__ void head_back_kernel(const __nv_bfloat16* h, int W, const float* w_out, const float* b_out,
+                                 unsigned M, unsigned Mp, float a_lo, float a_hi, const float* g_alpha, float* gf,
+                                 __nv_bfloat16* delta) {
+    const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (unsigned m = warp; m < Mp; m += nwarps) {
+        float g = 0.f;
+        if (m < M) {
+            float s = 0.f;
+            for (int j = lane; j < W; j += 32) s += __bfloat162float(h[(size_t)m * W + j]) * w_out[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            const float sg = 1.f / (1.f + expf(-(s + b_out[0])));
+            g = g_alpha[m] * (a_hi - a_lo) * sg * (1.f - sg);
+        }
+        if (lane == 0) gf[m] = g;
+        for (int j = lane; j < W; j += 32) {
+            const float hv = __bfloat162float(h[(size_t)m * W + j]);
+            delta[(size_t)m * W + j] = __float2bfloat16_rn(hv > 0.f ? g * w_out[j] : 0.f);
+        }
+    }
+}
+
+// out[j] = sum_m A[m][j] * (v ? v[m] : 1) over rows, in fixed order:
+// per-block partial sums, then a second pass.  A is BF16 or FP32.
+template <typename T>
+__device__ __forceinline__ float ld(const T* p, size_t i);
+template <>
+__device__ __forceinline__ float ld<float>(const float* p, size_t i) { return p[i]; }
+template <>
+__device__ __forceinline__ float ld<__nv_bfloat16>(const __nv_bfloat16* p, size_t i) {
+    return __bfloat162float(p[i]);
+}
+
+template <typename T>
+__global__ void colsum_partial_kernel(const T* A, const float* v, unsigned M, int C, unsigned rows_per_block,
+                                      double* part) {
+    const unsigned r0 = blockIdx.x * rows_per_block, r1 = min(M, r0 + rows_per_block);
+    for (int j = threadIdx.x; j < C; j += blockDim.x) {
+        float s = 0.f;   // FP32 within a block of rows, FP64 across blocks
+        for (unsigned m = r0; m < r1; ++m) s += ld<T>(A, (size_t)m * C + j) * (v ? v[m] : 1.f);
+        part[(size_t)blockIdx.x * C + j] = (double)s;
+    }
+}
+
+__global__ void colsum_final_kernel(const double* part, int nblk, int C, float* out) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < C; j += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += part[(size_t)b * C + j];
+        out[j] = (float)s;
+    }
+}
+
+// sum of split-K partials [splits][R][C] -> out[R][C] (fixed order)
+__global__ void split_reduce_kernel(const float* part, int splits, size_t n, float* out) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < splits; ++z) s += part[(size_t)z * n + e];
+        out[e] = s;
+    }
+}
+
+inline unsigned blocks_for(size_t n, unsigned t = kT) {
+    size_t b = (n + t - 1) / t;
+    if (b > 65535u * 16u) b = 65535u * 16u;
+    return (unsigned)(b ? b : 1);
+}
+
+}  // namespace
+
+size_t field_param_count(int F, int W, int depth) {
+    return (size_t)W * 6 * F + W + (size_t)(depth - 1) * ((size_t)W * W + W) + W + 1;
+}
+
+// Workspace of one field call (bytes) for M points.
+size_t field_workspace_bytes(const FieldDims& d, bool backward) {
+    const size_t Mp = d.Mp, W = d.W, D = (size_t)6 * d.F;
+    size_t b = 0;
+    auto add = [&](size_t x) { b += (x + 255) & ~(size_t)255; };
+    add((size_t)(d.nx + d.ny + d.nz) * 2 * d.F * 4);   // axis tables
+    add(Mp * D * 2);                                    // h0
+    for (int l = 0; l < d.depth; ++l) add(Mp * W * 2);  // h1 .. h_depth
+    add(((size_t)W * D + (size_t)(d.depth - 1) * W * W) * 2);   // BF16 weights
+    add(sizeof(int));
+    if (backward) {
+        add(((size_t)W * D + (size_t)(d.depth - 1) * W * W) * 2);   // transposed weights (unused for l = 0)
+        add(Mp * W * 2 * 2);     // delta ping-pong
+        add(Mp * 4);             // g_f
+        add(Mp * (W > D ? W : D) * 2 * 2);   // transposes of delta and h
+        add((size_t)d.splits * W * (W > D ? W : D) * 4);   // split-K partials
+        add((size_t)d.colsum_blocks * (W > D ? W : D) * 8);   // column-sum partials
+    }
+    return b;
+}
+
+// Carves the workspace identically to field_workspace_bytes.
+struct FieldWs {
+    float *tx, *ty, *tz;
+    __nv_bfloat16* h[16];
+    __nv_bfloat16* wb;      // BF16 weights, layer l at offset woff[l]
+    __nv_bfloat16* wt;      // BF16 transposed weights
+    __nv_bfloat16* dl[2];
+    float* gf;
+    __nv_bfloat16 *tA, *tB;
+    float* split;
+    double* colpart;
+    int* err;
+};
+
+static FieldWs carve(char* base, const FieldDims& d, bool backward) {
+    const size_t Mp = d.Mp, W = d.W, D = (size_t)6 * d.F, WD = W > D ? W : D;
+    FieldWs w{};
+    size_t off = 0;
+    auto take = [&](size_t x) { char* p = base + off; off += (x + 255) & ~(size_t)255; return p; };
+    char* tab = take((size_t)(d.nx + d.ny + d.nz) * 2 * d.F * 4);
+    w.tx = (float*)tab;
+    w.ty = w.tx + (size_t)d.nx * 2 * d.F;
+    w.tz = w.ty + (size_t)d.ny * 2 * d.F;
+    w.h[0] = (__nv_bfloat16*)take(Mp * D * 2);
+    for (int l = 1; l <= d.depth; ++l) w.h[l] = (__nv_bfloat16*)take(Mp * W * 2);
+    w.wb = (__nv_bfloat16*)take((W * D + (size_t)(d.depth - 1) * W * W) * 2);
+    w.err = (int*)take(sizeof(int));
+    if (backward) {
+        w.wt = (__nv_bfloat16*)take((W * D + (size_t)(d.depth - 1) * W * W) * 2);
+        char* dd = take(Mp * W * 2 * 2);
+        w.dl[0] = (__nv_bfloat16*)dd;
+        w.dl[1] = w.dl[0] + Mp * W;
+        w.gf = (float*)take(Mp * 4);
+        char* tt = take(Mp * WD * 2 * 2);
+        w.tA = (__nv_bfloat16*)tt;
+        w.tB = w.tA + Mp * WD;
+        w.split = (float*)take((size_t)d.splits * W * WD * 4);
+        w.colpart = (double*)take((size_t)d.colsum_blocks * WD * 8);
+    }
+    return w;
+}
+
+static cudaError_t forward_layers(const FieldDims& d, const float* theta, const float* band_w, FieldWs& w,
+                                  cudaStream_t s) {
+    const int F = d.F, W = d.W, D = 6 * F;
+    const float lo = (float)d.freq_lo, ratio_log = (float)log(d.freq_hi / d.freq_lo);
+    axis_table_kernel<<<blocks_for((size_t)d.nx * F), kT, 0, s>>>(w.tx, d.nx, F, lo, ratio_log, band_w);
+    axis_table_kernel<<<blocks_for((size_t)d.ny * F), kT, 0, s>>>(w.ty, d.ny, F, lo, ratio_log, band_w);
+    axis_table_kernel<<<blocks_for((size_t)d.nz * F), kT, 0, s>>>(w.tz, d.nz, F, lo, ratio_log, band_w);
+    features_kernel<<<blocks_for((size_t)d.Mp * D), kT, 0, s>>>(w.h[0], d.M, d.Mp, d.nx, d.ny, F, w.tx, w.ty, w.tz);
+    // BF16 copies of the weights
+    const float* p = theta;
+    size_t woff = 0;
+    for (int l = 0; l < d.depth; ++l) {
+        const int in = l == 0 ? D : W;
+        to_bf16_kernel<<<blocks_for((size_t)W * in), kT, 0, s>>>(p, w.wb + woff, (size_t)W * in);
+        p += (size_t)W * in + W;
+        woff += (size_t)W * in;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    p = theta;
+    woff = 0;
+    for (int l = 0; l < d.depth; ++l) {
+        const int in = l == 0 ? D : W;
+        const float* bias = p + (size_t)W * in;
+        e = umma_gemm(w.h[l], in, w.wb + woff, in, (int)d.Mp, W, in, 0 /*bias+relu*/, bias, nullptr, w.h[l + 1],
+                      nullptr, W, 1, w.err, s);
+        if (e != cudaSuccess) return e;
+        p += (size_t)W * in + W;
+        woff += (size_t)W * in;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t field_eval(const FieldDims& d, const float* theta, const float* band_w, float* alpha, char* ws,
+                       cudaStream_t s) {
+    FieldWs w = carve(ws, d, false);
+    cudaError_t e = cudaMemsetAsync(w.err, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    if ((e = forward_layers(d, theta, band_w, w, s)) != cudaSuccess) return e;
+    const float* w_out = theta + field_param_count(d.F, d.W, d.depth) - d.W - 1;
+    head_kernel<<<blocks_for((size_t)d.M * 32), kT, 0, s>>>(w.h[d.depth], d.W, w_out, w_out + d.W, d.M,
+                                                            (float)d.alpha_min, (float)d.alpha_max, alpha);
+    return cudaGetLastError();
+}
+
+cudaError_t field_backward(const FieldDims& d, const float* theta, const float* band_w, const float* g_alpha,
+                           float* g_theta, char* ws, cudaStream_t s) {
+    FieldWs w = carve(ws, d, true);
+    const int F = d.F, W = d.W, D = 6 * F;
+    cudaError_t e = cudaMemsetAsync(w.err, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    if ((e = forward_layers(d, theta, band_w, w, s)) != cudaSuccess) return e;
+    // parameter offsets
+    size_t poff[16], woff[16];
+    {
+        size_t p = 0, q = 0;
+        for (int l = 0; l < d.depth; ++l) {
+            const int in = l == 0 ? D : W;
+            poff[l] = p;
+            woff[l] = q;
+            p += (size_t)W * in + W;
+            q += (size_t)W * in;
+        }
+        poff[d.depth] = p;
+    }
+    const float* w_out = theta + poff[d.depth];
+    float* g_wout = g_theta + poff[d.depth];
+    // head
+    head_back_kernel<<<blocks_for((size_t)d.Mp * 32), kT, 0, s>>>(w.h[d.depth], W, w_out, w_out + W, d.M, d.Mp,
+                                                                  (float)d.alpha_min, (float)d.alpha_max, g_alpha,
+                                                                  w.gf, w.dl[0]);
+    // dw_out[j] = sum_m gf[m] h[m][j];  db_out = sum_m gf[m]
+    const unsigned rpb = (d.Mp + d.colsum_blocks - 1) / d.colsum_blocks;
+    colsum_partial_kernel<__nv_bfloat16><<<d.colsum_blocks, kT, 0, s>>>(w.h[d.depth], w.gf, d.Mp, W, rpb, w.colpart);
+    colsum_final_kernel<<<blocks_for(W), kT, 0, s>>>(w.colpart, d.colsum_blocks, W, g_wout);
+    colsum_partial_kernel<float><<<d.colsum_blocks, kT, 0, s>>>(w.gf, nullptr, d.Mp, 1, rpb, w.colpart);
+    colsum_final_kernel<<<1, 32, 0, s>>>(w.colpart, d.colsum_blocks, 1, g_wout + W);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // transposed BF16 weights W_l^T [in x W] for the input-gradient GEMMs
+    {
+        const float* p = theta;
+        for (int l = 0; l < d.depth; ++l) {
+            const int in = l == 0 ? D : W;
+            transpose_f32_bf16_kernel<<<blocks_for((size_t)W * in), kT, 0, s>>>(p, w.wt + woff[l], W, in);
+            p += (size_t)W * in + W;
+        }
+    }
+    // layers, top to bottom: delta_l = dJ/dz_{l+1} [Mp x W] lives in dl[cur]
+    int cur = 0;
+    const dim3 tb(32, 8);
+    for (int l = d.depth - 1; l >= 0; --l) {
+        const int in = l == 0 ? D : W;
+        // db_l = column sums of delta
+        colsum_partial_kernel<__nv_bfloat16><<<d.colsum_blocks, kT, 0, s>>>(w.dl[cur], nullptr, d.Mp, W, rpb,
+                                                                          w.colpart);
+        colsum_final_kernel<<<blocks_for(W), kT, 0, s>>>(w.colpart, d.colsum_blocks, W,
+                                                         g_theta + poff[l] + (size_t)W * in);
+        // dW_l = delta^T h_l: K-major operands are the transposes [W x Mp] and [in x Mp]
+        transpose_bf16_kernel<<<dim3((d.Mp + 31) / 32, (W + 31) / 32), tb, 0, s>>>(w.dl[cur], w.tA, d.Mp, W);
+        transpose_bf16_kernel<<<dim3((d.Mp + 31) / 32, (in + 31) / 32), tb, 0, s>>>(w.h[l], w.tB, d.Mp, in);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        e = umma_gemm(w.tA, (int)d.Mp, w.tB, (int)d.Mp, W, in, (int)d.Mp, 2 /*f32 partials*/, nullptr, nullptr,
+                      nullptr, w.split, in, d.splits, w.err, s);
+        if (e != cudaSuccess) return e;
+        split_reduce_kernel<<<blocks_for((size_t)W * in), kT, 0, s>>>(w.split, d.splits, (size_t)W * in,
+                                                                      g_theta + poff[l]);
+        // delta_{l-1} = (delta_l W_l) masked by h_l > 0
+        if (l > 0) {
+            e = umma_gemm(w.dl[cur], W, w.wt + woff[l], W, (int)d.Mp, in, W, 1 /*mask*/, nullptr, w.h[l],
+                          w.dl[cur ^ 1], nullptr, in, 1, w.err, s);
+            if (e != cudaSuccess) return e;
+            cur ^= 1;
+        }
+    }
+    return cudaGetLastError();
+}
+
+int field_error(const FieldDims& d, char* ws, cudaStream_t s, bool backward) {
+    FieldWs w = carve(ws, d, backward);
+    int h = 0;
+    if (cudaMemcpyAsync(&h, w.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return -1;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+    return h;
+}
+
+}  // namespace nefty

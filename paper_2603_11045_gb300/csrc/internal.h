@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -106,6 +107,13 @@ cudaError_t launch_adjoint(const AdjArgs<Real>& a, int grid, cudaStream_t s);
 template <typename Real>
 cudaError_t launch_cast(const double* in, Real* out, unsigned n, cudaStream_t s);
 
+// Total variation (tv.cu): per-block partial sums of the un-scaled terms into
+// partials[blocks]; grad_accum (or null) += lam * dx*dy*dz * dR/dalpha.
+int tv_blocks(unsigned N);
+template <typename Real>
+cudaError_t launch_tv(const Real* alpha, int nx, int ny, int nz, int bc, double dx, double dy, double dz,
+                      double lam, double eps, Real* grad_accum, double* partials, int blocks, cudaStream_t s);
+
 // ------------------------------------------------- tiled FP32 solver (cg_tiled.cu)
 namespace tiled {
 
@@ -178,6 +186,27 @@ struct AdjTiled {
 };
 
 }  // namespace tiled
+
+// -------------------------------------------------- neural field (field.cu)
+struct FieldDims {
+    int nx, ny, nz;
+    unsigned M, Mp;          // points (cells) and rows padded to a multiple of 128
+    int F, W, depth;         // bands per axis, hidden width, hidden layers
+    double freq_lo, freq_hi, alpha_min, alpha_max;
+    int splits;              // split-K factor of the weight-gradient GEMMs
+    int colsum_blocks;       // row blocks of the bias-gradient reductions
+};
+size_t field_param_count(int F, int W, int depth);
+size_t field_workspace_bytes(const FieldDims& d, bool backward);
+cudaError_t field_eval(const FieldDims& d, const float* theta, const float* band_w, float* alpha, char* ws,
+                       cudaStream_t s);
+cudaError_t field_backward(const FieldDims& d, const float* theta, const float* band_w, const float* g_alpha,
+                           float* g_theta, char* ws, cudaStream_t s);
+int field_error(const FieldDims& d, char* ws, cudaStream_t s, bool backward);
+// tcgen05 BF16 GEMM (umma_gemm.cu): D = A B^T, epi 0 bias+relu->bf16, 1 mask->bf16, 2 fp32 split partials.
+cudaError_t umma_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
+                      int epi, const float* bias, const __nv_bfloat16* mask, __nv_bfloat16* out_bf16,
+                      float* out_f32, int ldo, int splits, int* err, cudaStream_t s);
 
 int tiled_grid_blocks(int device);
 // Shared memory (bytes) the tiled kernels request dynamically.

@@ -1,0 +1,291 @@
+// BF16 GEMM on the 5th-generation tensor cores (tcgen05), for the neural
+// field's dense layers (Sec. 4.1, App. D.1).
+//
+//   D[m, n] = sum_k A[m, k] * B[n, k]        A: [M x K], B: [N x K], both BF16, K contiguous
+//
+// One CTA computes one 128 x 128 tile of D (or one split-K slice of it).
+// A and B tiles of 64 K-elements arrive by TMA (128-byte swizzle, the canonical
+// K-major layout the tensor core reads) in a four-stage shared-memory ring; a
+// single thread issues tcgen05.mma (M = 128, N = 128, K = 16 per instruction)
+// with the FP32 accumulator in tensor memory and releases each stage with
+// tcgen05.commit onto that stage's "empty" mbarrier.  After the last k-block the
+// four warps read their 32 accumulator lanes with tcgen05.ld and apply the
+// epilogue.  Every wait is bounded: on timeout the kernel records an error,
+// waits (bounded) for its own copies and MMAs, frees its tensor memory and
+// returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace nefty {
+namespace umma {
+
+constexpr int BM = 128, BN = 128, BK = 64;      // tile and k-block (64 BF16 = one 128-byte swizzle row)
+constexpr int STAGES = 4;
+constexpr int THREADS = 128;                     // 4 warps = the 128 accumulator lanes
+constexpr int TILE_BYTES = BM * BK * 2;          // 16 KB per operand per stage
+constexpr int STAGE_BYTES = 2 * TILE_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;   // + 1024-byte alignment slack
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t s_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long g_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void bar_init(uint32_t b, unsigned n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_expect_tx(uint32_t b, unsigned bytes) {
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(b), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool bar_wait(uint32_t b, unsigned parity) {
+    unsigned long long t0 = 0;
+    for (unsigned i = 0;; ++i) {
+        uint32_t done;
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(done) : "r"(b), "r"(parity) : "memory");
+        if (done) return true;
+        if ((i & 63u) == 63u) {
+            const unsigned long long t = g_ns();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > kWaitNs) return false;
+        }
+    }
+}
+__device__ __forceinline__ void tma2(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t b) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(b) : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile in the 128-byte swizzle
+// layout: 8-row atoms of 1024 bytes stacked along M/N (stride 1024), start
+// address in 16-byte units, descriptor version 1, swizzle mode 2 (128 B).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor: FP32 accumulator, BF16 A and B, both K-major,
+// N = BN, M = BM.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+enum Epi : int {
+    kEpiBiasReluBf16 = 0,   // out_bf16 = bf16(relu(acc + bias[n]))
+    kEpiMaskBf16 = 1,       // out_bf16 = bf16(acc * (mask_bf16[m, n] > 0))
+    kEpiF32 = 2,            // out_f32[split] = acc (split-K partial)
+};
+
+struct Args {
+    int M, N, K;            // K is a multiple of BK; M, N may be ragged (masked)
+    int k_blocks_per_split;
+    int epi;
+    const float* bias;      // [N]
+    const __nv_bfloat16* mask;   // [M, ldo]
+    __nv_bfloat16* out_bf16;     // [M, ldo]
+    float* out_f32;              // [splits][M, ldo]
+    int ldo;
+    int* err;
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, Args a) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long full[STAGES], empty[STAGES], done;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fail;
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int kb0 = blockIdx.z * a.k_blocks_per_split;
+    const int kb1 = min(a.K / BK, kb0 + a.k_blocks_per_split);
+    const int nk = kb1 - kb0;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            bar_init(s_u32(&full[s]), 1);
+            bar_init(s_u32(&empty[s]), 1);
+        }
+        bar_init(s_u32(&done), 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_u32(&s_tmem)),
+                     "r"(BN) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+
+    // ---- producer + MMA issue (one thread)
+    if (threadIdx.x == 0 && nk > 0) {
+        auto sa = [&](int s) { return s_u32(smem + s * STAGE_BYTES); };
+        auto sb = [&](int s) { return s_u32(smem + s * STAGE_BYTES + TILE_BYTES); };
+        auto load = [&](int i) {   // k-block kb0 + i into stage i % STAGES
+            const int s = i % STAGES;
+            bar_expect_tx(s_u32(&full[s]), STAGE_BYTES);
+            tma2(sa(s), &mapA, (kb0 + i) * BK, m0, s_u32(&full[s]));
+            tma2(sb(s), &mapB, (kb0 + i) * BK, n0, s_u32(&full[s]));
+        };
+        int issued = 0;
+        for (; issued < nk && issued < STAGES; ++issued) load(issued);
+        bool ok = true;
+        for (int i = 0; i < nk && ok; ++i) {
+            const int s = i % STAGES;
+            ok = bar_wait(s_u32(&full[s]), (unsigned)(i / STAGES) & 1u);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < BK / 16; ++j)   // K = 16 per instruction: 32 bytes along the swizzled row
+                mma(tmem, smem_desc(sa(s) + 32 * j), smem_desc(sb(s) + 32 * j), (i > 0 || j > 0) ? 1u : 0u);
+            mma_commit(s_u32(&empty[s]));
+            // refill the stage used one k-block ago once its MMAs are done
+            if (i > 0 && issued < nk) {
+                const int sp = (i - 1) % STAGES;
+                ok = bar_wait(s_u32(&empty[sp]), (unsigned)((i - 1) / STAGES) & 1u);
+                if (ok) load(issued++);
+            }
+        }
+        if (ok) {
+            mma_commit(s_u32(&done));
+        } else {
+            s_fail = 1;
+            atomicExch(a.err, 1);
+        }
+    }
+    __syncthreads();
+    bool ok = s_fail == 0;
+    if (ok && nk > 0) ok = bar_wait(s_u32(&done), 0);
+    if (!ok && threadIdx.x == 0) atomicExch(a.err, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    // ---- epilogue: warp w owns accumulator lanes (rows) 32w .. 32w+31
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            uint32_t v[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            if (nk > 0) {
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+                      "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+                      "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            } else {
+#pragma unroll
+                for (int t = 0; t < 32; ++t) v[t] = 0u;
+            }
+            if (row < a.M) {
+#pragma unroll
+                for (int t = 0; t < 32; ++t) {
+                    const int col = n0 + c0 + t;
+                    if (col >= a.N) continue;
+                    const float acc = __uint_as_float(v[t]);
+                    const size_t o = (size_t)row * a.ldo + col;
+                    if (a.epi == kEpiBiasReluBf16) {
+                        a.out_bf16[o] = __float2bfloat16_rn(fmaxf(acc + a.bias[col], 0.f));
+                    } else if (a.epi == kEpiMaskBf16) {
+                        a.out_bf16[o] = __float2bfloat16_rn(__bfloat162float(a.mask[o]) > 0.f ? acc : 0.f);
+                    } else {
+                        a.out_f32[(size_t)blockIdx.z * a.M * a.ldo + o] = acc;
+                    }
+                }
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        // wait (bounded) for whatever this CTA still has in flight
+        for (int s = 0; s < STAGES; ++s) bar_wait(s_u32(&empty[s]), 0);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+    }
+}
+
+}  // namespace umma
+
+// ------------------------------------------------------------------- host
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 2D BF16 map over [rows x cols] (cols contiguous, pitch ld elements), box
+// 64 x 128 with the 128-byte swizzle.
+bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld) {
+    auto enc = encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)umma::BK, (cuuint32_t)umma::BM};
+    const cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
+
+// D[M x N] = A[M x K] B[N x K]^T with the chosen epilogue.  K % 64 == 0,
+// lda/ldb in elements (multiples of 8).  splits > 1 only with kEpiF32.
+cudaError_t umma_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
+                      int epi, const float* bias, const __nv_bfloat16* mask, __nv_bfloat16* out_bf16,
+                      float* out_f32, int ldo, int splits, int* err, cudaStream_t s) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(umma::gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             umma::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (K % umma::BK != 0 || lda % 8 != 0 || ldb % 8 != 0 || splits < 1) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, M, K, lda) || !make_map(&mb, B, N, K, ldb)) return cudaErrorInvalidValue;
+    umma::Args a;
+    a.M = M; a.N = N; a.K = K;
+    const int kb = K / umma::BK;
+    a.k_blocks_per_split = (kb + splits - 1) / splits;
+    a.epi = epi;
+    a.bias = bias; a.mask = mask; a.out_bf16 = out_bf16; a.out_f32 = out_f32; a.ldo = ldo;
+    a.err = err;
+    dim3 grid((M + umma::BM - 1) / umma::BM, (N + umma::BN - 1) / umma::BN, splits);
+    umma::gemm_kernel<<<grid, umma::THREADS, umma::SMEM_BYTES, s>>>(ma, mb, a);
+    return cudaGetLastError();
+}
+
+}  // namespace nefty

@@ -195,6 +195,19 @@ class Solver:
                 "status": status}
 
 
+    def tv(self, prob: Problem, alpha, lam: float, eps: float, grad_accum=None, stream=None):
+        """lam * R(alpha) of Eq. tv_discrete; lam * dR/dalpha is added to grad_accum if given."""
+        dt = prob.torch_dtype
+        a_obj, a_ptr = _as_array(alpha, dt, prob.n_cells, "alpha", allow_none=False)
+        g_obj, g_ptr = _as_array(grad_accum, dt, prob.n_cells, "grad_accum")
+        out = ctypes.c_double(0.0)
+        cp = prob.to_c()
+        N.check(self._lib.nefty_tv(self._h, ctypes.byref(cp), a_ptr, float(lam), float(eps), ctypes.byref(out),
+                                   g_ptr, _stream_for(alpha, stream)), self._h)
+        del a_obj, g_obj
+        return out.value
+
+
 class HeatLoss(torch.autograd.Function):
     """J(alpha) = loss_scale * sum_n ||Pi T^n(alpha) - obs^n||^2 with the
     gradient from the discrete adjoint (Eq. adjoint_eq, Eq. grad_assembly).

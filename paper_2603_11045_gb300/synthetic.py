@@ -22,7 +22,7 @@ import numpy as np
 __all__ = [
     "Workload", "box_inclusion_case", "random_inclusions", "gaussian_pulse",
     "inclusion_case", "neural_field_case", "layered_delamination_case",
-    "paper_grid_case", "serving_jobs", "rng",
+    "paper_grid_case", "serving_jobs", "rng", "xavier_theta",
 ]
 
 
@@ -205,3 +205,20 @@ def serving_jobs(n_jobs=64, rate=4.0, seed=3000, steps=(200, 1000), sizes=GRID_S
                      "kind": kind, "iters": 10 if kind == "inversion" else 0,
                      "seed": int(seed * 100 + j)})
     return jobs
+
+
+def xavier_theta(F, W, depth, seed):
+    """Seeded Xavier-uniform weights and zero biases for the neural field
+    (App. D.1), packed as W_0 [W x 6F], b_0, W_l [W x W], b_l (l = 1..depth-1),
+    w_out [W], b_out [1]; weights row-major [out][in]."""
+    import math
+    g = rng(seed)
+    D = 6 * F
+    parts = []
+    for l in range(depth):
+        n_in = D if l == 0 else W
+        lim = math.sqrt(6.0 / (n_in + W))
+        parts += [g.uniform(-lim, lim, size=W * n_in), np.zeros(W)]
+    lim = math.sqrt(6.0 / (W + 1))
+    parts += [g.uniform(-lim, lim, size=W), np.zeros(1)]
+    return np.concatenate(parts)

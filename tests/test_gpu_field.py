@@ -1,0 +1,151 @@
+"""Tensor-core field path vs the FP64 reference (oracle/field.py).
+
+Tolerances: against the reference evaluated the way the tensor cores do it
+(BF16 weights and activations, exact products, FP32 vs FP64 sums) alpha agrees
+to rel-L2 <= 1e-4; against the exact FP64 model the BF16 path's error is
+stated and held to rel-L2 <= 2e-2; parameter gradients agree with FP64
+autograd of the reference to rel-L2 <= 2e-2 and cosine >= 0.999.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2603_11045_gb300 import synthetic as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def solver():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_11045_gb300.solver import Solver
+    s = Solver(0)
+    yield s
+    s.close()
+
+
+def rel(a, b):
+    a = torch.as_tensor(a).double().cpu().ravel()
+    b = torch.as_tensor(b).double().cpu().ravel()
+    return float((a - b).norm() / b.norm())
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (300, 256, 384), (129, 384, 256), (1000, 128, 128),
+                                   (64, 128, 4096)])
+def test_tensor_core_gemm_matches_torch(solver, M, N, K):
+    import ctypes
+    g = torch.Generator(device="cuda").manual_seed(M + N + K)
+    A = torch.randn(M, K, generator=g, device="cuda").to(torch.bfloat16)
+    B = torch.randn(N, K, generator=g, device="cuda").to(torch.bfloat16)
+    C = torch.empty(M, N, device="cuda")
+    st = solver._lib.nefty_gemm_bf16(solver._h, ctypes.c_void_p(A.data_ptr()), K, ctypes.c_void_p(B.data_ptr()), K,
+                                     M, N, K, ctypes.c_void_p(C.data_ptr()),
+                                     ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0, solver._lib.nefty_last_error(solver._h)
+    ref = A.double() @ B.double().T
+    assert rel(C, ref) <= 1e-5
+
+
+CASES = [dict(nx=12, ny=10, nz=6, n_freq=32, width=128, depth=2),
+         dict(nx=20, ny=16, nz=8, n_freq=64, width=256, depth=4)]
+
+
+def _spec(c):
+    from paper_2603_11045_gb300.field import FieldSpec
+    return FieldSpec(**c)
+
+
+@pytest.mark.parametrize("c", CASES)
+def test_field_eval_matches_reference(solver, c):
+    import oracle.field as OF
+    from paper_2603_11045_gb300.field import field_alpha, annealing_weights
+    spec = _spec(c)
+    th = S.xavier_theta(spec.n_freq, spec.width, spec.depth, 11)
+    th[-1] = 0.3
+    bw = annealing_weights(spec.n_freq, spec.n_freq * 0.6)
+    a = field_alpha(solver, spec, torch.tensor(th, dtype=torch.float32, device="cuda"),
+                    torch.tensor(bw, dtype=torch.float32))
+    th32 = torch.tensor(th, dtype=torch.float32).double()
+    bw32 = torch.tensor(bw, dtype=torch.float32).double()
+    args = (spec.nx, spec.ny, spec.nz, spec.n_freq, spec.width, spec.depth, spec.freq_lo, spec.freq_hi,
+            spec.alpha_min, spec.alpha_max)
+    emu = OF.field(th32, *args, band_weights=bw32, bf16=True)
+    exact = OF.field(th32, *args, band_weights=bw32, bf16=False)
+    assert rel(a, emu) <= 1e-4
+    assert float((a.double().cpu() - emu).abs().max()) <= 2e-3
+    assert rel(a, exact) <= 2e-2
+
+
+@pytest.mark.parametrize("c", CASES)
+def test_field_backward_matches_reference(solver, c):
+    import oracle.field as OF
+    from paper_2603_11045_gb300.field import field_alpha
+    spec = _spec(c)
+    th = S.xavier_theta(spec.n_freq, spec.width, spec.depth, 12)
+    theta = torch.tensor(th, dtype=torch.float32, device="cuda", requires_grad=True)
+    g_a = torch.tensor(S.rng(13).standard_normal((spec.nz, spec.ny, spec.nx)), dtype=torch.float32, device="cuda")
+    (field_alpha(solver, spec, theta) * g_a).sum().backward()
+    ref_th = torch.tensor(th, dtype=torch.float32).double().requires_grad_(True)
+    args = (spec.nx, spec.ny, spec.nz, spec.n_freq, spec.width, spec.depth, spec.freq_lo, spec.freq_hi,
+            spec.alpha_min, spec.alpha_max)
+    (OF.field(ref_th, *args, bf16=True) * g_a.double().cpu()).sum().backward()
+    g, r = theta.grad.double().cpu(), ref_th.grad
+    assert rel(g, r) <= 2e-2
+    assert float(g @ r / (g.norm() * r.norm())) >= 0.999
+
+
+def test_inversion_chain_finite_differences(solver, orc):
+    """Pattern (3) on a small grid: theta -> field -> heat solve -> surface MSE
+    + TV; the autograd gradient of the GPU chain vs central differences of the
+    FP64 reference chain (oracle field + oracle solver) on 16 random weights."""
+    import oracle.field as OF
+    from paper_2603_11045_gb300.field import FieldSpec, field_alpha
+    from paper_2603_11045_gb300.solver import Problem, HeatLoss
+    spec = FieldSpec(16, 16, 6, n_freq=32, width=128, depth=2, freq_lo=math.pi, freq_hi=8 * math.pi,
+                     alpha_min=0.05, alpha_max=2.0)
+    w = S.inclusion_case(nx=16, ny=16, nz=6, nt=20, seed=2003)
+    prob = Problem.from_workload(w, prec="fp32", rtol=1e-10)
+    op = orc.from_workload(w)
+    q = w.q_face.astype(np.float32).astype(np.float64)
+    obs = orc.forward(op, w.alpha, q_face=q, q_steps=3)["frames"].astype(np.float32)
+    lam, eps = 1e-3, 1e-3
+    th = S.xavier_theta(spec.n_freq, spec.width, spec.depth, 21)
+    th[-1] = 0.5
+    theta = torch.tensor(th, dtype=torch.float32, device="cuda", requires_grad=True)
+    alpha = field_alpha(solver, spec, theta)
+    J = HeatLoss.apply(alpha, solver, prob, torch.tensor(obs, device="cuda"),
+                       torch.tensor(q, dtype=torch.float32, device="cuda"), 3, None)
+    J.backward(retain_graph=True)
+    g_heat = theta.grad.clone()
+    theta.grad = None
+    g_tv = torch.zeros_like(alpha)
+    solver.tv(prob, alpha.detach().contiguous(), lam, eps, grad_accum=g_tv)
+    alpha.backward(g_tv)
+    grad = (g_heat + theta.grad).double().cpu().numpy()
+
+    th32 = torch.tensor(th, dtype=torch.float32).double().numpy()
+    args = (spec.nx, spec.ny, spec.nz, spec.n_freq, spec.width, spec.depth, spec.freq_lo, spec.freq_hi,
+            spec.alpha_min, spec.alpha_max)
+
+    def J_ref(t):
+        a = OF.field(torch.tensor(t), *args).numpy()
+        return (orc.forward(op, a, q_face=q, q_steps=3, obs=obs.astype(np.float64))["loss"]
+                + orc.tv(op, a, lam, eps, want_grad=False)[0])
+
+    # weights of the first layer's most active rows and of the output layer carry the signal
+    g = S.rng(22)
+    idx = np.concatenate([g.integers(0, spec.width * 6 * spec.n_freq, 10),
+                          len(th) - 1 - g.integers(1, spec.width + 1, 6)])
+    fd = []
+    for i in idx:
+        e = 1e-4 * max(1.0, abs(th32[i]))
+        tp = th32.copy(); tp[i] += e
+        tm = th32.copy(); tm[i] -= e
+        fd.append((J_ref(tp) - J_ref(tm)) / (2 * e))
+    fd = np.array(fd)
+    got = grad[idx]
+    assert np.linalg.norm(got - fd) <= 5e-2 * np.linalg.norm(fd)
+    assert float(got @ fd / (np.linalg.norm(got) * np.linalg.norm(fd))) >= 0.99

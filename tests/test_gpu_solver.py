@@ -273,3 +273,26 @@ def test_error_paths(solver):
     out = solver.forward(prob.with_(max_iter=1, rtol=1e-30), torch.ones(4, 8, 8, device="cuda:0"),
                          q_face=q, q_steps=1, allow_notconv=True)
     assert out["status"] == NEFTY_ENOTCONV and out["stats"]["not_converged"] >= 1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("shape", [(7, 5, 4), (33, 17, 6), (1, 4, 3), (2, 2, 2)])
+def test_tv_matches_oracle(solver, orc, prec, bc, shape):
+    """Eq. tv_discrete value and gradient (accumulated into an existing array)
+    vs the oracle, on random fields; odd, degenerate and wrapping shapes."""
+    from paper_2603_11045_gb300.solver import Problem
+    nx, ny, nz = shape
+    g = S.rng(7 + bc + nx)
+    alpha = _cast(g.uniform(0.05, 2.0, size=(nz, ny, nx)), prec)
+    prob = Problem(nx, ny, nz, dx=0.8, dy=1.3, dz=0.6, bc=bc, prec=prec)
+    op = orc.problem(nx, ny, nz, dx=0.8, dy=1.3, dz=0.6, bc=bc)
+    lam, eps = 1e-2, 1e-3
+    ref_v, ref_g = orc.tv(op, alpha, lam, eps)
+    base = g.standard_normal((nz, ny, nx))
+    acc = dev(base, prec)
+    v = solver.tv(prob, dev(alpha, prec), lam, eps, grad_accum=acc)
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    assert v == pytest.approx(ref_v, rel=tol)
+    got = acc.double().cpu().numpy() - _cast(base, prec)
+    assert np.abs(got - ref_g).max() <= (1e-12 if prec == "fp64" else 1e-5) * np.abs(ref_g).max()
