@@ -1,8 +1,10 @@
 #!/usr/bin/env python
-"""Benchmark of the NeFTY hot path on GB300: one step = the forward sweep plus
-the reverse adjoint sweep with the diffusivity gradient, on a synthetic
-256x256x48 grid over 1000 implicit-Euler steps (dt = 0.25, FP32 vectors and
-stencil, FP64 reductions).
+"""Benchmark of the NeFTY hot path on GB300: one step = one inversion step on a
+synthetic 256x256x48 grid over 1000 implicit-Euler steps (dt = 0.25): the
+neural field theta -> alpha (Fourier features, 4 x 256 ReLU MLP on the tensor
+cores), the forward sweep and the reverse adjoint sweep with dJ/dalpha (FP32
+vectors and stencil, compensated reductions), the TV regulariser's gradient
+(lambda 1e-4), and the field's backward pass to dJ/dtheta.
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own replica
 of the workload (no data-path collective; weak scaling) and rank 0 reports the
@@ -64,19 +66,39 @@ def parse():
     return ap.parse_args()
 
 
+TV_LAMBDA, TV_EPS = 1e-4, 1e-6
+FIELD_SEED = 2001
+
+
 def workload(args):
     from paper_2603_11045_gb300 import synthetic as S
     w = S.neural_field_case(nx=args.nx, ny=args.ny, nz=args.nz, nt=args.nt, dt=0.25)
-    # candidate field for the inversion step: the smooth background without
-    # the inclusions (the target frames come from the field with inclusions)
+    # candidate alpha for the CPU baseline (the GPU step takes alpha from the
+    # neural field): the smooth background without the inclusions
     g = S.rng(w.extra["seed"])
     cand = g.uniform(0.8, 1.2, size=(w.nz, w.ny, w.nx))
     return w, cand
 
 
+def field_spec(w):
+    from paper_2603_11045_gb300.field import FieldSpec
+    return FieldSpec(w.nx, w.ny, w.nz)   # 64 bands pi..128 pi, 4 x 256, alpha in [0.01, 2]
+
+
+def mlp_flops(spec):
+    """Multiply-adds x 2 of the dense layers: forward, and backward (input
+    gradients of layers 1..depth-1 plus weight gradients of all layers)."""
+    D, W, L, M = 6 * spec.n_freq, spec.width, spec.depth, spec.nx * spec.ny * spec.nz
+    fwd = 2.0 * M * (D * W + (L - 1) * W * W)
+    bwd = 2.0 * M * ((L - 1) * W * W) + fwd
+    return fwd, bwd
+
+
 def config_dict(args, w):
     return {"workload": f"inversion step, {w.nx}x{w.ny}x{w.nz} cells, {w.nt} implicit-Euler steps, dt={w.dt}",
             "grid": [w.nx, w.ny, w.nz], "nt": w.nt, "dt": w.dt, "prec": args.prec,
+            "field": "64 log-spaced bands (pi..128 pi) per axis -> 4 x 256 ReLU (BF16 tensor cores) -> [0.01, 2]",
+            "tv": {"lambda": TV_LAMBDA, "eps": TV_EPS},
             "solver": "Jacobi-PCG, rtol 1e-9 (FP32) / 1e-13 (FP64)",
             "bc": "zero-flux walls", "forcing": "Gaussian surface pulse, sigma 20 cells, 3 steps",
             "l2": "flushed between timed steps (256 MiB write)"}
@@ -183,6 +205,17 @@ def peaks():
         return None
 
 
+def field_launches(spec):
+    """Kernels of one nefty_field_eval + nefty_field_backward + nefty_tv call."""
+    L = spec.depth
+    ev = 3 + 1 + L + L + 1          # axis tables, features, BF16 weights, layer GEMMs, head
+    # backward: the forward layers again, head backward, 2 x 2 output-layer sums,
+    # L weight transposes, per layer (2 bias sums, 2 transposes, weight-gradient
+    # GEMM, split-K reduce) and L - 1 input-gradient GEMMs
+    bw = (ev - 1) + 1 + 4 + L + 6 * L + (L - 1)
+    return ev + bw + 1              # + TV
+
+
 def run_native(args):
     import torch
     import torch.distributed as dist
@@ -195,19 +228,50 @@ def run_native(args):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
+    import ctypes
+    from paper_2603_11045_gb300 import synthetic as S
+    from paper_2603_11045_gb300 import _native as NV
     w, cand = workload(args)
     prob = Problem.from_workload(w, prec=args.prec, ckpt_every=args.ckpt_every)
     dt = prob.torch_dtype
     solver = Solver(local)
+    spec = field_spec(w)
     q = torch.tensor(w.q_face, dtype=dt, device=dev)
-    # target frames from the field with inclusions (setup, not timed)
+    # target frames from the ground-truth field with inclusions (setup, not timed)
     obs = solver.forward(prob, torch.tensor(w.alpha, dtype=dt, device=dev), q_face=q, q_steps=w.q_steps)["frames"]
-    alpha = torch.tensor(cand, dtype=dt, device=dev)
+    theta = torch.tensor(S.xavier_theta(spec.n_freq, spec.width, spec.depth, FIELD_SEED), dtype=torch.float32,
+                         device=dev)
+    alpha = torch.empty(w.nz, w.ny, w.nx, dtype=torch.float32, device=dev)
+    g_theta = torch.empty_like(theta)
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    desc = spec.to_c()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    field_ms = []
+
+    def run_step(th, obs_, q_, g_out, timed=False):
+        """theta -> alpha -> J, dJ/dalpha (+ TV) -> dJ/dtheta, all through the C ABI."""
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if timed else None
+        if timed: e[0].record(stream)
+        NV.check(solver._lib.nefty_field_eval(solver._h, ctypes.byref(desc), ctypes.c_void_p(th.data_ptr()),
+                                              None, ctypes.c_void_p(alpha.data_ptr()), sp), solver._h)
+        if timed: e[1].record(stream)
+        a = alpha if dt == torch.float32 else alpha.double()
+        out = solver.adjoint_grad(prob, a, obs_, q_face=q_, q_steps=w.q_steps)
+        g = out["grad_alpha"]
+        solver.tv(prob, a, TV_LAMBDA, TV_EPS, grad_accum=g)
+        g32 = g if g.dtype == torch.float32 else g.float()
+        if timed: e[2].record(stream)
+        NV.check(solver._lib.nefty_field_backward(solver._h, ctypes.byref(desc), ctypes.c_void_p(th.data_ptr()), None,
+                                                  ctypes.c_void_p(g32.data_ptr()), ctypes.c_void_p(g_out.data_ptr()),
+                                                  sp), solver._h)
+        if timed:
+            e[3].record(stream)
+            field_ms.append((e, out["stats"]))
+        return out
 
     def step():
-        return solver.adjoint_grad(prob, alpha, obs, q_face=q, q_steps=w.q_steps)
+        return run_step(theta, obs, q, g_theta, timed=True)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -229,6 +293,8 @@ def run_native(args):
         dist.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    f_fwd = [e[0].elapsed_time(e[1]) for e, _ in field_ms[-args.steps:]]
+    f_bwd = [e[2].elapsed_time(e[3]) for e, _ in field_ms[-args.steps:]]
     total_ms = sum(step_ms)
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     if world > 1:
@@ -257,20 +323,33 @@ def run_native(args):
                 "cg_ms_per_step": cg_ms, "alg_bytes_per_step": alg_bytes,
                 "mean_cg_iters_per_solve": iters / max(1, steps_solved)}
 
-    # end to end through the C ABI with host buffers (pinned), copies inside
+    fwd_fl, bwd_fl = mlp_flops(spec)
+    pk_tf = (pk["bf16_tflops_sustained"] if pk and "bf16_tflops_sustained" in pk else 1700.0)
+    f_fwd_ms, f_bwd_ms = float(np.mean(f_fwd)), float(np.mean(f_bwd))
+    mlp_tf = (fwd_fl + bwd_fl) / ((f_fwd_ms + f_bwd_ms) / 1000.0) / 1e12
+    roofline_mlp = {"bound": "tensor", "achieved": mlp_tf, "peak": pk_tf, "unit": "TFLOP/s", "frac": mlp_tf / pk_tf,
+                    "traffic": None, "kernel": "tcgen05 BF16 GEMMs of the field (eval + backward calls)",
+                    "peak_source": "measured sustained bf16 (MEASURED_PEAKS.json)" if pk else "fallback",
+                    "field_eval_ms": f_fwd_ms, "field_backward_ms": f_bwd_ms,
+                    "flops_per_step": fwd_fl + bwd_fl}
+
+    # end to end through the C ABI with host buffers (pinned): theta, targets
+    # and flux go in, dJ/dtheta and the loss come back, copies inside
     e2e = None
     if rank == 0 or world > 1:
-        a_h = alpha.cpu().pin_memory()
+        th_h = theta.cpu().pin_memory()
         o_h = obs.cpu().pin_memory()
         q_h = q.cpu().pin_memory()
-        solver.adjoint_grad(prob, a_h, o_h, q_face=q_h, q_steps=w.q_steps)
+        g_h = torch.empty(theta.shape, dtype=torch.float32).pin_memory()
+        run_step(th_h, o_h, q_h, g_h)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            out_h = solver.adjoint_grad(prob, a_h, o_h, q_face=q_h, q_steps=w.q_steps)
+            run_step(th_h, o_h, q_h, g_h)
+        torch.cuda.synchronize(dev)
         e2e_s = (time.perf_counter() - t0) / args.steps
-        h2d = a_h.numel() * a_h.element_size() + o_h.numel() * o_h.element_size() + q_h.numel() * q_h.element_size()
-        d2h = out_h["grad_alpha"].numel() * out_h["grad_alpha"].element_size() + 8
+        h2d = th_h.numel() * 4 + o_h.numel() * o_h.element_size() + q_h.numel() * q_h.element_size()
+        d2h = g_h.numel() * 4 + 8
         e2e = {"value": w.n_cells * w.nt * world / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
@@ -286,7 +365,8 @@ def run_native(args):
                 "warmup": max(3, args.warmup), "ms_per_step": max_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if R == "fp32" else "f64",
                 "data": "synthetic", "config": config_dict(args, w), "parallelism": f"replicas x{world}",
-                "gpu_launches": launches * args.steps, "e2e": e2e, "roofline": roofline,
+                "gpu_launches": launches * args.steps + field_launches(spec) * args.steps, "e2e": e2e,
+                "roofline": roofline, "roofline_field": roofline_mlp,
                 "cpu_baseline": cpu, "clocks": clk,
                 "solver_stats": {k: stats[-1][k] for k in ("fwd_iters", "adj_iters", "recompute_iters",
                                                            "max_step_iters", "max_rel_residual",

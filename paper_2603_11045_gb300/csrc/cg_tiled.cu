@@ -11,7 +11,7 @@
 // cell from its own values; the only neighbour data a pass needs is u_{i+1}
 // itself, staged plane by plane in shared memory.
 //
-// Work layout: the grid is cut into 32 x 16 columns (one warp per row of 32
+// Work layout: the grid is cut into 32 x 32 columns (one warp per row of 32
 // cells along x) and the (tile, plane) pairs are split evenly over the CTAs;
 // each CTA marches up z through its planes, keeping the field of planes k-1 and
 // k+1 for its own column in registers and plane k with a one-cell halo ring in a
@@ -325,9 +325,9 @@ __device__ __forceinline__ void for_segments(const Geo& g, SegFn seg) {
 // zero), so this path serves grids with zero-flux lateral walls and nx % 4 == 0
 // (row pitch a multiple of 16 bytes).
 constexpr int NS = 6;                         // stages
-constexpr int HB = TX + 8, HR = TY + 2;       // halo box: x0-4 .. x0+35, y0-1 .. y0+16
-constexpr int SZ_H = HB * HR * 4;             // 2880
-constexpr int SZ_O = TX * TY * 4;             // 2048
+constexpr int HB = TX + 8, HR = TY + 2;       // halo box: x0-4 .. x0+35, y0-1 .. y0+TY
+constexpr int SZ_H = HB * HR * 4;             // 5440
+constexpr int SZ_O = TX * TY * 4;             // 4096
 constexpr int al128(int b) { return (b + 127) & ~127; }
 constexpr int OFF_U = 0;
 constexpr int OFF_W = OFF_U + al128(SZ_H);
@@ -370,15 +370,22 @@ __device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* map, 
         ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar) : "memory");
 }
 
+// Ring bookkeeping without division: copies are issued and waited in the same
+// order, so a stage index that advances by one (mod NS) and one parity bit per
+// stage describe both sides.
 struct TmaRing {
     unsigned char* base;   // NS stages, 128-byte aligned
     uint32_t bar0;         // shared address of NS mbarriers (8 bytes each)
-    unsigned issued;       // tickets issued (thread 0's count; equal to waited at segment ends)
-    unsigned waited;       // tickets waited (uniform)
+    unsigned issue_s;      // stage of the next copy (thread 0)
+    unsigned wait_s;       // stage of the next wait (uniform)
+    unsigned wait_ph;      // bit s: parity of the next wait on stage s (uniform)
+    unsigned in_flight;    // copies issued and not yet waited (thread 0)
 };
 
+__device__ __forceinline__ unsigned ring_next(unsigned s) { return s + 1 == NS ? 0u : s + 1; }
+
 __device__ __forceinline__ void issue_plane(TmaRing& R, const TmaMaps* M, int cur, int x0, int y0, int k) {
-    const unsigned st = R.issued % NS;
+    const unsigned st = R.issue_s;
     const uint32_t dst = smem_u32(R.base + st * STAGE_BYTES);
     const uint32_t bar = R.bar0 + 8u * st;
     mbar_expect_tx(bar, TX_BYTES);
@@ -388,14 +395,26 @@ __device__ __forceinline__ void issue_plane(TmaRing& R, const TmaMaps* M, int cu
     tma_load3(dst + OFF_A, &M->alpha, x0 - 4, y0 - 1, k, bar);
     tma_load3(dst + OFF_P, &M->p, x0, y0, k, bar);
     tma_load3(dst + OFF_D, &M->delta, x0, y0, k, bar);
-    R.issued += 1;
+    R.issue_s = ring_next(st);
+    R.in_flight += 1;
 }
 
-// After a timed-out wait: wait (again bounded) for every copy this CTA has
-// issued, so none is still landing in shared memory when the kernel exits.
-__device__ void drain(const TmaRing& R) {
-    for (unsigned t = R.issued > NS ? R.issued - NS : 0; t < R.issued; ++t)
-        mbar_wait(R.bar0 + 8u * (t % NS), (t / NS) & 1u);
+// Wait for the next stage in order; returns its index, or -1 on timeout.
+__device__ __forceinline__ int wait_next(TmaRing& R) {
+    const unsigned st = R.wait_s;
+    const bool ok = mbar_wait(R.bar0 + 8u * st, (R.wait_ph >> st) & 1u);
+    R.wait_ph ^= 1u << st;
+    R.wait_s = ring_next(st);
+    return ok ? (int)st : -1;
+}
+
+// After a timed-out wait: wait (again bounded) for the copies this CTA still
+// has in flight, so none is landing in shared memory when the kernel exits.
+__device__ void drain(TmaRing& R) {
+    while (R.in_flight > 0) {
+        wait_next(R);
+        R.in_flight -= 1;
+    }
 }
 
 // One single-reduction CG iteration over this CTA's segments, inputs staged by
@@ -407,6 +426,18 @@ __device__ bool iter_pass_tma(const Common& C, TmaRing& R, float (*fr)[BY][BX], 
     float* __restrict__ uo = C.v.u[cur ^ 1];
     float* __restrict__ wo = C.v.ws[cur ^ 1];
     float* __restrict__ so = C.v.ss[cur ^ 1];
+    // per-thread offsets that do not change with the plane
+    const int hb = (ty + 1) * HB + tx + 4;      // own cell in a halo box
+    const int ob = ty * TX + tx;                 // own cell in an own-cell box
+    const int fb = (ty + 1) * BX + tx + 1;       // own cell in the field tile
+    const int rslot = ring_slot();
+    int rhb = 0, rfb = 0;
+    if (rslot >= 0) {
+        int hy, hx;
+        ring_pos(rslot, hy, hx);
+        rhb = hy * HB + hx + 3;
+        rfb = hy * BX + hx;
+    }
     bool ok = true;
     if (threadIdx.x == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
     for_segments(g, [&](int tile, int k0, int k1) {
@@ -416,37 +447,19 @@ __device__ bool iter_pass_tma(const Common& C, TmaRing& R, float (*fr)[BY][BX], 
         const bool valid = x < g.nx && y < g.ny;
         const int kl = k0 > 0 ? k0 - 1 : 0;
         const int kh = k1 < g.nz ? k1 : g.nz - 1;
-        const unsigned t0 = R.waited;                 // ticket of plane kl
-        int next = kl;
-        if (threadIdx.x == 0) {
-            R.issued = t0;
+        int next = kl;   // next plane to copy (thread 0)
+        if (threadIdx.x == 0)
             while (next <= kh && next < kl + NS) issue_plane(R, C.maps, cur, x0, y0, next++);
-        } else {
-            next = min(kh + 1, kl + NS);
-        }
-        const int rslot = ring_slot();
-        auto stage = [&](int k) -> const unsigned char* { return R.base + ((t0 + (unsigned)(k - kl)) % NS) * STAGE_BYTES; };
-        auto wait_plane = [&](int k) -> bool {
-            const unsigned t = t0 + (unsigned)(k - kl);
-            R.waited = t + 1;
-            return mbar_wait(R.bar0 + 8u * (t % NS), (t / NS) & 1u);
-        };
-        // field u_{i+1} = u_i - a (ws_i + b ss_{i-1}) of plane k into fr[k % 3]
-        auto fill = [&](int k) -> float {
-            const unsigned char* st = stage(k);
+        auto stage_ptr = [&](int s) -> const unsigned char* { return R.base + (unsigned)s * STAGE_BYTES; };
+        // u_{i+1} = u_i - a (ws_i + b ss_{i-1}) at the own cell and the ring cell
+        // of one staged plane, into field buffer fbuf; returns the own value
+        auto fill = [&](const unsigned char* st, float* fbuf) -> float {
             const float* U = (const float*)(st + OFF_U);
             const float* W = (const float*)(st + OFF_W);
             const float* Sv = (const float*)(st + OFF_S);
-            float* buf = &fr[k % 3][0][0];
-            int hb = (ty + 1) * HB + tx + 4;
             const float vo = U[hb] - a * (first ? W[hb] : W[hb] + bt * Sv[hb]);
-            buf[(ty + 1) * BX + tx + 1] = vo;
-            if (rslot >= 0) {
-                int hy, hx;
-                ring_pos(rslot, hy, hx);
-                hb = hy * HB + hx + 3;
-                buf[hy * BX + hx] = U[hb] - a * (first ? W[hb] : W[hb] + bt * Sv[hb]);
-            }
+            fbuf[fb] = vo;
+            if (rslot >= 0) fbuf[rfb] = U[rhb] - a * (first ? W[rhb] : W[rhb] + bt * Sv[rhb]);
             return vo;
         };
         // A failed (timed-out) wait aborts the whole CTA together: the decision
@@ -457,59 +470,71 @@ __device__ bool iter_pass_tma(const Common& C, TmaRing& R, float (*fr)[BY][BX], 
             ok = false;
             return true;
         };
+        auto waited = [&]() { if (threadIdx.x == 0) R.in_flight -= 1; };
         float czm = 0.f, fzm = 0.f;
+        int sm1 = -1;
         bool w_ok = true;
-        if (k0 > 0) w_ok = wait_plane(k0 - 1);
-        if (k0 > 0 && w_ok) {
-            const unsigned char* st = stage(k0 - 1);
-            const int hb = (ty + 1) * HB + tx + 4;
-            const float* U = (const float*)(st + OFF_U);
-            const float* W = (const float*)(st + OFF_W);
-            const float* Sv = (const float*)(st + OFF_S);
-            fzm = U[hb] - a * (first ? W[hb] : W[hb] + bt * Sv[hb]);
+        if (k0 > 0) {
+            sm1 = wait_next(R);
+            waited();
+            w_ok = sm1 >= 0;
+            if (w_ok) {
+                const unsigned char* st = stage_ptr(sm1);
+                const float* U = (const float*)(st + OFF_U);
+                const float* W = (const float*)(st + OFF_W);
+                const float* Sv = (const float*)(st + OFF_S);
+                fzm = U[hb] - a * (first ? W[hb] : W[hb] + bt * Sv[hb]);
+            }
         }
-        w_ok = w_ok && wait_plane(k0);
-        if (k0 > 0 && w_ok) {
-            const int hb = (ty + 1) * HB + tx + 4;
-            czm = face(((const float*)(stage(k0) + OFF_A))[hb], ((const float*)(stage(k0 - 1) + OFF_A))[hb], C.kz);
+        int sk = -1;
+        if (w_ok) {
+            sk = wait_next(R);
+            waited();
+            w_ok = sk >= 0;
         }
-        float fc = w_ok ? fill(k0) : 0.f;
+        int fk = 0;   // field buffer of plane k (rotates 0, 1, 2)
+        float fc = 0.f;
+        if (w_ok) {
+            if (k0 > 0) czm = face(((const float*)(stage_ptr(sk) + OFF_A))[hb], ((const float*)(stage_ptr(sm1) + OFF_A))[hb], C.kz);
+            fc = fill(stage_ptr(sk), &fr[fk][0][0]);
+        }
         if (abort_uniform(w_ok)) return;
-        for (int k = k0; k < k1; ++k) {
+        unsigned c = (unsigned)k0 * g.S + (unsigned)y * g.nx + x;
+        for (int k = k0; k < k1; ++k, c += g.S) {
+            const int fk1 = fk == 2 ? 0 : fk + 1;
             float fzp = fc;
+            int sk1 = -1;
             w_ok = true;
             if (k + 1 < g.nz) {
-                w_ok = wait_plane(k + 1);
-                if (w_ok) fzp = fill(k + 1);
+                sk1 = wait_next(R);
+                waited();
+                w_ok = sk1 >= 0;
+                if (w_ok) fzp = fill(stage_ptr(sk1), &fr[fk1][0][0]);
             }
             if (abort_uniform(w_ok)) return;
             // plane k-1 is no longer read by anyone: refill its stage
             if (threadIdx.x == 0)
                 while (next <= kh && next <= k - 1 + NS) issue_plane(R, C.maps, cur, x0, y0, next++);
             if (valid) {
-                const unsigned char* st = stage(k);
-                const float* buf = &fr[k % 3][0][0];
-                const int b = (ty + 1) * BX + tx + 1;
-                const float fxm = buf[b - 1], fxp = buf[b + 1], fym = buf[b - BX], fyp = buf[b + BX];
+                const unsigned char* st = stage_ptr(sk);
+                const float* buf = &fr[fk][0][0];
+                const float fxm = buf[fb - 1], fxp = buf[fb + 1], fym = buf[fb - BX], fyp = buf[fb + BX];
                 const float fzmv = k > 0 ? fzm : fc;
                 const float* As = (const float*)(st + OFF_A);
-                const int ha = (ty + 1) * HB + tx + 4;
-                const float ac = As[ha];
-                const float cxp = face(ac, As[ha + 1], C.kx), cxm = face(ac, As[ha - 1], C.kx);
-                const float cyp = face(ac, As[ha + HB], C.ky), cym = face(ac, As[ha - HB], C.ky);
-                const float czp = k + 1 < g.nz ? face(ac, ((const float*)(stage(k + 1) + OFF_A))[ha], C.kz) : 0.f;
+                const float ac = As[hb];
+                const float cxp = face(ac, As[hb + 1], C.kx), cxm = face(ac, As[hb - 1], C.kx);
+                const float cyp = face(ac, As[hb + HB], C.ky), cym = face(ac, As[hb - HB], C.ky);
+                const float czp = sk1 >= 0 ? face(ac, ((const float*)(stage_ptr(sk1) + OFF_A))[hb], C.kz) : 0.f;
                 const float rob = k + 1 == g.nz ? C.robin : 0.f;
                 const float d = 1.f + cxp + cxm + cyp + cym + czp + czm + rob;
                 const float Au = fc + cxp * (fc - fxp) + cxm * (fc - fxm) + cyp * (fc - fyp) + cym * (fc - fym) +
                                  czp * (fc - fzp) + czm * (fc - fzmv) + rob * fc;
                 const float wn = rcp_approx(d) * Au;
-                const int hb = (ty + 1) * HB + tx + 4;
                 const float uold = ((const float*)(st + OFF_U))[hb];
                 const float wold = ((const float*)(st + OFF_W))[hb];
                 const float sn = first ? wold : wold + bt * ((const float*)(st + OFF_S))[hb];
-                const float pn = first ? uold : uold + bt * ((const float*)(st + OFF_P))[ty * TX + tx];
-                const float dl = ((const float*)(st + OFF_D))[ty * TX + tx] + a * pn;
-                const unsigned c = (unsigned)k * g.S + (unsigned)y * g.nx + x;
+                const float pn = first ? uold : uold + bt * ((const float*)(st + OFF_P))[ob];
+                const float dl = ((const float*)(st + OFF_D))[ob] + a * pn;
                 C.v.p[c] = pn;
                 C.v.delta[c] = dl;
                 uo[c] = fc;
@@ -523,6 +548,8 @@ __device__ bool iter_pass_tma(const Common& C, TmaRing& R, float (*fr)[BY][BX], 
             }
             fzm = fc;
             fc = fzp;
+            sk = sk1;
+            fk = fk1;
         }
         __syncthreads();
     });
@@ -737,15 +764,17 @@ __device__ __forceinline__ Sync make_sync(DevCtl* ctl, double* partials) {
 }
 
 // ------------------------------------------------------------- forward
-__global__ void __launch_bounds__(NT, 2) forward_tiled(FwdTiled a) {
+__global__ void __launch_bounds__(NT, 1) forward_tiled(FwdTiled a) {
     __shared__ float sm[3][BY][BX];
     extern __shared__ unsigned char dyn_smem[];
     __shared__ __align__(8) unsigned long long s_bars[NS];
     TmaRing ring;
     ring.base = (unsigned char*)(((uintptr_t)dyn_smem + 127) & ~(uintptr_t)127);
     ring.bar0 = smem_u32(&s_bars[0]);
-    ring.issued = 0;
-    ring.waited = 0;
+    ring.issue_s = 0;
+    ring.wait_s = 0;
+    ring.wait_ph = 0;
+    ring.in_flight = 0;
     if (a.c.maps) {
         if (threadIdx.x == 0) {
             for (int i = 0; i < NS; ++i) mbar_init(ring.bar0 + 8u * i, 1u);
@@ -800,15 +829,17 @@ __global__ void __launch_bounds__(NT, 2) forward_tiled(FwdTiled a) {
 // ------------------------------------------------------------- adjoint
 // Face-product gradient of step n at the own cells (Eq. grad_assembly):
 // g_c -= sum_f (2 dt / h_f^2) alpha_q^2 / (alpha_c + alpha_q)^2 (mu_c - mu_q)(T_c - T_q).
-__global__ void __launch_bounds__(NT, 2) adjoint_tiled(AdjTiled a) {
+__global__ void __launch_bounds__(NT, 1) adjoint_tiled(AdjTiled a) {
     __shared__ float sm[3][BY][BX];
     extern __shared__ unsigned char dyn_smem[];
     __shared__ __align__(8) unsigned long long s_bars[NS];
     TmaRing ring;
     ring.base = (unsigned char*)(((uintptr_t)dyn_smem + 127) & ~(uintptr_t)127);
     ring.bar0 = smem_u32(&s_bars[0]);
-    ring.issued = 0;
-    ring.waited = 0;
+    ring.issue_s = 0;
+    ring.wait_s = 0;
+    ring.wait_ph = 0;
+    ring.in_flight = 0;
     if (a.c.maps) {
         if (threadIdx.x == 0) {
             for (int i = 0; i < NS; ++i) mbar_init(ring.bar0 + 8u * i, 1u);

@@ -117,7 +117,7 @@ cudaError_t launch_tv(const Real* alpha, int nx, int ny, int nz, int bc, double 
 // ------------------------------------------------- tiled FP32 solver (cg_tiled.cu)
 namespace tiled {
 
-constexpr int TX = 32, TY = 16, NT = TX * TY;   // CTA: 32 x 16 columns, one thread each
+constexpr int TX = 32, TY = 32, NT = TX * TY;   // CTA: 32 x 32 columns, one thread each (one CTA per SM)
 
 struct Geo {
     int nx, ny, nz;
@@ -139,9 +139,9 @@ struct Vecs {
 
 // TMA descriptors of the arrays one CG iteration reads (tiled FP32 path).
 struct TmaMaps {
-    CUtensorMap u[2], ws[2], ss[2];   // box 40 x 18 at (x0-4, y0-1, k)
-    CUtensorMap alpha;                // box 40 x 18 at (x0-4, y0-1, k)
-    CUtensorMap p, delta;             // box 32 x 16 at (x0, y0, k)
+    CUtensorMap u[2], ws[2], ss[2];   // box 40 x 34 at (x0-4, y0-1, k)
+    CUtensorMap alpha;                // box 40 x 34 at (x0-4, y0-1, k)
+    CUtensorMap p, delta;             // box 32 x 32 at (x0, y0, k)
 };
 
 struct Common {
