@@ -252,6 +252,15 @@ struct Call {
     }
 
     static constexpr bool kTiled = std::is_same<Real, float>::value;
+    // every state slot of the call (slots of SB bytes) in one slab, so that a
+    // single tensor map reaches all of them
+    Real* slab = nullptr;
+    unsigned slab_planes = 0;
+    Real* carve_slab(Arena& a, size_t slots, size_t slot_bytes) {
+        slab = (Real*)a.take(slots * slot_bytes);
+        slab_planes = (unsigned)(slots * (slot_bytes / sizeof(Real)) / P.S);
+        return slab;
+    }
     tiled::Vecs tv{};
     tiled::TmaMaps* tmaps = nullptr;   // device copy (TMA-staged iterations), or null
 
@@ -298,7 +307,8 @@ struct Call {
             tiled::TmaMaps host;
             tiled::Geo g{};
             g.nx = P.nx; g.ny = P.ny; g.nz = P.nz; g.S = P.S;
-            if (!tiled_encode_maps(&host, g, tv.u, tv.ws, tv.ss, tv.p, tv.delta, (const float*)alpha.dev))
+            if (!tiled_encode_maps(&host, g, tv.u, tv.ws, tv.ss, tv.p, tv.delta, (const float*)alpha.dev,
+                                   (const float*)slab, slab_planes))
                 return NEFTY_OK;
             NEFTY_CUDA(h, cudaMemcpyAsync(tmaps, &host, sizeof host, cudaMemcpyHostToDevice, s));
             NEFTY_CUDA(h, cudaStreamSynchronize(s));
@@ -377,6 +387,8 @@ struct Call {
         c.g.tiles_x = (P.nx + tiled::TX - 1) / tiled::TX;
         c.g.units = (unsigned)(c.g.tiles_x * ((P.ny + tiled::TY - 1) / tiled::TY)) * (unsigned)P.nz;
         c.maps = use_tma ? tmaps : nullptr;
+        c.slab = (const float*)slab;
+        c.slab_planes = slab_planes;
         c.alpha = (const float*)alpha.dev;
         c.kx = (float)(P.dt / (P.dx * P.dx));
         c.ky = (float)(P.dt / (P.dy * P.dy));
@@ -446,6 +458,8 @@ struct Call {
         NEFTY_CUDA(h, cudaMemcpy(&hc, ctl, sizeof hc, cudaMemcpyDeviceToHost));
         if (hc.err == kDevTimeout)
             return fail(h, NEFTY_ETIMEOUT, "a grid barrier of the persistent solver timed out");
+        if (hc.err == kDevBadState)
+            return fail(h, NEFTY_ECUDA, "internal error: a solver state lies outside the state slab");
         if (want_loss && loss_out) {
             std::vector<double> lp(G);
             NEFTY_CUDA(h, cudaMemcpy(lp.data(), loss_partials, G * sizeof(double), cudaMemcpyDeviceToHost));
@@ -521,9 +535,10 @@ nefty_status run_forward(nefty_handle* h, const Prob& P, const void* alpha, cons
     const bool own_t0 = Call<Real>::kTiled || !C.T0.user;
     auto layout = [&](Arena& a) {
         C.place_common(a, 2 * nt);
-        work[0] = (Real*)a.take(SB);
-        work[1] = (Real*)a.take(SB);
-        t0buf = (Real*)a.take(own_t0 ? SB : 0);
+        Real* blk = C.carve_slab(a, own_t0 ? 3 : 2, SB);
+        work[0] = blk;
+        work[1] = blk + SB / R;
+        t0buf = own_t0 ? blk + 2 * (SB / R) : nullptr;
         fr.place(a);
         tf.place(a);
     };
@@ -593,7 +608,7 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
     {
         Arena a;
         C.place_common(a, 6 * nt + 4);
-        a.take(2 * N * R);        // mu
+        a.take(2 * (Call<Real>::kTiled ? 2 : 1) * N * R);   // mu
         a.take(N * sizeof(double));
         ga.place(a);
         gt.place(a);
@@ -614,16 +629,20 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
     const size_t SB = (Call<Real>::kTiled ? 2 : 1) * N * R;   // one state slot (see run_forward)
     auto layout = [&](Arena& a) {
         C.place_common(a, 6 * nt + 4);
-        mu[0] = (Real*)a.take(SB);
-        mu[1] = (Real*)a.take(SB);
         grad = (double*)a.take(N * sizeof(double));
         ga.place(a);
         gt.place(a);
-        for (int i = 0; i < nck; ++i) ck[i] = (Real*)a.take(SB);
-        for (int i = 0; i < nseg_buf; ++i) segbuf[i] = (Real*)a.take(SB);
+        // state slots: mu[2], checkpoints, recompute buffer, forward work pair
+        const size_t slots = 2 + (size_t)nck + (size_t)nseg_buf + (K > 1 ? 2 : 0);
+        Real* next = C.carve_slab(a, slots, SB);
+        auto slot = [&]() { Real* p = next; next += SB / R; return p; };
+        mu[0] = slot();
+        mu[1] = slot();
+        for (int i = 0; i < nck; ++i) ck[i] = slot();
+        for (int i = 0; i < nseg_buf; ++i) segbuf[i] = slot();
         if (K > 1) {
-            work[0] = (Real*)a.take(SB);
-            work[1] = (Real*)a.take(SB);
+            work[0] = slot();
+            work[1] = slot();
         }
     };
     Arena probe;

@@ -8,32 +8,42 @@
 // s = A p follows from s_i = w_i + beta_i s_{i-1}.  The kernel stores the
 // preconditioned vectors u, ws = M^{-1} w and ss = M^{-1} s, so that the next
 // iterate u_{i+1} = u_i - alpha_i (ws_i + beta_i ss_{i-1}) can be formed at any
-// cell from its own values; the only neighbour data a pass needs is u_{i+1}
-// itself, staged plane by plane in shared memory.
+// cell from that cell's own stored values; a pass needs nothing from its
+// neighbours but those values.
 //
-// Work layout: the grid is cut into 32 x 32 columns (one warp per row of 32
-// cells along x) and the (tile, plane) pairs are split evenly over the CTAs;
-// each CTA marches up z through its planes, keeping the field of planes k-1 and
-// k+1 for its own column in registers and plane k with a one-cell halo ring in a
-// triple-buffered shared tile.
+// Work layout: the grid is cut into 32 x 32 columns and the (tile, plane)
+// pairs are split evenly over the CTAs; each CTA marches up z through its
+// share.  A CTA has eight compute warps and one copy warp.  A compute thread
+// owns four consecutive cells along x (a quad) in one row of the tile.
+//
+// Iteration passes stage their inputs through the Tensor Memory Accelerator:
+// the copy warp streams every plane (u, ws, ss and alpha with a one-cell halo;
+// p and delta) into a ring of shared-memory stages guarded by full/empty
+// mbarriers, and the compute warps consume the stages in order with no
+// CTA-wide barrier.  A thread that needs u_{i+1} at a neighbour cell forms it
+// again from the staged values with the same fused multiply-adds as the
+// cell's owner, so every thread sees the same bits.  The passes that run once
+// per solve (initial residual, first product, gradient) and grids that TMA
+// cannot stage (periodic walls, nx % 4 != 0) read global memory directly.
 //
 // Numerics: the stencil is evaluated in flux form, A v = v + sum_f c_f (v_c - v_q)
 // (+ Robin sink), and each solve accumulates its increment delta separately so
 // that T^{n+1} = T^n + delta is rounded once per step.  Inner products are
-// summed per thread in FP32 over the thread's cells of one pass and then in FP64
-// across threads and CTAs in a fixed order, so repeated runs are bitwise equal.
+// accumulated per thread as compensated FP32 pairs and summed across threads
+// and CTAs in a fixed order, so repeated runs are bitwise equal.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "internal.h"
 
 namespace nefty {
 namespace tiled {
 
-constexpr int BX = TX + 2, BY = TY + 2;         // shared tile with halo
-constexpr int RING = 2 * BX + 2 * TY;           // halo cells per plane
+constexpr int NW = NT / 32;   // warps per CTA
 
 // ------------------------------------------------------------------ sync
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -57,7 +67,7 @@ __device__ __forceinline__ unsigned long long now_ns() {
 
 struct Sync {
     DevCtl* ctl;
-    double* partials;   // [2][kMaxRed][G]
+    double* partials;   // [2][kMaxRed][G] float2 pairs
     unsigned G;
     unsigned epoch;     // thread 0 only
     unsigned red;       // uniform
@@ -109,6 +119,17 @@ __device__ __forceinline__ void add_pair(float hi, float lo, float d, float& oh,
     two_sum(s, lo + e, oh, ol);
 }
 
+// Per-thread compensated accumulators of NV inner products.
+template <int NV>
+struct Acc {
+    float h[NV], l[NV];
+    __device__ Acc() {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) h[i] = l[i] = 0.f;
+    }
+    __device__ __forceinline__ void add(int i, float v) { add_pair(h[i], l[i], v, h[i], l[i]); }
+};
+
 // Compensated warp sum of (hi, lo) pairs; lane 0 holds the result.
 __device__ __forceinline__ void warp_sum2(float& hi, float& lo) {
 #pragma unroll
@@ -121,20 +142,22 @@ __device__ __forceinline__ void warp_sum2(float& hi, float& lo) {
     }
 }
 
-// Grid sum of NV values given per thread in FP32.  The sums run on the FP32
-// pipes as compensated (hi, lo) pairs, which keeps about twice the FP32
-// precision: per thread over its cells, then TwoSum trees over the warp, the
-// CTA and the G CTA partials (fixed order, so every run gives the same bits).
-// GB300's FP64 rate is a small fraction of its FP32 rate, so no FP64 arithmetic
-// is done per thread.  On return thread 0 holds the totals as doubles
-// (hi + lo); the other threads' out[] is unspecified.
+// Grid sum of NV compensated per-thread pairs.  The sums run on the FP32
+// pipes as (hi, lo) pairs, which keeps about twice the FP32 precision: TwoSum
+// trees over the warp, the CTA and the G CTA partials (fixed order, so every
+// run gives the same bits).  GB300's FP64 rate is a small fraction of its FP32
+// rate, so no FP64 arithmetic is done per thread.  On return thread 0 holds
+// the totals as doubles (hi + lo); the other threads' out[] is unspecified.
+// Every pass ends here, so this is also where each thread orders its global
+// stores of the pass before the TMA reads of later passes.
 template <int NV>
-__device__ bool grid_sum(Sync& g, const float (&in)[NV], double (&out)[NV]) {
-    __shared__ float s_h[NT / 32][kMaxRed], s_l[NT / 32][kMaxRed];
+__device__ bool grid_sum(Sync& g, const Acc<NV>& in, double (&out)[NV]) {
+    __shared__ float s_h[NW][kMaxRed], s_l[NW][kMaxRed];
+    asm volatile("fence.proxy.async.global;" ::: "memory");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
-        float hi = in[i], lo = 0.f;
+        float hi = in.h[i], lo = in.l[i];
         warp_sum2(hi, lo);
         if (lane == 0) { s_h[warp][i] = hi; s_l[warp][i] = lo; }
     }
@@ -143,7 +166,7 @@ __device__ bool grid_sum(Sync& g, const float (&in)[NV], double (&out)[NV]) {
     if (warp == 0) {
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
-            float hi = lane < NT / 32 ? s_h[lane][i] : 0.f, lo = lane < NT / 32 ? s_l[lane][i] : 0.f;
+            float hi = lane < NW ? s_h[lane][i] : 0.f, lo = lane < NW ? s_l[lane][i] : 0.f;
             warp_sum2(hi, lo);
             if (lane == 0) part[(size_t)i * g.G + blockIdx.x] = make_float2(hi, lo);
         }
@@ -169,7 +192,7 @@ __device__ bool grid_sum(Sync& g, const float (&in)[NV], double (&out)[NV]) {
 }
 
 __device__ double block_sum(double v) {
-    __shared__ double s[NT / 32];
+    __shared__ double s[NW];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -178,44 +201,14 @@ __device__ double block_sum(double v) {
     __syncthreads();
     double t = 0.0;
     if (warp == 0) {
-        t = lane < NT / 32 ? s[lane] : 0.0;
+        t = lane < NW ? s[lane] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     }
     return t;
 }
 
-// --------------------------------------------------------------- geometry
-// Map a lateral coordinate through the boundary condition: wrapped when
-// periodic, -1 when outside a zero-flux wall.
-__device__ __forceinline__ int map_x(const Geo& g, int x) {
-    if (x < 0) return g.px ? x + g.nx : -1;
-    if (x >= g.nx) { x = g.px ? x - g.nx : -1; return x < g.nx ? x : -1; }
-    return x;
-}
-__device__ __forceinline__ int map_y(const Geo& g, int y) {
-    if (y < 0) return g.py ? y + g.ny : -1;
-    if (y >= g.ny) { y = g.py ? y - g.ny : -1; return y < g.ny ? y : -1; }
-    return y;
-}
-
-// The halo ring's RING cells are spread over the high lanes of all warps
-// (slot r -> warp r % 16, lane 31 - r / 16), keeping thread 0 free to issue
-// copies and every warp's share of the ring equal.  Returns -1 for no slot.
-__device__ __forceinline__ int ring_slot() {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int r = (31 - lane) * (NT / 32) + warp;
-    return r < RING ? r : -1;
-}
-
-// Halo-ring slot t in [0, RING) -> (row, col) in the BY x BX shared tile.
-__device__ __forceinline__ void ring_pos(int t, int& hy, int& hx) {
-    if (t < BX) { hy = 0; hx = t; }
-    else if (t < 2 * BX) { hy = BY - 1; hx = t - BX; }
-    else if (t < 2 * BX + TY) { hy = t - 2 * BX + 1; hx = 0; }
-    else { hy = t - 2 * BX - TY + 1; hx = BX - 1; }
-}
-
+// --------------------------------------------------------------- operator
 // Hardware reciprocal (rcp.approx, about 1 ulp).  Used for the face values and
 // the Jacobi diagonal: their rounding moves the solution far less than the
 // FP32 CG arithmetic does, and every pass evaluates them identically.
@@ -226,78 +219,50 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 // Harmonic-mean face value dt * a_f = k * 2 a b / (a + b), k = dt / h^2, of the
-// face between cells of diffusivity a and b (Prop. 1).  Both cells that share a
-// face evaluate the same products on the same two values, so A stays exactly
+// face between cells of diffusivity a and b (Prop. 1).  face(a, b) and
+// face(b, a) are the same products of the same two values, so A stays exactly
 // symmetric.  b = 0 (a cell beyond a zero-flux wall, as TMA fills it) gives 0.
 __device__ __forceinline__ float face(float a, float b, float k) {
     return k * (2.f * a * b) * rcp_approx(a + b);
 }
 
-// Face values +x, -x, +y, -y of the own cell c = (x, y, k), from alpha.
-struct Faces { float xp, xm, yp, ym; };
-__device__ __forceinline__ Faces lateral_faces(const Geo& g, const float* __restrict__ al, unsigned c, int x,
-                                               int y, float ac, float kx, float ky) {
-    Faces f;
+// Neighbours of cell c = (x, y, k) in the order +x, -x, +y, -y, +z, -z; bit f
+// of m is set when neighbour f exists (inside the grid or across a periodic
+// wrap).  A missing neighbour is a zero-flux wall.
+struct Nb {
+    unsigned q[6];
+    unsigned m;
+};
+__device__ __forceinline__ Nb neighbours(const Geo& g, unsigned c, int x, int y, int k) {
+    Nb n;
+    n.m = 0;
     const unsigned wrap_y = (unsigned)(g.ny - 1) * g.nx;
-    f.xp = x + 1 < g.nx ? face(ac, al[c + 1], kx) : (g.px ? face(ac, al[c + 1 - g.nx], kx) : 0.f);
-    f.xm = x > 0 ? face(ac, al[c - 1], kx) : (g.px ? face(ac, al[c + g.nx - 1], kx) : 0.f);
-    f.yp = y + 1 < g.ny ? face(ac, al[c + g.nx], ky) : (g.py ? face(ac, al[c - wrap_y], ky) : 0.f);
-    f.ym = y > 0 ? face(ac, al[c - g.nx], ky) : (g.py ? face(ac, al[c + wrap_y], ky) : 0.f);
-    return f;
+    if (x + 1 < g.nx) { n.q[0] = c + 1; n.m |= 1u; } else if (g.px) { n.q[0] = c + 1 - g.nx; n.m |= 1u; }
+    if (x > 0) { n.q[1] = c - 1; n.m |= 2u; } else if (g.px) { n.q[1] = c + g.nx - 1; n.m |= 2u; }
+    if (y + 1 < g.ny) { n.q[2] = c + g.nx; n.m |= 4u; } else if (g.py) { n.q[2] = c - wrap_y; n.m |= 4u; }
+    if (y > 0) { n.q[3] = c - g.nx; n.m |= 8u; } else if (g.py) { n.q[3] = c + wrap_y; n.m |= 8u; }
+    if (k + 1 < g.nz) { n.q[4] = c + g.S; n.m |= 16u; }
+    if (k > 0) { n.q[5] = c - g.S; n.m |= 32u; }
+    return n;
 }
 
-// --------------------------------------------------------------- marching
-// Generic z-march over the planes [k0, k1) of one tile.  FieldFn(cell, own)
-// returns the stencil field at a global cell; BodyFn(k, c, x, y, valid,
-// fc, fxm, fxp, fym, fyp, fzm, fzp) consumes it at the own cell.  Cells outside
-// a zero-flux wall give 0 (their face value is 0, so they never contribute).
-template <class FieldFn, class BodyFn>
-__device__ __forceinline__ void march(const Geo& g, int tile, int k0, int k1, float (*sm)[BY][BX],
-                                      FieldFn field, BodyFn body) {
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int x0 = (tile % g.tiles_x) * TX, y0 = (tile / g.tiles_x) * TY;
-    const int x = x0 + tx, y = y0 + ty;
-    const bool valid = x < g.nx && y < g.ny;
-    // where this thread's box slot maps (own slot; invalid threads may map
-    // to a wrapped cell that a valid neighbour needs)
-    const int mx = map_x(g, x), my = map_y(g, y);
-    const bool own_mapped = mx >= 0 && my >= 0;
-    const unsigned own_col = own_mapped ? (unsigned)my * g.nx + mx : 0u;
-    // ring slot (first RING threads)
-    int rhy = 0, rhx = 0;
-    unsigned ring_col = 0;
-    bool ring_mapped = false;
-    const int rslot = ring_slot();
-    if (rslot >= 0) {
-        ring_pos(rslot, rhy, rhx);
-        const int gx = map_x(g, x0 - 1 + rhx), gy = map_y(g, y0 - 1 + rhy);
-        ring_mapped = gx >= 0 && gy >= 0;
-        ring_col = ring_mapped ? (unsigned)gy * g.nx + gx : 0u;
+// The six face values of cell c (0 where there is no neighbour).
+__device__ __forceinline__ void cell_faces(const Common& C, const Nb& n, float ac, float (&cf)[6]) {
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        const float kf = f < 2 ? C.kx : (f < 4 ? C.ky : C.kz);
+        cf[f] = (n.m >> f & 1u) ? face(ac, C.alpha[n.q[f]], kf) : 0.f;
     }
-    auto fill = [&](int k) -> float {   // plane k into sm[k % 3]; returns own value
-        float* buf = &sm[k % 3][0][0];
-        const float v = own_mapped ? field(own_col + (unsigned)k * g.S, valid) : 0.f;
-        buf[(ty + 1) * BX + tx + 1] = v;
-        if (rslot >= 0) buf[rhy * BX + rhx] = ring_mapped ? field(ring_col + (unsigned)k * g.S, false) : 0.f;
-        return v;
-    };
-    float fzm = 0.f;
-    if (k0 > 0 && own_mapped) fzm = field(own_col + (unsigned)(k0 - 1) * g.S, valid);
-    float fc = fill(k0);
-    for (int k = k0; k < k1; ++k) {
-        float fzp = fc;
-        if (k + 1 < g.nz) fzp = fill(k + 1);
-        __syncthreads();
-        const float* buf = &sm[k % 3][0][0];
-        const int b = (ty + 1) * BX + tx + 1;
-        const float fxm = buf[b - 1], fxp = buf[b + 1], fym = buf[b - BX], fyp = buf[b + BX];
-        body(k, own_col + (unsigned)k * g.S, x, y, valid, fc, fxm, fxp, fym, fyp, k > 0 ? fzm : fc, fzp);
-        fzm = fc;
-        fc = fzp;
-    }
-    __syncthreads();
 }
 
+// Diagonal of A: 1 + the face values (+x, -x, +y, -y, +z, -z, in this order)
+// + the Robin sink.  Every path sums in this order.
+__device__ __forceinline__ float diag(float cxp, float cxm, float cyp, float cym, float czp, float czm,
+                                      float rob) {
+    return 1.f + cxp + cxm + cyp + cym + czp + czm + rob;
+}
+
+// --------------------------------------------------------------- work split
 // Iterate over this CTA's (tile, plane) segments.
 template <class SegFn>
 __device__ __forceinline__ void for_segments(const Geo& g, SegFn seg) {
@@ -313,31 +278,65 @@ __device__ __forceinline__ void for_segments(const Geo& g, SegFn seg) {
     }
 }
 
+// Visit every own cell of this CTA's segments, plane by plane: compute thread
+// t owns the quad x = x0 + 4 (t % 8) .. + 3 in row y0 + t / 8 of each tile.
+// The copy warp visits nothing.
+template <class CellFn>
+__device__ __forceinline__ void for_cells(const Geo& g, CellFn f) {
+    if (threadIdx.x >= NCT) return;
+    const int qx = threadIdx.x & 7, row = threadIdx.x >> 3;
+    for_segments(g, [&](int tile, int k0, int k1) {
+        const int xq = (tile % g.tiles_x) * TX + qx * QX, y = (tile / g.tiles_x) * TY + row;
+        if (y >= g.ny || xq >= g.nx) return;
+        unsigned cb = (unsigned)k0 * g.S + (unsigned)y * g.nx + xq;
+        for (int k = k0; k < k1; ++k, cb += g.S) {
+#pragma unroll
+            for (int j = 0; j < QX; ++j)
+                if (xq + j < g.nx) f(k, cb + j, xq + j, y);
+        }
+    });
+}
 
 // ------------------------------------------------------------ TMA staging
-// The CG iteration pass can take its inputs through the Tensor Memory
-// Accelerator: for every plane a single thread issues bulk tensor copies of
-// the six arrays the pass reads (u, ws, ss and alpha with a one-cell halo; p
-// and delta) into one stage of a six-stage shared-memory ring, completing on
-// that stage's mbarrier.  Copies run four planes ahead of the plane being
-// computed.  Cells outside the grid
-// arrive as zeros, which is exactly a zero-flux wall (their face values are
-// zero), so this path serves grids with zero-flux lateral walls and nx % 4 == 0
-// (row pitch a multiple of 16 bytes).
+// A stage holds one plane of a tile in six slots.  A slot takes either a
+// 40 x 34 box at (x0 - 4, y0 - 1) -- the tile with a one-cell halo, widened on
+// the left to keep the copy 16-byte aligned -- or a 32 x 32 box of the own
+// cells at (x0, y0).  Cells outside the grid arrive as zeros, which is exactly
+// a zero-flux wall (their face values are zero), so this path serves grids
+// with zero-flux lateral walls and nx % 4 == 0 (row pitch a multiple of 16
+// bytes).  Every stencil pass of a solve is staged this way; only what the
+// slots hold differs (PassKind).
 constexpr int NS = 6;                         // stages
-constexpr int HB = TX + 8, HR = TY + 2;       // halo box: x0-4 .. x0+35, y0-1 .. y0+TY
+constexpr int HB = TX + 8, HR = TY + 2;       // halo box
 constexpr int SZ_H = HB * HR * 4;             // 5440
 constexpr int SZ_O = TX * TY * 4;             // 4096
 constexpr int al128(int b) { return (b + 127) & ~127; }
-constexpr int OFF_U = 0;
-constexpr int OFF_W = OFF_U + al128(SZ_H);
-constexpr int OFF_S = OFF_W + al128(SZ_H);
-constexpr int OFF_A = OFF_S + al128(SZ_H);
-constexpr int OFF_P = OFF_A + al128(SZ_H);
-constexpr int OFF_D = OFF_P + al128(SZ_O);
-constexpr int STAGE_BYTES = al128(OFF_D + SZ_O);
-constexpr unsigned TX_BYTES = 4 * SZ_H + 2 * SZ_O;
+constexpr int SLOT = al128(SZ_H);
+constexpr int STAGE_BYTES = 6 * SLOT;
 constexpr int DYN_SMEM = NS * STAGE_BYTES + 128;   // + alignment slack
+__device__ __forceinline__ constexpr int sl(int s) { return s * SLOT; }
+
+// What the slots of a staged pass hold (h: halo box, o: own box).
+enum PassKind : int {
+    kIter,    // 0 u_i h, 1 ws_i h, 2 ss_{i-1} h, 3 alpha h, 4 p o, 5 delta o
+    kInit1,   // 0 x0 hi h, 1 x0 lo h, 3 alpha h
+    kInit2,   // 0 u_0 h, 3 alpha h
+    kGrad     // 0 T hi h, 1 T lo h, 2 mu hi h, 3 alpha h, 4 mu lo h
+};
+struct PassIn {
+    int kind;
+    int cur;          // kIter: ping-pong index of the inputs
+    bool first;       // kIter: first iteration (no ss, no p)
+    unsigned zx, zm;  // slab plane 0 of the state read (x0, or T) and of mu
+};
+__device__ __forceinline__ unsigned pass_bytes(const PassIn& in) {
+    switch (in.kind) {
+        case kIter: return in.first ? 3 * SZ_H + SZ_O : 4 * SZ_H + 2 * SZ_O;
+        case kInit1: return 3 * SZ_H;
+        case kInit2: return 2 * SZ_H;
+        default: return 5 * SZ_H;
+    }
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -349,7 +348,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, unsigned bytes) {
     asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(bar), "r"(bytes)
                  : "memory");
 }
-// Bounded wait on an mbarrier phase; false after about one second.
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(bar) : "memory");
+}
+// Bounded wait for the completion of the mbarrier phase of the given parity;
+// false after about two seconds.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, unsigned parity) {
     unsigned long long t0 = 0;
     for (unsigned i = 0;; ++i) {
@@ -370,195 +373,636 @@ __device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* map, 
         ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar) : "memory");
 }
 
-// Ring bookkeeping without division: copies are issued and waited in the same
-// order, so a stage index that advances by one (mod NS) and one parity bit per
-// stage describe both sides.
-struct TmaRing {
+// The stage ring.  Planes are copied and consumed in the same order (the
+// for_segments order, pass after pass), so a stage index that advances by one
+// (mod NS) and one parity bit per stage describe each side.  A stage's full
+// barrier completes when its copies land; its empty barrier when all CW
+// compute warps are done with it.
+struct Ring {
     unsigned char* base;   // NS stages, 128-byte aligned
-    uint32_t bar0;         // shared address of NS mbarriers (8 bytes each)
-    unsigned issue_s;      // stage of the next copy (thread 0)
-    unsigned wait_s;       // stage of the next wait (uniform)
-    unsigned wait_ph;      // bit s: parity of the next wait on stage s (uniform)
-    unsigned in_flight;    // copies issued and not yet waited (thread 0)
+    uint32_t full0;        // shared addresses of the NS full / NS empty mbarriers
+    uint32_t empty0;
+    // copy side (lane 0 of the copy warp)
+    unsigned ps;           // stage of the next copy
+    unsigned pph;          // bit s: parity of the next empty-wait on stage s
+    unsigned fiss;         // bit s: number of copies issued into stage s, mod 2
+    unsigned used;         // bit s: stage s has received a copy
+    // compute side (same in every compute thread)
+    unsigned cs;           // stage of the next full-wait
+    unsigned cph;          // bit s: parity of the next full-wait on stage s
 };
 
 __device__ __forceinline__ unsigned ring_next(unsigned s) { return s + 1 == NS ? 0u : s + 1; }
 
-__device__ __forceinline__ void issue_plane(TmaRing& R, const TmaMaps* M, int cur, int x0, int y0, int k) {
-    const unsigned st = R.issue_s;
-    const uint32_t dst = smem_u32(R.base + st * STAGE_BYTES);
-    const uint32_t bar = R.bar0 + 8u * st;
-    mbar_expect_tx(bar, TX_BYTES);
-    tma_load3(dst + OFF_U, &M->u[cur], x0 - 4, y0 - 1, k, bar);
-    tma_load3(dst + OFF_W, &M->ws[cur], x0 - 4, y0 - 1, k, bar);
-    tma_load3(dst + OFF_S, &M->ss[cur], x0 - 4, y0 - 1, k, bar);
-    tma_load3(dst + OFF_A, &M->alpha, x0 - 4, y0 - 1, k, bar);
-    tma_load3(dst + OFF_P, &M->p, x0, y0, k, bar);
-    tma_load3(dst + OFF_D, &M->delta, x0, y0, k, bar);
-    R.issue_s = ring_next(st);
-    R.in_flight += 1;
-}
-
-// Wait for the next stage in order; returns its index, or -1 on timeout.
-__device__ __forceinline__ int wait_next(TmaRing& R) {
-    const unsigned st = R.wait_s;
-    const bool ok = mbar_wait(R.bar0 + 8u * st, (R.wait_ph >> st) & 1u);
-    R.wait_ph ^= 1u << st;
-    R.wait_s = ring_next(st);
-    return ok ? (int)st : -1;
-}
-
-// After a timed-out wait: wait (again bounded) for the copies this CTA still
-// has in flight, so none is landing in shared memory when the kernel exits.
-__device__ void drain(TmaRing& R) {
-    while (R.in_flight > 0) {
-        wait_next(R);
-        R.in_flight -= 1;
+__device__ Ring make_ring(unsigned char* dyn, unsigned long long* full, unsigned long long* empty, bool init) {
+    Ring R;
+    R.base = (unsigned char*)(((uintptr_t)dyn + 127) & ~(uintptr_t)127);
+    R.full0 = smem_u32(full);
+    R.empty0 = smem_u32(empty);
+    R.ps = 0;
+    R.pph = (1u << NS) - 1;   // a fresh barrier's preceding phase counts as complete
+    R.fiss = 0;
+    R.used = 0;
+    R.cs = 0;
+    R.cph = 0;
+    if (init) {
+        if (threadIdx.x == 0) {
+            for (int i = 0; i < NS; ++i) {
+                mbar_init(R.full0 + 8u * i, 1u);
+                mbar_init(R.empty0 + 8u * i, (unsigned)CW);
+            }
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        __syncthreads();
     }
+    return R;
 }
 
-// One single-reduction CG iteration over this CTA's segments, inputs staged by
-// TMA.  Same arithmetic as the plain-load pass in solve().
-__device__ bool iter_pass_tma(const Common& C, TmaRing& R, float (*fr)[BY][BX], int cur, float a, float bt,
-                              bool first, float (&acc)[3]) {
+// Copy side of one staged pass (lane 0 of the copy warp): every plane of
+// every segment, with the plane below and above each segment.  Returns false
+// if a stage did not come free in time.
+__device__ bool produce(const Common& C, Ring& R, const PassIn& in) {
     const Geo& g = C.g;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    float* __restrict__ uo = C.v.u[cur ^ 1];
-    float* __restrict__ wo = C.v.ws[cur ^ 1];
-    float* __restrict__ so = C.v.ss[cur ^ 1];
-    // per-thread offsets that do not change with the plane
-    const int hb = (ty + 1) * HB + tx + 4;      // own cell in a halo box
-    const int ob = ty * TX + tx;                 // own cell in an own-cell box
-    const int fb = (ty + 1) * BX + tx + 1;       // own cell in the field tile
-    const int rslot = ring_slot();
-    int rhb = 0, rfb = 0;
-    if (rslot >= 0) {
-        int hy, hx;
-        ring_pos(rslot, hy, hx);
-        rhb = hy * HB + hx + 3;
-        rfb = hy * BX + hx;
-    }
+    const TmaMaps* M = C.maps;
+    const unsigned bytes = pass_bytes(in);
     bool ok = true;
-    if (threadIdx.x == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
     for_segments(g, [&](int tile, int k0, int k1) {
         if (!ok) return;
         const int x0 = (tile % g.tiles_x) * TX, y0 = (tile / g.tiles_x) * TY;
-        const int x = x0 + tx, y = y0 + ty;
-        const bool valid = x < g.nx && y < g.ny;
-        const int kl = k0 > 0 ? k0 - 1 : 0;
-        const int kh = k1 < g.nz ? k1 : g.nz - 1;
-        int next = kl;   // next plane to copy (thread 0)
-        if (threadIdx.x == 0)
-            while (next <= kh && next < kl + NS) issue_plane(R, C.maps, cur, x0, y0, next++);
-        auto stage_ptr = [&](int s) -> const unsigned char* { return R.base + (unsigned)s * STAGE_BYTES; };
-        // u_{i+1} = u_i - a (ws_i + b ss_{i-1}) at the own cell and the ring cell
-        // of one staged plane, into field buffer fbuf; returns the own value
-        auto fill = [&](const unsigned char* st, float* fbuf) -> float {
-            const float* U = (const float*)(st + OFF_U);
-            const float* W = (const float*)(st + OFF_W);
-            const float* Sv = (const float*)(st + OFF_S);
-            const float vo = U[hb] - a * (first ? W[hb] : W[hb] + bt * Sv[hb]);
-            fbuf[fb] = vo;
-            if (rslot >= 0) fbuf[rfb] = U[rhb] - a * (first ? W[rhb] : W[rhb] + bt * Sv[rhb]);
-            return vo;
-        };
-        // A failed (timed-out) wait aborts the whole CTA together: the decision
-        // is taken with __syncthreads_or so no thread is left at a barrier.
-        auto abort_uniform = [&](bool mine_ok) -> bool {
-            if (!__syncthreads_or(mine_ok ? 0 : 1)) return false;
-            if (threadIdx.x == 0) drain(R);
-            ok = false;
-            return true;
-        };
-        auto waited = [&]() { if (threadIdx.x == 0) R.in_flight -= 1; };
-        float czm = 0.f, fzm = 0.f;
-        int sm1 = -1;
-        bool w_ok = true;
-        if (k0 > 0) {
-            sm1 = wait_next(R);
-            waited();
-            w_ok = sm1 >= 0;
-            if (w_ok) {
-                const unsigned char* st = stage_ptr(sm1);
-                const float* U = (const float*)(st + OFF_U);
-                const float* W = (const float*)(st + OFF_W);
-                const float* Sv = (const float*)(st + OFF_S);
-                fzm = U[hb] - a * (first ? W[hb] : W[hb] + bt * Sv[hb]);
+        const int kl = k0 > 0 ? k0 - 1 : 0, kh = k1 < g.nz ? k1 : g.nz - 1;
+        for (int k = kl; k <= kh; ++k) {
+            const unsigned st = R.ps;
+            if (!mbar_wait(R.empty0 + 8u * st, (R.pph >> st) & 1u)) { ok = false; return; }
+            R.pph ^= 1u << st;
+            const uint32_t dst = smem_u32(R.base + st * STAGE_BYTES), bar = R.full0 + 8u * st;
+            mbar_expect_tx(bar, bytes);
+            auto halo = [&](int s, const CUtensorMap* m, int z) { tma_load3(dst + sl(s), m, x0 - 4, y0 - 1, z, bar); };
+            switch (in.kind) {
+                case kIter:
+                    halo(0, &M->u[in.cur], k);
+                    halo(1, &M->ws[in.cur], k);
+                    if (!in.first) halo(2, &M->ss[in.cur], k);
+                    halo(3, &M->alpha, k);
+                    if (!in.first) tma_load3(dst + sl(4), &M->p, x0, y0, k, bar);
+                    tma_load3(dst + sl(5), &M->delta, x0, y0, k, bar);
+                    break;
+                case kInit1:
+                    halo(0, &M->states, (int)in.zx + k);
+                    halo(1, &M->states, (int)in.zx + g.nz + k);
+                    halo(3, &M->alpha, k);
+                    break;
+                case kInit2:
+                    halo(0, &M->u[0], k);
+                    halo(3, &M->alpha, k);
+                    break;
+                default:
+                    halo(0, &M->states, (int)in.zx + k);
+                    halo(1, &M->states, (int)in.zx + g.nz + k);
+                    halo(2, &M->states, (int)in.zm + k);
+                    halo(3, &M->alpha, k);
+                    halo(4, &M->states, (int)in.zm + g.nz + k);
+                    break;
             }
+            R.fiss ^= 1u << st;
+            R.used |= 1u << st;
+            R.ps = ring_next(st);
         }
-        int sk = -1;
-        if (w_ok) {
-            sk = wait_next(R);
-            waited();
-            w_ok = sk >= 0;
-        }
-        int fk = 0;   // field buffer of plane k (rotates 0, 1, 2)
-        float fc = 0.f;
-        if (w_ok) {
-            if (k0 > 0) czm = face(((const float*)(stage_ptr(sk) + OFF_A))[hb], ((const float*)(stage_ptr(sm1) + OFF_A))[hb], C.kz);
-            fc = fill(stage_ptr(sk), &fr[fk][0][0]);
-        }
-        if (abort_uniform(w_ok)) return;
-        unsigned c = (unsigned)k0 * g.S + (unsigned)y * g.nx + x;
-        for (int k = k0; k < k1; ++k, c += g.S) {
-            const int fk1 = fk == 2 ? 0 : fk + 1;
-            float fzp = fc;
-            int sk1 = -1;
-            w_ok = true;
-            if (k + 1 < g.nz) {
-                sk1 = wait_next(R);
-                waited();
-                w_ok = sk1 >= 0;
-                if (w_ok) fzp = fill(stage_ptr(sk1), &fr[fk1][0][0]);
-            }
-            if (abort_uniform(w_ok)) return;
-            // plane k-1 is no longer read by anyone: refill its stage
-            if (threadIdx.x == 0)
-                while (next <= kh && next <= k - 1 + NS) issue_plane(R, C.maps, cur, x0, y0, next++);
-            if (valid) {
-                const unsigned char* st = stage_ptr(sk);
-                const float* buf = &fr[fk][0][0];
-                const float fxm = buf[fb - 1], fxp = buf[fb + 1], fym = buf[fb - BX], fyp = buf[fb + BX];
-                const float fzmv = k > 0 ? fzm : fc;
-                const float* As = (const float*)(st + OFF_A);
-                const float ac = As[hb];
-                const float cxp = face(ac, As[hb + 1], C.kx), cxm = face(ac, As[hb - 1], C.kx);
-                const float cyp = face(ac, As[hb + HB], C.ky), cym = face(ac, As[hb - HB], C.ky);
-                const float czp = sk1 >= 0 ? face(ac, ((const float*)(stage_ptr(sk1) + OFF_A))[hb], C.kz) : 0.f;
-                const float rob = k + 1 == g.nz ? C.robin : 0.f;
-                const float d = 1.f + cxp + cxm + cyp + cym + czp + czm + rob;
-                const float Au = fc + cxp * (fc - fxp) + cxm * (fc - fxm) + cyp * (fc - fyp) + cym * (fc - fym) +
-                                 czp * (fc - fzp) + czm * (fc - fzmv) + rob * fc;
-                const float wn = rcp_approx(d) * Au;
-                const float uold = ((const float*)(st + OFF_U))[hb];
-                const float wold = ((const float*)(st + OFF_W))[hb];
-                const float sn = first ? wold : wold + bt * ((const float*)(st + OFF_S))[hb];
-                const float pn = first ? uold : uold + bt * ((const float*)(st + OFF_P))[ob];
-                const float dl = ((const float*)(st + OFF_D))[ob] + a * pn;
-                C.v.p[c] = pn;
-                C.v.delta[c] = dl;
-                uo[c] = fc;
-                wo[c] = wn;
-                so[c] = sn;
-                const float r = d * fc;
-                acc[0] += r * fc;
-                acc[1] += Au * fc;
-                acc[2] += r * r;
-                czm = czp;
-            }
-            fzm = fc;
-            fc = fzp;
-            sk = sk1;
-            fk = fk1;
-        }
-        __syncthreads();
     });
     return ok;
 }
 
-// Diagonal of A at the own cell from its six face values.
-__device__ __forceinline__ float diag(const Faces& f, float czp, float czm, float rob) {
-    return 1.f + f.xp + f.xm + f.yp + f.ym + czp + czm + rob;
+// After a failure: wait (again bounded) for the latest copy into every stage,
+// so no copy is landing in shared memory when the kernel exits.
+__device__ void drain(Ring& R) {
+    for (int s = 0; s < NS; ++s)
+        if (R.used >> s & 1u) mbar_wait(R.full0 + 8u * s, ((R.fiss >> s) & 1u) ^ 1u);
+}
+
+// Compute side of one staged pass: walk the same planes in the same order,
+// waiting for each stage and handing it back once every warp is done with it.
+// A compute thread owns the quad at halo-box index hb (own-box index ob).
+// Body holds the thread's values of the own quad on planes k-1, k, k+1:
+//   reset()            segment start;      below(st)  plane k0 - 1;
+//   own(st, has_below) plane k0;           above(st)  plane k + 1;
+//   top()              no plane above k;   shift()    k -> k + 1;
+//   plane(k, c, valid, st, st1) the work on plane k (st1: the stage of plane
+//                      k + 1, or null at the top).
+template <class Body>
+__device__ bool consume(const Geo& g, Ring& R, Body& B) {
+    const int lane = threadIdx.x & 31, qx = threadIdx.x & 7, row = threadIdx.x >> 3;
+    const int hb = (row + 1) * HB + 4 + 4 * qx;
+    const int ob = row * TX + 4 * qx;
+    bool ok = true;
+    auto wait = [&]() -> int {
+        const unsigned st = R.cs;
+        const bool done = mbar_wait(R.full0 + 8u * st, (R.cph >> st) & 1u);
+        R.cph ^= 1u << st;
+        R.cs = ring_next(st);
+        return done ? (int)st : -1;
+    };
+    auto release = [&](int st) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(R.empty0 + 8u * st);
+    };
+    auto stage = [&](int st) -> const unsigned char* { return R.base + (unsigned)st * STAGE_BYTES; };
+    for_segments(g, [&](int tile, int k0, int k1) {
+        if (!ok) return;
+        const int xq = (tile % g.tiles_x) * TX + 4 * qx, y = (tile / g.tiles_x) * TY + row;
+        const bool valid = xq < g.nx && y < g.ny;   // nx % 4 == 0: a quad is all in or all out
+        B.reset();
+        if (k0 > 0) {
+            const int s = wait();
+            if (s < 0) { ok = false; return; }
+            B.below(stage(s), hb);
+            release(s);
+        }
+        int sk = wait();
+        if (sk < 0) { ok = false; return; }
+        B.own(stage(sk), hb, k0 > 0);
+        unsigned c = (unsigned)k0 * g.S + (unsigned)y * g.nx + xq;
+        for (int k = k0; k < k1; ++k, c += g.S) {
+            int sk1 = -1;
+            if (k + 1 < g.nz) {
+                sk1 = wait();
+                if (sk1 < 0) { ok = false; return; }
+                B.above(stage(sk1), hb);
+            } else {
+                B.top();
+            }
+            B.plane(k, c, valid, stage(sk), sk1 >= 0 ? stage(sk1) : nullptr, hb, ob);
+            release(sk);
+            B.shift();
+            sk = sk1;
+        }
+        if (sk >= 0 && k1 < g.nz) release(sk);   // the plane above the segment
+    });
+    return ok;
+}
+
+__device__ __forceinline__ float4 lds4(const unsigned char* st, int off, int i) {
+    return *reinterpret_cast<const float4*>(st + off + 4 * i);
+}
+__device__ __forceinline__ float lds1(const unsigned char* st, int off, int i) {
+    return *reinterpret_cast<const float*>(st + off + 4 * i);
+}
+__device__ __forceinline__ void ld4(const unsigned char* st, int off, int i, float (&v)[4]) {
+    const float4 q = lds4(st, off, i);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void stg4(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void set4(float (&d)[4], float v) { d[0] = d[1] = d[2] = d[3] = v; }
+__device__ __forceinline__ void cpy4(float (&d)[4], const float (&s)[4]) {
+    d[0] = s[0]; d[1] = s[1]; d[2] = s[2]; d[3] = s[3];
+}
+
+// Lateral face values of the own quad from the staged alpha (slot 3):
+// cx[j] is the face between cells j - 1 and j of the quad (j = 0..4, cell -1
+// and cell 4 being the neighbours left and right of it); cyp / cym the +y / -y
+// faces of each cell.  Shared faces are evaluated once: face(a, b) and
+// face(b, a) are the same number.
+__device__ __forceinline__ void quad_faces(const unsigned char* st, int hb, const float (&ac)[4], float kx, float ky,
+                                           float (&cx)[5], float (&cyp)[4], float (&cym)[4]) {
+    float aym[4], ayp[4];
+    ld4(st, sl(3), hb - HB, aym);
+    ld4(st, sl(3), hb + HB, ayp);
+    cx[0] = face(ac[0], lds1(st, sl(3), hb - 1), kx);
+#pragma unroll
+    for (int j = 1; j < 4; ++j) cx[j] = face(ac[j - 1], ac[j], kx);
+    cx[4] = face(ac[3], lds1(st, sl(3), hb + 4), kx);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        cyp[j] = face(ac[j], ayp[j], ky);
+        cym[j] = face(ac[j], aym[j], ky);
+    }
+}
+
+// CG step scalars of one iteration pass.
+struct Step {
+    float a, bt;
+    bool first;
+    // s_i = ws_i + beta ss_{i-1} and u_{i+1} = u_i - alpha s_i at one cell; every
+    // thread that needs u_{i+1} at a cell evaluates exactly these two FMAs.
+    __device__ __forceinline__ float sdir(float w, float s) const { return first ? w : fmaf(bt, s, w); }
+    __device__ __forceinline__ float next(float u, float sn) const { return fmaf(-a, sn, u); }
+};
+
+// u_{i+1} (f), s_i (sn) and u_i (u) at the quad at halo-box index h of a stage.
+__device__ __forceinline__ void field4(const unsigned char* st, int h, const Step& S, float (&f)[4], float (&sn)[4],
+                                       float (&u)[4]) {
+    float w[4], s[4] = {0.f, 0.f, 0.f, 0.f};
+    ld4(st, sl(0), h, u);
+    ld4(st, sl(1), h, w);
+    if (!S.first) ld4(st, sl(2), h, s);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        sn[j] = S.sdir(w[j], s[j]);
+        f[j] = S.next(u[j], sn[j]);
+    }
+}
+__device__ __forceinline__ void field4(const unsigned char* st, int h, const Step& S, float (&f)[4]) {
+    float sn[4], u[4];
+    field4(st, h, S, f, sn, u);
+}
+__device__ __forceinline__ float field1(const unsigned char* st, int h, const Step& S) {
+    const float sv = S.first ? 0.f : lds1(st, sl(2), h);
+    return S.next(lds1(st, sl(0), h), S.sdir(lds1(st, sl(1), h), sv));
+}
+
+// ---- one CG iteration: u_{i+1}, ws_{i+1} = M^{-1} A u_{i+1}, ss_i, p_i, delta
+struct IterBody {
+    const Common& C;
+    const Step& S;
+    int cur;
+    Acc<3>& acc;
+    float fm[4], am[4];                    // plane k-1: u_{i+1}, alpha
+    float fc[4], sc[4], uc[4], ac[4];      // plane k: u_{i+1}, s_i, u_i, alpha
+    float fp[4], sp[4], up[4], ap[4];      // plane k+1
+    float czm[4], czp[4];                  // -z / +z faces of the own cells
+    __device__ IterBody(const Common& c, const Step& s, int cu, Acc<3>& a) : C(c), S(s), cur(cu), acc(a) {}
+    __device__ __forceinline__ void reset() { set4(fm, 0.f); set4(am, 0.f); set4(czm, 0.f); }
+    __device__ __forceinline__ void below(const unsigned char* st, int hb) {
+        field4(st, hb, S, fm);
+        ld4(st, sl(3), hb, am);
+    }
+    __device__ __forceinline__ void own(const unsigned char* st, int hb, bool has_below) {
+        field4(st, hb, S, fc, sc, uc);
+        ld4(st, sl(3), hb, ac);
+        if (has_below) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) czm[j] = face(ac[j], am[j], C.kz);
+        }
+    }
+    __device__ __forceinline__ void above(const unsigned char* st, int hb) {
+        field4(st, hb, S, fp, sp, up);
+        ld4(st, sl(3), hb, ap);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) czp[j] = face(ac[j], ap[j], C.kz);
+    }
+    __device__ __forceinline__ void top() {
+        cpy4(fp, fc);
+        set4(sp, 0.f); set4(up, 0.f); set4(ap, 0.f); set4(czp, 0.f);
+    }
+    __device__ __forceinline__ void plane(int k, unsigned c, bool valid, const unsigned char* st,
+                                          const unsigned char*, int hb, int ob) {
+        const Geo& g = C.g;
+        float fym[4], fyp[4], cx[5], cyp[4], cym[4];
+        field4(st, hb - HB, S, fym);
+        field4(st, hb + HB, S, fyp);
+        const float fxl = field1(st, hb - 1, S), fxr = field1(st, hb + 4, S);
+        quad_faces(st, hb, ac, C.kx, C.ky, cx, cyp, cym);
+        float pp[4] = {0.f, 0.f, 0.f, 0.f}, dd[4];
+        if (!S.first) ld4(st, sl(4), ob, pp);
+        ld4(st, sl(5), ob, dd);
+        const float rob = k + 1 == g.nz ? C.robin : 0.f;
+        float wn[4], pn[4], dl[4], s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float f = fc[j];
+            const float fxm = j > 0 ? fc[j - 1] : fxl, fxp = j < 3 ? fc[j + 1] : fxr;
+            const float fzmv = k > 0 ? fm[j] : f;
+            const float cxp = cx[j + 1], cxm = cx[j];
+            const float d = diag(cxp, cxm, cyp[j], cym[j], czp[j], czm[j], rob);
+            const float Au = f + cxp * (f - fxp) + cxm * (f - fxm) + cyp[j] * (f - fyp[j]) + cym[j] * (f - fym[j]) +
+                             czp[j] * (f - fp[j]) + czm[j] * (f - fzmv) + rob * f;
+            wn[j] = rcp_approx(d) * Au;
+            pn[j] = S.first ? uc[j] : fmaf(S.bt, pp[j], uc[j]);
+            dl[j] = fmaf(S.a, pn[j], dd[j]);
+            const float r = d * f;
+            s0 += r * f;
+            s1 += Au * f;
+            s2 += r * r;
+        }
+        if (valid) {
+            stg4(C.v.p + c, pn);
+            stg4(C.v.delta + c, dl);
+            stg4(C.v.u[cur ^ 1] + c, fc);
+            stg4(C.v.ws[cur ^ 1] + c, wn);
+            stg4(C.v.ss[cur ^ 1] + c, sc);
+            acc.add(0, s0);
+            acc.add(1, s1);
+            acc.add(2, s2);
+        }
+    }
+    __device__ __forceinline__ void shift() {
+        cpy4(fm, fc); cpy4(czm, czp);
+        cpy4(fc, fp); cpy4(sc, sp); cpy4(uc, up); cpy4(ac, ap);
+    }
+};
+
+// sh + sl += cf ((hc + lc) - (hq + lq)), error-free up to the final rounding
+// (TwoSum of the high parts, TwoProd through fmaf).  Zero faces add nothing.
+__device__ __forceinline__ void exact_term(float cf, float hc, float lc, float hq, float lq, float& sh, float& sl) {
+    if (cf == 0.f) return;
+    float dh, dhe;
+    two_sum(hc, -hq, dh, dhe);
+    const float dl = (lc - lq) + dhe;
+    const float pr = cf * dh;
+    const float pe = fmaf(cf, dh, -pr) + cf * dl;
+    float t, te;
+    two_sum(sh, pr, t, te);
+    sh = t;
+    sl += te + pe;
+}
+// sh + sl += rob (hc + lc), the Robin sink, the same way.
+__device__ __forceinline__ void exact_sink(float rob, float hc, float lc, float& sh, float& sl) {
+    if (rob == 0.f) return;
+    const float pr = rob * hc;
+    const float pe = fmaf(rob, hc, -pr) + rob * lc;
+    float t, te;
+    two_sum(sh, pr, t, te);
+    sh = t;
+    sl += te + pe;
+}
+
+// ---- init 1: r0 = e - (A - I) x0 exactly-ish, u0 = M^{-1} r0, delta = 0
+template <class RhsFn>
+struct Init1Body {
+    const Common& C;
+    RhsFn& rhs;
+    Acc<3>& acc;
+    float hm[4], lm[4], am[4];
+    float hc[4], lc[4], ac[4];
+    float hp[4], lp[4], ap[4];
+    float czm[4], czp[4];
+    __device__ Init1Body(const Common& c, RhsFn& r, Acc<3>& a) : C(c), rhs(r), acc(a) {}
+    __device__ __forceinline__ void reset() { set4(hm, 0.f); set4(lm, 0.f); set4(am, 0.f); set4(czm, 0.f); }
+    __device__ __forceinline__ void below(const unsigned char* st, int hb) {
+        ld4(st, sl(0), hb, hm);
+        ld4(st, sl(1), hb, lm);
+        ld4(st, sl(3), hb, am);
+    }
+    __device__ __forceinline__ void own(const unsigned char* st, int hb, bool has_below) {
+        ld4(st, sl(0), hb, hc);
+        ld4(st, sl(1), hb, lc);
+        ld4(st, sl(3), hb, ac);
+        if (has_below) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) czm[j] = face(ac[j], am[j], C.kz);
+        }
+    }
+    __device__ __forceinline__ void above(const unsigned char* st, int hb) {
+        ld4(st, sl(0), hb, hp);
+        ld4(st, sl(1), hb, lp);
+        ld4(st, sl(3), hb, ap);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) czp[j] = face(ac[j], ap[j], C.kz);
+    }
+    __device__ __forceinline__ void top() { set4(hp, 0.f); set4(lp, 0.f); set4(ap, 0.f); set4(czp, 0.f); }
+    __device__ __forceinline__ void plane(int k, unsigned c, bool valid, const unsigned char* st,
+                                          const unsigned char*, int hb, int) {
+        if (!valid) return;
+        const Geo& g = C.g;
+        float hym[4], lym[4], hyp[4], lyp[4], cx[5], cyp[4], cym[4];
+        ld4(st, sl(0), hb - HB, hym);
+        ld4(st, sl(1), hb - HB, lym);
+        ld4(st, sl(0), hb + HB, hyp);
+        ld4(st, sl(1), hb + HB, lyp);
+        const float hxl = lds1(st, sl(0), hb - 1), lxl = lds1(st, sl(1), hb - 1);
+        const float hxr = lds1(st, sl(0), hb + 4), lxr = lds1(st, sl(1), hb + 4);
+        quad_faces(st, hb, ac, C.kx, C.ky, cx, cyp, cym);
+        const float rob = k + 1 == g.nz ? C.robin : 0.f;
+        float u[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float sh = 0.f, sx = 0.f;
+            exact_term(cx[j + 1], hc[j], lc[j], j < 3 ? hc[j + 1] : hxr, j < 3 ? lc[j + 1] : lxr, sh, sx);
+            exact_term(cx[j], hc[j], lc[j], j > 0 ? hc[j - 1] : hxl, j > 0 ? lc[j - 1] : lxl, sh, sx);
+            exact_term(cyp[j], hc[j], lc[j], hyp[j], lyp[j], sh, sx);
+            exact_term(cym[j], hc[j], lc[j], hym[j], lym[j], sh, sx);
+            exact_term(czp[j], hc[j], lc[j], hp[j], lp[j], sh, sx);
+            exact_term(czm[j], hc[j], lc[j], hm[j], lm[j], sh, sx);
+            exact_sink(rob, hc[j], lc[j], sh, sx);
+            const float e = rhs(c + j, k);
+            const float r = (e - sh) - sx;
+            u[j] = rcp_approx(diag(cx[j + 1], cx[j], cyp[j], cym[j], czp[j], czm[j], rob)) * r;
+            const float b = (hc[j] + lc[j]) + e;
+            acc.add(0, b * b);
+            acc.add(1, r * u[j]);
+            acc.add(2, r * r);
+        }
+        const float z[4] = {0.f, 0.f, 0.f, 0.f};
+        stg4(C.v.u[0] + c, u);
+        stg4(C.v.delta + c, z);
+    }
+    __device__ __forceinline__ void shift() {
+        cpy4(hm, hc); cpy4(lm, lc); cpy4(czm, czp);
+        cpy4(hc, hp); cpy4(lc, lp); cpy4(ac, ap);
+    }
+};
+
+// ---- init 2: ws0 = M^{-1} A u0 ; (A u0, u0)
+struct Init2Body {
+    const Common& C;
+    Acc<1>& acc;
+    float um[4], am[4], uc[4], ac[4], up[4], ap[4], czm[4], czp[4];
+    __device__ Init2Body(const Common& c, Acc<1>& a) : C(c), acc(a) {}
+    __device__ __forceinline__ void reset() { set4(um, 0.f); set4(am, 0.f); set4(czm, 0.f); }
+    __device__ __forceinline__ void below(const unsigned char* st, int hb) {
+        ld4(st, sl(0), hb, um);
+        ld4(st, sl(3), hb, am);
+    }
+    __device__ __forceinline__ void own(const unsigned char* st, int hb, bool has_below) {
+        ld4(st, sl(0), hb, uc);
+        ld4(st, sl(3), hb, ac);
+        if (has_below) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) czm[j] = face(ac[j], am[j], C.kz);
+        }
+    }
+    __device__ __forceinline__ void above(const unsigned char* st, int hb) {
+        ld4(st, sl(0), hb, up);
+        ld4(st, sl(3), hb, ap);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) czp[j] = face(ac[j], ap[j], C.kz);
+    }
+    __device__ __forceinline__ void top() { set4(up, 0.f); set4(ap, 0.f); set4(czp, 0.f); }
+    __device__ __forceinline__ void plane(int k, unsigned c, bool valid, const unsigned char* st,
+                                          const unsigned char*, int hb, int) {
+        if (!valid) return;
+        float uym[4], uyp[4], cx[5], cyp[4], cym[4], w[4];
+        ld4(st, sl(0), hb - HB, uym);
+        ld4(st, sl(0), hb + HB, uyp);
+        const float uxl = lds1(st, sl(0), hb - 1), uxr = lds1(st, sl(0), hb + 4);
+        quad_faces(st, hb, ac, C.kx, C.ky, cx, cyp, cym);
+        const float rob = k + 1 == C.g.nz ? C.robin : 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float f = uc[j];
+            const float fxm = j > 0 ? uc[j - 1] : uxl, fxp = j < 3 ? uc[j + 1] : uxr;
+            const float cxp = cx[j + 1], cxm = cx[j];
+            const float Au = f + cxp * (f - fxp) + cxm * (f - fxm) + cyp[j] * (f - uyp[j]) + cym[j] * (f - uym[j]) +
+                             czp[j] * (f - up[j]) + czm[j] * (f - um[j]) + rob * f;
+            w[j] = rcp_approx(diag(cxp, cxm, cyp[j], cym[j], czp[j], czm[j], rob)) * Au;
+            acc.add(0, Au * f);
+        }
+        stg4(C.v.ws[0] + c, w);
+    }
+    __device__ __forceinline__ void shift() {
+        cpy4(um, uc); cpy4(czm, czp);
+        cpy4(uc, up); cpy4(ac, ap);
+    }
+};
+
+// ---- gradient of one step (Eq. grad_assembly) at the own cells:
+// g_c -= sum_f w_f h^2 (mu_c - mu_q)(T_c - T_q), h = alpha_q / (alpha_c + alpha_q),
+// with T and mu as compensated pairs, faces in the order +x, -x, +y, -y, +z, -z.
+// A cell beyond a zero-flux wall stages alpha_q = 0, so h = 0 and it adds
+// nothing.  Plane values are read from the stages when needed (the stage of
+// plane k + 1 is held while plane k is worked on); only the -z terms of the
+// next plane are carried in registers.
+struct GradBody {
+    double* grad;
+    float wx, wy, wz;
+    int nz;
+    float bth[4], btl[4], bmh[4], bml[4], bac[4];   // plane k0 - 1 (segment start only)
+    float zdn[4], zdn1[4];                          // -z terms of plane k and of plane k + 1
+    __device__ __forceinline__ static float term(float a0, float mc, float mcl, float tc, float tcl, float aq,
+                                                 float mq, float mql, float tq, float tql, float w) {
+        const float h = aq * rcp_approx(a0 + aq);
+        const float dm = (mc - mq) + (mcl - mql);
+        const float dT = (tc - tq) + (tcl - tql);
+        return w * h * h * dm * dT;
+    }
+    __device__ __forceinline__ static void load(const unsigned char* st, int hb, float (&t)[4], float (&tlo)[4],
+                                                float (&m)[4], float (&mlo)[4], float (&a)[4]) {
+        ld4(st, sl(0), hb, t);
+        ld4(st, sl(1), hb, tlo);
+        ld4(st, sl(2), hb, m);
+        ld4(st, sl(4), hb, mlo);
+        ld4(st, sl(3), hb, a);
+    }
+    __device__ __forceinline__ void reset() {}
+    __device__ __forceinline__ void below(const unsigned char* st, int hb) { load(st, hb, bth, btl, bmh, bml, bac); }
+    __device__ __forceinline__ void own(const unsigned char* st, int hb, bool has_below) {
+        if (!has_below) return;
+        float th[4], tl[4], mh[4], ml[4], ac[4];
+        load(st, hb, th, tl, mh, ml, ac);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            zdn[j] = term(ac[j], mh[j], ml[j], th[j], tl[j], bac[j], bmh[j], bml[j], bth[j], btl[j], wz);
+    }
+    __device__ __forceinline__ void above(const unsigned char*, int) {}
+    __device__ __forceinline__ void top() {}
+    __device__ __forceinline__ void plane(int k, unsigned c, bool valid, const unsigned char* st,
+                                          const unsigned char* st1, int hb, int) {
+        if (!valid) return;
+        float th[4], tl[4], mh[4], ml[4], ac[4];
+        load(st, hb, th, tl, mh, ml, ac);
+        float s[4] = {0.f, 0.f, 0.f, 0.f};
+        {   // +x, -x
+            const int hr = hb + 4, hl = hb - 1;
+            const float tr = lds1(st, sl(0), hr), trl = lds1(st, sl(1), hr), mr = lds1(st, sl(2), hr),
+                        mrl = lds1(st, sl(4), hr), ar = lds1(st, sl(3), hr);
+            const float tq = lds1(st, sl(0), hl), tql = lds1(st, sl(1), hl), mq = lds1(st, sl(2), hl),
+                        mql = lds1(st, sl(4), hl), aq = lds1(st, sl(3), hl);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                s[j] += j < 3 ? term(ac[j], mh[j], ml[j], th[j], tl[j], ac[j + 1], mh[j + 1], ml[j + 1], th[j + 1],
+                                     tl[j + 1], wx)
+                              : term(ac[j], mh[j], ml[j], th[j], tl[j], ar, mr, mrl, tr, trl, wx);
+                s[j] += j > 0 ? term(ac[j], mh[j], ml[j], th[j], tl[j], ac[j - 1], mh[j - 1], ml[j - 1], th[j - 1],
+                                     tl[j - 1], wx)
+                              : term(ac[j], mh[j], ml[j], th[j], tl[j], aq, mq, mql, tq, tql, wx);
+            }
+        }
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {   // +y, then -y
+            float t[4], tlo[4], m[4], mlo[4], a[4];
+            load(st, sd == 0 ? hb + HB : hb - HB, t, tlo, m, mlo, a);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) s[j] += term(ac[j], mh[j], ml[j], th[j], tl[j], a[j], m[j], mlo[j], t[j], tlo[j], wy);
+        }
+        if (st1) {   // +z, and the -z terms of plane k + 1
+            float t[4], tlo[4], m[4], mlo[4], a[4];
+            load(st1, hb, t, tlo, m, mlo, a);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                s[j] += term(ac[j], mh[j], ml[j], th[j], tl[j], a[j], m[j], mlo[j], t[j], tlo[j], wz);
+                zdn1[j] = term(a[j], m[j], mlo[j], t[j], tlo[j], ac[j], mh[j], ml[j], th[j], tl[j], wz);
+            }
+        }
+        double gd[4];
+        *reinterpret_cast<double2*>(&gd[0]) = *reinterpret_cast<const double2*>(grad + c);
+        *reinterpret_cast<double2*>(&gd[2]) = *reinterpret_cast<const double2*>(grad + c + 2);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (k > 0) s[j] += zdn[j];
+            gd[j] -= (double)s[j];
+        }
+        *reinterpret_cast<double2*>(grad + c) = *reinterpret_cast<const double2*>(&gd[0]);
+        *reinterpret_cast<double2*>(grad + c + 2) = *reinterpret_cast<const double2*>(&gd[2]);
+    }
+    __device__ __forceinline__ void shift() { cpy4(zdn, zdn1); }
+};
+
+// One staged pass: the copy thread streams the planes, the compute threads
+// run Body over them.  Returns false (CTA-uniform, with the error recorded and
+// every copy landed) if a wait timed out anywhere in the CTA.
+template <class Body>
+__device__ bool staged(const Common& C, Ring& R, const PassIn& in, Body& B) {
+    bool ok = true;
+    if (threadIdx.x < NCT) ok = consume(C.g, R, B);
+    else if (threadIdx.x == NCT) ok = produce(C, R, in);
+    if (__syncthreads_or(ok ? 0 : 1)) {
+        if (threadIdx.x == NCT) drain(R);
+        if (threadIdx.x == 0) atomicCAS(&C.ctl->err, kDevOk, kDevTimeout);
+        return false;
+    }
+    return true;
+}
+
+// Slab plane of a state (see Common::slab); false (with the error recorded)
+// if the pointer is not a state of the slab.  Uniform over the grid.
+__device__ __forceinline__ bool slab_plane(const Common& C, const float* p, unsigned* z) {
+    const long long off = (long long)(p - C.slab);
+    const long long S = C.g.S;
+    if (off < 0 || off % S != 0 || off / S + 2LL * C.g.nz > (long long)C.slab_planes) {
+        if (threadIdx.x == 0) atomicCAS(&C.ctl->err, kDevOk, kDevBadState);
+        return false;
+    }
+    *z = (unsigned)(off / S);
+    return true;
+}
+
+// One iteration pass with plain global loads (grids TMA cannot stage).
+__device__ void plain_pass(const Common& C, int cur, const Step& S, Acc<3>& acc) {
+    const Geo& g = C.g;
+    const float* __restrict__ ui = C.v.u[cur];
+    const float* __restrict__ wi = C.v.ws[cur];
+    const float* __restrict__ si = C.v.ss[cur];
+    float* __restrict__ uo = C.v.u[cur ^ 1];
+    float* __restrict__ wo = C.v.ws[cur ^ 1];
+    float* __restrict__ so = C.v.ss[cur ^ 1];
+    auto fld = [&](unsigned q) { return S.next(ui[q], S.sdir(wi[q], S.first ? 0.f : si[q])); };
+    for_cells(g, [&](int k, unsigned c, int x, int y) {
+        const Nb n = neighbours(g, c, x, y, k);
+        const float ac = C.alpha[c];
+        float cf[6];
+        cell_faces(C, n, ac, cf);
+        const float rob = k + 1 == g.nz ? C.robin : 0.f;
+        const float d = diag(cf[0], cf[1], cf[2], cf[3], cf[4], cf[5], rob);
+        const float uold = ui[c];
+        const float sn = S.sdir(wi[c], S.first ? 0.f : si[c]);
+        const float f = S.next(uold, sn);
+        float fq[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) fq[i] = (n.m >> i & 1u) ? fld(n.q[i]) : 0.f;
+        const float Au = f + cf[0] * (f - fq[0]) + cf[1] * (f - fq[1]) + cf[2] * (f - fq[2]) +
+                         cf[3] * (f - fq[3]) + cf[4] * (f - fq[4]) + cf[5] * (f - fq[5]) + rob * f;
+        const float pn = S.first ? uold : fmaf(S.bt, C.v.p[c], uold);
+        C.v.p[c] = pn;
+        C.v.delta[c] = fmaf(S.a, pn, C.v.delta[c]);
+        uo[c] = f;
+        wo[c] = rcp_approx(d) * Au;
+        so[c] = sn;
+        const float r = d * f;
+        acc.add(0, r * f);
+        acc.add(1, Au * f);
+        acc.add(2, r * r);
+    });
 }
 
 // --------------------------------------------------------------- solve
@@ -568,69 +1012,42 @@ __device__ __forceinline__ float diag(const Faces& f, float czp, float czm, floa
 // formed with error-free products and sums (TwoProd through fmaf, TwoSum), so
 // it is accurate relative to itself however small it is against x0; the CG
 // then runs in FP32 on the increment.  On return delta holds the increment.
-// Returns false if a barrier failed.
-template <class RhsFn>
-__device__ bool solve(const Common& C, Sync& sy, float (*sm)[BY][BX], TmaRing* ring,
-                      const float* __restrict__ x0, const float* __restrict__ x0lo, RhsFn rhs, int* it_out,
-                      double* rel_out) {
+// Returns false if a barrier or a stage wait failed.
+template <bool kTma, class RhsFn>
+__device__ bool solve(const Common& C, Sync& sy, Ring& ring, const float* __restrict__ x0,
+                      const float* __restrict__ x0lo, RhsFn rhs, int* it_out, double* rel_out) {
     const Geo& g = C.g;
     // ---- init 1: r0 = e - (A - I) x0, u0 = M^{-1} r0 ; bb, (r0,u0), (r0,r0)
-    float acc3[3] = {0.f, 0.f, 0.f};
-    const unsigned wrap_y = (unsigned)(g.ny - 1) * g.nx;
-    for_segments(g, [&](int tile, int k0, int k1) {
-        float czm = 0.f;
-        march(g, tile, k0, k1, sm,
-              [&](unsigned q, bool) { return x0[q]; },
-              [&](int k, unsigned c, int x, int y, bool valid, float fc, float fxm, float fxp, float fym,
-                  float fyp, float fzm, float fzp) {
-                  if (!valid) return;
-                  const float ac = C.alpha[c];
-                  if (k == k0 && k > 0) czm = face(ac, C.alpha[c - g.S], C.kz);
-                  const Faces f = lateral_faces(g, C.alpha, c, x, y, ac, C.kx, C.ky);
-                  const float czp = k + 1 < g.nz ? face(ac, C.alpha[c + g.S], C.kz) : 0.f;
-                  const float rob = k + 1 == g.nz ? C.robin : 0.f;
-                  const float lc = x0lo[c];
-                  float sh = 0.f, sl = 0.f;
-                  // sh + sl += cf * ((fc + lc) - (hq + lq)), error-free up to the final rounding
-                  auto term = [&](float cf, float hq, unsigned q) {
-                      if (cf == 0.f) return;
-                      float dh, dhe;
-                      two_sum(fc, -hq, dh, dhe);
-                      const float dl = (lc - x0lo[q]) + dhe;
-                      const float pr = cf * dh;
-                      const float pe = fmaf(cf, dh, -pr) + cf * dl;
-                      float t, te;
-                      two_sum(sh, pr, t, te);
-                      sh = t;
-                      sl += te + pe;
-                  };
-                  term(f.xp, fxp, x + 1 < g.nx ? c + 1 : c + 1 - g.nx);
-                  term(f.xm, fxm, x > 0 ? c - 1 : c + g.nx - 1);
-                  term(f.yp, fyp, y + 1 < g.ny ? c + g.nx : c - wrap_y);
-                  term(f.ym, fym, y > 0 ? c - g.nx : c + wrap_y);
-                  term(czp, fzp, c + g.S);
-                  term(czm, fzm, c - g.S);
-                  if (rob != 0.f) {
-                      const float pr = rob * fc;
-                      const float pe = fmaf(rob, fc, -pr) + rob * lc;
-                      float t, te;
-                      two_sum(sh, pr, t, te);
-                      sh = t;
-                      sl += te + pe;
-                  }
-                  const float e = rhs(c, k);
-                  const float r = (e - sh) - sl;
-                  const float dinv = rcp_approx(diag(f, czp, czm, rob));
-                  const float u = dinv * r;
-                  C.v.u[0][c] = u;
-                  C.v.delta[c] = 0.f;
-                  const float b = (fc + lc) + e;
-                  acc3[0] += b * b;
-                  acc3[1] += r * u;
-                  acc3[2] += r * r;
-                  czm = czp;
-              });
-    });
+    Acc<3> acc3;
+    if constexpr (kTma) {
+        PassIn in{kInit1, 0, false, 0u, 0u};
+        if (!slab_plane(C, x0, &in.zx)) return false;
+        Init1Body<RhsFn> B(C, rhs, acc3);
+        if (!staged(C, ring, in, B)) return false;
+    } else {
+        for_cells(g, [&](int k, unsigned c, int x, int y) {
+            const Nb n = neighbours(g, c, x, y, k);
+            const float ac = C.alpha[c];
+            float cf[6];
+            cell_faces(C, n, ac, cf);
+            const float rob = k + 1 == g.nz ? C.robin : 0.f;
+            const float fc = x0[c], lc = x0lo[c];
+            float sh = 0.f, sx = 0.f;
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+                if (n.m >> i & 1u) exact_term(cf[i], fc, lc, x0[n.q[i]], x0lo[n.q[i]], sh, sx);
+            exact_sink(rob, fc, lc, sh, sx);
+            const float e = rhs(c, k);
+            const float r = (e - sh) - sx;
+            const float u = rcp_approx(diag(cf[0], cf[1], cf[2], cf[3], cf[4], cf[5], rob)) * r;
+            C.v.u[0][c] = u;
+            C.v.delta[c] = 0.f;
+            const float b = (fc + lc) + e;
+            acc3.add(0, b * b);
+            acc3.add(1, r * u);
+            acc3.add(2, r * r);
+        });
+    }
     // CG scalars live in thread 0 (FP64); the FP32 step lengths and the stop
     // decision reach the other threads through shared memory.
     __shared__ float s_a, s_b;
@@ -644,28 +1061,29 @@ __device__ bool solve(const Common& C, Sync& sy, float (*sm)[BY][BX], TmaRing* r
     __syncthreads();
     if (s_go) {
         // ---- init 2: ws0 = M^{-1} A u0 ; (A u0, u0)
-        float acc1[1] = {0.f};
-        for_segments(g, [&](int tile, int k0, int k1) {
-            float czm = 0.f;
-            const float* u0 = C.v.u[0];
-            march(g, tile, k0, k1, sm,
-                  [&](unsigned q, bool) { return u0[q]; },
-                  [&](int k, unsigned c, int x, int y, bool valid, float fc, float fxm, float fxp, float fym,
-                      float fyp, float fzm, float fzp) {
-                      if (!valid) return;
-                      const float ac = C.alpha[c];
-                      if (k == k0 && k > 0) czm = face(ac, C.alpha[c - g.S], C.kz);
-                      const Faces f = lateral_faces(g, C.alpha, c, x, y, ac, C.kx, C.ky);
-                      const float czp = k + 1 < g.nz ? face(ac, C.alpha[c + g.S], C.kz) : 0.f;
-                      const float rob = k + 1 == g.nz ? C.robin : 0.f;
-                      const float Au = fc + f.xp * (fc - fxp) + f.xm * (fc - fxm) + f.yp * (fc - fyp) +
-                                       f.ym * (fc - fym) + czp * (fc - fzp) + czm * (fc - fzm) + rob * fc;
-                      const float dinv = rcp_approx(diag(f, czp, czm, rob));
-                      C.v.ws[0][c] = dinv * Au;
-                      acc1[0] += Au * fc;
-                      czm = czp;
-                  });
-        });
+        Acc<1> acc1;
+        if constexpr (kTma) {
+            const PassIn in{kInit2, 0, false, 0u, 0u};
+            Init2Body B(C, acc1);
+            if (!staged(C, ring, in, B)) return false;
+        } else {
+            const float* __restrict__ u0 = C.v.u[0];
+            for_cells(g, [&](int k, unsigned c, int x, int y) {
+                const Nb n = neighbours(g, c, x, y, k);
+                const float ac = C.alpha[c];
+                float cf[6];
+                cell_faces(C, n, ac, cf);
+                const float rob = k + 1 == g.nz ? C.robin : 0.f;
+                const float f = u0[c];
+                float fq[6];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) fq[i] = (n.m >> i & 1u) ? u0[n.q[i]] : 0.f;
+                const float Au = f + cf[0] * (f - fq[0]) + cf[1] * (f - fq[1]) + cf[2] * (f - fq[2]) +
+                                 cf[3] * (f - fq[3]) + cf[4] * (f - fq[4]) + cf[5] * (f - fq[5]) + rob * f;
+                C.v.ws[0][c] = rcp_approx(diag(cf[0], cf[1], cf[2], cf[3], cf[4], cf[5], rob)) * Au;
+                acc1.add(0, Au * f);
+            });
+        }
         double t1[1] = {0.0};
         if (!grid_sum<1>(sy, acc1, t1)) return false;
         double alpha = 0.0, beta = 0.0;
@@ -678,55 +1096,18 @@ __device__ bool solve(const Common& C, Sync& sy, float (*sm)[BY][BX], TmaRing* r
         int cur = 0;
         // ---- iterations: one pass, one reduction each
         while (true) {
-            const float a = s_a, bt = s_b;
-            const bool first = it == 0;
-            const float* __restrict__ ui = C.v.u[cur];
-            const float* __restrict__ wi = C.v.ws[cur];
-            const float* __restrict__ si = C.v.ss[cur];
-            float* __restrict__ uo = C.v.u[cur ^ 1];
-            float* __restrict__ wo = C.v.ws[cur ^ 1];
-            float* __restrict__ so = C.v.ss[cur ^ 1];
-            float acc[3] = {0.f, 0.f, 0.f};
-            if (C.maps) {
-                if (!iter_pass_tma(C, *ring, sm, cur, a, bt, first, acc)) {
-                    if (threadIdx.x == 0) atomicCAS(&C.ctl->err, kDevOk, kDevTimeout);
-                    return false;
-                }
-            } else
-            for_segments(g, [&](int tile, int k0, int k1) {
-                float czm = 0.f;
-                march(g, tile, k0, k1, sm,
-                      [&](unsigned q, bool) {
-                          const float sn = first ? wi[q] : wi[q] + bt * si[q];
-                          return ui[q] - a * sn;
-                      },
-                      [&](int k, unsigned c, int x, int y, bool valid, float fc, float fxm, float fxp,
-                          float fym, float fyp, float fzm, float fzp) {
-                          if (!valid) return;
-                          const float ac = C.alpha[c];
-                          if (k == k0 && k > 0) czm = face(ac, C.alpha[c - g.S], C.kz);
-                          const Faces f = lateral_faces(g, C.alpha, c, x, y, ac, C.kx, C.ky);
-                          const float czp = k + 1 < g.nz ? face(ac, C.alpha[c + g.S], C.kz) : 0.f;
-                          const float rob = k + 1 == g.nz ? C.robin : 0.f;
-                          const float d = diag(f, czp, czm, rob);
-                          const float Au = fc + f.xp * (fc - fxp) + f.xm * (fc - fxm) + f.yp * (fc - fyp) +
-                                           f.ym * (fc - fym) + czp * (fc - fzp) + czm * (fc - fzm) + rob * fc;
-                          const float wn = rcp_approx(d) * Au;
-                          const float uold = ui[c];
-                          const float sn = first ? wi[c] : wi[c] + bt * si[c];
-                          const float pn = first ? uold : uold + bt * C.v.p[c];
-                          C.v.p[c] = pn;
-                          C.v.delta[c] += a * pn;
-                          uo[c] = fc;
-                          wo[c] = wn;
-                          so[c] = sn;
-                          const float r = d * fc;
-                          acc[0] += r * fc;
-                          acc[1] += Au * fc;
-                          acc[2] += r * r;
-                          czm = czp;
-                      });
-            });
+            Step S;
+            S.a = s_a;
+            S.bt = s_b;
+            S.first = it == 0;
+            Acc<3> acc;
+            if constexpr (kTma) {
+                const PassIn in{kIter, cur, S.first, 0u, 0u};
+                IterBody B(C, S, cur, acc);
+                if (!staged(C, ring, in, B)) return false;
+            } else {
+                plain_pass(C, cur, S, acc);
+            }
             double t[3] = {0.0, 0.0, 0.0};
             if (!grid_sum<3>(sy, acc, t)) return false;
             ++it;
@@ -763,26 +1144,44 @@ __device__ __forceinline__ Sync make_sync(DevCtl* ctl, double* partials) {
     return s;
 }
 
-// ------------------------------------------------------------- forward
-__global__ void __launch_bounds__(NT, 1) forward_tiled(FwdTiled a) {
-    __shared__ float sm[3][BY][BX];
-    extern __shared__ unsigned char dyn_smem[];
-    __shared__ __align__(8) unsigned long long s_bars[NS];
-    TmaRing ring;
-    ring.base = (unsigned char*)(((uintptr_t)dyn_smem + 127) & ~(uintptr_t)127);
-    ring.bar0 = smem_u32(&s_bars[0]);
-    ring.issue_s = 0;
-    ring.wait_s = 0;
-    ring.wait_ph = 0;
-    ring.in_flight = 0;
-    if (a.c.maps) {
-        if (threadIdx.x == 0) {
-            for (int i = 0; i < NS; ++i) mbar_init(ring.bar0 + 8u * i, 1u);
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+// y = x + d as compensated pairs (hi in [0, N), lo in [N, 2N)), by every
+// thread of the grid; quads when N % 4 == 0.  Ends with the proxy fence that
+// orders these stores before later TMA reads of y.
+__device__ void add_state(const float* __restrict__ x, const float* __restrict__ d, float* __restrict__ y,
+                          unsigned N) {
+    const unsigned stride = gridDim.x * NT, t0 = blockIdx.x * NT + threadIdx.x;
+    if ((N & 3u) == 0) {
+        const unsigned N4 = N >> 2;
+        const float4* xh = reinterpret_cast<const float4*>(x);
+        const float4* xl = reinterpret_cast<const float4*>(x + N);
+        const float4* d4 = reinterpret_cast<const float4*>(d);
+        float4* yh = reinterpret_cast<float4*>(y);
+        float4* yl = reinterpret_cast<float4*>(y + N);
+#pragma unroll 2
+        for (unsigned i = t0; i < N4; i += stride) {
+            const float4 h = xh[i], l = xl[i], e = d4[i];
+            float4 oh, ol;
+            add_pair(h.x, l.x, e.x, oh.x, ol.x);
+            add_pair(h.y, l.y, e.y, oh.y, ol.y);
+            add_pair(h.z, l.z, e.z, oh.z, ol.z);
+            add_pair(h.w, l.w, e.w, oh.w, ol.w);
+            yh[i] = oh;
+            yl[i] = ol;
         }
-        __syncthreads();
+    } else {
+        for (unsigned c = t0; c < N; c += stride) add_pair(x[c], x[N + c], d[c], y[c], y[N + c]);
     }
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// ------------------------------------------------------------- forward
+// kTma: iterations and stencil passes staged through TMA (a.c.maps set);
+// otherwise plain global loads.
+template <bool kTma>
+__global__ void __launch_bounds__(NT, 1) forward_tiled(FwdTiled a) {
+    extern __shared__ unsigned char dyn_smem[];
+    __shared__ __align__(8) unsigned long long s_full[NS], s_empty[NS];
+    Ring ring = make_ring(dyn_smem, s_full, s_empty, kTma);
 
     Sync sy = make_sync(a.c.ctl, a.c.partials);
     const Geo& g = a.c.g;
@@ -798,7 +1197,7 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(FwdTiled a) {
         const float sc = a.src_scale;
         int it = 0;
         double rel = 0.0;
-        bool ok = solve(a.c, sy, sm, &ring, Tn, Tn + N,
+        bool ok = solve<kTma>(a.c, sy, ring, Tn, Tn + N,
                         [&](unsigned c, int k) { return (qmap && k == 0) ? sc * qmap[c] : 0.f; }, &it, &rel);
         if (!ok) return;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -807,7 +1206,7 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(FwdTiled a) {
             if (it >= a.c.max_iter && rel * rel > a.c.tol2) atomicAdd(&a.c.ctl->notconv, 1);
         }
         // T^{n+1} = T^n + delta, kept as a compensated pair
-        for (unsigned c = c0; c < N; c += stride) add_pair(Tn[c], Tn[N + c], a.c.v.delta[c], Tn1[c], Tn1[N + c]);
+        add_state(Tn, a.c.v.delta, Tn1, N);
         if (!barrier(sy)) return;
         if (a.frames || a.obs) {
             for (unsigned s = c0; s < S; s += stride) {
@@ -827,35 +1226,16 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(FwdTiled a) {
 }
 
 // ------------------------------------------------------------- adjoint
-// Face-product gradient of step n at the own cells (Eq. grad_assembly):
-// g_c -= sum_f (2 dt / h_f^2) alpha_q^2 / (alpha_c + alpha_q)^2 (mu_c - mu_q)(T_c - T_q).
+template <bool kTma>
 __global__ void __launch_bounds__(NT, 1) adjoint_tiled(AdjTiled a) {
-    __shared__ float sm[3][BY][BX];
     extern __shared__ unsigned char dyn_smem[];
-    __shared__ __align__(8) unsigned long long s_bars[NS];
-    TmaRing ring;
-    ring.base = (unsigned char*)(((uintptr_t)dyn_smem + 127) & ~(uintptr_t)127);
-    ring.bar0 = smem_u32(&s_bars[0]);
-    ring.issue_s = 0;
-    ring.wait_s = 0;
-    ring.wait_ph = 0;
-    ring.in_flight = 0;
-    if (a.c.maps) {
-        if (threadIdx.x == 0) {
-            for (int i = 0; i < NS; ++i) mbar_init(ring.bar0 + 8u * i, 1u);
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        }
-        __syncthreads();
-    }
+    __shared__ __align__(8) unsigned long long s_full[NS], s_empty[NS];
+    Ring ring = make_ring(dyn_smem, s_full, s_empty, kTma);
 
     Sync sy = make_sync(a.c.ctl, a.c.partials);
     const Geo& g = a.c.g;
     const unsigned N = g.S * (unsigned)g.nz, S = g.S;
-    const unsigned stride = gridDim.x * NT;
-    const unsigned c0 = blockIdx.x * NT + threadIdx.x;
     const float gs = a.g_scale;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     for (int n = a.n1; n > a.n0; --n) {
         const float* __restrict__ Tn = a.T[n - a.n0];
         const float* __restrict__ mnext = a.mu[(n + 1) & 1];
@@ -863,7 +1243,7 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(AdjTiled a) {
         const float* ob = a.obs + (size_t)(n - 1) * S;
         int it = 0;
         double rel = 0.0;
-        bool ok = solve(a.c, sy, sm, &ring, mnext, mnext + N,
+        bool ok = solve<kTma>(a.c, sy, ring, mnext, mnext + N,
                         [&](unsigned c, int) {
                             return (c >= a.obs_off && c < a.obs_off + S)
                                        ? gs * ((Tn[c] - ob[c - a.obs_off]) + Tn[N + c]) : 0.f;
@@ -875,81 +1255,90 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(AdjTiled a) {
             a.c.resid[a.n1 - n] = rel;
             if (it >= a.c.max_iter && rel * rel > a.c.tol2) atomicAdd(&a.c.ctl->notconv, 1);
         }
-        for (unsigned c = c0; c < N; c += stride) add_pair(mnext[c], mnext[N + c], a.c.v.delta[c], mu[c], mu[N + c]);
+        add_state(mnext, a.c.v.delta, mu, N);
         if (!barrier(sy)) return;
         // gradient of step n with mu^n and T^n (the next step writes only the
         // other mu buffer and the CG vectors, so no barrier is needed after it)
-        for_segments(g, [&](int tile, int k0, int k1) {
-            const int x = (tile % g.tiles_x) * TX + tx, y = (tile / g.tiles_x) * TY + ty;
-            if (x >= g.nx || y >= g.ny) return;
-            for (int k = k0; k < k1; ++k) {
-                const unsigned c = (unsigned)k * S + (unsigned)y * g.nx + x;
+        if constexpr (kTma) {
+            PassIn in{kGrad, 0, false, 0u, 0u};
+            if (!slab_plane(a.c, Tn, &in.zx) || !slab_plane(a.c, mu, &in.zm)) return;
+            GradBody B;
+            B.grad = a.grad;
+            B.wx = a.wx; B.wy = a.wy; B.wz = a.wz;
+            B.nz = g.nz;
+            if (!staged(a.c, ring, in, B)) return;
+        } else {
+            for_cells(g, [&](int k, unsigned c, int x, int y) {
+                const Nb nb = neighbours(g, c, x, y, k);
                 const float ac = a.alpha[c], mc = mu[c], tc = Tn[c], mcl = mu[N + c], tcl = Tn[N + c];
                 float s = 0.f;
-                auto term = [&](unsigned q, float w) {
+#pragma unroll
+                for (int f = 0; f < 6; ++f) {
+                    if (!(nb.m >> f & 1u)) continue;
+                    const unsigned q = nb.q[f];
+                    const float w = f < 2 ? a.wx : (f < 4 ? a.wy : a.wz);
                     const float aq = a.alpha[q];
-                    const float h = aq / (ac + aq);
+                    const float h = aq * rcp_approx(ac + aq);
                     const float dm = (mc - mu[q]) + (mcl - mu[N + q]);
                     const float dT = (tc - Tn[q]) + (tcl - Tn[N + q]);
                     s += w * h * h * dm * dT;
-                };
-                if (x + 1 < g.nx) term(c + 1, a.wx); else if (g.px) term(c + 1 - g.nx, a.wx);
-                if (x > 0) term(c - 1, a.wx); else if (g.px) term(c + g.nx - 1, a.wx);
-                if (y + 1 < g.ny) term(c + g.nx, a.wy);
-                else if (g.py) term(c - (unsigned)(g.ny - 1) * g.nx, a.wy);
-                if (y > 0) term(c - g.nx, a.wy);
-                else if (g.py) term(c + (unsigned)(g.ny - 1) * g.nx, a.wy);
-                if (k + 1 < g.nz) term(c + S, a.wz);
-                if (k > 0) term(c - S, a.wz);
+                }
                 a.grad[c] -= (double)s;
-            }
-        });
+            });
+        }
     }
 }
 
 }  // namespace tiled
 
 // ------------------------------------------------------------------ host
+// The TMA kernels take the stage ring in dynamic shared memory; the
+// plain-load kernels need none (and keep that memory as L1 cache).
 cudaError_t launch_forward_tiled(const tiled::FwdTiled& a, int grid, cudaStream_t s) {
     tiled::FwdTiled copy = a;
     void* args[] = {&copy};
-    return cudaLaunchCooperativeKernel((const void*)tiled::forward_tiled, dim3(grid), dim3(tiled::NT), args,
-                                       tiled::DYN_SMEM, s);
+    const bool tma = a.c.maps != nullptr;
+    const void* fn = tma ? (const void*)tiled::forward_tiled<true> : (const void*)tiled::forward_tiled<false>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(tiled::NT), args, tma ? tiled::DYN_SMEM : 0, s);
 }
 
 cudaError_t launch_adjoint_tiled(const tiled::AdjTiled& a, int grid, cudaStream_t s) {
     tiled::AdjTiled copy = a;
     void* args[] = {&copy};
-    return cudaLaunchCooperativeKernel((const void*)tiled::adjoint_tiled, dim3(grid), dim3(tiled::NT), args,
-                                       tiled::DYN_SMEM, s);
+    const bool tma = a.c.maps != nullptr;
+    const void* fn = tma ? (const void*)tiled::adjoint_tiled<true> : (const void*)tiled::adjoint_tiled<false>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(tiled::NT), args, tma ? tiled::DYN_SMEM : 0, s);
 }
 
 int tiled_dynamic_smem() { return tiled::DYN_SMEM; }
 
+// CTAs of the tiled kernels: as many as fit on the device at once (a
+// cooperative launch), at most two per SM; every kernel variant gets the same.
 int tiled_grid_blocks(int device) {
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return 0;
-    if (cudaFuncSetAttribute(tiled::forward_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, tiled::DYN_SMEM) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(tiled::adjoint_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, tiled::DYN_SMEM) !=
+    const void* tma_fns[2] = {(const void*)tiled::forward_tiled<true>, (const void*)tiled::adjoint_tiled<true>};
+    const void* all_fns[4] = {tma_fns[0], tma_fns[1], (const void*)tiled::forward_tiled<false>,
+                              (const void*)tiled::adjoint_tiled<false>};
+    for (const void* f : tma_fns)
+        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, tiled::DYN_SMEM) != cudaSuccess)
+            return 0;
+    int per = 2;
+    for (int i = 0; i < 4; ++i) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, all_fns[i], tiled::NT, i < 2 ? tiled::DYN_SMEM : 0) !=
             cudaSuccess)
-        return 0;
-    int a = 0, b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, tiled::forward_tiled, tiled::NT, tiled::DYN_SMEM) !=
-        cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tiled::adjoint_tiled, tiled::NT, tiled::DYN_SMEM) !=
-        cudaSuccess)
-        return 0;
-    int per = a < b ? a : b;
-    if (per > 2) per = 2;
+            return 0;
+        per = std::min(per, b);
+    }
     return per * prop.multiProcessorCount;
 }
 
-// Tensor maps of one iteration pass (see TmaMaps).  The encoder comes from the
+// Tensor maps of the staged passes (see TmaMaps).  The encoder comes from the
 // driver through the runtime's entry-point query, so no libcuda link is needed.
 bool tiled_encode_maps(tiled::TmaMaps* M, const tiled::Geo& g, float* const u[2], float* const ws[2],
-                       float* const ss[2], float* p, float* delta, const float* alpha) {
+                       float* const ss[2], float* p, float* delta, const float* alpha, const float* slab,
+                       unsigned slab_planes) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         void* fn = nullptr;
@@ -961,10 +1350,10 @@ bool tiled_encode_maps(tiled::TmaMaps* M, const tiled::Geo& g, float* const u[2]
         encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
     if (g.nx % 4 != 0) return false;
-    const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
     const cuuint64_t strides[2] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.S * 4};
     const cuuint32_t estr[3] = {1, 1, 1};
-    auto make = [&](CUtensorMap* m, const float* base, unsigned bx, unsigned by) {
+    auto make = [&](CUtensorMap* m, const float* base, unsigned bx, unsigned by, unsigned planes = 0) {
+        const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)(planes ? planes : g.nz)};
         const cuuint32_t box[3] = {bx, by, 1};
         return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -977,7 +1366,7 @@ bool tiled_encode_maps(tiled::TmaMaps* M, const tiled::Geo& g, float* const u[2]
         ok = ok && make(&M->ss[i], ss[i], tiled::HB, tiled::HR);
     }
     ok = ok && make(&M->alpha, alpha, tiled::HB, tiled::HR) && make(&M->p, p, tiled::TX, tiled::TY) &&
-         make(&M->delta, delta, tiled::TX, tiled::TY);
+         make(&M->delta, delta, tiled::TX, tiled::TY) && make(&M->states, slab, tiled::HB, tiled::HR, slab_planes);
     return ok;
 }
 

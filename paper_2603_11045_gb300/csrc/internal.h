@@ -19,7 +19,7 @@ constexpr int kMaxRed = 3;
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;
 
 // Device error word values.
-enum DevError : int { kDevOk = 0, kDevTimeout = 1, kDevBadAlpha = 2 };
+enum DevError : int { kDevOk = 0, kDevTimeout = 1, kDevBadAlpha = 2, kDevBadState = 3 };
 
 // Shared control block of one persistent launch (device memory, zeroed by the
 // host before each launch except `err`, which persists over a call).
@@ -117,7 +117,13 @@ cudaError_t launch_tv(const Real* alpha, int nx, int ny, int nz, int bc, double 
 // ------------------------------------------------- tiled FP32 solver (cg_tiled.cu)
 namespace tiled {
 
-constexpr int TX = 32, TY = 32, NT = TX * TY;   // CTA: 32 x 32 columns, one thread each (one CTA per SM)
+// CTA of the tiled kernels: CW compute warps and one copy warp.  A tile is a
+// 32 x 32 column of cells; a compute thread owns QX = 4 consecutive cells
+// along x in one row, so the CW = 8 compute warps cover the 32 rows.
+constexpr int TX = 32, TY = 32, QX = 4;
+constexpr int CW = TY * TX / (32 * QX);          // compute warps
+constexpr int NCT = CW * 32;                     // compute threads
+constexpr int NT = NCT + 32;                     // + the copy warp
 
 struct Geo {
     int nx, ny, nz;
@@ -142,11 +148,18 @@ struct TmaMaps {
     CUtensorMap u[2], ws[2], ss[2];   // box 40 x 34 at (x0-4, y0-1, k)
     CUtensorMap alpha;                // box 40 x 34 at (x0-4, y0-1, k)
     CUtensorMap p, delta;             // box 32 x 32 at (x0, y0, k)
+    CUtensorMap states;               // box 40 x 34 over the state slab (see Common::slab)
 };
 
 struct Common {
     Geo g;
     const TmaMaps* maps;   // device copy of the descriptors, or null (plain loads)
+    // Every state the kernels read (T^n and mu^n as compensated pairs of N
+    // floats each) lives in one slab of slab_planes planes: a state at slab
+    // offset o (floats) has its hi plane k at z = o / S + k and its lo plane k
+    // at z = o / S + nz + k.
+    const float* slab;
+    unsigned slab_planes;
     const float* alpha;    // cell diffusivity; face values are recomputed from it
     float kx, ky, kz;      // dt / h_d^2
     float robin;           // dt h / dz on k = nz-1
@@ -213,7 +226,8 @@ int tiled_grid_blocks(int device);
 int tiled_dynamic_smem();
 // Fill `maps` for the given device buffers; false if the driver refused.
 bool tiled_encode_maps(tiled::TmaMaps* maps, const tiled::Geo& g, float* const u[2], float* const ws[2],
-                       float* const ss[2], float* p, float* delta, const float* alpha);
+                       float* const ss[2], float* p, float* delta, const float* alpha, const float* slab,
+                       unsigned slab_planes);
 cudaError_t launch_forward_tiled(const tiled::FwdTiled& a, int grid, cudaStream_t s);
 cudaError_t launch_adjoint_tiled(const tiled::AdjTiled& a, int grid, cudaStream_t s);
 
