@@ -205,7 +205,7 @@ int grid_for_tiled(nefty_handle* h, const Prob& P) {
     const long units = tiles * P.nz;
     // at least two planes per CTA, so small grids keep their barriers cheap
     long want = std::max(1L, units / 2);
-    return (int)std::min<long>(want, h->grid_tiled);
+    return (int)std::min<long>(std::min<long>(want, h->grid_tiled), tiled::kMaxGrid);
 }
 
 template <typename Real>
@@ -255,27 +255,27 @@ struct Call {
     // every state slot of the call (slots of SB bytes) in one slab, so that a
     // single tensor map reaches all of them
     Real* slab = nullptr;
-    unsigned slab_planes = 0;
+    unsigned slab_halves = 0;   // blocks of N values in the slab
     Real* carve_slab(Arena& a, size_t slots, size_t slot_bytes) {
         slab = (Real*)a.take(slots * slot_bytes);
-        slab_planes = (unsigned)(slots * (slot_bytes / sizeof(Real)) / P.S);
+        slab_halves = (unsigned)(slots * (slot_bytes / sizeof(Real)) / P.N);
         return slab;
     }
     tiled::Vecs tv{};
-    tiled::TmaMaps* tmaps = nullptr;   // device copy (TMA-staged iterations), or null
+    tiled::TmaMaps host_maps{};        // descriptors of the TMA-staged passes (when use_tma)
 
     void place_common(Arena& a, size_t ntables) {
         const size_t N = P.N;
         coef = (Real*)a.take(5 * N * sizeof(Real));
         if (kTiled) {
+            // u, ws, ss of one ping-pong set and p, delta are contiguous (one copy each)
             for (int i = 0; i < 2; ++i) {
-                tv.u[i] = (float*)a.take(N * sizeof(float));
-                tv.ws[i] = (float*)a.take(N * sizeof(float));
-                tv.ss[i] = (float*)a.take(N * sizeof(float));
+                tv.u[i] = (float*)a.take(3 * N * sizeof(float));
+                tv.ws[i] = tv.u[i] + N;
+                tv.ss[i] = tv.u[i] + 2 * N;
             }
-            tv.p = (float*)a.take(N * sizeof(float));
-            tv.delta = (float*)a.take(N * sizeof(float));
-            tmaps = (tiled::TmaMaps*)a.take(sizeof(tiled::TmaMaps));
+            tv.p = (float*)a.take(2 * N * sizeof(float));
+            tv.delta = tv.p + N;
         } else {
             r = (Real*)a.take(N * sizeof(Real));
             p = (Real*)a.take(N * sizeof(Real));
@@ -304,14 +304,10 @@ struct Call {
     nefty_status prepare_tma() {
         if constexpr (kTiled) {
             if (P.bc != NEFTY_BC_NEUMANN || P.nx % 4 != 0) return NEFTY_OK;
-            tiled::TmaMaps host;
             tiled::Geo g{};
             g.nx = P.nx; g.ny = P.ny; g.nz = P.nz; g.S = P.S;
-            if (!tiled_encode_maps(&host, g, tv.u, tv.ws, tv.ss, tv.p, tv.delta, (const float*)alpha.dev,
-                                   (const float*)slab, slab_planes))
+            if (!tiled_encode_maps(&host_maps, g, tv, (const float*)alpha.dev, (const float*)slab, slab_halves))
                 return NEFTY_OK;
-            NEFTY_CUDA(h, cudaMemcpyAsync(tmaps, &host, sizeof host, cudaMemcpyHostToDevice, s));
-            NEFTY_CUDA(h, cudaStreamSynchronize(s));
             use_tma = true;
         }
         return NEFTY_OK;
@@ -386,9 +382,10 @@ struct Call {
         c.g.S = P.S;
         c.g.tiles_x = (P.nx + tiled::TX - 1) / tiled::TX;
         c.g.units = (unsigned)(c.g.tiles_x * ((P.ny + tiled::TY - 1) / tiled::TY)) * (unsigned)P.nz;
-        c.maps = use_tma ? tmaps : nullptr;
+        c.maps = host_maps;
+        c.tma = use_tma ? 1 : 0;
         c.slab = (const float*)slab;
-        c.slab_planes = slab_planes;
+        c.slab_halves = slab_halves;
         c.alpha = (const float*)alpha.dev;
         c.kx = (float)(P.dt / (P.dx * P.dx));
         c.ky = (float)(P.dt / (P.dy * P.dy));
@@ -397,7 +394,9 @@ struct Call {
         c.v = tv;
         c.ctl = ctl;
         c.partials = partials;
-        c.tol2 = P.rtol * P.rtol;
+        const double tol2 = P.rtol * P.rtol;
+        c.tol2_hi = (float)tol2;
+        c.tol2_lo = (float)(tol2 - (double)c.tol2_hi);
         c.max_iter = P.max_iter;
         c.iters = it;
         c.resid = rs;
@@ -744,7 +743,7 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
             ta.g_scale = (float)aa.g_scale;
             ta.obs_off = aa.obs_off;
             ta.obs = (const float*)C.obs.dev;
-            ta.grad = grad;
+            ta.grad = reinterpret_cast<float2*>(grad);   // N pairs in the N-double accumulator
             if (nefty_status e = C.launch_adj_tiled(ta)) return e;
         } else {
             aa.n0 = a0;
@@ -756,7 +755,10 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
         }
         adj_steps += a1 - a0;
     }
-    NEFTY_CUDA(h, launch_cast<Real>(grad, (Real*)ga.dev, P.N, s));
+    if constexpr (Call<Real>::kTiled)
+        NEFTY_CUDA(h, launch_cast_pairs(reinterpret_cast<const float2*>(grad), (float*)ga.dev, P.N, s));
+    else
+        NEFTY_CUDA(h, launch_cast<Real>(grad, (Real*)ga.dev, P.N, s));
     ++C.launches;
     if (gt.user) NEFTY_CUDA(h, cudaMemcpyAsync(gt.dev, mu[1], N * R, cudaMemcpyDeviceToDevice, s));
     for (Output* o : {&ga, &gt})

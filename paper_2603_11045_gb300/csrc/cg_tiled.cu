@@ -73,15 +73,17 @@ struct Sync {
     unsigned red;       // uniform
 };
 
-// Bounded grid barrier (see solver.cu): returns false on timeout or when
-// another CTA has flagged an error.
+// Bounded grid barrier: returns false on timeout or when another CTA has
+// flagged an error.  The CTA's writes are ordered before thread 0's release
+// add by the CTA barrier (release is cumulative), and the acquire load that
+// sees every arrival orders the other CTAs' writes before the closing CTA
+// barrier, so no separate fences are needed.
 __device__ bool barrier(Sync& g) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         g.epoch += 1;
         const unsigned target = g.epoch * g.G;
-        __threadfence();
         red_release(&g.ctl->bar, 1u);
         int ok = 1;
         unsigned spins = 0;
@@ -98,7 +100,6 @@ __device__ bool barrier(Sync& g) {
                 }
             }
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
@@ -130,28 +131,74 @@ struct Acc {
     __device__ __forceinline__ void add(int i, float v) { add_pair(h[i], l[i], v, h[i], l[i]); }
 };
 
-// Compensated warp sum of (hi, lo) pairs; lane 0 holds the result.
+// Compensated warp sum of (hi, lo) pairs, every lane gets the result: the
+// high parts are summed with TwoSum and the rounding errors collected in lo,
+// which is folded in only by the caller (the cascaded summation of Ogita,
+// Rump and Oishi, accurate as if computed in twice the precision).  The
+// dependency chain per level is one shuffle and one add.
 __device__ __forceinline__ void warp_sum2(float& hi, float& lo) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
         float sh, e;
         two_sum(hi, oh, sh, e);
+        hi = sh;
         lo = lo + ol + e;
-        two_sum(sh, lo, hi, lo);
     }
 }
+
+// --------------------------------------------------------- double-float
+// The CG scalars are kept as unevaluated sums hi + lo of two floats and
+// updated with error-free transformations on the FP32 pipes (Dekker's
+// double-length arithmetic): about 44 bits of precision at a fraction of the
+// latency of GB300's FP64 units.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_norm(float a, float b) {   // Fast2Sum: needs |a| >= |b| or a == 0
+    const float s = a + b;
+    return DF{s, b - (s - a)};
+}
+__device__ __forceinline__ DF df_make(float hi, float lo) {   // renormalise any pair
+    float s, e;
+    two_sum(hi, lo, s, e);
+    return DF{s, e};
+}
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+    float sh, sl, th, tl;
+    two_sum(x.hi, y.hi, sh, sl);
+    two_sum(x.lo, y.lo, th, tl);
+    const DF v = df_norm(sh, sl + th);
+    return df_norm(v.hi, tl + v.lo);
+}
+__device__ __forceinline__ DF df_neg(DF x) { return DF{-x.hi, -x.lo}; }
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+    const float ch = x.hi * y.hi;
+    const float cl1 = fmaf(x.hi, y.hi, -ch);
+    const float cl2 = fmaf(x.lo, y.hi, fmaf(x.hi, y.lo, x.lo * y.lo));
+    return df_norm(ch, cl1 + cl2);
+}
+__device__ __forceinline__ DF df_div(DF x, DF y) {
+    const float q1 = __fdiv_rn(x.hi, y.hi);
+    const float p = q1 * y.hi;
+    const float pe = fmaf(q1, y.hi, -p);
+    const float r = (((x.hi - p) - pe) + x.lo) - q1 * y.lo;   // x - q1 y
+    return df_norm(q1, __fdiv_rn(r, y.hi));
+}
+__device__ __forceinline__ bool df_le(DF x, DF y) { return x.hi < y.hi || (x.hi == y.hi && x.lo <= y.lo); }
 
 // Grid sum of NV compensated per-thread pairs.  The sums run on the FP32
 // pipes as (hi, lo) pairs, which keeps about twice the FP32 precision: TwoSum
 // trees over the warp, the CTA and the G CTA partials (fixed order, so every
 // run gives the same bits).  GB300's FP64 rate is a small fraction of its FP32
 // rate, so no FP64 arithmetic is done per thread.  On return thread 0 holds
-// the totals as doubles (hi + lo); the other threads' out[] is unspecified.
+// the totals as double-floats; the other threads' out[] is unspecified.
 // Every pass ends here, so this is also where each thread orders its global
-// stores of the pass before the TMA reads of later passes.
-template <int NV>
-__device__ bool grid_sum(Sync& g, const Acc<NV>& in, double (&out)[NV]) {
+// stores of the pass before the TMA reads of later passes.  after_barrier()
+// runs in every thread right after the grid barrier, before the partials are
+// summed (the copy thread starts the next pass's copies there).
+template <int NV, class Hook>
+__device__ bool grid_sum(Sync& g, const Acc<NV>& in, DF (&out)[NV], Hook after_barrier) {
     __shared__ float s_h[NW][kMaxRed], s_l[NW][kMaxRed];
     asm volatile("fence.proxy.async.global;" ::: "memory");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -162,29 +209,40 @@ __device__ bool grid_sum(Sync& g, const Acc<NV>& in, double (&out)[NV]) {
         if (lane == 0) { s_h[warp][i] = hi; s_l[warp][i] = lo; }
     }
     __syncthreads();
+    // partials: [2][G][kMaxRed] (hi, lo) pairs
     float2* part = reinterpret_cast<float2*>(g.partials) + (size_t)(g.red & 1u) * kMaxRed * g.G;
     if (warp == 0) {
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
             float hi = lane < NW ? s_h[lane][i] : 0.f, lo = lane < NW ? s_l[lane][i] : 0.f;
             warp_sum2(hi, lo);
-            if (lane == 0) part[(size_t)i * g.G + blockIdx.x] = make_float2(hi, lo);
+            if (lane == 0) part[(size_t)blockIdx.x * kMaxRed + i] = make_float2(hi, lo);
         }
     }
     if (!barrier(g)) return false;
+    after_barrier();
     if (warp == 0) {
+        // every load first, then the compensated sums in a fixed order
+        float2 v[kMaxGrid / 32][NV];
+#pragma unroll
+        for (int r = 0; r < kMaxGrid / 32; ++r) {
+            const unsigned b = lane + 32u * r;
+#pragma unroll
+            for (int i = 0; i < NV; ++i)
+                v[r][i] = b < g.G ? part[(size_t)b * kMaxRed + i] : make_float2(0.f, 0.f);
+        }
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
             float hi = 0.f, lo = 0.f;
-            for (unsigned b = lane; b < g.G; b += 32) {
-                const float2 v = part[(size_t)i * g.G + b];
+#pragma unroll
+            for (int r = 0; r < kMaxGrid / 32; ++r) {
                 float sh, e;
-                two_sum(hi, v.x, sh, e);
-                lo = lo + v.y + e;
-                two_sum(sh, lo, hi, lo);
+                two_sum(hi, v[r][i].x, sh, e);
+                hi = sh;
+                lo = lo + v[r][i].y + e;
             }
             warp_sum2(hi, lo);
-            out[i] = (double)hi + (double)lo;
+            out[i] = df_make(hi, lo);
         }
     }
     g.red += 1;
@@ -298,40 +356,52 @@ __device__ __forceinline__ void for_cells(const Geo& g, CellFn f) {
 }
 
 // ------------------------------------------------------------ TMA staging
-// A stage holds one plane of a tile in six slots.  A slot takes either a
-// 40 x 34 box at (x0 - 4, y0 - 1) -- the tile with a one-cell halo, widened on
-// the left to keep the copy 16-byte aligned -- or a 32 x 32 box of the own
-// cells at (x0, y0).  Cells outside the grid arrive as zeros, which is exactly
-// a zero-flux wall (their face values are zero), so this path serves grids
-// with zero-flux lateral walls and nx % 4 == 0 (row pitch a multiple of 16
-// bytes).  Every stencil pass of a solve is staged this way; only what the
-// slots hold differs (PassKind).
+// A stage holds one plane of a tile in six slots of one halo box each: a
+// 40 x 34 box at (x0 - 4, y0 - 1), the tile with a one-cell halo, widened on
+// the left to keep the copy 16-byte aligned.  Arrays that a pass reads
+// together sit in consecutive slots and arrive in one 4D copy (u, ws, ss;
+// the hi and lo halves of a state; p and delta, whose own-cell 32 x 32 boxes
+// share the last two slots).  Cells outside the grid arrive as zeros, which
+// is exactly a zero-flux wall (their face values are zero), so this path
+// serves grids with zero-flux lateral walls and nx % 4 == 0 (row pitch a
+// multiple of 16 bytes).  Every stencil pass of a solve is staged this way;
+// only what the slots hold differs (PassKind).
 constexpr int NS = 6;                         // stages
 constexpr int HB = TX + 8, HR = TY + 2;       // halo box
 constexpr int SZ_H = HB * HR * 4;             // 5440
 constexpr int SZ_O = TX * TY * 4;             // 4096
 constexpr int al128(int b) { return (b + 127) & ~127; }
-constexpr int SLOT = al128(SZ_H);
-constexpr int STAGE_BYTES = 6 * SLOT;
+// Every copy lands on a 128-byte boundary (the TMA requirement for its
+// shared-memory destination); the boxes of one 4D copy follow each other
+// densely.  Slots 0-2: one copy of up to three halo boxes; slot 3: alpha;
+// slots 4-5: a second pair (mu hi, lo), or the own-cell boxes p and delta.
+constexpr int OFF_A = al128(3 * SZ_H);        // 16384
+constexpr int OFF_B = al128(OFF_A + SZ_H);    // 21888
+constexpr int OFF_P = OFF_B, OFF_D = OFF_B + SZ_O;
+constexpr int STAGE_BYTES = al128(OFF_B + 2 * SZ_H);
 constexpr int DYN_SMEM = NS * STAGE_BYTES + 128;   // + alignment slack
-__device__ __forceinline__ constexpr int sl(int s) { return s * SLOT; }
+__device__ __forceinline__ constexpr int sl(int s) {
+    return s < 3 ? s * SZ_H : (s == 3 ? OFF_A : OFF_B + (s - 4) * SZ_H);
+}
+static_assert(OFF_A % 128 == 0 && OFF_B % 128 == 0 && STAGE_BYTES % 128 == 0, "TMA destinations");
+static_assert(OFF_D + SZ_O <= STAGE_BYTES && sl(5) + SZ_H <= STAGE_BYTES, "stage layout");
 
-// What the slots of a staged pass hold (h: halo box, o: own box).
+// What the slots of a staged pass hold.
 enum PassKind : int {
-    kIter,    // 0 u_i h, 1 ws_i h, 2 ss_{i-1} h, 3 alpha h, 4 p o, 5 delta o
-    kInit1,   // 0 x0 hi h, 1 x0 lo h, 3 alpha h
-    kInit2,   // 0 u_0 h, 3 alpha h
-    kGrad     // 0 T hi h, 1 T lo h, 2 mu hi h, 3 alpha h, 4 mu lo h
+    kIter,    // 0 u_i, 1 ws_i, 2 ss_{i-1}, 3 alpha, 4-5 p and delta (own boxes)
+    kInit1,   // 0 x0 hi, 1 x0 lo, 3 alpha
+    kInit2,   // 0 u_0, 3 alpha
+    kGrad     // 0 T hi, 1 T lo, 3 alpha, 4 mu hi, 5 mu lo
 };
 struct PassIn {
     int kind;
     int cur;          // kIter: ping-pong index of the inputs
-    bool first;       // kIter: first iteration (no ss, no p)
-    unsigned zx, zm;  // slab plane 0 of the state read (x0, or T) and of mu
+    bool first;       // kIter: first iteration (ss and p are not read)
+    unsigned zx, zm;  // slab half of the state read (x0, or T) and of mu
 };
 __device__ __forceinline__ unsigned pass_bytes(const PassIn& in) {
     switch (in.kind) {
-        case kIter: return in.first ? 3 * SZ_H + SZ_O : 4 * SZ_H + 2 * SZ_O;
+        case kIter: return 4 * SZ_H + 2 * SZ_O;
         case kInit1: return 3 * SZ_H;
         case kInit2: return 2 * SZ_H;
         default: return 5 * SZ_H;
@@ -371,6 +441,16 @@ __device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* map, 
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
         ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void tma_load4(uint32_t dst, const CUtensorMap* map, int x, int y, int z, int w,
+                                          uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar) : "memory");
+}
+// Bring a descriptor into the descriptor cache ahead of its first use.
+__device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
 }
 
 // The stage ring.  Planes are copied and consumed in the same order (the
@@ -419,49 +499,56 @@ __device__ Ring make_ring(unsigned char* dyn, unsigned long long* full, unsigned
     return R;
 }
 
-// Copy side of one staged pass (lane 0 of the copy warp): every plane of
-// every segment, with the plane below and above each segment.  Returns false
-// if a stage did not come free in time.
-__device__ bool produce(const Common& C, Ring& R, const PassIn& in) {
+// Planes one pass copies into this CTA's ring: every plane of every segment,
+// with the plane below and above each segment.
+__device__ __forceinline__ int pass_planes(const Geo& g) {
+    int n = 0;
+    for_segments(g, [&](int, int k0, int k1) {
+        n += (k1 < g.nz ? k1 : g.nz - 1) - (k0 > 0 ? k0 - 1 : 0) + 1;
+    });
+    return n;
+}
+
+// Copy side of one staged pass (lane 0 of the copy warp): planes [from, to)
+// of the pass, in ring order.  Returns false if a stage did not come free in
+// time.
+__device__ bool produce(const Common& C, Ring& R, const PassIn& in, int from, int to) {
     const Geo& g = C.g;
-    const TmaMaps* M = C.maps;
+    const TmaMaps* M = &C.maps;
     const unsigned bytes = pass_bytes(in);
     bool ok = true;
+    int idx = 0;
     for_segments(g, [&](int tile, int k0, int k1) {
         if (!ok) return;
         const int x0 = (tile % g.tiles_x) * TX, y0 = (tile / g.tiles_x) * TY;
         const int kl = k0 > 0 ? k0 - 1 : 0, kh = k1 < g.nz ? k1 : g.nz - 1;
-        for (int k = kl; k <= kh; ++k) {
+        for (int k = kl; k <= kh; ++k, ++idx) {
+            if (idx < from) continue;
+            if (idx >= to) return;
             const unsigned st = R.ps;
             if (!mbar_wait(R.empty0 + 8u * st, (R.pph >> st) & 1u)) { ok = false; return; }
             R.pph ^= 1u << st;
             const uint32_t dst = smem_u32(R.base + st * STAGE_BYTES), bar = R.full0 + 8u * st;
             mbar_expect_tx(bar, bytes);
-            auto halo = [&](int s, const CUtensorMap* m, int z) { tma_load3(dst + sl(s), m, x0 - 4, y0 - 1, z, bar); };
+            const int xh = x0 - 4, yh = y0 - 1;
             switch (in.kind) {
                 case kIter:
-                    halo(0, &M->u[in.cur], k);
-                    halo(1, &M->ws[in.cur], k);
-                    if (!in.first) halo(2, &M->ss[in.cur], k);
-                    halo(3, &M->alpha, k);
-                    if (!in.first) tma_load3(dst + sl(4), &M->p, x0, y0, k, bar);
-                    tma_load3(dst + sl(5), &M->delta, x0, y0, k, bar);
+                    tma_load4(dst, &M->uws[in.cur], xh, yh, k, 0, bar);
+                    tma_load3(dst + OFF_A, &M->alpha, xh, yh, k, bar);
+                    tma_load4(dst + OFF_P, &M->pd, x0, y0, k, 0, bar);
                     break;
                 case kInit1:
-                    halo(0, &M->states, (int)in.zx + k);
-                    halo(1, &M->states, (int)in.zx + g.nz + k);
-                    halo(3, &M->alpha, k);
+                    tma_load4(dst, &M->states, xh, yh, k, (int)in.zx, bar);
+                    tma_load3(dst + OFF_A, &M->alpha, xh, yh, k, bar);
                     break;
                 case kInit2:
-                    halo(0, &M->u[0], k);
-                    halo(3, &M->alpha, k);
+                    tma_load3(dst, &M->u0, xh, yh, k, bar);
+                    tma_load3(dst + OFF_A, &M->alpha, xh, yh, k, bar);
                     break;
                 default:
-                    halo(0, &M->states, (int)in.zx + k);
-                    halo(1, &M->states, (int)in.zx + g.nz + k);
-                    halo(2, &M->states, (int)in.zm + k);
-                    halo(3, &M->alpha, k);
-                    halo(4, &M->states, (int)in.zm + g.nz + k);
+                    tma_load4(dst, &M->states, xh, yh, k, (int)in.zx, bar);
+                    tma_load3(dst + OFF_A, &M->alpha, xh, yh, k, bar);
+                    tma_load4(dst + OFF_B, &M->states, xh, yh, k, (int)in.zm, bar);
                     break;
             }
             R.fiss ^= 1u << st;
@@ -654,8 +741,8 @@ struct IterBody {
         const float fxl = field1(st, hb - 1, S), fxr = field1(st, hb + 4, S);
         quad_faces(st, hb, ac, C.kx, C.ky, cx, cyp, cym);
         float pp[4] = {0.f, 0.f, 0.f, 0.f}, dd[4];
-        if (!S.first) ld4(st, sl(4), ob, pp);
-        ld4(st, sl(5), ob, dd);
+        if (!S.first) ld4(st, OFF_P, ob, pp);
+        ld4(st, OFF_D, ob, dd);
         const float rob = k + 1 == g.nz ? C.robin : 0.f;
         float wn[4], pn[4], dl[4], s0 = 0.f, s1 = 0.f, s2 = 0.f;
 #pragma unroll
@@ -854,7 +941,7 @@ struct Init2Body {
 // plane k + 1 is held while plane k is worked on); only the -z terms of the
 // next plane are carried in registers.
 struct GradBody {
-    double* grad;
+    float2* grad;          // dJ/dalpha accumulator, compensated (hi, lo) pairs
     float wx, wy, wz;
     int nz;
     float bth[4], btl[4], bmh[4], bml[4], bac[4];   // plane k0 - 1 (segment start only)
@@ -870,8 +957,8 @@ struct GradBody {
                                                 float (&m)[4], float (&mlo)[4], float (&a)[4]) {
         ld4(st, sl(0), hb, t);
         ld4(st, sl(1), hb, tlo);
-        ld4(st, sl(2), hb, m);
-        ld4(st, sl(4), hb, mlo);
+        ld4(st, sl(4), hb, m);
+        ld4(st, sl(5), hb, mlo);
         ld4(st, sl(3), hb, a);
     }
     __device__ __forceinline__ void reset() {}
@@ -894,10 +981,10 @@ struct GradBody {
         float s[4] = {0.f, 0.f, 0.f, 0.f};
         {   // +x, -x
             const int hr = hb + 4, hl = hb - 1;
-            const float tr = lds1(st, sl(0), hr), trl = lds1(st, sl(1), hr), mr = lds1(st, sl(2), hr),
-                        mrl = lds1(st, sl(4), hr), ar = lds1(st, sl(3), hr);
-            const float tq = lds1(st, sl(0), hl), tql = lds1(st, sl(1), hl), mq = lds1(st, sl(2), hl),
-                        mql = lds1(st, sl(4), hl), aq = lds1(st, sl(3), hl);
+            const float tr = lds1(st, sl(0), hr), trl = lds1(st, sl(1), hr), mr = lds1(st, sl(4), hr),
+                        mrl = lds1(st, sl(5), hr), ar = lds1(st, sl(3), hr);
+            const float tq = lds1(st, sl(0), hl), tql = lds1(st, sl(1), hl), mq = lds1(st, sl(4), hl),
+                        mql = lds1(st, sl(5), hl), aq = lds1(st, sl(3), hl);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 s[j] += j < 3 ? term(ac[j], mh[j], ml[j], th[j], tl[j], ac[j + 1], mh[j + 1], ml[j + 1], th[j + 1],
@@ -924,28 +1011,45 @@ struct GradBody {
                 zdn1[j] = term(a[j], m[j], mlo[j], t[j], tlo[j], ac[j], mh[j], ml[j], th[j], tl[j], wz);
             }
         }
-        double gd[4];
-        *reinterpret_cast<double2*>(&gd[0]) = *reinterpret_cast<const double2*>(grad + c);
-        *reinterpret_cast<double2*>(&gd[2]) = *reinterpret_cast<const double2*>(grad + c + 2);
+        float4 g01 = *reinterpret_cast<const float4*>(grad + c), g23 = *reinterpret_cast<const float4*>(grad + c + 2);
+        float gh[4] = {g01.x, g01.z, g23.x, g23.z}, gl[4] = {g01.y, g01.w, g23.y, g23.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (k > 0) s[j] += zdn[j];
-            gd[j] -= (double)s[j];
+            add_pair(gh[j], gl[j], -s[j], gh[j], gl[j]);
         }
-        *reinterpret_cast<double2*>(grad + c) = *reinterpret_cast<const double2*>(&gd[0]);
-        *reinterpret_cast<double2*>(grad + c + 2) = *reinterpret_cast<const double2*>(&gd[2]);
+        *reinterpret_cast<float4*>(grad + c) = make_float4(gh[0], gl[0], gh[1], gl[1]);
+        *reinterpret_cast<float4*>(grad + c + 2) = make_float4(gh[2], gl[2], gh[3], gl[3]);
     }
     __device__ __forceinline__ void shift() { cpy4(zdn, zdn1); }
 };
 
-// One staged pass: the copy thread streams the planes, the compute threads
-// run Body over them.  Returns false (CTA-uniform, with the error recorded and
-// every copy landed) if a wait timed out anywhere in the CTA.
-template <class Body>
-__device__ bool staged(const Common& C, Ring& R, const PassIn& in, Body& B) {
+// Compute threads: wait for the next n stages and hand them back unread
+// (copies started for a pass that is not run).
+__device__ bool discard(Ring& R, int n) {
+    const int lane = threadIdx.x & 31;
     bool ok = true;
-    if (threadIdx.x < NCT) ok = consume(C.g, R, B);
-    else if (threadIdx.x == NCT) ok = produce(C, R, in);
+    for (int i = 0; i < n; ++i) {
+        const unsigned st = R.cs;
+        ok = mbar_wait(R.full0 + 8u * st, (R.cph >> st) & 1u) && ok;
+        R.cph ^= 1u << st;
+        R.cs = ring_next(st);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(R.empty0 + 8u * st);
+    }
+    return ok;
+}
+
+// One staged pass: the copy thread streams the planes (from `from` on: the
+// first ones may have been started early, see Pipe), the compute threads run
+// Body over them.  Returns false (CTA-uniform, with the error recorded and
+// every copy landed) if a wait timed out anywhere in the CTA, or if `pre_ok`
+// (the early copies) is false in any thread.
+template <class Body>
+__device__ bool staged(const Common& C, Ring& R, const PassIn& in, Body& B, int from = 0, bool pre_ok = true) {
+    bool ok = pre_ok;
+    if (threadIdx.x < NCT) ok = consume(C.g, R, B) && ok;
+    else if (threadIdx.x == NCT) ok = produce(C, R, in, from, 1 << 30) && ok;
     if (__syncthreads_or(ok ? 0 : 1)) {
         if (threadIdx.x == NCT) drain(R);
         if (threadIdx.x == 0) atomicCAS(&C.ctl->err, kDevOk, kDevTimeout);
@@ -954,16 +1058,43 @@ __device__ bool staged(const Common& C, Ring& R, const PassIn& in, Body& B) {
     return true;
 }
 
-// Slab plane of a state (see Common::slab); false (with the error recorded)
+// Early copies.  Right after a grid barrier every stage of the ring is free,
+// so the copy thread can start the first stages of the pass that most likely
+// comes next; their latency then hides behind the reduction that follows the
+// barrier.  The pass takes over with staged(..., pipe.n, pipe.ok); if it does
+// not run, pipe_cancel() lets the compute threads discard the stages.
+struct Pipe {
+    int n;       // planes of the next pass already issued (same in every thread)
+    bool ok;     // copy thread: the early issue succeeded
+};
+__device__ __forceinline__ Pipe pipe_none() { return Pipe{0, true}; }
+constexpr int NPRE = 3;   // stages started early (the copy thread is back for the scalars sooner)
+__device__ __forceinline__ Pipe pipe_start(const Common& C, Ring& R, const PassIn& in) {
+    Pipe p{min(NPRE, pass_planes(C.g)), true};
+    if (threadIdx.x == NCT) p.ok = produce(C, R, in, 0, p.n);
+    return p;
+}
+__device__ bool pipe_cancel(const Common& C, Ring& R, const Pipe& p) {
+    bool ok = p.ok;
+    if (threadIdx.x < NCT) ok = discard(R, p.n) && ok;
+    if (__syncthreads_or(ok ? 0 : 1)) {
+        if (threadIdx.x == NCT) drain(R);
+        if (threadIdx.x == 0) atomicCAS(&C.ctl->err, kDevOk, kDevTimeout);
+        return false;
+    }
+    return true;
+}
+
+// Slab half of a state (see Common::slab); false (with the error recorded)
 // if the pointer is not a state of the slab.  Uniform over the grid.
-__device__ __forceinline__ bool slab_plane(const Common& C, const float* p, unsigned* z) {
+__device__ __forceinline__ bool slab_half(const Common& C, const float* p, unsigned* h) {
     const long long off = (long long)(p - C.slab);
-    const long long S = C.g.S;
-    if (off < 0 || off % S != 0 || off / S + 2LL * C.g.nz > (long long)C.slab_planes) {
+    const long long N = (long long)C.g.S * C.g.nz;
+    if (off < 0 || off % N != 0 || off / N + 2 > (long long)C.slab_halves) {
         if (threadIdx.x == 0) atomicCAS(&C.ctl->err, kDevOk, kDevBadState);
         return false;
     }
-    *z = (unsigned)(off / S);
+    *h = (unsigned)(off / N);
     return true;
 }
 
@@ -1012,18 +1143,21 @@ __device__ void plain_pass(const Common& C, int cur, const Step& S, Acc<3>& acc)
 // formed with error-free products and sums (TwoProd through fmaf, TwoSum), so
 // it is accurate relative to itself however small it is against x0; the CG
 // then runs in FP32 on the increment.  On return delta holds the increment.
-// Returns false if a barrier or a stage wait failed.
+// `pre`: early copies of the first pass (TMA path; see Pipe).  In thread 0:
+// *it_out iterations, *rel_out ||r|| / ||b||, *conv_out whether the stop test
+// passed.  Returns false if a barrier or a stage wait failed.
 template <bool kTma, class RhsFn>
-__device__ bool solve(const Common& C, Sync& sy, Ring& ring, const float* __restrict__ x0,
-                      const float* __restrict__ x0lo, RhsFn rhs, int* it_out, double* rel_out) {
+__device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, const float* __restrict__ x0,
+                      const float* __restrict__ x0lo, RhsFn rhs, int* it_out, float* rel_out, bool* conv_out) {
     const Geo& g = C.g;
+    Pipe pp = pipe_none();
     // ---- init 1: r0 = e - (A - I) x0, u0 = M^{-1} r0 ; bb, (r0,u0), (r0,r0)
     Acc<3> acc3;
     if constexpr (kTma) {
         PassIn in{kInit1, 0, false, 0u, 0u};
-        if (!slab_plane(C, x0, &in.zx)) return false;
+        if (!slab_half(C, x0, &in.zx)) return false;
         Init1Body<RhsFn> B(C, rhs, acc3);
-        if (!staged(C, ring, in, B)) return false;
+        if (!staged(C, ring, in, B, pre.n, pre.ok)) return false;
     } else {
         for_cells(g, [&](int k, unsigned c, int x, int y) {
             const Nb n = neighbours(g, c, x, y, k);
@@ -1052,20 +1186,27 @@ __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const float* __rest
     // decision reach the other threads through shared memory.
     __shared__ float s_a, s_b;
     __shared__ int s_go;
-    double t3[3] = {0.0, 0.0, 0.0};
-    if (!grid_sum<3>(sy, acc3, t3)) return false;
-    const double bb = t3[0], lim = C.tol2 * bb;
-    double gam = t3[1], rho = t3[2];
+    DF t3[3];
+    if (!grid_sum<3>(sy, acc3, t3, [&] {
+            if constexpr (kTma) pp = pipe_start(C, ring, PassIn{kInit2, 0, false, 0u, 0u});
+        }))
+        return false;
+    const DF bb = t3[0], lim = df_mul(DF{C.tol2_hi, C.tol2_lo}, bb);
+    DF gam = t3[1], rho = t3[2];
     int it = 0;
-    if (threadIdx.x == 0) s_go = (rho > lim && C.max_iter > 0) ? 1 : 0;
+    if (threadIdx.x == 0) s_go = (!df_le(rho, lim) && C.max_iter > 0) ? 1 : 0;
     __syncthreads();
-    if (s_go) {
+    if (!s_go) {
+        if constexpr (kTma) {
+            if (!pipe_cancel(C, ring, pp)) return false;
+        }
+    } else {
         // ---- init 2: ws0 = M^{-1} A u0 ; (A u0, u0)
         Acc<1> acc1;
         if constexpr (kTma) {
             const PassIn in{kInit2, 0, false, 0u, 0u};
             Init2Body B(C, acc1);
-            if (!staged(C, ring, in, B)) return false;
+            if (!staged(C, ring, in, B, pp.n, pp.ok)) return false;
         } else {
             const float* __restrict__ u0 = C.v.u[0];
             for_cells(g, [&](int k, unsigned c, int x, int y) {
@@ -1084,12 +1225,15 @@ __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const float* __rest
                 acc1.add(0, Au * f);
             });
         }
-        double t1[1] = {0.0};
-        if (!grid_sum<1>(sy, acc1, t1)) return false;
-        double alpha = 0.0, beta = 0.0;
+        DF t1[1];
+        if (!grid_sum<1>(sy, acc1, t1, [&] {
+                if constexpr (kTma) pp = pipe_start(C, ring, PassIn{kIter, 0, true, 0u, 0u});
+            }))
+            return false;
+        DF alpha{0.f, 0.f};
         if (threadIdx.x == 0) {
-            alpha = gam / t1[0];
-            s_a = (float)alpha;
+            alpha = df_div(gam, t1[0]);
+            s_a = alpha.hi;
             s_b = 0.f;
         }
         __syncthreads();
@@ -1104,34 +1248,53 @@ __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const float* __rest
             if constexpr (kTma) {
                 const PassIn in{kIter, cur, S.first, 0u, 0u};
                 IterBody B(C, S, cur, acc);
-                if (!staged(C, ring, in, B)) return false;
+                if (!staged(C, ring, in, B, pp.n, pp.ok)) return false;
             } else {
                 plain_pass(C, cur, S, acc);
             }
-            double t[3] = {0.0, 0.0, 0.0};
-            if (!grid_sum<3>(sy, acc, t)) return false;
+            DF t[3];
+            if (!grid_sum<3>(sy, acc, t, [&] {
+                    if constexpr (kTma) pp = pipe_start(C, ring, PassIn{kIter, cur ^ 1, false, 0u, 0u});
+                }))
+                return false;
             ++it;
             cur ^= 1;
             if (threadIdx.x == 0) {
                 rho = t[2];
-                const bool go = !(rho <= lim || it >= C.max_iter);
+                const bool go = !(df_le(rho, lim) || it >= C.max_iter);
                 if (go) {
-                    const double gam_new = t[0];
-                    beta = gam_new / gam;
-                    alpha = gam_new / (t[1] - beta * gam_new / alpha);
+                    // beta = gam' / gam ; alpha = gam' / ((w, u) - beta gam' / alpha)
+                    const DF gam_new = t[0];
+                    const DF beta = df_div(gam_new, gam);
+                    alpha = df_div(gam_new, df_add(t[1], df_neg(df_div(df_mul(beta, gam_new), alpha))));
                     gam = gam_new;
-                    s_a = (float)alpha;
-                    s_b = (float)beta;
+                    s_a = alpha.hi;
+                    s_b = beta.hi;
                 }
                 s_go = go ? 1 : 0;
             }
             __syncthreads();
-            if (!s_go) break;
+            if (!s_go) {
+                if constexpr (kTma) {
+                    if (!pipe_cancel(C, ring, pp)) return false;
+                }
+                break;
+            }
         }
     }
     *it_out = it;
-    *rel_out = bb > 0.0 ? sqrt(rho / bb) : 0.0;
+    *rel_out = bb.hi > 0.f ? sqrtf(rho.hi / bb.hi) : 0.f;
+    *conv_out = df_le(rho, lim);
     return true;
+}
+
+__device__ __forceinline__ void prefetch_maps(const TmaMaps& M) {
+    tma_prefetch_desc(&M.uws[0]);
+    tma_prefetch_desc(&M.uws[1]);
+    tma_prefetch_desc(&M.u0);
+    tma_prefetch_desc(&M.alpha);
+    tma_prefetch_desc(&M.pd);
+    tma_prefetch_desc(&M.states);
 }
 
 __device__ __forceinline__ Sync make_sync(DevCtl* ctl, double* partials) {
@@ -1175,13 +1338,14 @@ __device__ void add_state(const float* __restrict__ x, const float* __restrict__
 }
 
 // ------------------------------------------------------------- forward
-// kTma: iterations and stencil passes staged through TMA (a.c.maps set);
+// kTma: iterations and stencil passes staged through TMA (a.c.tma set);
 // otherwise plain global loads.
 template <bool kTma>
-__global__ void __launch_bounds__(NT, 1) forward_tiled(FwdTiled a) {
+__global__ void __launch_bounds__(NT, 1) forward_tiled(const __grid_constant__ FwdTiled a) {
     extern __shared__ unsigned char dyn_smem[];
     __shared__ __align__(8) unsigned long long s_full[NS], s_empty[NS];
     Ring ring = make_ring(dyn_smem, s_full, s_empty, kTma);
+    if (kTma && threadIdx.x == NCT) prefetch_maps(a.c.maps);
 
     Sync sy = make_sync(a.c.ctl, a.c.partials);
     const Geo& g = a.c.g;
@@ -1189,6 +1353,7 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(FwdTiled a) {
     const unsigned stride = gridDim.x * NT;
     const unsigned c0 = blockIdx.x * NT + threadIdx.x;
     double loss = 0.0;
+    Pipe pre = pipe_none();
     for (int n = a.n0; n < a.n1; ++n) {
         // states are compensated pairs: hi in [0, N), lo in [N, 2N)
         const float* __restrict__ Tn = a.src[n - a.n0];
@@ -1196,18 +1361,28 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(FwdTiled a) {
         const float* qmap = a.q_full ? a.q_full + (size_t)n * S : (n < a.q_steps ? a.q_face : nullptr);
         const float sc = a.src_scale;
         int it = 0;
-        double rel = 0.0;
-        bool ok = solve<kTma>(a.c, sy, ring, Tn, Tn + N,
-                        [&](unsigned c, int k) { return (qmap && k == 0) ? sc * qmap[c] : 0.f; }, &it, &rel);
+        float rel = 0.f;
+        bool conv = true;
+        bool ok = solve<kTma>(a.c, sy, ring, pre, Tn, Tn + N,
+                        [&](unsigned c, int k) { return (qmap && k == 0) ? sc * qmap[c] : 0.f; }, &it, &rel,
+                        &conv);
         if (!ok) return;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             a.c.iters[n - a.n0] = it;
             a.c.resid[n - a.n0] = rel;
-            if (it >= a.c.max_iter && rel * rel > a.c.tol2) atomicAdd(&a.c.ctl->notconv, 1);
+            if (!conv) atomicAdd(&a.c.ctl->notconv, 1);
         }
         // T^{n+1} = T^n + delta, kept as a compensated pair
         add_state(Tn, a.c.v.delta, Tn1, N);
         if (!barrier(sy)) return;
+        pre = pipe_none();
+        if constexpr (kTma) {   // the next step's first pass, behind the frame below
+            if (n + 1 < a.n1) {
+                PassIn in{kInit1, 0, false, 0u, 0u};
+                if (!slab_half(a.c, a.src[n + 1 - a.n0], &in.zx)) return;
+                pre = pipe_start(a.c, ring, in);
+            }
+        }
         if (a.frames || a.obs) {
             for (unsigned s = c0; s < S; s += stride) {
                 const float v = Tn1[a.obs_off + s];
@@ -1227,10 +1402,11 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(FwdTiled a) {
 
 // ------------------------------------------------------------- adjoint
 template <bool kTma>
-__global__ void __launch_bounds__(NT, 1) adjoint_tiled(AdjTiled a) {
+__global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ AdjTiled a) {
     extern __shared__ unsigned char dyn_smem[];
     __shared__ __align__(8) unsigned long long s_full[NS], s_empty[NS];
     Ring ring = make_ring(dyn_smem, s_full, s_empty, kTma);
+    if (kTma && threadIdx.x == NCT) prefetch_maps(a.c.maps);
 
     Sync sy = make_sync(a.c.ctl, a.c.partials);
     const Geo& g = a.c.g;
@@ -1242,18 +1418,19 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(AdjTiled a) {
         float* __restrict__ mu = a.mu[n & 1];
         const float* ob = a.obs + (size_t)(n - 1) * S;
         int it = 0;
-        double rel = 0.0;
-        bool ok = solve<kTma>(a.c, sy, ring, mnext, mnext + N,
+        float rel = 0.f;
+        bool conv = true;
+        bool ok = solve<kTma>(a.c, sy, ring, pipe_none(), mnext, mnext + N,
                         [&](unsigned c, int) {
                             return (c >= a.obs_off && c < a.obs_off + S)
                                        ? gs * ((Tn[c] - ob[c - a.obs_off]) + Tn[N + c]) : 0.f;
                         },
-                        &it, &rel);
+                        &it, &rel, &conv);
         if (!ok) return;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             a.c.iters[a.n1 - n] = it;
             a.c.resid[a.n1 - n] = rel;
-            if (it >= a.c.max_iter && rel * rel > a.c.tol2) atomicAdd(&a.c.ctl->notconv, 1);
+            if (!conv) atomicAdd(&a.c.ctl->notconv, 1);
         }
         add_state(mnext, a.c.v.delta, mu, N);
         if (!barrier(sy)) return;
@@ -1261,7 +1438,7 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(AdjTiled a) {
         // other mu buffer and the CG vectors, so no barrier is needed after it)
         if constexpr (kTma) {
             PassIn in{kGrad, 0, false, 0u, 0u};
-            if (!slab_plane(a.c, Tn, &in.zx) || !slab_plane(a.c, mu, &in.zm)) return;
+            if (!slab_half(a.c, Tn, &in.zx) || !slab_half(a.c, mu, &in.zm)) return;
             GradBody B;
             B.grad = a.grad;
             B.wx = a.wx; B.wy = a.wy; B.wz = a.wz;
@@ -1283,7 +1460,10 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(AdjTiled a) {
                     const float dT = (tc - Tn[q]) + (tcl - Tn[N + q]);
                     s += w * h * h * dm * dT;
                 }
-                a.grad[c] -= (double)s;
+                const float2 gv = a.grad[c];
+                float gh, gl;
+                add_pair(gv.x, gv.y, -s, gh, gl);
+                a.grad[c] = make_float2(gh, gl);
             });
         }
     }
@@ -1297,7 +1477,7 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(AdjTiled a) {
 cudaError_t launch_forward_tiled(const tiled::FwdTiled& a, int grid, cudaStream_t s) {
     tiled::FwdTiled copy = a;
     void* args[] = {&copy};
-    const bool tma = a.c.maps != nullptr;
+    const bool tma = a.c.tma != 0;
     const void* fn = tma ? (const void*)tiled::forward_tiled<true> : (const void*)tiled::forward_tiled<false>;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(tiled::NT), args, tma ? tiled::DYN_SMEM : 0, s);
 }
@@ -1305,12 +1485,25 @@ cudaError_t launch_forward_tiled(const tiled::FwdTiled& a, int grid, cudaStream_
 cudaError_t launch_adjoint_tiled(const tiled::AdjTiled& a, int grid, cudaStream_t s) {
     tiled::AdjTiled copy = a;
     void* args[] = {&copy};
-    const bool tma = a.c.maps != nullptr;
+    const bool tma = a.c.tma != 0;
     const void* fn = tma ? (const void*)tiled::adjoint_tiled<true> : (const void*)tiled::adjoint_tiled<false>;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(tiled::NT), args, tma ? tiled::DYN_SMEM : 0, s);
 }
 
 int tiled_dynamic_smem() { return tiled::DYN_SMEM; }
+
+namespace tiled {
+__global__ void cast_pairs(const float2* __restrict__ in, float* __restrict__ out, unsigned n) {
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = in[i].x + in[i].y;
+}
+}  // namespace tiled
+
+cudaError_t launch_cast_pairs(const float2* in, float* out, unsigned n, cudaStream_t s) {
+    const unsigned blocks = std::min(4096u, (n + 255u) / 256u);
+    tiled::cast_pairs<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
 
 // CTAs of the tiled kernels: as many as fit on the device at once (a
 // cooperative launch), at most two per SM; every kernel variant gets the same.
@@ -1336,9 +1529,8 @@ int tiled_grid_blocks(int device) {
 
 // Tensor maps of the staged passes (see TmaMaps).  The encoder comes from the
 // driver through the runtime's entry-point query, so no libcuda link is needed.
-bool tiled_encode_maps(tiled::TmaMaps* M, const tiled::Geo& g, float* const u[2], float* const ws[2],
-                       float* const ss[2], float* p, float* delta, const float* alpha, const float* slab,
-                       unsigned slab_planes) {
+bool tiled_encode_maps(tiled::TmaMaps* M, const tiled::Geo& g, const tiled::Vecs& v, const float* alpha,
+                       const float* slab, unsigned slab_halves) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         void* fn = nullptr;
@@ -1350,23 +1542,24 @@ bool tiled_encode_maps(tiled::TmaMaps* M, const tiled::Geo& g, float* const u[2]
         encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
     if (g.nx % 4 != 0) return false;
-    const cuuint64_t strides[2] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.S * 4};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    auto make = [&](CUtensorMap* m, const float* base, unsigned bx, unsigned by, unsigned planes = 0) {
-        const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)(planes ? planes : g.nz)};
-        const cuuint32_t box[3] = {bx, by, 1};
-        return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, estr,
+    const cuuint64_t N = (cuuint64_t)g.S * g.nz;
+    const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.S * 4, N * 4};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    // rank 3 (x, y, z) or, with nw > 0, rank 4 (x, y, z, w): w counts
+    // consecutive blocks of N floats
+    auto make = [&](CUtensorMap* m, const float* base, unsigned bx, unsigned by, unsigned nw, unsigned bw) {
+        const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, nw};
+        const cuuint32_t box[4] = {bx, by, 1, bw};
+        return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, nw ? 4 : 3, (void*)base, dims, strides, box, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     };
+    using tiled::HB;
+    using tiled::HR;
     bool ok = true;
-    for (int i = 0; i < 2; ++i) {
-        ok = ok && make(&M->u[i], u[i], tiled::HB, tiled::HR);
-        ok = ok && make(&M->ws[i], ws[i], tiled::HB, tiled::HR);
-        ok = ok && make(&M->ss[i], ss[i], tiled::HB, tiled::HR);
-    }
-    ok = ok && make(&M->alpha, alpha, tiled::HB, tiled::HR) && make(&M->p, p, tiled::TX, tiled::TY) &&
-         make(&M->delta, delta, tiled::TX, tiled::TY) && make(&M->states, slab, tiled::HB, tiled::HR, slab_planes);
+    for (int i = 0; i < 2; ++i) ok = ok && make(&M->uws[i], v.u[i], HB, HR, 3, 3);
+    ok = ok && make(&M->u0, v.u[0], HB, HR, 0, 1) && make(&M->alpha, alpha, HB, HR, 0, 1) &&
+         make(&M->pd, v.p, tiled::TX, tiled::TY, 2, 2) && make(&M->states, slab, HB, HR, slab_halves, 2);
     return ok;
 }
 

@@ -124,6 +124,7 @@ constexpr int TX = 32, TY = 32, QX = 4;
 constexpr int CW = TY * TX / (32 * QX);          // compute warps
 constexpr int NCT = CW * 32;                     // compute threads
 constexpr int NT = NCT + 32;                     // + the copy warp
+constexpr int kMaxGrid = 320;                    // most CTAs a tiled launch may have
 
 struct Geo {
     int nx, ny, nz;
@@ -137,36 +138,42 @@ struct Geo {
 // a halo in one pass and written in the next).
 struct Vecs {
     float* u[2];           // M^{-1} r
-    float* ws[2];          // M^{-1} A u
-    float* ss[2];          // M^{-1} A p
+    float* ws[2];          // M^{-1} A u      (= u[i] + N)
+    float* ss[2];          // M^{-1} A p      (= u[i] + 2N)
     float* p;
-    float* delta;          // increment of the current solve
+    float* delta;          // increment of the current solve (= p + N)
 };
 
-// TMA descriptors of the arrays one CG iteration reads (tiled FP32 path).
+// TMA descriptors of the staged passes (tiled FP32 path).  They travel by
+// value in the kernel parameters (which the kernels declare __grid_constant__),
+// so every copy reads its descriptor from parameter space.
 struct TmaMaps {
-    CUtensorMap u[2], ws[2], ss[2];   // box 40 x 34 at (x0-4, y0-1, k)
-    CUtensorMap alpha;                // box 40 x 34 at (x0-4, y0-1, k)
-    CUtensorMap p, delta;             // box 32 x 32 at (x0, y0, k)
-    CUtensorMap states;               // box 40 x 34 over the state slab (see Common::slab)
+    CUtensorMap uws[2];    // u, ws, ss of one ping-pong set (3 x N floats, contiguous):
+                           //   4D (x, y, z, 3), box 40 x 34 x 1 x 3 at (x0-4, y0-1, k, 0)
+    CUtensorMap u0;        // u of set 0 alone: box 40 x 34 x 1
+    CUtensorMap alpha;     // box 40 x 34 x 1 at (x0-4, y0-1, k)
+    CUtensorMap pd;        // p, delta (2 x N floats, contiguous): 4D, box 32 x 32 x 1 x 2 at (x0, y0, k, 0)
+    CUtensorMap states;    // the state slab as 4D (x, y, z, halves): box 40 x 34 x 1 x 2 at
+                           //   (x0-4, y0-1, k, h) reads the hi and lo halves of the state at half h
 };
 
 struct Common {
     Geo g;
-    const TmaMaps* maps;   // device copy of the descriptors, or null (plain loads)
+    TmaMaps maps;          // valid when tma != 0
+    int tma;               // passes staged through TMA (else plain loads)
     // Every state the kernels read (T^n and mu^n as compensated pairs of N
-    // floats each) lives in one slab of slab_planes planes: a state at slab
-    // offset o (floats) has its hi plane k at z = o / S + k and its lo plane k
-    // at z = o / S + nz + k.
+    // floats each) lives in one slab of `slab_halves` blocks of N floats; a
+    // state at slab offset o (floats) has its hi half at block o / N and its
+    // lo half at block o / N + 1.
     const float* slab;
-    unsigned slab_planes;
+    unsigned slab_halves;
     const float* alpha;    // cell diffusivity; face values are recomputed from it
     float kx, ky, kz;      // dt / h_d^2
     float robin;           // dt h / dz on k = nz-1
     Vecs v;
     DevCtl* ctl;
-    double* partials;      // [2][kMaxRed][G]
-    double tol2;
+    double* partials;      // [2][G][kMaxRed] (hi, lo) float pairs
+    float tol2_hi, tol2_lo;   // rtol^2 as a double-float
     int max_iter;
     int* iters;
     double* resid;
@@ -195,7 +202,7 @@ struct AdjTiled {
     float g_scale;         // 2 * loss_scale
     unsigned obs_off;
     const float* obs;
-    double* grad;
+    float2* grad;          // dJ/dalpha accumulator: compensated (hi, lo) pairs
 };
 
 }  // namespace tiled
@@ -225,10 +232,11 @@ int tiled_grid_blocks(int device);
 // Shared memory (bytes) the tiled kernels request dynamically.
 int tiled_dynamic_smem();
 // Fill `maps` for the given device buffers; false if the driver refused.
-bool tiled_encode_maps(tiled::TmaMaps* maps, const tiled::Geo& g, float* const u[2], float* const ws[2],
-                       float* const ss[2], float* p, float* delta, const float* alpha, const float* slab,
-                       unsigned slab_planes);
+bool tiled_encode_maps(tiled::TmaMaps* maps, const tiled::Geo& g, const tiled::Vecs& v, const float* alpha,
+                       const float* slab, unsigned slab_halves);
 cudaError_t launch_forward_tiled(const tiled::FwdTiled& a, int grid, cudaStream_t s);
 cudaError_t launch_adjoint_tiled(const tiled::AdjTiled& a, int grid, cudaStream_t s);
+// out[i] = in[i].x + in[i].y (the tiled gradient accumulator to FP32).
+cudaError_t launch_cast_pairs(const float2* in, float* out, unsigned n, cudaStream_t s);
 
 }  // namespace nefty
