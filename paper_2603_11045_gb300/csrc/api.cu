@@ -896,11 +896,12 @@ bool field_dims(const nefty_field_desc* d, FieldDims* out, std::string* why) {
         out->F = d->n_freq; out->W = d->width; out->depth = d->depth;
         out->freq_lo = d->freq_lo; out->freq_hi = d->freq_hi;
         out->alpha_min = d->alpha_min; out->alpha_max = d->alpha_max;
-        // split-K so the weight-gradient GEMMs cover about two waves of CTAs
+        // split-K of the weight-gradient GEMMs: one CTA per SM (per layer, see
+        // field_backward); `splits` bounds it for the partials buffer
+        out->sms = 152;
         const int kblocks = (int)(out->Mp / 64);
-        const int tiles = (out->W / 128) * ((6 * out->F > out->W ? 6 * out->F : out->W) / 128);
-        int sp = std::max(1, 304 / std::max(1, tiles));
-        out->splits = std::min(sp, kblocks);
+        const int min_tiles = ((out->W + 127) / 128) * ((std::min(6 * out->F, out->W) + 127) / 128);
+        out->splits = std::min(std::max(1, out->sms / std::max(1, min_tiles)), kblocks);
         out->colsum_blocks = (int)std::min<unsigned>(1024u, std::max(1u, out->Mp / 256u));
     }
     return true;
@@ -926,6 +927,16 @@ static nefty_status field_call(nefty_handle* h, const nefty_field_desc* d, const
     if (!field_dims(d, &fd, &why)) return fail(h, NEFTY_EINVAL, why);
     if (!theta || !out || (backward && !grad_alpha)) return fail(h, NEFTY_EINVAL, "missing array argument");
     DeviceGuard guard(h->device);
+    {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) == cudaSuccess && sms > 0 &&
+            sms != fd.sms) {
+            const int kblocks = (int)(fd.Mp / 64);
+            const int min_tiles = ((fd.W + 127) / 128) * ((std::min(6 * fd.F, fd.W) + 127) / 128);
+            fd.sms = sms;
+            fd.splits = std::min(std::max(1, sms / std::max(1, min_tiles)), kblocks);
+        }
+    }
     cudaStream_t s = (cudaStream_t)stream;
     const size_t P = field_param_count(fd.F, fd.W, fd.depth);
     Input th, bw, ga;

@@ -22,6 +22,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace nefty {
@@ -42,9 +44,34 @@ __global__ void axis_table_kernel(float* tab, int n, int F, float lo, float rati
 }
 
 // h0[c][d*2F + j] = tab_d[index_d(c)][j], as BF16, rows padded to Mp (zeros).
+// With F % 4 == 0 each thread writes 8 features (16 bytes) of one cell, which
+// never straddle two axes; otherwise one feature at a time.
 __global__ void features_kernel(__nv_bfloat16* h0, unsigned M, unsigned Mp, int nx, int ny, int F,
                                 const float* tx, const float* ty, const float* tz) {
-    const int D = 6 * F;
+    const int D = 6 * F, F2 = 2 * F;
+    if ((F & 3) == 0) {
+        const unsigned per = (unsigned)D / 8;   // 16-byte chunks per cell
+        for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)Mp * per;
+             e += (size_t)gridDim.x * blockDim.x) {
+            const unsigned c = (unsigned)(e / per);
+            const int f = (int)(e - (size_t)c * per) * 8;
+            uint4 out = make_uint4(0u, 0u, 0u, 0u);
+            if (c < M) {
+                const unsigned cy = c / (unsigned)nx, i = c - cy * (unsigned)nx;
+                const unsigned k = cy / (unsigned)ny, j = cy - k * (unsigned)ny;
+                const int d = f / F2, r = f - d * F2;
+                const float* row = d == 0 ? tx + (size_t)i * F2 : (d == 1 ? ty + (size_t)j * F2 : tz + (size_t)k * F2);
+                const float4 p = *reinterpret_cast<const float4*>(row + r);
+                const float4 q = *reinterpret_cast<const float4*>(row + r + 4);
+                const __nv_bfloat162 b0 = __floats2bfloat162_rn(p.x, p.y), b1 = __floats2bfloat162_rn(p.z, p.w);
+                const __nv_bfloat162 b2 = __floats2bfloat162_rn(q.x, q.y), b3 = __floats2bfloat162_rn(q.z, q.w);
+                out = make_uint4(*reinterpret_cast<const uint32_t*>(&b0), *reinterpret_cast<const uint32_t*>(&b1),
+                                 *reinterpret_cast<const uint32_t*>(&b2), *reinterpret_cast<const uint32_t*>(&b3));
+            }
+            reinterpret_cast<uint4*>(h0)[e] = out;
+        }
+        return;
+    }
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)Mp * D;
          e += (size_t)gridDim.x * blockDim.x) {
         const unsigned c = (unsigned)(e / D);
@@ -52,8 +79,8 @@ __global__ void features_kernel(__nv_bfloat16* h0, unsigned M, unsigned Mp, int 
         float v = 0.f;
         if (c < M) {
             const unsigned i = c % nx, j = (c / nx) % ny, k = c / ((unsigned)nx * ny);
-            const int d = f / (2 * F), r = f % (2 * F);
-            v = d == 0 ? tx[(size_t)i * 2 * F + r] : (d == 1 ? ty[(size_t)j * 2 * F + r] : tz[(size_t)k * 2 * F + r]);
+            const int d = f / F2, r = f % F2;
+            v = d == 0 ? tx[(size_t)i * F2 + r] : (d == 1 ? ty[(size_t)j * F2 + r] : tz[(size_t)k * F2 + r]);
         }
         h0[e] = __float2bfloat16_rn(v);
     }
@@ -195,7 +222,9 @@ size_t field_workspace_bytes(const FieldDims& d, bool backward) {
         add(((size_t)W * D + (size_t)(d.depth - 1) * W * W) * 2);   // transposed weights (unused for l = 0)
         add(Mp * W * 2 * 2);     // delta ping-pong
         add(Mp * 4);             // g_f
-        add(Mp * (W > D ? W : D) * 2 * 2);   // transposes of delta and h
+        for (int l = 1; l < d.depth; ++l) add(Mp * W * 2);   // h_l^T
+        add(Mp * W * 2);         // delta^T
+        add(Mp * D * 2);         // h_0^T
         add((size_t)d.splits * W * (W > D ? W : D) * 4);   // split-K partials
         add((size_t)d.colsum_blocks * (W > D ? W : D) * 8);   // column-sum partials
     }
@@ -210,7 +239,8 @@ struct FieldWs {
     __nv_bfloat16* wt;      // BF16 transposed weights
     __nv_bfloat16* dl[2];
     float* gf;
-    __nv_bfloat16 *tA, *tB;
+    __nv_bfloat16* hT[16];  // h_l^T [W x Mp], l = 1 .. depth-1 (written by the forward epilogues)
+    __nv_bfloat16 *tA, *tB; // delta^T [W x Mp], h_0^T [D x Mp]
     float* split;
     double* colpart;
     int* err;
@@ -235,17 +265,18 @@ static FieldWs carve(char* base, const FieldDims& d, bool backward) {
         w.dl[0] = (__nv_bfloat16*)dd;
         w.dl[1] = w.dl[0] + Mp * W;
         w.gf = (float*)take(Mp * 4);
-        char* tt = take(Mp * WD * 2 * 2);
-        w.tA = (__nv_bfloat16*)tt;
-        w.tB = w.tA + Mp * WD;
+        for (int l = 1; l < d.depth; ++l) w.hT[l] = (__nv_bfloat16*)take(Mp * W * 2);
+        w.tA = (__nv_bfloat16*)take(Mp * W * 2);
+        w.tB = (__nv_bfloat16*)take(Mp * D * 2);
         w.split = (float*)take((size_t)d.splits * W * WD * 4);
         w.colpart = (double*)take((size_t)d.colsum_blocks * WD * 8);
     }
     return w;
 }
 
+// with_t: the epilogues also write h_l^T (l = 1 .. depth-1) for the backward.
 static cudaError_t forward_layers(const FieldDims& d, const float* theta, const float* band_w, FieldWs& w,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, bool with_t) {
     const int F = d.F, W = d.W, D = 6 * F;
     const float lo = (float)d.freq_lo, ratio_log = (float)log(d.freq_hi / d.freq_lo);
     axis_table_kernel<<<blocks_for((size_t)d.nx * F), kT, 0, s>>>(w.tx, d.nx, F, lo, ratio_log, band_w);
@@ -268,8 +299,9 @@ static cudaError_t forward_layers(const FieldDims& d, const float* theta, const 
     for (int l = 0; l < d.depth; ++l) {
         const int in = l == 0 ? D : W;
         const float* bias = p + (size_t)W * in;
+        const bool t = with_t && l + 1 < d.depth;
         e = umma_gemm(w.h[l], in, w.wb + woff, in, (int)d.Mp, W, in, 0 /*bias+relu*/, bias, nullptr, w.h[l + 1],
-                      nullptr, W, 1, w.err, s);
+                      nullptr, W, 1, w.err, s, t ? w.hT[l + 1] : nullptr, t ? (int)d.Mp : 0);
         if (e != cudaSuccess) return e;
         p += (size_t)W * in + W;
         woff += (size_t)W * in;
@@ -282,7 +314,7 @@ cudaError_t field_eval(const FieldDims& d, const float* theta, const float* band
     FieldWs w = carve(ws, d, false);
     cudaError_t e = cudaMemsetAsync(w.err, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    if ((e = forward_layers(d, theta, band_w, w, s)) != cudaSuccess) return e;
+    if ((e = forward_layers(d, theta, band_w, w, s, false)) != cudaSuccess) return e;
     const float* w_out = theta + field_param_count(d.F, d.W, d.depth) - d.W - 1;
     head_kernel<<<blocks_for((size_t)d.M * 32), kT, 0, s>>>(w.h[d.depth], d.W, w_out, w_out + d.W, d.M,
                                                             (float)d.alpha_min, (float)d.alpha_max, alpha);
@@ -295,7 +327,7 @@ cudaError_t field_backward(const FieldDims& d, const float* theta, const float* 
     const int F = d.F, W = d.W, D = 6 * F;
     cudaError_t e = cudaMemsetAsync(w.err, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    if ((e = forward_layers(d, theta, band_w, w, s)) != cudaSuccess) return e;
+    if ((e = forward_layers(d, theta, band_w, w, s, true)) != cudaSuccess) return e;
     // parameter offsets
     size_t poff[16], woff[16];
     {
@@ -341,19 +373,26 @@ cudaError_t field_backward(const FieldDims& d, const float* theta, const float* 
                                                                           w.colpart);
         colsum_final_kernel<<<blocks_for(W), kT, 0, s>>>(w.colpart, d.colsum_blocks, W,
                                                          g_theta + poff[l] + (size_t)W * in);
-        // dW_l = delta^T h_l: K-major operands are the transposes [W x Mp] and [in x Mp]
-        transpose_bf16_kernel<<<dim3((d.Mp + 31) / 32, (W + 31) / 32), tb, 0, s>>>(w.dl[cur], w.tA, d.Mp, W);
-        transpose_bf16_kernel<<<dim3((d.Mp + 31) / 32, (in + 31) / 32), tb, 0, s>>>(w.h[l], w.tB, d.Mp, in);
+        // dW_l = delta^T h_l: K-major operands are the transposes [W x Mp] and [in x Mp].
+        // delta^T comes from the previous masked product's epilogue (top layer:
+        // transposed here); h_l^T from the forward epilogues (l = 0: transposed here).
+        if (l == d.depth - 1)
+            transpose_bf16_kernel<<<dim3((d.Mp + 31) / 32, (W + 31) / 32), tb, 0, s>>>(w.dl[cur], w.tA, d.Mp, W);
+        if (l == 0)
+            transpose_bf16_kernel<<<dim3((d.Mp + 31) / 32, (in + 31) / 32), tb, 0, s>>>(w.h[0], w.tB, d.Mp, in);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        e = umma_gemm(w.tA, (int)d.Mp, w.tB, (int)d.Mp, W, in, (int)d.Mp, 2 /*f32 partials*/, nullptr, nullptr,
-                      nullptr, w.split, in, d.splits, w.err, s);
+        // split-K: one CTA per SM over the layer's output tiles
+        const int tiles = ((W + 127) / 128) * ((in + 127) / 128);
+        const int splits = std::min(d.splits, std::max(1, d.sms / tiles));
+        e = umma_gemm(w.tA, (int)d.Mp, l == 0 ? w.tB : w.hT[l], (int)d.Mp, W, in, (int)d.Mp, 2 /*f32 partials*/,
+                      nullptr, nullptr, nullptr, w.split, in, splits, w.err, s);
         if (e != cudaSuccess) return e;
-        split_reduce_kernel<<<blocks_for((size_t)W * in), kT, 0, s>>>(w.split, d.splits, (size_t)W * in,
+        split_reduce_kernel<<<blocks_for((size_t)W * in), kT, 0, s>>>(w.split, splits, (size_t)W * in,
                                                                       g_theta + poff[l]);
         // delta_{l-1} = (delta_l W_l) masked by h_l > 0
         if (l > 0) {
             e = umma_gemm(w.dl[cur], W, w.wt + woff[l], W, (int)d.Mp, in, W, 1 /*mask*/, nullptr, w.h[l],
-                          w.dl[cur ^ 1], nullptr, in, 1, w.err, s);
+                          w.dl[cur ^ 1], nullptr, in, 1, w.err, s, w.tA, (int)d.Mp);
             if (e != cudaSuccess) return e;
             cur ^= 1;
         }

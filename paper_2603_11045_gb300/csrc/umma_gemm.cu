@@ -5,12 +5,15 @@
 //
 // One CTA computes one 128 x 128 tile of D (or one split-K slice of it).
 // A and B tiles of 64 K-elements arrive by TMA (128-byte swizzle, the canonical
-// K-major layout the tensor core reads) in a four-stage shared-memory ring; a
+// K-major layout the tensor core reads) in a shared-memory ring: two stages
+// when K is short (the layers' 256-384; three CTAs then share an SM and overlap
+// one tile's epilogue with the others' loads and MMAs), six for the long-K
+// weight-gradient products; a
 // single thread issues tcgen05.mma (M = 128, N = 128, K = 16 per instruction)
 // with the FP32 accumulator in tensor memory and releases each stage with
 // tcgen05.commit onto that stage's "empty" mbarrier.  After the last k-block the
 // four warps read their 32 accumulator lanes with tcgen05.ld and apply the
-// epilogue.  Every wait is bounded: on timeout the kernel records an error,
+// epilogue, each thread writing 16-byte pieces of its row.  Every wait is bounded: on timeout the kernel records an error,
 // waits (bounded) for its own copies and MMAs, frees its tensor memory and
 // returns.
 #include <cuda.h>
@@ -25,11 +28,12 @@ namespace nefty {
 namespace umma {
 
 constexpr int BM = 128, BN = 128, BK = 64;      // tile and k-block (64 BF16 = one 128-byte swizzle row)
-constexpr int STAGES = 4;
 constexpr int THREADS = 128;                     // 4 warps = the 128 accumulator lanes
 constexpr int TILE_BYTES = BM * BK * 2;          // 16 KB per operand per stage
 constexpr int STAGE_BYTES = 2 * TILE_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;   // + 1024-byte alignment slack
+constexpr int smem_bytes(int stages) { return stages * STAGE_BYTES + 1024; }   // + 1024-byte alignment slack
+// short K: 2 stages, 3 CTAs per SM (3 x 128 TMEM columns, 3 x 65 KB); long K: 6 stages, 1 CTA
+constexpr int ctas_per_sm(int stages) { return stages == 2 ? 3 : 1; }
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t s_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -103,10 +107,14 @@ struct Args {
     __nv_bfloat16* out_bf16;     // [M, ldo]
     float* out_f32;              // [splits][M, ldo]
     int ldo;
+    int vec;                     // ldo and every base 16-byte aligned: 16-byte epilogue stores
+    __nv_bfloat16* out_t;        // BF16 epilogues: also D^T [N, ldt] (or null)
+    int ldt;
     int* err;
 };
 
-__global__ void __launch_bounds__(THREADS, 1)
+template <int STAGES>
+__global__ void __launch_bounds__(THREADS, ctas_per_sm(STAGES))
 gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, Args a) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long full[STAGES], empty[STAGES], done;
@@ -179,7 +187,9 @@ gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
     if (!ok && threadIdx.x == 0) atomicExch(a.err, 1);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-    // ---- epilogue: warp w owns accumulator lanes (rows) 32w .. 32w+31
+    // ---- epilogue: warp w owns accumulator lanes (rows) 32w .. 32w+31; a thread
+    // holds 32 consecutive columns of its row per tcgen05.ld and writes them as
+    // 16-byte pieces when the chunk is whole and aligned (a.vec), else singly.
     if (ok) {
         const int row = m0 + warp * 32 + lane;
         for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -200,19 +210,68 @@ gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
 #pragma unroll
                 for (int t = 0; t < 32; ++t) v[t] = 0u;
             }
-            if (row < a.M) {
+            const int cb = n0 + c0;
+            if (row >= a.M || cb >= a.N) continue;
+            const size_t o = (size_t)row * a.ldo + cb;
+            if (a.vec && cb + 32 <= a.N) {
+                if (a.epi == kEpiF32) {
+                    float4* dst = reinterpret_cast<float4*>(a.out_f32 + (size_t)blockIdx.z * a.M * a.ldo + o);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        dst[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                                             __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+                } else {
+                    uint32_t mk[16];
+                    if (a.epi == kEpiMaskBf16) {
+                        const uint4* src = reinterpret_cast<const uint4*>(a.mask + o);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const uint4 w = src[q];
+                            mk[4 * q] = w.x; mk[4 * q + 1] = w.y; mk[4 * q + 2] = w.z; mk[4 * q + 3] = w.w;
+                        }
+                    }
+                    uint32_t pk[16];
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) {
+                        float x0 = __uint_as_float(v[2 * t]), x1 = __uint_as_float(v[2 * t + 1]);
+                        if (a.epi == kEpiBiasReluBf16) {
+                            x0 = fmaxf(x0 + a.bias[cb + 2 * t], 0.f);
+                            x1 = fmaxf(x1 + a.bias[cb + 2 * t + 1], 0.f);
+                        } else {   // mask: keep where the BF16 mask value is > 0
+                            const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162*>(&mk[t]);
+                            if (!(__low2float(m2) > 0.f)) x0 = 0.f;
+                            if (!(__high2float(m2) > 0.f)) x1 = 0.f;
+                        }
+                        const __nv_bfloat162 b2 = __floats2bfloat162_rn(x0, x1);
+                        pk[t] = *reinterpret_cast<const uint32_t*>(&b2);
+                    }
+                    uint4* dst = reinterpret_cast<uint4*>(a.out_bf16 + o);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+                    if (a.out_t) {   // the warp's 32 rows of one column are 64 contiguous bytes of D^T
+                        unsigned short* dt = reinterpret_cast<unsigned short*>(a.out_t) + (size_t)cb * a.ldt + row;
+#pragma unroll
+                        for (int t = 0; t < 16; ++t) {
+                            dt[(size_t)(2 * t) * a.ldt] = (unsigned short)(pk[t] & 0xFFFFu);
+                            dt[(size_t)(2 * t + 1) * a.ldt] = (unsigned short)(pk[t] >> 16);
+                        }
+                    }
+                }
+            } else {
 #pragma unroll
                 for (int t = 0; t < 32; ++t) {
-                    const int col = n0 + c0 + t;
+                    const int col = cb + t;
                     if (col >= a.N) continue;
                     const float acc = __uint_as_float(v[t]);
-                    const size_t o = (size_t)row * a.ldo + col;
-                    if (a.epi == kEpiBiasReluBf16) {
-                        a.out_bf16[o] = __float2bfloat16_rn(fmaxf(acc + a.bias[col], 0.f));
-                    } else if (a.epi == kEpiMaskBf16) {
-                        a.out_bf16[o] = __float2bfloat16_rn(__bfloat162float(a.mask[o]) > 0.f ? acc : 0.f);
+                    const size_t e = (size_t)row * a.ldo + col;
+                    if (a.epi == kEpiBiasReluBf16 || a.epi == kEpiMaskBf16) {
+                        const __nv_bfloat16 r = a.epi == kEpiBiasReluBf16
+                                                    ? __float2bfloat16_rn(fmaxf(acc + a.bias[col], 0.f))
+                                                    : __float2bfloat16_rn(__bfloat162float(a.mask[e]) > 0.f ? acc : 0.f);
+                        a.out_bf16[e] = r;
+                        if (a.out_t) a.out_t[(size_t)col * a.ldt + row] = r;
                     } else {
-                        a.out_f32[(size_t)blockIdx.z * a.M * a.ldo + o] = acc;
+                        a.out_f32[(size_t)blockIdx.z * a.M * a.ldo + e] = acc;
                     }
                 }
             }
@@ -261,19 +320,24 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld) {
 }
 }  // namespace
 
-// D[M x N] = A[M x K] B[N x K]^T with the chosen epilogue.  K % 64 == 0,
-// lda/ldb in elements (multiples of 8).  splits > 1 only with kEpiF32.
+// D[M x N] = A[M x K] B[N x K]^T with the chosen epilogue (and, for the BF16
+// epilogues, D^T into out_t when given).  K % 64 == 0, lda/ldb in elements
+// (multiples of 8).  splits > 1 only with kEpiF32.
 cudaError_t umma_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
                       int epi, const float* bias, const __nv_bfloat16* mask, __nv_bfloat16* out_bf16,
-                      float* out_f32, int ldo, int splits, int* err, cudaStream_t s) {
+                      float* out_f32, int ldo, int splits, int* err, cudaStream_t s, __nv_bfloat16* out_t, int ldt) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(umma::gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             umma::SMEM_BYTES);
+        cudaError_t e = cudaFuncSetAttribute(umma::gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             umma::smem_bytes(2));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(umma::gemm_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     umma::smem_bytes(6));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     if (K % umma::BK != 0 || lda % 8 != 0 || ldb % 8 != 0 || splits < 1) return cudaErrorInvalidValue;
+    if (out_t && (epi == umma::kEpiF32 || ldt < M)) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
     if (!make_map(&ma, A, M, K, lda) || !make_map(&mb, B, N, K, ldb)) return cudaErrorInvalidValue;
     umma::Args a;
@@ -282,9 +346,18 @@ cudaError_t umma_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, i
     a.k_blocks_per_split = (kb + splits - 1) / splits;
     a.epi = epi;
     a.bias = bias; a.mask = mask; a.out_bf16 = out_bf16; a.out_f32 = out_f32; a.ldo = ldo;
+    a.out_t = out_t;
+    a.ldt = ldt;
+    auto al16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
+    a.vec = (epi == umma::kEpiF32 ? (ldo % 4 == 0 && al16(out_f32))
+                                  : (ldo % 8 == 0 && al16(out_bf16) && (epi != umma::kEpiMaskBf16 || al16(mask))))
+                ? 1 : 0;
     a.err = err;
     dim3 grid((M + umma::BM - 1) / umma::BM, (N + umma::BN - 1) / umma::BN, splits);
-    umma::gemm_kernel<<<grid, umma::THREADS, umma::SMEM_BYTES, s>>>(ma, mb, a);
+    if (a.k_blocks_per_split <= 8)
+        umma::gemm_kernel<2><<<grid, umma::THREADS, umma::smem_bytes(2), s>>>(ma, mb, a);
+    else
+        umma::gemm_kernel<6><<<grid, umma::THREADS, umma::smem_bytes(6), s>>>(ma, mb, a);
     return cudaGetLastError();
 }
 
