@@ -233,6 +233,92 @@ nefty_status nefty_forward_static(int device, const nefty_problem *p, const void
                                   const void *q_face, int32_t q_steps, void *frames_out, void *T_final,
                                   const void *obs, double *loss_out, void *stream);
 
+/* ------------------------------------------------------------------ serving
+ * Continuous batching of ragged jobs (forward sweeps and short inversions on
+ * grids of any size) behind a non-blocking queue.  nefty_serve_start attaches
+ * a server to a handle; `lanes` worker threads, each with its own CUDA stream,
+ * its own workspace and a fixed share of the SMs (so that the lanes'
+ * persistent solver grids are resident side by side), take queued jobs in
+ * arrival order as soon as they are free.  Each lane owns mem_budget_bytes /
+ * lanes of device memory; a job's checkpoint stride is chosen within that share
+ * (every state kept when it fits, about sqrt(nt) checkpoints otherwise, as for
+ * ckpt_every = 0), and a job that cannot fit even then is refused at submit
+ * with NEFTY_ENOMEM.  A job's results depend only on the job and the lane share
+ * (the same bits alone or among other jobs).
+ *
+ * Job kinds:
+ *   NEFTY_JOB_FORWARD    nefty_forward on the job's arrays (frames_out, loss when obs given).
+ *   NEFTY_JOB_INVERSION  `iters` steps of projected gradient descent on alpha:
+ *                        alpha <- max(alpha - lr * dJ/dalpha, alpha_floor), each step one
+ *                        nefty_adjoint_grad; alpha is updated in place; result.loss is the
+ *                        loss of the last step's alpha (before its update).
+ * Arrays follow the conventions of nefty_forward (device or host memory, element type by
+ * problem.prec) and must stay valid until the job is DONE, FAILED or CANCELLED.
+ * The serving calls may be made from any thread; the other calls on the same
+ * handle stay the caller's to serialise. */
+typedef enum { NEFTY_JOB_FORWARD = 0, NEFTY_JOB_INVERSION = 1 } nefty_job_kind;
+typedef enum {
+    NEFTY_JOB_QUEUED = 0,
+    NEFTY_JOB_RUNNING = 1,
+    NEFTY_JOB_DONE = 2,
+    NEFTY_JOB_FAILED = 3,
+    NEFTY_JOB_CANCELLED = 4
+} nefty_job_state;
+
+typedef struct {
+    nefty_problem problem;
+    int32_t kind;               /* nefty_job_kind */
+    int32_t iters;              /* inversion steps (>= 1 for NEFTY_JOB_INVERSION) */
+    double lr;                  /* inversion step length (> 0) */
+    double alpha_floor;         /* inversion lower bound on alpha (> 0) */
+    void *alpha;                /* [nz*ny*nx]; updated in place by an inversion */
+    const void *T0;             /* or NULL */
+    const void *q_face;         /* or NULL */
+    int32_t q_steps;
+    const void *q_full;         /* or NULL */
+    const void *obs;            /* [nt*ny*nx]; required for an inversion */
+    void *frames_out;           /* forward: [nt*ny*nx] or NULL */
+} nefty_job;
+
+typedef struct {
+    int32_t state;              /* nefty_job_state */
+    int32_t status;             /* nefty_status of the job (NEFTY_OK while queued or running) */
+    int32_t lane;               /* lane that ran it, -1 before admission */
+    int32_t iters_done;         /* inversion steps completed */
+    uint64_t t_submit_ns;       /* steady-clock timestamps (ns); 0 = not reached */
+    uint64_t t_admit_ns;
+    uint64_t t_done_ns;
+    double loss;                /* see NEFTY_JOB_INVERSION; forward: the loss when obs was given */
+} nefty_job_result;
+
+typedef struct {
+    int32_t lanes;              /* concurrent jobs, 1..16 (0 = 2) */
+    int32_t max_queue;          /* queued-job limit for NEFTY_EBUSY (0 = 4096) */
+    uint64_t mem_budget_bytes;  /* device memory shared by the lanes (0 = 80% of free memory) */
+} nefty_serve_config;
+
+/* Start serving on h's device (cfg may be NULL for the defaults).
+ * NEFTY_EINVAL if a server is already attached. */
+nefty_status nefty_serve_start(nefty_handle *h, const nefty_serve_config *cfg);
+
+/* Queue a job (non-blocking); *job_id receives its id.  The job description is
+ * copied; the arrays it points to are not.  NEFTY_EINVAL (bad job), NEFTY_ENOMEM
+ * (cannot fit a lane's share), NEFTY_EBUSY (queue full, or no server). */
+nefty_status nefty_serve_submit(nefty_handle *h, const nefty_job *job, uint64_t *job_id);
+
+/* State of a job (non-blocking).  NEFTY_ENOTFOUND for an unknown id. */
+nefty_status nefty_serve_poll(nefty_handle *h, uint64_t job_id, nefty_job_result *out);
+
+/* Cancel a job: a queued job is dropped at once and a running inversion stops
+ * after its current step (both end NEFTY_JOB_CANCELLED); a running forward
+ * sweep, or a job already finished, is left as it is.  NEFTY_ENOTFOUND for an
+ * unknown id. */
+nefty_status nefty_serve_cancel(nefty_handle *h, uint64_t job_id);
+
+/* Stop serving: cancels queued jobs, waits for the running ones, frees the
+ * lanes.  Also done by nefty_destroy.  NEFTY_OK when no server is attached. */
+nefty_status nefty_serve_stop(nefty_handle *h);
+
 #ifdef __cplusplus
 }
 #endif

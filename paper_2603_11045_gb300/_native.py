@@ -50,6 +50,30 @@ class nefty_stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+NEFTY_JOB_FORWARD, NEFTY_JOB_INVERSION = 0, 1
+NEFTY_JOB_QUEUED, NEFTY_JOB_RUNNING, NEFTY_JOB_DONE, NEFTY_JOB_FAILED, NEFTY_JOB_CANCELLED = 0, 1, 2, 3, 4
+
+
+class nefty_job(ctypes.Structure):
+    _fields_ = [("problem", nefty_problem), ("kind", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("lr", ctypes.c_double), ("alpha_floor", ctypes.c_double), ("alpha", ctypes.c_void_p),
+                ("T0", ctypes.c_void_p), ("q_face", ctypes.c_void_p), ("q_steps", ctypes.c_int32),
+                ("q_full", ctypes.c_void_p), ("obs", ctypes.c_void_p), ("frames_out", ctypes.c_void_p)]
+
+
+class nefty_job_result(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("lane", ctypes.c_int32),
+                ("iters_done", ctypes.c_int32), ("t_submit_ns", ctypes.c_uint64), ("t_admit_ns", ctypes.c_uint64),
+                ("t_done_ns", ctypes.c_uint64), ("loss", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class nefty_serve_config(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_int32), ("max_queue", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_uint64)]
+
+
 class NeftyError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{status_name(status)}: {message}")
@@ -81,6 +105,11 @@ _SIGNATURES = {
                  ctypes.c_int),
     "nefty_forward_static": ([ctypes.c_int, _P, _vp, _vp, _vp, ctypes.c_int32, _vp, _vp, _vp,
                               ctypes.POINTER(ctypes.c_double), _vp], ctypes.c_int),
+    "nefty_serve_start": ([_vp, ctypes.POINTER(nefty_serve_config)], ctypes.c_int),
+    "nefty_serve_submit": ([_vp, ctypes.POINTER(nefty_job), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "nefty_serve_poll": ([_vp, ctypes.c_uint64, ctypes.POINTER(nefty_job_result)], ctypes.c_int),
+    "nefty_serve_cancel": ([_vp, ctypes.c_uint64], ctypes.c_int),
+    "nefty_serve_stop": ([_vp], ctypes.c_int),
 }
 
 

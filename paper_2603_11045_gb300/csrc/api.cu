@@ -23,8 +23,12 @@ struct nefty_handle {
     size_t ws_bytes = 0;
     int grid_max[2] = {0, 0};
     int grid_tiled = 0;
+    int grid_share = 1;          // the persistent grids use 1/grid_share of the device (serving lanes)
+    nefty::Server* server = nullptr;
     std::string err;
 };
+
+void nefty::set_grid_share(nefty_handle* h, int share) { h->grid_share = share > 1 ? share : 1; }
 
 static thread_local std::string t_err;
 
@@ -191,7 +195,7 @@ struct Output {
 
 int grid_for(nefty_handle* h, int prec, unsigned N) {
     if (h->grid_max[prec] == 0) h->grid_max[prec] = solver_grid_blocks(h->device, prec);
-    const int gmax = h->grid_max[prec];
+    const int gmax = std::max(1, h->grid_max[prec] / h->grid_share);
     // about four cells per thread; small grids use few CTAs so that the grid
     // barriers of the CG loop stay cheap.
     long want = ((long)N + (long)kThreads * 4 - 1) / ((long)kThreads * 4);
@@ -201,11 +205,12 @@ int grid_for(nefty_handle* h, int prec, unsigned N) {
 
 int grid_for_tiled(nefty_handle* h, const Prob& P) {
     if (h->grid_tiled == 0) h->grid_tiled = tiled_grid_blocks(h->device);
+    const int gmax = std::max(1, h->grid_tiled / h->grid_share);
     const long tiles = (long)((P.nx + tiled::TX - 1) / tiled::TX) * ((P.ny + tiled::TY - 1) / tiled::TY);
     const long units = tiles * P.nz;
     // at least two planes per CTA, so small grids keep their barriers cheap
     long want = std::max(1L, units / 2);
-    return (int)std::min<long>(std::min<long>(want, h->grid_tiled), tiled::kMaxGrid);
+    return (int)std::min<long>(std::min<long>(want, gmax), tiled::kMaxGrid);
 }
 
 template <typename Real>
@@ -508,11 +513,12 @@ struct Call {
     }
 };
 
+// dry != NULL: only size the workspace of the call into *dry.
 template <typename Real>
 nefty_status run_forward(nefty_handle* h, const Prob& P, const void* alpha, const void* T0,
                          const void* q_face, int q_steps, const void* q_full, void* frames_out,
                          void* T_final, const void* obs, double* loss_out, nefty_stats* st,
-                         cudaStream_t s) {
+                         cudaStream_t s, size_t* dry = nullptr) {
     const size_t N = P.N, S = P.S, nt = (size_t)P.nt, R = sizeof(Real);
     Call<Real> C;
     C.h = h; C.P = P; C.s = s; C.q_steps = q_steps;
@@ -543,6 +549,7 @@ nefty_status run_forward(nefty_handle* h, const Prob& P, const void* alpha, cons
     };
     Arena probe;
     layout(probe);
+    if (dry) { *dry = probe.off; return NEFTY_OK; }
     if (nefty_status e = ensure_workspace(h, probe.off)) return e;
     Arena arena;
     arena.base = (char*)h->ws;
@@ -586,7 +593,7 @@ template <typename Real>
 nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, const void* T0,
                          const void* q_face, int q_steps, const void* q_full, const void* obs,
                          double* loss_out, void* grad_alpha, void* grad_T0, nefty_stats* st,
-                         cudaStream_t s) {
+                         cudaStream_t s, size_t* dry = nullptr) {
     const size_t N = P.N, S = P.S, nt = (size_t)P.nt, R = sizeof(Real);
     Call<Real> C;
     C.h = h; C.P = P; C.s = s; C.q_steps = q_steps;
@@ -646,6 +653,7 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
     };
     Arena probe;
     layout(probe);
+    if (dry) { *dry = probe.off; return NEFTY_OK; }
     if (nefty_status e = ensure_workspace(h, probe.off)) return e;
     Arena arena;
     arena.base = (char*)h->ws;
@@ -769,6 +777,27 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
 
 }  // namespace
 
+// Workspace one forward (adjoint = false) or adjoint_grad call of the problem
+// would take on h, with its checkpoint stride chosen within h's budget.
+nefty_status nefty::job_workspace_bytes(nefty_handle* h, const nefty_problem* p, bool adjoint, const void* alpha,
+                                        const void* T0, const void* q_face, const void* q_full, const void* obs,
+                                        size_t* bytes) {
+    Prob P;
+    std::string why;
+    if (check_problem(p, &P, &why)) return fail(h, NEFTY_EINVAL, why);
+    DeviceGuard guard(h->device);
+    const int qs = q_face ? 1 : 0;
+    if (P.prec == NEFTY_FP32)
+        return adjoint ? run_adjoint<float>(h, P, alpha, T0, q_face, qs, q_full, obs, nullptr, nullptr, nullptr,
+                                            nullptr, nullptr, bytes)
+                       : run_forward<float>(h, P, alpha, T0, q_face, qs, q_full, nullptr, nullptr, obs, nullptr,
+                                            nullptr, nullptr, bytes);
+    return adjoint ? run_adjoint<double>(h, P, alpha, T0, q_face, qs, q_full, obs, nullptr, nullptr, nullptr,
+                                         nullptr, nullptr, bytes)
+                   : run_forward<double>(h, P, alpha, T0, q_face, qs, q_full, nullptr, nullptr, obs, nullptr,
+                                         nullptr, nullptr, bytes);
+}
+
 // ===================================================================== C ABI
 extern "C" {
 
@@ -822,6 +851,10 @@ nefty_status nefty_create(nefty_handle** out, int device, uint64_t mem_budget_by
 
 nefty_status nefty_destroy(nefty_handle* h) {
     if (!h) return NEFTY_OK;
+    if (h->server) {
+        server_stop(h->server);
+        h->server = nullptr;
+    }
     {
         DeviceGuard guard(h->device);
         if (h->ws) cudaFree(h->ws);
@@ -867,6 +900,52 @@ nefty_status nefty_adjoint_grad(nefty_handle* h, const nefty_problem* p, const v
                                   grad_T0, stats, s);
     return run_adjoint<double>(h, P, alpha, T0, q_face, q_steps, q_full, obs, loss_out, grad_alpha,
                                grad_T0, stats, s);
+}
+
+nefty_status nefty_serve_start(nefty_handle* h, const nefty_serve_config* cfg) {
+    if (!h) return fail(nullptr, NEFTY_EINVAL, "handle is NULL");
+    if (h->server) return fail(h, NEFTY_EINVAL, "a server is already attached to this handle");
+    nefty_status st = NEFTY_OK;
+    std::string why;
+    h->server = server_start(h->device, cfg, &st, &why);
+    if (!h->server) return fail(h, st, why);
+    return NEFTY_OK;
+}
+
+nefty_status nefty_serve_submit(nefty_handle* h, const nefty_job* job, uint64_t* job_id) {
+    if (!h) return fail(nullptr, NEFTY_EINVAL, "handle is NULL");
+    if (!job || !job_id) return fail(h, NEFTY_EINVAL, "job and job_id are required");
+    if (!h->server) return fail(h, NEFTY_EBUSY, "no server attached (nefty_serve_start)");
+    std::string why;
+    const nefty_status st = server_submit(h->server, job, job_id, &why);
+    if (st != NEFTY_OK) return fail(h, st, why);
+    return NEFTY_OK;
+}
+
+nefty_status nefty_serve_poll(nefty_handle* h, uint64_t job_id, nefty_job_result* out) {
+    if (!h) return fail(nullptr, NEFTY_EINVAL, "handle is NULL");
+    if (!out) return fail(h, NEFTY_EINVAL, "out is NULL");
+    if (!h->server) return fail(h, NEFTY_ENOTFOUND, "no server attached");
+    const nefty_status st = server_poll(h->server, job_id, out);
+    if (st != NEFTY_OK) return fail(h, st, "unknown job id");
+    return NEFTY_OK;
+}
+
+nefty_status nefty_serve_cancel(nefty_handle* h, uint64_t job_id) {
+    if (!h) return fail(nullptr, NEFTY_EINVAL, "handle is NULL");
+    if (!h->server) return fail(h, NEFTY_ENOTFOUND, "no server attached");
+    const nefty_status st = server_cancel(h->server, job_id);
+    if (st != NEFTY_OK) return fail(h, st, "unknown job id");
+    return NEFTY_OK;
+}
+
+nefty_status nefty_serve_stop(nefty_handle* h) {
+    if (!h) return fail(nullptr, NEFTY_EINVAL, "handle is NULL");
+    if (h->server) {
+        server_stop(h->server);
+        h->server = nullptr;
+    }
+    return NEFTY_OK;
 }
 
 }  // extern "C"

@@ -9,6 +9,8 @@
 
 #include <string>
 
+#include "nefty.h"
+
 namespace nefty {
 
 // Threads per CTA of the persistent solver kernels.
@@ -88,6 +90,19 @@ struct AdjArgs {
     int* iters;                        // per-step iterations, index n1 - n
     double* resid;
 };
+
+// ------------------------------------------------------------ serving (serve.cu)
+class Server;
+Server* server_start(int device, const nefty_serve_config* cfg, nefty_status* st, std::string* why);
+void server_stop(Server* s);
+nefty_status server_submit(Server* s, const nefty_job* job, uint64_t* id, std::string* why);
+nefty_status server_poll(Server* s, uint64_t id, nefty_job_result* out);
+nefty_status server_cancel(Server* s, uint64_t id);
+// api.cu: the persistent grids of h use 1/share of the device; workspace of a call.
+void set_grid_share(nefty_handle* h, int share);
+nefty_status job_workspace_bytes(nefty_handle* h, const nefty_problem* p, bool adjoint, const void* alpha,
+                                 const void* T0, const void* q_face, const void* q_full, const void* obs,
+                                 size_t* bytes);
 
 // Message returned by nefty_last_error(NULL) on the calling thread (api.cu).
 void set_thread_error(const char* msg);

@@ -1,0 +1,362 @@
+// Serving: continuous batching of ragged solver jobs behind a non-blocking
+// queue (the nefty_serve_* calls of nefty.h).
+//
+// A Server owns `lanes` worker threads.  Each lane has its own CUDA stream,
+// its own nefty_handle (so its own workspace, budget = total / lanes) and a
+// fixed share of the persistent solver's CTAs (1 / lanes of the SMs), so the
+// lanes' cooperative grids are resident side by side and never wait for one
+// another.  A lane takes the oldest queued job whenever it is free, so jobs of
+// any grid size and length stream through the device continuously.  The job's
+// checkpoint stride follows the lane's memory share (ckpt_every = 0), and
+// submit refuses, with NEFTY_ENOMEM, a job whose smallest workspace does not
+// fit a share.  A job runs only through the public solver calls on its lane's
+// handle, with the lane's fixed CTA count, so its results do not depend on
+// what the other lanes are doing.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.h"
+#include "nefty.h"
+
+namespace nefty {
+namespace {
+
+uint64_t steady_ns() {
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+// alpha <- max(alpha - lr * g, floor): one projected gradient step.
+template <typename Real>
+__global__ void project_step_kernel(Real* alpha, const Real* g, Real lr, Real lo, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const Real a = alpha[i] - lr * g[i];
+        alpha[i] = a > lo ? a : lo;
+    }
+}
+
+bool is_device(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct Job {
+    uint64_t id = 0;
+    nefty_job desc{};
+    nefty_job_result res{};
+    std::atomic<bool> cancel{false};
+};
+
+}  // namespace
+
+class Server {
+  public:
+    Server(int device, const nefty_serve_config& cfg) : device_(device), cfg_(cfg) {}
+
+    ~Server() { stop(); }
+
+    nefty_status start(std::string* why) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(device_);
+        nefty_status st = NEFTY_OK;
+        const uint64_t share = cfg_.mem_budget_bytes / (uint64_t)cfg_.lanes;
+        // the probe handle sizes jobs at submit; it never runs work
+        st = nefty_create(&probe_, device_, share);
+        for (int l = 0; l < cfg_.lanes && st == NEFTY_OK; ++l) {
+            nefty_handle* h = nullptr;
+            st = nefty_create(&h, device_, share);
+            if (st != NEFTY_OK) break;
+            set_grid_share(h, cfg_.lanes);
+            handles_.push_back(h);
+            cudaStream_t s = nullptr;
+            if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+                st = NEFTY_ECUDA;
+                break;
+            }
+            streams_.push_back(s);
+        }
+        if (probe_) set_grid_share(probe_, cfg_.lanes);
+        cudaSetDevice(cur);
+        if (st != NEFTY_OK) {
+            *why = std::string("cannot set up the serving lanes: ") + nefty_last_error(nullptr);
+            release();
+            return st;
+        }
+        for (int l = 0; l < cfg_.lanes; ++l) threads_.emplace_back([this, l] { lane_main(l); });
+        return NEFTY_OK;
+    }
+
+    nefty_status submit(const nefty_job& j, uint64_t* id, std::string* why) {
+        if (j.kind != NEFTY_JOB_FORWARD && j.kind != NEFTY_JOB_INVERSION) {
+            *why = "unknown job kind";
+            return NEFTY_EINVAL;
+        }
+        if (!j.alpha) {
+            *why = "job.alpha is NULL";
+            return NEFTY_EINVAL;
+        }
+        if (j.kind == NEFTY_JOB_INVERSION &&
+            (j.iters < 1 || !(j.lr > 0) || !(j.alpha_floor > 0) || !j.obs)) {
+            *why = "an inversion job needs iters >= 1, lr > 0, alpha_floor > 0 and obs";
+            return NEFTY_EINVAL;
+        }
+        nefty_status st = nefty_problem_check(&j.problem);
+        if (st != NEFTY_OK) {
+            *why = nefty_last_error(nullptr);
+            return st;
+        }
+        {
+            // smallest workspace of the job within one lane's share
+            std::lock_guard<std::mutex> lk(probe_mu_);
+            size_t bytes = 0;
+            st = job_workspace_bytes(probe_, &j.problem, j.kind == NEFTY_JOB_INVERSION, j.alpha, j.T0, j.q_face,
+                                     j.q_full, j.obs, &bytes);
+            if (st != NEFTY_OK) {
+                *why = nefty_last_error(probe_);
+                return st;
+            }
+            const uint64_t share = cfg_.mem_budget_bytes / (uint64_t)cfg_.lanes;
+            const size_t R = j.problem.prec == NEFTY_FP64 ? 8 : 4;
+            const size_t N = (size_t)j.problem.nx * j.problem.ny * j.problem.nz;
+            const size_t extra = j.kind == NEFTY_JOB_INVERSION ? 2 * N * R : 0;   // gradient + alpha copy
+            if (bytes + extra > share) {
+                *why = "the job needs " + std::to_string(bytes + extra) + " bytes, more than a lane's share of " +
+                       std::to_string(share);
+                return NEFTY_ENOMEM;
+            }
+        }
+        auto job = std::make_shared<Job>();
+        job->desc = j;
+        job->res.state = NEFTY_JOB_QUEUED;
+        job->res.status = NEFTY_OK;
+        job->res.lane = -1;
+        std::lock_guard<std::mutex> lk(mu_);
+        if (stopping_ || (int)queue_.size() >= cfg_.max_queue) {
+            *why = stopping_ ? "the server is stopping" : "the serving queue is full";
+            return NEFTY_EBUSY;
+        }
+        job->id = next_id_++;
+        job->res.t_submit_ns = steady_ns();
+        jobs_[job->id] = job;
+        queue_.push_back(job);
+        *id = job->id;
+        cv_.notify_one();
+        return NEFTY_OK;
+    }
+
+    nefty_status poll(uint64_t id, nefty_job_result* out) {
+        std::lock_guard<std::mutex> lk(mu_);
+        auto it = jobs_.find(id);
+        if (it == jobs_.end()) return NEFTY_ENOTFOUND;
+        *out = it->second->res;
+        return NEFTY_OK;
+    }
+
+    nefty_status cancel(uint64_t id) {
+        std::lock_guard<std::mutex> lk(mu_);
+        auto it = jobs_.find(id);
+        if (it == jobs_.end()) return NEFTY_ENOTFOUND;
+        Job& j = *it->second;
+        j.cancel = true;
+        if (j.res.state == NEFTY_JOB_QUEUED) {
+            queue_.erase(std::remove(queue_.begin(), queue_.end(), it->second), queue_.end());
+            j.res.state = NEFTY_JOB_CANCELLED;
+            j.res.status = NEFTY_ECANCELLED;
+            j.res.t_done_ns = steady_ns();
+        }
+        return NEFTY_OK;
+    }
+
+    void stop() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            if (stopping_ && threads_.empty()) return;
+            stopping_ = true;
+            for (auto& j : queue_) {
+                j->res.state = NEFTY_JOB_CANCELLED;
+                j->res.status = NEFTY_ECANCELLED;
+                j->res.t_done_ns = steady_ns();
+            }
+            queue_.clear();
+        }
+        cv_.notify_all();
+        for (auto& t : threads_) t.join();
+        threads_.clear();
+        release();
+    }
+
+  private:
+    void release() {
+        for (cudaStream_t s : streams_) cudaStreamDestroy(s);
+        streams_.clear();
+        for (nefty_handle* h : handles_) nefty_destroy(h);
+        handles_.clear();
+        if (probe_) nefty_destroy(probe_);
+        probe_ = nullptr;
+    }
+
+    void finish(Job& j, int state, nefty_status st) {
+        std::lock_guard<std::mutex> lk(mu_);
+        j.res.state = state;
+        j.res.status = st;
+        j.res.t_done_ns = steady_ns();
+    }
+
+    void lane_main(int lane) {
+        cudaSetDevice(device_);
+        nefty_handle* h = handles_[lane];
+        cudaStream_t s = streams_[lane];
+        while (true) {
+            std::shared_ptr<Job> job;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&] { return stopping_ || !queue_.empty(); });
+                if (queue_.empty()) return;   // stopping
+                job = queue_.front();
+                queue_.pop_front();
+                job->res.state = NEFTY_JOB_RUNNING;
+                job->res.lane = lane;
+                job->res.t_admit_ns = steady_ns();
+            }
+            run(*job, h, s);
+        }
+    }
+
+    void run(Job& job, nefty_handle* h, cudaStream_t s) {
+        const nefty_job& j = job.desc;
+        nefty_problem p = j.problem;
+        p.ckpt_every = p.ckpt_every > 0 ? p.ckpt_every : 0;
+        if (j.kind == NEFTY_JOB_FORWARD) {
+            double loss = 0.0;
+            const nefty_status st = nefty_forward(h, &p, j.alpha, j.T0, j.q_face, j.q_steps, j.q_full,
+                                                  j.frames_out, nullptr, j.obs, j.obs ? &loss : nullptr, nullptr, s);
+            {
+                std::lock_guard<std::mutex> lk(mu_);
+                job.res.loss = loss;
+            }
+            const bool ok = st == NEFTY_OK || st == NEFTY_ENOTCONV;
+            finish(job, ok ? NEFTY_JOB_DONE : NEFTY_JOB_FAILED, st);
+            return;
+        }
+        // inversion: projected gradient steps on a device copy of alpha
+        const size_t N = (size_t)p.nx * p.ny * p.nz;
+        const bool f64 = p.prec == NEFTY_FP64;
+        const size_t R = f64 ? 8 : 4;
+        const bool alpha_dev = is_device(j.alpha);
+        void* a = alpha_dev ? j.alpha : nullptr;
+        void* g = nullptr;
+        nefty_status st = NEFTY_OK;
+        if (cudaMallocAsync(&g, N * R, s) != cudaSuccess ||
+            (!alpha_dev && cudaMallocAsync(&a, N * R, s) != cudaSuccess)) {
+            cudaGetLastError();
+            st = NEFTY_ENOMEM;
+        }
+        if (st == NEFTY_OK && !alpha_dev &&
+            cudaMemcpyAsync(a, j.alpha, N * R, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            st = NEFTY_ECUDA;
+        bool cancelled = false;
+        for (int it = 0; st == NEFTY_OK && it < j.iters; ++it) {
+            if (job.cancel) {
+                cancelled = true;
+                break;
+            }
+            double loss = 0.0;
+            st = nefty_adjoint_grad(h, &p, a, j.T0, j.q_face, j.q_steps, j.q_full, j.obs, &loss, g, nullptr,
+                                    nullptr, s);
+            if (st != NEFTY_OK && st != NEFTY_ENOTCONV) break;
+            st = NEFTY_OK;
+            const unsigned blocks = (unsigned)std::min<size_t>(4096, (N + 255) / 256);
+            if (f64)
+                project_step_kernel<double><<<blocks, 256, 0, s>>>((double*)a, (const double*)g, j.lr, j.alpha_floor,
+                                                                    N);
+            else
+                project_step_kernel<float><<<blocks, 256, 0, s>>>((float*)a, (const float*)g, (float)j.lr,
+                                                                   (float)j.alpha_floor, N);
+            if (cudaGetLastError() != cudaSuccess) st = NEFTY_ECUDA;
+            std::lock_guard<std::mutex> lk(mu_);
+            job.res.loss = loss;
+            job.res.iters_done = it + 1;
+        }
+        if (!alpha_dev && a && st == NEFTY_OK &&
+            cudaMemcpyAsync(j.alpha, a, N * R, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            st = NEFTY_ECUDA;
+        if (g) cudaFreeAsync(g, s);
+        if (!alpha_dev && a) cudaFreeAsync(a, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess && st == NEFTY_OK) st = NEFTY_ECUDA;
+        if (cancelled) finish(job, NEFTY_JOB_CANCELLED, NEFTY_ECANCELLED);
+        else finish(job, st == NEFTY_OK ? NEFTY_JOB_DONE : NEFTY_JOB_FAILED, st);
+    }
+
+    int device_;
+    nefty_serve_config cfg_;
+    nefty_handle* probe_ = nullptr;
+    std::mutex probe_mu_;
+    std::vector<nefty_handle*> handles_;
+    std::vector<cudaStream_t> streams_;
+    std::vector<std::thread> threads_;
+    std::mutex mu_;
+    std::condition_variable cv_;
+    std::deque<std::shared_ptr<Job>> queue_;
+    std::unordered_map<uint64_t, std::shared_ptr<Job>> jobs_;
+    uint64_t next_id_ = 1;
+    bool stopping_ = false;
+};
+
+Server* server_start(int device, const nefty_serve_config* cfg, nefty_status* st, std::string* why) {
+    nefty_serve_config c{};
+    if (cfg) c = *cfg;
+    if (c.lanes == 0) c.lanes = 2;
+    if (c.max_queue == 0) c.max_queue = 4096;
+    if (c.lanes < 1 || c.lanes > 16 || c.max_queue < 1) {
+        *why = "need 1 <= lanes <= 16 and max_queue >= 1";
+        *st = NEFTY_EINVAL;
+        return nullptr;
+    }
+    if (c.mem_budget_bytes == 0) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(device);
+        size_t free_b = 0, total_b = 0;
+        const cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+        cudaSetDevice(cur);
+        if (e != cudaSuccess) {
+            *why = std::string("cudaMemGetInfo: ") + cudaGetErrorName(e);
+            *st = NEFTY_ECUDA;
+            return nullptr;
+        }
+        c.mem_budget_bytes = (uint64_t)(0.8 * (double)free_b);
+    }
+    Server* s = new Server(device, c);
+    *st = s->start(why);
+    if (*st != NEFTY_OK) {
+        delete s;
+        return nullptr;
+    }
+    return s;
+}
+void server_stop(Server* s) { delete s; }
+nefty_status server_submit(Server* s, const nefty_job* j, uint64_t* id, std::string* why) {
+    return s->submit(*j, id, why);
+}
+nefty_status server_poll(Server* s, uint64_t id, nefty_job_result* out) { return s->poll(id, out); }
+nefty_status server_cancel(Server* s, uint64_t id) { return s->cancel(id); }
+
+}  // namespace nefty

@@ -34,7 +34,11 @@ def test_exports_every_declared_symbol(lib):
 def test_struct_fields_match_header():
     from paper_2603_11045_gb300 import _native as N
     src = open(HEADER).read()
-    for struct, cls in (("nefty_problem", N.nefty_problem), ("nefty_stats", N.nefty_stats)):
+    structs = (("nefty_problem", N.nefty_problem), ("nefty_stats", N.nefty_stats), ("nefty_job", N.nefty_job),
+               ("nefty_job_result", N.nefty_job_result), ("nefty_serve_config", N.nefty_serve_config))
+    sizes = {"int32_t": 4, "double": 8, "int64_t": 8, "uint64_t": 8,
+             "nefty_problem": ctypes.sizeof(N.nefty_problem)}
+    for struct, cls in structs:
         body = re.search(r"typedef struct \{([^{}]*)\}\s*" + struct + ";", src, flags=re.S).group(1)
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
         decl = []
@@ -42,14 +46,15 @@ def test_struct_fields_match_header():
             line = line.strip()
             if not line:
                 continue
-            typ, names = line.split(None, 1)
+            words = line.replace("*", " * ").split()
+            pointer = "*" in words
+            words = [w for w in words if w not in ("*", "const")]
+            typ, names = words[0], " ".join(words[1:])
             for nm in names.split(","):
-                decl.append((nm.strip(), typ))
-        ctypes_names = [f[0] for f in cls._fields_]
-        assert [d[0] for d in decl] == ctypes_names
-        sizes = {"int32_t": 4, "double": 8, "int64_t": 8, "uint64_t": 8}
+                decl.append((nm.strip(), "pointer" if pointer else typ))
+        assert [d[0] for d in decl] == [f[0] for f in cls._fields_], struct
         for (nm, typ), (cn, ct) in zip(decl, cls._fields_):
-            assert ctypes.sizeof(ct) == sizes[typ], nm
+            assert ctypes.sizeof(ct) == (8 if typ == "pointer" else sizes[typ]), (struct, nm)
 
 
 def _problem(**kw):

@@ -1,0 +1,120 @@
+"""Serving queue (nefty_serve_*): continuous batching of ragged jobs.
+
+Checks on the GPU that a served job computes what the direct call computes,
+that its results are the same bits alone and among other jobs (each lane has
+a fixed share of the device), that cancellation and refusal work, and that
+the lanes really overlap jobs."""
+import pytest
+import torch
+
+from paper_2603_11045_gb300 import synthetic as S
+from paper_2603_11045_gb300.serve import Server
+from paper_2603_11045_gb300.solver import Problem, Solver
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(nx, ny, nz, nt, seed, prec="fp32"):
+    w = S.inclusion_case(nx=nx, ny=ny, nz=nz, nt=nt, seed=seed)
+    p = Problem.from_workload(w, prec=prec)
+    dt = p.torch_dtype
+    alpha = torch.tensor(w.alpha, dtype=dt, device="cuda")
+    q = torch.tensor(w.q_face, dtype=dt, device="cuda")
+    return w, p, alpha, q
+
+
+@pytest.fixture(scope="module")
+def solver():
+    s = Solver(0)
+    yield s
+    s.close()
+
+
+def test_forward_job_matches_direct_call(solver):
+    w, p, alpha, q = _case(64, 48, 16, 40, 3001)
+    direct = solver.forward(p, alpha, q_face=q, q_steps=w.q_steps)["frames"]
+    with Server(solver, lanes=2) as srv:
+        fr = torch.empty_like(direct)
+        jid = srv.submit(p, alpha, kind="forward", q_face=q, q_steps=w.q_steps, frames_out=fr)
+        r = srv.wait(jid)
+    assert r["state_name"] == "done" and r["status"] == 0, r
+    assert r["t_submit_ns"] <= r["t_admit_ns"] <= r["t_done_ns"]
+    err = (fr - direct).norm() / direct.norm()
+    assert err < 1e-5, float(err)
+
+
+def test_inversion_job_matches_python_loop(solver):
+    w, p, alpha, q = _case(48, 48, 12, 30, 3002)
+    obs = solver.forward(p, torch.tensor(w.alpha_target, dtype=torch.float32, device="cuda"), q_face=q,
+                         q_steps=w.q_steps)["frames"]
+    lr, floor, iters = 2.0, 0.05, 3
+    ref = alpha.clone()
+    losses = []
+    for _ in range(iters):
+        out = solver.adjoint_grad(p, ref, obs, q_face=q, q_steps=w.q_steps)
+        losses.append(out["loss"])
+        ref = torch.clamp(ref - lr * out["grad_alpha"], min=floor)
+    a = alpha.clone()
+    with Server(solver, lanes=2) as srv:
+        jid = srv.submit(p, a, kind="inversion", iters=iters, lr=lr, alpha_floor=floor, q_face=q,
+                         q_steps=w.q_steps, obs=obs)
+        r = srv.wait(jid)
+    assert r["state_name"] == "done" and r["iters_done"] == iters, r
+    assert abs(r["loss"] - losses[-1]) <= 1e-4 * abs(losses[-1]), (r["loss"], losses)
+    err = (a - ref).norm() / ref.norm()
+    assert err < 1e-5, float(err)
+    assert losses[-1] < losses[0]
+
+
+def test_same_bits_alone_and_in_the_mix(solver):
+    w, p, alpha, q = _case(64, 64, 16, 60, 3003)
+    others = [_case(*shape, seed) for shape, seed in (((96, 64, 24, 80), 3004), ((128, 96, 20, 50), 3005),
+                                                      ((32, 32, 8, 200), 3006))]
+    with Server(solver, lanes=3) as srv:
+        alone = torch.empty(p.nt, p.ny, p.nx, dtype=torch.float32, device="cuda")
+        r = srv.wait(srv.submit(p, alpha, q_face=q, q_steps=w.q_steps, frames_out=alone))
+        assert r["state_name"] == "done", r
+        ids, mixed = [], torch.empty_like(alone)
+        for k, (wo, po, ao, qo) in enumerate(others):
+            ids.append(srv.submit(po, ao, q_face=qo, q_steps=wo.q_steps))
+            if k == 1:
+                ids.append(srv.submit(p, alpha, q_face=q, q_steps=w.q_steps, frames_out=mixed))
+        res = [srv.wait(i) for i in ids]
+    assert all(x["state_name"] == "done" for x in res), res
+    assert torch.equal(alone, mixed)
+
+
+def test_cancel_queued_and_refuse_oversized(solver):
+    w, p, alpha, q = _case(128, 128, 32, 300, 3007)
+    with Server(solver, lanes=1, mem_budget_bytes=1 << 30) as srv:
+        first = srv.submit(p, alpha, q_face=q, q_steps=w.q_steps)
+        second = srv.submit(p, alpha, q_face=q, q_steps=w.q_steps)
+        srv.cancel(second)
+        r2 = srv.poll(second)
+        r1 = srv.wait(first)
+        assert r1["state_name"] == "done", r1
+        assert r2["state_name"] == "cancelled" and r2["t_admit_ns"] == 0, r2
+        big = Problem(nx=512, ny=512, nz=96, nt=2000, dt=0.2)
+        a_big = torch.ones(big.nz, big.ny, big.nx, device="cuda")
+        from paper_2603_11045_gb300._native import NeftyError, NEFTY_ENOMEM
+        with pytest.raises(NeftyError) as e:
+            srv.submit(big, a_big, kind="forward")
+        assert e.value.status == NEFTY_ENOMEM
+
+
+def test_lanes_overlap_jobs(solver):
+    """Two equal jobs on two lanes finish in well under twice one job's time."""
+    import time
+    w, p, alpha, q = _case(128, 128, 32, 150, 3008)
+    with Server(solver, lanes=2) as srv:
+        srv.wait(srv.submit(p, alpha, q_face=q, q_steps=w.q_steps))   # warm-up (workspace)
+        srv.wait(srv.submit(p, alpha, q_face=q, q_steps=w.q_steps))
+        t0 = time.perf_counter()
+        srv.wait(srv.submit(p, alpha, q_face=q, q_steps=w.q_steps))
+        one = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        a, b = srv.submit(p, alpha, q_face=q, q_steps=w.q_steps), srv.submit(p, alpha, q_face=q, q_steps=w.q_steps)
+        ra, rb = srv.wait(a), srv.wait(b)
+        two = time.perf_counter() - t0
+    assert {ra["lane"], rb["lane"]} == {0, 1}
+    assert two < 1.6 * one, (one, two)
