@@ -42,11 +42,11 @@ UNIT = "Gcell-steps/s"
 ALG_BYTES_ITER = {"fp32": 40, "fp64": 80}
 ALG_BYTES_STEP = {"fp32": 8, "fp64": 16}
 # DRAM bytes per cell per solver pass of the FP32 CG kernels, from the ncu
-# capture summarised in profiles/forward_tiled_256x256x48_nt20_ncu.md (28.9 GB
-# over 378 passes of 3,145,728 cells), scaled to the timed launches by their
-# pass count (CG iterations plus the init/finalise/gradient passes of each
-# solve).  None = no capture of the current kernels.
-DRAM_BYTES_PER_CELL_PASS = {"fp32": 24.3, "fp64": None}
+# capture summarised in profiles/forward_tiled_256x256x48_nt20_ncu.md, scaled
+# to the timed launches by their pass count (CG iterations plus the
+# init/finalise/gradient passes of each solve).  None = no capture of the
+# current kernels.
+DRAM_BYTES_PER_CELL_PASS = {"fp32": None, "fp64": None}
 
 
 def parse():
@@ -63,6 +63,13 @@ def parse():
     ap.add_argument("--ckpt-every", type=int, default=0)
     ap.add_argument("--cpu-sample-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="inversion", choices=["inversion", "serving"],
+                    help="inversion: the timed inversion step (default); serving: latency of a job stream")
+    ap.add_argument("--serve-scale", default="small", choices=["small", "full"],
+                    help="serving stream: small (24 jobs, <= 192x160x40, 50-200 steps, 3-step inversions) "
+                         "or full (64 jobs at 4/s, grids up to 256x256x64, 200-1000 steps, 10-step inversions)")
+    ap.add_argument("--serve-lanes", type=int, default=2)
+    ap.add_argument("--serve-no-fp64", action="store_true", help="skip the one-at-a-time FP64 replay")
     return ap.parse_args()
 
 
@@ -378,10 +385,92 @@ def run_native(args):
     return 0
 
 
+# ----------------------------------------------------------------- serving
+def run_serving(args):
+    """Replay a Poisson stream of ragged forward / inversion jobs through the
+    serving queue (arrival times honoured on the host clock) and report the
+    submit-to-done latency percentiles from the library's timestamps; then the
+    same stream one job at a time (one lane), in FP32 and in FP64."""
+    import torch
+    from paper_2603_11045_gb300 import synthetic as S
+    from paper_2603_11045_gb300.serve import Server
+    from paper_2603_11045_gb300.solver import Problem, Solver
+    if args.serve_scale == "full":
+        jobs = S.serving_jobs(n_jobs=64, rate=4.0, seed=3000)
+        inv_iters = 10
+    else:
+        jobs = S.serving_jobs(n_jobs=24, rate=8.0, seed=3000, steps=(50, 200), sizes=S.GRID_SIZES[:3])
+        inv_iters = 3
+    solver = Solver(0)
+    inputs = []
+    for j in jobs:   # device inputs, prepared before any timing
+        w = S.inclusion_case(nx=j["nx"], ny=j["ny"], nz=j["nz"], nt=j["nt"], seed=j["seed"])
+        p = Problem.from_workload(w, prec="fp32")
+        a = torch.tensor(w.alpha, dtype=torch.float32, device="cuda")
+        q = torch.tensor(w.q_face, dtype=torch.float32, device="cuda")
+        obs = None
+        if j["kind"] == "inversion":
+            obs = solver.forward(p, torch.tensor(w.alpha_target, dtype=torch.float32, device="cuda"), q_face=q,
+                                 q_steps=w.q_steps)["frames"]
+        inputs.append((j, w, p, a, q, obs))
+    torch.cuda.synchronize()
+
+    def replay(lanes, prec):
+        dt = torch.float32 if prec == "fp32" else torch.float64
+        srv = Server(solver, lanes=lanes)
+        jobs_in = [(j, w, p.with_(prec=prec), a.to(dt), q.to(dt), None if o is None else o.to(dt))
+                   for (j, w, p, a, q, o) in inputs]
+        # warm-up: one short job per lane (workspace, kernel modules)
+        warm = [srv.submit(jobs_in[0][2].with_(nt=5), jobs_in[0][3].clone(), q_face=jobs_in[0][4], q_steps=3)
+                for _ in range(lanes)]
+        for i in warm:
+            srv.wait(i)
+        t0 = time.monotonic()
+        ids = []
+        for (j, w, p, a, q, o) in jobs_in:
+            delay = t0 + j["arrival_s"] - time.monotonic()
+            if delay > 0:
+                time.sleep(delay)
+            if j["kind"] == "inversion":
+                ids.append(srv.submit(p, a.clone(), kind="inversion", iters=inv_iters, lr=1.0, alpha_floor=0.01,
+                                      q_face=q, q_steps=w.q_steps, obs=o))
+            else:
+                ids.append(srv.submit(p, a, q_face=q, q_steps=w.q_steps))
+        res = [srv.wait(i, timeout=3600) for i in ids]
+        srv.stop()
+        bad = [r for r in res if r["state_name"] != "done"]
+        lat = np.array([(r["t_done_ns"] - r["t_submit_ns"]) / 1e9 for r in res])
+        wait = np.array([(r["t_admit_ns"] - r["t_submit_ns"]) / 1e9 for r in res])
+        span = (max(r["t_done_ns"] for r in res) - min(r["t_submit_ns"] for r in res)) / 1e9
+        cell_steps = sum(j["nx"] * j["ny"] * j["nz"] * j["nt"] * (1 if j["kind"] == "forward" else 2 * inv_iters)
+                         for j in jobs)
+        return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                "mean_s": float(lat.mean()), "max_queue_wait_s": float(wait.max()), "makespan_s": span,
+                "gcell_steps_per_s": cell_steps / span / 1e9, "lanes": lanes, "prec": prec, "failed": len(bad)}
+
+    served = replay(args.serve_lanes, "fp32")
+    single = replay(1, "fp32")
+    fp64 = None if args.serve_no_fp64 else replay(1, "fp64")
+    solver.close()
+    n_fwd = sum(j["kind"] == "forward" for j in jobs)
+    line = {"metric": "serving p99 latency", "value": served["p99_s"], "unit": "s", "n_gpus": 1,
+            "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serving stream ({args.serve_scale}): {len(jobs)} jobs, Poisson arrivals, "
+                                   f"{n_fwd} forward + {len(jobs) - n_fwd} {inv_iters}-step inversions, "
+                                   f"grids {sorted({(j['nx'], j['ny'], j['nz']) for j in jobs})}, "
+                                   f"{min(j['nt'] for j in jobs)}-{max(j['nt'] for j in jobs)} steps",
+                       "lanes": args.serve_lanes},
+            "served": served, "one_at_a_time_fp32": single, "one_at_a_time_fp64": fp64}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_native(args)
 
 
