@@ -106,7 +106,7 @@ def config_dict(args, w):
             "grid": [w.nx, w.ny, w.nz], "nt": w.nt, "dt": w.dt, "prec": args.prec,
             "field": "64 log-spaced bands (pi..128 pi) per axis -> 4 x 256 ReLU (BF16 tensor cores) -> [0.01, 2]",
             "tv": {"lambda": TV_LAMBDA, "eps": TV_EPS},
-            "solver": "Jacobi-PCG, rtol 1e-9 (FP32) / 1e-13 (FP64)",
+            "solver": "Jacobi-PCG, rtol 5e-10 (FP32) / 1e-13 (FP64), CG start extrapolated from the last two increments (FP32)",
             "bc": "zero-flux walls", "forcing": "Gaussian surface pulse, sigma 20 cells, 3 steps",
             "l2": "flushed between timed steps (256 MiB write)"}
 

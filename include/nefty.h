@@ -78,12 +78,17 @@ typedef struct {
     int32_t prec;          /* nefty_precision: FP32 = float vectors and stencil, FP64 inner
                               products and residual norms; FP64 = double throughout */
     double rtol;           /* CG stop: ||b - A x||_2 <= rtol ||b||_2 (recursive residual);
-                              0 = 1e-9 (FP32) or 1e-13 (FP64) */
+                              0 = 5e-10 (FP32) or 1e-13 (FP64) */
     int32_t max_iter;      /* CG iteration cap per solve; 0 = 1000 */
     int32_t ckpt_every;    /* adjoint: 0 = automatic (every state kept if it fits the budget,
                               else a checkpoint every ceil(sqrt(nt)) steps), 1 = keep every
                               state, K >= 2 = checkpoint every K steps and recompute */
     double loss_scale;     /* 0 = 1/(nt*nx*ny), i.e. the surface mean-squared error */
+    int32_t extrap;        /* FP32 path: each solve starts from T^n plus an extrapolation of the
+                              previous steps' increments (the adjoint likewise from mu^(n+1));
+                              0 = default (2), -1 = none (start at T^n), 1 = the last increment,
+                              2 = linear extrapolation of the last two.  The FP64 path always
+                              starts at T^n. */
 } nefty_problem;
 
 /* Solver statistics of one call. */

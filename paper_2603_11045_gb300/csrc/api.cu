@@ -78,7 +78,7 @@ bool is_device_ptr(const void* p) {
 
 // Effective problem with defaults filled in.
 struct Prob {
-    int nx, ny, nz, nt, bc, obs_face, prec, max_iter, ckpt_every;
+    int nx, ny, nz, nt, bc, obs_face, prec, max_iter, ckpt_every, extrap;
     double dx, dy, dz, dt, robin_h, rtol, loss_scale;
     unsigned N, S;
 };
@@ -103,13 +103,15 @@ nefty_status check_problem(const nefty_problem* p, Prob* out, std::string* why) 
     if (p->max_iter < 0) { *why = "max_iter must be >= 0"; return NEFTY_EINVAL; }
     if (p->ckpt_every < 0) { *why = "ckpt_every must be >= 0"; return NEFTY_EINVAL; }
     if (p->loss_scale < 0 || !std::isfinite(p->loss_scale)) { *why = "loss_scale must be >= 0"; return NEFTY_EINVAL; }
+    if (p->extrap < -1 || p->extrap > 2) { *why = "extrap must be -1, 0, 1 or 2"; return NEFTY_EINVAL; }
     if (out) {
         out->nx = p->nx; out->ny = p->ny; out->nz = p->nz; out->nt = p->nt; out->bc = p->bc;
         out->obs_face = p->obs_face; out->prec = p->prec;
         out->max_iter = p->max_iter > 0 ? p->max_iter : 1000;
         out->ckpt_every = p->ckpt_every;
+        out->extrap = p->extrap == 0 ? 2 : (p->extrap < 0 ? 0 : p->extrap);   // increments used: 0, 1 or 2
         out->dx = p->dx; out->dy = p->dy; out->dz = p->dz; out->dt = p->dt; out->robin_h = p->robin_h;
-        out->rtol = p->rtol > 0 ? p->rtol : (p->prec == NEFTY_FP32 ? 1e-9 : 1e-13);
+        out->rtol = p->rtol > 0 ? p->rtol : (p->prec == NEFTY_FP32 ? 5e-10 : 1e-13);
         out->loss_scale = p->loss_scale > 0 ? p->loss_scale : 1.0 / ((double)p->nt * p->nx * p->ny);
         out->S = (unsigned)p->nx * (unsigned)p->ny;
         out->N = out->S * (unsigned)p->nz;
@@ -268,6 +270,8 @@ struct Call {
     }
     tiled::Vecs tv{};
     tiled::TmaMaps host_maps{};        // descriptors of the TMA-staged passes (when use_tma)
+    float* ring_f = nullptr;           // increment rings of the forward and adjoint sweeps ([2][N] each)
+    float* ring_a = nullptr;
 
     void place_common(Arena& a, size_t ntables) {
         const size_t N = P.N;
@@ -281,6 +285,8 @@ struct Call {
             }
             tv.p = (float*)a.take(2 * N * sizeof(float));
             tv.delta = tv.p + N;
+            ring_f = (float*)a.take(2 * N * sizeof(float));
+            ring_a = (float*)a.take(2 * N * sizeof(float));
         } else {
             r = (Real*)a.take(N * sizeof(Real));
             p = (Real*)a.take(N * sizeof(Real));
@@ -300,6 +306,10 @@ struct Call {
             if (in->user && in->stage)
                 NEFTY_CUDA(h, cudaMemcpyAsync(in->dev, in->user, in->bytes, cudaMemcpyHostToDevice, s));
         NEFTY_CUDA(h, cudaMemsetAsync(ctl, 0, sizeof(DevCtl), s));
+        if (kTiled) {   // no increment history yet
+            NEFTY_CUDA(h, cudaMemsetAsync(ring_f, 0, 2 * (size_t)P.N * sizeof(float), s));
+            NEFTY_CUDA(h, cudaMemsetAsync(ring_a, 0, 2 * (size_t)P.N * sizeof(float), s));
+        }
         return NEFTY_OK;
     }
 
@@ -311,7 +321,8 @@ struct Call {
             if (P.bc != NEFTY_BC_NEUMANN || P.nx % 4 != 0) return NEFTY_OK;
             tiled::Geo g{};
             g.nx = P.nx; g.ny = P.ny; g.nz = P.nz; g.S = P.S;
-            if (!tiled_encode_maps(&host_maps, g, tv, (const float*)alpha.dev, (const float*)slab, slab_halves))
+            if (!tiled_encode_maps(&host_maps, g, tv, (const float*)alpha.dev, (const float*)slab, slab_halves,
+                                   ring_f, ring_a))
                 return NEFTY_OK;
             use_tma = true;
         }
@@ -422,12 +433,19 @@ struct Call {
         return end_timed(t);
     }
     // forward launch over steps [n0, n1) with either kernel family
+    // ring_load / ring_save / hist0: the increment history (FP32 path, see FwdTiled)
     nefty_status forward_steps(int n0, int n1, Real* const* src, Real* const* dst, int* it, double* rs,
-                               Real* frames, const Real* obsp, double* lossp, int kind) {
+                               Real* frames, const Real* obsp, double* lossp, int kind,
+                               const Real* ring_load = nullptr, Real* const* ring_save = nullptr, int hist0 = 0) {
         if constexpr (kTiled) {
             tiled::FwdTiled a{};
             a.c = tiled_common(it, rs);
             a.n0 = n0; a.n1 = n1;
+            a.ring = ring_f;
+            a.extrap = P.extrap;
+            a.hist0 = hist0;
+            a.ring_load = ring_load;
+            a.ring_save = ring_save;
             a.src = src; a.dst = dst;
             a.q_face = (const float*)qf.dev;
             a.q_steps = qf.dev ? q_steps : 0;
@@ -633,18 +651,24 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
     std::vector<Real*> ck(nck), segbuf(nseg_buf);
     Real* work[2] = {nullptr, nullptr};
     const size_t SB = (Call<Real>::kTiled ? 2 : 1) * N * R;   // one state slot (see run_forward)
+    // FP32 checkpoints (K >= 2) also keep the two increments before them, so a
+    // recomputed segment starts from the same extrapolation as the first sweep
+    const bool ck_ring = Call<Real>::kTiled && K > 1;
     auto layout = [&](Arena& a) {
-        C.place_common(a, 6 * nt + 4);
+        C.place_common(a, 7 * nt + 4);
         grad = (double*)a.take(N * sizeof(double));
         ga.place(a);
         gt.place(a);
         // state slots: mu[2], checkpoints, recompute buffer, forward work pair
-        const size_t slots = 2 + (size_t)nck + (size_t)nseg_buf + (K > 1 ? 2 : 0);
+        const size_t slots = 2 + (size_t)nck * (ck_ring ? 2 : 1) + (size_t)nseg_buf + (K > 1 ? 2 : 0);
         Real* next = C.carve_slab(a, slots, SB);
         auto slot = [&]() { Real* p = next; next += SB / R; return p; };
         mu[0] = slot();
         mu[1] = slot();
-        for (int i = 0; i < nck; ++i) ck[i] = slot();
+        for (int i = 0; i < nck; ++i) {
+            ck[i] = slot();
+            if (ck_ring) slot();   // [delta^{gK-1}; delta^{gK-2}] right after the state
+        }
         for (int i = 0; i < nseg_buf; ++i) segbuf[i] = slot();
         if (K > 1) {
             work[0] = slot();
@@ -665,8 +689,9 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
     if (C.T0.user) NEFTY_CUDA(h, cudaMemcpyAsync(ck[0], C.T0.dev, N * R, cudaMemcpyDeviceToDevice, s));
     NEFTY_CUDA(h, cudaMemsetAsync(grad, 0, N * sizeof(double), s));
 
-    // Pointer tables: forward src/dst (2 nt), recompute src/dst (2 nt), adjoint T (nt + nseg).
-    std::vector<Real*> tab(6 * nt + 4, nullptr);
+    // Pointer tables: forward src/dst (2 nt), recompute src/dst (2 nt), adjoint T (nt + nseg),
+    // ring saves of the first sweep (nt).
+    std::vector<Real*> tab(7 * nt + 4, nullptr);
     Real** F_src = tab.data();
     Real** F_dst = tab.data() + nt;
     Real** R_src = tab.data() + 2 * nt;
@@ -677,9 +702,11 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
         if (n % K == 0 && n / K < nseg) return ck[n / K];
         return work[n & 1];
     };
+    Real** F_ring = tab.data() + 6 * nt + 4;
     for (int n = 0; n < P.nt; ++n) {
         F_src[n] = state_fwd(n);
         F_dst[n] = state_fwd(n + 1);
+        if (ck_ring && (n + 1) % K == 0 && (n + 1) / K < nseg) F_ring[n] = ck[(n + 1) / K] + 2 * N;
     }
     // segment g covers steps [g K, min(g K + K, nt)]; its recomputed states
     // T^{gK+j} go to segbuf[j-1], j = 1..len; T^{gK} is checkpoint g.
@@ -706,9 +733,11 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
     Real** dR_dst = C.tables + 3 * nt;
     Real** dA_T = C.tables + 4 * nt;
 
+    Real** dF_ring = C.tables + 6 * nt + 4;
     // forward sweep with the loss
     if (nefty_status e = C.forward_steps(0, P.nt, dF_src, dF_dst, C.iters, C.resid, nullptr,
-                                         (const Real*)C.obs.dev, C.loss_partials, 0))
+                                         (const Real*)C.obs.dev, C.loss_partials, 0, nullptr,
+                                         ck_ring ? dF_ring : nullptr, 0))
         return e;
 
     // reverse sweep, one segment at a time
@@ -734,7 +763,9 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
         const int a0 = g * seg_len, a1 = std::min(a0 + seg_len, P.nt);
         if (K > 1) {
             if (nefty_status e = C.forward_steps(a0, a1, dR_src + a0, dR_dst + a0, C.iters + nt + rec_steps,
-                                                 C.resid + nt + rec_steps, nullptr, nullptr, nullptr, 1))
+                                                 C.resid + nt + rec_steps, nullptr, nullptr, nullptr, 1,
+                                                 ck_ring && g > 0 ? ck[g] + 2 * N : nullptr, nullptr,
+                                                 std::min(a0, 2)))
                 return e;
             rec_steps += a1 - a0;
         }
@@ -743,6 +774,9 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
             ta.c = C.tiled_common(C.iters + 2 * nt + adj_steps, C.resid + 2 * nt + adj_steps);
             ta.n0 = a0;
             ta.n1 = a1;
+            ta.ring = C.ring_a;
+            ta.extrap = P.extrap;
+            ta.hist0 = std::min(adj_steps, 2);
             ta.T = (float* const*)(dA_T + seg_aoff[g]);
             ta.mu[0] = mu[0];
             ta.mu[1] = mu[1];

@@ -39,6 +39,7 @@ class Problem:
     max_iter: int = 0
     ckpt_every: int = 0
     loss_scale: float = 0.0
+    extrap: int = 0
 
     @classmethod
     def from_workload(cls, w, **kw) -> "Problem":
