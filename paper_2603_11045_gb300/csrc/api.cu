@@ -272,6 +272,7 @@ struct Call {
     tiled::TmaMaps host_maps{};        // descriptors of the TMA-staged passes (when use_tma)
     float* ring_f = nullptr;           // increment rings of the forward and adjoint sweeps ([2][N] each)
     float* ring_a = nullptr;
+    float* ystart = nullptr;           // the next solve's start (a slot of the state slab)
 
     void place_common(Arena& a, size_t ntables) {
         const size_t N = P.N;
@@ -321,8 +322,7 @@ struct Call {
             if (P.bc != NEFTY_BC_NEUMANN || P.nx % 4 != 0) return NEFTY_OK;
             tiled::Geo g{};
             g.nx = P.nx; g.ny = P.ny; g.nz = P.nz; g.S = P.S;
-            if (!tiled_encode_maps(&host_maps, g, tv, (const float*)alpha.dev, (const float*)slab, slab_halves,
-                                   ring_f, ring_a))
+            if (!tiled_encode_maps(&host_maps, g, tv, (const float*)alpha.dev, (const float*)slab, slab_halves))
                 return NEFTY_OK;
             use_tma = true;
         }
@@ -442,6 +442,7 @@ struct Call {
             a.c = tiled_common(it, rs);
             a.n0 = n0; a.n1 = n1;
             a.ring = ring_f;
+            a.ystart = ystart;
             a.extrap = P.extrap;
             a.hist0 = hist0;
             a.ring_load = ring_load;
@@ -558,10 +559,12 @@ nefty_status run_forward(nefty_handle* h, const Prob& P, const void* alpha, cons
     const bool own_t0 = Call<Real>::kTiled || !C.T0.user;
     auto layout = [&](Arena& a) {
         C.place_common(a, 2 * nt);
-        Real* blk = C.carve_slab(a, own_t0 ? 3 : 2, SB);
+        // slots: the work pair, the start of the next solve, T^0 (when copied in)
+        Real* blk = C.carve_slab(a, own_t0 ? 4 : 3, SB);
         work[0] = blk;
         work[1] = blk + SB / R;
-        t0buf = own_t0 ? blk + 2 * (SB / R) : nullptr;
+        if (Call<Real>::kTiled) C.ystart = (float*)(blk + 2 * (SB / R));
+        t0buf = own_t0 ? blk + 3 * (SB / R) : nullptr;
         fr.place(a);
         tf.place(a);
     };
@@ -632,7 +635,7 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
     {
         Arena a;
         C.place_common(a, 6 * nt + 4);
-        a.take(2 * (Call<Real>::kTiled ? 2 : 1) * N * R);   // mu
+        a.take(3 * (Call<Real>::kTiled ? 2 : 1) * N * R);   // mu pair and the start slot
         a.take(N * sizeof(double));
         ga.place(a);
         gt.place(a);
@@ -660,11 +663,13 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
         ga.place(a);
         gt.place(a);
         // state slots: mu[2], checkpoints, recompute buffer, forward work pair
-        const size_t slots = 2 + (size_t)nck * (ck_ring ? 2 : 1) + (size_t)nseg_buf + (K > 1 ? 2 : 0);
+        const size_t slots = 3 + (size_t)nck * (ck_ring ? 2 : 1) + (size_t)nseg_buf + (K > 1 ? 2 : 0);
         Real* next = C.carve_slab(a, slots, SB);
         auto slot = [&]() { Real* p = next; next += SB / R; return p; };
         mu[0] = slot();
         mu[1] = slot();
+        Real* ys = slot();   // the next solve's start
+        if (Call<Real>::kTiled) C.ystart = (float*)ys;
         for (int i = 0; i < nck; ++i) {
             ck[i] = slot();
             if (ck_ring) slot();   // [delta^{gK-1}; delta^{gK-2}] right after the state
@@ -775,6 +780,7 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
             ta.n0 = a0;
             ta.n1 = a1;
             ta.ring = C.ring_a;
+            ta.ystart = C.ystart;
             ta.extrap = P.extrap;
             ta.hist0 = std::min(adj_steps, 2);
             ta.T = (float* const*)(dA_T + seg_aoff[g]);

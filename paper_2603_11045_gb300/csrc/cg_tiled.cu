@@ -389,7 +389,7 @@ static_assert(OFF_D + SZ_O <= STAGE_BYTES && sl(5) + SZ_H <= STAGE_BYTES, "stage
 // What the slots of a staged pass hold.
 enum PassKind : int {
     kIter,    // 0 u_i, 1 ws_i, 2 ss_{i-1}, 3 alpha, 4-5 p and delta (own boxes)
-    kInit1,   // 0 x0 hi, 1 x0 lo, 3 alpha, 4-5 the increment ring (when used)
+    kInit1,   // 0 start hi, 1 start lo, 3 alpha, 4-5 p and delta (own boxes; delta = d when used)
     kInit2,   // 0 u_0, 3 alpha
     kGrad     // 0 T hi, 1 T lo, 3 alpha, 4 mu hi, 5 mu lo
 };
@@ -398,13 +398,12 @@ struct PassIn {
     int cur;          // kIter: ping-pong index of the inputs
     bool first;       // kIter: first iteration (ss and p are not read)
     unsigned zx, zm;  // slab half of the state read (x0, or T) and of mu
-    int ring;         // kInit1: increment ring (0 forward, 1 adjoint) staged in slots 4-5 when hu > 0
-    int hu;           // kInit1: increments the start uses (0, 1, 2)
+    int hu;           // kInit1: 0 = the start is x0 itself; > 0 = the start is y = x0 + d with d in delta
 };
 __device__ __forceinline__ unsigned pass_bytes(const PassIn& in) {
     switch (in.kind) {
         case kIter: return 4 * SZ_H + 2 * SZ_O;
-        case kInit1: return (in.hu > 0 ? 5 : 3) * SZ_H;
+        case kInit1: return 3 * SZ_H + (in.hu > 0 ? 2 * SZ_O : 0);
         case kInit2: return 2 * SZ_H;
         default: return 5 * SZ_H;
     }
@@ -542,7 +541,7 @@ __device__ bool produce(const Common& C, Ring& R, const PassIn& in, int from, in
                 case kInit1:
                     tma_load4(dst, &M->states, xh, yh, k, (int)in.zx, bar);
                     tma_load3(dst + OFF_A, &M->alpha, xh, yh, k, bar);
-                    if (in.hu > 0) tma_load4(dst + OFF_B, &M->ring[in.ring], xh, yh, k, 0, bar);
+                    if (in.hu > 0) tma_load4(dst + OFF_P, &M->pd, x0, y0, k, 0, bar);
                     break;
                 case kInit2:
                     tma_load3(dst, &M->u0, xh, yh, k, bar);
@@ -807,64 +806,31 @@ __device__ __forceinline__ void exact_sink(float rob, float hc, float lc, float&
     sl += te + pe;
 }
 
-// ---- init 1: the start of the increment, d (extrapolated from the ring), and
-// the residual of y = x0 + d, r0 = e - d - (A - I) y, error-free up to its final
-// rounding: y is formed as a compensated pair at every cell that needs it and
-// (A - I) y and d are accumulated with TwoProd / TwoSum, so r0 is accurate
-// relative to itself however small it is against x0 or d.  u0 = M^{-1} r0,
-// delta = d.
+// ---- init 1: the residual of the start y = x0 + d (d = 0 or the predicted
+// increment, see add_state), r0 = e - d - (A - I) y, formed error-free up to
+// its final rounding: (A - I) y from the compensated pairs y through TwoProd /
+// TwoSum, then d by TwoSum, so r0 is accurate relative to itself however small
+// it is against x0 or d.  u0 = M^{-1} r0; delta = d (already there when d != 0).
 template <class RhsFn>
 struct Init1Body {
     const Common& C;
     RhsFn& rhs;
     Acc<3>& acc;
-    int hu, nw;                        // increments used; ring slot (0/1) of the newest one
+    int hu;                            // 0: y = x0, d = 0
     float hm[4], lm[4], am[4];         // plane k-1: y as (hi, lo), alpha
-    float hc[4], lc[4], ac[4], dc[4];  // plane k: y, alpha, d
-    float hp[4], lp[4], ap[4], dn[4];  // plane k+1
+    float hc[4], lc[4], ac[4];
+    float hp[4], lp[4], ap[4];
     float czm[4], czp[4];
-    __device__ Init1Body(const Common& c, RhsFn& r, Acc<3>& a, int hu_, int nw_)
-        : C(c), rhs(r), acc(a), hu(hu_), nw(nw_) {}
-    // d at the quad / one cell at halo-box index h of a stage (ring slots 4-5)
-    __device__ __forceinline__ void pred4(const unsigned char* st, int h, float (&d)[4]) const {
-        if (hu == 0) { set4(d, 0.f); return; }
-        float n[4];
-        ld4(st, sl(4 + nw), h, n);
-        if (hu == 1) { cpy4(d, n); return; }
-        float o[4];
-        ld4(st, sl(5 - nw), h, o);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) d[j] = fmaf(2.f, n[j], -o[j]);
-    }
-    __device__ __forceinline__ float pred1(const unsigned char* st, int h) const {
-        if (hu == 0) return 0.f;
-        const float n = lds1(st, sl(4 + nw), h);
-        return hu == 1 ? n : fmaf(2.f, n, -lds1(st, sl(5 - nw), h));
-    }
-    // y = x0 + d as a compensated pair at the quad / one cell
-    __device__ __forceinline__ void y4(const unsigned char* st, int h, float (&yh)[4], float (&yl)[4],
-                                       float (&d)[4]) const {
-        float xh[4], xl[4];
-        ld4(st, sl(0), h, xh);
-        ld4(st, sl(1), h, xl);
-        pred4(st, h, d);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) add_pair(xh[j], xl[j], d[j], yh[j], yl[j]);
-    }
-    __device__ __forceinline__ void y4(const unsigned char* st, int h, float (&yh)[4], float (&yl)[4]) const {
-        float d[4];
-        y4(st, h, yh, yl, d);
-    }
-    __device__ __forceinline__ void y1(const unsigned char* st, int h, float& yh, float& yl) const {
-        add_pair(lds1(st, sl(0), h), lds1(st, sl(1), h), pred1(st, h), yh, yl);
-    }
+    __device__ Init1Body(const Common& c, RhsFn& r, Acc<3>& a, int hu_) : C(c), rhs(r), acc(a), hu(hu_) {}
     __device__ __forceinline__ void reset() { set4(hm, 0.f); set4(lm, 0.f); set4(am, 0.f); set4(czm, 0.f); }
     __device__ __forceinline__ void below(const unsigned char* st, int hb) {
-        y4(st, hb, hm, lm);
+        ld4(st, sl(0), hb, hm);
+        ld4(st, sl(1), hb, lm);
         ld4(st, sl(3), hb, am);
     }
     __device__ __forceinline__ void own(const unsigned char* st, int hb, bool has_below) {
-        y4(st, hb, hc, lc, dc);
+        ld4(st, sl(0), hb, hc);
+        ld4(st, sl(1), hb, lc);
         ld4(st, sl(3), hb, ac);
         if (has_below) {
 #pragma unroll
@@ -872,27 +838,28 @@ struct Init1Body {
         }
     }
     __device__ __forceinline__ void above(const unsigned char* st, int hb) {
-        y4(st, hb, hp, lp, dn);
+        ld4(st, sl(0), hb, hp);
+        ld4(st, sl(1), hb, lp);
         ld4(st, sl(3), hb, ap);
 #pragma unroll
         for (int j = 0; j < 4; ++j) czp[j] = face(ac[j], ap[j], C.kz);
     }
-    __device__ __forceinline__ void top() {
-        set4(hp, 0.f); set4(lp, 0.f); set4(ap, 0.f); set4(dn, 0.f); set4(czp, 0.f);
-    }
+    __device__ __forceinline__ void top() { set4(hp, 0.f); set4(lp, 0.f); set4(ap, 0.f); set4(czp, 0.f); }
     __device__ __forceinline__ void plane(int k, unsigned c, bool valid, const unsigned char* st,
-                                          const unsigned char*, int hb, int) {
+                                          const unsigned char*, int hb, int ob) {
         if (!valid) return;
         const Geo& g = C.g;
-        float hym[4], lym[4], hyp[4], lyp[4], cx[5], cyp[4], cym[4];
-        y4(st, hb - HB, hym, lym);
-        y4(st, hb + HB, hyp, lyp);
-        float hxl, lxl, hxr, lxr;
-        y1(st, hb - 1, hxl, lxl);
-        y1(st, hb + 4, hxr, lxr);
+        float hym[4], lym[4], hyp[4], lyp[4], cx[5], cyp[4], cym[4], d[4] = {0.f, 0.f, 0.f, 0.f};
+        ld4(st, sl(0), hb - HB, hym);
+        ld4(st, sl(1), hb - HB, lym);
+        ld4(st, sl(0), hb + HB, hyp);
+        ld4(st, sl(1), hb + HB, lyp);
+        if (hu > 0) ld4(st, OFF_D, ob, d);
+        const float hxl = lds1(st, sl(0), hb - 1), lxl = lds1(st, sl(1), hb - 1);
+        const float hxr = lds1(st, sl(0), hb + 4), lxr = lds1(st, sl(1), hb + 4);
         quad_faces(st, hb, ac, C.kx, C.ky, cx, cyp, cym);
         const float rob = k + 1 == g.nz ? C.robin : 0.f;
-        float u[4];
+        float u[4], s0 = 0.f, s1 = 0.f, s2 = 0.f;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             float sh = 0.f, sx = 0.f;
@@ -903,26 +870,29 @@ struct Init1Body {
             exact_term(czp[j], hc[j], lc[j], hp[j], lp[j], sh, sx);
             exact_term(czm[j], hc[j], lc[j], hm[j], lm[j], sh, sx);
             exact_sink(rob, hc[j], lc[j], sh, sx);
-            {   // + d
+            if (hu > 0) {   // + d
                 float t, te;
-                two_sum(sh, dc[j], t, te);
+                two_sum(sh, d[j], t, te);
                 sh = t;
                 sx += te;
             }
             const float e = rhs(c + j, k);
             const float r = (e - sh) - sx;
             u[j] = rcp_approx(diag(cx[j + 1], cx[j], cyp[j], cym[j], czp[j], czm[j], rob)) * r;
-            const float b = ((hc[j] - dc[j]) + lc[j]) + e;   // x0 + e, for ||b||
-            acc.add(0, b * b);
-            acc.add(1, r * u[j]);
-            acc.add(2, r * r);
+            const float b = ((hc[j] - d[j]) + lc[j]) + e;   // x0 + e, for ||b||
+            s0 += b * b;
+            s1 += r * u[j];
+            s2 += r * r;
         }
+        acc.add(0, s0);
+        acc.add(1, s1);
+        acc.add(2, s2);
         stg4(C.v.u[0] + c, u);
-        stg4(C.v.delta + c, dc);
+        if (hu == 0) stg4(C.v.delta + c, d);
     }
     __device__ __forceinline__ void shift() {
         cpy4(hm, hc); cpy4(lm, lc); cpy4(czm, czp);
-        cpy4(hc, hp); cpy4(lc, lp); cpy4(ac, ap); cpy4(dc, dn);
+        cpy4(hc, hp); cpy4(lc, lp); cpy4(ac, ap);
     }
 };
 
@@ -1192,52 +1162,42 @@ __device__ void plain_pass(const Common& C, int cur, const Step& S, Acc<3>& acc)
 // `pre`: early copies of the first pass (TMA path; see Pipe).  In thread 0:
 // *it_out iterations, *rel_out ||r|| / ||b||, *conv_out whether the stop test
 // passed.  Returns false if a barrier or a stage wait failed.
-// Start of one solve's increment (see FwdTiled): ring slot nw holds the newest
-// increment, hu of them are used.
-struct Pred {
-    const float* ring;   // [2][N]
-    int map;             // 0 forward, 1 adjoint ring (TMA descriptor)
-    int nw;
+// Start of one solve: y = x0 + d as compensated pairs (hi at y, lo at y + N);
+// hu == 0: y is the state x0 itself and d = 0; hu > 0: d is in delta (both
+// written by the previous step's add_state, or by prepare_start).
+struct Start {
+    const float* y;
     int hu;
 };
 
 template <bool kTma, class RhsFn>
-__device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, const Pred& pr,
-                      const float* __restrict__ x0, const float* __restrict__ x0lo, RhsFn rhs, int* it_out,
-                      float* rel_out, bool* conv_out) {
+__device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, const Start& st0, RhsFn rhs,
+                      int* it_out, float* rel_out, bool* conv_out) {
     const Geo& g = C.g;
     Pipe pp = pipe_none();
-    // ---- init 1: d, r0 = e - d - (A - I)(x0 + d), u0 = M^{-1} r0, delta = d ; bb, (r0,u0), (r0,r0)
+    // ---- init 1: r0 = e - d - (A - I) y, u0 = M^{-1} r0 ; bb, (r0,u0), (r0,r0)
     Acc<3> acc3;
     if constexpr (kTma) {
-        PassIn in{kInit1, 0, false, 0u, 0u, pr.map, pr.hu};
-        if (!slab_half(C, x0, &in.zx)) return false;
-        Init1Body<RhsFn> B(C, rhs, acc3, pr.hu, pr.nw);
+        PassIn in{kInit1, 0, false, 0u, 0u, st0.hu};
+        if (!slab_half(C, st0.y, &in.zx)) return false;
+        Init1Body<RhsFn> B(C, rhs, acc3, st0.hu);
         if (!staged(C, ring, in, B, pre.n, pre.ok)) return false;
     } else {
         const unsigned N = g.S * (unsigned)g.nz;
-        const float* __restrict__ rn = pr.ring + (size_t)pr.nw * N;
-        const float* __restrict__ ro = pr.ring + (size_t)(pr.nw ^ 1) * N;
-        auto dpred = [&](unsigned q) { return pr.hu == 0 ? 0.f : (pr.hu == 1 ? rn[q] : fmaf(2.f, rn[q], -ro[q])); };
+        const float* __restrict__ yh = st0.y;
+        const float* __restrict__ yl = st0.y + N;
         for_cells(g, [&](int k, unsigned c, int x, int y) {
             const Nb n = neighbours(g, c, x, y, k);
             const float ac = C.alpha[c];
             float cf[6];
             cell_faces(C, n, ac, cf);
             const float rob = k + 1 == g.nz ? C.robin : 0.f;
-            // y = x0 + d as compensated pairs; r0 = e - d - (A - I) y error-free
-            const float d = dpred(c);
-            float fc, lc;
-            add_pair(x0[c], x0lo[c], d, fc, lc);
+            const float fc = yh[c], lc = yl[c];
+            const float d = st0.hu > 0 ? C.v.delta[c] : 0.f;
             float sh = 0.f, sx = 0.f;
 #pragma unroll
             for (int i = 0; i < 6; ++i)
-                if (n.m >> i & 1u) {
-                    const unsigned q = n.q[i];
-                    float hq, lq;
-                    add_pair(x0[q], x0lo[q], dpred(q), hq, lq);
-                    exact_term(cf[i], fc, lc, hq, lq, sh, sx);
-                }
+                if (n.m >> i & 1u) exact_term(cf[i], fc, lc, yh[n.q[i]], yl[n.q[i]], sh, sx);
             exact_sink(rob, fc, lc, sh, sx);
             {
                 float t, te;
@@ -1250,7 +1210,7 @@ __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, co
             const float u = rcp_approx(diag(cf[0], cf[1], cf[2], cf[3], cf[4], cf[5], rob)) * r;
             C.v.u[0][c] = u;
             C.v.delta[c] = d;
-            const float b = (x0[c] + x0lo[c]) + e;
+            const float b = ((fc - d) + lc) + e;
             acc3.add(0, b * b);
             acc3.add(1, r * u);
             acc3.add(2, r * r);
@@ -1369,8 +1329,6 @@ __device__ __forceinline__ void prefetch_maps(const TmaMaps& M) {
     tma_prefetch_desc(&M.alpha);
     tma_prefetch_desc(&M.pd);
     tma_prefetch_desc(&M.states);
-    tma_prefetch_desc(&M.ring[0]);
-    tma_prefetch_desc(&M.ring[1]);
 }
 
 __device__ __forceinline__ Sync make_sync(DevCtl* ctl, double* partials) {
@@ -1383,20 +1341,30 @@ __device__ __forceinline__ Sync make_sync(DevCtl* ctl, double* partials) {
     return s;
 }
 
-// y = x + d as compensated pairs (hi in [0, N), lo in [N, 2N)), and d into
-// the ring slot rd, by every thread of the grid; quads when N % 4 == 0.  Ends
-// with the proxy fence that orders these stores before later TMA reads.
-__device__ void add_state(const float* __restrict__ x, const float* __restrict__ d, float* __restrict__ y,
-                          unsigned N, float* __restrict__ rd) {
+// The increment prediction of the next solve from its newest increment dn and
+// the one before, dold: hu = 1 repeats dn, hu = 2 extrapolates linearly.
+__device__ __forceinline__ float predict(int hu, float dn, float dold) {
+    return hu == 1 ? dn : fmaf(2.f, dn, -dold);
+}
+
+// End of a solve, by every thread of the grid (quads when N % 4 == 0):
+//   y = x + delta as compensated pairs (hi in [0, N), lo in [N, 2N)), the new state;
+//   rd = delta, the ring slot of this step's increment;
+//   when the next solve predicts (hu_next > 0): d = predict(delta, rold),
+//   delta = d and ys = y + d (the next start, as pairs).
+// Ends with the proxy fence that orders these stores before later TMA reads.
+__device__ void add_state(const float* __restrict__ x, float* __restrict__ delta, float* __restrict__ y,
+                          unsigned N, float* __restrict__ rd, const float* __restrict__ rold, int hu_next,
+                          float* __restrict__ ys) {
     const unsigned stride = gridDim.x * NT, t0 = blockIdx.x * NT + threadIdx.x;
     if ((N & 3u) == 0) {
         const unsigned N4 = N >> 2;
         const float4* xh = reinterpret_cast<const float4*>(x);
         const float4* xl = reinterpret_cast<const float4*>(x + N);
-        const float4* d4 = reinterpret_cast<const float4*>(d);
+        float4* d4 = reinterpret_cast<float4*>(delta);
         float4* yh = reinterpret_cast<float4*>(y);
         float4* yl = reinterpret_cast<float4*>(y + N);
-#pragma unroll 2
+#pragma unroll 4
         for (unsigned i = t0; i < N4; i += stride) {
             const float4 h = xh[i], l = xl[i], e = d4[i];
             float4 oh, ol;
@@ -1407,12 +1375,50 @@ __device__ void add_state(const float* __restrict__ x, const float* __restrict__
             yh[i] = oh;
             yl[i] = ol;
             reinterpret_cast<float4*>(rd)[i] = e;
+            if (hu_next > 0) {
+                const float4 o = reinterpret_cast<const float4*>(rold)[i];
+                const float4 dn = make_float4(predict(hu_next, e.x, o.x), predict(hu_next, e.y, o.y),
+                                              predict(hu_next, e.z, o.z), predict(hu_next, e.w, o.w));
+                float4 sh, sl;
+                add_pair(oh.x, ol.x, dn.x, sh.x, sl.x);
+                add_pair(oh.y, ol.y, dn.y, sh.y, sl.y);
+                add_pair(oh.z, ol.z, dn.z, sh.z, sl.z);
+                add_pair(oh.w, ol.w, dn.w, sh.w, sl.w);
+                d4[i] = dn;
+                reinterpret_cast<float4*>(ys)[i] = sh;
+                reinterpret_cast<float4*>(ys + N)[i] = sl;
+            }
         }
     } else {
         for (unsigned c = t0; c < N; c += stride) {
-            add_pair(x[c], x[N + c], d[c], y[c], y[N + c]);
-            rd[c] = d[c];
+            const float e = delta[c];
+            float oh, ol;
+            add_pair(x[c], x[N + c], e, oh, ol);
+            y[c] = oh;
+            y[N + c] = ol;
+            rd[c] = e;
+            if (hu_next > 0) {
+                const float dn = predict(hu_next, e, rold[c]);
+                delta[c] = dn;
+                add_pair(oh, ol, dn, ys[c], ys[N + c]);
+            }
         }
+    }
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// The start of a launch's first solve when it predicts (the previous step ran
+// in another launch): d = predict(rn, rold), delta = d, ys = x + d as pairs;
+// every thread of the grid, then the proxy fence.  The same arithmetic as
+// add_state, so a launch resumed from a checkpoint starts from the same bits.
+__device__ void prepare_start(const float* __restrict__ x, const float* __restrict__ rn,
+                              const float* __restrict__ rold, int hu, float* __restrict__ delta,
+                              float* __restrict__ ys, unsigned N) {
+    const unsigned stride = gridDim.x * NT, t0 = blockIdx.x * NT + threadIdx.x;
+    for (unsigned c = t0; c < N; c += stride) {
+        const float dn = predict(hu, rn[c], rold[c]);
+        delta[c] = dn;
+        add_pair(x[c], x[N + c], dn, ys[c], ys[N + c]);
     }
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
@@ -1444,21 +1450,21 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(const __grid_constant__ F
     const unsigned c0 = blockIdx.x * NT + threadIdx.x;
     double loss = 0.0;
     Pipe pre = pipe_none();
-    // increments of steps n0-1, n0-2 from a checkpoint (recompute launches)
+    // increments used by the start of step n (ring slot (m & 1) holds delta^m)
+    auto hu_at = [&](int n) { return min(a.extrap, min(a.hist0 + (n - a.n0), 2)); };
+    auto slot = [&](int m) { return a.ring + (size_t)(m & 1) * N; };
+    // increments of steps n0-1, n0-2 from a checkpoint (recompute launches),
+    // copied by the same threads that read them below
     if (a.ring_load) {
-        float* s_new = a.ring + (size_t)((a.n0 - 1) & 1) * N;
-        float* s_old = a.ring + (size_t)(a.n0 & 1) * N;
         for (unsigned i = c0; i < N; i += stride) {
-            s_new[i] = a.ring_load[i];
-            s_old[i] = a.ring_load[N + i];
+            slot(a.n0 - 1)[i] = a.ring_load[i];
+            slot(a.n0 - 2)[i] = a.ring_load[N + i];
         }
-        asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+    if (hu_at(a.n0) > 0) {
+        prepare_start(a.src[0], slot(a.n0 - 1), slot(a.n0 - 2), hu_at(a.n0), a.c.v.delta, a.ystart, N);
         if (!barrier(sy)) return;
     }
-    auto pred_at = [&](int n) {   // the start of step n's solve
-        const int hist = min(a.hist0 + (n - a.n0), 2);
-        return Pred{a.ring, 0, (n - 1) & 1, min(a.extrap, hist)};
-    };
     for (int n = a.n0; n < a.n1; ++n) {
         // states are compensated pairs: hi in [0, N), lo in [N, 2N)
         const float* __restrict__ Tn = a.src[n - a.n0];
@@ -1468,7 +1474,8 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(const __grid_constant__ F
         int it = 0;
         float rel = 0.f;
         bool conv = true;
-        bool ok = solve<kTma>(a.c, sy, ring, pre, pred_at(n), Tn, Tn + N,
+        const int hu = hu_at(n);
+        bool ok = solve<kTma>(a.c, sy, ring, pre, Start{hu > 0 ? a.ystart : Tn, hu},
                         [&](unsigned c, int k) { return (qmap && k == 0) ? sc * qmap[c] : 0.f; }, &it, &rel,
                         &conv);
         if (!ok) return;
@@ -1477,17 +1484,18 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(const __grid_constant__ F
             a.c.resid[n - a.n0] = rel;
             if (!conv) atomicAdd(&a.c.ctl->notconv, 1);
         }
-        // T^{n+1} = T^n + delta, kept as a compensated pair; delta^n into the ring
-        add_state(Tn, a.c.v.delta, Tn1, N, a.ring + (size_t)(n & 1) * N);
+        // T^{n+1} = T^n + delta as a compensated pair, delta^n into the ring, and
+        // the start of step n+1 when it predicts
+        const int hu1 = n + 1 < a.n1 ? hu_at(n + 1) : 0;
+        add_state(Tn, a.c.v.delta, Tn1, N, slot(n), slot(n - 1), hu1, a.ystart);
         if (!barrier(sy)) return;
         if (a.ring_save && a.ring_save[n - a.n0])   // a checkpoint keeps [delta^n; delta^{n-1}]
-            copy2(a.ring_save[n - a.n0], a.ring + (size_t)(n & 1) * N, a.ring + (size_t)((n - 1) & 1) * N, N);
+            copy2(a.ring_save[n - a.n0], slot(n), slot(n - 1), N);
         pre = pipe_none();
         if constexpr (kTma) {   // the next step's first pass, behind the frame below
             if (n + 1 < a.n1) {
-                const Pred pn = pred_at(n + 1);
-                PassIn in{kInit1, 0, false, 0u, 0u, 0, pn.hu};
-                if (!slab_half(a.c, a.src[n + 1 - a.n0], &in.zx)) return;
+                PassIn in{kInit1, 0, false, 0u, 0u, hu1};
+                if (!slab_half(a.c, hu1 > 0 ? a.ystart : a.src[n + 1 - a.n0], &in.zx)) return;
                 pre = pipe_start(a.c, ring, in);
             }
         }
@@ -1520,6 +1528,17 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ A
     const Geo& g = a.c.g;
     const unsigned N = g.S * (unsigned)g.nz, S = g.S;
     const float gs = a.g_scale;
+    const unsigned stride = gridDim.x * NT;
+    const unsigned c0 = blockIdx.x * NT + threadIdx.x;
+    (void)stride;
+    (void)c0;
+    // increments used by the start of step n (ring slot (m & 1) holds mu^m - mu^{m+1})
+    auto hu_at = [&](int n) { return min(a.extrap, min(a.hist0 + (a.n1 - n), 2)); };
+    auto slot = [&](int m) { return a.ring + (size_t)(m & 1) * N; };
+    if (hu_at(a.n1) > 0) {
+        prepare_start(a.mu[(a.n1 + 1) & 1], slot(a.n1 + 1), slot(a.n1 + 2), hu_at(a.n1), a.c.v.delta, a.ystart, N);
+        if (!barrier(sy)) return;
+    }
     for (int n = a.n1; n > a.n0; --n) {
         const float* __restrict__ Tn = a.T[n - a.n0];
         const float* __restrict__ mnext = a.mu[(n + 1) & 1];
@@ -1528,8 +1547,8 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ A
         int it = 0;
         float rel = 0.f;
         bool conv = true;
-        const Pred pr{a.ring, 1, (n + 1) & 1, min(a.extrap, min(a.hist0 + (a.n1 - n), 2))};
-        bool ok = solve<kTma>(a.c, sy, ring, pipe_none(), pr, mnext, mnext + N,
+        const int hu = hu_at(n);
+        bool ok = solve<kTma>(a.c, sy, ring, pipe_none(), Start{hu > 0 ? a.ystart : mnext, hu},
                         [&](unsigned c, int) {
                             return (c >= a.obs_off && c < a.obs_off + S)
                                        ? gs * ((Tn[c] - ob[c - a.obs_off]) + Tn[N + c]) : 0.f;
@@ -1541,7 +1560,7 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ A
             a.c.resid[a.n1 - n] = rel;
             if (!conv) atomicAdd(&a.c.ctl->notconv, 1);
         }
-        add_state(mnext, a.c.v.delta, mu, N, a.ring + (size_t)(n & 1) * N);   // mu^n - mu^{n+1}
+        add_state(mnext, a.c.v.delta, mu, N, slot(n), slot(n + 1), n - 1 > a.n0 ? hu_at(n - 1) : 0, a.ystart);
         if (!barrier(sy)) return;
         // gradient of step n with mu^n and T^n (the next step writes only the
         // other mu buffer and the CG vectors, so no barrier is needed after it)
@@ -1639,7 +1658,7 @@ int tiled_grid_blocks(int device) {
 // Tensor maps of the staged passes (see TmaMaps).  The encoder comes from the
 // driver through the runtime's entry-point query, so no libcuda link is needed.
 bool tiled_encode_maps(tiled::TmaMaps* M, const tiled::Geo& g, const tiled::Vecs& v, const float* alpha,
-                       const float* slab, unsigned slab_halves, const float* ring_fwd, const float* ring_adj) {
+                       const float* slab, unsigned slab_halves) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         void* fn = nullptr;
@@ -1668,8 +1687,7 @@ bool tiled_encode_maps(tiled::TmaMaps* M, const tiled::Geo& g, const tiled::Vecs
     bool ok = true;
     for (int i = 0; i < 2; ++i) ok = ok && make(&M->uws[i], v.u[i], HB, HR, 3, 3);
     ok = ok && make(&M->u0, v.u[0], HB, HR, 0, 1) && make(&M->alpha, alpha, HB, HR, 0, 1) &&
-         make(&M->pd, v.p, tiled::TX, tiled::TY, 2, 2) && make(&M->states, slab, HB, HR, slab_halves, 2) &&
-         make(&M->ring[0], ring_fwd, HB, HR, 2, 2) && make(&M->ring[1], ring_adj, HB, HR, 2, 2);
+         make(&M->pd, v.p, tiled::TX, tiled::TY, 2, 2) && make(&M->states, slab, HB, HR, slab_halves, 2);
     return ok;
 }
 

@@ -170,8 +170,6 @@ struct TmaMaps {
     CUtensorMap pd;        // p, delta (2 x N floats, contiguous): 4D, box 32 x 32 x 1 x 2 at (x0, y0, k, 0)
     CUtensorMap states;    // the state slab as 4D (x, y, z, halves): box 40 x 34 x 1 x 2 at
                            //   (x0-4, y0-1, k, h) reads the hi and lo halves of the state at half h
-    CUtensorMap ring[2];   // increment rings of the forward (0) and adjoint (1) sweeps, 4D (x, y, z, 2):
-                           //   box 40 x 34 x 1 x 2 at (x0-4, y0-1, k, 0) reads both slots
 };
 
 struct Common {
@@ -200,11 +198,14 @@ struct Common {
 // sweep holds its increment of step m (forward: T^{m+1} - T^m; adjoint:
 // mu^m - mu^{m+1}).  With h usable increments the start is x0 + d, d = 0
 // (h = 0), the newest increment (h = 1) or twice the newest minus the older
-// (h = 2); h = min(extrap, increments available).
+// (h = 2); h = min(extrap, increments available).  The end of each solve
+// writes the next start y = x0 + d (compensated pairs, a slot of the state
+// slab) and d (into delta).
 struct FwdTiled {
     Common c;
     int n0, n1;
     float* ring;              // [2][N]
+    float* ystart;            // [2][N] the next solve's start y = x0 + d (a slot of the state slab)
     int extrap;               // 0, 1, 2
     int hist0;                // increments valid at launch start (steps n0-1, n0-2)
     const float* ring_load;   // [delta^{n0-1}; delta^{n0-2}] copied in at launch start, or null
@@ -223,6 +224,7 @@ struct AdjTiled {
     Common c;
     int n0, n1;
     float* ring;              // [2][N] adjoint increments
+    float* ystart;            // as FwdTiled::ystart
     int extrap;
     int hist0;                // increments valid at launch start (steps n1+1, n1+2)
     float* const* T;
@@ -266,7 +268,7 @@ int tiled_grid_blocks(int device);
 int tiled_dynamic_smem();
 // Fill `maps` for the given device buffers; false if the driver refused.
 bool tiled_encode_maps(tiled::TmaMaps* maps, const tiled::Geo& g, const tiled::Vecs& v, const float* alpha,
-                       const float* slab, unsigned slab_halves, const float* ring_fwd, const float* ring_adj);
+                       const float* slab, unsigned slab_halves);
 cudaError_t launch_forward_tiled(const tiled::FwdTiled& a, int grid, cudaStream_t s);
 cudaError_t launch_adjoint_tiled(const tiled::AdjTiled& a, int grid, cudaStream_t s);
 // out[i] = in[i].x + in[i].y (the tiled gradient accumulator to FP32).
