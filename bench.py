@@ -63,8 +63,10 @@ def parse():
     ap.add_argument("--ckpt-every", type=int, default=0)
     ap.add_argument("--cpu-sample-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="inversion", choices=["inversion", "serving"],
-                    help="inversion: the timed inversion step (default); serving: latency of a job stream")
+    ap.add_argument("--workload", default="inversion", choices=["inversion", "serving", "stress"],
+                    help="inversion: the timed inversion step (default); serving: latency of a job stream; "
+                         "stress: one forward + adjoint at 512x512x96, 2000 steps, sqrt-checkpointing")
+    ap.add_argument("--stress-fp64", action="store_true", help="stress: also run the FP64 path and compare")
     ap.add_argument("--serve-scale", default="small", choices=["small", "full"],
                     help="serving stream: small (24 jobs, <= 192x160x40, 50-200 steps, 3-step inversions) "
                          "or full (64 jobs at 4/s, grids up to 256x256x64, 200-1000 steps, 10-step inversions)")
@@ -465,12 +467,70 @@ def run_serving(args):
     return 0
 
 
+# ------------------------------------------------------------------ stress
+def run_stress(args):
+    """The largest configuration: 512x512x96 cells, 2000 steps of dt = 0.2,
+    8 layers with 20 one-cell delaminations, checkpoint stride chosen by the
+    memory budget (every state kept does not fit, so about sqrt(nt)).  One
+    forward + adjoint gradient, timed with the library's CUDA events; device
+    memory the call holds; recompute overhead; with --stress-fp64 the FP64 path
+    on the same inputs and the agreement of the two gradients."""
+    import torch
+    from paper_2603_11045_gb300 import synthetic as S
+    from paper_2603_11045_gb300.solver import Problem, Solver
+    w = S.layered_delamination_case()
+    solver = Solver(0)
+    res = {}
+    for prec in (["fp32", "fp64"] if args.stress_fp64 else ["fp32"]):
+        dt = torch.float32 if prec == "fp32" else torch.float64
+        p = Problem.from_workload(w, prec=prec, rtol=1e-13 if prec == "fp64" else 0.0)
+        q = torch.tensor(w.q_face, dtype=dt, device="cuda")
+        obs = solver.forward(p, torch.tensor(w.alpha_target, dtype=dt, device="cuda"), q_face=q,
+                             q_steps=w.q_steps)["frames"]
+        a = torch.tensor(w.alpha, dtype=dt, device="cuda")
+        free0 = torch.cuda.mem_get_info()[0]
+        t0 = time.perf_counter()
+        out = solver.adjoint_grad(p, a, obs, q_face=q, q_steps=w.q_steps)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        st = out["stats"]
+        dev_ms = st["fwd_ms"] + st["adj_ms"] + st["recompute_ms"]
+        res[prec] = (out, {"prec": prec, "wall_s": wall, "device_ms": dev_ms,
+                           "gcell_steps_per_s": w.n_cells * w.nt / (dev_ms / 1e3) / 1e9,
+                           "ckpt_every": st["ckpt_every"], "states_held": st["n_checkpoints"],
+                           "workspace_gb": st["workspace_bytes"] / 1e9,
+                           "device_free_gb_before": free0 / 1e9,
+                           "recompute_overhead": st["recompute_ms"] / max(1e-9, st["fwd_ms"] + st["adj_ms"]),
+                           "iters": {"fwd": st["fwd_iters"], "recompute": st["recompute_iters"],
+                                     "adj": st["adj_iters"]},
+                           "fwd_ms": st["fwd_ms"], "recompute_ms": st["recompute_ms"], "adj_ms": st["adj_ms"],
+                           "loss": out["loss"]})
+        del obs, a, q
+        torch.cuda.empty_cache()
+    line = {"metric": "stress fwd+adjoint Gcell-steps/s", "value": res["fp32"][1]["gcell_steps_per_s"],
+            "unit": "Gcell-steps/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"stress: {w.nx}x{w.ny}x{w.nz} cells, {w.nt} steps dt={w.dt}, 8 layers + 20 "
+                                   "delaminations, Gaussian pulse 3 steps, checkpoint stride by memory budget"},
+            "fp32": res["fp32"][1]}
+    if "fp64" in res:
+        g32, g64 = res["fp32"][0]["grad_alpha"].double(), res["fp64"][0]["grad_alpha"]
+        line["fp64"] = res["fp64"][1]
+        line["fp32_vs_fp64"] = {"grad_rel_l2": float((g32 - g64).norm() / g64.norm()),
+                                "grad_cosine": float((g32 * g64).sum() / (g32.norm() * g64.norm())),
+                                "loss_rel": abs(res["fp32"][1]["loss"] - res["fp64"][1]["loss"]) / abs(res["fp64"][1]["loss"])}
+    solver.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "stress":
+        return run_stress(args)
     return run_native(args)
 
 
