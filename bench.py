@@ -225,6 +225,19 @@ def field_launches(spec):
     return ev + bw + 1              # + TV
 
 
+def aggregate(total_ms, units_per_rank, world, device):
+    """Whole-job figures of a replica run: the slowest rank's time (all-reduce
+    MAX over the process group when world > 1) and the units all ranks
+    processed per second, in billions.  Returns (max_ms, value)."""
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    return max_ms, units_per_rank * world / (max_ms / 1000.0) / 1e9
+
+
 def run_native(args):
     import torch
     import torch.distributed as dist
@@ -305,12 +318,7 @@ def run_native(args):
     f_fwd = [e[0].elapsed_time(e[1]) for e, _ in field_ms[-args.steps:]]
     f_bwd = [e[2].elapsed_time(e[3]) for e, _ in field_ms[-args.steps:]]
     total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
-    units = w.n_cells * w.nt * args.steps * world
-    value = units / (max_ms / 1000.0) / 1e9
+    max_ms, value = aggregate(total_ms, w.n_cells * w.nt * args.steps, world, dev)
 
     # roofline of the fused CG kernel (forward + adjoint + recompute launches)
     R = args.prec
