@@ -70,7 +70,9 @@ def parse():
     ap.add_argument("--serve-scale", default="small", choices=["small", "full"],
                     help="serving stream: small (24 jobs, <= 192x160x40, 50-200 steps, 3-step inversions) "
                          "or full (64 jobs at 4/s, grids up to 256x256x64, 200-1000 steps, 10-step inversions)")
-    ap.add_argument("--serve-lanes", type=int, default=2)
+    ap.add_argument("--serve-lanes", type=int, default=8, help="job slots of the batched server")
+    ap.add_argument("--serve-unbatched-lanes", type=int, default=2,
+                    help="lanes of the comparison replay in which each lane runs its own grid")
     ap.add_argument("--serve-no-fp64", action="store_true", help="skip the one-at-a-time FP64 replay")
     return ap.parse_args()
 
@@ -399,8 +401,12 @@ def run_native(args):
 def run_serving(args):
     """Replay a Poisson stream of ragged forward / inversion jobs through the
     serving queue (arrival times honoured on the host clock) and report the
-    submit-to-done latency percentiles from the library's timestamps; then the
-    same stream one job at a time (one lane), in FP32 and in FP64."""
+    submit-to-done latency percentiles from the library's timestamps: served
+    with batched launches (the running jobs' sweeps in one persistent grid),
+    served on lanes that each run their own grid, and one job at a time in
+    FP32 and in FP64.  The forward jobs' surface frames of the batched FP32
+    replay are compared with those of the FP64 one (surface-temperature
+    error at which the latencies are compared)."""
     import torch
     from paper_2603_11045_gb300 import synthetic as S
     from paper_2603_11045_gb300.serve import Server
@@ -425,9 +431,9 @@ def run_serving(args):
         inputs.append((j, w, p, a, q, obs))
     torch.cuda.synchronize()
 
-    def replay(lanes, prec):
+    def replay(lanes, prec, batched, keep_frames=False):
         dt = torch.float32 if prec == "fp32" else torch.float64
-        srv = Server(solver, lanes=lanes)
+        srv = Server(solver, lanes=lanes, batched=batched)
         jobs_in = [(j, w, p.with_(prec=prec), a.to(dt), q.to(dt), None if o is None else o.to(dt))
                    for (j, w, p, a, q, o) in inputs]
         # warm-up: one short job per lane (workspace, kernel modules)
@@ -435,9 +441,15 @@ def run_serving(args):
                 for _ in range(lanes)]
         for i in warm:
             srv.wait(i)
+        frames = {}
+        if keep_frames:
+            for k, (j, w, p, a, q, o) in enumerate(jobs_in):
+                if j["kind"] == "forward":
+                    frames[k] = torch.empty(p.nt, p.ny, p.nx, dtype=dt, device="cuda")
+        torch.cuda.synchronize()
         t0 = time.monotonic()
         ids = []
-        for (j, w, p, a, q, o) in jobs_in:
+        for k, (j, w, p, a, q, o) in enumerate(jobs_in):
             delay = t0 + j["arrival_s"] - time.monotonic()
             if delay > 0:
                 time.sleep(delay)
@@ -445,7 +457,7 @@ def run_serving(args):
                 ids.append(srv.submit(p, a.clone(), kind="inversion", iters=inv_iters, lr=1.0, alpha_floor=0.01,
                                       q_face=q, q_steps=w.q_steps, obs=o))
             else:
-                ids.append(srv.submit(p, a, q_face=q, q_steps=w.q_steps))
+                ids.append(srv.submit(p, a, q_face=q, q_steps=w.q_steps, frames_out=frames.get(k)))
         res = [srv.wait(i, timeout=3600) for i in ids]
         srv.stop()
         bad = [r for r in res if r["state_name"] != "done"]
@@ -454,13 +466,25 @@ def run_serving(args):
         span = (max(r["t_done_ns"] for r in res) - min(r["t_submit_ns"] for r in res)) / 1e9
         cell_steps = sum(j["nx"] * j["ny"] * j["nz"] * j["nt"] * (1 if j["kind"] == "forward" else 2 * inv_iters)
                          for j in jobs)
-        return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-                "mean_s": float(lat.mean()), "max_queue_wait_s": float(wait.max()), "makespan_s": span,
-                "gcell_steps_per_s": cell_steps / span / 1e9, "lanes": lanes, "prec": prec, "failed": len(bad)}
+        out = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+               "mean_s": float(lat.mean()), "max_queue_wait_s": float(wait.max()), "makespan_s": span,
+               "gcell_steps_per_s": cell_steps / span / 1e9, "lanes": lanes, "prec": prec, "batched": batched,
+               "failed": len(bad)}
+        if batched:
+            out["launches_per_job_mean"] = float(np.mean([r["launches"] for r in res]))
+            out["jobs_sharing_launches"] = int(sum(r["shared_launches"] > 0 for r in res))
+        return out, frames
 
-    served = replay(args.serve_lanes, "fp32")
-    single = replay(1, "fp32")
-    fp64 = None if args.serve_no_fp64 else replay(1, "fp64")
+    served, fr32 = replay(args.serve_lanes, "fp32", True, keep_frames=not args.serve_no_fp64)
+    lanes_only, _ = replay(args.serve_unbatched_lanes, "fp32", False)
+    single, _ = replay(1, "fp32", False)
+    fp64, surf = None, None
+    if not args.serve_no_fp64:
+        fp64, fr64 = replay(1, "fp64", False, keep_frames=True)
+        errs = [float((fr32[k].double() - fr64[k]).norm() / fr64[k].norm()) for k in fr32]
+        surf = {"forward_jobs": len(errs), "max_rel_l2": max(errs), "median_rel_l2": float(np.median(errs))}
+        del fr64
+    del fr32
     solver.close()
     n_fwd = sum(j["kind"] == "forward" for j in jobs)
     line = {"metric": "serving p99 latency", "value": served["p99_s"], "unit": "s", "n_gpus": 1,
@@ -470,7 +494,8 @@ def run_serving(args):
                                    f"grids {sorted({(j['nx'], j['ny'], j['nz']) for j in jobs})}, "
                                    f"{min(j['nt'] for j in jobs)}-{max(j['nt'] for j in jobs)} steps",
                        "lanes": args.serve_lanes},
-            "served": served, "one_at_a_time_fp32": single, "one_at_a_time_fp64": fp64}
+            "served": served, "served_unbatched_lanes": lanes_only, "one_at_a_time_fp32": single,
+            "one_at_a_time_fp64": fp64, "surface_fp32_batched_vs_fp64": surf}
     print(json.dumps(line), flush=True)
     return 0
 

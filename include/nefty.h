@@ -241,15 +241,23 @@ nefty_status nefty_forward_static(int device, const nefty_problem *p, const void
 /* ------------------------------------------------------------------ serving
  * Continuous batching of ragged jobs (forward sweeps and short inversions on
  * grids of any size) behind a non-blocking queue.  nefty_serve_start attaches
- * a server to a handle; `lanes` worker threads, each with its own CUDA stream,
- * its own workspace and a fixed share of the SMs (so that the lanes'
- * persistent solver grids are resident side by side), take queued jobs in
- * arrival order as soon as they are free.  Each lane owns mem_budget_bytes /
- * lanes of device memory; a job's checkpoint stride is chosen within that share
- * (every state kept when it fits, about sqrt(nt) checkpoints otherwise, as for
- * ckpt_every = 0), and a job that cannot fit even then is refused at submit
- * with NEFTY_ENOMEM.  A job's results depend only on the job and the lane share
- * (the same bits alone or among other jobs).
+ * a server to a handle; `lanes` worker threads (job slots), each with its own
+ * CUDA stream and workspace, take queued jobs in arrival order as soon as they
+ * are free.  Each lane owns mem_budget_bytes / lanes of device memory; a job's
+ * checkpoint stride is chosen within that share (every state kept when it
+ * fits, about sqrt(nt) checkpoints otherwise, as for ckpt_every = 0), and a job
+ * that cannot fit even then is refused at submit with NEFTY_ENOMEM.
+ *
+ * Batched (the default): the FP32 sweeps of all running jobs whose grids have
+ * zero-flux walls and nx % 4 == 0 run together in ONE persistent launch over
+ * the whole device, whatever their grid sizes and step counts; each sweep is
+ * cut into chunks (chunk_steps), and a launch carries the next
+ * chunk of every running job, so a newly admitted job joins the launch that
+ * follows.  Other sweeps (FP64, periodic walls, nx % 4 != 0) and unbatched
+ * servers (batched = -1) run each lane's own persistent grid on 1 / lanes of
+ * the SMs, resident beside the others.  Either way a job's results depend only
+ * on the job and the server's configuration: the same bits alone or among
+ * other jobs.
  *
  * Job kinds:
  *   NEFTY_JOB_FORWARD    nefty_forward on the job's arrays (frames_out, loss when obs given).
@@ -294,12 +302,17 @@ typedef struct {
     uint64_t t_admit_ns;
     uint64_t t_done_ns;
     double loss;                /* see NEFTY_JOB_INVERSION; forward: the loss when obs was given */
+    int32_t launches;           /* batched launches that carried the job's sweeps */
+    int32_t shared_launches;    /* ... of which carried other jobs' sweeps too */
 } nefty_job_result;
 
 typedef struct {
     int32_t lanes;              /* concurrent jobs, 1..16 (0 = 2) */
     int32_t max_queue;          /* queued-job limit for NEFTY_EBUSY (0 = 4096) */
     uint64_t mem_budget_bytes;  /* device memory shared by the lanes (0 = 80% of free memory) */
+    int32_t batched;            /* 0 or 1: batched launches (see above); -1: each lane its own grid */
+    int32_t chunk_steps;        /* batched: time steps of a sweep per launch (0 = about 2^25 cell-steps,
+                                   at least 4); smaller chunks admit new jobs sooner */
 } nefty_serve_config;
 
 /* Start serving on h's device (cfg may be NULL for the defaults).

@@ -64,14 +64,16 @@ class nefty_job(ctypes.Structure):
 class nefty_job_result(ctypes.Structure):
     _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("lane", ctypes.c_int32),
                 ("iters_done", ctypes.c_int32), ("t_submit_ns", ctypes.c_uint64), ("t_admit_ns", ctypes.c_uint64),
-                ("t_done_ns", ctypes.c_uint64), ("loss", ctypes.c_double)]
+                ("t_done_ns", ctypes.c_uint64), ("loss", ctypes.c_double), ("launches", ctypes.c_int32),
+                ("shared_launches", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class nefty_serve_config(ctypes.Structure):
-    _fields_ = [("lanes", ctypes.c_int32), ("max_queue", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_uint64)]
+    _fields_ = [("lanes", ctypes.c_int32), ("max_queue", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_uint64),
+                ("batched", ctypes.c_int32), ("chunk_steps", ctypes.c_int32)]
 
 
 class NeftyError(RuntimeError):

@@ -24,11 +24,19 @@ struct nefty_handle {
     int grid_max[2] = {0, 0};
     int grid_tiled = 0;
     int grid_share = 1;          // the persistent grids use 1/grid_share of the device (serving lanes)
+    nefty::Batcher* batch = nullptr;   // serving: TMA-staged sweeps run in the batcher's shared launches
+    int batch_launches = 0;      // launches that carried this handle's sweeps
+    int batch_shared = 0;        // ... of which carried other handles' sweeps too
     nefty::Server* server = nullptr;
     std::string err;
 };
 
 void nefty::set_grid_share(nefty_handle* h, int share) { h->grid_share = share > 1 ? share : 1; }
+void nefty::set_batcher(nefty_handle* h, Batcher* b) { h->batch = b; }
+void nefty::batch_counts(nefty_handle* h, int* launches, int* shared) {
+    *launches = h->batch_launches;
+    *shared = h->batch_shared;
+}
 
 static thread_local std::string t_err;
 
@@ -205,8 +213,14 @@ int grid_for(nefty_handle* h, int prec, unsigned N) {
     return (int)std::min<long>(want, gmax);
 }
 
+// Whether the tiled kernels stage this problem through TMA (zero-flux walls,
+// 16-byte row pitch); the encoder may still refuse (see prepare_tma).
+bool tma_grid(const Prob& P) { return P.bc == NEFTY_BC_NEUMANN && P.nx % 4 == 0; }
+
 int grid_for_tiled(nefty_handle* h, const Prob& P) {
     if (h->grid_tiled == 0) h->grid_tiled = tiled_grid_blocks(h->device);
+    // batched sweeps all run on the batcher's grid
+    if (h->batch && tma_grid(P)) return batcher_grid(h->batch);
     const int gmax = std::max(1, h->grid_tiled / h->grid_share);
     const long tiles = (long)((P.nx + tiled::TX - 1) / tiled::TX) * ((P.ny + tiled::TY - 1) / tiled::TY);
     const long units = tiles * P.nz;
@@ -319,7 +333,7 @@ struct Call {
     bool use_tma = false;
     nefty_status prepare_tma() {
         if constexpr (kTiled) {
-            if (P.bc != NEFTY_BC_NEUMANN || P.nx % 4 != 0) return NEFTY_OK;
+            if (!tma_grid(P)) return NEFTY_OK;
             tiled::Geo g{};
             g.nx = P.nx; g.ny = P.ny; g.nz = P.nz; g.S = P.S;
             if (!tiled_encode_maps(&host_maps, g, tv, (const float*)alpha.dev, (const float*)slab, slab_halves))
@@ -418,18 +432,78 @@ struct Call {
         c.resid = rs;
         return c;
     }
+    // Batched sweeps (serving): a sweep is cut into chunks of a few time
+    // steps, so that a launch of the batcher stays short and newly admitted
+    // jobs join the next one; the chunks of a sweep ride consecutive launches,
+    // and the call's stream continues after the last.
+    int batch_chunk() const { return batcher_chunk(h->batch, P.N); }
+    nefty_status run_batched(std::vector<tiled::BatchSweep>& chunks) {
+        int launched = 0, shared = 0;
+        std::string why;
+        const nefty_status e = batcher_run(h->batch, chunks, G, s, &launched, &shared, &why);
+        h->batch_launches += launched;
+        h->batch_shared += shared;
+        launches += (int)chunks.size() - 1;
+        if (e != NEFTY_OK) return fail(h, e, why);
+        return NEFTY_OK;
+    }
+    nefty_status batched_fwd(const tiled::FwdTiled& a) {
+        // the chunks add their frame losses into loss_partials
+        if (a.loss_partials) NEFTY_CUDA(h, cudaMemsetAsync(a.loss_partials, 0, (size_t)G * sizeof(double), s));
+        std::vector<tiled::BatchSweep> chunks;
+        for (int m0 = a.n0; m0 < a.n1; m0 += batch_chunk()) {
+            tiled::BatchSweep w{};
+            w.adjoint = 0;
+            w.f = a;
+            w.f.n0 = m0;
+            w.f.n1 = std::min(a.n1, m0 + batch_chunk());
+            w.f.src = a.src + (m0 - a.n0);
+            w.f.dst = a.dst + (m0 - a.n0);
+            w.f.hist0 = std::min(a.hist0 + (m0 - a.n0), 2);
+            w.f.ring_load = m0 == a.n0 ? a.ring_load : nullptr;
+            w.f.ring_save = a.ring_save ? a.ring_save + (m0 - a.n0) : nullptr;
+            w.f.c.iters = a.c.iters + (m0 - a.n0);
+            w.f.c.resid = a.c.resid + (m0 - a.n0);
+            chunks.push_back(w);
+        }
+        return run_batched(chunks);
+    }
+    nefty_status batched_adj(const tiled::AdjTiled& a) {
+        std::vector<tiled::BatchSweep> chunks;
+        for (int m1 = a.n1; m1 > a.n0; m1 -= batch_chunk()) {
+            tiled::BatchSweep w{};
+            w.adjoint = 1;
+            w.a = a;
+            w.a.n1 = m1;
+            w.a.n0 = std::max(a.n0, m1 - batch_chunk());
+            w.a.T = a.T + (w.a.n0 - a.n0);
+            w.a.hist0 = std::min(a.hist0 + (a.n1 - m1), 2);
+            w.a.c.iters = a.c.iters + (a.n1 - m1);
+            w.a.c.resid = a.c.resid + (a.n1 - m1);
+            chunks.push_back(w);
+        }
+        return run_batched(chunks);
+    }
     nefty_status launch_fwd_tiled(const tiled::FwdTiled& a, int kind) {
         NEFTY_CUDA(h, cudaMemsetAsync(&ctl->bar, 0, sizeof(unsigned), s));
         Timed t;
         if (nefty_status e = begin_timed(kind, &t)) return e;
-        NEFTY_CUDA(h, launch_forward_tiled(a, G, s));
+        if (h->batch && use_tma) {
+            if (nefty_status e = batched_fwd(a)) return e;
+        } else {
+            NEFTY_CUDA(h, launch_forward_tiled(a, G, s));
+        }
         return end_timed(t);
     }
     nefty_status launch_adj_tiled(const tiled::AdjTiled& a) {
         NEFTY_CUDA(h, cudaMemsetAsync(&ctl->bar, 0, sizeof(unsigned), s));
         Timed t;
         if (nefty_status e = begin_timed(2, &t)) return e;
-        NEFTY_CUDA(h, launch_adjoint_tiled(a, G, s));
+        if (h->batch && use_tma) {
+            if (nefty_status e = batched_adj(a)) return e;
+        } else {
+            NEFTY_CUDA(h, launch_adjoint_tiled(a, G, s));
+        }
         return end_timed(t);
     }
     // forward launch over steps [n0, n1) with either kernel family

@@ -23,8 +23,9 @@
 // CTA-wide barrier.  A thread that needs u_{i+1} at a neighbour cell forms it
 // again from the staged values with the same fused multiply-adds as the
 // cell's owner, so every thread sees the same bits.  The passes that run once
-// per solve (initial residual, first product, gradient) and grids that TMA
-// cannot stage (periodic walls, nx % 4 != 0) read global memory directly.
+// per solve (initial residual, first product, gradient) are staged the same
+// way; grids that TMA cannot stage (periodic walls, nx % 4 != 0) read global
+// memory directly.
 //
 // Numerics: the stencil is evaluated in flux form, A v = v + sum_f c_f (v_c - v_q)
 // (+ Robin sink), and each solve accumulates its increment delta separately so
@@ -1597,6 +1598,369 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ A
     }
 }
 
+// ------------------------------------------------------------- batched sweeps
+// Serving runs the sweeps of several jobs (forward or adjoint, ragged grids)
+// in one persistent launch.  Each sweep keeps the step sequence of its own
+// launch (forward_tiled / adjoint_tiled) and runs it as a state machine: per
+// grid-wide pass every unfinished sweep does its next pass over its own
+// units (split over all CTAs as in a launch of its own), then one grid
+// barrier and one reduction serve every sweep's inner products.  A sweep's
+// arithmetic, its reduction order and the split of its units depend only on
+// the sweep and the grid size, so its results are the same bits alone or in
+// any mix.  Only TMA-staged sweeps are batched.
+enum SwPhase : int { kSwPrep, kSwInit1, kSwInit2, kSwIter, kSwAdd, kSwTail, kSwDone };
+
+struct SwState {
+    int ph;      // the sweep's next pass
+    int n;       // step of the current solve
+    int post;    // the previous step's post-work is due (frames and ring save; gradient)
+    int it, cur; // CG iterations so far; ping-pong index of the iteration inputs
+    float a, b;  // step lengths of the next iteration pass
+};
+struct SwScalars {   // CG scalars of the current solve (thread 0)
+    DF bb, lim, gam, rho, al;
+};
+
+__device__ __forceinline__ int sw_nv(int ph) { return ph == kSwInit1 || ph == kSwIter ? 3 : (ph == kSwInit2 ? 1 : 0); }
+
+__device__ __forceinline__ int fwd_hu(const FwdTiled& a, int n) { return min(a.extrap, min(a.hist0 + (n - a.n0), 2)); }
+__device__ __forceinline__ int adj_hu(const AdjTiled& a, int n) { return min(a.extrap, min(a.hist0 + (a.n1 - n), 2)); }
+
+__device__ __forceinline__ SwState sw_begin(const BatchSweep& w) {
+    SwState s{};
+    if (w.adjoint) {
+        s.n = w.a.n1;
+        s.ph = w.a.n1 <= w.a.n0 ? kSwDone : (adj_hu(w.a, w.a.n1) > 0 ? kSwPrep : kSwInit1);
+    } else {
+        s.n = w.f.n0;
+        s.ph = w.f.n1 <= w.f.n0 ? kSwDone : ((w.f.ring_load || fwd_hu(w.f, w.f.n0) > 0) ? kSwPrep : kSwInit1);
+    }
+    return s;
+}
+
+// One side of a staged pass: the compute threads consume, the copy thread
+// (threadIdx.x == NCT) produces; no other thread calls this.
+template <class Body>
+__device__ __forceinline__ bool stage_side(const Common& C, Ring& R, const PassIn& in, Body& B) {
+    if (threadIdx.x < NCT) return consume(C.g, R, B);
+    return produce(C, R, in, 0, 1 << 30);
+}
+
+// The staged passes both kinds share: the first product and an iteration.
+__device__ bool sw_cg_side(const Common& C, const SwState& st, Ring& ring, Acc<3>& acc) {
+    if (st.ph == kSwInit2) {
+        Acc<1> acc1;
+        Init2Body Bd(C, acc1);
+        const bool ok = stage_side(C, ring, PassIn{kInit2, 0, false, 0u, 0u}, Bd);
+        acc.h[0] = acc1.h[0];
+        acc.l[0] = acc1.l[0];
+        return ok;
+    }
+    Step S;
+    S.a = st.a;
+    S.bt = st.b;
+    S.first = st.it == 0;
+    IterBody Bd(C, S, st.cur, acc);
+    return stage_side(C, ring, PassIn{kIter, st.cur, S.first, 0u, 0u}, Bd);
+}
+
+// The staged work of a sweep in one grid-wide pass (compute threads and the
+// copy thread): the adjoint's gradient of the step just updated, then the
+// solve's pass (initial residual, first product or iteration).
+__device__ bool sw_staged(const BatchSweep& w, const SwState& st, Ring& ring, Acc<3>& acc) {
+    if (w.adjoint) {
+        const AdjTiled& a = w.a;
+        const unsigned N = a.c.g.S * (unsigned)a.c.g.nz, S = a.c.g.S;
+        if (st.post) {   // gradient of step m with mu^m and T^m
+            const int m = st.n + 1;
+            PassIn in{kGrad, 0, false, 0u, 0u};
+            if (!slab_half(a.c, a.T[m - a.n0], &in.zx) || !slab_half(a.c, a.mu[m & 1], &in.zm)) return false;
+            GradBody Bd;
+            Bd.grad = a.grad;
+            Bd.wx = a.wx; Bd.wy = a.wy; Bd.wz = a.wz;
+            Bd.nz = a.c.g.nz;
+            if (!stage_side(a.c, ring, in, Bd)) return false;
+        }
+        if (st.ph == kSwInit1) {
+            const int n = st.n, hu = adj_hu(a, n);
+            const float* __restrict__ Tn = a.T[n - a.n0];
+            const float* ob = a.obs + (size_t)(n - 1) * S;
+            const float gs = a.g_scale;
+            auto rhs = [&](unsigned c, int) {
+                return (c >= a.obs_off && c < a.obs_off + S) ? gs * ((Tn[c] - ob[c - a.obs_off]) + Tn[N + c]) : 0.f;
+            };
+            PassIn in{kInit1, 0, false, 0u, 0u, hu};
+            if (!slab_half(a.c, hu > 0 ? a.ystart : a.mu[(n + 1) & 1], &in.zx)) return false;
+            Init1Body<decltype(rhs)> Bd(a.c, rhs, acc, hu);
+            return stage_side(a.c, ring, in, Bd);
+        }
+        if (st.ph == kSwInit2 || st.ph == kSwIter) return sw_cg_side(a.c, st, ring, acc);
+        return true;
+    }
+    const FwdTiled& a = w.f;
+    if (st.ph == kSwInit1) {
+        const int n = st.n, hu = fwd_hu(a, n);
+        const unsigned S = a.c.g.S;
+        const float* qmap = a.q_full ? a.q_full + (size_t)n * S : (n < a.q_steps ? a.q_face : nullptr);
+        const float sc = a.src_scale;
+        auto rhs = [&](unsigned c, int k) { return (qmap && k == 0) ? sc * qmap[c] : 0.f; };
+        PassIn in{kInit1, 0, false, 0u, 0u, hu};
+        if (!slab_half(a.c, hu > 0 ? a.ystart : a.src[n - a.n0], &in.zx)) return false;
+        Init1Body<decltype(rhs)> Bd(a.c, rhs, acc, hu);
+        return stage_side(a.c, ring, in, Bd);
+    }
+    if (st.ph == kSwInit2 || st.ph == kSwIter) return sw_cg_side(a.c, st, ring, acc);
+    return true;
+}
+
+// The unstaged work of a sweep in one grid-wide pass (every thread, after
+// the staged work of all sweeps): the forward's ring save and frame of the
+// step just updated, the start of a launch, the state update.
+__device__ void sw_unstaged(const BatchSweep& w, const SwState& st, double& loss) {
+    const unsigned stride = gridDim.x * NT, c0 = blockIdx.x * NT + threadIdx.x;
+    if (w.adjoint) {
+        const AdjTiled& a = w.a;
+        const unsigned N = a.c.g.S * (unsigned)a.c.g.nz;
+        auto slot = [&](int m) { return a.ring + (size_t)(m & 1) * N; };
+        if (st.ph == kSwPrep) {
+            prepare_start(a.mu[(a.n1 + 1) & 1], slot(a.n1 + 1), slot(a.n1 + 2), adj_hu(a, a.n1), a.c.v.delta,
+                          a.ystart, N);
+        } else if (st.ph == kSwAdd) {
+            const int n = st.n;
+            add_state(a.mu[(n + 1) & 1], a.c.v.delta, a.mu[n & 1], N, slot(n), slot(n + 1),
+                      n - 1 > a.n0 ? adj_hu(a, n - 1) : 0, a.ystart);
+        }
+        return;
+    }
+    const FwdTiled& a = w.f;
+    const unsigned N = a.c.g.S * (unsigned)a.c.g.nz, S = a.c.g.S;
+    auto slot = [&](int m) { return a.ring + (size_t)(m & 1) * N; };
+    if (st.post) {   // step m has ended: ring save and frame of T^{m+1}
+        const int m = st.n - 1;
+        const float* Tn1 = a.dst[m - a.n0];
+        if (a.ring_save && a.ring_save[m - a.n0]) copy2(a.ring_save[m - a.n0], slot(m), slot(m - 1), N);
+        if (a.frames || a.obs) {
+            for (unsigned s = c0; s < S; s += stride) {
+                const float v = Tn1[a.obs_off + s];
+                if (a.frames) a.frames[(size_t)m * S + s] = v;
+                if (a.obs) {
+                    const double e = ((double)v - (double)a.obs[(size_t)m * S + s]) + (double)Tn1[N + a.obs_off + s];
+                    loss += e * e;
+                }
+            }
+        }
+    }
+    if (st.ph == kSwPrep) {
+        if (a.ring_load) {
+            for (unsigned i = c0; i < N; i += stride) {
+                slot(a.n0 - 1)[i] = a.ring_load[i];
+                slot(a.n0 - 2)[i] = a.ring_load[N + i];
+            }
+        }
+        if (fwd_hu(a, a.n0) > 0)
+            prepare_start(a.src[0], slot(a.n0 - 1), slot(a.n0 - 2), fwd_hu(a, a.n0), a.c.v.delta, a.ystart, N);
+    } else if (st.ph == kSwAdd) {
+        const int n = st.n;
+        const int hu1 = n + 1 < a.n1 ? fwd_hu(a, n + 1) : 0;
+        add_state(a.src[n - a.n0], a.c.v.delta, a.dst[n - a.n0], N, slot(n), slot(n - 1), hu1, a.ystart);
+    }
+}
+
+// The end of a solve (thread 0): iterations, relative residual and the
+// not-converged count of the sweep.
+__device__ void sw_record(const Common& C, int idx, int it, const SwScalars& q) {
+    const bool conv = df_le(q.rho, q.lim);
+    if (blockIdx.x == 0) {
+        C.iters[idx] = it;
+        C.resid[idx] = q.bb.hi > 0.f ? sqrtf(q.rho.hi / q.bb.hi) : 0.f;
+        if (!conv) atomicAdd(&C.ctl->notconv, 1);
+    }
+}
+
+// The sweep's state after a pass whose sums are t[0..2] (thread 0); the same
+// decisions as solve() and the step loops of the sweep kernels.
+__device__ void sw_advance(const BatchSweep& w, SwState& s, SwScalars& q, const DF* t) {
+    const Common& C = w.adjoint ? w.a.c : w.f.c;
+    const int idx = w.adjoint ? w.a.n1 - s.n : s.n - w.f.n0;
+    const bool was_add = s.ph == kSwAdd;
+    switch (s.ph) {
+        case kSwPrep:
+            s.ph = kSwInit1;
+            break;
+        case kSwInit1:
+            q.bb = t[0];
+            q.lim = df_mul(DF{C.tol2_hi, C.tol2_lo}, q.bb);
+            q.gam = t[1];
+            q.rho = t[2];
+            s.it = 0;
+            if (!df_le(q.rho, q.lim) && C.max_iter > 0) {
+                s.ph = kSwInit2;
+            } else {
+                sw_record(C, idx, 0, q);
+                s.ph = kSwAdd;
+            }
+            break;
+        case kSwInit2:
+            q.al = df_div(q.gam, t[0]);
+            s.a = q.al.hi;
+            s.b = 0.f;
+            s.cur = 0;
+            s.ph = kSwIter;
+            break;
+        case kSwIter: {
+            ++s.it;
+            s.cur ^= 1;
+            q.rho = t[2];
+            if (!(df_le(q.rho, q.lim) || s.it >= C.max_iter)) {
+                const DF gam_new = t[0];
+                const DF beta = df_div(gam_new, q.gam);
+                q.al = df_div(gam_new, df_add(t[1], df_neg(df_div(df_mul(beta, gam_new), q.al))));
+                q.gam = gam_new;
+                s.a = q.al.hi;
+                s.b = beta.hi;
+            } else {
+                sw_record(C, idx, s.it, q);
+                s.ph = kSwAdd;
+            }
+            break;
+        }
+        case kSwAdd:
+            if (w.adjoint) {
+                s.n -= 1;
+                s.ph = s.n > w.a.n0 ? kSwInit1 : kSwTail;
+            } else {
+                s.n += 1;
+                s.ph = s.n < w.f.n1 ? kSwInit1 : kSwTail;
+            }
+            break;
+        default:
+            s.ph = kSwDone;
+            break;
+    }
+    // the post-work of a step runs at the start of the pass after its update
+    s.post = was_add ? 1 : 0;
+}
+
+// One grid barrier and the grid-wide sums of the first nv values of the
+// per-warp partials wh/wl (compensated, the same order as grid_sum for every
+// value).  Every CTA gets the totals in tot[0, nv).
+__device__ bool batch_sum(Sync& g, int nv, float (*wh)[kBatchRed], float (*wl)[kBatchRed], DF* tot) {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    float2* part = reinterpret_cast<float2*>(g.partials) + (size_t)(g.red & 1u) * kBatchRed * g.G;
+    for (int i = warp; i < nv; i += NW) {
+        float hi = lane < NW ? wh[lane][i] : 0.f, lo = lane < NW ? wl[lane][i] : 0.f;
+        warp_sum2(hi, lo);
+        if (lane == 0) part[(size_t)blockIdx.x * kBatchRed + i] = make_float2(hi, lo);
+    }
+    if (!barrier(g)) return false;
+    for (int i = warp; i < nv; i += NW) {
+        float2 v[kMaxGrid / 32];
+#pragma unroll
+        for (int r = 0; r < kMaxGrid / 32; ++r) {
+            const unsigned b = lane + 32u * r;
+            v[r] = b < g.G ? part[(size_t)b * kBatchRed + i] : make_float2(0.f, 0.f);
+        }
+        float hi = 0.f, lo = 0.f;
+#pragma unroll
+        for (int r = 0; r < kMaxGrid / 32; ++r) {
+            float sh, e;
+            two_sum(hi, v[r].x, sh, e);
+            hi = sh;
+            lo = lo + v[r].y + e;
+        }
+        warp_sum2(hi, lo);
+        if (lane == 0) tot[i] = df_make(hi, lo);
+    }
+    g.red += 1;
+    __syncthreads();
+    return true;
+}
+
+static_assert(sizeof(BatchArgs) <= 32764, "kernel parameter space");
+
+__global__ void __launch_bounds__(NT, 1) batch_tiled(const __grid_constant__ BatchArgs B) {
+    extern __shared__ unsigned char dyn_smem[];
+    __shared__ __align__(8) unsigned long long s_full[NS], s_empty[NS];
+    __shared__ SwState s_st[kMaxBatch];
+    __shared__ SwScalars s_q[kMaxBatch];
+    __shared__ float s_wh[NW][kBatchRed], s_wl[NW][kBatchRed];
+    __shared__ DF s_tot[kBatchRed];
+    Ring ring = make_ring(dyn_smem, s_full, s_empty, true);
+    const int ns = min(B.n, kMaxBatch);
+    if (threadIdx.x == NCT)
+        for (int j = 0; j < ns; ++j) prefetch_maps(B.s[j].adjoint ? B.s[j].a.c.maps : B.s[j].f.c.maps);
+    Sync sy = make_sync(B.ctl, B.partials);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double loss[kMaxBatch];
+    for (int j = 0; j < kMaxBatch; ++j) loss[j] = 0.0;
+    if (threadIdx.x == 0)
+        for (int j = 0; j < ns; ++j) s_st[j] = sw_begin(B.s[j]);
+    for (int i = threadIdx.x; i < NW * kBatchRed; i += NT) {   // the copy warp's row stays zero
+        s_wh[i / kBatchRed][i % kBatchRed] = 0.f;
+        s_wl[i / kBatchRed][i % kBatchRed] = 0.f;
+    }
+    __syncthreads();
+    bool ok = true;
+    while (true) {
+        int live = 0, nv = 0;
+        for (int j = 0; j < ns; ++j)
+            if (s_st[j].ph != kSwDone) {
+                ++live;
+                nv = 3 * (j + 1);
+            }
+        if (live == 0) break;
+        // staged work of every sweep: the copy thread streams their planes
+        // back to back, the compute warps consume them in the same order
+        if (threadIdx.x < NCT || threadIdx.x == NCT) {
+            for (int j = 0; j < ns && ok; ++j) {
+                const SwState st = s_st[j];
+                Acc<3> acc;
+                if (st.ph != kSwDone) ok = sw_staged(B.s[j], st, ring, acc);
+                if (threadIdx.x < NCT) {
+                    ok = __all_sync(0xffffffffu, ok);   // the warp stays together for the sums
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        float hi = acc.h[i], lo = acc.l[i];
+                        warp_sum2(hi, lo);
+                        if (lane == 0) { s_wh[warp][3 * j + i] = hi; s_wl[warp][3 * j + i] = lo; }
+                    }
+                }
+            }
+        }
+        if (__syncthreads_or(ok ? 0 : 1)) {
+            if (threadIdx.x == NCT) drain(ring);
+            ok = false;
+            break;
+        }
+        for (int j = 0; j < ns; ++j) {
+            const SwState st = s_st[j];
+            if (st.ph != kSwDone) sw_unstaged(B.s[j], st, loss[j]);
+        }
+        if (!batch_sum(sy, nv, s_wh, s_wl, s_tot)) { ok = false; break; }
+        if (threadIdx.x == 0)
+            for (int j = 0; j < ns; ++j)
+                if (s_st[j].ph != kSwDone) sw_advance(B.s[j], s_st[j], s_q[j], s_tot + 3 * j);
+        __syncthreads();
+    }
+    if (ok) {
+        for (int j = 0; j < ns; ++j)
+            if (!B.s[j].adjoint && B.s[j].f.loss_partials) {
+                const double t = block_sum(loss[j]);   // chunks of a sweep add up
+                if (threadIdx.x == 0) B.s[j].f.loss_partials[blockIdx.x] += t;
+            }
+    } else if (threadIdx.x == 0) {
+        atomicCAS(&B.ctl->err, kDevOk, kDevTimeout);
+    }
+    // a failed launch fails every sweep in it
+    if (threadIdx.x == 0) {
+        const int e = ld_relaxed(&B.ctl->err);
+        if (e != kDevOk)
+            for (int j = 0; j < ns; ++j) atomicCAS(&(B.s[j].adjoint ? B.s[j].a.c.ctl : B.s[j].f.c.ctl)->err, kDevOk, e);
+    }
+}
+
 }  // namespace tiled
 
 // ------------------------------------------------------------------ host
@@ -1616,6 +1980,13 @@ cudaError_t launch_adjoint_tiled(const tiled::AdjTiled& a, int grid, cudaStream_
     const bool tma = a.c.tma != 0;
     const void* fn = tma ? (const void*)tiled::adjoint_tiled<true> : (const void*)tiled::adjoint_tiled<false>;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(tiled::NT), args, tma ? tiled::DYN_SMEM : 0, s);
+}
+
+cudaError_t launch_batch_tiled(const tiled::BatchArgs& b, int grid, cudaStream_t s) {
+    tiled::BatchArgs copy = b;
+    void* args[] = {&copy};
+    return cudaLaunchCooperativeKernel((const void*)tiled::batch_tiled, dim3(grid), dim3(tiled::NT), args,
+                                       tiled::DYN_SMEM, s);
 }
 
 int tiled_dynamic_smem() { return tiled::DYN_SMEM; }
@@ -1638,16 +2009,17 @@ cudaError_t launch_cast_pairs(const float2* in, float* out, unsigned n, cudaStre
 int tiled_grid_blocks(int device) {
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return 0;
-    const void* tma_fns[2] = {(const void*)tiled::forward_tiled<true>, (const void*)tiled::adjoint_tiled<true>};
-    const void* all_fns[4] = {tma_fns[0], tma_fns[1], (const void*)tiled::forward_tiled<false>,
+    const void* tma_fns[3] = {(const void*)tiled::forward_tiled<true>, (const void*)tiled::adjoint_tiled<true>,
+                              (const void*)tiled::batch_tiled};
+    const void* all_fns[5] = {tma_fns[0], tma_fns[1], tma_fns[2], (const void*)tiled::forward_tiled<false>,
                               (const void*)tiled::adjoint_tiled<false>};
     for (const void* f : tma_fns)
         if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, tiled::DYN_SMEM) != cudaSuccess)
             return 0;
     int per = 2;
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 5; ++i) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, all_fns[i], tiled::NT, i < 2 ? tiled::DYN_SMEM : 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, all_fns[i], tiled::NT, i < 3 ? tiled::DYN_SMEM : 0) !=
             cudaSuccess)
             return 0;
         per = std::min(per, b);

@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "nefty.h"
 
@@ -93,6 +94,7 @@ struct AdjArgs {
 
 // ------------------------------------------------------------ serving (serve.cu)
 class Server;
+class Batcher;
 Server* server_start(int device, const nefty_serve_config* cfg, nefty_status* st, std::string* why);
 void server_stop(Server* s);
 nefty_status server_submit(Server* s, const nefty_job* job, uint64_t* id, std::string* why);
@@ -237,6 +239,26 @@ struct AdjTiled {
     float2* grad;          // dJ/dalpha accumulator: compensated (hi, lo) pairs
 };
 
+// Several sweeps in one persistent launch (serving).  A sweep is the
+// argument block of one forward or adjoint launch; every sweep of a batch
+// advances by one of its passes per grid-wide pass, and the passes of all
+// sweeps share the grid barrier and the reduction that ends each pass.
+constexpr int kMaxBatch = 16;
+constexpr int kBatchRed = 3 * kMaxBatch;   // reduced values per grid-wide pass
+struct BatchSweep {
+    int adjoint;           // 0: f is used, 1: a is used
+    union {
+        FwdTiled f;
+        AdjTiled a;
+    };
+};
+struct BatchArgs {
+    int n;                 // sweeps in s[0, n)
+    DevCtl* ctl;           // barrier counter and error word of the launch
+    double* partials;      // [2][G][kBatchRed] (hi, lo) float pairs
+    BatchSweep s[kMaxBatch];
+};
+
 }  // namespace tiled
 
 // -------------------------------------------------- neural field (field.cu)
@@ -271,6 +293,23 @@ bool tiled_encode_maps(tiled::TmaMaps* maps, const tiled::Geo& g, const tiled::V
                        const float* slab, unsigned slab_halves);
 cudaError_t launch_forward_tiled(const tiled::FwdTiled& a, int grid, cudaStream_t s);
 cudaError_t launch_adjoint_tiled(const tiled::AdjTiled& a, int grid, cudaStream_t s);
+// One batched launch (TMA-staged sweeps only; b.ctl->bar zeroed by the caller).
+cudaError_t launch_batch_tiled(const tiled::BatchArgs& b, int grid, cudaStream_t s);
+// Batched serving launches (serve.cu).  A Batcher owns one stream and runs the
+// sweeps handed to batcher_run from any thread in shared persistent launches
+// (tiled::batch_tiled) on the whole device.
+// api.cu: h's TMA-staged sweeps go to b (null: h launches its own grids);
+// the launches that carried h's sweeps so far, and those shared with others.
+void set_batcher(nefty_handle* h, Batcher* b);
+void batch_counts(nefty_handle* h, int* launches, int* shared);
+int batcher_grid(Batcher* b);
+int batcher_chunk(Batcher* b, unsigned N);   // time steps per chunk of a sweep on N cells
+// Runs the chunks (consecutive parts of one sweep, in order) in launches of b
+// after the work issued on s so far; returns once the last chunk is launched,
+// with s ordered after that launch.  *launches / *shared: launches used, and
+// those that carried other sweeps too.  grid must be batcher_grid(b).
+nefty_status batcher_run(Batcher* b, std::vector<tiled::BatchSweep>& chunks, int grid, cudaStream_t s,
+                         int* launches, int* shared, std::string* why);
 // out[i] = in[i].x + in[i].y (the tiled gradient accumulator to FP32).
 cudaError_t launch_cast_pairs(const float2* in, float* out, unsigned n, cudaStream_t s);
 

@@ -1,17 +1,24 @@
 // Serving: continuous batching of ragged solver jobs behind a non-blocking
 // queue (the nefty_serve_* calls of nefty.h).
 //
-// A Server owns `lanes` worker threads.  Each lane has its own CUDA stream,
-// its own nefty_handle (so its own workspace, budget = total / lanes) and a
-// fixed share of the persistent solver's CTAs (1 / lanes of the SMs), so the
-// lanes' cooperative grids are resident side by side and never wait for one
-// another.  A lane takes the oldest queued job whenever it is free, so jobs of
-// any grid size and length stream through the device continuously.  The job's
-// checkpoint stride follows the lane's memory share (ckpt_every = 0), and
-// submit refuses, with NEFTY_ENOMEM, a job whose smallest workspace does not
-// fit a share.  A job runs only through the public solver calls on its lane's
-// handle, with the lane's fixed CTA count, so its results do not depend on
-// what the other lanes are doing.
+// A Server owns `lanes` worker threads (job slots).  Each lane has its own
+// CUDA stream and its own nefty_handle (so its own workspace, budget = total /
+// lanes), takes the oldest queued job whenever it is free and runs it through
+// the public solver calls on its handle.  The job's checkpoint stride follows
+// the lane's memory share (ckpt_every = 0), and submit refuses, with
+// NEFTY_ENOMEM, a job whose smallest workspace does not fit a share.
+//
+// Batched mode: the lanes' handles hand their TMA-staged FP32 sweeps to one
+// Batcher instead of launching them.  The Batcher thread repeatedly takes the
+// next chunk of every pending sweep (at most kMaxBatch, in arrival order),
+// launches them together as one persistent grid over the whole device
+// (tiled::batch_tiled), and composes the next launch when that one is done, so
+// a job admitted meanwhile joins the next launch.  Ordering: a launch waits
+// for the work each lane issued before its sweep (an event per request), and
+// a lane's stream waits for the launch that carried its sweep's last chunk.
+// Unbatched mode (and the sweeps the batch kernel does not take) runs each
+// lane's own cooperative grid on 1 / lanes of the SMs, resident beside the
+// others.  In both modes a job's results do not depend on the other jobs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -64,7 +71,190 @@ struct Job {
     std::atomic<bool> cancel{false};
 };
 
+// One sweep handed to the Batcher: its chunks, launched in order.
+struct BatchReq {
+    std::vector<tiled::BatchSweep>* chunks = nullptr;
+    size_t next = 0;               // first chunk not launched yet
+    cudaEvent_t ready = nullptr;   // the lane's work before the sweep
+    cudaStream_t stream = nullptr; // the lane's stream, ordered after the last chunk
+    int launches = 0, shared = 0;
+    cudaError_t err = cudaSuccess;
+    bool finished = false;
+};
+
 }  // namespace
+
+class Batcher {
+  public:
+    Batcher(int device, int chunk_steps) : device_(device), chunk_steps_(chunk_steps) {}
+    ~Batcher() { stop(); }
+
+    nefty_status start(std::string* why) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(device_);
+        nefty_status st = NEFTY_OK;
+        grid_ = std::min(tiled_grid_blocks(device_), tiled::kMaxGrid);
+        const size_t part = 2 * (size_t)tiled::kBatchRed * (size_t)std::max(grid_, 1) * sizeof(float2);
+        if (grid_ <= 0) {
+            *why = "cannot size the batched solver grid on this device";
+            st = NEFTY_ECUDA;
+        } else if (cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking) != cudaSuccess ||
+                   cudaEventCreateWithFlags(&done_, cudaEventDisableTiming) != cudaSuccess) {
+            *why = "cannot create the batcher's stream";
+            st = NEFTY_ECUDA;
+        } else if (cudaMalloc(&ctl_, sizeof(DevCtl)) != cudaSuccess || cudaMalloc(&partials_, part) != cudaSuccess) {
+            *why = "cannot allocate the batcher's control block";
+            st = NEFTY_ENOMEM;
+        }
+        cudaGetLastError();
+        cudaSetDevice(cur);
+        if (st != NEFTY_OK) {
+            release();
+            return st;
+        }
+        thread_ = std::thread([this] { main(); });
+        return NEFTY_OK;
+    }
+
+    void stop() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stopping_ = true;
+        }
+        cv_.notify_all();
+        if (thread_.joinable()) thread_.join();
+        release();
+    }
+
+    int grid() const { return grid_; }
+    int chunk(unsigned N) const {
+        if (chunk_steps_ > 0) return chunk_steps_;
+        return std::max(4, (int)std::min(1e6, 33554432.0 / (double)N));
+    }
+
+    nefty_status run(std::vector<tiled::BatchSweep>& chunks, int grid, cudaStream_t s, int* launches,
+                     int* shared, std::string* why) {
+        *launches = *shared = 0;
+        if (chunks.empty()) return NEFTY_OK;
+        if (grid != grid_) {
+            *why = "internal error: a batched sweep was sized for another grid";
+            return NEFTY_ECUDA;
+        }
+        BatchReq r;
+        r.chunks = &chunks;
+        r.stream = s;
+        if (cudaEventCreateWithFlags(&r.ready, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(r.ready, s) != cudaSuccess) {
+            cudaGetLastError();
+            if (r.ready) cudaEventDestroy(r.ready);
+            *why = "cannot record the start of a batched sweep";
+            return NEFTY_ECUDA;
+        }
+        {
+            std::unique_lock<std::mutex> lk(mu_);
+            if (stopping_) {
+                cudaEventDestroy(r.ready);
+                *why = "the batcher is stopping";
+                return NEFTY_EBUSY;
+            }
+            pending_.push_back(&r);
+            cv_.notify_all();
+            cv_.wait(lk, [&] { return r.finished; });
+        }
+        cudaEventDestroy(r.ready);
+        *launches = r.launches;
+        *shared = r.shared;
+        if (r.err != cudaSuccess) {
+            *why = std::string("batched solver launch: ") + cudaGetErrorName(r.err);
+            return NEFTY_ECUDA;
+        }
+        return NEFTY_OK;
+    }
+
+  private:
+    void release() {
+        if (ctl_) cudaFree(ctl_);
+        if (partials_) cudaFree(partials_);
+        if (done_) cudaEventDestroy(done_);
+        if (stream_) cudaStreamDestroy(stream_);
+        ctl_ = nullptr;
+        partials_ = nullptr;
+        done_ = nullptr;
+        stream_ = nullptr;
+    }
+
+    void main() {
+        cudaSetDevice(device_);
+        tiled::BatchArgs args;
+        while (true) {
+            std::vector<BatchReq*> take;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&] { return stopping_ || !pending_.empty(); });
+                if (pending_.empty()) return;   // stopping, nothing left
+                for (BatchReq* r : pending_) {
+                    if ((int)take.size() == tiled::kMaxBatch) break;
+                    take.push_back(r);
+                }
+            }
+            // one launch with the next chunk of every request taken
+            args.n = (int)take.size();
+            args.ctl = ctl_;
+            args.partials = (double*)partials_;
+            cudaError_t e = cudaSuccess;
+            for (int i = 0; i < args.n && e == cudaSuccess; ++i) {
+                args.s[i] = (*take[i]->chunks)[take[i]->next];
+                e = cudaStreamWaitEvent(stream_, take[i]->ready, 0);
+            }
+            if (e == cudaSuccess) e = cudaMemsetAsync(ctl_, 0, sizeof(DevCtl), stream_);
+            if (e == cudaSuccess) e = launch_batch_tiled(args, grid_, stream_);
+            if (e == cudaSuccess) e = cudaEventRecord(done_, stream_);
+            if (e != cudaSuccess) cudaGetLastError();
+            {
+                std::lock_guard<std::mutex> lk(mu_);
+                for (BatchReq* r : take) {
+                    r->next += 1;
+                    r->launches += 1;
+                    if (args.n > 1) r->shared += 1;
+                    if (e != cudaSuccess) r->err = e;
+                    if (e != cudaSuccess || r->next == r->chunks->size()) {
+                        // the lane continues after this launch
+                        if (e == cudaSuccess) cudaStreamWaitEvent(r->stream, done_, 0);
+                        r->finished = true;
+                        pending_.erase(std::find(pending_.begin(), pending_.end(), r));
+                    }
+                }
+                ++launches_;
+            }
+            cv_.notify_all();
+            // the next launch is composed once this one is done, from every
+            // sweep pending by then
+            if (e == cudaSuccess) cudaEventSynchronize(done_);
+        }
+    }
+
+    int device_;
+    int chunk_steps_;
+    int grid_ = 0;
+    cudaStream_t stream_ = nullptr;
+    cudaEvent_t done_ = nullptr;
+    DevCtl* ctl_ = nullptr;
+    void* partials_ = nullptr;
+    std::thread thread_;
+    std::mutex mu_;
+    std::condition_variable cv_;
+    std::deque<BatchReq*> pending_;
+    bool stopping_ = false;
+    long long launches_ = 0;
+};
+
+int batcher_grid(Batcher* b) { return b->grid(); }
+int batcher_chunk(Batcher* b, unsigned N) { return b->chunk(N); }
+nefty_status batcher_run(Batcher* b, std::vector<tiled::BatchSweep>& chunks, int grid, cudaStream_t s,
+                         int* launches, int* shared, std::string* why) {
+    return b->run(chunks, grid, s, launches, shared, why);
+}
 
 class Server {
   public:
@@ -78,6 +268,15 @@ class Server {
         cudaSetDevice(device_);
         nefty_status st = NEFTY_OK;
         const uint64_t share = cfg_.mem_budget_bytes / (uint64_t)cfg_.lanes;
+        if (cfg_.batched >= 0) {
+            batcher_ = std::make_unique<Batcher>(device_, cfg_.chunk_steps);
+            st = batcher_->start(why);
+            if (st != NEFTY_OK) {
+                batcher_.reset();
+                cudaSetDevice(cur);
+                return st;
+            }
+        }
         // the probe handle sizes jobs at submit; it never runs work
         st = nefty_create(&probe_, device_, share);
         for (int l = 0; l < cfg_.lanes && st == NEFTY_OK; ++l) {
@@ -85,6 +284,7 @@ class Server {
             st = nefty_create(&h, device_, share);
             if (st != NEFTY_OK) break;
             set_grid_share(h, cfg_.lanes);
+            if (batcher_) set_batcher(h, batcher_.get());
             handles_.push_back(h);
             cudaStream_t s = nullptr;
             if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
@@ -93,7 +293,10 @@ class Server {
             }
             streams_.push_back(s);
         }
-        if (probe_) set_grid_share(probe_, cfg_.lanes);
+        if (probe_) {
+            set_grid_share(probe_, cfg_.lanes);
+            if (batcher_) set_batcher(probe_, batcher_.get());
+        }
         cudaSetDevice(cur);
         if (st != NEFTY_OK) {
             *why = std::string("cannot set up the serving lanes: ") + nefty_last_error(nullptr);
@@ -211,6 +414,7 @@ class Server {
         handles_.clear();
         if (probe_) nefty_destroy(probe_);
         probe_ = nullptr;
+        batcher_.reset();   // after the lanes, whose sweeps it runs
     }
 
     void finish(Job& j, int state, nefty_status st) {
@@ -244,10 +448,13 @@ class Server {
         const nefty_job& j = job.desc;
         nefty_problem p = j.problem;
         p.ckpt_every = p.ckpt_every > 0 ? p.ckpt_every : 0;
+        int l0 = 0, s0 = 0;
+        batch_counts(h, &l0, &s0);
         if (j.kind == NEFTY_JOB_FORWARD) {
             double loss = 0.0;
             const nefty_status st = nefty_forward(h, &p, j.alpha, j.T0, j.q_face, j.q_steps, j.q_full,
                                                   j.frames_out, nullptr, j.obs, j.obs ? &loss : nullptr, nullptr, s);
+            count_launches(job, h, l0, s0);
             {
                 std::lock_guard<std::mutex> lk(mu_);
                 job.res.loss = loss;
@@ -291,6 +498,7 @@ class Server {
                 project_step_kernel<float><<<blocks, 256, 0, s>>>((float*)a, (const float*)g, (float)j.lr,
                                                                    (float)j.alpha_floor, N);
             if (cudaGetLastError() != cudaSuccess) st = NEFTY_ECUDA;
+            count_launches(job, h, l0, s0);
             std::lock_guard<std::mutex> lk(mu_);
             job.res.loss = loss;
             job.res.iters_done = it + 1;
@@ -305,8 +513,18 @@ class Server {
         else finish(job, st == NEFTY_OK ? NEFTY_JOB_DONE : NEFTY_JOB_FAILED, st);
     }
 
+    // launches of the batcher that carried h's sweeps since (l0, s0)
+    void count_launches(Job& job, nefty_handle* h, int l0, int s0) {
+        int l = 0, sh = 0;
+        batch_counts(h, &l, &sh);
+        std::lock_guard<std::mutex> lk(mu_);
+        job.res.launches = l - l0;
+        job.res.shared_launches = sh - s0;
+    }
+
     int device_;
     nefty_serve_config cfg_;
+    std::unique_ptr<Batcher> batcher_;
     nefty_handle* probe_ = nullptr;
     std::mutex probe_mu_;
     std::vector<nefty_handle*> handles_;
@@ -325,8 +543,9 @@ Server* server_start(int device, const nefty_serve_config* cfg, nefty_status* st
     if (cfg) c = *cfg;
     if (c.lanes == 0) c.lanes = 2;
     if (c.max_queue == 0) c.max_queue = 4096;
-    if (c.lanes < 1 || c.lanes > 16 || c.max_queue < 1) {
-        *why = "need 1 <= lanes <= 16 and max_queue >= 1";
+    if (c.lanes < 1 || c.lanes > tiled::kMaxBatch || c.max_queue < 1 || c.batched < -1 || c.batched > 1 ||
+        c.chunk_steps < 0) {
+        *why = "need 1 <= lanes <= 16, max_queue >= 1, batched in {-1, 0, 1} and chunk_steps >= 0";
         *st = NEFTY_EINVAL;
         return nullptr;
     }

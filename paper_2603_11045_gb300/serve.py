@@ -1,7 +1,8 @@
 """Python face of libnefty's serving queue (nefty_serve_* in include/nefty.h).
 
-``Server`` attaches a queue with ``lanes`` concurrent workers to a ``Solver``'s
-handle.  ``submit`` copies the job description into the library and returns a
+``Server`` attaches a queue with ``lanes`` concurrent workers (job slots) to a
+``Solver``'s handle; with ``batched`` the running jobs' FP32 sweeps share one
+persistent launch.  ``submit`` copies the job description into the library and returns a
 job id at once; the arrays stay referenced here until the job has finished.
 Every step of a job runs in libnefty (its own threads, streams and kernels);
 this module only marshals arguments.
@@ -24,10 +25,12 @@ _FINAL = (N.NEFTY_JOB_DONE, N.NEFTY_JOB_FAILED, N.NEFTY_JOB_CANCELLED)
 
 
 class Server:
-    def __init__(self, solver: Solver, lanes: int = 2, max_queue: int = 0, mem_budget_bytes: int = 0):
+    def __init__(self, solver: Solver, lanes: int = 2, max_queue: int = 0, mem_budget_bytes: int = 0,
+                 batched: bool = True, chunk_steps: int = 0):
         self.solver = solver
         self._lib = solver._lib
-        cfg = N.nefty_serve_config(int(lanes), int(max_queue), int(mem_budget_bytes))
+        cfg = N.nefty_serve_config(int(lanes), int(max_queue), int(mem_budget_bytes), 1 if batched else -1,
+                                   int(chunk_steps))
         N.check(self._lib.nefty_serve_start(solver._h, ctypes.byref(cfg)), solver._h)
         self._keep = {}
 

@@ -1,9 +1,11 @@
 """Serving queue (nefty_serve_*): continuous batching of ragged jobs.
 
-Checks on the GPU that a served job computes what the direct call computes,
-that its results are the same bits alone and among other jobs (each lane has
-a fixed share of the device), that cancellation and refusal work, and that
-the lanes really overlap jobs."""
+Checks on the GPU, with batched launches (the running jobs' sweeps in one
+persistent grid) and with one grid per lane, that a served job computes what
+the direct call computes, that its results are the same bits alone and among
+other jobs, that sweeps cut into many chunks and jobs that cannot be batched
+still give the direct call's results, that cancellation and refusal work, and
+that jobs really overlap on the device."""
 import pytest
 import torch
 
@@ -30,20 +32,23 @@ def solver():
     s.close()
 
 
-def test_forward_job_matches_direct_call(solver):
+@pytest.mark.parametrize("batched", [True, False])
+def test_forward_job_matches_direct_call(solver, batched):
     w, p, alpha, q = _case(64, 48, 16, 40, 3001)
     direct = solver.forward(p, alpha, q_face=q, q_steps=w.q_steps)["frames"]
-    with Server(solver, lanes=2) as srv:
+    with Server(solver, lanes=2, batched=batched) as srv:
         fr = torch.empty_like(direct)
         jid = srv.submit(p, alpha, kind="forward", q_face=q, q_steps=w.q_steps, frames_out=fr)
         r = srv.wait(jid)
     assert r["state_name"] == "done" and r["status"] == 0, r
     assert r["t_submit_ns"] <= r["t_admit_ns"] <= r["t_done_ns"]
+    assert (r["launches"] >= 1) == batched, r
     err = (fr - direct).norm() / direct.norm()
     assert err < 1e-5, float(err)
 
 
-def test_inversion_job_matches_python_loop(solver):
+@pytest.mark.parametrize("batched", [True, False])
+def test_inversion_job_matches_python_loop(solver, batched):
     w, p, alpha, q = _case(48, 48, 12, 30, 3002)
     obs = solver.forward(p, torch.tensor(w.alpha_target, dtype=torch.float32, device="cuda"), q_face=q,
                          q_steps=w.q_steps)["frames"]
@@ -55,7 +60,7 @@ def test_inversion_job_matches_python_loop(solver):
         losses.append(out["loss"])
         ref = torch.clamp(ref - lr * out["grad_alpha"], min=floor)
     a = alpha.clone()
-    with Server(solver, lanes=2) as srv:
+    with Server(solver, lanes=2, batched=batched) as srv:
         jid = srv.submit(p, a, kind="inversion", iters=iters, lr=lr, alpha_floor=floor, q_face=q,
                          q_steps=w.q_steps, obs=obs)
         r = srv.wait(jid)
@@ -66,14 +71,16 @@ def test_inversion_job_matches_python_loop(solver):
     assert losses[-1] < losses[0]
 
 
-def test_same_bits_alone_and_in_the_mix(solver):
+@pytest.mark.parametrize("batched", [True, False])
+def test_same_bits_alone_and_in_the_mix(solver, batched):
     w, p, alpha, q = _case(64, 64, 16, 60, 3003)
     others = [_case(*shape, seed) for shape, seed in (((96, 64, 24, 80), 3004), ((128, 96, 20, 50), 3005),
                                                       ((32, 32, 8, 200), 3006))]
-    with Server(solver, lanes=3) as srv:
+    with Server(solver, lanes=3, batched=batched, chunk_steps=9) as srv:
         alone = torch.empty(p.nt, p.ny, p.nx, dtype=torch.float32, device="cuda")
         r = srv.wait(srv.submit(p, alpha, q_face=q, q_steps=w.q_steps, frames_out=alone))
         assert r["state_name"] == "done", r
+        assert r["shared_launches"] == 0, r
         ids, mixed = [], torch.empty_like(alone)
         for k, (wo, po, ao, qo) in enumerate(others):
             ids.append(srv.submit(po, ao, q_face=qo, q_steps=wo.q_steps))
@@ -81,7 +88,52 @@ def test_same_bits_alone_and_in_the_mix(solver):
                 ids.append(srv.submit(p, alpha, q_face=q, q_steps=w.q_steps, frames_out=mixed))
         res = [srv.wait(i) for i in ids]
     assert all(x["state_name"] == "done" for x in res), res
+    if batched:   # 60 steps in chunks of 9: 7 launches, shared with the jobs submitted before it
+        assert res[2]["launches"] == 7 and res[2]["shared_launches"] > 0, res[2]
     assert torch.equal(alone, mixed)
+
+
+def test_batched_ragged_mix_matches_direct_calls(solver):
+    """Forward jobs with a loss, an inversion and a grid the batch kernel does
+    not take (nx % 4 != 0) served together, their sweeps cut into 7-step
+    chunks: each result matches the direct call on the solver's own handle."""
+    shapes = (((64, 48, 16, 45), 3101), ((96, 64, 24, 30), 3102), ((30, 28, 8, 40), 3103))
+    cases = [_case(*shape, seed) for shape, seed in shapes]
+    targets, direct = [], []
+    for w, p, alpha, q in cases:
+        at = torch.tensor(w.alpha_target, dtype=torch.float32, device="cuda")
+        obs = solver.forward(p, at, q_face=q, q_steps=w.q_steps)["frames"]
+        targets.append(obs)
+        direct.append(solver.forward(p, alpha, q_face=q, q_steps=w.q_steps, obs=obs))
+    wi, pi, ai, qi = _case(48, 48, 12, 30, 3104)
+    obs_i = solver.forward(pi, torch.tensor(wi.alpha_target, dtype=torch.float32, device="cuda"), q_face=qi,
+                           q_steps=wi.q_steps)["frames"]
+    lr, floor, iters = 2.0, 0.05, 2
+    ref = ai.clone()
+    for _ in range(iters):
+        out = solver.adjoint_grad(pi, ref, obs_i, q_face=qi, q_steps=wi.q_steps)
+        ref = torch.clamp(ref - lr * out["grad_alpha"], min=floor)
+    with Server(solver, lanes=4, chunk_steps=7) as srv:
+        frames, ids = [], []
+        a_inv = ai.clone()
+        ids.append(srv.submit(pi, a_inv, kind="inversion", iters=iters, lr=lr, alpha_floor=floor, q_face=qi,
+                              q_steps=wi.q_steps, obs=obs_i))
+        for (w, p, alpha, q), obs in zip(cases, targets):
+            fr = torch.empty(p.nt, p.ny, p.nx, dtype=torch.float32, device="cuda")
+            frames.append(fr)
+            ids.append(srv.submit(p, alpha, q_face=q, q_steps=w.q_steps, obs=obs, frames_out=fr))
+        res = [srv.wait(i) for i in ids]
+    assert all(r["state_name"] == "done" and r["status"] == 0 for r in res), res
+    inv, fwd = res[0], res[1:]
+    assert inv["shared_launches"] > 0, inv
+    assert fwd[0]["launches"] == 7 and fwd[1]["launches"] == 5, fwd   # ceil(45 / 7), ceil(30 / 7)
+    assert fwd[2]["launches"] == 0, fwd[2]                             # nx % 4 != 0: the lane's own grid
+    for fr, d, r in zip(frames, direct, fwd):
+        err = (fr - d["frames"]).norm() / d["frames"].norm()
+        assert err < 1e-5, float(err)
+        assert abs(r["loss"] - d["loss"]) <= 1e-5 * abs(d["loss"]), (r["loss"], d["loss"])
+    err = (a_inv - ref).norm() / ref.norm()
+    assert err < 1e-5, float(err)
 
 
 def test_cancel_queued_and_refuse_oversized(solver):
@@ -102,11 +154,15 @@ def test_cancel_queued_and_refuse_oversized(solver):
         assert e.value.status == NEFTY_ENOMEM
 
 
-def test_lanes_overlap_jobs(solver):
-    """Two equal jobs on two lanes finish in well under twice one job's time."""
+@pytest.mark.parametrize("batched", [True, False])
+def test_lanes_overlap_jobs(solver, batched):
+    """Two equal jobs on two lanes finish in well under twice one job's time:
+    on lanes with their own grids (each job then has half of the device), and
+    batched, where one job alone has the whole device and two share each
+    launch (its grid barriers and reductions)."""
     import time
     w, p, alpha, q = _case(128, 128, 32, 150, 3008)
-    with Server(solver, lanes=2) as srv:
+    with Server(solver, lanes=2, batched=batched) as srv:
         srv.wait(srv.submit(p, alpha, q_face=q, q_steps=w.q_steps))   # warm-up (workspace)
         srv.wait(srv.submit(p, alpha, q_face=q, q_steps=w.q_steps))
         t0 = time.perf_counter()
@@ -117,4 +173,6 @@ def test_lanes_overlap_jobs(solver):
         ra, rb = srv.wait(a), srv.wait(b)
         two = time.perf_counter() - t0
     assert {ra["lane"], rb["lane"]} == {0, 1}
-    assert two < 1.6 * one, (one, two)
+    if batched:
+        assert ra["shared_launches"] > 0 and rb["shared_launches"] > 0, (ra, rb)
+    assert two < (1.9 if batched else 1.6) * one, (one, two)
