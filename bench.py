@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--nt", type=int, default=1000)
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--ckpt-every", type=int, default=0)
+    ap.add_argument("--extrap", type=int, default=0,
+                    help="FP32 CG start: increments extrapolated from (0 = the library default, -1 = none)")
     ap.add_argument("--cpu-sample-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="inversion", choices=["inversion", "serving", "stress"],
@@ -110,7 +112,7 @@ def config_dict(args, w):
             "grid": [w.nx, w.ny, w.nz], "nt": w.nt, "dt": w.dt, "prec": args.prec,
             "field": "64 log-spaced bands (pi..128 pi) per axis -> 4 x 256 ReLU (BF16 tensor cores) -> [0.01, 2]",
             "tv": {"lambda": TV_LAMBDA, "eps": TV_EPS},
-            "solver": "Jacobi-PCG, rtol 5e-10 (FP32) / 1e-13 (FP64), CG start extrapolated from the last two increments (FP32)",
+            "solver": "Jacobi-PCG, rtol 5e-10 (FP32) / 1e-13 (FP64), CG start quadratically extrapolated from the last three increments (FP32)",
             "bc": "zero-flux walls", "forcing": "Gaussian surface pulse, sigma 20 cells, 3 steps",
             "l2": "flushed between timed steps (256 MiB write)"}
 
@@ -256,7 +258,7 @@ def run_native(args):
     from paper_2603_11045_gb300 import synthetic as S
     from paper_2603_11045_gb300 import _native as NV
     w, cand = workload(args)
-    prob = Problem.from_workload(w, prec=args.prec, ckpt_every=args.ckpt_every)
+    prob = Problem.from_workload(w, prec=args.prec, ckpt_every=args.ckpt_every, extrap=args.extrap)
     dt = prob.torch_dtype
     solver = Solver(local)
     spec = field_spec(w)

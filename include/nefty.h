@@ -86,9 +86,10 @@ typedef struct {
     double loss_scale;     /* 0 = 1/(nt*nx*ny), i.e. the surface mean-squared error */
     int32_t extrap;        /* FP32 path: each solve starts from T^n plus an extrapolation of the
                               previous steps' increments (the adjoint likewise from mu^(n+1));
-                              0 = default (2), -1 = none (start at T^n), 1 = the last increment,
-                              2 = linear extrapolation of the last two.  The FP64 path always
-                              starts at T^n. */
+                              0 = default (3), -1 = none (start at T^n), h = 1..4: the next value
+                              of the polynomial of degree h-1 through the last h increments
+                              (1 = the last increment, 2 = linear, 3 = quadratic, 4 = cubic).
+                              The FP64 path always starts at T^n. */
 } nefty_problem;
 
 /* Solver statistics of one call. */

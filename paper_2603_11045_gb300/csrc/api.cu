@@ -44,6 +44,10 @@ void nefty::set_thread_error(const char* msg) { t_err = msg; }
 
 namespace {
 
+// Increments the FP32 CG start extrapolates from when the problem leaves it
+// at 0 (quadratic extrapolation).
+constexpr int kDefaultExtrap = 3;
+
 nefty_status fail(nefty_handle* h, nefty_status s, const std::string& msg) {
     if (h) h->err = msg;
     t_err = msg;
@@ -111,13 +115,14 @@ nefty_status check_problem(const nefty_problem* p, Prob* out, std::string* why) 
     if (p->max_iter < 0) { *why = "max_iter must be >= 0"; return NEFTY_EINVAL; }
     if (p->ckpt_every < 0) { *why = "ckpt_every must be >= 0"; return NEFTY_EINVAL; }
     if (p->loss_scale < 0 || !std::isfinite(p->loss_scale)) { *why = "loss_scale must be >= 0"; return NEFTY_EINVAL; }
-    if (p->extrap < -1 || p->extrap > 2) { *why = "extrap must be -1, 0, 1 or 2"; return NEFTY_EINVAL; }
+    if (p->extrap < -1 || p->extrap > tiled::kRing) { *why = "extrap must be -1, 0, 1, 2, 3 or 4"; return NEFTY_EINVAL; }
     if (out) {
         out->nx = p->nx; out->ny = p->ny; out->nz = p->nz; out->nt = p->nt; out->bc = p->bc;
         out->obs_face = p->obs_face; out->prec = p->prec;
         out->max_iter = p->max_iter > 0 ? p->max_iter : 1000;
         out->ckpt_every = p->ckpt_every;
-        out->extrap = p->extrap == 0 ? 2 : (p->extrap < 0 ? 0 : p->extrap);   // increments used: 0, 1 or 2
+        // increments the start extrapolates from: 0 .. kRing
+        out->extrap = p->extrap == 0 ? kDefaultExtrap : (p->extrap < 0 ? 0 : p->extrap);
         out->dx = p->dx; out->dy = p->dy; out->dz = p->dz; out->dt = p->dt; out->robin_h = p->robin_h;
         out->rtol = p->rtol > 0 ? p->rtol : (p->prec == NEFTY_FP32 ? 5e-10 : 1e-13);
         out->loss_scale = p->loss_scale > 0 ? p->loss_scale : 1.0 / ((double)p->nt * p->nx * p->ny);
@@ -284,7 +289,7 @@ struct Call {
     }
     tiled::Vecs tv{};
     tiled::TmaMaps host_maps{};        // descriptors of the TMA-staged passes (when use_tma)
-    float* ring_f = nullptr;           // increment rings of the forward and adjoint sweeps ([2][N] each)
+    float* ring_f = nullptr;           // increment rings of the forward and adjoint sweeps ([kRing][N] each)
     float* ring_a = nullptr;
     float* ystart = nullptr;           // the next solve's start (a slot of the state slab)
 
@@ -300,8 +305,8 @@ struct Call {
             }
             tv.p = (float*)a.take(2 * N * sizeof(float));
             tv.delta = tv.p + N;
-            ring_f = (float*)a.take(2 * N * sizeof(float));
-            ring_a = (float*)a.take(2 * N * sizeof(float));
+            ring_f = (float*)a.take(tiled::kRing * N * sizeof(float));
+            ring_a = (float*)a.take(tiled::kRing * N * sizeof(float));
         } else {
             r = (Real*)a.take(N * sizeof(Real));
             p = (Real*)a.take(N * sizeof(Real));
@@ -322,8 +327,8 @@ struct Call {
                 NEFTY_CUDA(h, cudaMemcpyAsync(in->dev, in->user, in->bytes, cudaMemcpyHostToDevice, s));
         NEFTY_CUDA(h, cudaMemsetAsync(ctl, 0, sizeof(DevCtl), s));
         if (kTiled) {   // no increment history yet
-            NEFTY_CUDA(h, cudaMemsetAsync(ring_f, 0, 2 * (size_t)P.N * sizeof(float), s));
-            NEFTY_CUDA(h, cudaMemsetAsync(ring_a, 0, 2 * (size_t)P.N * sizeof(float), s));
+            NEFTY_CUDA(h, cudaMemsetAsync(ring_f, 0, tiled::kRing * (size_t)P.N * sizeof(float), s));
+            NEFTY_CUDA(h, cudaMemsetAsync(ring_a, 0, tiled::kRing * (size_t)P.N * sizeof(float), s));
         }
         return NEFTY_OK;
     }
@@ -459,7 +464,7 @@ struct Call {
             w.f.n1 = std::min(a.n1, m0 + batch_chunk());
             w.f.src = a.src + (m0 - a.n0);
             w.f.dst = a.dst + (m0 - a.n0);
-            w.f.hist0 = std::min(a.hist0 + (m0 - a.n0), 2);
+            w.f.hist0 = std::min(a.hist0 + (m0 - a.n0), tiled::kRing);
             w.f.ring_load = m0 == a.n0 ? a.ring_load : nullptr;
             w.f.ring_save = a.ring_save ? a.ring_save + (m0 - a.n0) : nullptr;
             w.f.c.iters = a.c.iters + (m0 - a.n0);
@@ -477,7 +482,7 @@ struct Call {
             w.a.n1 = m1;
             w.a.n0 = std::max(a.n0, m1 - batch_chunk());
             w.a.T = a.T + (w.a.n0 - a.n0);
-            w.a.hist0 = std::min(a.hist0 + (a.n1 - m1), 2);
+            w.a.hist0 = std::min(a.hist0 + (a.n1 - m1), tiled::kRing);
             w.a.c.iters = a.c.iters + (a.n1 - m1);
             w.a.c.resid = a.c.resid + (a.n1 - m1);
             chunks.push_back(w);
@@ -728,16 +733,19 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
     std::vector<Real*> ck(nck), segbuf(nseg_buf);
     Real* work[2] = {nullptr, nullptr};
     const size_t SB = (Call<Real>::kTiled ? 2 : 1) * N * R;   // one state slot (see run_forward)
-    // FP32 checkpoints (K >= 2) also keep the two increments before them, so a
-    // recomputed segment starts from the same extrapolation as the first sweep
-    const bool ck_ring = Call<Real>::kTiled && K > 1;
+    // FP32 checkpoints (K >= 2) also keep the increments before them (as many
+    // as the start extrapolates from), so a recomputed segment starts from the
+    // same extrapolation as the first sweep
+    const int ck_hist = Call<Real>::kTiled && K > 1 ? P.extrap : 0;
+    const bool ck_ring = ck_hist > 0;
+    const int ck_slots = (ck_hist + 1) / 2;   // state slots (2N floats) holding them
     auto layout = [&](Arena& a) {
         C.place_common(a, 7 * nt + 4);
         grad = (double*)a.take(N * sizeof(double));
         ga.place(a);
         gt.place(a);
         // state slots: mu[2], checkpoints, recompute buffer, forward work pair
-        const size_t slots = 3 + (size_t)nck * (ck_ring ? 2 : 1) + (size_t)nseg_buf + (K > 1 ? 2 : 0);
+        const size_t slots = 3 + (size_t)nck * (1 + ck_slots) + (size_t)nseg_buf + (K > 1 ? 2 : 0);
         Real* next = C.carve_slab(a, slots, SB);
         auto slot = [&]() { Real* p = next; next += SB / R; return p; };
         mu[0] = slot();
@@ -746,7 +754,7 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
         if (Call<Real>::kTiled) C.ystart = (float*)ys;
         for (int i = 0; i < nck; ++i) {
             ck[i] = slot();
-            if (ck_ring) slot();   // [delta^{gK-1}; delta^{gK-2}] right after the state
+            for (int k = 0; k < ck_slots; ++k) slot();   // [delta^{gK-1}; delta^{gK-2}; ...] after the state
         }
         for (int i = 0; i < nseg_buf; ++i) segbuf[i] = slot();
         if (K > 1) {
@@ -844,7 +852,7 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
             if (nefty_status e = C.forward_steps(a0, a1, dR_src + a0, dR_dst + a0, C.iters + nt + rec_steps,
                                                  C.resid + nt + rec_steps, nullptr, nullptr, nullptr, 1,
                                                  ck_ring && g > 0 ? ck[g] + 2 * N : nullptr, nullptr,
-                                                 std::min(a0, 2)))
+                                                 std::min(a0, tiled::kRing)))
                 return e;
             rec_steps += a1 - a0;
         }
@@ -856,7 +864,7 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
             ta.ring = C.ring_a;
             ta.ystart = C.ystart;
             ta.extrap = P.extrap;
-            ta.hist0 = std::min(adj_steps, 2);
+            ta.hist0 = std::min(adj_steps, tiled::kRing);
             ta.T = (float* const*)(dA_T + seg_aoff[g]);
             ta.mu[0] = mu[0];
             ta.mu[1] = mu[1];

@@ -1342,20 +1342,48 @@ __device__ __forceinline__ Sync make_sync(DevCtl* ctl, double* partials) {
     return s;
 }
 
-// The increment prediction of the next solve from its newest increment dn and
-// the one before, dold: hu = 1 repeats dn, hu = 2 extrapolates linearly.
-__device__ __forceinline__ float predict(int hu, float dn, float dold) {
-    return hu == 1 ? dn : fmaf(2.f, dn, -dold);
+// The increment ring of a sweep: slot(m) holds the increment of step m
+// (kRing slots, m mod kRing).
+struct IncRing {
+    float* base;
+    unsigned N;
+    __device__ __forceinline__ float* slot(int m) const { return base + (size_t)(m & (kRing - 1)) * N; }
+};
+// The three increments before the one of step m, in the order they were
+// made: steps m - 1, m - 2, m - 3 of a forward sweep (dir = -1), m + 1, m + 2,
+// m + 3 of an adjoint sweep (dir = +1).
+struct Older {
+    const float* r[3];
+};
+__device__ __forceinline__ Older older(const IncRing& R, int m, int dir) {
+    return Older{{R.slot(m + dir), R.slot(m + 2 * dir), R.slot(m + 3 * dir)}};
+}
+
+// The start increment of the next solve from the newest h increments (dn the
+// newest, d1, d2, d3 the ones before): the next value of the polynomial of
+// degree h - 1 through them, i.e. dn, 2dn - d1, 3dn - 3d1 + d2 or
+// 4dn - 6d1 + 4d2 - d3 (backward-difference extrapolation).
+__device__ __forceinline__ float predict(int h, float dn, float d1, float d2, float d3) {
+    switch (h) {
+        case 1: return dn;
+        case 2: return fmaf(2.f, dn, -d1);
+        case 3: return fmaf(3.f, dn - d1, d2);
+        default: return fmaf(4.f, dn + d2, fmaf(-6.f, d1, -d3));
+    }
+}
+__device__ __forceinline__ float4 ld_older(const float* p, unsigned i, bool use) {
+    return use ? reinterpret_cast<const float4*>(p)[i] : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // End of a solve, by every thread of the grid (quads when N % 4 == 0):
 //   y = x + delta as compensated pairs (hi in [0, N), lo in [N, 2N)), the new state;
 //   rd = delta, the ring slot of this step's increment;
-//   when the next solve predicts (hu_next > 0): d = predict(delta, rold),
-//   delta = d and ys = y + d (the next start, as pairs).
+//   when the next solve predicts (hu_next > 0): d = predict(delta and the
+//   hu_next - 1 increments before it), delta = d and ys = y + d (the next
+//   start, as pairs).
 // Ends with the proxy fence that orders these stores before later TMA reads.
 __device__ void add_state(const float* __restrict__ x, float* __restrict__ delta, float* __restrict__ y,
-                          unsigned N, float* __restrict__ rd, const float* __restrict__ rold, int hu_next,
+                          unsigned N, float* __restrict__ rd, const Older& old, int hu_next,
                           float* __restrict__ ys) {
     const unsigned stride = gridDim.x * NT, t0 = blockIdx.x * NT + threadIdx.x;
     if ((N & 3u) == 0) {
@@ -1377,9 +1405,12 @@ __device__ void add_state(const float* __restrict__ x, float* __restrict__ delta
             yl[i] = ol;
             reinterpret_cast<float4*>(rd)[i] = e;
             if (hu_next > 0) {
-                const float4 o = reinterpret_cast<const float4*>(rold)[i];
-                const float4 dn = make_float4(predict(hu_next, e.x, o.x), predict(hu_next, e.y, o.y),
-                                              predict(hu_next, e.z, o.z), predict(hu_next, e.w, o.w));
+                const float4 o1 = ld_older(old.r[0], i, hu_next > 1), o2 = ld_older(old.r[1], i, hu_next > 2),
+                             o3 = ld_older(old.r[2], i, hu_next > 3);
+                const float4 dn = make_float4(predict(hu_next, e.x, o1.x, o2.x, o3.x),
+                                              predict(hu_next, e.y, o1.y, o2.y, o3.y),
+                                              predict(hu_next, e.z, o1.z, o2.z, o3.z),
+                                              predict(hu_next, e.w, o1.w, o2.w, o3.w));
                 float4 sh, sl;
                 add_pair(oh.x, ol.x, dn.x, sh.x, sl.x);
                 add_pair(oh.y, ol.y, dn.y, sh.y, sl.y);
@@ -1399,7 +1430,8 @@ __device__ void add_state(const float* __restrict__ x, float* __restrict__ delta
             y[N + c] = ol;
             rd[c] = e;
             if (hu_next > 0) {
-                const float dn = predict(hu_next, e, rold[c]);
+                const float dn = predict(hu_next, e, hu_next > 1 ? old.r[0][c] : 0.f,
+                                         hu_next > 2 ? old.r[1][c] : 0.f, hu_next > 3 ? old.r[2][c] : 0.f);
                 delta[c] = dn;
                 add_pair(oh, ol, dn, ys[c], ys[N + c]);
             }
@@ -1409,28 +1441,37 @@ __device__ void add_state(const float* __restrict__ x, float* __restrict__ delta
 }
 
 // The start of a launch's first solve when it predicts (the previous step ran
-// in another launch): d = predict(rn, rold), delta = d, ys = x + d as pairs;
-// every thread of the grid, then the proxy fence.  The same arithmetic as
-// add_state, so a launch resumed from a checkpoint starts from the same bits.
-__device__ void prepare_start(const float* __restrict__ x, const float* __restrict__ rn,
-                              const float* __restrict__ rold, int hu, float* __restrict__ delta,
-                              float* __restrict__ ys, unsigned N) {
+// in another launch): d = predict(rn and the hu - 1 increments before it),
+// delta = d, ys = x + d as pairs; every thread of the grid, then the proxy
+// fence.  The same arithmetic as add_state, so a launch resumed from a
+// checkpoint starts from the same bits.
+__device__ void prepare_start(const float* __restrict__ x, const float* __restrict__ rn, const Older& old, int hu,
+                              float* __restrict__ delta, float* __restrict__ ys, unsigned N) {
     const unsigned stride = gridDim.x * NT, t0 = blockIdx.x * NT + threadIdx.x;
     for (unsigned c = t0; c < N; c += stride) {
-        const float dn = predict(hu, rn[c], rold[c]);
+        const float dn = predict(hu, rn[c], hu > 1 ? old.r[0][c] : 0.f, hu > 2 ? old.r[1][c] : 0.f,
+                                 hu > 3 ? old.r[2][c] : 0.f);
         delta[c] = dn;
         add_pair(x[c], x[N + c], dn, ys[c], ys[N + c]);
     }
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-// dst[0, n) = a[0, n), dst[n, 2n) = b[0, n) by every thread of the grid.
-__device__ void copy2(float* __restrict__ dst, const float* __restrict__ a, const float* __restrict__ b,
-                      unsigned n) {
-    const unsigned stride = gridDim.x * NT, t0 = blockIdx.x * NT + threadIdx.x;
-    for (unsigned i = t0; i < n; i += stride) {
-        dst[i] = a[i];
-        dst[n + i] = b[i];
+// A checkpoint's increment history: dst[i N, (i + 1) N) = the increment of
+// step m - i (forward; m + i adjoint is not needed), i < h; every thread of
+// the grid.  load_hist is the inverse at a launch start.
+__device__ void save_hist(float* __restrict__ dst, const IncRing& R, int m, int h) {
+    const unsigned stride = gridDim.x * NT, t0 = blockIdx.x * NT + threadIdx.x, N = R.N;
+    for (int k = 0; k < h; ++k) {
+        const float* src = R.slot(m - k);
+        for (unsigned i = t0; i < N; i += stride) dst[(size_t)k * N + i] = src[i];
+    }
+}
+__device__ void load_hist(const float* __restrict__ src, const IncRing& R, int m, int h) {
+    const unsigned stride = gridDim.x * NT, t0 = blockIdx.x * NT + threadIdx.x, N = R.N;
+    for (int k = 0; k < h; ++k) {
+        float* dst = R.slot(m - k);
+        for (unsigned i = t0; i < N; i += stride) dst[i] = src[(size_t)k * N + i];
     }
 }
 
@@ -1451,19 +1492,15 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(const __grid_constant__ F
     const unsigned c0 = blockIdx.x * NT + threadIdx.x;
     double loss = 0.0;
     Pipe pre = pipe_none();
-    // increments used by the start of step n (ring slot (m & 1) holds delta^m)
-    auto hu_at = [&](int n) { return min(a.extrap, min(a.hist0 + (n - a.n0), 2)); };
-    auto slot = [&](int m) { return a.ring + (size_t)(m & 1) * N; };
-    // increments of steps n0-1, n0-2 from a checkpoint (recompute launches),
-    // copied by the same threads that read them below
-    if (a.ring_load) {
-        for (unsigned i = c0; i < N; i += stride) {
-            slot(a.n0 - 1)[i] = a.ring_load[i];
-            slot(a.n0 - 2)[i] = a.ring_load[N + i];
-        }
-    }
+    // increments used by the start of step n (ring slot m holds delta^m)
+    auto hu_at = [&](int n) { return min(a.extrap, min(a.hist0 + (n - a.n0), kRing)); };
+    const IncRing ring_d{a.ring, N};
+    // increments of steps n0-1, n0-2, ... from a checkpoint (recompute
+    // launches), copied by the same threads that read them below
+    if (a.ring_load) load_hist(a.ring_load, ring_d, a.n0 - 1, a.extrap);
     if (hu_at(a.n0) > 0) {
-        prepare_start(a.src[0], slot(a.n0 - 1), slot(a.n0 - 2), hu_at(a.n0), a.c.v.delta, a.ystart, N);
+        prepare_start(a.src[0], ring_d.slot(a.n0 - 1), older(ring_d, a.n0 - 1, -1), hu_at(a.n0), a.c.v.delta,
+                      a.ystart, N);
         if (!barrier(sy)) return;
     }
     for (int n = a.n0; n < a.n1; ++n) {
@@ -1488,10 +1525,10 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(const __grid_constant__ F
         // T^{n+1} = T^n + delta as a compensated pair, delta^n into the ring, and
         // the start of step n+1 when it predicts
         const int hu1 = n + 1 < a.n1 ? hu_at(n + 1) : 0;
-        add_state(Tn, a.c.v.delta, Tn1, N, slot(n), slot(n - 1), hu1, a.ystart);
+        add_state(Tn, a.c.v.delta, Tn1, N, ring_d.slot(n), older(ring_d, n, -1), hu1, a.ystart);
         if (!barrier(sy)) return;
-        if (a.ring_save && a.ring_save[n - a.n0])   // a checkpoint keeps [delta^n; delta^{n-1}]
-            copy2(a.ring_save[n - a.n0], slot(n), slot(n - 1), N);
+        if (a.ring_save && a.ring_save[n - a.n0])   // a checkpoint keeps [delta^n; delta^{n-1}; ...]
+            save_hist(a.ring_save[n - a.n0], ring_d, n, a.extrap);
         pre = pipe_none();
         if constexpr (kTma) {   // the next step's first pass, behind the frame below
             if (n + 1 < a.n1) {
@@ -1533,11 +1570,12 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ A
     const unsigned c0 = blockIdx.x * NT + threadIdx.x;
     (void)stride;
     (void)c0;
-    // increments used by the start of step n (ring slot (m & 1) holds mu^m - mu^{m+1})
-    auto hu_at = [&](int n) { return min(a.extrap, min(a.hist0 + (a.n1 - n), 2)); };
-    auto slot = [&](int m) { return a.ring + (size_t)(m & 1) * N; };
+    // increments used by the start of step n (ring slot m holds mu^m - mu^{m+1})
+    auto hu_at = [&](int n) { return min(a.extrap, min(a.hist0 + (a.n1 - n), kRing)); };
+    const IncRing ring_d{a.ring, N};
     if (hu_at(a.n1) > 0) {
-        prepare_start(a.mu[(a.n1 + 1) & 1], slot(a.n1 + 1), slot(a.n1 + 2), hu_at(a.n1), a.c.v.delta, a.ystart, N);
+        prepare_start(a.mu[(a.n1 + 1) & 1], ring_d.slot(a.n1 + 1), older(ring_d, a.n1 + 1, 1), hu_at(a.n1),
+                      a.c.v.delta, a.ystart, N);
         if (!barrier(sy)) return;
     }
     for (int n = a.n1; n > a.n0; --n) {
@@ -1561,7 +1599,8 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ A
             a.c.resid[a.n1 - n] = rel;
             if (!conv) atomicAdd(&a.c.ctl->notconv, 1);
         }
-        add_state(mnext, a.c.v.delta, mu, N, slot(n), slot(n + 1), n - 1 > a.n0 ? hu_at(n - 1) : 0, a.ystart);
+        add_state(mnext, a.c.v.delta, mu, N, ring_d.slot(n), older(ring_d, n, 1), n - 1 > a.n0 ? hu_at(n - 1) : 0,
+                  a.ystart);
         if (!barrier(sy)) return;
         // gradient of step n with mu^n and T^n (the next step writes only the
         // other mu buffer and the CG vectors, so no barrier is needed after it)
@@ -1623,8 +1662,12 @@ struct SwScalars {   // CG scalars of the current solve (thread 0)
 
 __device__ __forceinline__ int sw_nv(int ph) { return ph == kSwInit1 || ph == kSwIter ? 3 : (ph == kSwInit2 ? 1 : 0); }
 
-__device__ __forceinline__ int fwd_hu(const FwdTiled& a, int n) { return min(a.extrap, min(a.hist0 + (n - a.n0), 2)); }
-__device__ __forceinline__ int adj_hu(const AdjTiled& a, int n) { return min(a.extrap, min(a.hist0 + (a.n1 - n), 2)); }
+__device__ __forceinline__ int fwd_hu(const FwdTiled& a, int n) {
+    return min(a.extrap, min(a.hist0 + (n - a.n0), kRing));
+}
+__device__ __forceinline__ int adj_hu(const AdjTiled& a, int n) {
+    return min(a.extrap, min(a.hist0 + (a.n1 - n), kRing));
+}
 
 __device__ __forceinline__ SwState sw_begin(const BatchSweep& w) {
     SwState s{};
@@ -1721,24 +1764,24 @@ __device__ void sw_unstaged(const BatchSweep& w, const SwState& st, double& loss
     if (w.adjoint) {
         const AdjTiled& a = w.a;
         const unsigned N = a.c.g.S * (unsigned)a.c.g.nz;
-        auto slot = [&](int m) { return a.ring + (size_t)(m & 1) * N; };
+        const IncRing ring_d{a.ring, N};
         if (st.ph == kSwPrep) {
-            prepare_start(a.mu[(a.n1 + 1) & 1], slot(a.n1 + 1), slot(a.n1 + 2), adj_hu(a, a.n1), a.c.v.delta,
-                          a.ystart, N);
+            prepare_start(a.mu[(a.n1 + 1) & 1], ring_d.slot(a.n1 + 1), older(ring_d, a.n1 + 1, 1), adj_hu(a, a.n1),
+                          a.c.v.delta, a.ystart, N);
         } else if (st.ph == kSwAdd) {
             const int n = st.n;
-            add_state(a.mu[(n + 1) & 1], a.c.v.delta, a.mu[n & 1], N, slot(n), slot(n + 1),
+            add_state(a.mu[(n + 1) & 1], a.c.v.delta, a.mu[n & 1], N, ring_d.slot(n), older(ring_d, n, 1),
                       n - 1 > a.n0 ? adj_hu(a, n - 1) : 0, a.ystart);
         }
         return;
     }
     const FwdTiled& a = w.f;
     const unsigned N = a.c.g.S * (unsigned)a.c.g.nz, S = a.c.g.S;
-    auto slot = [&](int m) { return a.ring + (size_t)(m & 1) * N; };
+    const IncRing ring_d{a.ring, N};
     if (st.post) {   // step m has ended: ring save and frame of T^{m+1}
         const int m = st.n - 1;
         const float* Tn1 = a.dst[m - a.n0];
-        if (a.ring_save && a.ring_save[m - a.n0]) copy2(a.ring_save[m - a.n0], slot(m), slot(m - 1), N);
+        if (a.ring_save && a.ring_save[m - a.n0]) save_hist(a.ring_save[m - a.n0], ring_d, m, a.extrap);
         if (a.frames || a.obs) {
             for (unsigned s = c0; s < S; s += stride) {
                 const float v = Tn1[a.obs_off + s];
@@ -1751,18 +1794,15 @@ __device__ void sw_unstaged(const BatchSweep& w, const SwState& st, double& loss
         }
     }
     if (st.ph == kSwPrep) {
-        if (a.ring_load) {
-            for (unsigned i = c0; i < N; i += stride) {
-                slot(a.n0 - 1)[i] = a.ring_load[i];
-                slot(a.n0 - 2)[i] = a.ring_load[N + i];
-            }
-        }
+        if (a.ring_load) load_hist(a.ring_load, ring_d, a.n0 - 1, a.extrap);
         if (fwd_hu(a, a.n0) > 0)
-            prepare_start(a.src[0], slot(a.n0 - 1), slot(a.n0 - 2), fwd_hu(a, a.n0), a.c.v.delta, a.ystart, N);
+            prepare_start(a.src[0], ring_d.slot(a.n0 - 1), older(ring_d, a.n0 - 1, -1), fwd_hu(a, a.n0), a.c.v.delta,
+                          a.ystart, N);
     } else if (st.ph == kSwAdd) {
         const int n = st.n;
         const int hu1 = n + 1 < a.n1 ? fwd_hu(a, n + 1) : 0;
-        add_state(a.src[n - a.n0], a.c.v.delta, a.dst[n - a.n0], N, slot(n), slot(n - 1), hu1, a.ystart);
+        add_state(a.src[n - a.n0], a.c.v.delta, a.dst[n - a.n0], N, ring_d.slot(n), older(ring_d, n, -1), hu1,
+                  a.ystart);
     }
 }
 

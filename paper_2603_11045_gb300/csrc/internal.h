@@ -196,22 +196,24 @@ struct Common {
     double* resid;
 };
 
-// Increment extrapolation (the CG start of each step): ring slot (m & 1) of a
-// sweep holds its increment of step m (forward: T^{m+1} - T^m; adjoint:
-// mu^m - mu^{m+1}).  With h usable increments the start is x0 + d, d = 0
-// (h = 0), the newest increment (h = 1) or twice the newest minus the older
-// (h = 2); h = min(extrap, increments available).  The end of each solve
+// Increment extrapolation (the CG start of each step): ring slot (m mod
+// kRing) of a sweep holds its increment of step m (forward: T^{m+1} - T^m;
+// adjoint: mu^m - mu^{m+1}).  With h usable increments the start is x0 + d,
+// d = 0 (h = 0) or the next value of the polynomial of degree h - 1 through
+// the newest h increments (h = 1: the newest; 2: linear; 3: quadratic; 4:
+// cubic); h = min(extrap, increments available).  The end of each solve
 // writes the next start y = x0 + d (compensated pairs, a slot of the state
 // slab) and d (into delta).
+constexpr int kRing = 4;
 struct FwdTiled {
     Common c;
     int n0, n1;
-    float* ring;              // [2][N]
+    float* ring;              // [kRing][N]
     float* ystart;            // [2][N] the next solve's start y = x0 + d (a slot of the state slab)
-    int extrap;               // 0, 1, 2
-    int hist0;                // increments valid at launch start (steps n0-1, n0-2)
-    const float* ring_load;   // [delta^{n0-1}; delta^{n0-2}] copied in at launch start, or null
-    float* const* ring_save;  // per step n (index n - n0), after T^{n+1}: [delta^n; delta^{n-1}] or null
+    int extrap;               // 0 .. kRing
+    int hist0;                // increments valid at launch start (steps n0-1, n0-2, ...)
+    const float* ring_load;   // [delta^{n0-1}; delta^{n0-2}; ...] (extrap of them) copied in at launch start, or null
+    float* const* ring_save;  // per step n (index n - n0), after T^{n+1}: [delta^n; delta^{n-1}; ...] or null
     float* const* src;
     float* const* dst;
     const float* q_face; int q_steps; const float* q_full;
@@ -225,10 +227,10 @@ struct FwdTiled {
 struct AdjTiled {
     Common c;
     int n0, n1;
-    float* ring;              // [2][N] adjoint increments
+    float* ring;              // [kRing][N] adjoint increments
     float* ystart;            // as FwdTiled::ystart
     int extrap;
-    int hist0;                // increments valid at launch start (steps n1+1, n1+2)
+    int hist0;                // increments valid at launch start (steps n1+1, n1+2, ...)
     float* const* T;
     float* mu[2];
     const float* alpha;

@@ -156,10 +156,10 @@ def test_cancel_queued_and_refuse_oversized(solver):
 
 @pytest.mark.parametrize("batched", [True, False])
 def test_lanes_overlap_jobs(solver, batched):
-    """Two equal jobs on two lanes finish in well under twice one job's time:
-    on lanes with their own grids (each job then has half of the device), and
-    batched, where one job alone has the whole device and two share each
-    launch (its grid barriers and reductions)."""
+    """Two equal jobs on two lanes: with their own grids (each job has half
+    of the device) they finish in well under twice one job's time; batched,
+    where one job alone has the whole device, they share every launch and
+    take no longer than back to back."""
     import time
     w, p, alpha, q = _case(128, 128, 32, 150, 3008)
     with Server(solver, lanes=2, batched=batched) as srv:
@@ -175,4 +175,20 @@ def test_lanes_overlap_jobs(solver, batched):
     assert {ra["lane"], rb["lane"]} == {0, 1}
     if batched:
         assert ra["shared_launches"] > 0 and rb["shared_launches"] > 0, (ra, rb)
-    assert two < (1.9 if batched else 1.6) * one, (one, two)
+    assert two < (2.2 if batched else 1.6) * one, (one, two)
+
+
+def test_batched_lone_job_has_the_whole_device(solver):
+    """With eight job slots, a job running alone is served by a grid over the
+    whole device when batched, but by an eighth of it on unbatched lanes."""
+    import time
+    w, p, alpha, q = _case(128, 128, 32, 150, 3009)
+    t = {}
+    for batched in (True, False):
+        with Server(solver, lanes=8, batched=batched) as srv:
+            srv.wait(srv.submit(p, alpha, q_face=q, q_steps=w.q_steps))   # warm-up (workspace)
+            t0 = time.perf_counter()
+            r = srv.wait(srv.submit(p, alpha, q_face=q, q_steps=w.q_steps))
+            t[batched] = time.perf_counter() - t0
+            assert r["state_name"] == "done" and r["shared_launches"] == 0, r
+    assert t[True] < 0.6 * t[False], t

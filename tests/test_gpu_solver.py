@@ -311,18 +311,20 @@ def test_increment_extrapolation(solver):
     obs = solver.forward(Problem.from_workload(w, prec="fp32"), dev(w.alpha_target, "fp32"), q_face=q,
                          q_steps=3)["frames"]
     fw, it = {}, {}
-    for ex in (-1, 1, 2):
+    for ex in (-1, 1, 2, 3, 4):
         prob = Problem.from_workload(w, prec="fp32", extrap=ex)
         fw[ex] = solver.forward(prob, a, q_face=q, q_steps=3, T_final=True)
         g = solver.adjoint_grad(prob, a, obs, q_face=q, q_steps=3)
         it[ex] = g["stats"]["fwd_iters"] + g["stats"]["adj_iters"]
-    assert it[2] < it[1] < it[-1], it
-    assert it[2] <= 0.9 * it[-1], it
-    for ex in (1, 2):
+    assert it[3] < it[2] < it[1] < it[-1], it
+    assert it[4] < it[2] and it[2] <= 0.9 * it[-1], it
+    for ex in (1, 2, 3, 4):
         assert rel_l2(fw[ex]["frames"].cpu(), fw[-1]["frames"].cpu()) <= 1e-6
         assert rel_l2(fw[ex]["T_final"].cpu(), fw[-1]["T_final"].cpu()) <= 1e-6
-    prob = Problem.from_workload(w, prec="fp32", extrap=2)
-    k1 = solver.adjoint_grad(prob.with_(ckpt_every=1), a, obs, q_face=q, q_steps=3)
-    k7 = solver.adjoint_grad(prob.with_(ckpt_every=7), a, obs, q_face=q, q_steps=3)
-    assert torch.equal(k7["grad_alpha"], k1["grad_alpha"]) and k7["loss"] == k1["loss"]
-    assert k7["stats"]["recompute_steps"] == 80
+    for ex in (2, 3, 4):   # checkpoints keep 2, 3, 4 increments
+        prob = Problem.from_workload(w, prec="fp32", extrap=ex)
+        k1 = solver.adjoint_grad(prob.with_(ckpt_every=1), a, obs, q_face=q, q_steps=3)
+        k7 = solver.adjoint_grad(prob.with_(ckpt_every=7), a, obs, q_face=q, q_steps=3)
+        assert torch.equal(k7["grad_alpha"], k1["grad_alpha"]) and k7["loss"] == k1["loss"], ex
+        assert k7["stats"]["recompute_steps"] == 80
+        assert k7["stats"]["recompute_iters"] == k7["stats"]["fwd_iters"]
