@@ -827,6 +827,23 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
                                          ck_ring ? dF_ring : nullptr, 0))
         return e;
 
+    // FP32: the adjoint sweep runs on a power-of-two multiple 2^k of the
+    // adjoint problem (exact, as it is linear), with k chosen from the surface
+    // misfit so that mu is of order one; its squared norms and error terms
+    // then stay in the normal range of FP32 however small the misfit is.  The
+    // gradient and dJ/dT0 are scaled back by 2^-k.
+    double adj_scale = 1.0;
+    if constexpr (Call<Real>::kTiled) {
+        std::vector<double> lp(C.G);
+        NEFTY_CUDA(h, cudaMemcpyAsync(lp.data(), C.loss_partials, C.G * sizeof(double), cudaMemcpyDeviceToHost, s));
+        NEFTY_CUDA(h, cudaStreamSynchronize(s));
+        double sq = 0.0;
+        for (double v : lp) sq += v;
+        const double src = 2.0 * P.loss_scale * std::sqrt(sq / ((double)P.nt * (double)P.S));
+        if (src > 0.0 && std::isfinite(src))
+            adj_scale = std::ldexp(1.0, std::max(-120, std::min(120, -(int)std::lround(std::log2(src)))));
+    }
+
     // reverse sweep, one segment at a time
     NEFTY_CUDA(h, cudaMemsetAsync(mu[(P.nt + 1) & 1], 0, SB, s));
     int rec_steps = 0, adj_steps = 0;
@@ -870,7 +887,7 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
             ta.mu[1] = mu[1];
             ta.alpha = (const float*)C.alpha.dev;
             ta.wx = (float)aa.wx; ta.wy = (float)aa.wy; ta.wz = (float)aa.wz;
-            ta.g_scale = (float)aa.g_scale;
+            ta.g_scale = (float)(aa.g_scale * adj_scale);
             ta.obs_off = aa.obs_off;
             ta.obs = (const float*)C.obs.dev;
             ta.grad = reinterpret_cast<float2*>(grad);   // N pairs in the N-double accumulator
@@ -885,12 +902,17 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
         }
         adj_steps += a1 - a0;
     }
-    if constexpr (Call<Real>::kTiled)
-        NEFTY_CUDA(h, launch_cast_pairs(reinterpret_cast<const float2*>(grad), (float*)ga.dev, P.N, s));
-    else
+    if constexpr (Call<Real>::kTiled) {
+        const float unscale = (float)(1.0 / adj_scale);
+        NEFTY_CUDA(h, launch_cast_pairs(reinterpret_cast<const float2*>(grad), (float*)ga.dev, P.N, unscale, s));
+        if (gt.user)   // dJ/dT0 = mu^1, a compensated pair
+            NEFTY_CUDA(h, launch_cast_split_pairs((const float*)mu[1], (const float*)mu[1] + N, (float*)gt.dev, P.N,
+                                                  unscale, s));
+    } else {
         NEFTY_CUDA(h, launch_cast<Real>(grad, (Real*)ga.dev, P.N, s));
+        if (gt.user) NEFTY_CUDA(h, cudaMemcpyAsync(gt.dev, mu[1], N * R, cudaMemcpyDeviceToDevice, s));
+    }
     ++C.launches;
-    if (gt.user) NEFTY_CUDA(h, cudaMemcpyAsync(gt.dev, mu[1], N * R, cudaMemcpyDeviceToDevice, s));
     for (Output* o : {&ga, &gt})
         if (o->user && o->stage)
             NEFTY_CUDA(h, cudaMemcpyAsync(o->user, o->dev, o->bytes, cudaMemcpyDeviceToHost, s));

@@ -782,19 +782,33 @@ struct IterBody {
     }
 };
 
-// sh + sl += cf ((hc + lc) - (hq + lq)), error-free up to the final rounding
-// (TwoSum of the high parts, TwoProd through fmaf).  Zero faces add nothing.
-__device__ __forceinline__ void exact_term(float cf, float hc, float lc, float hq, float lq, float& sh, float& sl) {
-    if (cf == 0.f) return;
+// The flux term cf ((hc + lc) - (hq + lq)) of a face as pr + pe: the high
+// difference by TwoSum, the product by TwoProd through fmaf; pr is its
+// rounded value.  The same face seen from the other cell gives exactly
+// (-pr, -pe) (TwoSum's error is unique, and negation is exact), so a face
+// between two cells of one thread is formed once.
+struct FaceTerm {
+    float pr, pe;
+};
+__device__ __forceinline__ FaceTerm face_term(float cf, float hc, float lc, float hq, float lq) {
     float dh, dhe;
     two_sum(hc, -hq, dh, dhe);
     const float dl = (lc - lq) + dhe;
     const float pr = cf * dh;
-    const float pe = fmaf(cf, dh, -pr) + cf * dl;
+    return FaceTerm{pr, fmaf(cf, dh, -pr) + cf * dl};
+}
+__device__ __forceinline__ FaceTerm neg(FaceTerm f) { return FaceTerm{-f.pr, -f.pe}; }
+// sh + sl += pr + pe, error-free up to the final rounding (a zero face adds nothing).
+__device__ __forceinline__ void add_term(FaceTerm f, float& sh, float& sl) {
     float t, te;
-    two_sum(sh, pr, t, te);
+    two_sum(sh, f.pr, t, te);
     sh = t;
-    sl += te + pe;
+    sl += te + f.pe;
+}
+// sh + sl += cf ((hc + lc) - (hq + lq)) for a face of one cell.
+__device__ __forceinline__ void exact_term(float cf, float hc, float lc, float hq, float lq, float& sh, float& sl) {
+    if (cf == 0.f) return;
+    add_term(face_term(cf, hc, lc, hq, lq), sh, sl);
 }
 // sh + sl += rob (hc + lc), the Robin sink, the same way.
 __device__ __forceinline__ void exact_sink(float rob, float hc, float lc, float& sh, float& sl) {
@@ -822,8 +836,13 @@ struct Init1Body {
     float hc[4], lc[4], ac[4];
     float hp[4], lp[4], ap[4];
     float czm[4], czp[4];
+    FaceTerm zdn[4];                   // the -z face terms of plane k (the +z ones of plane k-1, negated)
     __device__ Init1Body(const Common& c, RhsFn& r, Acc<3>& a, int hu_) : C(c), rhs(r), acc(a), hu(hu_) {}
-    __device__ __forceinline__ void reset() { set4(hm, 0.f); set4(lm, 0.f); set4(am, 0.f); set4(czm, 0.f); }
+    __device__ __forceinline__ void reset() {
+        set4(hm, 0.f); set4(lm, 0.f); set4(am, 0.f); set4(czm, 0.f);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) zdn[j] = FaceTerm{0.f, 0.f};
+    }
     __device__ __forceinline__ void below(const unsigned char* st, int hb) {
         ld4(st, sl(0), hb, hm);
         ld4(st, sl(1), hb, lm);
@@ -835,7 +854,10 @@ struct Init1Body {
         ld4(st, sl(3), hb, ac);
         if (has_below) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) czm[j] = face(ac[j], am[j], C.kz);
+            for (int j = 0; j < 4; ++j) {
+                czm[j] = face(ac[j], am[j], C.kz);
+                zdn[j] = face_term(czm[j], hc[j], lc[j], hm[j], lm[j]);
+            }
         }
     }
     __device__ __forceinline__ void above(const unsigned char* st, int hb) {
@@ -860,16 +882,25 @@ struct Init1Body {
         const float hxr = lds1(st, sl(0), hb + 4), lxr = lds1(st, sl(1), hb + 4);
         quad_faces(st, hb, ac, C.kx, C.ky, cx, cyp, cym);
         const float rob = k + 1 == g.nz ? C.robin : 0.f;
+        // x faces: X[f] between cells f - 1 and f seen from the left (f = 1..3),
+        // X[0] / X[4] the outer faces seen from cells 0 / 3
+        FaceTerm X[5];
+        X[0] = face_term(cx[0], hc[0], lc[0], hxl, lxl);
+#pragma unroll
+        for (int f = 1; f < 4; ++f) X[f] = face_term(cx[f], hc[f - 1], lc[f - 1], hc[f], lc[f]);
+        X[4] = face_term(cx[4], hc[3], lc[3], hxr, lxr);
         float u[4], s0 = 0.f, s1 = 0.f, s2 = 0.f;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             float sh = 0.f, sx = 0.f;
-            exact_term(cx[j + 1], hc[j], lc[j], j < 3 ? hc[j + 1] : hxr, j < 3 ? lc[j + 1] : lxr, sh, sx);
-            exact_term(cx[j], hc[j], lc[j], j > 0 ? hc[j - 1] : hxl, j > 0 ? lc[j - 1] : lxl, sh, sx);
+            const FaceTerm zup = face_term(czp[j], hc[j], lc[j], hp[j], lp[j]);
+            add_term(X[j + 1], sh, sx);
+            add_term(j > 0 ? neg(X[j]) : X[0], sh, sx);
             exact_term(cyp[j], hc[j], lc[j], hyp[j], lyp[j], sh, sx);
             exact_term(cym[j], hc[j], lc[j], hym[j], lym[j], sh, sx);
-            exact_term(czp[j], hc[j], lc[j], hp[j], lp[j], sh, sx);
-            exact_term(czm[j], hc[j], lc[j], hm[j], lm[j], sh, sx);
+            add_term(zup, sh, sx);
+            add_term(zdn[j], sh, sx);
+            zdn[j] = neg(zup);   // the -z term of the cell above
             exact_sink(rob, hc[j], lc[j], sh, sx);
             if (hu > 0) {   // + d
                 float t, te;
@@ -952,11 +983,15 @@ struct Init2Body {
 
 // ---- gradient of one step (Eq. grad_assembly) at the own cells:
 // g_c -= sum_f w_f h^2 (mu_c - mu_q)(T_c - T_q), h = alpha_q / (alpha_c + alpha_q),
-// with T and mu as compensated pairs, faces in the order +x, -x, +y, -y, +z, -z.
-// A cell beyond a zero-flux wall stages alpha_q = 0, so h = 0 and it adds
-// nothing.  Plane values are read from the stages when needed (the stage of
-// plane k + 1 is held while plane k is worked on); only the -z terms of the
-// next plane are carried in registers.
+// with T and mu as compensated pairs.  A face between two cells of the same
+// thread (inside the quad along x, and along z between consecutive planes)
+// is evaluated once for both: P = w (mu_c - mu_q)(T_c - T_q) is symmetric,
+// and the two cells take P (alpha_q / s)^2 and P (alpha_c / s)^2 with
+// s = alpha_c + alpha_q.  A cell beyond a zero-flux wall stages alpha_q = 0,
+// so h = 0 and it adds nothing.  Plane values are read from the stages when
+// needed (the stage of plane k + 1 is held while plane k is worked on); only
+// the -z terms of the next plane are carried in registers, and the plane's
+// accumulator is loaded before its terms are formed.
 struct GradBody {
     float2* grad;          // dJ/dalpha accumulator, compensated (hi, lo) pairs
     float wx, wy, wz;
@@ -969,6 +1004,17 @@ struct GradBody {
         const float dm = (mc - mq) + (mcl - mql);
         const float dT = (tc - tq) + (tcl - tql);
         return w * h * h * dm * dT;
+    }
+    // the face (c, q) for both cells: to_c as term(c, q), to_q as term(q, c)
+    __device__ __forceinline__ static void pair(float ac, float mc, float mcl, float tc, float tcl, float aq, float mq,
+                                                float mql, float tq, float tql, float w, float& to_c, float& to_q) {
+        const float inv = rcp_approx(ac + aq);
+        const float hc = aq * inv, hq = ac * inv;
+        const float dm = (mc - mq) + (mcl - mql);
+        const float dT = (tc - tq) + (tcl - tql);
+        const float P = w * dm * dT;
+        to_c = hc * hc * P;
+        to_q = hq * hq * P;
     }
     __device__ __forceinline__ static void load(const unsigned char* st, int hb, float (&t)[4], float (&tlo)[4],
                                                 float (&m)[4], float (&mlo)[4], float (&a)[4]) {
@@ -993,24 +1039,25 @@ struct GradBody {
     __device__ __forceinline__ void plane(int k, unsigned c, bool valid, const unsigned char* st,
                                           const unsigned char* st1, int hb, int) {
         if (!valid) return;
+        const float4 g01 = *reinterpret_cast<const float4*>(grad + c);
+        const float4 g23 = *reinterpret_cast<const float4*>(grad + c + 2);
         float th[4], tl[4], mh[4], ml[4], ac[4];
         load(st, hb, th, tl, mh, ml, ac);
         float s[4] = {0.f, 0.f, 0.f, 0.f};
-        {   // +x, -x
-            const int hr = hb + 4, hl = hb - 1;
-            const float tr = lds1(st, sl(0), hr), trl = lds1(st, sl(1), hr), mr = lds1(st, sl(4), hr),
-                        mrl = lds1(st, sl(5), hr), ar = lds1(st, sl(3), hr);
-            const float tq = lds1(st, sl(0), hl), tql = lds1(st, sl(1), hl), mq = lds1(st, sl(4), hl),
-                        mql = lds1(st, sl(5), hl), aq = lds1(st, sl(3), hl);
+        {   // x: the three faces inside the quad once for both cells, then the two outer faces
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                s[j] += j < 3 ? term(ac[j], mh[j], ml[j], th[j], tl[j], ac[j + 1], mh[j + 1], ml[j + 1], th[j + 1],
-                                     tl[j + 1], wx)
-                              : term(ac[j], mh[j], ml[j], th[j], tl[j], ar, mr, mrl, tr, trl, wx);
-                s[j] += j > 0 ? term(ac[j], mh[j], ml[j], th[j], tl[j], ac[j - 1], mh[j - 1], ml[j - 1], th[j - 1],
-                                     tl[j - 1], wx)
-                              : term(ac[j], mh[j], ml[j], th[j], tl[j], aq, mq, mql, tq, tql, wx);
+            for (int j = 0; j < 3; ++j) {
+                float a2b, b2a;
+                pair(ac[j], mh[j], ml[j], th[j], tl[j], ac[j + 1], mh[j + 1], ml[j + 1], th[j + 1], tl[j + 1], wx,
+                     a2b, b2a);
+                s[j] += a2b;
+                s[j + 1] += b2a;
             }
+            const int hr = hb + 4, hl = hb - 1;
+            s[3] += term(ac[3], mh[3], ml[3], th[3], tl[3], lds1(st, sl(3), hr), lds1(st, sl(4), hr),
+                         lds1(st, sl(5), hr), lds1(st, sl(0), hr), lds1(st, sl(1), hr), wx);
+            s[0] += term(ac[0], mh[0], ml[0], th[0], tl[0], lds1(st, sl(3), hl), lds1(st, sl(4), hl),
+                         lds1(st, sl(5), hl), lds1(st, sl(0), hl), lds1(st, sl(1), hl), wx);
         }
 #pragma unroll
         for (int sd = 0; sd < 2; ++sd) {   // +y, then -y
@@ -1024,11 +1071,11 @@ struct GradBody {
             load(st1, hb, t, tlo, m, mlo, a);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                s[j] += term(ac[j], mh[j], ml[j], th[j], tl[j], a[j], m[j], mlo[j], t[j], tlo[j], wz);
-                zdn1[j] = term(a[j], m[j], mlo[j], t[j], tlo[j], ac[j], mh[j], ml[j], th[j], tl[j], wz);
+                float up;
+                pair(ac[j], mh[j], ml[j], th[j], tl[j], a[j], m[j], mlo[j], t[j], tlo[j], wz, up, zdn1[j]);
+                s[j] += up;
             }
         }
-        float4 g01 = *reinterpret_cast<const float4*>(grad + c), g23 = *reinterpret_cast<const float4*>(grad + c + 2);
         float gh[4] = {g01.x, g01.z, g23.x, g23.z}, gl[4] = {g01.y, g01.w, g23.y, g23.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -2032,15 +2079,26 @@ cudaError_t launch_batch_tiled(const tiled::BatchArgs& b, int grid, cudaStream_t
 int tiled_dynamic_smem() { return tiled::DYN_SMEM; }
 
 namespace tiled {
-__global__ void cast_pairs(const float2* __restrict__ in, float* __restrict__ out, unsigned n) {
+__global__ void cast_pairs(const float2* __restrict__ in, float* __restrict__ out, unsigned n, float scale) {
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        out[i] = in[i].x + in[i].y;
+        out[i] = (in[i].x + in[i].y) * scale;
+}
+__global__ void cast_split_pairs(const float* __restrict__ hi, const float* __restrict__ lo, float* __restrict__ out,
+                                 unsigned n, float scale) {
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = (hi[i] + lo[i]) * scale;
 }
 }  // namespace tiled
 
-cudaError_t launch_cast_pairs(const float2* in, float* out, unsigned n, cudaStream_t s) {
+cudaError_t launch_cast_pairs(const float2* in, float* out, unsigned n, float scale, cudaStream_t s) {
     const unsigned blocks = std::min(4096u, (n + 255u) / 256u);
-    tiled::cast_pairs<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(in, out, n);
+    tiled::cast_pairs<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(in, out, n, scale);
+    return cudaGetLastError();
+}
+cudaError_t launch_cast_split_pairs(const float* hi, const float* lo, float* out, unsigned n, float scale,
+                                    cudaStream_t s) {
+    const unsigned blocks = std::min(4096u, (n + 255u) / 256u);
+    tiled::cast_split_pairs<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(hi, lo, out, n, scale);
     return cudaGetLastError();
 }
 

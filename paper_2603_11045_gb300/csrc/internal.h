@@ -312,7 +312,10 @@ int batcher_chunk(Batcher* b, unsigned N);   // time steps per chunk of a sweep 
 // those that carried other sweeps too.  grid must be batcher_grid(b).
 nefty_status batcher_run(Batcher* b, std::vector<tiled::BatchSweep>& chunks, int grid, cudaStream_t s,
                          int* launches, int* shared, std::string* why);
-// out[i] = in[i].x + in[i].y (the tiled gradient accumulator to FP32).
-cudaError_t launch_cast_pairs(const float2* in, float* out, unsigned n, cudaStream_t s);
+// out[i] = (in[i].x + in[i].y) * scale (the tiled gradient accumulator to FP32);
+// the split form reads a state's hi and lo halves.
+cudaError_t launch_cast_pairs(const float2* in, float* out, unsigned n, float scale, cudaStream_t s);
+cudaError_t launch_cast_split_pairs(const float* hi, const float* lo, float* out, unsigned n, float scale,
+                                    cudaStream_t s);
 
 }  // namespace nefty

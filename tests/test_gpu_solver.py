@@ -328,3 +328,26 @@ def test_increment_extrapolation(solver):
         assert torch.equal(k7["grad_alpha"], k1["grad_alpha"]) and k7["loss"] == k1["loss"], ex
         assert k7["stats"]["recompute_steps"] == 80
         assert k7["stats"]["recompute_iters"] == k7["stats"]["fwd_iters"]
+
+
+def test_fp32_adjoint_tiny_misfit_scale(solver):
+    """The FP32 adjoint sweep runs on a power-of-two multiple of the adjoint
+    problem chosen from the misfit: with the loss scaled by 1e-30 (an adjoint
+    field near 1e-35, whose squared norms would underflow FP32 and stall the
+    CG) every solve converges and the gradient is the unscaled one times
+    1e-30."""
+    from paper_2603_11045_gb300.solver import Problem
+    w = S.inclusion_case(nx=64, ny=64, nz=16, nt=60, seed=1012)
+    p = Problem.from_workload(w, prec="fp32")
+    a, q = dev(w.alpha, "fp32"), dev(w.q_face, "fp32")
+    obs = solver.forward(p, dev(w.alpha_target, "fp32"), q_face=q, q_steps=3)["frames"]
+    ref = solver.adjoint_grad(p, a, obs, q_face=q, q_steps=3, grad_T0=True)
+    s0 = 1.0 / (p.nt * p.nx * p.ny)
+    tiny = solver.adjoint_grad(p.with_(loss_scale=1e-30 * s0), a, obs, q_face=q, q_steps=3, grad_T0=True)
+    assert tiny["stats"]["not_converged"] == 0
+    assert tiny["stats"]["adj_iters"] <= 1.5 * ref["stats"]["adj_iters"], (tiny["stats"], ref["stats"])
+    assert tiny["loss"] == pytest.approx(1e-30 * ref["loss"], rel=1e-12)
+    for key in ("grad_alpha", "grad_T0"):
+        g = tiny[key].double().cpu() / 1e-30
+        assert torch.isfinite(g).all()
+        assert rel_l2(g, ref[key].double().cpu()) <= 1e-5, key
