@@ -996,8 +996,11 @@ struct GradBody {
     float2* grad;          // dJ/dalpha accumulator, compensated (hi, lo) pairs
     float wx, wy, wz;
     int nz;
+    unsigned S;            // cells per plane
     float bth[4], btl[4], bmh[4], bml[4], bac[4];   // plane k0 - 1 (segment start only)
     float zdn[4], zdn1[4];                          // -z terms of plane k and of plane k + 1
+    float4 gq[2];          // the accumulator of the quad on the next plane, loaded a plane ahead
+    bool have;
     __device__ __forceinline__ static float term(float a0, float mc, float mcl, float tc, float tcl, float aq,
                                                  float mq, float mql, float tq, float tql, float w) {
         const float h = aq * rcp_approx(a0 + aq);
@@ -1024,7 +1027,7 @@ struct GradBody {
         ld4(st, sl(5), hb, mlo);
         ld4(st, sl(3), hb, a);
     }
-    __device__ __forceinline__ void reset() {}
+    __device__ __forceinline__ void reset() { have = false; }
     __device__ __forceinline__ void below(const unsigned char* st, int hb) { load(st, hb, bth, btl, bmh, bml, bac); }
     __device__ __forceinline__ void own(const unsigned char* st, int hb, bool has_below) {
         if (!has_below) return;
@@ -1039,8 +1042,13 @@ struct GradBody {
     __device__ __forceinline__ void plane(int k, unsigned c, bool valid, const unsigned char* st,
                                           const unsigned char* st1, int hb, int) {
         if (!valid) return;
-        const float4 g01 = *reinterpret_cast<const float4*>(grad + c);
-        const float4 g23 = *reinterpret_cast<const float4*>(grad + c + 2);
+        const float4 g01 = have ? gq[0] : *reinterpret_cast<const float4*>(grad + c);
+        const float4 g23 = have ? gq[1] : *reinterpret_cast<const float4*>(grad + c + 2);
+        have = k + 1 < nz;   // the next plane's accumulator (the same cells one plane up)
+        if (have) {
+            gq[0] = *reinterpret_cast<const float4*>(grad + c + S);
+            gq[1] = *reinterpret_cast<const float4*>(grad + c + S + 2);
+        }
         float th[4], tl[4], mh[4], ml[4], ac[4];
         load(st, hb, th, tl, mh, ml, ac);
         float s[4] = {0.f, 0.f, 0.f, 0.f};
@@ -1431,41 +1439,72 @@ __device__ __forceinline__ float4 ld_older(const float* p, unsigned i, bool use)
 // Ends with the proxy fence that orders these stores before later TMA reads.
 __device__ void add_state(const float* __restrict__ x, float* __restrict__ delta, float* __restrict__ y,
                           unsigned N, float* __restrict__ rd, const Older& old, int hu_next,
-                          float* __restrict__ ys) {
+                          float* __restrict__ ys, bool stream_y) {
     const unsigned stride = gridDim.x * NT, t0 = blockIdx.x * NT + threadIdx.x;
     if ((N & 3u) == 0) {
+        // Batches of two quads per thread: every load of a batch is issued
+        // before its stores.  x (the old state) is not read again soon, so it
+        // streams past L2 (evict-first), and so does the new state y when
+        // stream_y (a forward state, read again only a step later); delta,
+        // the ring and the next start stay there for the passes that follow.
+        constexpr int B = 2;
         const unsigned N4 = N >> 2;
-        const float4* xh = reinterpret_cast<const float4*>(x);
-        const float4* xl = reinterpret_cast<const float4*>(x + N);
-        float4* d4 = reinterpret_cast<float4*>(delta);
-        float4* yh = reinterpret_cast<float4*>(y);
-        float4* yl = reinterpret_cast<float4*>(y + N);
-#pragma unroll 4
-        for (unsigned i = t0; i < N4; i += stride) {
-            const float4 h = xh[i], l = xl[i], e = d4[i];
-            float4 oh, ol;
-            add_pair(h.x, l.x, e.x, oh.x, ol.x);
-            add_pair(h.y, l.y, e.y, oh.y, ol.y);
-            add_pair(h.z, l.z, e.z, oh.z, ol.z);
-            add_pair(h.w, l.w, e.w, oh.w, ol.w);
-            yh[i] = oh;
-            yl[i] = ol;
-            reinterpret_cast<float4*>(rd)[i] = e;
-            if (hu_next > 0) {
-                const float4 o1 = ld_older(old.r[0], i, hu_next > 1), o2 = ld_older(old.r[1], i, hu_next > 2),
-                             o3 = ld_older(old.r[2], i, hu_next > 3);
-                const float4 dn = make_float4(predict(hu_next, e.x, o1.x, o2.x, o3.x),
-                                              predict(hu_next, e.y, o1.y, o2.y, o3.y),
-                                              predict(hu_next, e.z, o1.z, o2.z, o3.z),
-                                              predict(hu_next, e.w, o1.w, o2.w, o3.w));
-                float4 sh, sl;
-                add_pair(oh.x, ol.x, dn.x, sh.x, sl.x);
-                add_pair(oh.y, ol.y, dn.y, sh.y, sl.y);
-                add_pair(oh.z, ol.z, dn.z, sh.z, sl.z);
-                add_pair(oh.w, ol.w, dn.w, sh.w, sl.w);
-                d4[i] = dn;
-                reinterpret_cast<float4*>(ys)[i] = sh;
-                reinterpret_cast<float4*>(ys + N)[i] = sl;
+        const float4* __restrict__ xh = reinterpret_cast<const float4*>(x);
+        const float4* __restrict__ xl = reinterpret_cast<const float4*>(x + N);
+        float4* __restrict__ d4 = reinterpret_cast<float4*>(delta);
+        float4* __restrict__ yh = reinterpret_cast<float4*>(y);
+        float4* __restrict__ yl = reinterpret_cast<float4*>(y + N);
+        float4* __restrict__ r4 = reinterpret_cast<float4*>(rd);
+        const float4* __restrict__ o1p = reinterpret_cast<const float4*>(old.r[0]);
+        const float4* __restrict__ o2p = reinterpret_cast<const float4*>(old.r[1]);
+        const float4* __restrict__ o3p = reinterpret_cast<const float4*>(old.r[2]);
+        float4* __restrict__ sh4 = reinterpret_cast<float4*>(ys);
+        float4* __restrict__ sl4 = reinterpret_cast<float4*>(ys + N);
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (unsigned i0 = t0; i0 < N4; i0 += B * stride) {
+            float4 h[B], l[B], e[B], o1[B], o2[B], o3[B];
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                const unsigned i = i0 + u * stride;
+                const bool in = i < N4;
+                h[u] = in ? __ldcs(xh + i) : z4;
+                l[u] = in ? __ldcs(xl + i) : z4;
+                e[u] = in ? d4[i] : z4;
+                o1[u] = in && hu_next > 1 ? o1p[i] : z4;
+                o2[u] = in && hu_next > 2 ? o2p[i] : z4;
+                o3[u] = in && hu_next > 3 ? o3p[i] : z4;
+            }
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                const unsigned i = i0 + u * stride;
+                if (i >= N4) break;
+                float4 oh, ol;
+                add_pair(h[u].x, l[u].x, e[u].x, oh.x, ol.x);
+                add_pair(h[u].y, l[u].y, e[u].y, oh.y, ol.y);
+                add_pair(h[u].z, l[u].z, e[u].z, oh.z, ol.z);
+                add_pair(h[u].w, l[u].w, e[u].w, oh.w, ol.w);
+                if (stream_y) {
+                    __stcs(yh + i, oh);
+                    __stcs(yl + i, ol);
+                } else {
+                    yh[i] = oh;
+                    yl[i] = ol;
+                }
+                r4[i] = e[u];
+                if (hu_next > 0) {
+                    const float4 dn = make_float4(predict(hu_next, e[u].x, o1[u].x, o2[u].x, o3[u].x),
+                                                  predict(hu_next, e[u].y, o1[u].y, o2[u].y, o3[u].y),
+                                                  predict(hu_next, e[u].z, o1[u].z, o2[u].z, o3[u].z),
+                                                  predict(hu_next, e[u].w, o1[u].w, o2[u].w, o3[u].w));
+                    float4 sh, sl;
+                    add_pair(oh.x, ol.x, dn.x, sh.x, sl.x);
+                    add_pair(oh.y, ol.y, dn.y, sh.y, sl.y);
+                    add_pair(oh.z, ol.z, dn.z, sh.z, sl.z);
+                    add_pair(oh.w, ol.w, dn.w, sh.w, sl.w);
+                    d4[i] = dn;
+                    sh4[i] = sh;
+                    sl4[i] = sl;
+                }
             }
         }
     } else {
@@ -1572,7 +1611,7 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(const __grid_constant__ F
         // T^{n+1} = T^n + delta as a compensated pair, delta^n into the ring, and
         // the start of step n+1 when it predicts
         const int hu1 = n + 1 < a.n1 ? hu_at(n + 1) : 0;
-        add_state(Tn, a.c.v.delta, Tn1, N, ring_d.slot(n), older(ring_d, n, -1), hu1, a.ystart);
+        add_state(Tn, a.c.v.delta, Tn1, N, ring_d.slot(n), older(ring_d, n, -1), hu1, a.ystart, true);
         if (!barrier(sy)) return;
         if (a.ring_save && a.ring_save[n - a.n0])   // a checkpoint keeps [delta^n; delta^{n-1}; ...]
             save_hist(a.ring_save[n - a.n0], ring_d, n, a.extrap);
@@ -1647,7 +1686,7 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ A
             if (!conv) atomicAdd(&a.c.ctl->notconv, 1);
         }
         add_state(mnext, a.c.v.delta, mu, N, ring_d.slot(n), older(ring_d, n, 1), n - 1 > a.n0 ? hu_at(n - 1) : 0,
-                  a.ystart);
+                  a.ystart, false);
         if (!barrier(sy)) return;
         // gradient of step n with mu^n and T^n (the next step writes only the
         // other mu buffer and the CG vectors, so no barrier is needed after it)
@@ -1658,6 +1697,7 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ A
             B.grad = a.grad;
             B.wx = a.wx; B.wy = a.wy; B.wz = a.wz;
             B.nz = g.nz;
+            B.S = g.S;
             if (!staged(a.c, ring, in, B)) return;
         } else {
             for_cells(g, [&](int k, unsigned c, int x, int y) {
@@ -1769,6 +1809,7 @@ __device__ bool sw_staged(const BatchSweep& w, const SwState& st, Ring& ring, Ac
             Bd.grad = a.grad;
             Bd.wx = a.wx; Bd.wy = a.wy; Bd.wz = a.wz;
             Bd.nz = a.c.g.nz;
+            Bd.S = a.c.g.S;
             if (!stage_side(a.c, ring, in, Bd)) return false;
         }
         if (st.ph == kSwInit1) {
@@ -1818,7 +1859,7 @@ __device__ void sw_unstaged(const BatchSweep& w, const SwState& st, double& loss
         } else if (st.ph == kSwAdd) {
             const int n = st.n;
             add_state(a.mu[(n + 1) & 1], a.c.v.delta, a.mu[n & 1], N, ring_d.slot(n), older(ring_d, n, 1),
-                      n - 1 > a.n0 ? adj_hu(a, n - 1) : 0, a.ystart);
+                      n - 1 > a.n0 ? adj_hu(a, n - 1) : 0, a.ystart, false);
         }
         return;
     }
@@ -1849,7 +1890,7 @@ __device__ void sw_unstaged(const BatchSweep& w, const SwState& st, double& loss
         const int n = st.n;
         const int hu1 = n + 1 < a.n1 ? fwd_hu(a, n + 1) : 0;
         add_state(a.src[n - a.n0], a.c.v.delta, a.dst[n - a.n0], N, ring_d.slot(n), older(ring_d, n, -1), hu1,
-                  a.ystart);
+                  a.ystart, true);
     }
 }
 
