@@ -1272,17 +1272,54 @@ __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, co
             acc3.add(2, r * r);
         });
     }
-    // CG scalars live in thread 0 (FP64); the FP32 step lengths and the stop
-    // decision reach the other threads through shared memory.
+    // CG scalars live in thread 0 (double-floats); the FP32 step lengths and
+    // the stop decision reach the other threads through shared memory.  The
+    // sums of the initial residual join the one of the first product: a grid
+    // barrier between the two passes (u0 complete, its stores ordered before
+    // the copies of the next pass), one reduction after both.
     __shared__ float s_a, s_b;
     __shared__ int s_go;
-    DF t3[3];
-    if (!grid_sum<3>(sy, acc3, t3, [&] {
-            if constexpr (kTma) pp = pipe_start(C, ring, PassIn{kInit2, 0, false, 0u, 0u});
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    if (!barrier(sy)) return false;
+    // ---- init 2: ws0 = M^{-1} A u0 ; (A u0, u0)
+    Acc<1> acc1;
+    if constexpr (kTma) {
+        const PassIn in{kInit2, 0, false, 0u, 0u};
+        Init2Body B(C, acc1);
+        if (!staged(C, ring, in, B)) return false;
+    } else {
+        const float* __restrict__ u0 = C.v.u[0];
+        for_cells(g, [&](int k, unsigned c, int x, int y) {
+            const Nb n = neighbours(g, c, x, y, k);
+            const float ac = C.alpha[c];
+            float cf[6];
+            cell_faces(C, n, ac, cf);
+            const float rob = k + 1 == g.nz ? C.robin : 0.f;
+            const float f = u0[c];
+            float fq[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) fq[i] = (n.m >> i & 1u) ? u0[n.q[i]] : 0.f;
+            const float Au = f + cf[0] * (f - fq[0]) + cf[1] * (f - fq[1]) + cf[2] * (f - fq[2]) +
+                             cf[3] * (f - fq[3]) + cf[4] * (f - fq[4]) + cf[5] * (f - fq[5]) + rob * f;
+            C.v.ws[0][c] = rcp_approx(diag(cf[0], cf[1], cf[2], cf[3], cf[4], cf[5], rob)) * Au;
+            acc1.add(0, Au * f);
+        });
+    }
+    Acc<4> acc4;   // bb, (r0, u0), (r0, r0), (A u0, u0)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        acc4.h[i] = acc3.h[i];
+        acc4.l[i] = acc3.l[i];
+    }
+    acc4.h[3] = acc1.h[0];
+    acc4.l[3] = acc1.l[0];
+    DF t4[4];
+    if (!grid_sum<4>(sy, acc4, t4, [&] {
+            if constexpr (kTma) pp = pipe_start(C, ring, PassIn{kIter, 0, true, 0u, 0u});
         }))
         return false;
-    const DF bb = t3[0], lim = df_mul(DF{C.tol2_hi, C.tol2_lo}, bb);
-    DF gam = t3[1], rho = t3[2];
+    const DF bb = t4[0], lim = df_mul(DF{C.tol2_hi, C.tol2_lo}, bb);
+    DF gam = t4[1], rho = t4[2];
     int it = 0;
     if (threadIdx.x == 0) s_go = (!df_le(rho, lim) && C.max_iter > 0) ? 1 : 0;
     __syncthreads();
@@ -1291,38 +1328,9 @@ __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, co
             if (!pipe_cancel(C, ring, pp)) return false;
         }
     } else {
-        // ---- init 2: ws0 = M^{-1} A u0 ; (A u0, u0)
-        Acc<1> acc1;
-        if constexpr (kTma) {
-            const PassIn in{kInit2, 0, false, 0u, 0u};
-            Init2Body B(C, acc1);
-            if (!staged(C, ring, in, B, pp.n, pp.ok)) return false;
-        } else {
-            const float* __restrict__ u0 = C.v.u[0];
-            for_cells(g, [&](int k, unsigned c, int x, int y) {
-                const Nb n = neighbours(g, c, x, y, k);
-                const float ac = C.alpha[c];
-                float cf[6];
-                cell_faces(C, n, ac, cf);
-                const float rob = k + 1 == g.nz ? C.robin : 0.f;
-                const float f = u0[c];
-                float fq[6];
-#pragma unroll
-                for (int i = 0; i < 6; ++i) fq[i] = (n.m >> i & 1u) ? u0[n.q[i]] : 0.f;
-                const float Au = f + cf[0] * (f - fq[0]) + cf[1] * (f - fq[1]) + cf[2] * (f - fq[2]) +
-                                 cf[3] * (f - fq[3]) + cf[4] * (f - fq[4]) + cf[5] * (f - fq[5]) + rob * f;
-                C.v.ws[0][c] = rcp_approx(diag(cf[0], cf[1], cf[2], cf[3], cf[4], cf[5], rob)) * Au;
-                acc1.add(0, Au * f);
-            });
-        }
-        DF t1[1];
-        if (!grid_sum<1>(sy, acc1, t1, [&] {
-                if constexpr (kTma) pp = pipe_start(C, ring, PassIn{kIter, 0, true, 0u, 0u});
-            }))
-            return false;
         DF alpha{0.f, 0.f};
         if (threadIdx.x == 0) {
-            alpha = df_div(gam, t1[0]);
+            alpha = df_div(gam, t4[3]);
             s_a = alpha.hi;
             s_b = 0.f;
         }

@@ -17,7 +17,7 @@ namespace nefty {
 // Threads per CTA of the persistent solver kernels.
 constexpr int kThreads = 512;
 // Maximum number of values reduced together across the grid.
-constexpr int kMaxRed = 3;
+constexpr int kMaxRed = 4;
 // Device-side wait limit of a grid barrier (nanoseconds of %globaltimer).
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;
 
