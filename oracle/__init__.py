@@ -7,7 +7,8 @@ imports this package and shares no code with it.
 ``nefty_oracle.c`` (plain C, FP64, no fast-math) implements the paper's
 definitions: CSR assembly of A(alpha) = I - dt L(alpha) with harmonic-mean face
 conductances (Prop. 1, App. D.2), one CG solve per implicit-Euler step to a
-1e-14 relative residual (Eq. state_eq), the reverse-time adjoint with A^T formed
+1e-14 relative residual (Eq. state_eq) or, as the paper's own inner solver,
+a fixed number K of Jacobi sweeps from the warm start (Eq. jacobi_iter), the reverse-time adjoint with A^T formed
 by transposition (Eq. adjoint_eq), the gradient through the explicitly assembled
 Jacobian d(L T)/d alpha (Eq. grad_assembly) and the discrete TV (Eq.
 tv_discrete).  ``field.py`` holds the FP64 neural-field reference (Sec. 4.1,
@@ -62,10 +63,10 @@ def _lib():
             lib.orc_apply_L.argtypes = [P, vp, vp, vp]
             lib.orc_apply_L.restype = ctypes.c_int
             lib.orc_forward.argtypes = [P, vp, vp, vp, ctypes.c_int, vp, vp, vp, vp, vp, vp,
-                                        ctypes.c_double, ctypes.c_int, ctypes.c_int]
+                                        ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             lib.orc_forward.restype = ctypes.c_int
             lib.orc_adjoint_grad.argtypes = [P, vp, vp, vp, ctypes.c_int, vp, vp, vp, vp, vp,
-                                             ctypes.c_double, ctypes.c_int]
+                                             ctypes.c_double, ctypes.c_int, ctypes.c_int]
             lib.orc_adjoint_grad.restype = ctypes.c_int
             lib.orc_tv.argtypes = [P, vp, ctypes.c_double, ctypes.c_double, vp]
             lib.orc_tv.restype = ctypes.c_double
@@ -137,8 +138,10 @@ def apply_L(p: _Problem, alpha, T):
 
 
 def forward(p: _Problem, alpha, T0=None, q_face=None, q_steps=0, q_full=None, obs=None,
-            keep_states=False, tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER, dense=False):
-    """Run the implicit-Euler forward sweep; returns dict(frames, loss, states, iters)."""
+            keep_states=False, tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER, dense=False, jacobi_k=0):
+    """Run the implicit-Euler forward sweep; returns dict(frames, loss, states, iters).
+    jacobi_k > 0: each step is jacobi_k Jacobi sweeps from T^n (App. D.2) instead
+    of a converged solve."""
     N, S = _n(p), p.nx * p.ny
     alpha = _f64(alpha, N)
     T0 = _f64(T0, N)
@@ -151,7 +154,7 @@ def forward(p: _Problem, alpha, T0=None, q_face=None, q_steps=0, q_full=None, ob
     iters = np.zeros(p.nt, np.int32)
     rc = _lib().orc_forward(ctypes.byref(p), _ptr(alpha), _ptr(T0), _ptr(q_face), int(q_steps),
                             _ptr(q_full), _ptr(obs), _ptr(frames), _ptr(states), ctypes.byref(loss),
-                            _ptr(iters), tol, max_iter, 1 if dense else 0)
+                            _ptr(iters), tol, max_iter, 1 if dense else 0, int(jacobi_k))
     if rc:
         raise OracleError(f"forward rc={rc}")
     return {"frames": frames, "loss": loss.value if obs is not None else None,
@@ -159,8 +162,10 @@ def forward(p: _Problem, alpha, T0=None, q_face=None, q_steps=0, q_full=None, ob
 
 
 def adjoint_grad(p: _Problem, alpha, T0=None, q_face=None, q_steps=0, q_full=None, obs=None,
-                 tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER):
-    """Loss, dJ/dalpha and dJ/dT0 by the discrete adjoint; returns a dict."""
+                 tol=DEFAULT_TOL, max_iter=DEFAULT_MAX_ITER, jacobi_k=0):
+    """Loss, dJ/dalpha and dJ/dT0 by the discrete adjoint; returns a dict.
+    jacobi_k > 0: every forward and adjoint solve is jacobi_k Jacobi sweeps
+    from its warm start (T^n, mu^(n+1)), the paper's inner solver."""
     N, S = _n(p), p.nx * p.ny
     alpha = _f64(alpha, N)
     T0 = _f64(T0, N)
@@ -172,7 +177,7 @@ def adjoint_grad(p: _Problem, alpha, T0=None, q_face=None, q_steps=0, q_full=Non
     loss = ctypes.c_double(0.0)
     rc = _lib().orc_adjoint_grad(ctypes.byref(p), _ptr(alpha), _ptr(T0), _ptr(q_face), int(q_steps),
                                  _ptr(q_full), _ptr(obs), ctypes.byref(loss), _ptr(grad), _ptr(gT0),
-                                 tol, max_iter)
+                                 tol, max_iter, int(jacobi_k))
     if rc:
         raise OracleError(f"adjoint rc={rc}")
     return {"loss": loss.value, "grad_alpha": grad, "grad_T0": gT0}

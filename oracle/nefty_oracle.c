@@ -255,6 +255,27 @@ done:
     return it;
 }
 
+/* K sweeps of the paper's Jacobi inner solver (App. D.2, Eq. jacobi_iter):
+ * x <- D^{-1} (b - R x) with M = D + R, D the diagonal of M and R the rest,
+ * starting from the x given (the warm start) and with no stopping test. */
+static void jacobi_solve(const orc_csr *M, const double *b, double *x, int K) {
+    int n = M->n;
+    double *y = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int kappa = 0; kappa < K; ++kappa) {
+        #pragma omp parallel for schedule(static) if (n >= 200000)
+        for (int r = 0; r < n; ++r) {
+            double d = 0.0, rx = 0.0;
+            for (int64_t e = M->rp[r]; e < M->rp[r + 1]; ++e) {
+                if (M->ci[e] == r) d = M->v[e];
+                else rx += M->v[e] * x[M->ci[e]];
+            }
+            y[r] = (b[r] - rx) / d;
+        }
+        memcpy(x, y, sizeof(double) * (size_t)n);
+    }
+    free(y);
+}
+
 /* --------------------------------------------------------- dense LU */
 /* Gaussian elimination with partial pivoting on a dense copy of M; the
  * factors overwrite lu, the row permutation is stored in piv. */
@@ -338,10 +359,11 @@ int orc_apply_L(const orc_problem *g, const double *alpha, const double *T, doub
 /* Forward sweep.  states (optional) receives T^0..T^nt, frames (optional)
  * receives Pi T^1..Pi T^nt, loss (optional) the objective when obs is given,
  * iters (optional) the CG iteration count of each step.  dense != 0 solves each
- * step by dense LU instead of CG. */
+ * step by dense LU instead of CG; jacobi_k > 0 by jacobi_k Jacobi sweeps from
+ * T^n (the paper's inner solver). */
 int orc_forward(const orc_problem *g, const double *alpha, const double *T0, const double *q_face,
                 int q_steps, const double *q_full, const double *obs, double *frames, double *states,
-                double *loss, int *iters, double tol, int max_iter, int dense) {
+                double *loss, int *iters, double tol, int max_iter, int dense, int jacobi_k) {
     int64_t N = (int64_t)g->nx * g->ny * g->nz;
     int64_t S = (int64_t)g->nx * g->ny;
     orc_csr A;
@@ -365,6 +387,10 @@ int orc_forward(const orc_problem *g, const double *alpha, const double *T0, con
         step_rhs(g, n, Tn, q_face, q_steps, q_full, b);
         if (dense) {
             dense_lu_solve((int)N, lu, piv, b, Tn1);
+        } else if (jacobi_k > 0) {
+            memcpy(Tn1, Tn, sizeof(double) * (size_t)N); /* T^(0) = T^n */
+            jacobi_solve(&A, b, Tn1, jacobi_k);
+            if (iters) iters[n] = jacobi_k;
         } else {
             memcpy(Tn1, Tn, sizeof(double) * (size_t)N); /* warm start x0 = T^n */
             int it = cg_solve(&A, b, Tn1, tol, max_iter);
@@ -412,15 +438,18 @@ static int assemble_jacobian_LT(const orc_problem *g, const double *alpha, const
 }
 
 /* Forward (all states kept), then the reverse-time adjoint recurrence with
- * A^T formed by transposition, then gradient assembly. */
+ * A^T formed by transposition, then gradient assembly.  jacobi_k > 0: every
+ * forward and adjoint solve is jacobi_k Jacobi sweeps from the warm start
+ * (T^n, mu^(n+1)), as the paper's inner solver. */
 int orc_adjoint_grad(const orc_problem *g, const double *alpha, const double *T0, const double *q_face,
                      int q_steps, const double *q_full, const double *obs, double *loss, double *grad_alpha,
-                     double *grad_T0, double tol, int max_iter) {
+                     double *grad_T0, double tol, int max_iter, int jacobi_k) {
     int64_t N = (int64_t)g->nx * g->ny * g->nz;
     int64_t S = (int64_t)g->nx * g->ny;
     double *states = (double *)malloc(sizeof(double) * (size_t)N * (size_t)(g->nt + 1));
     if (!states) return ORC_ENOMEM;
-    int rc = orc_forward(g, alpha, T0, q_face, q_steps, q_full, obs, NULL, states, loss, NULL, tol, max_iter, 0);
+    int rc = orc_forward(g, alpha, T0, q_face, q_steps, q_full, obs, NULL, states, loss, NULL, tol, max_iter, 0,
+                         jacobi_k);
     if (rc && rc != ORC_ENOTCONV) { free(states); return rc; }
     orc_csr A, At;
     int rc2 = assemble_A(g, alpha, &A);
@@ -441,8 +470,12 @@ int orc_adjoint_grad(const orc_problem *g, const double *alpha, const double *T0
             for (int64_t s = 0; s < S; ++s)
                 rhs[o + s] += 2.0 * g->loss_scale * (Tn[o + s] - obs[(int64_t)(n - 1) * S + s]);
         memcpy(mu, mu_next, sizeof(double) * (size_t)N); /* warm start from mu^{n+1} */
-        int it = cg_solve(&At, rhs, mu, tol, max_iter);
-        if (it < 0) rc = ORC_ENOTCONV;
+        if (jacobi_k > 0) {
+            jacobi_solve(&At, rhs, mu, jacobi_k);
+        } else {
+            int it = cg_solve(&At, rhs, mu, tol, max_iter);
+            if (it < 0) rc = ORC_ENOTCONV;
+        }
         /* grad += dt * J(T^n)^T mu^n, summed entry by entry */
         orc_csr Jm;
         rc2 = assemble_jacobian_LT(g, alpha, Tn, &Jm);
