@@ -80,9 +80,12 @@ typedef struct {
     double rtol;           /* CG stop: ||b - A x||_2 <= rtol ||b||_2 (recursive residual);
                               0 = 5e-10 (FP32) or 1e-13 (FP64) */
     int32_t max_iter;      /* CG iteration cap per solve; 0 = 1000 */
-    int32_t ckpt_every;    /* adjoint: 0 = automatic (every state kept if it fits the budget,
-                              else a checkpoint every ceil(sqrt(nt)) steps), 1 = keep every
-                              state, K >= 2 = checkpoint every K steps and recompute */
+    int32_t ckpt_every;    /* adjoint: 0 = automatic: every state kept if it fits the budget,
+                              else checkpoints every K steps over the first B steps (recomputed
+                              segment by segment) and every state of the last nt - B steps, with
+                              K and B chosen to recompute the fewest steps the budget allows;
+                              1 = keep every state; K >= 2 = checkpoint every K steps over the
+                              whole horizon and recompute */
     double loss_scale;     /* 0 = 1/(nt*nx*ny), i.e. the surface mean-squared error */
     int32_t extrap;        /* FP32 path: each solve starts from T^n plus an extrapolation of the
                               previous steps' increments (the adjoint likewise from mu^(n+1));
@@ -90,6 +93,11 @@ typedef struct {
                               of the polynomial of degree h-1 through the last h increments
                               (1 = the last increment, 2 = linear, 3 = quadratic, 4 = cubic).
                               The FP64 path always starts at T^n. */
+    int32_t jacobi_k;      /* 0 = each solve is the converged Jacobi-PCG above; K >= 1 = the
+                              paper's inner solver (App. D.2, Eq. jacobi_iter): exactly K Jacobi
+                              sweeps T <- D^-1 (b - R T) per solve from the warm start T^n (the
+                              adjoint from mu^(n+1)), with no stopping test and no extrapolation;
+                              rtol, max_iter and extrap are then ignored.  At most 100000. */
 } nefty_problem;
 
 /* Solver statistics of one call. */
@@ -100,7 +108,8 @@ typedef struct {
     int32_t fwd_steps, recompute_steps, adj_steps;
     int32_t max_step_iters;     /* largest CG iteration count of any solve */
     int32_t not_converged;      /* solves that hit max_iter */
-    int32_t ckpt_every;         /* checkpoint stride used (1 = every state kept) */
+    int32_t ckpt_every;         /* checkpoint stride used (1 = every state kept); recompute_steps
+                                   is the length of the checkpointed part */
     int32_t n_checkpoints;      /* states held for the reverse sweep */
     double max_rel_residual;    /* largest final ||r||/||b|| over all solves */
     uint64_t workspace_bytes;   /* device workspace held by the handle */
@@ -226,6 +235,7 @@ nefty_status nefty_tv(nefty_handle *h, const nefty_problem *p, const void *alpha
  *   alpha, T0, q_face, frames_out, T_final, obs: as for nefty_forward, but every
  *               non-NULL array must be DEVICE memory (no host staging).
  *   loss_out    host double*, or NULL; needs obs.
+ * Each solve is the converged Jacobi-PCG (p->jacobi_k must be 0).
  * Limits: the problem's scratch, 10 values per cell (40 B FP32, 80 B FP64) plus
  * about 2 MiB of fixed tables, must fit the 48 MiB array (e.g. about 1.1 M cells
  * FP32, 0.57 M cells FP64), and nt <= 65536; larger problems return NEFTY_EINVAL
@@ -245,9 +255,8 @@ nefty_status nefty_forward_static(int device, const nefty_problem *p, const void
  * a server to a handle; `lanes` worker threads (job slots), each with its own
  * CUDA stream and workspace, take queued jobs in arrival order as soon as they
  * are free.  Each lane owns mem_budget_bytes / lanes of device memory; a job's
- * checkpoint stride is chosen within that share (every state kept when it
- * fits, about sqrt(nt) checkpoints otherwise, as for ckpt_every = 0), and a job
- * that cannot fit even then is refused at submit with NEFTY_ENOMEM.
+ * checkpoint plan is chosen within that share (as for ckpt_every = 0), and a
+ * job that cannot fit even then is refused at submit with NEFTY_ENOMEM.
  *
  * Batched (the default): the FP32 sweeps of all running jobs whose grids have
  * zero-flux walls and nx % 4 == 0 run together in ONE persistent launch over

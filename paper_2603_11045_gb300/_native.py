@@ -25,7 +25,8 @@ class nefty_problem(ctypes.Structure):
                 ("dt", ctypes.c_double), ("nt", ctypes.c_int32), ("bc", ctypes.c_int32),
                 ("robin_h", ctypes.c_double), ("obs_face", ctypes.c_int32), ("prec", ctypes.c_int32),
                 ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("ckpt_every", ctypes.c_int32),
-                ("loss_scale", ctypes.c_double), ("extrap", ctypes.c_int32)]
+                ("loss_scale", ctypes.c_double), ("extrap", ctypes.c_int32),
+                ("jacobi_k", ctypes.c_int32)]
 
 
 class nefty_field_desc(ctypes.Structure):

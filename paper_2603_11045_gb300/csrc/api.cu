@@ -90,7 +90,7 @@ bool is_device_ptr(const void* p) {
 
 // Effective problem with defaults filled in.
 struct Prob {
-    int nx, ny, nz, nt, bc, obs_face, prec, max_iter, ckpt_every, extrap;
+    int nx, ny, nz, nt, bc, obs_face, prec, max_iter, ckpt_every, extrap, jacobi_k;
     double dx, dy, dz, dt, robin_h, rtol, loss_scale;
     unsigned N, S;
 };
@@ -116,6 +116,7 @@ nefty_status check_problem(const nefty_problem* p, Prob* out, std::string* why) 
     if (p->ckpt_every < 0) { *why = "ckpt_every must be >= 0"; return NEFTY_EINVAL; }
     if (p->loss_scale < 0 || !std::isfinite(p->loss_scale)) { *why = "loss_scale must be >= 0"; return NEFTY_EINVAL; }
     if (p->extrap < -1 || p->extrap > tiled::kRing) { *why = "extrap must be -1, 0, 1, 2, 3 or 4"; return NEFTY_EINVAL; }
+    if (p->jacobi_k < 0 || p->jacobi_k > 100000) { *why = "jacobi_k must be in [0, 100000]"; return NEFTY_EINVAL; }
     if (out) {
         out->nx = p->nx; out->ny = p->ny; out->nz = p->nz; out->nt = p->nt; out->bc = p->bc;
         out->obs_face = p->obs_face; out->prec = p->prec;
@@ -123,6 +124,9 @@ nefty_status check_problem(const nefty_problem* p, Prob* out, std::string* why) 
         out->ckpt_every = p->ckpt_every;
         // increments the start extrapolates from: 0 .. kRing
         out->extrap = p->extrap == 0 ? kDefaultExtrap : (p->extrap < 0 ? 0 : p->extrap);
+        // the paper's fixed Jacobi sweeps start from T^n (mu^(n+1)) exactly
+        out->jacobi_k = p->jacobi_k;
+        if (out->jacobi_k > 0) out->extrap = 0;
         out->dx = p->dx; out->dy = p->dy; out->dz = p->dz; out->dt = p->dt; out->robin_h = p->robin_h;
         out->rtol = p->rtol > 0 ? p->rtol : (p->prec == NEFTY_FP32 ? 5e-10 : 1e-13);
         out->loss_scale = p->loss_scale > 0 ? p->loss_scale : 1.0 / ((double)p->nt * p->nx * p->ny);
@@ -225,7 +229,7 @@ bool tma_grid(const Prob& P) { return P.bc == NEFTY_BC_NEUMANN && P.nx % 4 == 0;
 int grid_for_tiled(nefty_handle* h, const Prob& P) {
     if (h->grid_tiled == 0) h->grid_tiled = tiled_grid_blocks(h->device);
     // batched sweeps all run on the batcher's grid
-    if (h->batch && tma_grid(P)) return batcher_grid(h->batch);
+    if (h->batch && tma_grid(P) && P.jacobi_k == 0) return batcher_grid(h->batch);
     const int gmax = std::max(1, h->grid_tiled / h->grid_share);
     const long tiles = (long)((P.nx + tiled::TX - 1) / tiled::TX) * ((P.ny + tiled::TY - 1) / tiled::TY);
     const long units = tiles * P.nz;
@@ -363,7 +367,7 @@ struct Call {
     }
 
     FwdArgs<Real> fwd_args(int n0, int n1, Real* const* src, Real* const* dst, int* it, double* rs) {
-        FwdArgs<Real> a;
+        FwdArgs<Real> a{};
         a.op = make_view<Real>(P, coef);
         a.r = r; a.p = p; a.q = q;
         a.n0 = n0; a.n1 = n1;
@@ -382,6 +386,7 @@ struct Call {
         a.iters = it;
         a.resid = rs;
         a.loss_partials = nullptr;
+        a.jacobi_k = P.jacobi_k;
         return a;
     }
     int q_steps = 0;
@@ -433,6 +438,7 @@ struct Call {
         c.tol2_hi = (float)tol2;
         c.tol2_lo = (float)(tol2 - (double)c.tol2_hi);
         c.max_iter = P.max_iter;
+        c.jacobi_k = P.jacobi_k;
         c.iters = it;
         c.resid = rs;
         return c;
@@ -493,7 +499,7 @@ struct Call {
         NEFTY_CUDA(h, cudaMemsetAsync(&ctl->bar, 0, sizeof(unsigned), s));
         Timed t;
         if (nefty_status e = begin_timed(kind, &t)) return e;
-        if (h->batch && use_tma) {
+        if (h->batch && use_tma && P.jacobi_k == 0) {
             if (nefty_status e = batched_fwd(a)) return e;
         } else {
             NEFTY_CUDA(h, launch_forward_tiled(a, G, s));
@@ -504,7 +510,7 @@ struct Call {
         NEFTY_CUDA(h, cudaMemsetAsync(&ctl->bar, 0, sizeof(unsigned), s));
         Timed t;
         if (nefty_status e = begin_timed(2, &t)) return e;
-        if (h->batch && use_tma) {
+        if (h->batch && use_tma && P.jacobi_k == 0) {
             if (nefty_status e = batched_adj(a)) return e;
         } else {
             NEFTY_CUDA(h, launch_adjoint_tiled(a, G, s));
@@ -679,14 +685,58 @@ nefty_status run_forward(nefty_handle* h, const Prob& P, const void* alpha, cons
     return C.finish(loss_out, true, st, P.nt, 0, 0, 1, 2);
 }
 
-// Checkpoint stride of the reverse sweep: 1 keeps every state.
-int choose_stride(const Prob& P, size_t fixed_bytes, uint64_t budget) {
-    if (P.ckpt_every >= 1) return std::min(P.ckpt_every, P.nt);
-    const size_t state = (size_t)P.N * 8;   // an FP32 compensated pair or an FP64 value
-    const size_t all = (size_t)(P.nt + 1) * state + fixed_bytes;
-    if (all <= budget) return 1;
-    int K = (int)std::ceil(std::sqrt((double)P.nt));
-    return std::max(K, 2);
+// Storage plan of the reverse sweep.  The first gB segments of K steps,
+// [0, B) with B = min(gB K, nt), keep only their first state (a checkpoint)
+// in the forward sweep and are recomputed from it segment by segment; every
+// state of the tail [B, nt] is kept and needs no recompute.  gB = 0 keeps
+// every state.  States are counted in slots of one state each (SB bytes),
+// with c extra slots per checkpoint for its increment history.
+struct CkPlan {
+    int K;    // segment length (1 when gB == 0)
+    int gB;   // recomputed segments
+};
+long long plan_slots(int nt, int K, int gB, int c) {
+    const long long B = std::min((long long)gB * K, (long long)nt);
+    return 3 + (long long)gB * (1 + c) + (gB > 0 ? K + 2 : 0) + (B < nt ? nt - B + 1 : 0);
+}
+// ckpt_every = 1: every state; >= 2: every segment of that length recomputed;
+// 0: every state when it fits the budget, else the (K, gB) that fits and
+// recomputes the fewest steps (the tail takes whatever memory is left, so with
+// plenty of memory far less than one extra forward sweep is recomputed).
+CkPlan plan_checkpoints(const Prob& P, size_t fixed_bytes, uint64_t budget, size_t slot_bytes, int c) {
+    const int nt = P.nt;
+    if (P.ckpt_every == 1) return CkPlan{1, 0};
+    if (P.ckpt_every >= 2) {
+        const int K = std::min(P.ckpt_every, nt);
+        return CkPlan{K, (nt + K - 1) / K};
+    }
+    // state slots that fit (the slab's own alignment padding is under 256 B)
+    const uint64_t avail = budget > fixed_bytes + 256 ? budget - fixed_bytes - 256 : 0;
+    const long long M = (long long)(avail / slot_bytes);
+    if (plan_slots(nt, 1, 0, c) <= M) return CkPlan{1, 0};
+    const int Ks = std::max(2, (int)std::ceil(std::sqrt((double)nt)));
+    CkPlan best{Ks, (nt + Ks - 1) / Ks};   // when nothing fits: about sqrt(nt) checkpoints
+    long long best_cost = -1, best_slots = 0;
+    for (int K = 2; K <= nt; ++K) {
+        const int gmax = (nt + K - 1) / K;
+        // with a tail, slots fall by K - 1 - c per extra segment
+        int g = gmax;
+        if (K > 1 + c) {
+            const long long need = (long long)nt + K + 6 - M;
+            g = need <= 0 ? 1 : (int)std::min<long long>(gmax, (need + (K - 1 - c) - 1) / (K - 1 - c));
+            g = std::max(g, 1);
+        }
+        while (g < gmax && plan_slots(nt, K, g, c) > M) ++g;
+        const long long sl = plan_slots(nt, K, g, c);
+        if (sl > M) continue;
+        const long long cost = std::min((long long)g * K, (long long)nt);
+        if (best_cost < 0 || cost < best_cost || (cost == best_cost && sl < best_slots)) {
+            best = CkPlan{K, g};
+            best_cost = cost;
+            best_slots = sl;
+        }
+    }
+    return best;
 }
 
 template <typename Real>
@@ -713,54 +763,52 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
     size_t fixed = 0;
     {
         Arena a;
-        C.place_common(a, 6 * nt + 4);
-        a.take(3 * (Call<Real>::kTiled ? 2 : 1) * N * R);   // mu pair and the start slot
+        C.place_common(a, 7 * nt + 4);
         a.take(N * sizeof(double));
         ga.place(a);
         gt.place(a);
         fixed = a.off;
     }
-    const int K = choose_stride(P, fixed, h->budget);
-    // every state kept: the reverse sweep is one segment [0, nt]
-    const int nseg = K == 1 ? 1 : (P.nt + K - 1) / K;
-    const int seg_len = K == 1 ? P.nt : K;
-    // K == 1: states[0..nt]; K >= 2: checkpoints at n = 0, K, 2K, ... (< nt),
-    // two forward work buffers, and a recompute buffer of K states.
-    const int nck = K == 1 ? P.nt + 1 : nseg;
-    const int nseg_buf = K == 1 ? 0 : K;
-    Real* mu[2];
-    double* grad = nullptr;
-    std::vector<Real*> ck(nck), segbuf(nseg_buf);
-    Real* work[2] = {nullptr, nullptr};
     const size_t SB = (Call<Real>::kTiled ? 2 : 1) * N * R;   // one state slot (see run_forward)
-    // FP32 checkpoints (K >= 2) also keep the increments before them (as many
-    // as the start extrapolates from), so a recomputed segment starts from the
-    // same extrapolation as the first sweep
-    const int ck_hist = Call<Real>::kTiled && K > 1 ? P.extrap : 0;
+    // FP32 checkpoints also keep the increments before them (as many as the
+    // start extrapolates from), so a recomputed segment starts from the same
+    // extrapolation as the first sweep
+    const int ck_hist_if = Call<Real>::kTiled ? P.extrap : 0;
+    const CkPlan plan = plan_checkpoints(P, fixed, h->budget, SB, (ck_hist_if + 1) / 2);
+    const int K = plan.K, gB = plan.gB;
+    const int B = (int)std::min((long long)gB * K, (long long)P.nt);   // recomputed steps [0, B)
+    const int ntail = B < P.nt ? P.nt - B + 1 : 0;                     // kept states T^B .. T^nt
+    const int ck_hist = gB > 0 ? ck_hist_if : 0;
     const bool ck_ring = ck_hist > 0;
     const int ck_slots = (ck_hist + 1) / 2;   // state slots (2N floats) holding them
+    Real* mu[2];
+    double* grad = nullptr;
+    std::vector<Real*> ck(gB), segbuf(gB > 0 ? K : 0), tail(ntail);
+    Real* work[2] = {nullptr, nullptr};
     auto layout = [&](Arena& a) {
         C.place_common(a, 7 * nt + 4);
         grad = (double*)a.take(N * sizeof(double));
         ga.place(a);
         gt.place(a);
-        // state slots: mu[2], checkpoints, recompute buffer, forward work pair
-        const size_t slots = 3 + (size_t)nck * (1 + ck_slots) + (size_t)nseg_buf + (K > 1 ? 2 : 0);
+        // state slots: mu[2], the next start, checkpoints, recompute buffer,
+        // forward work pair, kept tail
+        const size_t slots = (size_t)plan_slots(P.nt, K, gB, ck_slots);
         Real* next = C.carve_slab(a, slots, SB);
         auto slot = [&]() { Real* p = next; next += SB / R; return p; };
         mu[0] = slot();
         mu[1] = slot();
         Real* ys = slot();   // the next solve's start
         if (Call<Real>::kTiled) C.ystart = (float*)ys;
-        for (int i = 0; i < nck; ++i) {
+        for (int i = 0; i < gB; ++i) {
             ck[i] = slot();
             for (int k = 0; k < ck_slots; ++k) slot();   // [delta^{gK-1}; delta^{gK-2}; ...] after the state
         }
-        for (int i = 0; i < nseg_buf; ++i) segbuf[i] = slot();
-        if (K > 1) {
+        for (auto& p : segbuf) p = slot();
+        if (gB > 0) {
             work[0] = slot();
             work[1] = slot();
         }
+        for (auto& p : tail) p = slot();
     };
     Arena probe;
     layout(probe);
@@ -772,46 +820,50 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
     if (nefty_status e = C.upload_inputs()) return e;
     if (nefty_status e = C.coefficients()) return e;
     if (nefty_status e = C.prepare_tma()) return e;
-    NEFTY_CUDA(h, cudaMemsetAsync(ck[0], 0, SB, s));
-    if (C.T0.user) NEFTY_CUDA(h, cudaMemcpyAsync(ck[0], C.T0.dev, N * R, cudaMemcpyDeviceToDevice, s));
+    // where the first sweep keeps T^n
+    auto state_fwd = [&](int n) -> Real* {
+        if (ntail > 0 && n >= B) return tail[n - B];
+        if (n % K == 0 && n / K < gB) return ck[n / K];
+        return work[n & 1];
+    };
+    NEFTY_CUDA(h, cudaMemsetAsync(state_fwd(0), 0, SB, s));
+    if (C.T0.user) NEFTY_CUDA(h, cudaMemcpyAsync(state_fwd(0), C.T0.dev, N * R, cudaMemcpyDeviceToDevice, s));
     NEFTY_CUDA(h, cudaMemsetAsync(grad, 0, N * sizeof(double), s));
 
-    // Pointer tables: forward src/dst (2 nt), recompute src/dst (2 nt), adjoint T (nt + nseg),
-    // ring saves of the first sweep (nt).
+    // Pointer tables: forward src/dst (2 nt), recompute src/dst (2 nt), adjoint T
+    // (nt + segments), ring saves of the first sweep (nt).
     std::vector<Real*> tab(7 * nt + 4, nullptr);
     Real** F_src = tab.data();
     Real** F_dst = tab.data() + nt;
     Real** R_src = tab.data() + 2 * nt;
     Real** R_dst = tab.data() + 3 * nt;
     Real** A_T = tab.data() + 4 * nt;
-    auto state_fwd = [&](int n) -> Real* {   // where the first sweep keeps T^n
-        if (K == 1) return ck[n];
-        if (n % K == 0 && n / K < nseg) return ck[n / K];
-        return work[n & 1];
-    };
     Real** F_ring = tab.data() + 6 * nt + 4;
     for (int n = 0; n < P.nt; ++n) {
         F_src[n] = state_fwd(n);
         F_dst[n] = state_fwd(n + 1);
-        if (ck_ring && (n + 1) % K == 0 && (n + 1) / K < nseg) F_ring[n] = ck[(n + 1) / K] + 2 * N;
+        if (ck_ring && n + 1 < B && (n + 1) % K == 0) F_ring[n] = ck[(n + 1) / K] + 2 * N;
     }
-    // segment g covers steps [g K, min(g K + K, nt)]; its recomputed states
-    // T^{gK+j} go to segbuf[j-1], j = 1..len; T^{gK} is checkpoint g.
+    // Reverse-sweep segments, latest first: the kept tail [B, nt], then
+    // segment g = gB-1 .. 0 over [g K, min(g K + K, B)], recomputed from
+    // checkpoint g into segbuf (T^{gK+j} -> segbuf[j-1]).
+    struct Seg { int a0, a1; bool rec; size_t aoff; };
+    std::vector<Seg> segs;
     size_t aoff = 0;
-    std::vector<size_t> seg_aoff(nseg);
-    for (int g = 0; g < nseg; ++g) {
-        const int a0 = g * seg_len, a1 = std::min(a0 + seg_len, P.nt);
-        seg_aoff[g] = aoff;
-        for (int n = a0; n <= a1; ++n) {
-            Real* Tn = (K == 1) ? ck[n] : (n == a0 ? ck[g] : segbuf[n - a0 - 1]);
-            A_T[aoff + (n - a0)] = Tn;
-        }
+    if (ntail > 0) {
+        segs.push_back(Seg{B, P.nt, false, aoff});
+        for (int n = B; n <= P.nt; ++n) A_T[aoff + (n - B)] = tail[n - B];
+        aoff += (size_t)ntail;
+    }
+    for (int g = gB - 1; g >= 0; --g) {
+        const int a0 = g * K, a1 = std::min(a0 + K, B);
+        segs.push_back(Seg{a0, a1, true, aoff});
+        for (int n = a0; n <= a1; ++n) A_T[aoff + (n - a0)] = n == a0 ? ck[g] : segbuf[n - a0 - 1];
         aoff += (size_t)(a1 - a0 + 1);
-        if (K > 1)
-            for (int n = a0; n < a1; ++n) {
-                R_src[n] = n == a0 ? ck[g] : segbuf[n - a0 - 1];
-                R_dst[n] = segbuf[n - a0];
-            }
+        for (int n = a0; n < a1; ++n) {
+            R_src[n] = n == a0 ? ck[g] : segbuf[n - a0 - 1];
+            R_dst[n] = segbuf[n - a0];
+        }
     }
     NEFTY_CUDA(h, cudaMemcpyAsync(C.tables, tab.data(), tab.size() * sizeof(Real*), cudaMemcpyHostToDevice, s));
     Real** dF_src = C.tables;
@@ -847,7 +899,7 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
     // reverse sweep, one segment at a time
     NEFTY_CUDA(h, cudaMemsetAsync(mu[(P.nt + 1) & 1], 0, SB, s));
     int rec_steps = 0, adj_steps = 0;
-    AdjArgs<Real> aa;
+    AdjArgs<Real> aa{};
     aa.op = make_view<Real>(P, C.coef);
     aa.r = C.r; aa.p = C.p; aa.q = C.q;
     aa.mu[0] = mu[0]; aa.mu[1] = mu[1];
@@ -861,11 +913,13 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
     aa.grad = grad;
     aa.tol2 = P.rtol * P.rtol;
     aa.max_iter = P.max_iter;
+    aa.jacobi_k = P.jacobi_k;
     aa.ctl = C.ctl;
     aa.partials = C.partials;
-    for (int g = nseg - 1; g >= 0; --g) {
-        const int a0 = g * seg_len, a1 = std::min(a0 + seg_len, P.nt);
-        if (K > 1) {
+    for (const Seg& sg : segs) {
+        const int a0 = sg.a0, a1 = sg.a1;
+        if (sg.rec) {
+            const int g = a0 / K;
             if (nefty_status e = C.forward_steps(a0, a1, dR_src + a0, dR_dst + a0, C.iters + nt + rec_steps,
                                                  C.resid + nt + rec_steps, nullptr, nullptr, nullptr, 1,
                                                  ck_ring && g > 0 ? ck[g] + 2 * N : nullptr, nullptr,
@@ -882,7 +936,7 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
             ta.ystart = C.ystart;
             ta.extrap = P.extrap;
             ta.hist0 = std::min(adj_steps, tiled::kRing);
-            ta.T = (float* const*)(dA_T + seg_aoff[g]);
+            ta.T = (float* const*)(dA_T + sg.aoff);
             ta.mu[0] = mu[0];
             ta.mu[1] = mu[1];
             ta.alpha = (const float*)C.alpha.dev;
@@ -895,7 +949,7 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
         } else {
             aa.n0 = a0;
             aa.n1 = a1;
-            aa.T = dA_T + seg_aoff[g];
+            aa.T = dA_T + sg.aoff;
             aa.iters = C.iters + 2 * nt + adj_steps;
             aa.resid = C.resid + 2 * nt + adj_steps;
             if (nefty_status e = C.launch_adj(aa)) return e;
@@ -916,7 +970,7 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
     for (Output* o : {&ga, &gt})
         if (o->user && o->stage)
             NEFTY_CUDA(h, cudaMemcpyAsync(o->user, o->dev, o->bytes, cudaMemcpyDeviceToHost, s));
-    return C.finish(loss_out, true, st, P.nt, rec_steps, adj_steps, K, nck + nseg_buf);
+    return C.finish(loss_out, true, st, P.nt, rec_steps, adj_steps, K, gB + (int)segbuf.size() + ntail);
 }
 
 }  // namespace

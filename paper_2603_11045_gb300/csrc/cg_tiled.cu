@@ -392,7 +392,8 @@ enum PassKind : int {
     kIter,    // 0 u_i, 1 ws_i, 2 ss_{i-1}, 3 alpha, 4-5 p and delta (own boxes)
     kInit1,   // 0 start hi, 1 start lo, 3 alpha, 4-5 p and delta (own boxes; delta = d when used)
     kInit2,   // 0 u_0, 3 alpha
-    kGrad     // 0 T hi, 1 T lo, 3 alpha, 4 mu hi, 5 mu lo
+    kGrad,    // 0 T hi, 1 T lo, 3 alpha, 4 mu hi, 5 mu lo
+    kJacobi   // 0-2 u, ws, ss of set 0 (u0 and the two sweep buffers), 3 alpha
 };
 struct PassIn {
     int kind;
@@ -406,6 +407,7 @@ __device__ __forceinline__ unsigned pass_bytes(const PassIn& in) {
         case kIter: return 4 * SZ_H + 2 * SZ_O;
         case kInit1: return 3 * SZ_H + (in.hu > 0 ? 2 * SZ_O : 0);
         case kInit2: return 2 * SZ_H;
+        case kJacobi: return 4 * SZ_H;
         default: return 5 * SZ_H;
     }
 }
@@ -546,6 +548,10 @@ __device__ bool produce(const Common& C, Ring& R, const PassIn& in, int from, in
                     break;
                 case kInit2:
                     tma_load3(dst, &M->u0, xh, yh, k, bar);
+                    tma_load3(dst + OFF_A, &M->alpha, xh, yh, k, bar);
+                    break;
+                case kJacobi:
+                    tma_load4(dst, &M->uws[0], xh, yh, k, 0, bar);
                     tma_load3(dst + OFF_A, &M->alpha, xh, yh, k, bar);
                     break;
                 default:
@@ -981,6 +987,60 @@ struct Init2Body {
     }
 };
 
+// ---- one sweep of the paper's Jacobi inner solver (App. D.2, Eq. jacobi_iter)
+// on the increment delta = T - T^(0): the sweep T <- D^{-1}(b - R T) reads
+// delta' = u0 + D^{-1} sum_f c_f delta_q with u0 = D^{-1} r0 (slot 0) and
+// delta in slot `src` (0 for the first sweep, when delta = u0; else 1 or 2).
+struct JacobiBody {
+    const Common& C;
+    int src;
+    float* out;
+    float dm[4], am[4], dc[4], ac[4], dp[4], ap[4], czm[4], czp[4];
+    __device__ JacobiBody(const Common& c, int s, float* o) : C(c), src(s), out(o) {}
+    __device__ __forceinline__ void reset() { set4(dm, 0.f); set4(am, 0.f); set4(czm, 0.f); }
+    __device__ __forceinline__ void below(const unsigned char* st, int hb) {
+        ld4(st, sl(src), hb, dm);
+        ld4(st, sl(3), hb, am);
+    }
+    __device__ __forceinline__ void own(const unsigned char* st, int hb, bool has_below) {
+        ld4(st, sl(src), hb, dc);
+        ld4(st, sl(3), hb, ac);
+        if (has_below) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) czm[j] = face(ac[j], am[j], C.kz);
+        }
+    }
+    __device__ __forceinline__ void above(const unsigned char* st, int hb) {
+        ld4(st, sl(src), hb, dp);
+        ld4(st, sl(3), hb, ap);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) czp[j] = face(ac[j], ap[j], C.kz);
+    }
+    __device__ __forceinline__ void top() { set4(dp, 0.f); set4(ap, 0.f); set4(czp, 0.f); }
+    __device__ __forceinline__ void plane(int k, unsigned c, bool valid, const unsigned char* st,
+                                          const unsigned char*, int hb, int) {
+        if (!valid) return;
+        float dym[4], dyp[4], u0[4], cx[5], cyp[4], cym[4], o[4];
+        ld4(st, sl(src), hb - HB, dym);
+        ld4(st, sl(src), hb + HB, dyp);
+        ld4(st, sl(0), hb, u0);
+        const float dxl = lds1(st, sl(src), hb - 1), dxr = lds1(st, sl(src), hb + 4);
+        quad_faces(st, hb, ac, C.kx, C.ky, cx, cyp, cym);
+        const float rob = k + 1 == C.g.nz ? C.robin : 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float sum = cx[j + 1] * (j < 3 ? dc[j + 1] : dxr) + cx[j] * (j > 0 ? dc[j - 1] : dxl) +
+                              cyp[j] * dyp[j] + cym[j] * dym[j] + czp[j] * dp[j] + czm[j] * dm[j];
+            o[j] = fmaf(rcp_approx(diag(cx[j + 1], cx[j], cyp[j], cym[j], czp[j], czm[j], rob)), sum, u0[j]);
+        }
+        stg4(out + c, o);
+    }
+    __device__ __forceinline__ void shift() {
+        cpy4(dm, dc); cpy4(czm, czp);
+        cpy4(dc, dp); cpy4(ac, ap);
+    }
+};
+
 // ---- gradient of one step (Eq. grad_assembly) at the own cells:
 // g_c -= sum_f w_f h^2 (mu_c - mu_q)(T_c - T_q), h = alpha_q / (alpha_c + alpha_q),
 // with T and mu as compensated pairs.  A face between two cells of the same
@@ -1386,6 +1446,79 @@ __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, co
     return true;
 }
 
+// One solve by the paper's inner solver (App. D.2): exactly K Jacobi sweeps
+// from the warm start x0 (st0.hu must be 0), on the increment as in solve():
+// the initial-residual pass gives u0 = D^{-1} r0, which is the first sweep;
+// sweeps 2..K alternate between the ws and ss buffers of set 0, the last one
+// writes delta.  No reduction, one grid barrier per sweep.
+template <bool kTma, class RhsFn>
+__device__ bool solve_jacobi(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, const Start& st0, RhsFn rhs,
+                             int K) {
+    const Geo& g = C.g;
+    Acc<3> acc3;   // the pass's sums are not needed here
+    if constexpr (kTma) {
+        PassIn in{kInit1, 0, false, 0u, 0u, 0};
+        if (!slab_half(C, st0.y, &in.zx)) return false;
+        Init1Body<RhsFn> B(C, rhs, acc3, 0);
+        if (!staged(C, ring, in, B, pre.n, pre.ok)) return false;
+    } else {
+        const unsigned N = g.S * (unsigned)g.nz;
+        const float* __restrict__ yh = st0.y;
+        const float* __restrict__ yl = st0.y + N;
+        for_cells(g, [&](int k, unsigned c, int x, int y) {
+            const Nb n = neighbours(g, c, x, y, k);
+            const float ac = C.alpha[c];
+            float cf[6];
+            cell_faces(C, n, ac, cf);
+            const float rob = k + 1 == g.nz ? C.robin : 0.f;
+            const float fc = yh[c], lc = yl[c];
+            float sh = 0.f, sx = 0.f;
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+                if (n.m >> i & 1u) exact_term(cf[i], fc, lc, yh[n.q[i]], yl[n.q[i]], sh, sx);
+            exact_sink(rob, fc, lc, sh, sx);
+            const float r = (rhs(c, k) - sh) - sx;
+            C.v.u[0][c] = rcp_approx(diag(cf[0], cf[1], cf[2], cf[3], cf[4], cf[5], rob)) * r;
+        });
+    }
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    if (!barrier(sy)) return false;
+    const unsigned N = g.S * (unsigned)g.nz;
+    if (K <= 1) {   // delta = u0
+        const unsigned stride = gridDim.x * NT;
+        for (unsigned c = blockIdx.x * NT + threadIdx.x; c < N; c += stride) C.v.delta[c] = C.v.u[0][c];
+        return barrier(sy);
+    }
+    int src = 0;   // slot (and buffer of set 0) holding the current delta
+    for (int kappa = 1; kappa < K; ++kappa) {
+        const int dst = src == 1 ? 2 : 1;
+        float* out = kappa == K - 1 ? C.v.delta : (dst == 1 ? C.v.ws[0] : C.v.ss[0]);
+        if constexpr (kTma) {
+            JacobiBody B(C, src, out);
+            if (!staged(C, ring, PassIn{kJacobi, 0, false, 0u, 0u}, B)) return false;
+        } else {
+            const float* __restrict__ in = src == 0 ? C.v.u[0] : (src == 1 ? C.v.ws[0] : C.v.ss[0]);
+            const float* __restrict__ u0 = C.v.u[0];
+            for_cells(g, [&](int k, unsigned c, int x, int y) {
+                const Nb n = neighbours(g, c, x, y, k);
+                const float ac = C.alpha[c];
+                float cf[6];
+                cell_faces(C, n, ac, cf);
+                const float rob = k + 1 == g.nz ? C.robin : 0.f;
+                float sum = 0.f;
+#pragma unroll
+                for (int i = 0; i < 6; ++i)
+                    if (n.m >> i & 1u) sum += cf[i] * in[n.q[i]];
+                out[c] = fmaf(rcp_approx(diag(cf[0], cf[1], cf[2], cf[3], cf[4], cf[5], rob)), sum, u0[c]);
+            });
+        }
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        if (!barrier(sy)) return false;
+        src = dst;
+    }
+    return true;
+}
+
 __device__ __forceinline__ void prefetch_maps(const TmaMaps& M) {
     tma_prefetch_desc(&M.uws[0]);
     tma_prefetch_desc(&M.uws[1]);
@@ -1607,9 +1740,14 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(const __grid_constant__ F
         float rel = 0.f;
         bool conv = true;
         const int hu = hu_at(n);
-        bool ok = solve<kTma>(a.c, sy, ring, pre, Start{hu > 0 ? a.ystart : Tn, hu},
-                        [&](unsigned c, int k) { return (qmap && k == 0) ? sc * qmap[c] : 0.f; }, &it, &rel,
-                        &conv);
+        auto rhs = [&](unsigned c, int k) { return (qmap && k == 0) ? sc * qmap[c] : 0.f; };
+        bool ok;
+        if (a.c.jacobi_k > 0) {   // the paper's inner solver: K sweeps from T^n
+            ok = solve_jacobi<kTma>(a.c, sy, ring, pre, Start{Tn, 0}, rhs, a.c.jacobi_k);
+            it = a.c.jacobi_k;
+        } else {
+            ok = solve<kTma>(a.c, sy, ring, pre, Start{hu > 0 ? a.ystart : Tn, hu}, rhs, &it, &rel, &conv);
+        }
         if (!ok) return;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             a.c.iters[n - a.n0] = it;
@@ -1681,12 +1819,17 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ A
         float rel = 0.f;
         bool conv = true;
         const int hu = hu_at(n);
-        bool ok = solve<kTma>(a.c, sy, ring, pipe_none(), Start{hu > 0 ? a.ystart : mnext, hu},
-                        [&](unsigned c, int) {
-                            return (c >= a.obs_off && c < a.obs_off + S)
-                                       ? gs * ((Tn[c] - ob[c - a.obs_off]) + Tn[N + c]) : 0.f;
-                        },
-                        &it, &rel, &conv);
+        auto rhs = [&](unsigned c, int) {
+            return (c >= a.obs_off && c < a.obs_off + S) ? gs * ((Tn[c] - ob[c - a.obs_off]) + Tn[N + c]) : 0.f;
+        };
+        bool ok;
+        if (a.c.jacobi_k > 0) {   // the paper's inner solver: K sweeps from mu^{n+1}
+            ok = solve_jacobi<kTma>(a.c, sy, ring, pipe_none(), Start{mnext, 0}, rhs, a.c.jacobi_k);
+            it = a.c.jacobi_k;
+        } else {
+            ok = solve<kTma>(a.c, sy, ring, pipe_none(), Start{hu > 0 ? a.ystart : mnext, hu}, rhs, &it, &rel,
+                             &conv);
+        }
         if (!ok) return;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             a.c.iters[a.n1 - n] = it;

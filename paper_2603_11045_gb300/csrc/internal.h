@@ -68,6 +68,7 @@ struct FwdArgs {
     int* iters;                        // per-step CG iterations [n1 - n0]
     double* resid;                     // per-step final ||r||/||b||
     double* loss_partials;             // [G] per-CTA sum of squared frame errors
+    int jacobi_k;                      // > 0: K Jacobi sweeps per solve instead of CG
 };
 
 // Arguments of the adjoint persistent kernel: steps n = n1 down to n0 + 1.
@@ -90,6 +91,7 @@ struct AdjArgs {
     double* partials;
     int* iters;                        // per-step iterations, index n1 - n
     double* resid;
+    int jacobi_k;                      // > 0: K Jacobi sweeps per solve instead of CG
 };
 
 // ------------------------------------------------------------ serving (serve.cu)
@@ -192,6 +194,7 @@ struct Common {
     double* partials;      // [2][G][kMaxRed] (hi, lo) float pairs
     float tol2_hi, tol2_lo;   // rtol^2 as a double-float
     int max_iter;
+    int jacobi_k;          // > 0: every solve is K Jacobi sweeps from its warm start (no CG)
     int* iters;
     double* resid;
 };

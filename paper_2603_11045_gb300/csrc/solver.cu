@@ -229,6 +229,33 @@ __device__ bool cg_iterate(Grid& g, const OperatorView<Real>& op, Real* __restri
     return true;
 }
 
+// The paper's inner solver (App. D.2, Eq. jacobi_iter) on the increment:
+// with T^(0) the warm start and r0 = b - A T^(0), the sweep
+// T <- D^{-1}(b - R T) is delta <- delta + D^{-1}(r0 - A delta) for
+// delta = T - T^(0).  Given p = D^{-1} r0 (the first sweep from delta = 0),
+// runs the other K - 1 sweeps (ping-pong p / q) and leaves delta^(K) in x.
+template <typename Real>
+__device__ bool jacobi_iterate(Grid& g, const OperatorView<Real>& op, Real* __restrict__ x,
+                               const Real* __restrict__ r, Real* __restrict__ p, Real* __restrict__ q, int K) {
+    const unsigned N = op.N;
+    const unsigned stride = gridDim.x * kThreads;
+    const unsigned c0 = blockIdx.x * kThreads + threadIdx.x;
+    if (K <= 1) {
+        for (unsigned c = c0; c < N; c += stride) x[c] = p[c];
+        return true;
+    }
+    Real* in = p;
+    Real* spare = q;
+    for (int kappa = 1; kappa < K; ++kappa) {
+        Real* out = kappa == K - 1 ? x : spare;
+        for (unsigned c = c0; c < N; c += stride) out[c] = in[c] + op.dinv[c] * (r[c] - apply_A(op, in, c));
+        if (!grid_sync(g)) return false;
+        spare = in;
+        in = out;
+    }
+    return true;
+}
+
 __device__ __forceinline__ Grid make_grid(DevCtl* ctl, double* partials) {
     Grid g;
     g.ctl = ctl;
@@ -271,12 +298,16 @@ __global__ void __launch_bounds__(kThreads) forward_kernel(FwdArgs<Real> a) {
         if (!grid_sum<3>(g, s3)) return;
         int it = 0;
         double rel = 0.0;
-        if (!cg_iterate(g, op, x, a.r, a.p, a.q, s3[0], s3[1], s3[2], a.tol2, a.max_iter, &it, &rel))
+        if (a.jacobi_k > 0) {
+            if (!jacobi_iterate(g, op, x, a.r, a.p, a.q, a.jacobi_k)) return;
+            it = a.jacobi_k;
+        } else if (!cg_iterate(g, op, x, a.r, a.p, a.q, s3[0], s3[1], s3[2], a.tol2, a.max_iter, &it, &rel)) {
             return;
+        }
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             a.iters[n - a.n0] = it;
             a.resid[n - a.n0] = rel;
-            if (it >= a.max_iter && rel * rel > a.tol2) atomicAdd(&a.ctl->notconv, 1);
+            if (a.jacobi_k == 0 && it >= a.max_iter && rel * rel > a.tol2) atomicAdd(&a.ctl->notconv, 1);
         }
         // T^{n+1} = T^n + delta: the increment was accumulated on its own so that
         // corrections far below one ulp of T survive; one rounding per step.
@@ -386,12 +417,16 @@ __global__ void __launch_bounds__(kThreads) adjoint_kernel(AdjArgs<Real> a) {
         if (!grid_sum<3>(g, s3)) return;
         int it = 0;
         double rel = 0.0;
-        if (!cg_iterate(g, op, x, a.r, a.p, a.q, s3[0], s3[1], s3[2], a.tol2, a.max_iter, &it, &rel))
+        if (a.jacobi_k > 0) {
+            if (!jacobi_iterate(g, op, x, a.r, a.p, a.q, a.jacobi_k)) return;
+            it = a.jacobi_k;
+        } else if (!cg_iterate(g, op, x, a.r, a.p, a.q, s3[0], s3[1], s3[2], a.tol2, a.max_iter, &it, &rel)) {
             return;
+        }
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             a.iters[a.n1 - n] = it;
             a.resid[a.n1 - n] = rel;
-            if (it >= a.max_iter && rel * rel > a.tol2) atomicAdd(&a.ctl->notconv, 1);
+            if (a.jacobi_k == 0 && it >= a.max_iter && rel * rel > a.tol2) atomicAdd(&a.ctl->notconv, 1);
         }
         // mu^n = mu^{n+1} + delta (increment accumulated on its own, as forward)
         for (unsigned c = c0; c < N; c += stride) x[c] = mnext[c] + x[c];

@@ -144,7 +144,7 @@ nefty_status run(int dev, char* base, const nefty_problem& p, const void* alpha,
     }
     static_tables_kernel<Real><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(tab, tab + nt, t0, w0, w1, (int)nt);
     NS_CUDA(cudaGetLastError());
-    FwdArgs<Real> a;
+    FwdArgs<Real> a{};
     a.op.nx = p.nx; a.op.ny = p.ny; a.op.nz = p.nz;
     a.op.px = p.bc == NEFTY_BC_PERIODIC_XY && p.nx > 1;
     a.op.py = p.bc == NEFTY_BC_PERIODIC_XY && p.ny > 1;
@@ -195,6 +195,7 @@ extern "C" nefty_status nefty_forward_static(int device, const nefty_problem* p,
                                              double* loss_out, void* stream) {
     using namespace nefty;
     if (nefty_problem_check(p) != NEFTY_OK) return NEFTY_EINVAL;   // message already set
+    if (p->jacobi_k != 0) return fail(NEFTY_EINVAL, "jacobi_k is not supported by the no-allocation entry point");
     if (!alpha) return fail(NEFTY_EINVAL, "alpha is NULL");
     if (loss_out && !obs) return fail(NEFTY_EINVAL, "loss_out needs obs");
     if (q_steps < 0) return fail(NEFTY_EINVAL, "q_steps must be >= 0");

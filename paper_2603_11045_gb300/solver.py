@@ -40,6 +40,7 @@ class Problem:
     ckpt_every: int = 0
     loss_scale: float = 0.0
     extrap: int = 0
+    jacobi_k: int = 0
 
     @classmethod
     def from_workload(cls, w, **kw) -> "Problem":

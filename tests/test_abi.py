@@ -66,7 +66,7 @@ def _problem(**kw):
 
 @pytest.mark.parametrize("bad", [dict(nx=0), dict(nt=0), dict(dx=0.0), dict(dz=-1.0), dict(dt=0.0),
                                  dict(bc=7), dict(obs_face=2), dict(robin_h=-0.1), dict(rtol=-1.0),
-                                 dict(max_iter=-1), dict(ckpt_every=-2), dict(loss_scale=-1.0), dict(extrap=5), dict(extrap=-2),
+                                 dict(max_iter=-1), dict(ckpt_every=-2), dict(loss_scale=-1.0), dict(extrap=5), dict(extrap=-2), dict(jacobi_k=-1), dict(jacobi_k=100001),
                                  dict(nx=2048, ny=2048, nz=512), dict(dx=float("nan"))])
 def test_problem_validation_rejects(lib, bad):
     p = _problem(**bad)

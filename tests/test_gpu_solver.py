@@ -351,3 +351,96 @@ def test_fp32_adjoint_tiny_misfit_scale(solver):
         g = tiny[key].double().cpu() / 1e-30
         assert torch.isfinite(g).all()
         assert rel_l2(g, ref[key].double().cpu()) <= 1e-5, key
+
+
+def test_budget_checkpoint_plan_keeps_a_tail():
+    """With a memory budget between the every-state and the sqrt(nt)
+    layouts, the automatic plan checkpoints the first part of the horizon
+    and keeps every state of the rest: fewer steps recomputed than a full
+    forward sweep, the workspace within the budget, and the gradient bitwise
+    equal to keeping every state (recomputed segments replay the first sweep's
+    bits)."""
+    from paper_2603_11045_gb300.solver import Problem, Solver
+    w = S.inclusion_case(nx=64, ny=64, nz=16, nt=80, seed=1013)
+    prob = Problem.from_workload(w, prec="fp32")
+    a, q = dev(w.alpha, "fp32"), dev(w.q_face, "fp32")
+    with Solver(0) as s0:
+        obs = s0.forward(prob, dev(w.alpha_target, "fp32"), q_face=q, q_steps=3)["frames"]
+    runs = {}
+    for key, kw in (("all", dict(ckpt_every=1)), ("sqrt", dict(ckpt_every=9))):
+        with Solver(0) as s:
+            runs[key] = s.adjoint_grad(prob.with_(**kw), a, obs, q_face=q, q_steps=3)
+    w_all = runs["all"]["stats"]["workspace_bytes"]
+    w_sqrt = runs["sqrt"]["stats"]["workspace_bytes"]
+    assert w_sqrt < w_all
+    budget = (w_all + w_sqrt) // 2
+    with Solver(0, mem_budget_bytes=budget) as s:
+        auto = s.adjoint_grad(prob, a, obs, q_face=q, q_steps=3)
+    st = auto["stats"]
+    assert 0 < st["recompute_steps"] < prob.nt, st
+    assert st["recompute_steps"] < runs["sqrt"]["stats"]["recompute_steps"], st
+    assert st["workspace_bytes"] <= budget, (st["workspace_bytes"], budget)
+    assert torch.equal(auto["grad_alpha"], runs["all"]["grad_alpha"])
+    assert auto["loss"] == runs["all"]["loss"]
+
+
+# ------------------------------------------------------------- Jacobi-K mode
+def _jacobi_pair(solver, orc, w, prec, K, ckpt_every=0):
+    """GPU and oracle with every solve K Jacobi sweeps from its warm start."""
+    from paper_2603_11045_gb300.solver import Problem
+    alpha, q = _cast(w.alpha, prec), _cast(w.q_face, prec)
+    op = orc.from_workload(w)
+    obs = _cast(orc.forward(op, _cast(w.alpha_target, prec), q_face=q, q_steps=w.q_steps,
+                            jacobi_k=K)["frames"], prec)
+    ref = orc.adjoint_grad(op, alpha, q_face=q, q_steps=w.q_steps, obs=obs, jacobi_k=K)
+    ref_f = orc.forward(op, alpha, q_face=q, q_steps=w.q_steps, jacobi_k=K)
+    prob = Problem.from_workload(w, prec=prec, jacobi_k=K, ckpt_every=ckpt_every)
+    f = solver.forward(prob, dev(alpha, prec), q_face=dev(q, prec), q_steps=w.q_steps)
+    g = solver.adjoint_grad(prob, dev(alpha, prec), dev(obs, prec), q_face=dev(q, prec), q_steps=w.q_steps,
+                            grad_T0=True)
+    return dict(frames=f["frames"].cpu().numpy(), ref_frames=ref_f["frames"], loss=g["loss"],
+                ref_loss=ref["loss"], grad=g["grad_alpha"].cpu().numpy(), ref_grad=ref["grad_alpha"],
+                gT0=g["grad_T0"].cpu().numpy(), ref_gT0=ref["grad_T0"], stats=g["stats"])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape,K", [((32, 32, 8), 50), ((30, 28, 6), 7), ((36, 20, 5), 1)])
+def test_jacobi_k_matches_oracle(solver, orc, prec, shape, K):
+    """The paper's inner solver (App. D.2): K Jacobi sweeps per forward and
+    adjoint solve, on the TMA-staged grid (32x32x8, the paper's K = 50), a grid
+    the plain-load kernels take (nx % 4 != 0) and K = 1."""
+    nx, ny, nz = shape
+    w = S.inclusion_case(nx=nx, ny=ny, nz=nz, nt=40, seed=1020 + K)
+    r = _jacobi_pair(solver, orc, w, prec, K)
+    assert rel_l2(r["frames"], r["ref_frames"]) <= SURF_TOL[prec]
+    assert r["loss"] == pytest.approx(r["ref_loss"], rel=1e-9 if prec == "fp64" else 1e-4)
+    gtol = 1e-9 if prec == "fp64" else 1e-3
+    assert rel_l2(r["grad"], r["ref_grad"]) <= gtol and cosine(r["grad"], r["ref_grad"]) >= 0.9999
+    assert rel_l2(r["gT0"], r["ref_gT0"]) <= gtol
+    assert r["stats"]["fwd_iters"] == K * w.nt and r["stats"]["adj_iters"] == K * w.nt
+    assert r["stats"]["not_converged"] == 0
+
+
+def test_jacobi_k_is_not_the_converged_solve(solver, orc):
+    """A few sweeps leave the Jacobi error of App. D.2 in the state: frames
+    differ from the converged solve, and approach it as K grows."""
+    from paper_2603_11045_gb300.solver import Problem
+    w = S.inclusion_case(nx=32, ny=32, nz=8, nt=20, seed=1030)
+    a, q = dev(w.alpha, "fp64"), dev(w.q_face, "fp64")
+    exact = solver.forward(Problem.from_workload(w, prec="fp64", rtol=1e-14), a, q_face=q, q_steps=3)["frames"]
+    errs = [rel_l2(solver.forward(Problem.from_workload(w, prec="fp64", jacobi_k=K), a, q_face=q,
+                                  q_steps=3)["frames"].cpu(), exact.cpu()) for K in (2, 8, 32)]
+    assert errs[0] > 1e-4 and errs[0] > errs[1] > errs[2], errs
+
+
+def test_jacobi_k_recompute_is_bitwise(solver):
+    """Checkpoint recompute replays the sweeps exactly (FP32, K = 9)."""
+    from paper_2603_11045_gb300.solver import Problem
+    w = S.inclusion_case(nx=64, ny=64, nz=16, nt=30, seed=1031)
+    a, q = dev(w.alpha, "fp32"), dev(w.q_face, "fp32")
+    prob = Problem.from_workload(w, prec="fp32", jacobi_k=9)
+    obs = solver.forward(prob, dev(w.alpha_target, "fp32"), q_face=q, q_steps=3)["frames"]
+    k1 = solver.adjoint_grad(prob.with_(ckpt_every=1), a, obs, q_face=q, q_steps=3)
+    k7 = solver.adjoint_grad(prob.with_(ckpt_every=7), a, obs, q_face=q, q_steps=3)
+    assert torch.equal(k7["grad_alpha"], k1["grad_alpha"]) and k7["loss"] == k1["loss"]
+    assert k7["stats"]["recompute_steps"] == 30
