@@ -65,7 +65,7 @@ def parse():
                     help="FP32 CG start: increments extrapolated from (0 = the library default, -1 = none)")
     ap.add_argument("--cpu-sample-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="inversion", choices=["inversion", "serving", "stress"],
+    ap.add_argument("--workload", default="inversion", choices=["inversion", "serving", "stress", "jacobi"],
                     help="inversion: the timed inversion step (default); serving: latency of a job stream; "
                          "stress: one forward + adjoint at 512x512x96, 2000 steps, sqrt-checkpointing")
     ap.add_argument("--stress-fp64", action="store_true", help="stress: also run the FP64 path and compare")
@@ -502,6 +502,68 @@ def run_serving(args):
     return 0
 
 
+# ------------------------------------------------------------------ jacobi
+def run_jacobi(args):
+    """The paper's inner solver against the converged one (App. D.2: K = 50
+    unrolled Jacobi sweeps per solve, whose result the paper takes as the
+    exact state).  For K Jacobi sweeps per forward and adjoint solve (FP32):
+    the surface frames' and the gradient's distance from the converged FP64
+    solve (rtol 1e-13), and the device time per forward + adjoint step, beside
+    the FP32 Jacobi-PCG path, on the paper's grid and on the bench grid."""
+    import torch
+    from paper_2603_11045_gb300 import synthetic as S
+    from paper_2603_11045_gb300.solver import Problem, Solver
+
+    def rel(a, b):
+        return float((a.double() - b.double()).norm() / b.double().norm())
+
+    def cos(a, b):
+        a, b = a.double().flatten(), b.double().flatten()
+        return float(a @ b / (a.norm() * b.norm()))
+
+    import dataclasses
+    w2 = S.inclusion_case(nx=256, ny=256, nz=48, nt=200, seed=2001)
+    # candidate alpha = 1 against targets from the inclusion field: a misfit
+    # far above FP32 rounding, so the gradients can be compared
+    w2 = dataclasses.replace(w2, alpha=np.ones_like(w2.alpha), alpha_target=w2.alpha)
+    cases = [("paper grid 64x64x16, dx 0.156, dz 0.0625, dt 0.05, 100 frames, periodic lateral, post-flash T0",
+              S.paper_grid_case()),
+             ("inclusion field 256x256x48, dt 0.25, 200 steps, surface pulse, candidate alpha = 1", w2)]
+    solver = Solver(0)
+    out = []
+    for name, w in cases:
+        def arr(x, dt):
+            return None if x is None else torch.tensor(x, dtype=dt, device="cuda")
+        p64 = Problem.from_workload(w, prec="fp64", rtol=1e-13)
+        q64, T064 = arr(w.q_face, torch.float64), arr(w.T0, torch.float64)
+        obs = solver.forward(p64, arr(w.alpha_target, torch.float64), T0=T064, q_face=q64,
+                             q_steps=w.q_steps)["frames"]
+        a64 = arr(w.alpha, torch.float64)
+        ref_f = solver.forward(p64, a64, T0=T064, q_face=q64, q_steps=w.q_steps)["frames"]
+        ref_g = solver.adjoint_grad(p64, a64, obs, T0=T064, q_face=q64, q_steps=w.q_steps)["grad_alpha"]
+        q32, T032, a32, obs32 = (arr(w.q_face, torch.float32), arr(w.T0, torch.float32),
+                                 arr(w.alpha, torch.float32), obs.float())
+        rows = []
+        for K in [0, 10, 25, 50, 100, 200]:
+            p = Problem.from_workload(w, prec="fp32", jacobi_k=K)
+            f = solver.forward(p, a32, T0=T032, q_face=q32, q_steps=w.q_steps)["frames"]
+            solver.adjoint_grad(p, a32, obs32, T0=T032, q_face=q32, q_steps=w.q_steps)   # warm-up
+            g = solver.adjoint_grad(p, a32, obs32, T0=T032, q_face=q32, q_steps=w.q_steps)
+            st = g["stats"]
+            rows.append({"solver": "Jacobi-PCG (converged)" if K == 0 else f"Jacobi K={K}",
+                         "surface_rel_l2": rel(f, ref_f), "grad_rel_l2": rel(g["grad_alpha"], ref_g),
+                         "grad_cosine": cos(g["grad_alpha"], ref_g),
+                         "ms_per_step": (st["fwd_ms"] + st["adj_ms"] + st["recompute_ms"]) / w.nt,
+                         "iters_per_solve": (st["fwd_iters"] + st["adj_iters"]) / (2 * w.nt)})
+        out.append({"case": name, "cells": w.nx * w.ny * w.nz, "steps": w.nt, "rows": rows})
+        torch.cuda.empty_cache()
+    solver.close()
+    print(json.dumps({"metric": "Jacobi-K vs converged solve", "unit": "rel-L2 / ms", "n_gpus": 1,
+                      "dtype": "f32", "data": "synthetic", "reference": "FP64 Jacobi-PCG, rtol 1e-13",
+                      "cases": out}), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ stress
 def run_stress(args):
     """The largest configuration: 512x512x96 cells, 2000 steps of dt = 0.2,
@@ -566,6 +628,8 @@ def main():
         return run_serving(args)
     if args.workload == "stress":
         return run_stress(args)
+    if args.workload == "jacobi":
+        return run_jacobi(args)
     return run_native(args)
 
 

@@ -321,7 +321,7 @@ typedef struct {
     int32_t max_queue;          /* queued-job limit for NEFTY_EBUSY (0 = 4096) */
     uint64_t mem_budget_bytes;  /* device memory shared by the lanes (0 = 80% of free memory) */
     int32_t batched;            /* 0 or 1: batched launches (see above); -1: each lane its own grid */
-    int32_t chunk_steps;        /* batched: time steps of a sweep per launch (0 = about 2^25 cell-steps,
+    int32_t chunk_steps;        /* batched: time steps of a sweep per launch (0 = about 2^27 cell-steps,
                                    at least 4); smaller chunks admit new jobs sooner */
 } nefty_serve_config;
 

@@ -32,6 +32,11 @@ struct nefty_handle {
 };
 
 void nefty::set_grid_share(nefty_handle* h, int share) { h->grid_share = share > 1 ? share : 1; }
+uint64_t nefty::set_budget(nefty_handle* h, uint64_t bytes) {
+    const uint64_t old = h->budget;
+    h->budget = bytes;
+    return old;
+}
 void nefty::set_batcher(nefty_handle* h, Batcher* b) { h->batch = b; }
 void nefty::batch_counts(nefty_handle* h, int* launches, int* shared) {
     *launches = h->batch_launches;

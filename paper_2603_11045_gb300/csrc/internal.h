@@ -102,8 +102,10 @@ void server_stop(Server* s);
 nefty_status server_submit(Server* s, const nefty_job* job, uint64_t* id, std::string* why);
 nefty_status server_poll(Server* s, uint64_t id, nefty_job_result* out);
 nefty_status server_cancel(Server* s, uint64_t id);
-// api.cu: the persistent grids of h use 1/share of the device; workspace of a call.
+// api.cu: the persistent grids of h use 1/share of the device; h's memory
+// budget (returns the previous one); workspace of a call.
 void set_grid_share(nefty_handle* h, int share);
+uint64_t set_budget(nefty_handle* h, uint64_t bytes);
 nefty_status job_workspace_bytes(nefty_handle* h, const nefty_problem* p, bool adjoint, const void* alpha,
                                  const void* T0, const void* q_face, const void* q_full, const void* obs,
                                  size_t* bytes);

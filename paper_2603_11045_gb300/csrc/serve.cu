@@ -130,7 +130,7 @@ class Batcher {
     int grid() const { return grid_; }
     int chunk(unsigned N) const {
         if (chunk_steps_ > 0) return chunk_steps_;
-        return std::max(4, (int)std::min(1e6, 33554432.0 / (double)N));
+        return std::max(4, (int)std::min(1e6, 134217728.0 / (double)N));
     }
 
     nefty_status run(std::vector<tiled::BatchSweep>& chunks, int grid, cudaStream_t s, int* launches,
@@ -327,20 +327,24 @@ class Server {
             return st;
         }
         {
-            // smallest workspace of the job within one lane's share
+            // the job's workspace, planned within one lane's share less what
+            // the job holds outside the workspace (inversions: gradient and
+            // alpha copy), exactly as its lane will plan it
             std::lock_guard<std::mutex> lk(probe_mu_);
-            size_t bytes = 0;
-            st = job_workspace_bytes(probe_, &j.problem, j.kind == NEFTY_JOB_INVERSION, j.alpha, j.T0, j.q_face,
-                                     j.q_full, j.obs, &bytes);
-            if (st != NEFTY_OK) {
-                *why = nefty_last_error(probe_);
-                return st;
-            }
             const uint64_t share = cfg_.mem_budget_bytes / (uint64_t)cfg_.lanes;
-            const size_t R = j.problem.prec == NEFTY_FP64 ? 8 : 4;
-            const size_t N = (size_t)j.problem.nx * j.problem.ny * j.problem.nz;
-            const size_t extra = j.kind == NEFTY_JOB_INVERSION ? 2 * N * R : 0;   // gradient + alpha copy
-            if (bytes + extra > share) {
+            const uint64_t extra = job_extra_bytes(j);
+            size_t bytes = 0;
+            if (extra < share) {
+                const uint64_t old = set_budget(probe_, share - extra);
+                st = job_workspace_bytes(probe_, &j.problem, j.kind == NEFTY_JOB_INVERSION, j.alpha, j.T0,
+                                         j.q_face, j.q_full, j.obs, &bytes);
+                set_budget(probe_, old);
+                if (st != NEFTY_OK) {
+                    *why = nefty_last_error(probe_);
+                    return st;
+                }
+            }
+            if (extra >= share || bytes + extra > share) {
                 *why = "the job needs " + std::to_string(bytes + extra) + " bytes, more than a lane's share of " +
                        std::to_string(share);
                 return NEFTY_ENOMEM;
@@ -444,7 +448,22 @@ class Server {
         }
     }
 
+    // Device memory a job holds outside its handle's workspace.
+    static uint64_t job_extra_bytes(const nefty_job& j) {
+        const uint64_t R = j.problem.prec == NEFTY_FP64 ? 8 : 4;
+        const uint64_t N = (uint64_t)j.problem.nx * j.problem.ny * j.problem.nz;
+        return j.kind == NEFTY_JOB_INVERSION ? 2 * N * R : 0;   // gradient + alpha copy
+    }
+
     void run(Job& job, nefty_handle* h, cudaStream_t s) {
+        // the workspace is planned within the lane's share less the job's other memory
+        const uint64_t share = cfg_.mem_budget_bytes / (uint64_t)cfg_.lanes;
+        set_budget(h, share - job_extra_bytes(job.desc));
+        run_job(job, h, s);
+        set_budget(h, share);
+    }
+
+    void run_job(Job& job, nefty_handle* h, cudaStream_t s) {
         const nefty_job& j = job.desc;
         nefty_problem p = j.problem;
         p.ckpt_every = p.ckpt_every > 0 ? p.ckpt_every : 0;

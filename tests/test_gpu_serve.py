@@ -162,7 +162,7 @@ def test_lanes_overlap_jobs(solver, batched):
     take no longer than back to back."""
     import time
     w, p, alpha, q = _case(128, 128, 32, 150, 3008)
-    with Server(solver, lanes=2, batched=batched) as srv:
+    with Server(solver, lanes=2, batched=batched, chunk_steps=16) as srv:
         srv.wait(srv.submit(p, alpha, q_face=q, q_steps=w.q_steps))   # warm-up (workspace)
         srv.wait(srv.submit(p, alpha, q_face=q, q_steps=w.q_steps))
         t0 = time.perf_counter()
