@@ -46,7 +46,7 @@ ALG_BYTES_STEP = {"fp32": 8, "fp64": 16}
 # to the timed launches by their pass count (CG iterations plus the
 # init/finalise/gradient passes of each solve).  None = no capture of the
 # current kernels.
-DRAM_BYTES_PER_CELL_PASS = {"fp32": 24.1, "fp64": None}
+DRAM_BYTES_PER_CELL_PASS = {"fp32": 24.2, "fp64": None}
 
 
 def parse():

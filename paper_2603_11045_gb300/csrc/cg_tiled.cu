@@ -1705,7 +1705,7 @@ __device__ void load_hist(const float* __restrict__ src, const IncRing& R, int m
 // ------------------------------------------------------------- forward
 // kTma: iterations and stencil passes staged through TMA (a.c.tma set);
 // otherwise plain global loads.
-template <bool kTma>
+template <bool kTma, bool kJac>
 __global__ void __launch_bounds__(NT, 1) forward_tiled(const __grid_constant__ FwdTiled a) {
     extern __shared__ unsigned char dyn_smem[];
     __shared__ __align__(8) unsigned long long s_full[NS], s_empty[NS];
@@ -1742,7 +1742,7 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(const __grid_constant__ F
         const int hu = hu_at(n);
         auto rhs = [&](unsigned c, int k) { return (qmap && k == 0) ? sc * qmap[c] : 0.f; };
         bool ok;
-        if (a.c.jacobi_k > 0) {   // the paper's inner solver: K sweeps from T^n
+        if constexpr (kJac) {   // the paper's inner solver: K sweeps from T^n
             ok = solve_jacobi<kTma>(a.c, sy, ring, pre, Start{Tn, 0}, rhs, a.c.jacobi_k);
             it = a.c.jacobi_k;
         } else {
@@ -1787,7 +1787,7 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(const __grid_constant__ F
 }
 
 // ------------------------------------------------------------- adjoint
-template <bool kTma>
+template <bool kTma, bool kJac>
 __global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ AdjTiled a) {
     extern __shared__ unsigned char dyn_smem[];
     __shared__ __align__(8) unsigned long long s_full[NS], s_empty[NS];
@@ -1823,7 +1823,7 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ A
             return (c >= a.obs_off && c < a.obs_off + S) ? gs * ((Tn[c] - ob[c - a.obs_off]) + Tn[N + c]) : 0.f;
         };
         bool ok;
-        if (a.c.jacobi_k > 0) {   // the paper's inner solver: K sweeps from mu^{n+1}
+        if constexpr (kJac) {   // the paper's inner solver: K sweeps from mu^{n+1}
             ok = solve_jacobi<kTma>(a.c, sy, ring, pipe_none(), Start{mnext, 0}, rhs, a.c.jacobi_k);
             it = a.c.jacobi_k;
         } else {
@@ -2249,7 +2249,10 @@ cudaError_t launch_forward_tiled(const tiled::FwdTiled& a, int grid, cudaStream_
     tiled::FwdTiled copy = a;
     void* args[] = {&copy};
     const bool tma = a.c.tma != 0;
-    const void* fn = tma ? (const void*)tiled::forward_tiled<true> : (const void*)tiled::forward_tiled<false>;
+    // the Jacobi-K sweeps are their own instantiations, so the PCG kernels carry none of their code
+    const bool jac = a.c.jacobi_k > 0;
+    const void* fn = tma ? (jac ? (const void*)tiled::forward_tiled<true, true> : (const void*)tiled::forward_tiled<true, false>)
+                         : (jac ? (const void*)tiled::forward_tiled<false, true> : (const void*)tiled::forward_tiled<false, false>);
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(tiled::NT), args, tma ? tiled::DYN_SMEM : 0, s);
 }
 
@@ -2257,7 +2260,9 @@ cudaError_t launch_adjoint_tiled(const tiled::AdjTiled& a, int grid, cudaStream_
     tiled::AdjTiled copy = a;
     void* args[] = {&copy};
     const bool tma = a.c.tma != 0;
-    const void* fn = tma ? (const void*)tiled::adjoint_tiled<true> : (const void*)tiled::adjoint_tiled<false>;
+    const bool jac = a.c.jacobi_k > 0;
+    const void* fn = tma ? (jac ? (const void*)tiled::adjoint_tiled<true, true> : (const void*)tiled::adjoint_tiled<true, false>)
+                         : (jac ? (const void*)tiled::adjoint_tiled<false, true> : (const void*)tiled::adjoint_tiled<false, false>);
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(tiled::NT), args, tma ? tiled::DYN_SMEM : 0, s);
 }
 
@@ -2299,17 +2304,22 @@ cudaError_t launch_cast_split_pairs(const float* hi, const float* lo, float* out
 int tiled_grid_blocks(int device) {
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return 0;
-    const void* tma_fns[3] = {(const void*)tiled::forward_tiled<true>, (const void*)tiled::adjoint_tiled<true>,
-                              (const void*)tiled::batch_tiled};
-    const void* all_fns[5] = {tma_fns[0], tma_fns[1], tma_fns[2], (const void*)tiled::forward_tiled<false>,
-                              (const void*)tiled::adjoint_tiled<false>};
+    const void* tma_fns[5] = {(const void*)tiled::forward_tiled<true, false>,
+                              (const void*)tiled::adjoint_tiled<true, false>,
+                              (const void*)tiled::forward_tiled<true, true>,
+                              (const void*)tiled::adjoint_tiled<true, true>, (const void*)tiled::batch_tiled};
+    const void* all_fns[9] = {tma_fns[0], tma_fns[1], tma_fns[2], tma_fns[3], tma_fns[4],
+                              (const void*)tiled::forward_tiled<false, false>,
+                              (const void*)tiled::adjoint_tiled<false, false>,
+                              (const void*)tiled::forward_tiled<false, true>,
+                              (const void*)tiled::adjoint_tiled<false, true>};
     for (const void* f : tma_fns)
         if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, tiled::DYN_SMEM) != cudaSuccess)
             return 0;
     int per = 2;
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < 9; ++i) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, all_fns[i], tiled::NT, i < 3 ? tiled::DYN_SMEM : 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, all_fns[i], tiled::NT, i < 5 ? tiled::DYN_SMEM : 0) !=
             cudaSuccess)
             return 0;
         per = std::min(per, b);
