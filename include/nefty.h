@@ -170,12 +170,17 @@ nefty_status nefty_adjoint_grad(nefty_handle *h, const nefty_problem *p, const v
  * features d*2F + 2b, d*2F + 2b + 1 = band_weights[b] * (sin(w_b x_d), cos(w_b x_d)) (band
  * weights: the frequency-annealing weights of Eq. fa_schedule, NULL = 1).  Then `depth` hidden
  * ReLU layers of `width` units and a linear output f; alpha = alpha_min + (alpha_max - alpha_min)
- * * sigmoid(f) (Eq. bracket).  Dense layers run in BF16 on the tensor cores with FP32
- * accumulation; features, head, biases and gradients are FP32.
- * Parameter vector (FP32, packed): W_0 [width x 6 n_freq], b_0 [width], then W_l [width x width],
- * b_l [width] for l = 1 .. depth-1, then w_out [width], b_out [1]; weights row-major [out][in].
- * Constraints: n_freq a multiple of 32, width a multiple of 128, 1 <= depth <= 15,
- * 0 < freq_lo <= freq_hi, 0 < alpha_min < alpha_max. */
+ * * sigmoid(f) (Eq. bracket).  With skip_layer = s > 0 the encoding is re-injected at hidden
+ * layer s (App. D.1): its input is [h_s, features] (width + 6 n_freq values).  Dense layers run
+ * in BF16 on the tensor cores with FP32 accumulation; features, head, biases and gradients are
+ * FP32.
+ * Parameter vector (FP32, packed): W_0 [width x 6 n_freq], b_0 [width], then W_l [width x in_l],
+ * b_l [width] for l = 1 .. depth-1 (in_l = width + 6 n_freq for l = skip_layer, else width),
+ * then w_out [width], b_out [1]; weights row-major [out][in].
+ * Constraints: 1 <= n_freq <= 1024, width a multiple of 128, 1 <= depth <= 15,
+ * skip_layer 0 or in 1 .. depth-1, 0 < freq_lo <= freq_hi, 0 < alpha_min < alpha_max.
+ * The paper's field (App. D.4): n_freq 12 with freq_lo = pi, freq_hi = 2^11 pi (the bands
+ * 2^k pi), width 512, depth 10, skip_layer 4. */
 typedef struct {
     int32_t nx, ny, nz;     /* grid; the field is evaluated at every cell centre */
     int32_t n_freq;         /* bands per axis */
@@ -183,6 +188,8 @@ typedef struct {
     int32_t depth;          /* hidden layers */
     double freq_lo, freq_hi;
     double alpha_min, alpha_max;
+    int32_t skip_layer;     /* 0 = none; s = 1 .. depth-1: the encoding joins the input of layer s */
+    int32_t reserved;       /* 0 */
 } nefty_field_desc;
 
 /* Number of FP32 parameters of the packed vector for `d` (0 if d is invalid). */

@@ -56,12 +56,13 @@ def encode(X, F, freq_lo, freq_hi, band_weights=None):
     return torch.cat(cols, dim=1)
 
 
-def unpack(theta, F, W, depth):
+def unpack(theta, F, W, depth, skip=0):
+    """Split the packed parameters; layer `skip` (> 0) takes [h, gamma(x)] as input."""
     theta = torch.as_tensor(theta, dtype=torch.float64)
     D = 6 * F
     out, p = [], 0
     for l in range(depth):
-        n_in = D if l == 0 else W
+        n_in = D if l == 0 else (W + D if l == skip else W)
         Wl = theta[p:p + W * n_in].reshape(W, n_in); p += W * n_in
         bl = theta[p:p + W]; p += W
         out.append((Wl, bl))
@@ -71,23 +72,28 @@ def unpack(theta, F, W, depth):
     return out, w_out, b_out
 
 
-def param_count(F, W, depth):
-    return W * 6 * F + W + (depth - 1) * (W * W + W) + W + 1
+def param_count(F, W, depth, skip=0):
+    return W * 6 * F + W + (depth - 1) * (W * W + W) + (W * 6 * F if skip else 0) + W + 1
 
 
 def _bf16(t):
     return t.to(torch.bfloat16).to(torch.float64)
 
 
-def field(theta, nx, ny, nz, F, W, depth, freq_lo, freq_hi, alpha_min, alpha_max, band_weights=None, bf16=False):
-    """alpha at every cell centre, [nz, ny, nx] (differentiable in theta)."""
-    layers, w_out, b_out = unpack(theta, F, W, depth)
-    h = encode(cell_centres(nx, ny, nz), F, freq_lo, freq_hi, band_weights)
+def field(theta, nx, ny, nz, F, W, depth, freq_lo, freq_hi, alpha_min, alpha_max, band_weights=None, bf16=False,
+          skip=0):
+    """alpha at every cell centre, [nz, ny, nx] (differentiable in theta).
+    skip > 0: the encoding is concatenated to the input of hidden layer `skip`
+    (App. D.1, the re-injection at the middle layer)."""
+    layers, w_out, b_out = unpack(theta, F, W, depth, skip)
+    gamma = encode(cell_centres(nx, ny, nz), F, freq_lo, freq_hi, band_weights)
     if bf16:
-        h = _bf16(h)
-    for Wl, bl in layers:
+        gamma = _bf16(gamma)
+    h = gamma
+    for l, (Wl, bl) in enumerate(layers):
         Wl = _bf16(Wl) if bf16 else Wl
-        h = torch.relu(h @ Wl.T + bl)
+        x = torch.cat([h, gamma], dim=1) if (skip and l == skip) else h
+        h = torch.relu(x @ Wl.T + bl)
         if bf16:
             h = _bf16(h)
     f = h @ w_out + b_out

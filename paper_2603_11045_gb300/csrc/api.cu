@@ -1160,9 +1160,14 @@ bool field_dims(const nefty_field_desc* d, FieldDims* out, std::string* why) {
     if (d->nx < 1 || d->ny < 1 || d->nz < 1) { *why = "field grid must be >= 1 in each direction"; return false; }
     const double cells = (double)d->nx * d->ny * d->nz;
     if (cells >= 2147483647.0 - 128) { *why = "field grid too large"; return false; }
-    if (d->n_freq < 32 || d->n_freq % 32 != 0) { *why = "n_freq must be a positive multiple of 32"; return false; }
+    if (d->n_freq < 1 || d->n_freq > 1024) { *why = "n_freq must be in 1..1024"; return false; }
     if (d->width < 128 || d->width % 128 != 0) { *why = "width must be a positive multiple of 128"; return false; }
     if (d->depth < 1 || d->depth > 15) { *why = "depth must be in 1..15"; return false; }
+    if (d->skip_layer < 0 || (d->skip_layer > 0 && d->skip_layer >= d->depth)) {
+        *why = "skip_layer must be 0 (none) or a hidden layer 1..depth-1";
+        return false;
+    }
+    if (d->reserved != 0) { *why = "reserved must be 0"; return false; }
     if (!(d->freq_lo > 0) || !(d->freq_hi >= d->freq_lo) || !std::isfinite(d->freq_hi)) {
         *why = "need 0 < freq_lo <= freq_hi";
         return false;
@@ -1176,13 +1181,15 @@ bool field_dims(const nefty_field_desc* d, FieldDims* out, std::string* why) {
         out->M = (unsigned)cells;
         out->Mp = (out->M + 127u) / 128u * 128u;
         out->F = d->n_freq; out->W = d->width; out->depth = d->depth;
+        out->skip = d->skip_layer;
+        out->Dp = (6 * d->n_freq + 63) / 64 * 64;
         out->freq_lo = d->freq_lo; out->freq_hi = d->freq_hi;
         out->alpha_min = d->alpha_min; out->alpha_max = d->alpha_max;
         // split-K of the weight-gradient GEMMs: one CTA per SM (per layer, see
         // field_backward); `splits` bounds it for the partials buffer
         out->sms = 152;
         const int kblocks = (int)(out->Mp / 64);
-        const int min_tiles = ((out->W + 127) / 128) * ((std::min(6 * out->F, out->W) + 127) / 128);
+        const int min_tiles = ((out->W + 127) / 128) * ((std::min(out->Dp, out->W) + 127) / 128);
         out->splits = std::min(std::max(1, out->sms / std::max(1, min_tiles)), kblocks);
         out->colsum_blocks = (int)std::min<unsigned>(1024u, std::max(1u, out->Mp / 256u));
     }
@@ -1197,7 +1204,7 @@ uint64_t nefty_field_param_count(const nefty_field_desc* d) {
     FieldDims fd;
     std::string why;
     if (!field_dims(d, &fd, &why)) return 0;
-    return field_param_count(fd.F, fd.W, fd.depth);
+    return field_param_count(fd.F, fd.W, fd.depth, fd.skip);
 }
 
 static nefty_status field_call(nefty_handle* h, const nefty_field_desc* d, const float* theta,
@@ -1214,13 +1221,13 @@ static nefty_status field_call(nefty_handle* h, const nefty_field_desc* d, const
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) == cudaSuccess && sms > 0 &&
             sms != fd.sms) {
             const int kblocks = (int)(fd.Mp / 64);
-            const int min_tiles = ((fd.W + 127) / 128) * ((std::min(6 * fd.F, fd.W) + 127) / 128);
+            const int min_tiles = ((fd.W + 127) / 128) * ((std::min(fd.Dp, fd.W) + 127) / 128);
             fd.sms = sms;
             fd.splits = std::min(std::max(1, sms / std::max(1, min_tiles)), kblocks);
         }
     }
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t P = field_param_count(fd.F, fd.W, fd.depth);
+    const size_t P = field_param_count(fd.F, fd.W, fd.depth, fd.skip);
     Input th, bw, ga;
     th.plan(theta, P * 4);
     bw.plan(band_weights, (size_t)fd.F * 4);

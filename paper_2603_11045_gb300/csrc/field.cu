@@ -12,11 +12,18 @@
 //
 // Network: h_0 = gamma(x) (6F), h_{l+1} = relu(W_l h_l + b_l) for l < depth
 // (width W), f = w_out . h_depth + b_out, alpha = alpha_min +
-// (alpha_max - alpha_min) * sigmoid(f) (Eq. bracket).
+// (alpha_max - alpha_min) * sigmoid(f) (Eq. bracket).  With a skip layer s
+// (App. D.1: the encoding re-injected at the middle layer), layer s reads
+// [h_s | gamma(x)] (W + 6F inputs).
 //
 // Parameter vector theta (FP32, packed): W_0 [W x 6F], b_0 [W], then for
-// l = 1 .. depth-1: W_l [W x W], b_l [W]; then w_out [W], b_out [1].  Weights are
-// row-major [out][in].
+// l = 1 .. depth-1: W_l [W x in_l], b_l [W] (in_l = W + 6F for l = s, else W);
+// then w_out [W], b_out [1].  Weights are row-major [out][in].
+//
+// Storage: the feature block is zero-padded to Dp = 6F rounded up to 64 columns
+// (the tensor-core K step), so every GEMM has K a multiple of 64 for any F; the
+// BF16 weight copies carry the matching zero columns, and the layer-s input
+// buffer holds h_s and the padded features side by side.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -43,20 +50,21 @@ __global__ void axis_table_kernel(float* tab, int n, int F, float lo, float rati
     }
 }
 
-// h0[c][d*2F + j] = tab_d[index_d(c)][j], as BF16, rows padded to Mp (zeros).
-// With F % 4 == 0 each thread writes 8 features (16 bytes) of one cell, which
-// never straddle two axes; otherwise one feature at a time.
-__global__ void features_kernel(__nv_bfloat16* h0, unsigned M, unsigned Mp, int nx, int ny, int F,
+// h0[c][d*2F + j] = tab_d[index_d(c)][j], as BF16, rows padded to Mp and
+// columns to Dp (zeros).  With F % 4 == 0 each thread writes 8 features (16
+// bytes) of one cell, which never straddle two axes; otherwise one feature at
+// a time.
+__global__ void features_kernel(__nv_bfloat16* h0, unsigned M, unsigned Mp, int nx, int ny, int F, int Dp,
                                 const float* tx, const float* ty, const float* tz) {
     const int D = 6 * F, F2 = 2 * F;
     if ((F & 3) == 0) {
-        const unsigned per = (unsigned)D / 8;   // 16-byte chunks per cell
+        const unsigned per = (unsigned)Dp / 8;   // 16-byte chunks per cell
         for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)Mp * per;
              e += (size_t)gridDim.x * blockDim.x) {
             const unsigned c = (unsigned)(e / per);
             const int f = (int)(e - (size_t)c * per) * 8;
             uint4 out = make_uint4(0u, 0u, 0u, 0u);
-            if (c < M) {
+            if (c < M && f < D) {
                 const unsigned cy = c / (unsigned)nx, i = c - cy * (unsigned)nx;
                 const unsigned k = cy / (unsigned)ny, j = cy - k * (unsigned)ny;
                 const int d = f / F2, r = f - d * F2;
@@ -72,12 +80,12 @@ __global__ void features_kernel(__nv_bfloat16* h0, unsigned M, unsigned Mp, int 
         }
         return;
     }
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)Mp * D;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)Mp * Dp;
          e += (size_t)gridDim.x * blockDim.x) {
-        const unsigned c = (unsigned)(e / D);
-        const int f = (int)(e % D);
+        const unsigned c = (unsigned)(e / Dp);
+        const int f = (int)(e % Dp);
         float v = 0.f;
-        if (c < M) {
+        if (c < M && f < D) {
             const unsigned i = c % nx, j = (c / nx) % ny, k = c / ((unsigned)nx * ny);
             const int d = f / F2, r = f % F2;
             v = d == 0 ? tx[(size_t)i * F2 + r] : (d == 1 ? ty[(size_t)j * F2 + r] : tz[(size_t)k * F2 + r]);
@@ -86,17 +94,34 @@ __global__ void features_kernel(__nv_bfloat16* h0, unsigned M, unsigned Mp, int 
     }
 }
 
-__global__ void to_bf16_kernel(const float* src, __nv_bfloat16* dst, size_t n) {
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-        dst[e] = __float2bfloat16_rn(src[e]);
+// dst [R x Cp] = bf16(src [R x C]) with zero columns C .. Cp-1.
+__global__ void to_bf16_kernel(const float* src, __nv_bfloat16* dst, int R, int C, int Cp) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)R * Cp;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / Cp), c = (int)(e % Cp);
+        dst[e] = __float2bfloat16_rn(c < C ? src[(size_t)r * C + c] : 0.f);
+    }
 }
 
-// dst[c][r] = bf16(src[r][c]) : transpose of a [R x C] FP32 matrix to BF16.
-__global__ void transpose_f32_bf16_kernel(const float* src, __nv_bfloat16* dst, int R, int C) {
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)R * C;
+// dst [Cp x R] = bf16(src [R x C])^T with zero rows C .. Cp-1.
+__global__ void transpose_f32_bf16_kernel(const float* src, __nv_bfloat16* dst, int R, int C, int Cp) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)R * Cp;
          e += (size_t)gridDim.x * blockDim.x) {
         const int c = (int)(e / R), r = (int)(e % R);
-        dst[e] = __float2bfloat16_rn(src[(size_t)r * C + c]);
+        dst[e] = __float2bfloat16_rn(c < C ? src[(size_t)r * C + c] : 0.f);
+    }
+}
+
+// dst[m][col0 + j] = src[m][j] for j < n, rows of lds / ldd elements (BF16);
+// n, col0, lds, ldd are multiples of 8, so each thread moves 16 bytes.
+__global__ void copy_cols_kernel(const __nv_bfloat16* src, int lds, __nv_bfloat16* dst, int ldd, int col0, int n,
+                                 unsigned rows) {
+    const unsigned per = (unsigned)n / 8;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)rows * per;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const unsigned m = (unsigned)(e / per), j = (unsigned)(e % per) * 8;
+        *reinterpret_cast<uint4*>(dst + (size_t)m * ldd + col0 + j) =
+            *reinterpret_cast<const uint4*>(src + (size_t)m * lds + j);
     }
 }
 
@@ -187,11 +212,15 @@ __global__ void colsum_final_kernel(const double* part, int nblk, int C, float* 
     }
 }
 
-// sum of split-K partials [splits][R][C] -> out[R][C] (fixed order)
-__global__ void split_reduce_kernel(const float* part, int splits, size_t n, float* out) {
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+// sum of split-K partials [splits][R][Cp] -> out[R][C], C <= Cp (fixed order;
+// the padded columns are dropped)
+__global__ void split_reduce_kernel(const float* part, int splits, int R, int Cp, int C, float* out) {
+    const size_t n = (size_t)R * Cp;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)R * C;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = e / C, c = e % C, i = r * Cp + c;
         float s = 0.f;
-        for (int z = 0; z < splits; ++z) s += part[(size_t)z * n + e];
+        for (int z = 0; z < splits; ++z) s += part[(size_t)z * n + i];
         out[e] = s;
     }
 }
@@ -204,29 +233,43 @@ inline unsigned blocks_for(size_t n, unsigned t = kT) {
 
 }  // namespace
 
-size_t field_param_count(int F, int W, int depth) {
-    return (size_t)W * 6 * F + W + (size_t)(depth - 1) * ((size_t)W * W + W) + W + 1;
+// Inputs of layer l: in the packed parameters (in_packed) and as stored
+// (in_store, the feature block padded to Dp); h_ld(l) is the leading dimension
+// of h[l], the input of layer l (l = depth: the head's input).
+static inline int in_packed(const FieldDims& d, int l) {
+    return l == 0 ? 6 * d.F : (l == d.skip ? d.W + 6 * d.F : d.W);
+}
+static inline int in_store(const FieldDims& d, int l) { return l == 0 ? d.Dp : (l == d.skip ? d.W + d.Dp : d.W); }
+static inline int h_ld(const FieldDims& d, int l) { return l < d.depth ? in_store(d, l) : d.W; }
+
+size_t field_param_count(int F, int W, int depth, int skip) {
+    size_t n = (size_t)W * 6 * F + W;
+    for (int l = 1; l < depth; ++l) n += (size_t)W * (l == skip ? W + 6 * F : W) + W;
+    return n + W + 1;
 }
 
 // Workspace of one field call (bytes) for M points.
 size_t field_workspace_bytes(const FieldDims& d, bool backward) {
-    const size_t Mp = d.Mp, W = d.W, D = (size_t)6 * d.F;
-    size_t b = 0;
+    const size_t Mp = d.Mp, W = d.W;
+    size_t b = 0, wsum = 0, maxin = 0;
+    for (int l = 0; l < d.depth; ++l) {
+        wsum += W * (size_t)in_store(d, l);
+        maxin = std::max(maxin, (size_t)in_store(d, l));
+    }
     auto add = [&](size_t x) { b += (x + 255) & ~(size_t)255; };
     add((size_t)(d.nx + d.ny + d.nz) * 2 * d.F * 4);   // axis tables
-    add(Mp * D * 2);                                    // h0
-    for (int l = 0; l < d.depth; ++l) add(Mp * W * 2);  // h1 .. h_depth
-    add(((size_t)W * D + (size_t)(d.depth - 1) * W * W) * 2);   // BF16 weights
+    for (int l = 0; l <= d.depth; ++l) add(Mp * (size_t)h_ld(d, l) * 2);   // h_0 .. h_depth
+    add(wsum * 2);                                      // BF16 weights
     add(sizeof(int));
     if (backward) {
-        add(((size_t)W * D + (size_t)(d.depth - 1) * W * W) * 2);   // transposed weights (unused for l = 0)
-        add(Mp * W * 2 * 2);     // delta ping-pong
-        add(Mp * 4);             // g_f
-        for (int l = 1; l < d.depth; ++l) add(Mp * W * 2);   // h_l^T
-        add(Mp * W * 2);         // delta^T
-        add(Mp * D * 2);         // h_0^T
-        add((size_t)d.splits * W * (W > D ? W : D) * 4);   // split-K partials
-        add((size_t)d.colsum_blocks * (W > D ? W : D) * 8);   // column-sum partials
+        add(wsum * 2);                                  // transposed weights
+        add(Mp * W * 2 * 2);                            // delta ping-pong
+        add(Mp * 4);                                    // g_f
+        for (int l = 1; l < d.depth; ++l) add(Mp * (size_t)in_store(d, l) * 2);   // h_l^T
+        add(Mp * W * 2);                                // delta^T
+        add(Mp * (size_t)d.Dp * 2);                     // h_0^T
+        add((size_t)d.splits * W * maxin * 4);          // split-K partials
+        add((size_t)d.colsum_blocks * W * 8);           // column-sum partials
     }
     return b;
 }
@@ -239,15 +282,20 @@ struct FieldWs {
     __nv_bfloat16* wt;      // BF16 transposed weights
     __nv_bfloat16* dl[2];
     float* gf;
-    __nv_bfloat16* hT[16];  // h_l^T [W x Mp], l = 1 .. depth-1 (written by the forward epilogues)
-    __nv_bfloat16 *tA, *tB; // delta^T [W x Mp], h_0^T [D x Mp]
+    __nv_bfloat16* hT[16];  // h_l^T [in_store(l) x Mp], l = 1 .. depth-1
+    __nv_bfloat16 *tA, *tB; // delta^T [W x Mp], h_0^T [Dp x Mp]
     float* split;
     double* colpart;
     int* err;
 };
 
 static FieldWs carve(char* base, const FieldDims& d, bool backward) {
-    const size_t Mp = d.Mp, W = d.W, D = (size_t)6 * d.F, WD = W > D ? W : D;
+    const size_t Mp = d.Mp, W = d.W;
+    size_t wsum = 0, maxin = 0;
+    for (int l = 0; l < d.depth; ++l) {
+        wsum += W * (size_t)in_store(d, l);
+        maxin = std::max(maxin, (size_t)in_store(d, l));
+    }
     FieldWs w{};
     size_t off = 0;
     auto take = [&](size_t x) { char* p = base + off; off += (x + 255) & ~(size_t)255; return p; };
@@ -255,21 +303,20 @@ static FieldWs carve(char* base, const FieldDims& d, bool backward) {
     w.tx = (float*)tab;
     w.ty = w.tx + (size_t)d.nx * 2 * d.F;
     w.tz = w.ty + (size_t)d.ny * 2 * d.F;
-    w.h[0] = (__nv_bfloat16*)take(Mp * D * 2);
-    for (int l = 1; l <= d.depth; ++l) w.h[l] = (__nv_bfloat16*)take(Mp * W * 2);
-    w.wb = (__nv_bfloat16*)take((W * D + (size_t)(d.depth - 1) * W * W) * 2);
+    for (int l = 0; l <= d.depth; ++l) w.h[l] = (__nv_bfloat16*)take(Mp * (size_t)h_ld(d, l) * 2);
+    w.wb = (__nv_bfloat16*)take(wsum * 2);
     w.err = (int*)take(sizeof(int));
     if (backward) {
-        w.wt = (__nv_bfloat16*)take((W * D + (size_t)(d.depth - 1) * W * W) * 2);
+        w.wt = (__nv_bfloat16*)take(wsum * 2);
         char* dd = take(Mp * W * 2 * 2);
         w.dl[0] = (__nv_bfloat16*)dd;
         w.dl[1] = w.dl[0] + Mp * W;
         w.gf = (float*)take(Mp * 4);
-        for (int l = 1; l < d.depth; ++l) w.hT[l] = (__nv_bfloat16*)take(Mp * W * 2);
+        for (int l = 1; l < d.depth; ++l) w.hT[l] = (__nv_bfloat16*)take(Mp * (size_t)in_store(d, l) * 2);
         w.tA = (__nv_bfloat16*)take(Mp * W * 2);
-        w.tB = (__nv_bfloat16*)take(Mp * D * 2);
-        w.split = (float*)take((size_t)d.splits * W * WD * 4);
-        w.colpart = (double*)take((size_t)d.colsum_blocks * WD * 8);
+        w.tB = (__nv_bfloat16*)take(Mp * (size_t)d.Dp * 2);
+        w.split = (float*)take((size_t)d.splits * W * maxin * 4);
+        w.colpart = (double*)take((size_t)d.colsum_blocks * W * 8);
     }
     return w;
 }
@@ -277,34 +324,38 @@ static FieldWs carve(char* base, const FieldDims& d, bool backward) {
 // with_t: the epilogues also write h_l^T (l = 1 .. depth-1) for the backward.
 static cudaError_t forward_layers(const FieldDims& d, const float* theta, const float* band_w, FieldWs& w,
                                   cudaStream_t s, bool with_t) {
-    const int F = d.F, W = d.W, D = 6 * F;
+    const int F = d.F, W = d.W;
     const float lo = (float)d.freq_lo, ratio_log = (float)log(d.freq_hi / d.freq_lo);
     axis_table_kernel<<<blocks_for((size_t)d.nx * F), kT, 0, s>>>(w.tx, d.nx, F, lo, ratio_log, band_w);
     axis_table_kernel<<<blocks_for((size_t)d.ny * F), kT, 0, s>>>(w.ty, d.ny, F, lo, ratio_log, band_w);
     axis_table_kernel<<<blocks_for((size_t)d.nz * F), kT, 0, s>>>(w.tz, d.nz, F, lo, ratio_log, band_w);
-    features_kernel<<<blocks_for((size_t)d.Mp * D), kT, 0, s>>>(w.h[0], d.M, d.Mp, d.nx, d.ny, F, w.tx, w.ty, w.tz);
-    // BF16 copies of the weights
+    features_kernel<<<blocks_for((size_t)d.Mp * d.Dp), kT, 0, s>>>(w.h[0], d.M, d.Mp, d.nx, d.ny, F, d.Dp, w.tx, w.ty,
+                                                                   w.tz);
+    if (d.skip > 0)   // the encoding beside h_s in the skip layer's input
+        copy_cols_kernel<<<blocks_for((size_t)d.Mp * d.Dp / 8), kT, 0, s>>>(w.h[0], d.Dp, w.h[d.skip], W + d.Dp, W,
+                                                                           d.Dp, d.Mp);
+    // BF16 copies of the weights, zero-padded to the stored inputs
     const float* p = theta;
     size_t woff = 0;
     for (int l = 0; l < d.depth; ++l) {
-        const int in = l == 0 ? D : W;
-        to_bf16_kernel<<<blocks_for((size_t)W * in), kT, 0, s>>>(p, w.wb + woff, (size_t)W * in);
+        const int in = in_packed(d, l), ins = in_store(d, l);
+        to_bf16_kernel<<<blocks_for((size_t)W * ins), kT, 0, s>>>(p, w.wb + woff, W, in, ins);
         p += (size_t)W * in + W;
-        woff += (size_t)W * in;
+        woff += (size_t)W * ins;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     p = theta;
     woff = 0;
     for (int l = 0; l < d.depth; ++l) {
-        const int in = l == 0 ? D : W;
+        const int in = in_packed(d, l), ins = in_store(d, l);
         const float* bias = p + (size_t)W * in;
         const bool t = with_t && l + 1 < d.depth;
-        e = umma_gemm(w.h[l], in, w.wb + woff, in, (int)d.Mp, W, in, 0 /*bias+relu*/, bias, nullptr, w.h[l + 1],
-                      nullptr, W, 1, w.err, s, t ? w.hT[l + 1] : nullptr, t ? (int)d.Mp : 0);
+        e = umma_gemm(w.h[l], ins, w.wb + woff, ins, (int)d.Mp, W, ins, 0 /*bias+relu*/, bias, nullptr, w.h[l + 1],
+                      nullptr, h_ld(d, l + 1), 1, w.err, s, t ? w.hT[l + 1] : nullptr, t ? (int)d.Mp : 0);
         if (e != cudaSuccess) return e;
         p += (size_t)W * in + W;
-        woff += (size_t)W * in;
+        woff += (size_t)W * ins;
     }
     return cudaSuccess;
 }
@@ -315,7 +366,7 @@ cudaError_t field_eval(const FieldDims& d, const float* theta, const float* band
     cudaError_t e = cudaMemsetAsync(w.err, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     if ((e = forward_layers(d, theta, band_w, w, s, false)) != cudaSuccess) return e;
-    const float* w_out = theta + field_param_count(d.F, d.W, d.depth) - d.W - 1;
+    const float* w_out = theta + field_param_count(d.F, d.W, d.depth, d.skip) - d.W - 1;
     head_kernel<<<blocks_for((size_t)d.M * 32), kT, 0, s>>>(w.h[d.depth], d.W, w_out, w_out + d.W, d.M,
                                                             (float)d.alpha_min, (float)d.alpha_max, alpha);
     return cudaGetLastError();
@@ -324,20 +375,19 @@ cudaError_t field_eval(const FieldDims& d, const float* theta, const float* band
 cudaError_t field_backward(const FieldDims& d, const float* theta, const float* band_w, const float* g_alpha,
                            float* g_theta, char* ws, cudaStream_t s) {
     FieldWs w = carve(ws, d, true);
-    const int F = d.F, W = d.W, D = 6 * F;
+    const int W = d.W;
     cudaError_t e = cudaMemsetAsync(w.err, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     if ((e = forward_layers(d, theta, band_w, w, s, true)) != cudaSuccess) return e;
-    // parameter offsets
+    // parameter offsets (packed) and weight-copy offsets (stored)
     size_t poff[16], woff[16];
     {
         size_t p = 0, q = 0;
         for (int l = 0; l < d.depth; ++l) {
-            const int in = l == 0 ? D : W;
             poff[l] = p;
             woff[l] = q;
-            p += (size_t)W * in + W;
-            q += (size_t)W * in;
+            p += (size_t)W * in_packed(d, l) + W;
+            q += (size_t)W * in_store(d, l);
         }
         poff[d.depth] = p;
     }
@@ -354,45 +404,52 @@ cudaError_t field_backward(const FieldDims& d, const float* theta, const float* 
     colsum_partial_kernel<float><<<d.colsum_blocks, kT, 0, s>>>(w.gf, nullptr, d.Mp, 1, rpb, w.colpart);
     colsum_final_kernel<<<1, 32, 0, s>>>(w.colpart, d.colsum_blocks, 1, g_wout + W);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // transposed BF16 weights W_l^T [in x W] for the input-gradient GEMMs
+    // transposed BF16 weights W_l^T [in_store x W] for the input-gradient GEMMs
     {
         const float* p = theta;
         for (int l = 0; l < d.depth; ++l) {
-            const int in = l == 0 ? D : W;
-            transpose_f32_bf16_kernel<<<blocks_for((size_t)W * in), kT, 0, s>>>(p, w.wt + woff[l], W, in);
+            const int in = in_packed(d, l), ins = in_store(d, l);
+            transpose_f32_bf16_kernel<<<blocks_for((size_t)W * ins), kT, 0, s>>>(p, w.wt + woff[l], W, in, ins);
             p += (size_t)W * in + W;
         }
     }
+    // h_0^T, also the encoding rows of the skip layer's h^T
+    const dim3 tb(32, 8);
+    transpose_bf16_kernel<<<dim3((d.Mp + 31) / 32, (d.Dp + 31) / 32), tb, 0, s>>>(w.h[0], w.tB, d.Mp, d.Dp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (d.skip > 0 && d.skip < d.depth) {
+        e = cudaMemcpyAsync(w.hT[d.skip] + (size_t)W * d.Mp, w.tB, (size_t)d.Dp * d.Mp * 2, cudaMemcpyDeviceToDevice,
+                            s);
+        if (e != cudaSuccess) return e;
+    }
     // layers, top to bottom: delta_l = dJ/dz_{l+1} [Mp x W] lives in dl[cur]
     int cur = 0;
-    const dim3 tb(32, 8);
     for (int l = d.depth - 1; l >= 0; --l) {
-        const int in = l == 0 ? D : W;
+        const int in = in_packed(d, l), ins = in_store(d, l);
         // db_l = column sums of delta
         colsum_partial_kernel<__nv_bfloat16><<<d.colsum_blocks, kT, 0, s>>>(w.dl[cur], nullptr, d.Mp, W, rpb,
                                                                           w.colpart);
         colsum_final_kernel<<<blocks_for(W), kT, 0, s>>>(w.colpart, d.colsum_blocks, W,
                                                          g_theta + poff[l] + (size_t)W * in);
-        // dW_l = delta^T h_l: K-major operands are the transposes [W x Mp] and [in x Mp].
+        // dW_l = delta^T h_l: K-major operands are the transposes [W x Mp] and [ins x Mp].
         // delta^T comes from the previous masked product's epilogue (top layer:
-        // transposed here); h_l^T from the forward epilogues (l = 0: transposed here).
+        // transposed here); h_l^T from the forward epilogues (l = 0: h_0^T).
         if (l == d.depth - 1)
             transpose_bf16_kernel<<<dim3((d.Mp + 31) / 32, (W + 31) / 32), tb, 0, s>>>(w.dl[cur], w.tA, d.Mp, W);
-        if (l == 0)
-            transpose_bf16_kernel<<<dim3((d.Mp + 31) / 32, (in + 31) / 32), tb, 0, s>>>(w.h[0], w.tB, d.Mp, in);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // split-K: one CTA per SM over the layer's output tiles
-        const int tiles = ((W + 127) / 128) * ((in + 127) / 128);
+        const int tiles = ((W + 127) / 128) * ((ins + 127) / 128);
         const int splits = std::min(d.splits, std::max(1, d.sms / tiles));
-        e = umma_gemm(w.tA, (int)d.Mp, l == 0 ? w.tB : w.hT[l], (int)d.Mp, W, in, (int)d.Mp, 2 /*f32 partials*/,
-                      nullptr, nullptr, nullptr, w.split, in, splits, w.err, s);
+        e = umma_gemm(w.tA, (int)d.Mp, l == 0 ? w.tB : w.hT[l], (int)d.Mp, W, ins, (int)d.Mp, 2 /*f32 partials*/,
+                      nullptr, nullptr, nullptr, w.split, ins, splits, w.err, s);
         if (e != cudaSuccess) return e;
-        split_reduce_kernel<<<blocks_for((size_t)W * in), kT, 0, s>>>(w.split, splits, (size_t)W * in,
+        split_reduce_kernel<<<blocks_for((size_t)W * in), kT, 0, s>>>(w.split, splits, W, ins, in,
                                                                       g_theta + poff[l]);
-        // delta_{l-1} = (delta_l W_l) masked by h_l > 0
+        // delta_{l-1} = (delta_l W_l[:, :W]) masked by h_l > 0 (the h part of the
+        // skip layer's input; its encoding part needs no gradient)
         if (l > 0) {
-            e = umma_gemm(w.dl[cur], W, w.wt + woff[l], W, (int)d.Mp, in, W, 1 /*mask*/, nullptr, w.h[l],
-                          w.dl[cur ^ 1], nullptr, in, 1, w.err, s, w.tA, (int)d.Mp);
+            e = umma_gemm(w.dl[cur], W, w.wt + woff[l], W, (int)d.Mp, W, W, 1 /*mask*/, nullptr, w.h[l],
+                          w.dl[cur ^ 1], nullptr, W, 1, w.err, s, w.tA, (int)d.Mp, h_ld(d, l));
             if (e != cudaSuccess) return e;
             cur ^= 1;
         }

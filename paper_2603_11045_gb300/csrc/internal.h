@@ -273,12 +273,14 @@ struct FieldDims {
     int nx, ny, nz;
     unsigned M, Mp;          // points (cells) and rows padded to a multiple of 128
     int F, W, depth;         // bands per axis, hidden width, hidden layers
+    int skip;                // hidden layer whose input is [h | gamma(x)] (0 = none)
+    int Dp;                  // 6F rounded up to a multiple of 64 (zero-padded feature columns)
     double freq_lo, freq_hi, alpha_min, alpha_max;
     int sms;                 // SMs of the device (split-K sizing)
     int splits;              // largest split-K factor of the weight-gradient GEMMs
     int colsum_blocks;       // row blocks of the bias-gradient reductions
 };
-size_t field_param_count(int F, int W, int depth);
+size_t field_param_count(int F, int W, int depth, int skip);
 size_t field_workspace_bytes(const FieldDims& d, bool backward);
 cudaError_t field_eval(const FieldDims& d, const float* theta, const float* band_w, float* alpha, char* ws,
                        cudaStream_t s);
@@ -286,11 +288,12 @@ cudaError_t field_backward(const FieldDims& d, const float* theta, const float* 
                            float* g_theta, char* ws, cudaStream_t s);
 int field_error(const FieldDims& d, char* ws, cudaStream_t s, bool backward);
 // tcgen05 BF16 GEMM (umma_gemm.cu): D = A B^T, epi 0 bias+relu->bf16, 1 mask->bf16, 2 fp32 split partials;
-// the BF16 epilogues can also write D^T [N x ldt] (out_t).
+// the BF16 epilogues can also write D^T [N x ldt] (out_t); the mask has leading
+// dimension ldm (0 = ldo).
 cudaError_t umma_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
                       int epi, const float* bias, const __nv_bfloat16* mask, __nv_bfloat16* out_bf16,
                       float* out_f32, int ldo, int splits, int* err, cudaStream_t s,
-                      __nv_bfloat16* out_t = nullptr, int ldt = 0);
+                      __nv_bfloat16* out_t = nullptr, int ldt = 0, int ldm = 0);
 
 int tiled_grid_blocks(int device);
 // Shared memory (bytes) the tiled kernels request dynamically.

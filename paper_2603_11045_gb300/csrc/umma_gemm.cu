@@ -103,11 +103,12 @@ struct Args {
     int k_blocks_per_split;
     int epi;
     const float* bias;      // [N]
-    const __nv_bfloat16* mask;   // [M, ldo]
+    const __nv_bfloat16* mask;   // [M, ldm]
     __nv_bfloat16* out_bf16;     // [M, ldo]
     float* out_f32;              // [splits][M, ldo]
     int ldo;
-    int vec;                     // ldo and every base 16-byte aligned: 16-byte epilogue stores
+    int ldm;                     // leading dimension of mask
+    int vec;                     // ldo, ldm and every base 16-byte aligned: 16-byte epilogue stores
     __nv_bfloat16* out_t;        // BF16 epilogues: also D^T [N, ldt] (or null)
     int ldt;
     int* err;
@@ -223,7 +224,7 @@ gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
                 } else {
                     uint32_t mk[16];
                     if (a.epi == kEpiMaskBf16) {
-                        const uint4* src = reinterpret_cast<const uint4*>(a.mask + o);
+                        const uint4* src = reinterpret_cast<const uint4*>(a.mask + (size_t)row * a.ldm + cb);
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const uint4 w = src[q];
@@ -267,7 +268,9 @@ gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
                     if (a.epi == kEpiBiasReluBf16 || a.epi == kEpiMaskBf16) {
                         const __nv_bfloat16 r = a.epi == kEpiBiasReluBf16
                                                     ? __float2bfloat16_rn(fmaxf(acc + a.bias[col], 0.f))
-                                                    : __float2bfloat16_rn(__bfloat162float(a.mask[e]) > 0.f ? acc : 0.f);
+                                                    : __float2bfloat16_rn(
+                                                          __bfloat162float(a.mask[(size_t)row * a.ldm + col]) > 0.f
+                                                              ? acc : 0.f);
                         a.out_bf16[e] = r;
                         if (a.out_t) a.out_t[(size_t)col * a.ldt + row] = r;
                     } else {
@@ -325,7 +328,8 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld) {
 // (multiples of 8).  splits > 1 only with kEpiF32.
 cudaError_t umma_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
                       int epi, const float* bias, const __nv_bfloat16* mask, __nv_bfloat16* out_bf16,
-                      float* out_f32, int ldo, int splits, int* err, cudaStream_t s, __nv_bfloat16* out_t, int ldt) {
+                      float* out_f32, int ldo, int splits, int* err, cudaStream_t s, __nv_bfloat16* out_t, int ldt,
+                      int ldm) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(umma::gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -346,11 +350,13 @@ cudaError_t umma_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, i
     a.k_blocks_per_split = (kb + splits - 1) / splits;
     a.epi = epi;
     a.bias = bias; a.mask = mask; a.out_bf16 = out_bf16; a.out_f32 = out_f32; a.ldo = ldo;
+    a.ldm = ldm > 0 ? ldm : ldo;
     a.out_t = out_t;
     a.ldt = ldt;
     auto al16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
     a.vec = (epi == umma::kEpiF32 ? (ldo % 4 == 0 && al16(out_f32))
-                                  : (ldo % 8 == 0 && al16(out_bf16) && (epi != umma::kEpiMaskBf16 || al16(mask))))
+                                  : (ldo % 8 == 0 && al16(out_bf16) &&
+                                     (epi != umma::kEpiMaskBf16 || (al16(mask) && a.ldm % 8 == 0))))
                 ? 1 : 0;
     a.err = err;
     dim3 grid((M + umma::BM - 1) / umma::BM, (N + umma::BN - 1) / umma::BN, splits);

@@ -35,10 +35,17 @@ class FieldSpec:
     freq_hi: float = 128 * math.pi
     alpha_min: float = 0.01
     alpha_max: float = 2.0
+    skip_layer: int = 0
+
+    @classmethod
+    def paper(cls, nx: int, ny: int, nz: int, alpha_min: float = 0.003, alpha_max: float = 0.25) -> "FieldSpec":
+        """The paper's field (App. D.4): 12 bands 2^k pi, 10 x 512, skip at layer 4."""
+        return cls(nx, ny, nz, n_freq=12, width=512, depth=10, freq_lo=math.pi, freq_hi=2.0 ** 11 * math.pi,
+                   alpha_min=alpha_min, alpha_max=alpha_max, skip_layer=4)
 
     def to_c(self) -> N.nefty_field_desc:
         return N.nefty_field_desc(self.nx, self.ny, self.nz, self.n_freq, self.width, self.depth,
-                                  self.freq_lo, self.freq_hi, self.alpha_min, self.alpha_max)
+                                  self.freq_lo, self.freq_hi, self.alpha_min, self.alpha_max, self.skip_layer, 0)
 
     @property
     def n_params(self) -> int:
@@ -103,7 +110,7 @@ class NeuralField(torch.nn.Module):
     def __init__(self, solver, spec: FieldSpec, seed: int = 0, device="cuda"):
         super().__init__()
         self.solver, self.spec = solver, spec
-        th = synthetic.xavier_theta(spec.n_freq, spec.width, spec.depth, seed)
+        th = synthetic.xavier_theta(spec.n_freq, spec.width, spec.depth, seed, skip=spec.skip_layer)
         assert th.size == spec.n_params
         self.theta = torch.nn.Parameter(torch.tensor(th, dtype=torch.float32, device=device))
 

@@ -207,16 +207,17 @@ def serving_jobs(n_jobs=64, rate=4.0, seed=3000, steps=(200, 1000), sizes=GRID_S
     return jobs
 
 
-def xavier_theta(F, W, depth, seed):
+def xavier_theta(F, W, depth, seed, skip=0):
     """Seeded Xavier-uniform weights and zero biases for the neural field
-    (App. D.1), packed as W_0 [W x 6F], b_0, W_l [W x W], b_l (l = 1..depth-1),
-    w_out [W], b_out [1]; weights row-major [out][in]."""
+    (App. D.1), packed as W_0 [W x 6F], b_0, W_l [W x in_l], b_l (l = 1..depth-1;
+    in_l = W + 6F at the skip layer, else W), w_out [W], b_out [1]; weights
+    row-major [out][in]."""
     import math
     g = rng(seed)
     D = 6 * F
     parts = []
     for l in range(depth):
-        n_in = D if l == 0 else W
+        n_in = D if l == 0 else (W + D if l == skip else W)
         lim = math.sqrt(6.0 / (n_in + W))
         parts += [g.uniform(-lim, lim, size=W * n_in), np.zeros(W)]
     lim = math.sqrt(6.0 / (W + 1))

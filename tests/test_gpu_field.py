@@ -50,7 +50,12 @@ def test_tensor_core_gemm_matches_torch(solver, M, N, K):
 
 
 CASES = [dict(nx=12, ny=10, nz=6, n_freq=32, width=128, depth=2),
-         dict(nx=20, ny=16, nz=8, n_freq=64, width=256, depth=4)]
+         dict(nx=20, ny=16, nz=8, n_freq=64, width=256, depth=4),
+         # band counts that are not multiples of 32 (padded feature block), a skip layer
+         dict(nx=14, ny=9, nz=5, n_freq=5, width=128, depth=3, skip_layer=2),
+         # the paper's field (App. D.4): 12 bands 2^k pi, 10 x 512, skip at layer 4
+         dict(nx=16, ny=16, nz=4, n_freq=12, width=512, depth=10, skip_layer=4, freq_lo=math.pi,
+              freq_hi=2.0 ** 11 * math.pi, alpha_min=0.003, alpha_max=0.25)]
 
 
 def _spec(c):
@@ -63,7 +68,7 @@ def test_field_eval_matches_reference(solver, c):
     import oracle.field as OF
     from paper_2603_11045_gb300.field import field_alpha, annealing_weights
     spec = _spec(c)
-    th = S.xavier_theta(spec.n_freq, spec.width, spec.depth, 11)
+    th = S.xavier_theta(spec.n_freq, spec.width, spec.depth, 11, skip=spec.skip_layer)
     th[-1] = 0.3
     bw = annealing_weights(spec.n_freq, spec.n_freq * 0.6)
     a = field_alpha(solver, spec, torch.tensor(th, dtype=torch.float32, device="cuda"),
@@ -72,8 +77,8 @@ def test_field_eval_matches_reference(solver, c):
     bw32 = torch.tensor(bw, dtype=torch.float32).double()
     args = (spec.nx, spec.ny, spec.nz, spec.n_freq, spec.width, spec.depth, spec.freq_lo, spec.freq_hi,
             spec.alpha_min, spec.alpha_max)
-    emu = OF.field(th32, *args, band_weights=bw32, bf16=True)
-    exact = OF.field(th32, *args, band_weights=bw32, bf16=False)
+    emu = OF.field(th32, *args, band_weights=bw32, bf16=True, skip=spec.skip_layer)
+    exact = OF.field(th32, *args, band_weights=bw32, bf16=False, skip=spec.skip_layer)
     assert rel(a, emu) <= 1e-4
     assert float((a.double().cpu() - emu).abs().max()) <= 2e-3
     assert rel(a, exact) <= 2e-2
@@ -84,17 +89,27 @@ def test_field_backward_matches_reference(solver, c):
     import oracle.field as OF
     from paper_2603_11045_gb300.field import field_alpha
     spec = _spec(c)
-    th = S.xavier_theta(spec.n_freq, spec.width, spec.depth, 12)
+    th = S.xavier_theta(spec.n_freq, spec.width, spec.depth, 12, skip=spec.skip_layer)
     theta = torch.tensor(th, dtype=torch.float32, device="cuda", requires_grad=True)
     g_a = torch.tensor(S.rng(13).standard_normal((spec.nz, spec.ny, spec.nx)), dtype=torch.float32, device="cuda")
     (field_alpha(solver, spec, theta) * g_a).sum().backward()
     ref_th = torch.tensor(th, dtype=torch.float32).double().requires_grad_(True)
     args = (spec.nx, spec.ny, spec.nz, spec.n_freq, spec.width, spec.depth, spec.freq_lo, spec.freq_hi,
             spec.alpha_min, spec.alpha_max)
-    (OF.field(ref_th, *args, bf16=True) * g_a.double().cpu()).sum().backward()
-    g, r = theta.grad.double().cpu(), ref_th.grad
-    assert rel(g, r) <= 2e-2
-    assert float(g @ r / (g.norm() * r.norm())) >= 0.999
+    (OF.field(ref_th, *args, bf16=True, skip=spec.skip_layer) * g_a.double().cpu()).sum().backward()
+    ex_th = torch.tensor(th, dtype=torch.float32).double().requires_grad_(True)
+    (OF.field(ex_th, *args, bf16=False, skip=spec.skip_layer) * g_a.double().cpu()).sum().backward()
+    g, r, x = theta.grad.double().cpu(), ref_th.grad, ex_th.grad
+    # The tensor-core path rounds activations, weights and the back-propagated
+    # deltas to BF16; the emulating reference rounds activations and weights
+    # only.  Both stand off the FP64 gradient by the BF16 spread, which grows
+    # with depth (about 15 % at 10 x 512): the GPU gradient must be as close
+    # to the emulation as that spread allows, and as well aligned with FP64.
+    spread = rel(r, x)
+    assert rel(g, r) <= max(2e-2, 1.5 * spread), (rel(g, r), spread)
+    cos_ref = float(r @ x / (r.norm() * x.norm()))
+    assert float(g @ r / (g.norm() * r.norm())) >= min(0.999, cos_ref - 0.01)
+    assert float(g @ x / (g.norm() * x.norm())) >= min(0.999, cos_ref - 0.01)
 
 
 def test_inversion_chain_finite_differences(solver, orc):

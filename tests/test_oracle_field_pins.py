@@ -86,3 +86,68 @@ def test_field_gradient_finite_differences(F):
         fd = ((F.field(tp, 4, 3, 2, Fq, W, depth, 1.0, 8.0, 0.01, 2.0) * g_a).sum()
               - (F.field(tm, 4, 3, 2, Fq, W, depth, 1.0, 8.0, 0.01, 2.0) * g_a).sum()) / (2 * e)
         assert float(th.grad[i]) == pytest.approx(float(fd), rel=1e-6, abs=1e-9)
+
+
+def test_skip_with_zero_encoding_columns_is_the_plain_network(F):
+    """App. D.1 skip connection: with the encoding columns of the skip layer's
+    weights zero, the network is exactly the one without the skip on the same
+    hidden weights."""
+    Fq, W, depth, s = 4, 8, 4, 2
+    D = 6 * Fq
+    th = torch.tensor(S.xavier_theta(Fq, W, depth, 11, skip=s), dtype=torch.float64)
+    assert th.numel() == F.param_count(Fq, W, depth, s)
+    layers, w_out, b_out = F.unpack(th, Fq, W, depth, s)
+    Ws, bs = layers[s]
+    Ws = Ws.clone(); Ws[:, W:] = 0.0
+    plain = []
+    for l, (Wl, bl) in enumerate(layers):
+        Wl = Ws[:, :W] if l == s else Wl
+        plain += [Wl.reshape(-1), bl + 0.1 * l]
+    plain += [w_out, b_out]
+    packed = []
+    for l, (Wl, bl) in enumerate(layers):
+        packed += [(Ws if l == s else Wl).reshape(-1), bl + 0.1 * l]
+    packed += [w_out, b_out]
+    a_skip = F.field(torch.cat(packed), 3, 4, 2, Fq, W, depth, 1.0, 8.0, 0.01, 2.0, skip=s)
+    a_plain = F.field(torch.cat(plain), 3, 4, 2, Fq, W, depth, 1.0, 8.0, 0.01, 2.0)
+    assert torch.allclose(a_skip, a_plain, rtol=0, atol=1e-15)
+
+
+def test_skip_reinjects_the_encoding_closed_form(F):
+    """All layers before the skip layer zero (so h_s = 0): one unit of the skip
+    layer reading the sin feature of x band 1 in the re-injected block gives
+    alpha = lo + (hi-lo) sigmoid(relu(sin(w1 x)) - 0.2), which pins where the
+    encoding sits in the skip layer's input."""
+    Fq, W, depth, s = 4, 8, 3, 2
+    D = 6 * Fq
+    th = torch.zeros(F.param_count(Fq, W, depth, s), dtype=torch.float64)
+    p_s = (W * D + W) + (W * W + W)                 # start of W_2 (after layers 0 and 1)
+    th[p_s + 0 * (W + D) + W + (0 * 2 * Fq + 1 * 2 + 0)] = 1.0   # W_2[0, W + (axis x, band 1, sin)]
+    p_out = p_s + W * (W + D) + W
+    th[p_out + 0] = 1.0
+    th[-1] = -0.2
+    nx, ny, nz = 6, 2, 3
+    a = F.field(th, nx, ny, nz, Fq, W, depth, 1.0, 27.0, 0.02, 1.0, skip=s)
+    x = 2.0 * (np.arange(nx) + 0.5) / nx - 1.0
+    w1 = 1.0 * 27.0 ** (1 / 3)
+    expect = 0.02 + 0.98 / (1 + np.exp(-(np.maximum(np.sin(w1 * x), 0.0) - 0.2)))
+    assert np.allclose(a.numpy(), np.broadcast_to(expect[None, None, :], (nz, ny, nx)), atol=1e-14)
+
+
+def test_skip_field_gradient_finite_differences(F):
+    """Autograd through the concatenation vs central differences."""
+    Fq, W, depth, s = 3, 8, 4, 2
+    th0 = torch.tensor(S.xavier_theta(Fq, W, depth, 12, skip=s), dtype=torch.float64)
+    g_a = torch.tensor(S.rng(13).standard_normal((2, 3, 4)))
+    th = th0.clone().requires_grad_(True)
+    J = (F.field(th, 4, 3, 2, Fq, W, depth, 1.0, 8.0, 0.01, 2.0, skip=s) * g_a).sum()
+    J.backward()
+    p_s = (W * 6 * Fq + W) + (W * W + W)
+    idx = list(S.rng(14).integers(0, th0.numel(), 8)) + [p_s + W + 5, p_s + 3 * (W + 6 * Fq) + W + 1]
+    for i in idx:
+        e = 1e-6
+        tp = th0.clone(); tp[i] += e
+        tm = th0.clone(); tm[i] -= e
+        fd = ((F.field(tp, 4, 3, 2, Fq, W, depth, 1.0, 8.0, 0.01, 2.0, skip=s) * g_a).sum()
+              - (F.field(tm, 4, 3, 2, Fq, W, depth, 1.0, 8.0, 0.01, 2.0, skip=s) * g_a).sum()) / (2 * e)
+        assert float(th.grad[i]) == pytest.approx(float(fd), rel=1e-6, abs=1e-9)
