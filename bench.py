@@ -24,6 +24,7 @@ import os
 import signal
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -131,7 +132,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples (summarised in the JSON line's "clocks")
+        self.path = os.path.join(os.environ.get("NEFTY_BENCH_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"nefty_clocks_rank{index}_{os.getpid()}.csv")
 
     def start(self):
         try:
