@@ -1059,8 +1059,6 @@ struct GradBody {
     unsigned S;            // cells per plane
     float bth[4], btl[4], bmh[4], bml[4], bac[4];   // plane k0 - 1 (segment start only)
     float zdn[4], zdn1[4];                          // -z terms of plane k and of plane k + 1
-    float4 gq[2];          // the accumulator of the quad on the next plane, loaded a plane ahead
-    bool have;
     __device__ __forceinline__ static float term(float a0, float mc, float mcl, float tc, float tcl, float aq,
                                                  float mq, float mql, float tq, float tql, float w) {
         const float h = aq * rcp_approx(a0 + aq);
@@ -1087,7 +1085,7 @@ struct GradBody {
         ld4(st, sl(5), hb, mlo);
         ld4(st, sl(3), hb, a);
     }
-    __device__ __forceinline__ void reset() { have = false; }
+    __device__ __forceinline__ void reset() {}
     __device__ __forceinline__ void below(const unsigned char* st, int hb) { load(st, hb, bth, btl, bmh, bml, bac); }
     __device__ __forceinline__ void own(const unsigned char* st, int hb, bool has_below) {
         if (!has_below) return;
@@ -1102,13 +1100,8 @@ struct GradBody {
     __device__ __forceinline__ void plane(int k, unsigned c, bool valid, const unsigned char* st,
                                           const unsigned char* st1, int hb, int) {
         if (!valid) return;
-        const float4 g01 = have ? gq[0] : *reinterpret_cast<const float4*>(grad + c);
-        const float4 g23 = have ? gq[1] : *reinterpret_cast<const float4*>(grad + c + 2);
-        have = k + 1 < nz;   // the next plane's accumulator (the same cells one plane up)
-        if (have) {
-            gq[0] = *reinterpret_cast<const float4*>(grad + c + S);
-            gq[1] = *reinterpret_cast<const float4*>(grad + c + S + 2);
-        }
+        const float4 g01 = *reinterpret_cast<const float4*>(grad + c);
+        const float4 g23 = *reinterpret_cast<const float4*>(grad + c + 2);
         float th[4], tl[4], mh[4], ml[4], ac[4];
         load(st, hb, th, tl, mh, ml, ac);
         float s[4] = {0.f, 0.f, 0.f, 0.f};
@@ -1740,7 +1733,7 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(const __grid_constant__ F
         float rel = 0.f;
         bool conv = true;
         const int hu = hu_at(n);
-        auto rhs = [&](unsigned c, int k) { return (qmap && k == 0) ? sc * qmap[c] : 0.f; };
+        auto rhs = [=](unsigned c, int k) { return (qmap && k == 0) ? sc * qmap[c] : 0.f; };
         bool ok;
         if constexpr (kJac) {   // the paper's inner solver: K sweeps from T^n
             ok = solve_jacobi<kTma>(a.c, sy, ring, pre, Start{Tn, 0}, rhs, a.c.jacobi_k);
@@ -1819,8 +1812,9 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ A
         float rel = 0.f;
         bool conv = true;
         const int hu = hu_at(n);
-        auto rhs = [&](unsigned c, int) {
-            return (c >= a.obs_off && c < a.obs_off + S) ? gs * ((Tn[c] - ob[c - a.obs_off]) + Tn[N + c]) : 0.f;
+        const unsigned o0 = a.obs_off;
+        auto rhs = [=](unsigned c, int) {
+            return (c - o0 < S) ? gs * ((Tn[c] - ob[c - o0]) + Tn[N + c]) : 0.f;
         };
         bool ok;
         if constexpr (kJac) {   // the paper's inner solver: K sweeps from mu^{n+1}
@@ -1985,7 +1979,7 @@ __device__ bool sw_staged(const BatchSweep& w, const SwState& st, Ring& ring, Ac
         const unsigned S = a.c.g.S;
         const float* qmap = a.q_full ? a.q_full + (size_t)n * S : (n < a.q_steps ? a.q_face : nullptr);
         const float sc = a.src_scale;
-        auto rhs = [&](unsigned c, int k) { return (qmap && k == 0) ? sc * qmap[c] : 0.f; };
+        auto rhs = [=](unsigned c, int k) { return (qmap && k == 0) ? sc * qmap[c] : 0.f; };
         PassIn in{kInit1, 0, false, 0u, 0u, hu};
         if (!slab_half(a.c, hu > 0 ? a.ystart : a.src[n - a.n0], &in.zx)) return false;
         Init1Body<decltype(rhs)> Bd(a.c, rhs, acc, hu);
