@@ -444,3 +444,25 @@ def test_jacobi_k_recompute_is_bitwise(solver):
     k7 = solver.adjoint_grad(prob.with_(ckpt_every=7), a, obs, q_face=q, q_steps=3)
     assert torch.equal(k7["grad_alpha"], k1["grad_alpha"]) and k7["loss"] == k1["loss"]
     assert k7["stats"]["recompute_steps"] == 30
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_jacobi_k_paper_grid_matches_oracle(solver, orc, prec):
+    """The paper's own setting: its grid (64x64x16, dx 0.156, dz 0.0625,
+    periodic lateral walls, post-flash T0) with K = 50 Jacobi sweeps per
+    solve, against the oracle's Jacobi mode."""
+    from paper_2603_11045_gb300.solver import Problem
+    w = S.paper_grid_case(seed=5001, nt=20)
+    alpha, T0 = _cast(w.alpha, prec), _cast(w.T0, prec)
+    op = orc.from_workload(w)
+    obs = _cast(orc.forward(op, _cast(w.alpha_target, prec), T0=T0, jacobi_k=50)["frames"], prec)
+    ref = orc.adjoint_grad(op, alpha, T0=T0, obs=obs, jacobi_k=50)
+    ref_f = orc.forward(op, alpha, T0=T0, jacobi_k=50)["frames"]
+    prob = Problem.from_workload(w, prec=prec, jacobi_k=50)
+    f = solver.forward(prob, dev(alpha, prec), T0=dev(T0, prec))["frames"].cpu().numpy()
+    g = solver.adjoint_grad(prob, dev(alpha, prec), dev(obs, prec), T0=dev(T0, prec))
+    assert rel_l2(f, ref_f) <= SURF_TOL[prec]
+    gtol = 1e-9 if prec == "fp64" else 1e-3
+    gg = g["grad_alpha"].cpu().numpy()
+    assert rel_l2(gg, ref["grad_alpha"]) <= gtol and cosine(gg, ref["grad_alpha"]) >= 0.9999
+    assert g["loss"] == pytest.approx(ref["loss"], rel=1e-9 if prec == "fp64" else 1e-4)
