@@ -192,6 +192,23 @@ def cpu_cores():
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
+def oracle_single_thread(args):
+    """The same oracle sample (one time step) on one host thread, in a fresh
+    process with OMP_NUM_THREADS=1; None if that process fails."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1", "--warmup", "0",
+           "--cpu-sample-steps", "1", "--nx", str(args.nx), "--ny", str(args.ny), "--nz", str(args.nz),
+           "--nt", str(args.nt)]
+    env = dict(os.environ, OMP_NUM_THREADS="1", RANK="0")
+    try:
+        res = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=300)
+        line = json.loads(res.stdout.strip().splitlines()[-1])
+        return {"value": line["value"], "unit": line["unit"], "cores": 1,
+                "sample": f"first 1 of {args.nt} steps of the same grid, forward + adjoint, FP64, "
+                          f"{line['ms_per_step'] / 1000:.1f} s"}
+    except Exception:
+        return None
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -388,6 +405,8 @@ def run_native(args):
         v, s = oracle_sample(args, w, cand, steps)
         cpu = {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                "sample": f"first {steps} of {w.nt} steps of the same grid, forward + adjoint, FP64, {s:.1f} s"}
+        if cpu_cores() > 1:
+            cpu["single_thread"] = oracle_single_thread(args)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
