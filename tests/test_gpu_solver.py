@@ -216,6 +216,22 @@ def test_gradient_directional_fd_fp64(solver):
     assert (Jp - Jm) / (2 * eps) == pytest.approx(float((g * d).sum()), rel=1e-6)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_bench_grid_first_steps_match_oracle(solver, orc, prec):
+    """The bench's grid at full size (256x256x48; FP32: the persistent
+    TMA-staged kernels on every SM with the extrapolated start, as the bench
+    runs them) over the first 4 steps of its pulse, against the oracle at the
+    same size: surface frames and loss, and for FP64 the gradient and dJ/dT0
+    as well.  Candidate alpha = 1, targets from the ground-truth field."""
+    w = S.neural_field_case(nt=4)
+    w = S.Workload(w.name, w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.dt, w.nt, alpha=np.ones_like(w.alpha),
+                   q_face=w.q_face, q_steps=w.q_steps, alpha_target=w.alpha_target)
+    out = run_pair(solver, orc, w, prec, check_grad=prec == "fp64")
+    if prec == "fp32":
+        assert out["stats"]["grid_blocks"] >= 128   # one persistent CTA per SM
+    assert_parity(out, prec, grad=prec == "fp64")
+
+
 def test_energy_and_maximum_principle_large(solver):
     """Full 256x256x48 grid (FP32): with zero-flux walls total heat equals the
     deposited heat, and without sources the field stays within its initial
