@@ -43,12 +43,13 @@ UNIT = "Gcell-steps/s"
 # solution write (8 B).  FP64 doubles both.
 ALG_BYTES_ITER = {"fp32": 40, "fp64": 80}
 ALG_BYTES_STEP = {"fp32": 8, "fp64": 16}
-# DRAM bytes per cell per solver pass of the FP32 CG kernels, from the ncu
-# capture summarised in profiles/forward_tiled_256x256x48_nt20_ncu.md, scaled
-# to the timed launches by their pass count (CG iterations plus the
+# DRAM bytes per cell per solver pass of the FP32 CG kernels, from one ncu
+# capture of each sweep on the 256x256x48 grid (20 steps): forward and
+# recompute launches, and the reverse sweep with the gradient.  Scaled to the
+# timed launches by their pass counts (CG iterations plus the
 # init/finalise/gradient passes of each solve).  None = no capture of the
 # current kernels.
-DRAM_BYTES_PER_CELL_PASS = {"fp32": 24.2, "fp64": None}
+DRAM_BYTES_PER_CELL_PASS = {"fp32": {"fwd": 24.2, "adj": 25.6}, "fp64": None}
 
 
 def parse():
@@ -360,9 +361,12 @@ def run_native(args):
     peak = pk["hbm_gbs"] if pk else 6800.0
     achieved = alg_bytes / (cg_ms / 1000.0) / 1e9
     st0 = stats[0]
-    passes = (iters + 3 * (st0["fwd_steps"] + st0["recompute_steps"]) + 4 * st0["adj_steps"])
+    fwd_iters = sum(s["fwd_iters"] + s["recompute_iters"] for s in stats) / len(stats)
+    adj_iters = sum(s["adj_iters"] for s in stats) / len(stats)
+    fwd_passes = fwd_iters + 3 * (st0["fwd_steps"] + st0["recompute_steps"])
+    adj_passes = adj_iters + 4 * st0["adj_steps"]
     bpp = DRAM_BYTES_PER_CELL_PASS[R]
-    traffic = None if bpp is None else bpp * w.n_cells * passes
+    traffic = None if bpp is None else w.n_cells * (bpp["fwd"] * fwd_passes + bpp["adj"] * adj_passes)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_note": "DRAM bytes per step, ncu capture scaled by solver passes", "kernel": "persistent fused Jacobi-PCG (forward_kernel + adjoint_kernel)",
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback",
