@@ -111,6 +111,7 @@ struct Args {
     int vec;                     // ldo, ldm and every base 16-byte aligned: 16-byte epilogue stores
     __nv_bfloat16* out_t;        // BF16 epilogues: also D^T [N, ldt] (or null)
     int ldt;
+    int n_tiles;                 // output tiles along N
     int* err;
 };
 
@@ -123,7 +124,9 @@ gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
     __shared__ int s_fail;
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    // the N tiles of one M tile are consecutive CTAs, so the A tile they share
+    // is read from DRAM once and from L2 by the others
+    const int m0 = (int)(blockIdx.x / (unsigned)a.n_tiles) * BM, n0 = (int)(blockIdx.x % (unsigned)a.n_tiles) * BN;
     const int kb0 = blockIdx.z * a.k_blocks_per_split;
     const int kb1 = min(a.K / BK, kb0 + a.k_blocks_per_split);
     const int nk = kb1 - kb0;
@@ -359,7 +362,10 @@ cudaError_t umma_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, i
                                      (epi != umma::kEpiMaskBf16 || (al16(mask) && a.ldm % 8 == 0))))
                 ? 1 : 0;
     a.err = err;
-    dim3 grid((M + umma::BM - 1) / umma::BM, (N + umma::BN - 1) / umma::BN, splits);
+    a.n_tiles = (N + umma::BN - 1) / umma::BN;
+    const long long tiles = (long long)((M + umma::BM - 1) / umma::BM) * a.n_tiles;
+    if (tiles < 1 || tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)tiles, 1, splits);
     if (a.k_blocks_per_split <= 8)
         umma::gemm_kernel<2><<<grid, umma::THREADS, umma::smem_bytes(2), s>>>(ma, mb, a);
     else
