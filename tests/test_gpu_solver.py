@@ -232,6 +232,20 @@ def test_bench_grid_first_steps_match_oracle(solver, orc, prec):
     assert_parity(out, prec, grad=prec == "fp64")
 
 
+def test_largest_grid_first_steps_match_oracle(solver, orc):
+    """The largest workload's grid (512x512x96 = 25.2 M cells, layered with
+    delaminations): the FP32 forward sweep in its persistent TMA-staged
+    kernel against the oracle at full size, over the first 2 steps of the
+    pulse (surface frames)."""
+    from paper_2603_11045_gb300.solver import Problem
+    w = S.layered_delamination_case(nt=2)
+    ref = orc.forward(orc.from_workload(w), w.alpha, q_face=w.q_face, q_steps=w.q_steps)["frames"]
+    prob = Problem.from_workload(w, prec="fp32")
+    out = solver.forward(prob, dev(w.alpha, "fp32"), q_face=dev(w.q_face, "fp32"), q_steps=w.q_steps)
+    assert out["stats"]["grid_blocks"] >= 128
+    assert rel_l2(out["frames"].cpu().numpy(), ref) <= SURF_TOL["fp32"]
+
+
 def test_energy_and_maximum_principle_large(solver):
     """Full 256x256x48 grid (FP32): with zero-flux walls total heat equals the
     deposited heat, and without sources the field stays within its initial
