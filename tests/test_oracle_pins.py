@@ -375,3 +375,52 @@ def test_tv_gradient_fd(orc, bc):
         a2 = alpha.ravel().copy(); a2[i] -= 1e-7
         fd.append((orc.tv(p, a1, lam, eps, False)[0] - orc.tv(p, a2, lam, eps, False)[0]) / 2e-7)
     assert np.abs(grad.ravel() - np.array(fd)).max() <= 1e-7 * np.abs(fd).max()
+
+
+@pytest.mark.parametrize("axis", ["x", "y"])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_tv_lateral_ramp_wrap_closed_form(orc, axis, bc):
+    """Eq. tv_discrete on a lateral ramp alpha = c * i (or c * j).  Every cell
+    before the last column (row) has the forward difference c / h.  On the
+    last one the difference wraps to the first column when the lateral walls
+    are periodic, a jump of -c (n - 1) / h, and vanishes with zero-flux walls.
+    The gradient (eps > 0) is zero inside the ramp, where the two forward
+    differences a cell enters are equal, and takes closed values at the two
+    ends, which carry the wrap."""
+    nx, ny, nz = 5, 4, 3
+    dx, dy, dz, c, lam, eps = 0.5, 1.5, 0.25, 0.3, 2.0, 1e-2
+    n, h = (nx, dx) if axis == "x" else (ny, dy)
+    idx = np.arange(n, dtype=np.float64) * c
+    alpha = np.broadcast_to(idx[None, None, :] if axis == "x" else idx[None, :, None], (nz, ny, nx)).copy() + 1.0
+    p = orc.problem(nx, ny, nz, dx=dx, dy=dy, dz=dz, bc=bc)
+    V = dx * dy * dz
+    lines = nx * ny * nz // n   # ramps along the axis
+    # eps = 0: the value alone
+    val0, _ = orc.tv(p, alpha, lam=lam, eps=0.0)
+    per_line = (n - 1) * c / h + ((n - 1) * c / h if bc == 1 else 0.0)
+    assert val0 == pytest.approx(lam * V * lines * per_line, rel=1e-14)
+    # eps > 0: value and gradient
+    val, grad = orc.tv(p, alpha, lam=lam, eps=eps)
+    t_in = np.hypot(c / h, eps)
+    t_last = np.hypot((n - 1) * c / h, eps) if bc == 1 else eps
+    assert val == pytest.approx(lam * V * lines * ((n - 1) * t_in + t_last), rel=1e-14)
+    want = np.zeros(n)
+    want[0] = -lam * V * c / (h * h * t_in)
+    want[n - 1] = lam * V * c / (h * h * t_in)
+    if bc == 1:   # the wrapped difference of the last cell, -c (n - 1) / h
+        w = lam * V * (n - 1) * c / (h * h * t_last)
+        want[0] -= w
+        want[n - 1] += w
+    full = np.broadcast_to(want[None, None, :] if axis == "x" else want[None, :, None], (nz, ny, nx))
+    assert np.abs(grad - full).max() <= 1e-13 * np.abs(want).max()
+
+
+def test_tv_z_never_wraps(orc):
+    """The z difference vanishes on the last slice with periodic lateral walls
+    too (Eq. tv_discrete wraps only x and y): a z ramp gives the same value
+    under both wall settings, (nz - 1) slices of c / dz."""
+    nx, ny, nz, dz, c = 3, 4, 6, 0.5, 0.2
+    alpha = (1.0 + c * np.arange(nz))[:, None, None] * np.ones((nz, ny, nx))
+    vals = [orc.tv(orc.problem(nx, ny, nz, dz=dz, bc=bc), alpha, lam=1.0, eps=0.0)[0] for bc in (0, 1)]
+    assert vals[1] == pytest.approx(dz * nx * ny * (nz - 1) * c / dz, rel=1e-14)
+    assert vals[0] == vals[1]
