@@ -137,6 +137,19 @@ const char *nefty_last_error(const nefty_handle *h);
 /* Static name of a status code. */
 const char *nefty_status_string(nefty_status s);
 
+/* Fault injection for tests of the bounded device-side waits; the paper has
+ * no counterpart.  Every grid barrier of the solver kernels waits at most a
+ * limit of %globaltimer time (2 s by default) and then gives up: the launch
+ * records the failure, ends, and the call returns NEFTY_ETIMEOUT with the
+ * CUDA context intact.  With missing_arrivals > 0, every grid barrier of the
+ * later solver launches of `h` (forward and adjoint sweeps, both precisions)
+ * waits for that many CTAs more than the launch has, an arrival that never
+ * comes, so the limit runs out on purpose; wait_limit_ns > 0 replaces the
+ * 2 s limit of those launches (0 = 2 s).  (0, 0) restores normal operation.
+ * Pipeline (mbarrier) waits inside a pass keep their own limit.  Limits:
+ * missing_arrivals <= 1024, wait_limit_ns <= 60 s; NEFTY_EINVAL otherwise. */
+nefty_status nefty_debug_barrier_fault(nefty_handle *h, uint32_t missing_arrivals, uint64_t wait_limit_ns);
+
 /* Host-only validation of a problem (no device work): NEFTY_OK or NEFTY_EINVAL. */
 nefty_status nefty_problem_check(const nefty_problem *p);
 
@@ -226,32 +239,37 @@ nefty_status nefty_tv(nefty_handle *h, const nefty_problem *p, const void *alpha
 
 /* Forward sweep that allocates no device memory.
  *
- * The paper has no counterpart; this is an integration entry point.  Some
- * callers may not allocate device memory when they need a solve: code running
- * while a stream is captured into a CUDA graph in global capture mode (where
- * cudaMalloc is an illegal call), real-time or serving loops that reserve the
- * whole device up front and cannot take the implicit synchronisation of
- * cudaMalloc/cudaFree, and hosts that hand out memory only from their own
- * pool.  This call needs no handle and calls no allocator: its scratch is one
- * static device array of 48 MiB that every GPU loading the library holds until
- * the process exits.
+ * The paper has no counterpart; this entry point exists for integration.
+ * nefty_forward takes its scratch from a handle that grows with cudaMalloc.
+ * Some callers cannot allow that when they need a solve: a serving or
+ * real-time loop that has reserved the whole device for its own buffers (so
+ * no memory is left to allocate), a loop that cannot take the device-wide
+ * synchronisation cudaMalloc and cudaFree may imply, or a host application or
+ * plug-in framework that hands out device memory only from its own pool.
+ * This call needs no handle and calls no allocator (no cudaMalloc, no
+ * cudaFree, no allocating library routine): its scratch is one static device
+ * array of 48 MiB that every GPU loading the library holds until the process
+ * exits.
  *
  *   device      CUDA device to run on (made current for the call, then restored).
- *   p           as for nefty_forward (FP32 or FP64; the FP64 kernel family of
- *               nefty_forward runs in both precisions here).
+ *   p           as for nefty_forward, with the same defaults for rtol and
+ *               max_iter (FP32 or FP64; the FP64 kernel family of nefty_forward
+ *               runs in both precisions here).
  *   alpha, T0, q_face, frames_out, T_final, obs: as for nefty_forward, but every
- *               non-NULL array must be DEVICE memory (no host staging).
+ *               non-NULL array must be device memory of `device` (or managed
+ *               memory): nothing is staged.
  *   loss_out    host double*, or NULL; needs obs.
  * Each solve is the converged Jacobi-PCG (p->jacobi_k must be 0).
  * Limits: the problem's scratch, 10 values per cell (40 B FP32, 80 B FP64) plus
  * about 2 MiB of fixed tables, must fit the 48 MiB array (e.g. about 1.1 M cells
  * FP32, 0.57 M cells FP64), and nt <= 65536; larger problems return NEFTY_EINVAL
- * with a message, and so do host arrays.
- * The first call on each device resolves the array's device address; make that
- * first call before any stream capture.  All calls on a device share the array
- * and it keeps the last call's contents (the call clears what must start at
- * zero), so calls whose work overlaps on the GPU race and must be serialised by
- * the caller.  Returns after the work on `stream` has completed. */
+ * with a message, and so do host arrays and arrays on another device.
+ * Set-up: the first call on each device, with that device current, looks up
+ * the array's device address (cudaGetSymbolAddress) and sizes the launch; make
+ * that first call before any stream capture.  All calls on a device share the
+ * array and it keeps the last call's contents (each call clears what must start
+ * at zero), so calls whose work overlaps on the GPU race and must be serialised
+ * by the caller.  Returns after the work on `stream` has completed. */
 nefty_status nefty_forward_static(int device, const nefty_problem *p, const void *alpha, const void *T0,
                                   const void *q_face, int32_t q_steps, void *frames_out, void *T_final,
                                   const void *obs, double *loss_out, void *stream);

@@ -96,6 +96,7 @@ _SIGNATURES = {
     "nefty_last_error": ([_vp], ctypes.c_char_p),
     "nefty_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "nefty_problem_check": ([_P], ctypes.c_int),
+    "nefty_debug_barrier_fault": ([_vp, ctypes.c_uint32, ctypes.c_uint64], ctypes.c_int),
     "nefty_forward": ([_vp, _P, _vp, _vp, _vp, ctypes.c_int32, _vp, _vp, _vp, _vp,
                        ctypes.POINTER(ctypes.c_double), _ST, _vp], ctypes.c_int),
     "nefty_adjoint_grad": ([_vp, _P, _vp, _vp, _vp, ctypes.c_int32, _vp, _vp,

@@ -29,6 +29,9 @@ struct nefty_handle {
     int batch_shared = 0;        // ... of which carried other handles' sweeps too
     nefty::Server* server = nullptr;
     std::string err;
+    // fault injection of the solver launches (nefty_debug_barrier_fault)
+    uint32_t fault_missing = 0;
+    uint64_t fault_wait_ns = 0;
 };
 
 void nefty::set_grid_share(nefty_handle* h, int share) { h->grid_share = share > 1 ? share : 1; }
@@ -83,14 +86,21 @@ struct DeviceGuard {
     }
 };
 
-bool is_device_ptr(const void* p) {
-    if (!p) return false;
+// Where an array lives, seen from device `dev`: host memory (staged by the
+// call), memory the kernels on `dev` may read in place (device memory of
+// `dev`, or managed memory), or device memory of another GPU, which the
+// kernels on `dev` must never dereference.
+enum PtrKind { kPtrHost, kPtrDevice, kPtrOtherDevice };
+PtrKind ptr_kind(const void* p, int dev) {
+    if (!p) return kPtrHost;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return kPtrHost;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return kPtrDevice;
+    if (at.type == cudaMemoryTypeDevice) return at.device == dev ? kPtrDevice : kPtrOtherDevice;
+    return kPtrHost;
 }
 
 // Effective problem with defaults filled in.
@@ -125,7 +135,7 @@ nefty_status check_problem(const nefty_problem* p, Prob* out, std::string* why) 
     if (out) {
         out->nx = p->nx; out->ny = p->ny; out->nz = p->nz; out->nt = p->nt; out->bc = p->bc;
         out->obs_face = p->obs_face; out->prec = p->prec;
-        out->max_iter = p->max_iter > 0 ? p->max_iter : 1000;
+        out->max_iter = p->max_iter > 0 ? p->max_iter : kDefaultMaxIter;
         out->ckpt_every = p->ckpt_every;
         // increments the start extrapolates from: 0 .. kRing
         out->extrap = p->extrap == 0 ? kDefaultExtrap : (p->extrap < 0 ? 0 : p->extrap);
@@ -133,7 +143,7 @@ nefty_status check_problem(const nefty_problem* p, Prob* out, std::string* why) 
         out->jacobi_k = p->jacobi_k;
         if (out->jacobi_k > 0) out->extrap = 0;
         out->dx = p->dx; out->dy = p->dy; out->dz = p->dz; out->dt = p->dt; out->robin_h = p->robin_h;
-        out->rtol = p->rtol > 0 ? p->rtol : (p->prec == NEFTY_FP32 ? 5e-10 : 1e-13);
+        out->rtol = p->rtol > 0 ? p->rtol : (p->prec == NEFTY_FP32 ? kDefaultRtolFp32 : kDefaultRtolFp64);
         out->loss_scale = p->loss_scale > 0 ? p->loss_scale : 1.0 / ((double)p->nt * p->nx * p->ny);
         out->S = (unsigned)p->nx * (unsigned)p->ny;
         out->N = out->S * (unsigned)p->nz;
@@ -185,11 +195,14 @@ struct Input {
     const void* user = nullptr;
     size_t bytes = 0;
     bool stage = false;
+    bool foreign = false;   // device memory of another GPU: rejected by the call
     void* dev = nullptr;
-    void plan(const void* p, size_t b) {
+    void plan(const void* p, size_t b, int device) {
         user = p;
         bytes = b;
-        stage = p && !is_device_ptr(p);
+        const PtrKind k = ptr_kind(p, device);
+        stage = p && k == kPtrHost;
+        foreign = p && k == kPtrOtherDevice;
     }
     void place(Arena& a) {
         if (!user) { dev = nullptr; return; }
@@ -204,11 +217,14 @@ struct Output {
     void* user = nullptr;
     size_t bytes = 0;
     bool stage = false;
+    bool foreign = false;   // device memory of another GPU: rejected by the call
     void* dev = nullptr;
-    void plan(void* p, size_t b) {
+    void plan(void* p, size_t b, int device) {
         user = p;
         bytes = b;
-        stage = p && !is_device_ptr(p);
+        const PtrKind k = ptr_kind(p, device);
+        stage = p && k == kPtrHost;
+        foreign = p && k == kPtrOtherDevice;
     }
     void place(Arena& a) {
         if (!user) { dev = nullptr; return; }
@@ -216,6 +232,15 @@ struct Output {
         else { a.take(0); dev = user; }
     }
 };
+
+// EINVAL when any planned array is device memory of a GPU other than the
+// handle's: the kernels would dereference it without peer access.
+template <class... A>
+nefty_status reject_foreign(nefty_handle* h, const A&... arrays) {
+    const bool any = (false || ... || arrays.foreign);
+    if (any) return fail(h, NEFTY_EINVAL, "an array is device memory of another GPU than the handle's");
+    return NEFTY_OK;
+}
 
 int grid_for(nefty_handle* h, int prec, unsigned N) {
     if (h->grid_max[prec] == 0) h->grid_max[prec] = solver_grid_blocks(h->device, prec);
@@ -335,6 +360,13 @@ struct Call {
             if (in->user && in->stage)
                 NEFTY_CUDA(h, cudaMemcpyAsync(in->dev, in->user, in->bytes, cudaMemcpyHostToDevice, s));
         NEFTY_CUDA(h, cudaMemsetAsync(ctl, 0, sizeof(DevCtl), s));
+        if (h->fault_missing || h->fault_wait_ns) {   // test hook: see nefty_debug_barrier_fault
+            DevCtl init{};
+            init.missing = h->fault_missing;
+            init.wait_ns = h->fault_wait_ns;
+            NEFTY_CUDA(h, cudaMemcpyAsync(ctl, &init, sizeof init, cudaMemcpyHostToDevice, s));
+            NEFTY_CUDA(h, cudaStreamSynchronize(s));   // init lives on this stack frame
+        }
         if (kTiled) {   // no increment history yet
             NEFTY_CUDA(h, cudaMemsetAsync(ring_f, 0, tiled::kRing * (size_t)P.N * sizeof(float), s));
             NEFTY_CUDA(h, cudaMemsetAsync(ring_a, 0, tiled::kRing * (size_t)P.N * sizeof(float), s));
@@ -634,14 +666,15 @@ nefty_status run_forward(nefty_handle* h, const Prob& P, const void* alpha, cons
     C.timing = st != nullptr;
     C.G = Call<Real>::kTiled ? grid_for_tiled(h, P) : grid_for(h, P.prec, P.N);
     if (C.G <= 0) return fail(h, NEFTY_ECUDA, "cannot size the persistent solver grid on this device");
-    C.alpha.plan(alpha, N * R);
-    C.T0.plan(T0, N * R);
-    C.qf.plan(q_face, S * R);
-    C.qfull.plan(q_full, nt * S * R);
-    C.obs.plan(loss_out ? obs : nullptr, nt * S * R);
+    C.alpha.plan(alpha, N * R, h->device);
+    C.T0.plan(T0, N * R, h->device);
+    C.qf.plan(q_face, S * R, h->device);
+    C.qfull.plan(q_full, nt * S * R, h->device);
+    C.obs.plan(loss_out ? obs : nullptr, nt * S * R, h->device);
     Output fr, tf;
-    fr.plan(frames_out, nt * S * R);
-    tf.plan(T_final, N * R);
+    fr.plan(frames_out, nt * S * R, h->device);
+    tf.plan(T_final, N * R, h->device);
+    if (nefty_status e = reject_foreign(h, C.alpha, C.T0, C.qf, C.qfull, C.obs, fr, tf)) return e;
     Real *work[2], *t0buf = nullptr;
     // one state = N values; the FP32 path keeps it as a compensated (hi, lo)
     // pair, so its state slots hold 2N floats
@@ -755,14 +788,15 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
     C.timing = st != nullptr;
     C.G = Call<Real>::kTiled ? grid_for_tiled(h, P) : grid_for(h, P.prec, P.N);
     if (C.G <= 0) return fail(h, NEFTY_ECUDA, "cannot size the persistent solver grid on this device");
-    C.alpha.plan(alpha, N * R);
-    C.T0.plan(T0, N * R);
-    C.qf.plan(q_face, S * R);
-    C.qfull.plan(q_full, nt * S * R);
-    C.obs.plan(obs, nt * S * R);
+    C.alpha.plan(alpha, N * R, h->device);
+    C.T0.plan(T0, N * R, h->device);
+    C.qf.plan(q_face, S * R, h->device);
+    C.qfull.plan(q_full, nt * S * R, h->device);
+    C.obs.plan(obs, nt * S * R, h->device);
     Output ga, gt;
-    ga.plan(grad_alpha, N * R);
-    gt.plan(grad_T0, N * R);
+    ga.plan(grad_alpha, N * R, h->device);
+    gt.plan(grad_T0, N * R, h->device);
+    if (nefty_status e = reject_foreign(h, C.alpha, C.T0, C.qf, C.qfull, C.obs, ga, gt)) return e;
 
     // Fixed part of the workspace (everything except stored states).
     size_t fixed = 0;
@@ -1019,6 +1053,15 @@ const char* nefty_status_string(nefty_status s) {
     return "NEFTY_UNKNOWN";
 }
 
+nefty_status nefty_debug_barrier_fault(nefty_handle* h, uint32_t missing_arrivals, uint64_t wait_limit_ns) {
+    if (!h) return fail(nullptr, NEFTY_EINVAL, "handle is NULL");
+    if (missing_arrivals > 1024u) return fail(h, NEFTY_EINVAL, "missing_arrivals must be <= 1024");
+    if (wait_limit_ns > 60ull * 1000000000ull) return fail(h, NEFTY_EINVAL, "wait_limit_ns must be <= 60 s");
+    h->fault_missing = missing_arrivals;
+    h->fault_wait_ns = wait_limit_ns;
+    return NEFTY_OK;
+}
+
 const char* nefty_last_error(const nefty_handle* h) {
     if (h) return h->err.c_str();
     return t_err.c_str();
@@ -1229,11 +1272,12 @@ static nefty_status field_call(nefty_handle* h, const nefty_field_desc* d, const
     cudaStream_t s = (cudaStream_t)stream;
     const size_t P = field_param_count(fd.F, fd.W, fd.depth, fd.skip);
     Input th, bw, ga;
-    th.plan(theta, P * 4);
-    bw.plan(band_weights, (size_t)fd.F * 4);
-    ga.plan(backward ? grad_alpha : nullptr, (size_t)fd.M * 4);
+    th.plan(theta, P * 4, h->device);
+    bw.plan(band_weights, (size_t)fd.F * 4, h->device);
+    ga.plan(backward ? grad_alpha : nullptr, (size_t)fd.M * 4, h->device);
     Output o;
-    o.plan(out, (backward ? P : (size_t)fd.M) * 4);
+    o.plan(out, (backward ? P : (size_t)fd.M) * 4, h->device);
+    if (nefty_status e = reject_foreign(h, th, bw, ga, o)) return e;
     char* fws = nullptr;
     const size_t fbytes = field_workspace_bytes(fd, backward);
     auto layout = [&](Arena& a) {
@@ -1276,7 +1320,9 @@ nefty_status nefty_gemm_bf16(nefty_handle* h, const void* A, int32_t lda, const 
     if (!h) return fail(nullptr, NEFTY_EINVAL, "handle is NULL");
     if (!A || !B || !C || M < 1 || N < 1 || K < 64 || K % 64 || lda % 8 || ldb % 8 || lda < K || ldb < K)
         return fail(h, NEFTY_EINVAL, "gemm: bad arguments");
-    if (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(C)) return fail(h, NEFTY_EINVAL, "gemm: device pointers only");
+    if (ptr_kind(A, h->device) != kPtrDevice || ptr_kind(B, h->device) != kPtrDevice ||
+        ptr_kind(C, h->device) != kPtrDevice)
+        return fail(h, NEFTY_EINVAL, "gemm: device pointers of the handle's GPU only");
     DeviceGuard guard(h->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (nefty_status e = ensure_workspace(h, 256)) return e;
@@ -1305,9 +1351,10 @@ nefty_status nefty_tv(nefty_handle* h, const nefty_problem* p, const void* alpha
     const size_t R = P.prec == NEFTY_FP32 ? 4 : 8, N = P.N;
     const int blocks = tv_blocks(P.N);
     Input a;
-    a.plan(alpha, N * R);
+    a.plan(alpha, N * R, h->device);
     Output g;
-    g.plan(grad_alpha_accum, N * R);
+    g.plan(grad_alpha_accum, N * R, h->device);
+    if (nefty_status e = reject_foreign(h, a, g)) return e;
     double* partials = nullptr;
     auto layout = [&](Arena& ar) {
         partials = (double*)ar.take((size_t)blocks * sizeof(double));

@@ -72,6 +72,8 @@ struct Sync {
     unsigned G;
     unsigned epoch;     // thread 0 only
     unsigned red;       // uniform
+    unsigned missing;   // arrivals that never come (fault injection; 0 normally)
+    unsigned long long wait_ns;   // barrier wait limit
 };
 
 // Bounded grid barrier: returns false on timeout or when another CTA has
@@ -84,7 +86,7 @@ __device__ bool barrier(Sync& g) {
     __syncthreads();
     if (threadIdx.x == 0) {
         g.epoch += 1;
-        const unsigned target = g.epoch * g.G;
+        const unsigned target = g.epoch * g.G + g.missing;
         red_release(&g.ctl->bar, 1u);
         int ok = 1;
         unsigned spins = 0;
@@ -94,7 +96,7 @@ __device__ bool barrier(Sync& g) {
                 if (ld_relaxed(&g.ctl->err) != kDevOk) { ok = 0; break; }
                 const unsigned long long t = now_ns();
                 if (t0 == 0) t0 = t;
-                else if (t - t0 > kBarrierTimeoutNs) {
+                else if (t - t0 > g.wait_ns) {
                     atomicCAS(&g.ctl->err, kDevOk, kDevTimeout);
                     ok = 0;
                     break;
@@ -1528,6 +1530,8 @@ __device__ __forceinline__ Sync make_sync(DevCtl* ctl, double* partials) {
     s.G = gridDim.x;
     s.epoch = 0;
     s.red = 0;
+    s.missing = ctl->missing;
+    s.wait_ns = ctl->wait_ns ? ctl->wait_ns : kBarrierTimeoutNs;
     return s;
 }
 

@@ -18,6 +18,11 @@ namespace nefty {
 constexpr int kThreads = 512;
 // Maximum number of values reduced together across the grid.
 constexpr int kMaxRed = 4;
+// Defaults of a problem's CG stop test (rtol = 0, max_iter = 0), shared by
+// every entry point.
+constexpr double kDefaultRtolFp32 = 5e-10;
+constexpr double kDefaultRtolFp64 = 1e-13;
+constexpr int kDefaultMaxIter = 1000;
 // Device-side wait limit of a grid barrier (nanoseconds of %globaltimer).
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;
 
@@ -30,7 +35,8 @@ struct DevCtl {
     unsigned int bar;      // grid-barrier arrival counter
     int err;               // DevError of the call
     int notconv;           // number of solves that hit max_iter
-    int pad;
+    unsigned int missing;  // fault injection (tests): arrivals every grid barrier waits for in vain; 0 normally
+    unsigned long long wait_ns;   // grid-barrier wait limit (%globaltimer ns); 0 = kBarrierTimeoutNs
 };
 
 // Grid geometry and the precomputed operator of A(alpha) = I - dt L(alpha).

@@ -45,18 +45,21 @@ struct Grid {
     unsigned G;
     unsigned epoch;
     unsigned red;
+    unsigned missing;              // arrivals that never come (fault injection; 0 normally)
+    unsigned long long wait_ns;    // barrier wait limit
 };
 
 // Grid-wide barrier.  Thread 0 of each CTA arrives with a release add on the
 // monotonic counter and polls it with acquire loads.  The wait is bounded:
-// after kBarrierTimeoutNs, or when another CTA has flagged an error, the CTA
+// after the launch's limit (DevCtl::wait_ns, by default kBarrierTimeoutNs),
+// or when another CTA has flagged an error, the CTA
 // records kDevTimeout and every thread returns false so the kernel can exit.
 __device__ bool grid_sync(Grid& g) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         g.epoch += 1;
-        const unsigned target = g.epoch * g.G;
+        const unsigned target = g.epoch * g.G + g.missing;
         __threadfence();
         red_release_add_u32(&g.ctl->bar, 1u);
         int ok = 1;
@@ -68,7 +71,7 @@ __device__ bool grid_sync(Grid& g) {
                 const unsigned long long t = global_ns();
                 if (t0 == 0) {
                     t0 = t;
-                } else if (t - t0 > kBarrierTimeoutNs) {
+                } else if (t - t0 > g.wait_ns) {
                     atomicCAS(&g.ctl->err, kDevOk, kDevTimeout);
                     ok = 0;
                     break;
@@ -263,6 +266,8 @@ __device__ __forceinline__ Grid make_grid(DevCtl* ctl, double* partials) {
     g.G = gridDim.x;
     g.epoch = 0;
     g.red = 0;
+    g.missing = ctl->missing;
+    g.wait_ns = ctl->wait_ns ? ctl->wait_ns : kBarrierTimeoutNs;
     return g;
 }
 

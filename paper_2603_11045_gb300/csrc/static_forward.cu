@@ -1,17 +1,18 @@
 // nefty_forward_static: the forward sweep for callers that cannot allocate
 // device memory.
 //
-// Some callers may not call cudaMalloc at the moment they need a solve: code
-// that runs while a CUDA stream is being captured into a graph in global
-// capture mode (allocation is an illegal call there), real-time or serving
-// loops that pre-reserve the whole device and must not trigger the implicit
-// synchronisation of cudaMalloc/cudaFree, and hosts that hand out device
-// memory only through their own pool.  This entry point therefore takes every
-// input and output from the caller and keeps all of its scratch (operator
-// coefficients, CG vectors, two state buffers, the grid-barrier control word,
-// reduction partials and per-step tables) in one file-scope device array of
-// kStaticScratchBytes.  The array exists on every GPU that loads the library
-// and is held until the process exits.
+// nefty_forward draws its scratch from a handle that grows with cudaMalloc.
+// Some callers cannot let that happen when they need a solve: a serving or
+// real-time loop that has already reserved the whole device for its own
+// buffers (there is nothing left to allocate), a loop that cannot take the
+// device-wide synchronisation that cudaMalloc and cudaFree may imply, or a
+// host application or plug-in framework that hands out device memory only
+// from its own pool and forbids the library to call the CUDA allocator.
+// This entry point takes every input and output from the caller and keeps all
+// of its scratch (operator coefficients, CG vectors, two state buffers, the
+// grid-barrier control word, reduction partials and per-step tables) in one
+// file-scope device array of kStaticScratchBytes.  The array exists on every
+// GPU that loads the library and is held until the process exits.
 //
 // The persistent PCG forward kernel and the coefficient kernel are the ones
 // nefty_forward launches for FP64 problems (solver.cu); only where their scratch
@@ -52,14 +53,18 @@ __global__ void static_tables_kernel(Real** src, Real** dst, const Real* t0, Rea
     }
 }
 
-bool on_device(const void* p) {
+// True when the kernels on `dev` may read p in place: NULL, device memory of
+// `dev` itself or managed memory.  Host memory and device memory of another
+// GPU are refused (no staging buffer can be allocated here).
+bool on_device(const void* p, int dev) {
     if (!p) return true;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 nefty_status fail(nefty_status s, const std::string& m) {
@@ -161,9 +166,9 @@ nefty_status run(int dev, char* base, const nefty_problem& p, const void* alpha,
     a.obs_off = p.obs_face ? (unsigned)(p.nz - 1) * (unsigned)S : 0u;
     a.obs = loss_out ? (const Real*)obs : nullptr;
     a.frames = (Real*)frames_out;
-    const double rtol = p.rtol > 0 ? p.rtol : (p.prec == NEFTY_FP32 ? 1e-9 : 1e-13);
+    const double rtol = p.rtol > 0 ? p.rtol : (p.prec == NEFTY_FP32 ? kDefaultRtolFp32 : kDefaultRtolFp64);
     a.tol2 = rtol * rtol;
-    a.max_iter = p.max_iter > 0 ? p.max_iter : 1000;
+    a.max_iter = p.max_iter > 0 ? p.max_iter : kDefaultMaxIter;
     a.ctl = ctl;
     a.partials = partials;
     a.iters = iters;
@@ -211,9 +216,11 @@ extern "C" nefty_status nefty_forward_static(int device, const nefty_problem* p,
     }
     nefty_status st = NEFTY_OK;
     void* base = nullptr;
-    if (!on_device(alpha) || !on_device(T0) || !on_device(q_face) || !on_device(frames_out) ||
-        !on_device(T_final) || !on_device(obs)) {
-        st = fail(NEFTY_EINVAL, "every array must be device memory (host arrays would need staging buffers)");
+    if (!on_device(alpha, device) || !on_device(T0, device) || !on_device(q_face, device) ||
+        !on_device(frames_out, device) || !on_device(T_final, device) || !on_device(obs, device)) {
+        st = fail(NEFTY_EINVAL,
+                  "every array must be device memory of the requested device (host arrays would need staging "
+                  "buffers)");
     } else if ((st = setup(device, &base)) == NEFTY_OK) {
         cudaStream_t s = (cudaStream_t)stream;
         st = p->prec == NEFTY_FP32

@@ -93,3 +93,9 @@ def test_create_without_device_fails_cleanly(lib):
 def test_status_strings(lib):
     assert lib.nefty_status_string(0) == b"NEFTY_OK"
     assert lib.nefty_status_string(3) == b"NEFTY_ENOTCONV"
+
+
+def test_debug_barrier_fault_needs_a_handle(lib):
+    """The fault-injection hook validates its handle on the host (no device work)."""
+    assert lib.nefty_debug_barrier_fault(None, 1, 0) == 1   # NEFTY_EINVAL
+    assert b"handle" in lib.nefty_last_error(None)

@@ -496,3 +496,32 @@ def test_jacobi_k_paper_grid_matches_oracle(solver, orc, prec):
     gg = g["grad_alpha"].cpu().numpy()
     assert rel_l2(gg, ref["grad_alpha"]) <= gtol and cosine(gg, ref["grad_alpha"]) >= 0.9999
     assert g["loss"] == pytest.approx(ref["loss"], rel=1e-9 if prec == "fp64" else 1e-4)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_grid_barrier_timeout_is_reported_and_the_handle_recovers(prec):
+    """A grid barrier that waits for an arrival that never comes (fault
+    injection: one CTA more than the launch has) gives up after its limit
+    (50 ms here): the call returns NEFTY_ETIMEOUT, no kernel is left running
+    (the device synchronises), and the next normal call on the same handle
+    returns the same bits as before the fault, forward and adjoint."""
+    from paper_2603_11045_gb300.solver import Problem, Solver
+    from paper_2603_11045_gb300._native import NeftyError, NEFTY_ETIMEOUT
+    w = S.inclusion_case(nx=64, ny=48, nz=12, nt=12, seed=1040)
+    prob = Problem.from_workload(w, prec=prec)
+    a, q = dev(w.alpha, prec), dev(w.q_face, prec)
+    with Solver(0) as s:
+        obs = s.forward(prob, dev(w.alpha_target, prec), q_face=q, q_steps=3)["frames"]
+        ref = s.adjoint_grad(prob, a, obs, q_face=q, q_steps=3)
+        assert s._lib.nefty_debug_barrier_fault(s._h, 1, 50_000_000) == 0
+        for call in (lambda: s.forward(prob, a, q_face=q, q_steps=3),
+                     lambda: s.adjoint_grad(prob, a, obs, q_face=q, q_steps=3)):
+            with pytest.raises(NeftyError) as e:
+                call()
+            assert e.value.status == NEFTY_ETIMEOUT
+            assert "timed out" in str(e.value)
+            torch.cuda.synchronize()
+        assert s._lib.nefty_debug_barrier_fault(s._h, 0, 0) == 0
+        again = s.adjoint_grad(prob, a, obs, q_face=q, q_steps=3)
+        assert torch.equal(again["grad_alpha"], ref["grad_alpha"]) and again["loss"] == ref["loss"]
+        assert s._lib.nefty_debug_barrier_fault(s._h, 2000, 0) != 0   # beyond the documented limit
