@@ -37,8 +37,14 @@ def annealing_weights(F, beta):
     return 0.5 * (1.0 - torch.cos(math.pi * torch.clamp(beta - k, 0.0, 1.0)))
 
 
-def cell_centres(nx, ny, nz):
-    """[N, 3] normalised centres in the cell order c = (k ny + j) nx + i."""
+def cell_centres(nx, ny, nz, cells=None):
+    """[N, 3] normalised centres in the cell order c = (k ny + j) nx + i, or,
+    with ``cells`` (flat cell indices c), the centres of those cells only."""
+    if cells is not None:
+        c = torch.as_tensor(cells, dtype=torch.int64)
+        i, j, k = c % nx, (c // nx) % ny, c // (nx * ny)
+        return torch.stack([2.0 * (t.to(torch.float64) + 0.5) / n - 1.0 for t, n in ((i, nx), (j, ny), (k, nz))],
+                           dim=1)
     axes = [2.0 * (torch.arange(n, dtype=torch.float64) + 0.5) / n - 1.0 for n in (nx, ny, nz)]
     z, y, x = torch.meshgrid(axes[2], axes[1], axes[0], indexing="ij")
     return torch.stack([x.reshape(-1), y.reshape(-1), z.reshape(-1)], dim=1)
@@ -81,12 +87,13 @@ def _bf16(t):
 
 
 def field(theta, nx, ny, nz, F, W, depth, freq_lo, freq_hi, alpha_min, alpha_max, band_weights=None, bf16=False,
-          skip=0):
-    """alpha at every cell centre, [nz, ny, nx] (differentiable in theta).
+          skip=0, cells=None):
+    """alpha at every cell centre, [nz, ny, nx] (differentiable in theta), or
+    at the given flat cell indices only ([len(cells)]).
     skip > 0: the encoding is concatenated to the input of hidden layer `skip`
     (App. D.1, the re-injection at the middle layer)."""
     layers, w_out, b_out = unpack(theta, F, W, depth, skip)
-    gamma = encode(cell_centres(nx, ny, nz), F, freq_lo, freq_hi, band_weights)
+    gamma = encode(cell_centres(nx, ny, nz, cells), F, freq_lo, freq_hi, band_weights)
     if bf16:
         gamma = _bf16(gamma)
     h = gamma
@@ -97,4 +104,5 @@ def field(theta, nx, ny, nz, F, W, depth, freq_lo, freq_hi, alpha_min, alpha_max
         if bf16:
             h = _bf16(h)
     f = h @ w_out + b_out
-    return (alpha_min + (alpha_max - alpha_min) * torch.sigmoid(f)).reshape(nz, ny, nx)
+    alpha = alpha_min + (alpha_max - alpha_min) * torch.sigmoid(f)
+    return alpha if cells is not None else alpha.reshape(nz, ny, nx)

@@ -151,3 +151,24 @@ def test_skip_field_gradient_finite_differences(F):
         fd = ((F.field(tp, 4, 3, 2, Fq, W, depth, 1.0, 8.0, 0.01, 2.0, skip=s) * g_a).sum()
               - (F.field(tm, 4, 3, 2, Fq, W, depth, 1.0, 8.0, 0.01, 2.0, skip=s) * g_a).sum()) / (2 * e)
         assert float(th.grad[i]) == pytest.approx(float(fd), rel=1e-6, abs=1e-9)
+
+
+def test_field_at_chosen_cells_is_the_full_field_there(F):
+    """Evaluating at a list of flat cell indices c = (k ny + j) nx + i gives the
+    centre 2 (i + 1/2) / n - 1 per axis (checked by hand on three cells) and
+    the full field's values at those cells, bit for bit."""
+    nx, ny, nz = 7, 5, 3
+    cells = torch.tensor([0, nx * ny * nz - 1, (2 * ny + 3) * nx + 4])
+    OF = F
+    X = OF.cell_centres(nx, ny, nz, cells)
+    want = torch.tensor([[1 / 7 - 1, 1 / 5 - 1, 1 / 3 - 1], [13 / 7 - 1, 9 / 5 - 1, 5 / 3 - 1],
+                         [9 / 7 - 1, 7 / 5 - 1, 5 / 3 - 1]], dtype=torch.float64)
+    assert torch.allclose(X, want, rtol=0, atol=1e-15)
+    nf, W, depth = 3, 8, 2
+    th = torch.tensor(S.rng(31).standard_normal(OF.param_count(nf, W, depth)) * 0.5)
+    args = (nx, ny, nz, nf, W, depth, math.pi, 4 * math.pi, 0.01, 2.0)
+    full = OF.field(th, *args).reshape(-1)
+    some = torch.tensor(S.rng(32).choice(nx * ny * nz, 20, replace=False))
+    for bf16 in (False, True):
+        full = OF.field(th, *args, bf16=bf16).reshape(-1)
+        assert torch.equal(OF.field(th, *args, bf16=bf16, cells=some), full[some])
