@@ -37,25 +37,44 @@ import numpy as np  # noqa: E402
 
 METRIC = "fwd+adjoint Gcell-steps/s"
 UNIT = "Gcell-steps/s"
-# Algorithmic bytes of one fused Jacobi-PCG iteration per cell (FP32 path):
-# read + write of x, r, p (24 B) and a read of the three face values plus the
-# Jacobi diagonal (16 B); per time step one right-hand-side read and one
-# solution write (8 B).  FP64 doubles both.
-ALG_BYTES_ITER = {"fp32": 40, "fp64": 80}
+# Algorithmic bytes per cell.  The FP32 path reads alpha and recomputes the
+# face values in every pass: one PCG iteration reads and writes x, r, p (24 B)
+# and reads alpha (4 B).  The FP64 path reads three stored face values and the
+# Jacobi diagonal instead, all words 8 B (48 + 32 B).  Each time step also
+# reads its right-hand side and writes its solution (8 B, FP64 16 B), and each
+# adjoint step's gradient assembly reads T^n and updates an FP64 accumulator
+# (4 + 16 B, FP64 8 + 16 B).
+ALG_BYTES_ITER = {"fp32": 28, "fp64": 80}
 ALG_BYTES_STEP = {"fp32": 8, "fp64": 16}
+ALG_BYTES_GRAD = {"fp32": 20, "fp64": 24}
 # DRAM bytes per cell per solver pass of the FP32 CG kernels, from one ncu
-# capture of each sweep on the 256x256x48 grid (20 steps): forward and
-# recompute launches, and the reverse sweep with the gradient.  Scaled to the
-# timed launches by their pass counts (CG iterations plus the
-# init/finalise/gradient passes of each solve).  None = no capture of the
-# current kernels.
-DRAM_BYTES_PER_CELL_PASS = {"fp32": {"fwd": 24.2, "adj": 25.6}, "fp64": None}
+# capture of each sweep on the 256x256x48 grid (20 steps): the forward sweep
+# and the reverse sweep with the gradient, with the fixed passes per solve of
+# those kernels.  bench.py scales them to the timed launches by their pass
+# counts (CG iterations plus the fixed passes) as an ESTIMATE of the timed
+# traffic, and only while the kernel source still hashes to the captured one:
+# once the kernels change the figure is stale and `traffic` is null.
+DRAM_CAPTURE = {
+    "fp32": {"fwd": 24.2, "adj": 25.6, "fixed_passes_fwd": 3, "fixed_passes_adj": 4,
+             "kernel_source": "paper_2603_11045_gb300/csrc/cg_tiled.cu", "kernel_sha16": "8d5cbc83a361e42e",
+             "profiles": ["profiles/forward_tiled_256x256x48_nt20_ncu.md",
+                          "profiles/adjoint_tiled_256x256x48_nt20_ncu.md"]},
+    "fp64": None,
+}
+KERNELS = {"fp32": "tiled::forward_tiled + tiled::adjoint_tiled (persistent single-reduction Jacobi-PCG, TMA-staged)",
+           "fp64": "nefty::forward_kernel + nefty::adjoint_kernel (persistent Jacobi-PCG, FP64)"}
+
+
+def source_sha16(rel_path):
+    import hashlib
+    with open(os.path.join(ROOT, rel_path), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--nx", type=int, default=256)
@@ -68,6 +87,8 @@ def parse():
                     help="FP32 CG start: increments extrapolated from (0 = the library default, -1 = none)")
     ap.add_argument("--cpu-sample-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-error", action="store_true",
+                    help="skip the FP32-vs-FP64 error of the timed configuration (run after timing)")
     ap.add_argument("--paper-iters", type=int, default=300, help="paper-inversion: Adam iterations")
     ap.add_argument("--paper-jacobi-k", type=int, default=50,
                     help="paper-inversion: Jacobi sweeps per solve (the paper's 50; 0 = converged Jacobi-PCG)")
@@ -355,21 +376,36 @@ def run_native(args):
     cg_ms = sum(s["fwd_ms"] + s["adj_ms"] + s["recompute_ms"] for s in stats) / len(stats)
     launches = stats[0]["kernel_launches"]
     iters = sum(s["fwd_iters"] + s["adj_iters"] + s["recompute_iters"] for s in stats) / len(stats)
-    steps_solved = stats[0]["fwd_steps"] + stats[0]["adj_steps"] + stats[0]["recompute_steps"]
-    alg_bytes = w.n_cells * (iters * ALG_BYTES_ITER[R] + steps_solved * ALG_BYTES_STEP[R])
+    st0 = stats[0]
+    steps_solved = st0["fwd_steps"] + st0["adj_steps"] + st0["recompute_steps"]
+    alg_bytes = w.n_cells * (iters * ALG_BYTES_ITER[R] + steps_solved * ALG_BYTES_STEP[R]
+                             + st0["adj_steps"] * ALG_BYTES_GRAD[R])
     pk = peaks()
     peak = pk["hbm_gbs"] if pk else 6800.0
     achieved = alg_bytes / (cg_ms / 1000.0) / 1e9
-    st0 = stats[0]
     fwd_iters = sum(s["fwd_iters"] + s["recompute_iters"] for s in stats) / len(stats)
     adj_iters = sum(s["adj_iters"] for s in stats) / len(stats)
-    fwd_passes = fwd_iters + 3 * (st0["fwd_steps"] + st0["recompute_steps"])
-    adj_passes = adj_iters + 4 * st0["adj_steps"]
-    bpp = DRAM_BYTES_PER_CELL_PASS[R]
-    traffic = None if bpp is None else w.n_cells * (bpp["fwd"] * fwd_passes + bpp["adj"] * adj_passes)
+    cap = DRAM_CAPTURE[R]
+    traffic, traffic_note = None, "no ncu capture of these kernels"
+    if cap is not None:
+        if source_sha16(cap["kernel_source"]) != cap["kernel_sha16"]:
+            traffic_note = "stale: the kernel source changed since the ncu capture"
+        else:
+            fwd_passes = fwd_iters + cap["fixed_passes_fwd"] * (st0["fwd_steps"] + st0["recompute_steps"])
+            adj_passes = adj_iters + cap["fixed_passes_adj"] * st0["adj_steps"]
+            traffic = w.n_cells * (cap["fwd"] * fwd_passes + cap["adj"] * adj_passes)
+            traffic_note = ("estimate: DRAM bytes per cell-pass of one ncu capture per sweep (" +
+                            ", ".join(cap["profiles"]) + "), scaled by the timed step's solver passes")
+    dram_gbs = None if traffic is None else traffic / (cg_ms / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "traffic_note": "DRAM bytes per step, ncu capture scaled by solver passes", "kernel": "persistent fused Jacobi-PCG (forward_kernel + adjoint_kernel)",
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback",
+                "traffic": traffic, "traffic_note": traffic_note,
+                "dram_gbs": dram_gbs, "dram_frac": None if dram_gbs is None else dram_gbs / peak,
+                "kernel": KERNELS[R],
+                "peak_source": ("of measured: MEASURED_PEAKS.json hbm_gbs (burst copy)" if pk
+                                else "of fallback: 6.8 TB/s"),
+                "alg_bytes_note": (f"{ALG_BYTES_ITER[R]} B per cell per CG iteration, {ALG_BYTES_STEP[R]} B per "
+                                   f"cell per solved step, {ALG_BYTES_GRAD[R]} B per cell per adjoint step "
+                                   "(gradient assembly)"),
                 "cg_ms_per_step": cg_ms, "alg_bytes_per_step": alg_bytes,
                 "mean_cg_iters_per_solve": iters / max(1, steps_solved)}
 
@@ -382,6 +418,33 @@ def run_native(args):
                     "peak_source": "measured sustained bf16 (MEASURED_PEAKS.json)" if pk else "fallback",
                     "field_eval_ms": f_fwd_ms, "field_backward_ms": f_bwd_ms,
                     "flops_per_step": fwd_fl + bwd_fl}
+
+    # error of the timed configuration against the FP64 GPU path, outside the
+    # timed region: the same alpha (the field's output of theta), targets and
+    # flux through the FP32 path as timed and through the FP64 path (rtol
+    # 1e-13); surface frames, loss and dJ/dalpha (before the TV term)
+    error = None
+    if R == "fp32" and not args.no_error:
+        a32 = alpha.clone()
+        p64 = prob.with_(prec="fp64", rtol=0.0, extrap=0)
+        f32 = solver.forward(prob, a32, q_face=q, q_steps=w.q_steps, obs=obs)
+        g32 = solver.adjoint_grad(prob, a32, obs, q_face=q, q_steps=w.q_steps)
+        a64, q64, o64 = a32.double(), q.double(), obs.double()
+        f64 = solver.forward(p64, a64, q_face=q64, q_steps=w.q_steps, obs=o64)
+        g64 = solver.adjoint_grad(p64, a64, o64, q_face=q64, q_steps=w.q_steps)
+
+        def rel(x, y):
+            return float((x.double() - y).norm() / y.norm())
+
+        gx, gy = g32["grad_alpha"].double().flatten(), g64["grad_alpha"].flatten()
+        error = {"against": "FP64 GPU path (rtol 1e-13) on the same alpha, targets and flux",
+                 "surface_rel_l2": rel(f32["frames"], f64["frames"]),
+                 "loss_rel": abs(f32["loss"] - f64["loss"]) / abs(f64["loss"]),
+                 "grad_alpha_rel_l2": rel(gx, gy),
+                 "grad_alpha_cosine": float(gx @ gy / (gx.norm() * gy.norm())),
+                 "bars": {"surface_rel_l2": 1e-5, "grad_alpha_rel_l2": 1e-3, "grad_alpha_cosine": 0.9999}}
+        del f32, g32, f64, g64, a64, q64, o64, gx, gy, a32
+        torch.cuda.empty_cache()
 
     # end to end through the C ABI with host buffers (pinned): theta, targets
     # and flux go in, dJ/dtheta and the loss come back, copies inside
@@ -418,6 +481,9 @@ def run_native(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if R == "fp32" else "f64",
                 "data": "synthetic", "config": config_dict(args, w), "parallelism": f"replicas x{world}",
                 "gpu_launches": launches * args.steps + field_launches(spec) * args.steps, "e2e": e2e,
+                "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                               "max": float(max(step_ms)), "per": "inversion step (device time, CUDA events)"},
+                "error": error,
                 "roofline": roofline, "roofline_field": roofline_mlp,
                 "cpu_baseline": cpu, "clocks": clk,
                 "solver_stats": {k: stats[-1][k] for k in ("fwd_iters", "adj_iters", "recompute_iters",
