@@ -185,8 +185,8 @@ nefty_status nefty_adjoint_grad(nefty_handle *h, const nefty_problem *p, const v
  * ReLU layers of `width` units and a linear output f; alpha = alpha_min + (alpha_max - alpha_min)
  * * sigmoid(f) (Eq. bracket).  With skip_layer = s > 0 the encoding is re-injected at hidden
  * layer s (App. D.1): its input is [h_s, features] (width + 6 n_freq values).  Dense layers run
- * in BF16 on the tensor cores with FP32 accumulation; features, head, biases and gradients are
- * FP32.
+ * on the tensor cores with BF16 operands (or split BF16 operands, see `precision`) and FP32
+ * accumulation; features, head, biases and gradients are FP32.
  * Parameter vector (FP32, packed): W_0 [width x 6 n_freq], b_0 [width], then W_l [width x in_l],
  * b_l [width] for l = 1 .. depth-1 (in_l = width + 6 n_freq for l = skip_layer, else width),
  * then w_out [width], b_out [1]; weights row-major [out][in].
@@ -202,7 +202,11 @@ typedef struct {
     double freq_lo, freq_hi;
     double alpha_min, alpha_max;
     int32_t skip_layer;     /* 0 = none; s = 1 .. depth-1: the encoding joins the input of layer s */
-    int32_t reserved;       /* 0 */
+    int32_t precision;      /* 0 = BF16 operands (default); 1 = split BF16: every weight, activation
+                               and back-propagated delta v is held as hi = bf16(v) plus
+                               lo = bf16(v - hi) (about 16 significant bits) and every product
+                               takes the three tensor-core products hi*hi + hi*lo + lo*hi into the
+                               same FP32 accumulator: 3x the tensor work and activation memory */
 } nefty_field_desc;
 
 /* Number of FP32 parameters of the packed vector for `d` (0 if d is invalid). */

@@ -34,7 +34,7 @@ class nefty_field_desc(ctypes.Structure):
                 ("n_freq", ctypes.c_int32), ("width", ctypes.c_int32), ("depth", ctypes.c_int32),
                 ("freq_lo", ctypes.c_double), ("freq_hi", ctypes.c_double),
                 ("alpha_min", ctypes.c_double), ("alpha_max", ctypes.c_double),
-                ("skip_layer", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("skip_layer", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
 class nefty_stats(ctypes.Structure):

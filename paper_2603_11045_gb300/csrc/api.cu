@@ -1210,7 +1210,7 @@ bool field_dims(const nefty_field_desc* d, FieldDims* out, std::string* why) {
         *why = "skip_layer must be 0 (none) or a hidden layer 1..depth-1";
         return false;
     }
-    if (d->reserved != 0) { *why = "reserved must be 0"; return false; }
+    if (d->precision != 0 && d->precision != 1) { *why = "precision must be 0 (BF16) or 1 (split BF16)"; return false; }
     if (!(d->freq_lo > 0) || !(d->freq_hi >= d->freq_lo) || !std::isfinite(d->freq_hi)) {
         *why = "need 0 < freq_lo <= freq_hi";
         return false;
@@ -1226,6 +1226,7 @@ bool field_dims(const nefty_field_desc* d, FieldDims* out, std::string* why) {
         out->F = d->n_freq; out->W = d->width; out->depth = d->depth;
         out->skip = d->skip_layer;
         out->Dp = (6 * d->n_freq + 63) / 64 * 64;
+        out->ns = d->precision == 1 ? 3 : 1;
         out->freq_lo = d->freq_lo; out->freq_hi = d->freq_hi;
         out->alpha_min = d->alpha_min; out->alpha_max = d->alpha_max;
         // split-K of the weight-gradient GEMMs: one CTA per SM (per layer, see

@@ -281,6 +281,7 @@ struct FieldDims {
     int F, W, depth;         // bands per axis, hidden width, hidden layers
     int skip;                // hidden layer whose input is [h | gamma(x)] (0 = none)
     int Dp;                  // 6F rounded up to a multiple of 64 (zero-padded feature columns)
+    int ns;                  // BF16 blocks per stored value: 1 (BF16) or 3 (split BF16, see field.cu)
     double freq_lo, freq_hi, alpha_min, alpha_max;
     int sms;                 // SMs of the device (split-K sizing)
     int splits;              // largest split-K factor of the weight-gradient GEMMs
@@ -295,11 +296,16 @@ cudaError_t field_backward(const FieldDims& d, const float* theta, const float* 
 int field_error(const FieldDims& d, char* ws, cudaStream_t s, bool backward);
 // tcgen05 BF16 GEMM (umma_gemm.cu): D = A B^T, epi 0 bias+relu->bf16, 1 mask->bf16, 2 fp32 split partials;
 // the BF16 epilogues can also write D^T [N x ldt] (out_t); the mask has leading
-// dimension ldm (0 = ldo).
+// dimension ldm (0 = ldo).  Split BF16 outputs (so, tso > 0): each value as
+// hi = bf16(v), lo = bf16(v - hi), written [hi | hi | lo] at column offsets
+// 0, so, 2 so of out_bf16 and at 0, tso, 2 tso of out_t ([hi | lo | hi] when
+// t_order = 1): the operand layouts of a K-concatenated split product
+// [Ah | Ah | Al] [Bh | Bl | Bh]^T = Ah Bh^T + Ah Bl^T + Al Bh^T.
 cudaError_t umma_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
                       int epi, const float* bias, const __nv_bfloat16* mask, __nv_bfloat16* out_bf16,
                       float* out_f32, int ldo, int splits, int* err, cudaStream_t s,
-                      __nv_bfloat16* out_t = nullptr, int ldt = 0, int ldm = 0);
+                      __nv_bfloat16* out_t = nullptr, int ldt = 0, int ldm = 0, int so = 0, int tso = 0,
+                      int t_order = 0);
 
 int tiled_grid_blocks(int device);
 // Shared memory (bytes) the tiled kernels request dynamically.

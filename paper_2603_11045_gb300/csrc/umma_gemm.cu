@@ -113,6 +113,11 @@ struct Args {
     int ldt;
     int n_tiles;                 // output tiles along N
     int* err;
+    // Split BF16 outputs (0 = plain): a value v is written as hi = bf16(v) and
+    // lo = bf16(v - hi).  out_bf16 gets [hi | hi | lo] at column offsets 0,
+    // so, 2 so; out_t gets three blocks at column offsets 0, tso, 2 tso in the
+    // order [hi | hi | lo] (t_order 0) or [hi | lo | hi] (t_order 1).
+    int so, tso, t_order;
 };
 
 template <int STAGES>
@@ -226,6 +231,7 @@ gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
                                              __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
                 } else {
                     uint32_t mk[16];
+                    float xs[32];   // the values before rounding (split outputs)
                     if (a.epi == kEpiMaskBf16) {
                         const uint4* src = reinterpret_cast<const uint4*>(a.mask + (size_t)row * a.ldm + cb);
 #pragma unroll
@@ -248,16 +254,43 @@ gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
                         }
                         const __nv_bfloat162 b2 = __floats2bfloat162_rn(x0, x1);
                         pk[t] = *reinterpret_cast<const uint32_t*>(&b2);
+                        xs[2 * t] = x0;
+                        xs[2 * t + 1] = x1;
+                    }
+                    uint32_t pl[16];   // lo parts of a split output
+                    if (a.so || a.tso) {
+#pragma unroll
+                        for (int t = 0; t < 16; ++t) {
+                            const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&pk[t]);
+                            const __nv_bfloat162 l2 = __floats2bfloat162_rn(xs[2 * t] - __low2float(h2),
+                                                                            xs[2 * t + 1] - __high2float(h2));
+                            pl[t] = *reinterpret_cast<const uint32_t*>(&l2);
+                        }
                     }
                     uint4* dst = reinterpret_cast<uint4*>(a.out_bf16 + o);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
-                    if (a.out_t) {   // the warp's 32 rows of one column are 64 contiguous bytes of D^T
-                        unsigned short* dt = reinterpret_cast<unsigned short*>(a.out_t) + (size_t)cb * a.ldt + row;
+                    if (a.so) {
+                        uint4* d1 = reinterpret_cast<uint4*>(a.out_bf16 + o + a.so);
+                        uint4* d2 = reinterpret_cast<uint4*>(a.out_bf16 + o + 2 * (size_t)a.so);
 #pragma unroll
-                        for (int t = 0; t < 16; ++t) {
-                            dt[(size_t)(2 * t) * a.ldt] = (unsigned short)(pk[t] & 0xFFFFu);
-                            dt[(size_t)(2 * t + 1) * a.ldt] = (unsigned short)(pk[t] >> 16);
+                        for (int q = 0; q < 4; ++q) {
+                            d1[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+                            d2[q] = make_uint4(pl[4 * q], pl[4 * q + 1], pl[4 * q + 2], pl[4 * q + 3]);
+                        }
+                    }
+                    if (a.out_t) {   // the warp's 32 rows of one column are 64 contiguous bytes of D^T
+                        const int nb = a.tso ? 3 : 1;
+                        for (int b = 0; b < nb; ++b) {
+                            const bool lo = b == (a.t_order == 0 ? 2 : 1);
+                            const uint32_t* src = lo ? pl : pk;
+                            unsigned short* dt = reinterpret_cast<unsigned short*>(a.out_t) + (size_t)cb * a.ldt +
+                                                 (size_t)b * a.tso + row;
+#pragma unroll
+                            for (int t = 0; t < 16; ++t) {
+                                dt[(size_t)(2 * t) * a.ldt] = (unsigned short)(src[t] & 0xFFFFu);
+                                dt[(size_t)(2 * t + 1) * a.ldt] = (unsigned short)(src[t] >> 16);
+                            }
                         }
                     }
                 }
@@ -275,7 +308,21 @@ gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
                                                           __bfloat162float(a.mask[(size_t)row * a.ldm + col]) > 0.f
                                                               ? acc : 0.f);
                         a.out_bf16[e] = r;
-                        if (a.out_t) a.out_t[(size_t)col * a.ldt + row] = r;
+                        const float xv = a.epi == kEpiBiasReluBf16
+                                             ? fmaxf(acc + a.bias[col], 0.f)
+                                             : (__bfloat162float(a.mask[(size_t)row * a.ldm + col]) > 0.f ? acc : 0.f);
+                        const __nv_bfloat16 rl = __float2bfloat16_rn(xv - __bfloat162float(r));
+                        if (a.so) {
+                            a.out_bf16[e + a.so] = r;
+                            a.out_bf16[e + 2 * (size_t)a.so] = rl;
+                        }
+                        if (a.out_t) {
+                            const int nb = a.tso ? 3 : 1;
+                            for (int b = 0; b < nb; ++b) {
+                                const bool lo = b == (a.t_order == 0 ? 2 : 1);
+                                a.out_t[(size_t)col * a.ldt + (size_t)b * a.tso + row] = lo ? rl : r;
+                            }
+                        }
                     } else {
                         a.out_f32[(size_t)blockIdx.z * a.M * a.ldo + e] = acc;
                     }
@@ -332,7 +379,7 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld) {
 cudaError_t umma_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
                       int epi, const float* bias, const __nv_bfloat16* mask, __nv_bfloat16* out_bf16,
                       float* out_f32, int ldo, int splits, int* err, cudaStream_t s, __nv_bfloat16* out_t, int ldt,
-                      int ldm) {
+                      int ldm, int so, int tso, int t_order) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(umma::gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -345,6 +392,8 @@ cudaError_t umma_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, i
     }
     if (K % umma::BK != 0 || lda % 8 != 0 || ldb % 8 != 0 || splits < 1) return cudaErrorInvalidValue;
     if (out_t && (epi == umma::kEpiF32 || ldt < M)) return cudaErrorInvalidValue;
+    if ((so || tso) && epi == umma::kEpiF32) return cudaErrorInvalidValue;
+    if (so < 0 || so % 8 != 0 || tso < 0 || (tso && (tso < M || ldt < 2 * tso + M))) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
     if (!make_map(&ma, A, M, K, lda) || !make_map(&mb, B, N, K, ldb)) return cudaErrorInvalidValue;
     umma::Args a;
@@ -356,6 +405,9 @@ cudaError_t umma_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, i
     a.ldm = ldm > 0 ? ldm : ldo;
     a.out_t = out_t;
     a.ldt = ldt;
+    a.so = so;
+    a.tso = out_t ? tso : 0;
+    a.t_order = t_order;
     auto al16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
     a.vec = (epi == umma::kEpiF32 ? (ldo % 4 == 0 && al16(out_f32))
                                   : (ldo % 8 == 0 && al16(out_bf16) &&

@@ -36,16 +36,19 @@ class FieldSpec:
     alpha_min: float = 0.01
     alpha_max: float = 2.0
     skip_layer: int = 0
+    precision: int = 0      # 0: BF16 operands; 1: split BF16 (hi + lo, three products each)
 
     @classmethod
-    def paper(cls, nx: int, ny: int, nz: int, alpha_min: float = 0.003, alpha_max: float = 0.25) -> "FieldSpec":
+    def paper(cls, nx: int, ny: int, nz: int, alpha_min: float = 0.003, alpha_max: float = 0.25,
+              precision: int = 0) -> "FieldSpec":
         """The paper's field (App. D.4): 12 bands 2^k pi, 10 x 512, skip at layer 4."""
         return cls(nx, ny, nz, n_freq=12, width=512, depth=10, freq_lo=math.pi, freq_hi=2.0 ** 11 * math.pi,
-                   alpha_min=alpha_min, alpha_max=alpha_max, skip_layer=4)
+                   alpha_min=alpha_min, alpha_max=alpha_max, skip_layer=4, precision=precision)
 
     def to_c(self) -> N.nefty_field_desc:
         return N.nefty_field_desc(self.nx, self.ny, self.nz, self.n_freq, self.width, self.depth,
-                                  self.freq_lo, self.freq_hi, self.alpha_min, self.alpha_max, self.skip_layer, 0)
+                                  self.freq_lo, self.freq_hi, self.alpha_min, self.alpha_max, self.skip_layer,
+                                  self.precision)
 
     @property
     def n_params(self) -> int:
