@@ -118,6 +118,9 @@ typedef struct {
     double fwd_ms;              /* device time of the forward-sweep launches (CUDA events) */
     double recompute_ms;        /* device time of the checkpoint-recompute launches */
     double adj_ms;              /* device time of the adjoint-sweep launches */
+    int32_t tma_staged;         /* 1: the FP32 sweeps ran on the TMA-staged kernels (nx % 4 == 0, either
+                                   wall setting); 0: plain global loads (nx % 4 != 0) or the FP64 path */
+    int32_t reserved;           /* 0 */
 } nefty_stats;
 
 typedef struct nefty_handle nefty_handle;
@@ -288,11 +291,11 @@ nefty_status nefty_forward_static(int device, const nefty_problem *p, const void
  * job that cannot fit even then is refused at submit with NEFTY_ENOMEM.
  *
  * Batched (the default): the FP32 sweeps of all running jobs whose grids have
- * zero-flux walls and nx % 4 == 0 run together in ONE persistent launch over
+ * nx % 4 == 0 (either wall setting) run together in ONE persistent launch over
  * the whole device, whatever their grid sizes and step counts; each sweep is
  * cut into chunks (chunk_steps), and a launch carries the next
  * chunk of every running job, so a newly admitted job joins the launch that
- * follows.  Other sweeps (FP64, periodic walls, nx % 4 != 0) and unbatched
+ * follows.  Other sweeps (FP64, nx % 4 != 0, Jacobi-K) and unbatched
  * servers (batched = -1) run each lane's own persistent grid on 1 / lanes of
  * the SMs, resident beside the others.  Either way a job's results depend only
  * on the job and the server's configuration: the same bits alone or among

@@ -252,9 +252,10 @@ int grid_for(nefty_handle* h, int prec, unsigned N) {
     return (int)std::min<long>(want, gmax);
 }
 
-// Whether the tiled kernels stage this problem through TMA (zero-flux walls,
-// 16-byte row pitch); the encoder may still refuse (see prepare_tma).
-bool tma_grid(const Prob& P) { return P.bc == NEFTY_BC_NEUMANN && P.nx % 4 == 0; }
+// Whether the tiled kernels stage this problem through TMA (16-byte row
+// pitch; zero-flux or periodic lateral walls); the encoder may still refuse
+// (see prepare_tma).
+bool tma_grid(const Prob& P) { return P.nx % 4 == 0; }
 
 int grid_for_tiled(nefty_handle* h, const Prob& P) {
     if (h->grid_tiled == 0) h->grid_tiled = tiled_grid_blocks(h->device);
@@ -374,8 +375,8 @@ struct Call {
         return NEFTY_OK;
     }
 
-    // TMA-staged iterations serve zero-flux lateral walls with a 16-byte row
-    // pitch; other grids take the plain-load pass.
+    // TMA-staged passes serve grids with a 16-byte row pitch (either wall
+    // setting); other grids take the plain-load pass.
     bool use_tma = false;
     nefty_status prepare_tma() {
         if constexpr (kTiled) {
@@ -635,6 +636,7 @@ struct Call {
             st->workspace_bytes = h->ws_bytes;
             st->grid_blocks = G;
             st->kernel_launches = launches;
+            st->tma_staged = use_tma ? 1 : 0;
             double ms[3] = {0.0, 0.0, 0.0};
             for (auto& t : timed) {
                 float v = 0.f;

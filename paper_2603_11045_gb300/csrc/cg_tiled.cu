@@ -24,7 +24,8 @@
 // again from the staged values with the same fused multiply-adds as the
 // cell's owner, so every thread sees the same bits.  The passes that run once
 // per solve (initial residual, first product, gradient) are staged the same
-// way; grids that TMA cannot stage (periodic walls, nx % 4 != 0) read global
+// way (periodic lateral walls included: the wrapped halo cells are fetched by
+// the threads that read them); grids TMA cannot stage (nx % 4 != 0) read global
 // memory directly.
 //
 // Numerics: the stencil is evaluated in flux form, A v = v + sum_f c_f (v_c - v_q)
@@ -38,6 +39,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "internal.h"
 
@@ -345,7 +347,7 @@ __device__ __forceinline__ void for_segments(const Geo& g, SegFn seg) {
 template <class CellFn>
 __device__ __forceinline__ void for_cells(const Geo& g, CellFn f) {
     if (threadIdx.x >= NCT) return;
-    const int qx = threadIdx.x & 7, row = threadIdx.x >> 3;
+    const int qx = threadIdx.x % (TX / QX), row = threadIdx.x / (TX / QX);
     for_segments(g, [&](int tile, int k0, int k1) {
         const int xq = (tile % g.tiles_x) * TX + qx * QX, y = (tile / g.tiles_x) * TY + row;
         if (y >= g.ny || xq >= g.nx) return;
@@ -365,8 +367,9 @@ __device__ __forceinline__ void for_cells(const Geo& g, CellFn f) {
 // together sit in consecutive slots and arrive in one 4D copy (u, ws, ss;
 // the hi and lo halves of a state; p and delta, whose own-cell 32 x 32 boxes
 // share the last two slots).  Cells outside the grid arrive as zeros, which
-// is exactly a zero-flux wall (their face values are zero), so this path
-// serves grids with zero-flux lateral walls and nx % 4 == 0 (row pitch a
+// is exactly a zero-flux wall (their face values are zero); with periodic
+// walls the wrapped cells are patched in (wrap_patch).  The path serves grids
+// with nx % 4 == 0 (row pitch a
 // multiple of 16 bytes).  Every stencil pass of a solve is staged this way;
 // only what the slots hold differs (PassKind).
 constexpr int NS = 6;                         // stages
@@ -577,6 +580,72 @@ __device__ void drain(Ring& R) {
         if (R.used >> s & 1u) mbar_wait(R.full0 + 8u * s, ((R.fiss >> s) & 1u) ^ 1u);
 }
 
+// ---- periodic lateral walls on the staged path.  The halo boxes arrive with
+// zeros beyond the grid (a zero-flux wall).  With periodic walls the cells a
+// thread reads across a lateral wall are fetched from the opposite edge by
+// that thread itself, straight into the stage (cp.async from global, no
+// registers held), right after the stage lands and one plane before it is
+// worked on; cp_wait() precedes the plane's work.  Only the thread that reads
+// a patched position writes it (the halo row above row 0, the one below the
+// last row, the column left of x = 0 and right of x = nx - 1), and corner
+// cells are never read by the 7-point stencil.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const float* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const float* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Global array staged in halo slot j of a pass (null if the slot holds no
+// halo box for this kind of pass).
+__device__ __forceinline__ const float* halo_src(const Common& C, const PassIn& in, int j) {
+    const size_t N = (size_t)C.g.S * C.g.nz;
+    if (j == 3) return C.alpha;
+    switch (in.kind) {
+        case kIter: return j < 3 ? C.v.u[in.cur] + (size_t)j * N : nullptr;
+        case kJacobi: return j < 3 ? C.v.u[0] + (size_t)j * N : nullptr;
+        case kInit2: return j == 0 ? C.v.u[0] : nullptr;
+        case kInit1: return j < 2 ? C.slab + (size_t)(in.zx + j) * N : nullptr;
+        default:   // kGrad: T (hi, lo) in slots 0-1, mu (hi, lo) in slots 4-5, slot 2 unused
+            if (j < 2) return C.slab + (size_t)(in.zx + j) * N;
+            if (j >= 4) return C.slab + (size_t)(in.zm + (j - 4)) * N;
+            return nullptr;
+    }
+}
+
+// The wrapped halo cells this thread reads on plane k (stage st), requested
+// by cp.async.  (xq, y): the thread's first cell; valid: it has cells.
+__device__ __forceinline__ void wrap_patch(const Common& C, const PassIn& in, const unsigned char* st, int k, int xq,
+                                           int y, bool valid, int hb) {
+    const Geo& g = C.g;
+    if (!valid) return;
+    const bool top = g.py && y == 0, bot = g.py && y == g.ny - 1;
+    const bool lft = g.px && xq == 0, rgt = g.px && xq + QX == g.nx;
+    if (!(top || bot || lft || rgt)) return;
+    const size_t plane = (size_t)k * g.S;
+    const uint32_t base = smem_u32(st);
+    const int nslot = in.kind == kGrad ? 6 : 4;
+    for (int j = 0; j < nslot; ++j) {
+        const float* src = halo_src(C, in, j);
+        if (!src) continue;
+        src += plane;
+        const uint32_t sb = base + (uint32_t)sl(j);
+        if (top) {
+            const float* q = src + (size_t)(g.ny - 1) * g.nx + xq;
+            if constexpr (QX == 4) cp_async16(sb + 4u * (hb - HB), q);
+            else for (int t = 0; t < QX; ++t) cp_async4(sb + 4u * (hb - HB + t), q + t);
+        }
+        if (bot) {
+            const float* q = src + xq;
+            if constexpr (QX == 4) cp_async16(sb + 4u * (hb + HB), q);
+            else for (int t = 0; t < QX; ++t) cp_async4(sb + 4u * (hb + HB + t), q + t);
+        }
+        if (lft) cp_async4(sb + 4u * (hb - 1), src + (size_t)y * g.nx + (g.nx - 1));
+        if (rgt) cp_async4(sb + 4u * (hb + QX), src + (size_t)y * g.nx);
+    }
+}
+
 // Compute side of one staged pass: walk the same planes in the same order,
 // waiting for each stage and handing it back once every warp is done with it.
 // A compute thread owns the quad at halo-box index hb (own-box index ob).
@@ -586,11 +655,15 @@ __device__ void drain(Ring& R) {
 //   top()              no plane above k;   shift()    k -> k + 1;
 //   plane(k, c, valid, st, st1) the work on plane k (st1: the stage of plane
 //                      k + 1, or null at the top).
-template <class Body>
-__device__ bool consume(const Geo& g, Ring& R, Body& B) {
-    const int lane = threadIdx.x & 31, qx = threadIdx.x & 7, row = threadIdx.x >> 3;
-    const int hb = (row + 1) * HB + 4 + 4 * qx;
-    const int ob = row * TX + 4 * qx;
+// kWrap: periodic lateral walls, the wrapped halo cells are patched in (a
+// separate instantiation, so the zero-flux path carries none of its code).
+template <bool kWrap, class Body>
+__device__ bool consume(const Common& C, const PassIn& in, Ring& R, Body& B) {
+    const Geo& g = C.g;
+    const int lane = threadIdx.x & 31, qx = threadIdx.x % (TX / QX), row = threadIdx.x / (TX / QX);
+    const int hb = (row + 1) * HB + 4 + QX * qx;
+    const int ob = row * TX + QX * qx;
+    constexpr bool wrap = kWrap;
     bool ok = true;
     auto wait = [&]() -> int {
         const unsigned st = R.cs;
@@ -600,14 +673,17 @@ __device__ bool consume(const Geo& g, Ring& R, Body& B) {
         return done ? (int)st : -1;
     };
     auto release = [&](int st) {
+        // generic-proxy writes into the stage (the wrap patches) before the
+        // next TMA copy into it
+        if constexpr (wrap) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(R.empty0 + 8u * st);
     };
     auto stage = [&](int st) -> const unsigned char* { return R.base + (unsigned)st * STAGE_BYTES; };
     for_segments(g, [&](int tile, int k0, int k1) {
         if (!ok) return;
-        const int xq = (tile % g.tiles_x) * TX + 4 * qx, y = (tile / g.tiles_x) * TY + row;
-        const bool valid = xq < g.nx && y < g.ny;   // nx % 4 == 0: a quad is all in or all out
+        const int xq = (tile % g.tiles_x) * TX + QX * qx, y = (tile / g.tiles_x) * TY + row;
+        const bool valid = xq < g.nx && y < g.ny;   // nx % 4 == 0: a thread's cells are all in or all out
         B.reset();
         if (k0 > 0) {
             const int s = wait();
@@ -617,6 +693,7 @@ __device__ bool consume(const Geo& g, Ring& R, Body& B) {
         }
         int sk = wait();
         if (sk < 0) { ok = false; return; }
+        if constexpr (wrap) wrap_patch(C, in, stage(sk), k0, xq, y, valid, hb);
         B.own(stage(sk), hb, k0 > 0);
         unsigned c = (unsigned)k0 * g.S + (unsigned)y * g.nx + xq;
         for (int k = k0; k < k1; ++k, c += g.S) {
@@ -628,6 +705,10 @@ __device__ bool consume(const Geo& g, Ring& R, Body& B) {
             } else {
                 B.top();
             }
+            if constexpr (wrap) {   // plane k's patches land; plane k + 1's are requested behind this plane's work
+                cp_wait();
+                if (sk1 >= 0 && k + 1 < k1) wrap_patch(C, in, stage(sk1), k + 1, xq, y, valid, hb);
+            }
             B.plane(k, c, valid, stage(sk), sk1 >= 0 ? stage(sk1) : nullptr, hb, ob);
             release(sk);
             B.shift();
@@ -638,22 +719,31 @@ __device__ bool consume(const Geo& g, Ring& R, Body& B) {
     return ok;
 }
 
-__device__ __forceinline__ float4 lds4(const unsigned char* st, int off, int i) {
-    return *reinterpret_cast<const float4*>(st + off + 4 * i);
-}
 __device__ __forceinline__ float lds1(const unsigned char* st, int off, int i) {
     return *reinterpret_cast<const float*>(st + off + 4 * i);
 }
-__device__ __forceinline__ void ld4(const unsigned char* st, int off, int i, float (&v)[4]) {
-    const float4 q = lds4(st, off, i);
-    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+// The QX values of a thread's cells (or of the QX cells at halo-box index i):
+// one 8- or 16-byte shared load, one global store.
+__device__ __forceinline__ void ldq(const unsigned char* st, int off, int i, float (&v)[QX]) {
+    if constexpr (QX == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(st + off + 4 * i);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+        const float2 q = *reinterpret_cast<const float2*>(st + off + 4 * i);
+        v[0] = q.x; v[1] = q.y;
+    }
 }
-__device__ __forceinline__ void stg4(float* p, const float (&v)[4]) {
-    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+__device__ __forceinline__ void stgq(float* p, const float (&v)[QX]) {
+    if constexpr (QX == 4) *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
 }
-__device__ __forceinline__ void set4(float (&d)[4], float v) { d[0] = d[1] = d[2] = d[3] = v; }
-__device__ __forceinline__ void cpy4(float (&d)[4], const float (&s)[4]) {
-    d[0] = s[0]; d[1] = s[1]; d[2] = s[2]; d[3] = s[3];
+__device__ __forceinline__ void setq(float (&d)[QX], float v) {
+#pragma unroll
+    for (int j = 0; j < QX; ++j) d[j] = v;
+}
+__device__ __forceinline__ void cpyq(float (&d)[QX], const float (&s)[QX]) {
+#pragma unroll
+    for (int j = 0; j < QX; ++j) d[j] = s[j];
 }
 
 // Lateral face values of the own quad from the staged alpha (slot 3):
@@ -661,17 +751,17 @@ __device__ __forceinline__ void cpy4(float (&d)[4], const float (&s)[4]) {
 // and cell 4 being the neighbours left and right of it); cyp / cym the +y / -y
 // faces of each cell.  Shared faces are evaluated once: face(a, b) and
 // face(b, a) are the same number.
-__device__ __forceinline__ void quad_faces(const unsigned char* st, int hb, const float (&ac)[4], float kx, float ky,
-                                           float (&cx)[5], float (&cyp)[4], float (&cym)[4]) {
-    float aym[4], ayp[4];
-    ld4(st, sl(3), hb - HB, aym);
-    ld4(st, sl(3), hb + HB, ayp);
+__device__ __forceinline__ void quad_faces(const unsigned char* st, int hb, const float (&ac)[QX], float kx, float ky,
+                                           float (&cx)[QX + 1], float (&cyp)[QX], float (&cym)[QX]) {
+    float aym[QX], ayp[QX];
+    ldq(st, sl(3), hb - HB, aym);
+    ldq(st, sl(3), hb + HB, ayp);
     cx[0] = face(ac[0], lds1(st, sl(3), hb - 1), kx);
 #pragma unroll
-    for (int j = 1; j < 4; ++j) cx[j] = face(ac[j - 1], ac[j], kx);
-    cx[4] = face(ac[3], lds1(st, sl(3), hb + 4), kx);
+    for (int j = 1; j < QX; ++j) cx[j] = face(ac[j - 1], ac[j], kx);
+    cx[QX] = face(ac[QX - 1], lds1(st, sl(3), hb + QX), kx);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < QX; ++j) {
         cyp[j] = face(ac[j], ayp[j], ky);
         cym[j] = face(ac[j], aym[j], ky);
     }
@@ -688,21 +778,21 @@ struct Step {
 };
 
 // u_{i+1} (f), s_i (sn) and u_i (u) at the quad at halo-box index h of a stage.
-__device__ __forceinline__ void field4(const unsigned char* st, int h, const Step& S, float (&f)[4], float (&sn)[4],
-                                       float (&u)[4]) {
-    float w[4], s[4] = {0.f, 0.f, 0.f, 0.f};
-    ld4(st, sl(0), h, u);
-    ld4(st, sl(1), h, w);
-    if (!S.first) ld4(st, sl(2), h, s);
+__device__ __forceinline__ void fieldq(const unsigned char* st, int h, const Step& S, float (&f)[QX], float (&sn)[QX],
+                                       float (&u)[QX]) {
+    float w[QX], s[QX] = {};
+    ldq(st, sl(0), h, u);
+    ldq(st, sl(1), h, w);
+    if (!S.first) ldq(st, sl(2), h, s);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < QX; ++j) {
         sn[j] = S.sdir(w[j], s[j]);
         f[j] = S.next(u[j], sn[j]);
     }
 }
-__device__ __forceinline__ void field4(const unsigned char* st, int h, const Step& S, float (&f)[4]) {
-    float sn[4], u[4];
-    field4(st, h, S, f, sn, u);
+__device__ __forceinline__ void fieldq(const unsigned char* st, int h, const Step& S, float (&f)[QX]) {
+    float sn[QX], u[QX];
+    fieldq(st, h, S, f, sn, u);
 }
 __device__ __forceinline__ float field1(const unsigned char* st, int h, const Step& S) {
     const float sv = S.first ? 0.f : lds1(st, sl(2), h);
@@ -715,51 +805,51 @@ struct IterBody {
     const Step& S;
     int cur;
     Acc<3>& acc;
-    float fm[4], am[4];                    // plane k-1: u_{i+1}, alpha
-    float fc[4], sc[4], uc[4], ac[4];      // plane k: u_{i+1}, s_i, u_i, alpha
-    float fp[4], sp[4], up[4], ap[4];      // plane k+1
-    float czm[4], czp[4];                  // -z / +z faces of the own cells
+    float fm[QX], am[QX];                    // plane k-1: u_{i+1}, alpha
+    float fc[QX], sc[QX], uc[QX], ac[QX];      // plane k: u_{i+1}, s_i, u_i, alpha
+    float fp[QX], sp[QX], up[QX], ap[QX];      // plane k+1
+    float czm[QX], czp[QX];                  // -z / +z faces of the own cells
     __device__ IterBody(const Common& c, const Step& s, int cu, Acc<3>& a) : C(c), S(s), cur(cu), acc(a) {}
-    __device__ __forceinline__ void reset() { set4(fm, 0.f); set4(am, 0.f); set4(czm, 0.f); }
+    __device__ __forceinline__ void reset() { setq(fm, 0.f); setq(am, 0.f); setq(czm, 0.f); }
     __device__ __forceinline__ void below(const unsigned char* st, int hb) {
-        field4(st, hb, S, fm);
-        ld4(st, sl(3), hb, am);
+        fieldq(st, hb, S, fm);
+        ldq(st, sl(3), hb, am);
     }
     __device__ __forceinline__ void own(const unsigned char* st, int hb, bool has_below) {
-        field4(st, hb, S, fc, sc, uc);
-        ld4(st, sl(3), hb, ac);
+        fieldq(st, hb, S, fc, sc, uc);
+        ldq(st, sl(3), hb, ac);
         if (has_below) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) czm[j] = face(ac[j], am[j], C.kz);
+            for (int j = 0; j < QX; ++j) czm[j] = face(ac[j], am[j], C.kz);
         }
     }
     __device__ __forceinline__ void above(const unsigned char* st, int hb) {
-        field4(st, hb, S, fp, sp, up);
-        ld4(st, sl(3), hb, ap);
+        fieldq(st, hb, S, fp, sp, up);
+        ldq(st, sl(3), hb, ap);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) czp[j] = face(ac[j], ap[j], C.kz);
+        for (int j = 0; j < QX; ++j) czp[j] = face(ac[j], ap[j], C.kz);
     }
     __device__ __forceinline__ void top() {
-        cpy4(fp, fc);
-        set4(sp, 0.f); set4(up, 0.f); set4(ap, 0.f); set4(czp, 0.f);
+        cpyq(fp, fc);
+        setq(sp, 0.f); setq(up, 0.f); setq(ap, 0.f); setq(czp, 0.f);
     }
     __device__ __forceinline__ void plane(int k, unsigned c, bool valid, const unsigned char* st,
                                           const unsigned char*, int hb, int ob) {
         const Geo& g = C.g;
-        float fym[4], fyp[4], cx[5], cyp[4], cym[4];
-        field4(st, hb - HB, S, fym);
-        field4(st, hb + HB, S, fyp);
-        const float fxl = field1(st, hb - 1, S), fxr = field1(st, hb + 4, S);
+        float fym[QX], fyp[QX], cx[QX + 1], cyp[QX], cym[QX];
+        fieldq(st, hb - HB, S, fym);
+        fieldq(st, hb + HB, S, fyp);
+        const float fxl = field1(st, hb - 1, S), fxr = field1(st, hb + QX, S);
         quad_faces(st, hb, ac, C.kx, C.ky, cx, cyp, cym);
-        float pp[4] = {0.f, 0.f, 0.f, 0.f}, dd[4];
-        if (!S.first) ld4(st, OFF_P, ob, pp);
-        ld4(st, OFF_D, ob, dd);
+        float pp[QX] = {}, dd[QX];
+        if (!S.first) ldq(st, OFF_P, ob, pp);
+        ldq(st, OFF_D, ob, dd);
         const float rob = k + 1 == g.nz ? C.robin : 0.f;
-        float wn[4], pn[4], dl[4], s0 = 0.f, s1 = 0.f, s2 = 0.f;
+        float wn[QX], pn[QX], dl[QX], s0 = 0.f, s1 = 0.f, s2 = 0.f;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < QX; ++j) {
             const float f = fc[j];
-            const float fxm = j > 0 ? fc[j - 1] : fxl, fxp = j < 3 ? fc[j + 1] : fxr;
+            const float fxm = j > 0 ? fc[j - 1] : fxl, fxp = j < QX - 1 ? fc[j + 1] : fxr;
             const float fzmv = k > 0 ? fm[j] : f;
             const float cxp = cx[j + 1], cxm = cx[j];
             const float d = diag(cxp, cxm, cyp[j], cym[j], czp[j], czm[j], rob);
@@ -774,19 +864,19 @@ struct IterBody {
             s2 += r * r;
         }
         if (valid) {
-            stg4(C.v.p + c, pn);
-            stg4(C.v.delta + c, dl);
-            stg4(C.v.u[cur ^ 1] + c, fc);
-            stg4(C.v.ws[cur ^ 1] + c, wn);
-            stg4(C.v.ss[cur ^ 1] + c, sc);
+            stgq(C.v.p + c, pn);
+            stgq(C.v.delta + c, dl);
+            stgq(C.v.u[cur ^ 1] + c, fc);
+            stgq(C.v.ws[cur ^ 1] + c, wn);
+            stgq(C.v.ss[cur ^ 1] + c, sc);
             acc.add(0, s0);
             acc.add(1, s1);
             acc.add(2, s2);
         }
     }
     __device__ __forceinline__ void shift() {
-        cpy4(fm, fc); cpy4(czm, czp);
-        cpy4(fc, fp); cpy4(sc, sp); cpy4(uc, up); cpy4(ac, ap);
+        cpyq(fm, fc); cpyq(czm, czp);
+        cpyq(fc, fp); cpyq(sc, sp); cpyq(uc, up); cpyq(ac, ap);
     }
 };
 
@@ -840,66 +930,66 @@ struct Init1Body {
     RhsFn& rhs;
     Acc<3>& acc;
     int hu;                            // 0: y = x0, d = 0
-    float hm[4], lm[4], am[4];         // plane k-1: y as (hi, lo), alpha
-    float hc[4], lc[4], ac[4];
-    float hp[4], lp[4], ap[4];
-    float czm[4], czp[4];
-    FaceTerm zdn[4];                   // the -z face terms of plane k (the +z ones of plane k-1, negated)
+    float hm[QX], lm[QX], am[QX];         // plane k-1: y as (hi, lo), alpha
+    float hc[QX], lc[QX], ac[QX];
+    float hp[QX], lp[QX], ap[QX];
+    float czm[QX], czp[QX];
+    FaceTerm zdn[QX];                   // the -z face terms of plane k (the +z ones of plane k-1, negated)
     __device__ Init1Body(const Common& c, RhsFn& r, Acc<3>& a, int hu_) : C(c), rhs(r), acc(a), hu(hu_) {}
     __device__ __forceinline__ void reset() {
-        set4(hm, 0.f); set4(lm, 0.f); set4(am, 0.f); set4(czm, 0.f);
+        setq(hm, 0.f); setq(lm, 0.f); setq(am, 0.f); setq(czm, 0.f);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) zdn[j] = FaceTerm{0.f, 0.f};
+        for (int j = 0; j < QX; ++j) zdn[j] = FaceTerm{0.f, 0.f};
     }
     __device__ __forceinline__ void below(const unsigned char* st, int hb) {
-        ld4(st, sl(0), hb, hm);
-        ld4(st, sl(1), hb, lm);
-        ld4(st, sl(3), hb, am);
+        ldq(st, sl(0), hb, hm);
+        ldq(st, sl(1), hb, lm);
+        ldq(st, sl(3), hb, am);
     }
     __device__ __forceinline__ void own(const unsigned char* st, int hb, bool has_below) {
-        ld4(st, sl(0), hb, hc);
-        ld4(st, sl(1), hb, lc);
-        ld4(st, sl(3), hb, ac);
+        ldq(st, sl(0), hb, hc);
+        ldq(st, sl(1), hb, lc);
+        ldq(st, sl(3), hb, ac);
         if (has_below) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < QX; ++j) {
                 czm[j] = face(ac[j], am[j], C.kz);
                 zdn[j] = face_term(czm[j], hc[j], lc[j], hm[j], lm[j]);
             }
         }
     }
     __device__ __forceinline__ void above(const unsigned char* st, int hb) {
-        ld4(st, sl(0), hb, hp);
-        ld4(st, sl(1), hb, lp);
-        ld4(st, sl(3), hb, ap);
+        ldq(st, sl(0), hb, hp);
+        ldq(st, sl(1), hb, lp);
+        ldq(st, sl(3), hb, ap);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) czp[j] = face(ac[j], ap[j], C.kz);
+        for (int j = 0; j < QX; ++j) czp[j] = face(ac[j], ap[j], C.kz);
     }
-    __device__ __forceinline__ void top() { set4(hp, 0.f); set4(lp, 0.f); set4(ap, 0.f); set4(czp, 0.f); }
+    __device__ __forceinline__ void top() { setq(hp, 0.f); setq(lp, 0.f); setq(ap, 0.f); setq(czp, 0.f); }
     __device__ __forceinline__ void plane(int k, unsigned c, bool valid, const unsigned char* st,
                                           const unsigned char*, int hb, int ob) {
         if (!valid) return;
         const Geo& g = C.g;
-        float hym[4], lym[4], hyp[4], lyp[4], cx[5], cyp[4], cym[4], d[4] = {0.f, 0.f, 0.f, 0.f};
-        ld4(st, sl(0), hb - HB, hym);
-        ld4(st, sl(1), hb - HB, lym);
-        ld4(st, sl(0), hb + HB, hyp);
-        ld4(st, sl(1), hb + HB, lyp);
-        if (hu > 0) ld4(st, OFF_D, ob, d);
+        float hym[QX], lym[QX], hyp[QX], lyp[QX], cx[QX + 1], cyp[QX], cym[QX], d[QX] = {};
+        ldq(st, sl(0), hb - HB, hym);
+        ldq(st, sl(1), hb - HB, lym);
+        ldq(st, sl(0), hb + HB, hyp);
+        ldq(st, sl(1), hb + HB, lyp);
+        if (hu > 0) ldq(st, OFF_D, ob, d);
         const float hxl = lds1(st, sl(0), hb - 1), lxl = lds1(st, sl(1), hb - 1);
-        const float hxr = lds1(st, sl(0), hb + 4), lxr = lds1(st, sl(1), hb + 4);
+        const float hxr = lds1(st, sl(0), hb + QX), lxr = lds1(st, sl(1), hb + QX);
         quad_faces(st, hb, ac, C.kx, C.ky, cx, cyp, cym);
         const float rob = k + 1 == g.nz ? C.robin : 0.f;
         // x faces: X[f] between cells f - 1 and f seen from the left (f = 1..3),
-        // X[0] / X[4] the outer faces seen from cells 0 / 3
-        FaceTerm X[5];
+        // X[0] / X[QX] the outer faces seen from cells 0 / 3
+        FaceTerm X[QX + 1];
         X[0] = face_term(cx[0], hc[0], lc[0], hxl, lxl);
 #pragma unroll
-        for (int f = 1; f < 4; ++f) X[f] = face_term(cx[f], hc[f - 1], lc[f - 1], hc[f], lc[f]);
-        X[4] = face_term(cx[4], hc[3], lc[3], hxr, lxr);
-        float u[4], s0 = 0.f, s1 = 0.f, s2 = 0.f;
+        for (int f = 1; f < QX; ++f) X[f] = face_term(cx[f], hc[f - 1], lc[f - 1], hc[f], lc[f]);
+        X[QX] = face_term(cx[QX], hc[QX - 1], lc[QX - 1], hxr, lxr);
+        float u[QX], s0 = 0.f, s1 = 0.f, s2 = 0.f;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < QX; ++j) {
             float sh = 0.f, sx = 0.f;
             const FaceTerm zup = face_term(czp[j], hc[j], lc[j], hp[j], lp[j]);
             add_term(X[j + 1], sh, sx);
@@ -927,12 +1017,12 @@ struct Init1Body {
         acc.add(0, s0);
         acc.add(1, s1);
         acc.add(2, s2);
-        stg4(C.v.u[0] + c, u);
-        if (hu == 0) stg4(C.v.delta + c, d);
+        stgq(C.v.u[0] + c, u);
+        if (hu == 0) stgq(C.v.delta + c, d);
     }
     __device__ __forceinline__ void shift() {
-        cpy4(hm, hc); cpy4(lm, lc); cpy4(czm, czp);
-        cpy4(hc, hp); cpy4(lc, lp); cpy4(ac, ap);
+        cpyq(hm, hc); cpyq(lm, lc); cpyq(czm, czp);
+        cpyq(hc, hp); cpyq(lc, lp); cpyq(ac, ap);
     }
 };
 
@@ -940,52 +1030,52 @@ struct Init1Body {
 struct Init2Body {
     const Common& C;
     Acc<1>& acc;
-    float um[4], am[4], uc[4], ac[4], up[4], ap[4], czm[4], czp[4];
+    float um[QX], am[QX], uc[QX], ac[QX], up[QX], ap[QX], czm[QX], czp[QX];
     __device__ Init2Body(const Common& c, Acc<1>& a) : C(c), acc(a) {}
-    __device__ __forceinline__ void reset() { set4(um, 0.f); set4(am, 0.f); set4(czm, 0.f); }
+    __device__ __forceinline__ void reset() { setq(um, 0.f); setq(am, 0.f); setq(czm, 0.f); }
     __device__ __forceinline__ void below(const unsigned char* st, int hb) {
-        ld4(st, sl(0), hb, um);
-        ld4(st, sl(3), hb, am);
+        ldq(st, sl(0), hb, um);
+        ldq(st, sl(3), hb, am);
     }
     __device__ __forceinline__ void own(const unsigned char* st, int hb, bool has_below) {
-        ld4(st, sl(0), hb, uc);
-        ld4(st, sl(3), hb, ac);
+        ldq(st, sl(0), hb, uc);
+        ldq(st, sl(3), hb, ac);
         if (has_below) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) czm[j] = face(ac[j], am[j], C.kz);
+            for (int j = 0; j < QX; ++j) czm[j] = face(ac[j], am[j], C.kz);
         }
     }
     __device__ __forceinline__ void above(const unsigned char* st, int hb) {
-        ld4(st, sl(0), hb, up);
-        ld4(st, sl(3), hb, ap);
+        ldq(st, sl(0), hb, up);
+        ldq(st, sl(3), hb, ap);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) czp[j] = face(ac[j], ap[j], C.kz);
+        for (int j = 0; j < QX; ++j) czp[j] = face(ac[j], ap[j], C.kz);
     }
-    __device__ __forceinline__ void top() { set4(up, 0.f); set4(ap, 0.f); set4(czp, 0.f); }
+    __device__ __forceinline__ void top() { setq(up, 0.f); setq(ap, 0.f); setq(czp, 0.f); }
     __device__ __forceinline__ void plane(int k, unsigned c, bool valid, const unsigned char* st,
                                           const unsigned char*, int hb, int) {
         if (!valid) return;
-        float uym[4], uyp[4], cx[5], cyp[4], cym[4], w[4];
-        ld4(st, sl(0), hb - HB, uym);
-        ld4(st, sl(0), hb + HB, uyp);
-        const float uxl = lds1(st, sl(0), hb - 1), uxr = lds1(st, sl(0), hb + 4);
+        float uym[QX], uyp[QX], cx[QX + 1], cyp[QX], cym[QX], w[QX];
+        ldq(st, sl(0), hb - HB, uym);
+        ldq(st, sl(0), hb + HB, uyp);
+        const float uxl = lds1(st, sl(0), hb - 1), uxr = lds1(st, sl(0), hb + QX);
         quad_faces(st, hb, ac, C.kx, C.ky, cx, cyp, cym);
         const float rob = k + 1 == C.g.nz ? C.robin : 0.f;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < QX; ++j) {
             const float f = uc[j];
-            const float fxm = j > 0 ? uc[j - 1] : uxl, fxp = j < 3 ? uc[j + 1] : uxr;
+            const float fxm = j > 0 ? uc[j - 1] : uxl, fxp = j < QX - 1 ? uc[j + 1] : uxr;
             const float cxp = cx[j + 1], cxm = cx[j];
             const float Au = f + cxp * (f - fxp) + cxm * (f - fxm) + cyp[j] * (f - uyp[j]) + cym[j] * (f - uym[j]) +
                              czp[j] * (f - up[j]) + czm[j] * (f - um[j]) + rob * f;
             w[j] = rcp_approx(diag(cxp, cxm, cyp[j], cym[j], czp[j], czm[j], rob)) * Au;
             acc.add(0, Au * f);
         }
-        stg4(C.v.ws[0] + c, w);
+        stgq(C.v.ws[0] + c, w);
     }
     __device__ __forceinline__ void shift() {
-        cpy4(um, uc); cpy4(czm, czp);
-        cpy4(uc, up); cpy4(ac, ap);
+        cpyq(um, uc); cpyq(czm, czp);
+        cpyq(uc, up); cpyq(ac, ap);
     }
 };
 
@@ -997,49 +1087,49 @@ struct JacobiBody {
     const Common& C;
     int src;
     float* out;
-    float dm[4], am[4], dc[4], ac[4], dp[4], ap[4], czm[4], czp[4];
+    float dm[QX], am[QX], dc[QX], ac[QX], dp[QX], ap[QX], czm[QX], czp[QX];
     __device__ JacobiBody(const Common& c, int s, float* o) : C(c), src(s), out(o) {}
-    __device__ __forceinline__ void reset() { set4(dm, 0.f); set4(am, 0.f); set4(czm, 0.f); }
+    __device__ __forceinline__ void reset() { setq(dm, 0.f); setq(am, 0.f); setq(czm, 0.f); }
     __device__ __forceinline__ void below(const unsigned char* st, int hb) {
-        ld4(st, sl(src), hb, dm);
-        ld4(st, sl(3), hb, am);
+        ldq(st, sl(src), hb, dm);
+        ldq(st, sl(3), hb, am);
     }
     __device__ __forceinline__ void own(const unsigned char* st, int hb, bool has_below) {
-        ld4(st, sl(src), hb, dc);
-        ld4(st, sl(3), hb, ac);
+        ldq(st, sl(src), hb, dc);
+        ldq(st, sl(3), hb, ac);
         if (has_below) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) czm[j] = face(ac[j], am[j], C.kz);
+            for (int j = 0; j < QX; ++j) czm[j] = face(ac[j], am[j], C.kz);
         }
     }
     __device__ __forceinline__ void above(const unsigned char* st, int hb) {
-        ld4(st, sl(src), hb, dp);
-        ld4(st, sl(3), hb, ap);
+        ldq(st, sl(src), hb, dp);
+        ldq(st, sl(3), hb, ap);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) czp[j] = face(ac[j], ap[j], C.kz);
+        for (int j = 0; j < QX; ++j) czp[j] = face(ac[j], ap[j], C.kz);
     }
-    __device__ __forceinline__ void top() { set4(dp, 0.f); set4(ap, 0.f); set4(czp, 0.f); }
+    __device__ __forceinline__ void top() { setq(dp, 0.f); setq(ap, 0.f); setq(czp, 0.f); }
     __device__ __forceinline__ void plane(int k, unsigned c, bool valid, const unsigned char* st,
                                           const unsigned char*, int hb, int) {
         if (!valid) return;
-        float dym[4], dyp[4], u0[4], cx[5], cyp[4], cym[4], o[4];
-        ld4(st, sl(src), hb - HB, dym);
-        ld4(st, sl(src), hb + HB, dyp);
-        ld4(st, sl(0), hb, u0);
-        const float dxl = lds1(st, sl(src), hb - 1), dxr = lds1(st, sl(src), hb + 4);
+        float dym[QX], dyp[QX], u0[QX], cx[QX + 1], cyp[QX], cym[QX], o[QX];
+        ldq(st, sl(src), hb - HB, dym);
+        ldq(st, sl(src), hb + HB, dyp);
+        ldq(st, sl(0), hb, u0);
+        const float dxl = lds1(st, sl(src), hb - 1), dxr = lds1(st, sl(src), hb + QX);
         quad_faces(st, hb, ac, C.kx, C.ky, cx, cyp, cym);
         const float rob = k + 1 == C.g.nz ? C.robin : 0.f;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float sum = cx[j + 1] * (j < 3 ? dc[j + 1] : dxr) + cx[j] * (j > 0 ? dc[j - 1] : dxl) +
+        for (int j = 0; j < QX; ++j) {
+            const float sum = cx[j + 1] * (j < QX - 1 ? dc[j + 1] : dxr) + cx[j] * (j > 0 ? dc[j - 1] : dxl) +
                               cyp[j] * dyp[j] + cym[j] * dym[j] + czp[j] * dp[j] + czm[j] * dm[j];
             o[j] = fmaf(rcp_approx(diag(cx[j + 1], cx[j], cyp[j], cym[j], czp[j], czm[j], rob)), sum, u0[j]);
         }
-        stg4(out + c, o);
+        stgq(out + c, o);
     }
     __device__ __forceinline__ void shift() {
-        cpy4(dm, dc); cpy4(czm, czp);
-        cpy4(dc, dp); cpy4(ac, ap);
+        cpyq(dm, dc); cpyq(czm, czp);
+        cpyq(dc, dp); cpyq(ac, ap);
     }
 };
 
@@ -1059,8 +1149,8 @@ struct GradBody {
     float wx, wy, wz;
     int nz;
     unsigned S;            // cells per plane
-    float bth[4], btl[4], bmh[4], bml[4], bac[4];   // plane k0 - 1 (segment start only)
-    float zdn[4], zdn1[4];                          // -z terms of plane k and of plane k + 1
+    float bth[QX], btl[QX], bmh[QX], bml[QX], bac[QX];   // plane k0 - 1 (segment start only)
+    float zdn[QX], zdn1[QX];                          // -z terms of plane k and of plane k + 1
     __device__ __forceinline__ static float term(float a0, float mc, float mcl, float tc, float tcl, float aq,
                                                  float mq, float mql, float tq, float tql, float w) {
         const float h = aq * rcp_approx(a0 + aq);
@@ -1079,22 +1169,22 @@ struct GradBody {
         to_c = hc * hc * P;
         to_q = hq * hq * P;
     }
-    __device__ __forceinline__ static void load(const unsigned char* st, int hb, float (&t)[4], float (&tlo)[4],
-                                                float (&m)[4], float (&mlo)[4], float (&a)[4]) {
-        ld4(st, sl(0), hb, t);
-        ld4(st, sl(1), hb, tlo);
-        ld4(st, sl(4), hb, m);
-        ld4(st, sl(5), hb, mlo);
-        ld4(st, sl(3), hb, a);
+    __device__ __forceinline__ static void load(const unsigned char* st, int hb, float (&t)[QX], float (&tlo)[QX],
+                                                float (&m)[QX], float (&mlo)[QX], float (&a)[QX]) {
+        ldq(st, sl(0), hb, t);
+        ldq(st, sl(1), hb, tlo);
+        ldq(st, sl(4), hb, m);
+        ldq(st, sl(5), hb, mlo);
+        ldq(st, sl(3), hb, a);
     }
     __device__ __forceinline__ void reset() {}
     __device__ __forceinline__ void below(const unsigned char* st, int hb) { load(st, hb, bth, btl, bmh, bml, bac); }
     __device__ __forceinline__ void own(const unsigned char* st, int hb, bool has_below) {
         if (!has_below) return;
-        float th[4], tl[4], mh[4], ml[4], ac[4];
+        float th[QX], tl[QX], mh[QX], ml[QX], ac[QX];
         load(st, hb, th, tl, mh, ml, ac);
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < QX; ++j)
             zdn[j] = term(ac[j], mh[j], ml[j], th[j], tl[j], bac[j], bmh[j], bml[j], bth[j], btl[j], wz);
     }
     __device__ __forceinline__ void above(const unsigned char*, int) {}
@@ -1102,53 +1192,60 @@ struct GradBody {
     __device__ __forceinline__ void plane(int k, unsigned c, bool valid, const unsigned char* st,
                                           const unsigned char* st1, int hb, int) {
         if (!valid) return;
-        const float4 g01 = *reinterpret_cast<const float4*>(grad + c);
-        const float4 g23 = *reinterpret_cast<const float4*>(grad + c + 2);
-        float th[4], tl[4], mh[4], ml[4], ac[4];
+        float4 gv[QX / 2];   // the cells' accumulator pairs, two per 16-byte load
+#pragma unroll
+        for (int q = 0; q < QX / 2; ++q) gv[q] = *reinterpret_cast<const float4*>(grad + c + 2 * q);
+        float th[QX], tl[QX], mh[QX], ml[QX], ac[QX];
         load(st, hb, th, tl, mh, ml, ac);
-        float s[4] = {0.f, 0.f, 0.f, 0.f};
+        float s[QX] = {};
         {   // x: the three faces inside the quad once for both cells, then the two outer faces
 #pragma unroll
-            for (int j = 0; j < 3; ++j) {
+            for (int j = 0; j < QX - 1; ++j) {
                 float a2b, b2a;
                 pair(ac[j], mh[j], ml[j], th[j], tl[j], ac[j + 1], mh[j + 1], ml[j + 1], th[j + 1], tl[j + 1], wx,
                      a2b, b2a);
                 s[j] += a2b;
                 s[j + 1] += b2a;
             }
-            const int hr = hb + 4, hl = hb - 1;
-            s[3] += term(ac[3], mh[3], ml[3], th[3], tl[3], lds1(st, sl(3), hr), lds1(st, sl(4), hr),
+            const int hr = hb + QX, hl = hb - 1;
+            s[QX - 1] += term(ac[QX - 1], mh[QX - 1], ml[QX - 1], th[QX - 1], tl[QX - 1], lds1(st, sl(3), hr), lds1(st, sl(4), hr),
                          lds1(st, sl(5), hr), lds1(st, sl(0), hr), lds1(st, sl(1), hr), wx);
             s[0] += term(ac[0], mh[0], ml[0], th[0], tl[0], lds1(st, sl(3), hl), lds1(st, sl(4), hl),
                          lds1(st, sl(5), hl), lds1(st, sl(0), hl), lds1(st, sl(1), hl), wx);
         }
 #pragma unroll
         for (int sd = 0; sd < 2; ++sd) {   // +y, then -y
-            float t[4], tlo[4], m[4], mlo[4], a[4];
+            float t[QX], tlo[QX], m[QX], mlo[QX], a[QX];
             load(st, sd == 0 ? hb + HB : hb - HB, t, tlo, m, mlo, a);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) s[j] += term(ac[j], mh[j], ml[j], th[j], tl[j], a[j], m[j], mlo[j], t[j], tlo[j], wy);
+            for (int j = 0; j < QX; ++j) s[j] += term(ac[j], mh[j], ml[j], th[j], tl[j], a[j], m[j], mlo[j], t[j], tlo[j], wy);
         }
         if (st1) {   // +z, and the -z terms of plane k + 1
-            float t[4], tlo[4], m[4], mlo[4], a[4];
+            float t[QX], tlo[QX], m[QX], mlo[QX], a[QX];
             load(st1, hb, t, tlo, m, mlo, a);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < QX; ++j) {
                 float up;
                 pair(ac[j], mh[j], ml[j], th[j], tl[j], a[j], m[j], mlo[j], t[j], tlo[j], wz, up, zdn1[j]);
                 s[j] += up;
             }
         }
-        float gh[4] = {g01.x, g01.z, g23.x, g23.z}, gl[4] = {g01.y, g01.w, g23.y, g23.w};
+        float gh[QX], gl[QX];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int q = 0; q < QX / 2; ++q) {
+            gh[2 * q] = gv[q].x; gl[2 * q] = gv[q].y;
+            gh[2 * q + 1] = gv[q].z; gl[2 * q + 1] = gv[q].w;
+        }
+#pragma unroll
+        for (int j = 0; j < QX; ++j) {
             if (k > 0) s[j] += zdn[j];
             add_pair(gh[j], gl[j], -s[j], gh[j], gl[j]);
         }
-        *reinterpret_cast<float4*>(grad + c) = make_float4(gh[0], gl[0], gh[1], gl[1]);
-        *reinterpret_cast<float4*>(grad + c + 2) = make_float4(gh[2], gl[2], gh[3], gl[3]);
+#pragma unroll
+        for (int q = 0; q < QX / 2; ++q)
+            *reinterpret_cast<float4*>(grad + c + 2 * q) = make_float4(gh[2 * q], gl[2 * q], gh[2 * q + 1], gl[2 * q + 1]);
     }
-    __device__ __forceinline__ void shift() { cpy4(zdn, zdn1); }
+    __device__ __forceinline__ void shift() { cpyq(zdn, zdn1); }
 };
 
 // Compute threads: wait for the next n stages and hand them back unread
@@ -1172,10 +1269,10 @@ __device__ bool discard(Ring& R, int n) {
 // Body over them.  Returns false (CTA-uniform, with the error recorded and
 // every copy landed) if a wait timed out anywhere in the CTA, or if `pre_ok`
 // (the early copies) is false in any thread.
-template <class Body>
+template <bool kWrap, class Body>
 __device__ bool staged(const Common& C, Ring& R, const PassIn& in, Body& B, int from = 0, bool pre_ok = true) {
     bool ok = pre_ok;
-    if (threadIdx.x < NCT) ok = consume(C.g, R, B) && ok;
+    if (threadIdx.x < NCT) ok = consume<kWrap>(C, in, R, B) && ok;
     else if (threadIdx.x == NCT) ok = produce(C, R, in, from, 1 << 30) && ok;
     if (__syncthreads_or(ok ? 0 : 1)) {
         if (threadIdx.x == NCT) drain(R);
@@ -1281,9 +1378,10 @@ struct Start {
     int hu;
 };
 
-template <bool kTma, class RhsFn>
+template <int kMode, class RhsFn>
 __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, const Start& st0, RhsFn rhs,
                       int* it_out, float* rel_out, bool* conv_out) {
+    constexpr bool kTma = kMode > 0, kWrap = kMode == 2;
     const Geo& g = C.g;
     Pipe pp = pipe_none();
     // ---- init 1: r0 = e - d - (A - I) y, u0 = M^{-1} r0 ; bb, (r0,u0), (r0,r0)
@@ -1292,7 +1390,7 @@ __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, co
         PassIn in{kInit1, 0, false, 0u, 0u, st0.hu};
         if (!slab_half(C, st0.y, &in.zx)) return false;
         Init1Body<RhsFn> B(C, rhs, acc3, st0.hu);
-        if (!staged(C, ring, in, B, pre.n, pre.ok)) return false;
+        if (!staged<kWrap>(C, ring, in, B, pre.n, pre.ok)) return false;
     } else {
         const unsigned N = g.S * (unsigned)g.nz;
         const float* __restrict__ yh = st0.y;
@@ -1341,7 +1439,7 @@ __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, co
     if constexpr (kTma) {
         const PassIn in{kInit2, 0, false, 0u, 0u};
         Init2Body B(C, acc1);
-        if (!staged(C, ring, in, B)) return false;
+        if (!staged<kWrap>(C, ring, in, B)) return false;
     } else {
         const float* __restrict__ u0 = C.v.u[0];
         for_cells(g, [&](int k, unsigned c, int x, int y) {
@@ -1401,7 +1499,7 @@ __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, co
             if constexpr (kTma) {
                 const PassIn in{kIter, cur, S.first, 0u, 0u};
                 IterBody B(C, S, cur, acc);
-                if (!staged(C, ring, in, B, pp.n, pp.ok)) return false;
+                if (!staged<kWrap>(C, ring, in, B, pp.n, pp.ok)) return false;
             } else {
                 plain_pass(C, cur, S, acc);
             }
@@ -1446,16 +1544,17 @@ __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, co
 // the initial-residual pass gives u0 = D^{-1} r0, which is the first sweep;
 // sweeps 2..K alternate between the ws and ss buffers of set 0, the last one
 // writes delta.  No reduction, one grid barrier per sweep.
-template <bool kTma, class RhsFn>
+template <int kMode, class RhsFn>
 __device__ bool solve_jacobi(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, const Start& st0, RhsFn rhs,
                              int K) {
+    constexpr bool kTma = kMode > 0, kWrap = kMode == 2;
     const Geo& g = C.g;
     Acc<3> acc3;   // the pass's sums are not needed here
     if constexpr (kTma) {
         PassIn in{kInit1, 0, false, 0u, 0u, 0};
         if (!slab_half(C, st0.y, &in.zx)) return false;
         Init1Body<RhsFn> B(C, rhs, acc3, 0);
-        if (!staged(C, ring, in, B, pre.n, pre.ok)) return false;
+        if (!staged<kWrap>(C, ring, in, B, pre.n, pre.ok)) return false;
     } else {
         const unsigned N = g.S * (unsigned)g.nz;
         const float* __restrict__ yh = st0.y;
@@ -1490,7 +1589,7 @@ __device__ bool solve_jacobi(const Common& C, Sync& sy, Ring& ring, const Pipe& 
         float* out = kappa == K - 1 ? C.v.delta : (dst == 1 ? C.v.ws[0] : C.v.ss[0]);
         if constexpr (kTma) {
             JacobiBody B(C, src, out);
-            if (!staged(C, ring, PassIn{kJacobi, 0, false, 0u, 0u}, B)) return false;
+            if (!staged<kWrap>(C, ring, PassIn{kJacobi, 0, false, 0u, 0u}, B)) return false;
         } else {
             const float* __restrict__ in = src == 0 ? C.v.u[0] : (src == 1 ? C.v.ws[0] : C.v.ss[0]);
             const float* __restrict__ u0 = C.v.u[0];
@@ -1702,8 +1801,9 @@ __device__ void load_hist(const float* __restrict__ src, const IncRing& R, int m
 // ------------------------------------------------------------- forward
 // kTma: iterations and stencil passes staged through TMA (a.c.tma set);
 // otherwise plain global loads.
-template <bool kTma, bool kJac>
+template <int kMode, bool kJac>
 __global__ void __launch_bounds__(NT, 1) forward_tiled(const __grid_constant__ FwdTiled a) {
+    constexpr bool kTma = kMode > 0;
     extern __shared__ unsigned char dyn_smem[];
     __shared__ __align__(8) unsigned long long s_full[NS], s_empty[NS];
     Ring ring = make_ring(dyn_smem, s_full, s_empty, kTma);
@@ -1740,10 +1840,10 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(const __grid_constant__ F
         auto rhs = [=](unsigned c, int k) { return (qmap && k == 0) ? sc * qmap[c] : 0.f; };
         bool ok;
         if constexpr (kJac) {   // the paper's inner solver: K sweeps from T^n
-            ok = solve_jacobi<kTma>(a.c, sy, ring, pre, Start{Tn, 0}, rhs, a.c.jacobi_k);
+            ok = solve_jacobi<kMode>(a.c, sy, ring, pre, Start{Tn, 0}, rhs, a.c.jacobi_k);
             it = a.c.jacobi_k;
         } else {
-            ok = solve<kTma>(a.c, sy, ring, pre, Start{hu > 0 ? a.ystart : Tn, hu}, rhs, &it, &rel, &conv);
+            ok = solve<kMode>(a.c, sy, ring, pre, Start{hu > 0 ? a.ystart : Tn, hu}, rhs, &it, &rel, &conv);
         }
         if (!ok) return;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1784,8 +1884,9 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(const __grid_constant__ F
 }
 
 // ------------------------------------------------------------- adjoint
-template <bool kTma, bool kJac>
+template <int kMode, bool kJac>
 __global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ AdjTiled a) {
+    constexpr bool kTma = kMode > 0;
     extern __shared__ unsigned char dyn_smem[];
     __shared__ __align__(8) unsigned long long s_full[NS], s_empty[NS];
     Ring ring = make_ring(dyn_smem, s_full, s_empty, kTma);
@@ -1822,10 +1923,10 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ A
         };
         bool ok;
         if constexpr (kJac) {   // the paper's inner solver: K sweeps from mu^{n+1}
-            ok = solve_jacobi<kTma>(a.c, sy, ring, pipe_none(), Start{mnext, 0}, rhs, a.c.jacobi_k);
+            ok = solve_jacobi<kMode>(a.c, sy, ring, pipe_none(), Start{mnext, 0}, rhs, a.c.jacobi_k);
             it = a.c.jacobi_k;
         } else {
-            ok = solve<kTma>(a.c, sy, ring, pipe_none(), Start{hu > 0 ? a.ystart : mnext, hu}, rhs, &it, &rel,
+            ok = solve<kMode>(a.c, sy, ring, pipe_none(), Start{hu > 0 ? a.ystart : mnext, hu}, rhs, &it, &rel,
                              &conv);
         }
         if (!ok) return;
@@ -1847,7 +1948,7 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ A
             B.wx = a.wx; B.wy = a.wy; B.wz = a.wz;
             B.nz = g.nz;
             B.S = g.S;
-            if (!staged(a.c, ring, in, B)) return;
+            if (!staged<kMode == 2>(a.c, ring, in, B)) return;
         } else {
             for_cells(g, [&](int k, unsigned c, int x, int y) {
                 const Nb nb = neighbours(g, c, x, y, k);
@@ -1921,7 +2022,7 @@ __device__ __forceinline__ SwState sw_begin(const BatchSweep& w) {
 // (threadIdx.x == NCT) produces; no other thread calls this.
 template <class Body>
 __device__ __forceinline__ bool stage_side(const Common& C, Ring& R, const PassIn& in, Body& B) {
-    if (threadIdx.x < NCT) return consume(C.g, R, B);
+    if (threadIdx.x < NCT) return (C.g.px || C.g.py) ? consume<true>(C, in, R, B) : consume<false>(C, in, R, B);
     return produce(C, R, in, 0, 1 << 30);
 }
 
@@ -2243,25 +2344,36 @@ __global__ void __launch_bounds__(NT, 1) batch_tiled(const __grid_constant__ Bat
 // ------------------------------------------------------------------ host
 // The TMA kernels take the stage ring in dynamic shared memory; the
 // plain-load kernels need none (and keep that memory as L1 cache).
+// Kernel variant of a launch: mode 0 = plain loads, 1 = TMA-staged, 2 =
+// TMA-staged with periodic lateral walls; the Jacobi-K sweeps are their own
+// instantiations, so the PCG kernels carry none of their code.
+static int tiled_mode(const tiled::Common& c) { return c.tma ? ((c.g.px || c.g.py) ? 2 : 1) : 0; }
+
+template <bool kJac>
+static const void* forward_fn(int mode) {
+    return mode == 0 ? (const void*)tiled::forward_tiled<0, kJac>
+                     : (mode == 1 ? (const void*)tiled::forward_tiled<1, kJac> : (const void*)tiled::forward_tiled<2, kJac>);
+}
+template <bool kJac>
+static const void* adjoint_fn(int mode) {
+    return mode == 0 ? (const void*)tiled::adjoint_tiled<0, kJac>
+                     : (mode == 1 ? (const void*)tiled::adjoint_tiled<1, kJac> : (const void*)tiled::adjoint_tiled<2, kJac>);
+}
+
 cudaError_t launch_forward_tiled(const tiled::FwdTiled& a, int grid, cudaStream_t s) {
     tiled::FwdTiled copy = a;
     void* args[] = {&copy};
-    const bool tma = a.c.tma != 0;
-    // the Jacobi-K sweeps are their own instantiations, so the PCG kernels carry none of their code
-    const bool jac = a.c.jacobi_k > 0;
-    const void* fn = tma ? (jac ? (const void*)tiled::forward_tiled<true, true> : (const void*)tiled::forward_tiled<true, false>)
-                         : (jac ? (const void*)tiled::forward_tiled<false, true> : (const void*)tiled::forward_tiled<false, false>);
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(tiled::NT), args, tma ? tiled::DYN_SMEM : 0, s);
+    const int mode = tiled_mode(a.c);
+    const void* fn = a.c.jacobi_k > 0 ? forward_fn<true>(mode) : forward_fn<false>(mode);
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(tiled::NT), args, mode ? tiled::DYN_SMEM : 0, s);
 }
 
 cudaError_t launch_adjoint_tiled(const tiled::AdjTiled& a, int grid, cudaStream_t s) {
     tiled::AdjTiled copy = a;
     void* args[] = {&copy};
-    const bool tma = a.c.tma != 0;
-    const bool jac = a.c.jacobi_k > 0;
-    const void* fn = tma ? (jac ? (const void*)tiled::adjoint_tiled<true, true> : (const void*)tiled::adjoint_tiled<true, false>)
-                         : (jac ? (const void*)tiled::adjoint_tiled<false, true> : (const void*)tiled::adjoint_tiled<false, false>);
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(tiled::NT), args, tma ? tiled::DYN_SMEM : 0, s);
+    const int mode = tiled_mode(a.c);
+    const void* fn = a.c.jacobi_k > 0 ? adjoint_fn<true>(mode) : adjoint_fn<false>(mode);
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(tiled::NT), args, mode ? tiled::DYN_SMEM : 0, s);
 }
 
 cudaError_t launch_batch_tiled(const tiled::BatchArgs& b, int grid, cudaStream_t s) {
@@ -2302,24 +2414,23 @@ cudaError_t launch_cast_split_pairs(const float* hi, const float* lo, float* out
 int tiled_grid_blocks(int device) {
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return 0;
-    const void* tma_fns[5] = {(const void*)tiled::forward_tiled<true, false>,
-                              (const void*)tiled::adjoint_tiled<true, false>,
-                              (const void*)tiled::forward_tiled<true, true>,
-                              (const void*)tiled::adjoint_tiled<true, true>, (const void*)tiled::batch_tiled};
-    const void* all_fns[9] = {tma_fns[0], tma_fns[1], tma_fns[2], tma_fns[3], tma_fns[4],
-                              (const void*)tiled::forward_tiled<false, false>,
-                              (const void*)tiled::adjoint_tiled<false, false>,
-                              (const void*)tiled::forward_tiled<false, true>,
-                              (const void*)tiled::adjoint_tiled<false, true>};
+    std::vector<const void*> tma_fns = {(const void*)tiled::batch_tiled}, plain_fns;
+    for (int mode = 0; mode < 3; ++mode)
+        for (const void* f : {forward_fn<false>(mode), forward_fn<true>(mode), adjoint_fn<false>(mode),
+                              adjoint_fn<true>(mode)})
+            (mode ? tma_fns : plain_fns).push_back(f);
     for (const void* f : tma_fns)
         if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, tiled::DYN_SMEM) != cudaSuccess)
             return 0;
     int per = 2;
-    for (int i = 0; i < 9; ++i) {
+    for (const void* f : tma_fns) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, all_fns[i], tiled::NT, i < 5 ? tiled::DYN_SMEM : 0) !=
-            cudaSuccess)
-            return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, tiled::NT, tiled::DYN_SMEM) != cudaSuccess) return 0;
+        per = std::min(per, b);
+    }
+    for (const void* f : plain_fns) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, tiled::NT, 0) != cudaSuccess) return 0;
         per = std::min(per, b);
     }
     return per * prop.multiProcessorCount;

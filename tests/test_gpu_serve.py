@@ -192,3 +192,20 @@ def test_batched_lone_job_has_the_whole_device(solver):
             t[batched] = time.perf_counter() - t0
             assert r["state_name"] == "done" and r["shared_launches"] == 0, r
     assert t[True] < 0.6 * t[False], t
+
+
+def test_periodic_job_joins_the_batched_launches(solver):
+    """A job on the paper's grid (periodic lateral walls) is batched like any
+    other FP32 job whose rows are 16-byte multiples, and its frames match the
+    direct call."""
+    w = S.paper_grid_case(nt=20)
+    p = Problem.from_workload(w, prec="fp32")
+    alpha = torch.tensor(w.alpha, dtype=torch.float32, device="cuda")
+    T0 = torch.tensor(w.T0, dtype=torch.float32, device="cuda")
+    direct = solver.forward(p, alpha, T0=T0)["frames"]
+    with Server(solver, lanes=2, chunk_steps=6) as srv:
+        fr = torch.empty_like(direct)
+        r = srv.wait(srv.submit(p, alpha, T0=T0, frames_out=fr))
+    assert r["state_name"] == "done" and r["launches"] == 4, r   # ceil(20 / 6)
+    err = (fr - direct).norm() / direct.norm()
+    assert err < 1e-5, float(err)
