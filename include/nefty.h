@@ -120,7 +120,8 @@ typedef struct {
     double adj_ms;              /* device time of the adjoint-sweep launches */
     int32_t tma_staged;         /* 1: the FP32 sweeps ran on the TMA-staged kernels (nx % 4 == 0, either
                                    wall setting); 0: plain global loads (nx % 4 != 0) or the FP64 path */
-    int32_t reserved;           /* 0 */
+    int32_t folded_last_iters;  /* solves whose last CG iteration was applied by the state update (its
+                                   residual norm known before its pass), so that its pass was left out */
 } nefty_stats;
 
 typedef struct nefty_handle nefty_handle;

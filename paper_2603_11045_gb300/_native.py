@@ -46,7 +46,7 @@ class nefty_stats(ctypes.Structure):
                 ("max_rel_residual", ctypes.c_double), ("workspace_bytes", ctypes.c_uint64),
                 ("grid_blocks", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
                 ("fwd_ms", ctypes.c_double), ("recompute_ms", ctypes.c_double),
-                ("adj_ms", ctypes.c_double), ("tma_staged", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("adj_ms", ctypes.c_double), ("tma_staged", ctypes.c_int32), ("folded_last_iters", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

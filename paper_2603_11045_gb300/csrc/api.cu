@@ -637,6 +637,7 @@ struct Call {
             st->grid_blocks = G;
             st->kernel_launches = launches;
             st->tma_staged = use_tma ? 1 : 0;
+            st->folded_last_iters = hc.folded;
             double ms[3] = {0.0, 0.0, 0.0};
             for (auto& t : timed) {
                 float v = 0.f;

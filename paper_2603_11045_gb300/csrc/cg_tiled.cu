@@ -227,14 +227,93 @@ __device__ bool grid_sum(Sync& g, const Acc<NV>& in, DF (&out)[NV], Hook after_b
     if (!barrier(g)) return false;
     after_barrier();
     if (warp == 0) {
-        // every load first, then the compensated sums in a fixed order
+        // in groups of up to four values: every load of a group first, then
+        // its compensated sums in a fixed order
+#pragma unroll
+        for (int i0 = 0; i0 < NV; i0 += 4) {
+            float2 v[kMaxGrid / 32][4];
+#pragma unroll
+            for (int r = 0; r < kMaxGrid / 32; ++r) {
+                const unsigned b = lane + 32u * r;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    v[r][i] = (i0 + i < NV && b < g.G) ? part[(size_t)b * kMaxRed + i0 + i] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (i0 + i >= NV) break;
+                float hi = 0.f, lo = 0.f;
+#pragma unroll
+                for (int r = 0; r < kMaxGrid / 32; ++r) {
+                    float sh, e;
+                    two_sum(hi, v[r][i].x, sh, e);
+                    hi = sh;
+                    lo = lo + v[r][i].y + e;
+                }
+                warp_sum2(hi, lo);
+                out[i0 + i] = df_make(hi, lo);
+            }
+        }
+    }
+    g.red += 1;
+    return true;
+}
+
+// grid_sum plus NP values reduced in plain FP32 (warp trees, CTA partials
+// and a fixed-order grid sum, as grid_sum but without the compensation): the
+// residual-norm expansion's sums, whose use needs about 1e-5 of relative
+// accuracy.  They ride in partial slots NV .. NV + NP - 1.
+template <int NV, int NP, class Hook>
+__device__ bool grid_sum_p(Sync& g, const Acc<NV>& in, const float (&pin)[NP], DF (&out)[NV], float (&pout)[NP],
+                           Hook after_barrier) {
+    static_assert(NV + NP <= kMaxRed, "reduction slots");
+    __shared__ float s_h[NW][kMaxRed], s_l[NW][kMaxRed];
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        float hi = in.h[i], lo = in.l[i];
+        warp_sum2(hi, lo);
+        if (lane == 0) { s_h[warp][i] = hi; s_l[warp][i] = lo; }
+    }
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        float v = pin[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_h[warp][NV + i] = v;
+    }
+    __syncthreads();
+    float2* part = reinterpret_cast<float2*>(g.partials) + (size_t)(g.red & 1u) * kMaxRed * g.G;
+    if (warp == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            float hi = lane < NW ? s_h[lane][i] : 0.f, lo = lane < NW ? s_l[lane][i] : 0.f;
+            warp_sum2(hi, lo);
+            if (lane == 0) part[(size_t)blockIdx.x * kMaxRed + i] = make_float2(hi, lo);
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            float v = lane < NW ? s_h[lane][NV + i] : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) part[(size_t)blockIdx.x * kMaxRed + NV + i] = make_float2(v, 0.f);
+        }
+    }
+    if (!barrier(g)) return false;
+    after_barrier();
+    if (warp == 0) {
+        // every load first, then the sums in a fixed order
         float2 v[kMaxGrid / 32][NV];
+        float w[kMaxGrid / 32][NP];
 #pragma unroll
         for (int r = 0; r < kMaxGrid / 32; ++r) {
             const unsigned b = lane + 32u * r;
 #pragma unroll
             for (int i = 0; i < NV; ++i)
                 v[r][i] = b < g.G ? part[(size_t)b * kMaxRed + i] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < NP; ++i) w[r][i] = b < g.G ? part[(size_t)b * kMaxRed + NV + i].x : 0.f;
         }
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
@@ -248,6 +327,15 @@ __device__ bool grid_sum(Sync& g, const Acc<NV>& in, DF (&out)[NV], Hook after_b
             }
             warp_sum2(hi, lo);
             out[i] = df_make(hi, lo);
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            float t = 0.f;
+#pragma unroll
+            for (int r = 0; r < kMaxGrid / 32; ++r) t += w[r][i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            pout[i] = t;
         }
     }
     g.red += 1;
@@ -800,16 +888,23 @@ __device__ __forceinline__ float field1(const unsigned char* st, int h, const St
 }
 
 // ---- one CG iteration: u_{i+1}, ws_{i+1} = M^{-1} A u_{i+1}, ss_i, p_i, delta
+// kPred: also the five sums that give the next iteration's residual norm
+// before its pass (see solve()): with r = D u_{i+1}, e = D ws_{i+1} = A u_{i+1}
+// and t = D s_i, q = (r.e, r.t, e.e, e.t, t.t), per thread in plain FP32 (the
+// expansion they feed is accurate well past what its use needs).
+template <bool kPred = false>
 struct IterBody {
     const Common& C;
     const Step& S;
     int cur;
     Acc<3>& acc;
+    float* q = nullptr;                      // kPred: [5] per-thread sums
     float fm[QX], am[QX];                    // plane k-1: u_{i+1}, alpha
     float fc[QX], sc[QX], uc[QX], ac[QX];      // plane k: u_{i+1}, s_i, u_i, alpha
     float fp[QX], sp[QX], up[QX], ap[QX];      // plane k+1
     float czm[QX], czp[QX];                  // -z / +z faces of the own cells
-    __device__ IterBody(const Common& c, const Step& s, int cu, Acc<3>& a) : C(c), S(s), cur(cu), acc(a) {}
+    __device__ IterBody(const Common& c, const Step& s, int cu, Acc<3>& a, float* q5 = nullptr)
+        : C(c), S(s), cur(cu), acc(a), q(q5) {}
     __device__ __forceinline__ void reset() { setq(fm, 0.f); setq(am, 0.f); setq(czm, 0.f); }
     __device__ __forceinline__ void below(const unsigned char* st, int hb) {
         fieldq(st, hb, S, fm);
@@ -846,6 +941,7 @@ struct IterBody {
         ldq(st, OFF_D, ob, dd);
         const float rob = k + 1 == g.nz ? C.robin : 0.f;
         float wn[QX], pn[QX], dl[QX], s0 = 0.f, s1 = 0.f, s2 = 0.f;
+        float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f, q4 = 0.f;
 #pragma unroll
         for (int j = 0; j < QX; ++j) {
             const float f = fc[j];
@@ -862,6 +958,14 @@ struct IterBody {
             s0 += r * f;
             s1 += Au * f;
             s2 += r * r;
+            if constexpr (kPred) {   // e = D ws_{i+1} = A u_{i+1}
+                const float e = Au, t = d * sc[j];
+                q0 = fmaf(r, e, q0);
+                q1 = fmaf(r, t, q1);
+                q2 = fmaf(e, e, q2);
+                q3 = fmaf(e, t, q3);
+                q4 = fmaf(t, t, q4);
+            }
         }
         if (valid) {
             stgq(C.v.p + c, pn);
@@ -872,6 +976,9 @@ struct IterBody {
             acc.add(0, s0);
             acc.add(1, s1);
             acc.add(2, s2);
+            if constexpr (kPred) {
+                q[0] += q0; q[1] += q1; q[2] += q2; q[3] += q3; q[4] += q4;
+            }
         }
     }
     __device__ __forceinline__ void shift() {
@@ -1026,12 +1133,15 @@ struct Init1Body {
     }
 };
 
-// ---- init 2: ws0 = M^{-1} A u0 ; (A u0, u0)
+// ---- init 2: ws0 = M^{-1} A u0 ; (A u0, u0); with q (the first
+// iteration's residual-norm expansion, see IterBody): r = D u0, e = D ws0,
+// q = (r.e, e.e) per thread
 struct Init2Body {
     const Common& C;
     Acc<1>& acc;
+    float* q;
     float um[QX], am[QX], uc[QX], ac[QX], up[QX], ap[QX], czm[QX], czp[QX];
-    __device__ Init2Body(const Common& c, Acc<1>& a) : C(c), acc(a) {}
+    __device__ Init2Body(const Common& c, Acc<1>& a, float* q2 = nullptr) : C(c), acc(a), q(q2) {}
     __device__ __forceinline__ void reset() { setq(um, 0.f); setq(am, 0.f); setq(czm, 0.f); }
     __device__ __forceinline__ void below(const unsigned char* st, int hb) {
         ldq(st, sl(0), hb, um);
@@ -1055,7 +1165,7 @@ struct Init2Body {
     __device__ __forceinline__ void plane(int k, unsigned c, bool valid, const unsigned char* st,
                                           const unsigned char*, int hb, int) {
         if (!valid) return;
-        float uym[QX], uyp[QX], cx[QX + 1], cyp[QX], cym[QX], w[QX];
+        float uym[QX], uyp[QX], cx[QX + 1], cyp[QX], cym[QX], w[QX], qe = 0.f, qq = 0.f;
         ldq(st, sl(0), hb - HB, uym);
         ldq(st, sl(0), hb + HB, uyp);
         const float uxl = lds1(st, sl(0), hb - 1), uxr = lds1(st, sl(0), hb + QX);
@@ -1068,8 +1178,16 @@ struct Init2Body {
             const float cxp = cx[j + 1], cxm = cx[j];
             const float Au = f + cxp * (f - fxp) + cxm * (f - fxm) + cyp[j] * (f - uyp[j]) + cym[j] * (f - uym[j]) +
                              czp[j] * (f - up[j]) + czm[j] * (f - um[j]) + rob * f;
-            w[j] = rcp_approx(diag(cxp, cxm, cyp[j], cym[j], czp[j], czm[j], rob)) * Au;
+            const float d = diag(cxp, cxm, cyp[j], cym[j], czp[j], czm[j], rob);
+            w[j] = rcp_approx(d) * Au;
             acc.add(0, Au * f);
+            const float r = d * f;   // and e = D ws0 = A u0
+            qe = fmaf(r, Au, qe);
+            qq = fmaf(Au, Au, qq);
+        }
+        if (q) {
+            q[0] += qe;
+            q[1] += qq;
         }
         stgq(C.v.ws[0] + c, w);
     }
@@ -1378,12 +1496,45 @@ struct Start {
     int hu;
 };
 
+// The last CG iteration of a solve, when its pass is left out: its whole
+// effect on the state is delta += a p with p = u (the first iteration) or
+// p = u + b p_prev, u = u[cur] and p_prev = p, which the state update applies
+// with the same arithmetic as an iteration pass (see solve()).
+struct Final {
+    int apply;
+    float a, b;
+    int first, cur;
+};
+
+// ||D u_next||^2 for u_next = u - A (w + (B/A) t') expanded in the sums of the
+// pass that made u, w and t': rho = (r, r), q = (r.e, r.t, e.e, e.t, t.t) with
+// r = D u, e = D w, t = D t'; A = alpha, B = alpha beta:
+// rho - 2A q0 - 2B q1 + A^2 q2 + 2AB q3 + B^2 q4.  Single precision: the terms
+// are about rho and the result one to four decades smaller, and the sums
+// carry about 1e-6 of relative error, so the expansion is good to about 1e-4
+// of itself, which is what a stop decision needs.
+__device__ __forceinline__ float next_rho(float rho, float A, float B, float q0, float q1, float q2, float q3,
+                                          float q4) {
+    float v = fmaf(-2.f * A, q0, rho);
+    v = fmaf(-2.f * B, q1, v);
+    v = fmaf(A * A, q2, v);
+    v = fmaf(2.f * A * B, q3, v);
+    return fmaf(B * B, q4, v);
+}
+
+// kPred (the staged kernels): the residual norm of the next iteration is
+// known before its pass (next_rho, from five more sums of the pass before);
+// when it passes the stop test, that iteration's pass (whose product A u and
+// stores would be discarded) is left out and its update returned in *fin
+// for the state update.  The stop test then sees the expanded norm, equal to
+// the pass's own sum up to rounding.
 template <int kMode, class RhsFn>
 __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, const Start& st0, RhsFn rhs,
-                      int* it_out, float* rel_out, bool* conv_out) {
-    constexpr bool kTma = kMode > 0, kWrap = kMode == 2;
+                      int* it_out, float* rel_out, bool* conv_out, Final* fin) {
+    constexpr bool kTma = kMode > 0, kWrap = kMode == 2, kPred = kTma;
     const Geo& g = C.g;
     Pipe pp = pipe_none();
+    *fin = Final{0, 0.f, 0.f, 0, 0};
     // ---- init 1: r0 = e - d - (A - I) y, u0 = M^{-1} r0 ; bb, (r0,u0), (r0,r0)
     Acc<3> acc3;
     if constexpr (kTma) {
@@ -1431,14 +1582,15 @@ __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, co
     // barrier between the two passes (u0 complete, its stores ordered before
     // the copies of the next pass), one reduction after both.
     __shared__ float s_a, s_b;
-    __shared__ int s_go;
+    __shared__ int s_go, s_fin;
     asm volatile("fence.proxy.async.global;" ::: "memory");
     if (!barrier(sy)) return false;
     // ---- init 2: ws0 = M^{-1} A u0 ; (A u0, u0)
     Acc<1> acc1;
+    float q2[2] = {0.f, 0.f};
     if constexpr (kTma) {
         const PassIn in{kInit2, 0, false, 0u, 0u};
-        Init2Body B(C, acc1);
+        Init2Body B(C, acc1, q2);
         if (!staged<kWrap>(C, ring, in, B)) return false;
     } else {
         const float* __restrict__ u0 = C.v.u[0];
@@ -1458,7 +1610,8 @@ __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, co
             acc1.add(0, Au * f);
         });
     }
-    Acc<4> acc4;   // bb, (r0, u0), (r0, r0), (A u0, u0)
+    // bb, (r0, u0), (r0, r0), (A u0, u0) [+ the expansion's (r.e, e.e) of init 2]
+    Acc<4> acc4;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         acc4.h[i] = acc3.h[i];
@@ -1467,10 +1620,15 @@ __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, co
     acc4.h[3] = acc1.h[0];
     acc4.l[3] = acc1.l[0];
     DF t4[4];
-    if (!grid_sum<4>(sy, acc4, t4, [&] {
-            if constexpr (kTma) pp = pipe_start(C, ring, PassIn{kIter, 0, true, 0u, 0u});
-        }))
-        return false;
+    float e4[2] = {0.f, 0.f};
+    auto early = [&] {
+        if constexpr (kTma) pp = pipe_start(C, ring, PassIn{kIter, 0, true, 0u, 0u});
+    };
+    if constexpr (kPred) {
+        if (!grid_sum_p<4, 2>(sy, acc4, q2, t4, e4, early)) return false;
+    } else {
+        if (!grid_sum<4>(sy, acc4, t4, early)) return false;
+    }
     const DF bb = t4[0], lim = df_mul(DF{C.tol2_hi, C.tol2_lo}, bb);
     DF gam = t4[1], rho = t4[2];
     int it = 0;
@@ -1486,50 +1644,87 @@ __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, co
             alpha = df_div(gam, t4[3]);
             s_a = alpha.hi;
             s_b = 0.f;
+            s_fin = 0;
+            if constexpr (kPred) {   // the first iteration's residual norm, before its pass
+                const float pr = next_rho(rho.hi, alpha.hi, 0.f, e4[0], 0.f, e4[1], 0.f, 0.f);
+                if (pr <= lim.hi) {
+                    rho = DF{pr, 0.f};
+                    s_fin = 1;
+                }
+            }
         }
         __syncthreads();
         int cur = 0;
-        // ---- iterations: one pass, one reduction each
-        while (true) {
-            Step S;
-            S.a = s_a;
-            S.bt = s_b;
-            S.first = it == 0;
-            Acc<3> acc;
+        if (s_fin) {   // the first iteration is the last: its update goes to the state update
             if constexpr (kTma) {
-                const PassIn in{kIter, cur, S.first, 0u, 0u};
-                IterBody B(C, S, cur, acc);
-                if (!staged<kWrap>(C, ring, in, B, pp.n, pp.ok)) return false;
-            } else {
-                plain_pass(C, cur, S, acc);
+                if (!pipe_cancel(C, ring, pp)) return false;
             }
-            DF t[3];
-            if (!grid_sum<3>(sy, acc, t, [&] {
-                    if constexpr (kTma) pp = pipe_start(C, ring, PassIn{kIter, cur ^ 1, false, 0u, 0u});
-                }))
-                return false;
-            ++it;
-            cur ^= 1;
-            if (threadIdx.x == 0) {
-                rho = t[2];
-                const bool go = !(df_le(rho, lim) || it >= C.max_iter);
-                if (go) {
-                    // beta = gam' / gam ; alpha = gam' / ((w, u) - beta gam' / alpha)
-                    const DF gam_new = t[0];
-                    const DF beta = df_div(gam_new, gam);
-                    alpha = df_div(gam_new, df_add(t[1], df_neg(df_div(df_mul(beta, gam_new), alpha))));
-                    gam = gam_new;
-                    s_a = alpha.hi;
-                    s_b = beta.hi;
-                }
-                s_go = go ? 1 : 0;
-            }
-            __syncthreads();
-            if (!s_go) {
+            *fin = Final{1, s_a, 0.f, 1, cur};
+            it = 1;
+        } else {
+            // ---- iterations: one pass, one reduction each
+            while (true) {
+                Step S;
+                S.a = s_a;
+                S.bt = s_b;
+                S.first = it == 0;
+                // (r,u), (Au,u), (r,r) [+ the expansion's five sums of the next norm]
+                Acc<3> acc;
+                float q5[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
                 if constexpr (kTma) {
-                    if (!pipe_cancel(C, ring, pp)) return false;
+                    const PassIn in{kIter, cur, S.first, 0u, 0u};
+                    IterBody<kPred> B(C, S, cur, acc, q5);
+                    if (!staged<kWrap>(C, ring, in, B, pp.n, pp.ok)) return false;
+                } else {
+                    plain_pass(C, cur, S, acc);
                 }
-                break;
+                DF t[3];
+                float e5[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+                auto early = [&] {
+                    if constexpr (kTma) pp = pipe_start(C, ring, PassIn{kIter, cur ^ 1, false, 0u, 0u});
+                };
+                if constexpr (kPred) {
+                    if (!grid_sum_p<3, 5>(sy, acc, q5, t, e5, early)) return false;
+                } else {
+                    if (!grid_sum<3>(sy, acc, t, early)) return false;
+                }
+                ++it;
+                cur ^= 1;
+                if (threadIdx.x == 0) {
+                    rho = t[2];
+                    bool go = !(df_le(rho, lim) || it >= C.max_iter);
+                    s_fin = 0;
+                    if (go) {
+                        // beta = gam' / gam ; alpha = gam' / ((w, u) - beta gam' / alpha)
+                        const DF gam_new = t[0];
+                        const DF beta = df_div(gam_new, gam);
+                        alpha = df_div(gam_new, df_add(t[1], df_neg(df_div(df_mul(beta, gam_new), alpha))));
+                        gam = gam_new;
+                        s_a = alpha.hi;
+                        s_b = beta.hi;
+                        if constexpr (kPred) {   // the next iteration's residual norm, before its pass
+                            const float pr = next_rho(rho.hi, alpha.hi, alpha.hi * beta.hi, e5[0], e5[1], e5[2],
+                                                      e5[3], e5[4]);
+                            if (pr <= lim.hi) {
+                                rho = DF{pr, 0.f};
+                                s_fin = 1;
+                                go = false;
+                            }
+                        }
+                    }
+                    s_go = go ? 1 : 0;
+                }
+                __syncthreads();
+                if (!s_go) {
+                    if constexpr (kTma) {
+                        if (!pipe_cancel(C, ring, pp)) return false;
+                    }
+                    if (s_fin) {   // the next iteration is the last: its update goes to the state update
+                        *fin = Final{1, s_a, s_b, 0, cur};
+                        ++it;
+                    }
+                    break;
+                }
             }
         }
     }
@@ -1674,10 +1869,20 @@ __device__ __forceinline__ float4 ld_older(const float* p, unsigned i, bool use)
 //   hu_next - 1 increments before it), delta = d and ys = y + d (the next
 //   start, as pairs).
 // Ends with the proxy fence that orders these stores before later TMA reads.
+// fin (when fin.apply): the solve's last iteration, whose pass was left out,
+// is applied first: delta += a p with p = u[fin.cur] (+ b p_prev), the same
+// fused multiply-adds as an iteration pass.
 __device__ void add_state(const float* __restrict__ x, float* __restrict__ delta, float* __restrict__ y,
                           unsigned N, float* __restrict__ rd, const Older& old, int hu_next,
-                          float* __restrict__ ys, bool stream_y) {
+                          float* __restrict__ ys, bool stream_y, const Final& fin = Final{0, 0.f, 0.f, 0, 0},
+                          const Vecs* vv = nullptr) {
     const unsigned stride = gridDim.x * NT, t0 = blockIdx.x * NT + threadIdx.x;
+    const bool fa = fin.apply && vv;
+    const float* __restrict__ fu = fa ? vv->u[fin.cur] : nullptr;
+    const float* __restrict__ fp = fa ? vv->p : nullptr;
+    auto last = [&](float dv, float uv, float pv) {   // delta + a (u or u + b p)
+        return fmaf(fin.a, fin.first ? uv : fmaf(fin.b, pv, uv), dv);
+    };
     if ((N & 3u) == 0) {
         // Batches of two quads per thread: every load of a batch is issued
         // before its stores.  x (the old state) is not read again soon, so it
@@ -1698,6 +1903,8 @@ __device__ void add_state(const float* __restrict__ x, float* __restrict__ delta
         float4* __restrict__ sh4 = reinterpret_cast<float4*>(ys);
         float4* __restrict__ sl4 = reinterpret_cast<float4*>(ys + N);
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4* __restrict__ fu4 = reinterpret_cast<const float4*>(fu);
+        const float4* __restrict__ fp4 = reinterpret_cast<const float4*>(fp);
         for (unsigned i0 = t0; i0 < N4; i0 += B * stride) {
             float4 h[B], l[B], e[B], o1[B], o2[B], o3[B];
 #pragma unroll
@@ -1710,6 +1917,11 @@ __device__ void add_state(const float* __restrict__ x, float* __restrict__ delta
                 o1[u] = in && hu_next > 1 ? o1p[i] : z4;
                 o2[u] = in && hu_next > 2 ? o2p[i] : z4;
                 o3[u] = in && hu_next > 3 ? o3p[i] : z4;
+                if (fa && in) {
+                    const float4 uu = fu4[i], pq = fin.first ? z4 : fp4[i];
+                    e[u] = make_float4(last(e[u].x, uu.x, pq.x), last(e[u].y, uu.y, pq.y), last(e[u].z, uu.z, pq.z),
+                                       last(e[u].w, uu.w, pq.w));
+                }
             }
 #pragma unroll
             for (int u = 0; u < B; ++u) {
@@ -1746,7 +1958,7 @@ __device__ void add_state(const float* __restrict__ x, float* __restrict__ delta
         }
     } else {
         for (unsigned c = t0; c < N; c += stride) {
-            const float e = delta[c];
+            const float e = fa ? last(delta[c], fu[c], fin.first ? 0.f : fp[c]) : delta[c];
             float oh, ol;
             add_pair(x[c], x[N + c], e, oh, ol);
             y[c] = oh;
@@ -1836,6 +2048,7 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(const __grid_constant__ F
         int it = 0;
         float rel = 0.f;
         bool conv = true;
+        Final fin{0, 0.f, 0.f, 0, 0};
         const int hu = hu_at(n);
         auto rhs = [=](unsigned c, int k) { return (qmap && k == 0) ? sc * qmap[c] : 0.f; };
         bool ok;
@@ -1843,18 +2056,19 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(const __grid_constant__ F
             ok = solve_jacobi<kMode>(a.c, sy, ring, pre, Start{Tn, 0}, rhs, a.c.jacobi_k);
             it = a.c.jacobi_k;
         } else {
-            ok = solve<kMode>(a.c, sy, ring, pre, Start{hu > 0 ? a.ystart : Tn, hu}, rhs, &it, &rel, &conv);
+            ok = solve<kMode>(a.c, sy, ring, pre, Start{hu > 0 ? a.ystart : Tn, hu}, rhs, &it, &rel, &conv, &fin);
         }
         if (!ok) return;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             a.c.iters[n - a.n0] = it;
             a.c.resid[n - a.n0] = rel;
             if (!conv) atomicAdd(&a.c.ctl->notconv, 1);
+            if (fin.apply) atomicAdd(&a.c.ctl->folded, 1);
         }
         // T^{n+1} = T^n + delta as a compensated pair, delta^n into the ring, and
         // the start of step n+1 when it predicts
         const int hu1 = n + 1 < a.n1 ? hu_at(n + 1) : 0;
-        add_state(Tn, a.c.v.delta, Tn1, N, ring_d.slot(n), older(ring_d, n, -1), hu1, a.ystart, true);
+        add_state(Tn, a.c.v.delta, Tn1, N, ring_d.slot(n), older(ring_d, n, -1), hu1, a.ystart, true, fin, &a.c.v);
         if (!barrier(sy)) return;
         if (a.ring_save && a.ring_save[n - a.n0])   // a checkpoint keeps [delta^n; delta^{n-1}; ...]
             save_hist(a.ring_save[n - a.n0], ring_d, n, a.extrap);
@@ -1916,6 +2130,7 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ A
         int it = 0;
         float rel = 0.f;
         bool conv = true;
+        Final fin{0, 0.f, 0.f, 0, 0};
         const int hu = hu_at(n);
         const unsigned o0 = a.obs_off;
         auto rhs = [=](unsigned c, int) {
@@ -1927,16 +2142,17 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ A
             it = a.c.jacobi_k;
         } else {
             ok = solve<kMode>(a.c, sy, ring, pipe_none(), Start{hu > 0 ? a.ystart : mnext, hu}, rhs, &it, &rel,
-                             &conv);
+                             &conv, &fin);
         }
         if (!ok) return;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             a.c.iters[a.n1 - n] = it;
             a.c.resid[a.n1 - n] = rel;
             if (!conv) atomicAdd(&a.c.ctl->notconv, 1);
+            if (fin.apply) atomicAdd(&a.c.ctl->folded, 1);
         }
         add_state(mnext, a.c.v.delta, mu, N, ring_d.slot(n), older(ring_d, n, 1), n - 1 > a.n0 ? hu_at(n - 1) : 0,
-                  a.ystart, false);
+                  a.ystart, false, fin, &a.c.v);
         if (!barrier(sy)) return;
         // gradient of step n with mu^n and T^n (the next step writes only the
         // other mu buffer and the CG vectors, so no barrier is needed after it)

@@ -17,7 +17,7 @@ namespace nefty {
 // Threads per CTA of the persistent solver kernels.
 constexpr int kThreads = 512;
 // Maximum number of values reduced together across the grid.
-constexpr int kMaxRed = 4;
+constexpr int kMaxRed = 8;
 // Defaults of a problem's CG stop test (rtol = 0, max_iter = 0), shared by
 // every entry point.
 constexpr double kDefaultRtolFp32 = 5e-10;
@@ -37,6 +37,8 @@ struct DevCtl {
     int notconv;           // number of solves that hit max_iter
     unsigned int missing;  // fault injection (tests): arrivals every grid barrier waits for in vain; 0 normally
     unsigned long long wait_ns;   // grid-barrier wait limit (%globaltimer ns); 0 = kBarrierTimeoutNs
+    int folded;            // solves whose last CG iteration was applied by the state update
+    int pad;
 };
 
 // Grid geometry and the precomputed operator of A(alpha) = I - dt L(alpha).
