@@ -293,14 +293,16 @@ nefty_status nefty_forward_static(int device, const nefty_problem *p, const void
  *
  * Batched (the default): the FP32 sweeps of all running jobs whose grids have
  * nx % 4 == 0 (either wall setting) run together in ONE persistent launch over
- * the whole device, whatever their grid sizes and step counts; each sweep is
- * cut into chunks (chunk_steps), and a launch carries the next
- * chunk of every running job, so a newly admitted job joins the launch that
- * follows.  Other sweeps (FP64, nx % 4 != 0, Jacobi-K) and unbatched
- * servers (batched = -1) run each lane's own persistent grid on 1 / lanes of
- * the SMs, resident beside the others.  Either way a job's results depend only
- * on the job and the server's configuration: the same bits alone or among
- * other jobs.
+ * the whole device, whatever their grid sizes and step counts: each sweep runs
+ * on its own range of the launch's CTAs, sized in proportion to its work per
+ * step, with its own grid barriers.  Each sweep is cut into chunks of
+ * chunk_steps steps, and a launch carries the next chunk of every running
+ * job, so a newly admitted job joins the launch that follows.  Other sweeps
+ * (FP64, nx % 4 != 0, Jacobi-K) and unbatched servers (batched = -1) run each
+ * lane's own persistent grid on 1 / lanes of the SMs, resident beside the
+ * others.  On lanes a job's results are the same bits alone or among other
+ * jobs; batched, its CTA share depends on the mix, which changes only the
+ * order of its reductions (results agree to rounding).
  *
  * Job kinds:
  *   NEFTY_JOB_FORWARD    nefty_forward on the job's arrays (frames_out, loss when obs given).
@@ -354,8 +356,8 @@ typedef struct {
     int32_t max_queue;          /* queued-job limit for NEFTY_EBUSY (0 = 4096) */
     uint64_t mem_budget_bytes;  /* device memory shared by the lanes (0 = 80% of free memory) */
     int32_t batched;            /* 0 or 1: batched launches (see above); -1: each lane its own grid */
-    int32_t chunk_steps;        /* batched: time steps of a sweep per launch (0 = about 2^27 cell-steps,
-                                   at least 4); smaller chunks admit new jobs sooner */
+    int32_t chunk_steps;        /* batched: time steps of a sweep per launch (0 = 32); smaller chunks
+                                   admit new jobs sooner */
 } nefty_serve_config;
 
 /* Start serving on h's device (cfg may be NULL for the defaults).

@@ -446,7 +446,7 @@ struct Call {
         return NEFTY_OK;
     }
     nefty_status launch_fwd(const FwdArgs<Real>& a, int kind = 0) {
-        NEFTY_CUDA(h, cudaMemsetAsync(&ctl->bar, 0, sizeof(unsigned), s));
+        NEFTY_CUDA(h, cudaMemsetAsync(&ctl->bar, 0, 2 * sizeof(unsigned), s));
         Timed t;
         if (nefty_status e = begin_timed(kind, &t)) return e;
         NEFTY_CUDA(h, launch_forward<Real>(a, G, s));
@@ -513,6 +513,7 @@ struct Call {
             w.f.ring_save = a.ring_save ? a.ring_save + (m0 - a.n0) : nullptr;
             w.f.c.iters = a.c.iters + (m0 - a.n0);
             w.f.c.resid = a.c.resid + (m0 - a.n0);
+            w.f.loss_add = 1;
             chunks.push_back(w);
         }
         return run_batched(chunks);
@@ -534,7 +535,7 @@ struct Call {
         return run_batched(chunks);
     }
     nefty_status launch_fwd_tiled(const tiled::FwdTiled& a, int kind) {
-        NEFTY_CUDA(h, cudaMemsetAsync(&ctl->bar, 0, sizeof(unsigned), s));
+        NEFTY_CUDA(h, cudaMemsetAsync(&ctl->bar, 0, 2 * sizeof(unsigned), s));
         Timed t;
         if (nefty_status e = begin_timed(kind, &t)) return e;
         if (h->batch && use_tma && P.jacobi_k == 0) {
@@ -545,7 +546,7 @@ struct Call {
         return end_timed(t);
     }
     nefty_status launch_adj_tiled(const tiled::AdjTiled& a) {
-        NEFTY_CUDA(h, cudaMemsetAsync(&ctl->bar, 0, sizeof(unsigned), s));
+        NEFTY_CUDA(h, cudaMemsetAsync(&ctl->bar, 0, 2 * sizeof(unsigned), s));
         Timed t;
         if (nefty_status e = begin_timed(2, &t)) return e;
         if (h->batch && use_tma && P.jacobi_k == 0) {
@@ -589,7 +590,7 @@ struct Call {
         }
     }
     nefty_status launch_adj(const AdjArgs<Real>& a) {
-        NEFTY_CUDA(h, cudaMemsetAsync(&ctl->bar, 0, sizeof(unsigned), s));
+        NEFTY_CUDA(h, cudaMemsetAsync(&ctl->bar, 0, 2 * sizeof(unsigned), s));
         Timed t;
         if (nefty_status e = begin_timed(2, &t)) return e;
         NEFTY_CUDA(h, launch_adjoint<Real>(a, G, s));

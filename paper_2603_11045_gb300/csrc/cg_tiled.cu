@@ -48,6 +48,14 @@ namespace tiled {
 
 constexpr int NW = NT / 32;   // warps per CTA
 
+// The CTA's index within, and the number of CTAs of, the sweep it works on:
+// cta_id() and cta_count() in a launch of one sweep; in a grouped launch
+// (several sweeps, each on its own range of CTAs) the index within the range
+// and the range's size.  Set by each kernel before any sweep code runs.
+static __shared__ unsigned s_cta, s_ncta;
+__device__ __forceinline__ unsigned cta_id() { return s_cta; }
+__device__ __forceinline__ unsigned cta_count() { return s_ncta; }
+
 // ------------------------------------------------------------------ sync
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
@@ -70,6 +78,7 @@ __device__ __forceinline__ unsigned long long now_ns() {
 
 struct Sync {
     DevCtl* ctl;
+    unsigned* bar;      // the arrival counter in use (ctl->bar or ctl->bar2)
     double* partials;   // [2][kMaxRed][G] float2 pairs
     unsigned G;
     unsigned epoch;     // thread 0 only
@@ -89,11 +98,11 @@ __device__ bool barrier(Sync& g) {
     if (threadIdx.x == 0) {
         g.epoch += 1;
         const unsigned target = g.epoch * g.G + g.missing;
-        red_release(&g.ctl->bar, 1u);
+        red_release(g.bar, 1u);
         int ok = 1;
         unsigned spins = 0;
         unsigned long long t0 = 0;
-        while (ld_acquire(&g.ctl->bar) < target) {
+        while (ld_acquire(g.bar) < target) {
             if ((++spins & 63u) == 0) {
                 if (ld_relaxed(&g.ctl->err) != kDevOk) { ok = 0; break; }
                 const unsigned long long t = now_ns();
@@ -221,7 +230,7 @@ __device__ bool grid_sum(Sync& g, const Acc<NV>& in, DF (&out)[NV], Hook after_b
         for (int i = 0; i < NV; ++i) {
             float hi = lane < NW ? s_h[lane][i] : 0.f, lo = lane < NW ? s_l[lane][i] : 0.f;
             warp_sum2(hi, lo);
-            if (lane == 0) part[(size_t)blockIdx.x * kMaxRed + i] = make_float2(hi, lo);
+            if (lane == 0) part[(size_t)cta_id() * kMaxRed + i] = make_float2(hi, lo);
         }
     }
     if (!barrier(g)) return false;
@@ -290,14 +299,14 @@ __device__ bool grid_sum_p(Sync& g, const Acc<NV>& in, const float (&pin)[NP], D
         for (int i = 0; i < NV; ++i) {
             float hi = lane < NW ? s_h[lane][i] : 0.f, lo = lane < NW ? s_l[lane][i] : 0.f;
             warp_sum2(hi, lo);
-            if (lane == 0) part[(size_t)blockIdx.x * kMaxRed + i] = make_float2(hi, lo);
+            if (lane == 0) part[(size_t)cta_id() * kMaxRed + i] = make_float2(hi, lo);
         }
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
             float v = lane < NW ? s_h[lane][NV + i] : 0.f;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) part[(size_t)blockIdx.x * kMaxRed + NV + i] = make_float2(v, 0.f);
+            if (lane == 0) part[(size_t)cta_id() * kMaxRed + NV + i] = make_float2(v, 0.f);
         }
     }
     if (!barrier(g)) return false;
@@ -418,8 +427,8 @@ __device__ __forceinline__ float diag(float cxp, float cxm, float cyp, float cym
 template <class SegFn>
 __device__ __forceinline__ void for_segments(const Geo& g, SegFn seg) {
     const unsigned long long U = g.units;
-    unsigned u = (unsigned)(U * blockIdx.x / gridDim.x);
-    const unsigned ue = (unsigned)(U * (blockIdx.x + 1) / gridDim.x);
+    unsigned u = (unsigned)(U * cta_id() / cta_count());
+    const unsigned ue = (unsigned)(U * (cta_id() + 1) / cta_count());
     while (u < ue) {
         const int tile = (int)(u / g.nz);
         const int k0 = (int)(u % g.nz);
@@ -1774,8 +1783,8 @@ __device__ bool solve_jacobi(const Common& C, Sync& sy, Ring& ring, const Pipe& 
     if (!barrier(sy)) return false;
     const unsigned N = g.S * (unsigned)g.nz;
     if (K <= 1) {   // delta = u0
-        const unsigned stride = gridDim.x * NT;
-        for (unsigned c = blockIdx.x * NT + threadIdx.x; c < N; c += stride) C.v.delta[c] = C.v.u[0][c];
+        const unsigned stride = cta_count() * NT;
+        for (unsigned c = cta_id() * NT + threadIdx.x; c < N; c += stride) C.v.delta[c] = C.v.u[0][c];
         return barrier(sy);
     }
     int src = 0;   // slot (and buffer of set 0) holding the current delta
@@ -1817,11 +1826,12 @@ __device__ __forceinline__ void prefetch_maps(const TmaMaps& M) {
     tma_prefetch_desc(&M.states);
 }
 
-__device__ __forceinline__ Sync make_sync(DevCtl* ctl, double* partials) {
+__device__ __forceinline__ Sync make_sync(DevCtl* ctl, double* partials, int bar_sel = 0) {
     Sync s;
     s.ctl = ctl;
+    s.bar = bar_sel ? &ctl->bar2 : &ctl->bar;
     s.partials = partials;
-    s.G = gridDim.x;
+    s.G = cta_count();
     s.epoch = 0;
     s.red = 0;
     s.missing = ctl->missing;
@@ -1876,7 +1886,7 @@ __device__ void add_state(const float* __restrict__ x, float* __restrict__ delta
                           unsigned N, float* __restrict__ rd, const Older& old, int hu_next,
                           float* __restrict__ ys, bool stream_y, const Final& fin = Final{0, 0.f, 0.f, 0, 0},
                           const Vecs* vv = nullptr) {
-    const unsigned stride = gridDim.x * NT, t0 = blockIdx.x * NT + threadIdx.x;
+    const unsigned stride = cta_count() * NT, t0 = cta_id() * NT + threadIdx.x;
     const bool fa = fin.apply && vv;
     const float* __restrict__ fu = fa ? vv->u[fin.cur] : nullptr;
     const float* __restrict__ fp = fa ? vv->p : nullptr;
@@ -1982,7 +1992,7 @@ __device__ void add_state(const float* __restrict__ x, float* __restrict__ delta
 // checkpoint starts from the same bits.
 __device__ void prepare_start(const float* __restrict__ x, const float* __restrict__ rn, const Older& old, int hu,
                               float* __restrict__ delta, float* __restrict__ ys, unsigned N) {
-    const unsigned stride = gridDim.x * NT, t0 = blockIdx.x * NT + threadIdx.x;
+    const unsigned stride = cta_count() * NT, t0 = cta_id() * NT + threadIdx.x;
     for (unsigned c = t0; c < N; c += stride) {
         const float dn = predict(hu, rn[c], hu > 1 ? old.r[0][c] : 0.f, hu > 2 ? old.r[1][c] : 0.f,
                                  hu > 3 ? old.r[2][c] : 0.f);
@@ -1996,14 +2006,14 @@ __device__ void prepare_start(const float* __restrict__ x, const float* __restri
 // step m - i (forward; m + i adjoint is not needed), i < h; every thread of
 // the grid.  load_hist is the inverse at a launch start.
 __device__ void save_hist(float* __restrict__ dst, const IncRing& R, int m, int h) {
-    const unsigned stride = gridDim.x * NT, t0 = blockIdx.x * NT + threadIdx.x, N = R.N;
+    const unsigned stride = cta_count() * NT, t0 = cta_id() * NT + threadIdx.x, N = R.N;
     for (int k = 0; k < h; ++k) {
         const float* src = R.slot(m - k);
         for (unsigned i = t0; i < N; i += stride) dst[(size_t)k * N + i] = src[i];
     }
 }
 __device__ void load_hist(const float* __restrict__ src, const IncRing& R, int m, int h) {
-    const unsigned stride = gridDim.x * NT, t0 = blockIdx.x * NT + threadIdx.x, N = R.N;
+    const unsigned stride = cta_count() * NT, t0 = cta_id() * NT + threadIdx.x, N = R.N;
     for (int k = 0; k < h; ++k) {
         float* dst = R.slot(m - k);
         for (unsigned i = t0; i < N; i += stride) dst[i] = src[(size_t)k * N + i];
@@ -2014,18 +2024,18 @@ __device__ void load_hist(const float* __restrict__ src, const IncRing& R, int m
 // kTma: iterations and stencil passes staged through TMA (a.c.tma set);
 // otherwise plain global loads.
 template <int kMode, bool kJac>
-__global__ void __launch_bounds__(NT, 1) forward_tiled(const __grid_constant__ FwdTiled a) {
+__device__ __forceinline__ void forward_sweep(const FwdTiled& a) {
     constexpr bool kTma = kMode > 0;
     extern __shared__ unsigned char dyn_smem[];
     __shared__ __align__(8) unsigned long long s_full[NS], s_empty[NS];
     Ring ring = make_ring(dyn_smem, s_full, s_empty, kTma);
     if (kTma && threadIdx.x == NCT) prefetch_maps(a.c.maps);
 
-    Sync sy = make_sync(a.c.ctl, a.c.partials);
+    Sync sy = make_sync(a.c.ctl, a.c.partials, a.c.bar_sel);
     const Geo& g = a.c.g;
     const unsigned N = g.S * (unsigned)g.nz, S = g.S;
-    const unsigned stride = gridDim.x * NT;
-    const unsigned c0 = blockIdx.x * NT + threadIdx.x;
+    const unsigned stride = cta_count() * NT;
+    const unsigned c0 = cta_id() * NT + threadIdx.x;
     double loss = 0.0;
     Pipe pre = pipe_none();
     // increments used by the start of step n (ring slot m holds delta^m)
@@ -2059,7 +2069,7 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(const __grid_constant__ F
             ok = solve<kMode>(a.c, sy, ring, pre, Start{hu > 0 ? a.ystart : Tn, hu}, rhs, &it, &rel, &conv, &fin);
         }
         if (!ok) return;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (cta_id() == 0 && threadIdx.x == 0) {
             a.c.iters[n - a.n0] = it;
             a.c.resid[n - a.n0] = rel;
             if (!conv) atomicAdd(&a.c.ctl->notconv, 1);
@@ -2093,25 +2103,28 @@ __global__ void __launch_bounds__(NT, 1) forward_tiled(const __grid_constant__ F
     }
     if (a.loss_partials) {
         const double t = block_sum(loss);
-        if (threadIdx.x == 0) a.loss_partials[blockIdx.x] = t;
+        if (threadIdx.x == 0) {
+            if (a.loss_add) a.loss_partials[cta_id()] += t;   // chunks of one sweep add up
+            else a.loss_partials[cta_id()] = t;
+        }
     }
 }
 
 // ------------------------------------------------------------- adjoint
 template <int kMode, bool kJac>
-__global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ AdjTiled a) {
+__device__ __forceinline__ void adjoint_sweep(const AdjTiled& a) {
     constexpr bool kTma = kMode > 0;
     extern __shared__ unsigned char dyn_smem[];
     __shared__ __align__(8) unsigned long long s_full[NS], s_empty[NS];
     Ring ring = make_ring(dyn_smem, s_full, s_empty, kTma);
     if (kTma && threadIdx.x == NCT) prefetch_maps(a.c.maps);
 
-    Sync sy = make_sync(a.c.ctl, a.c.partials);
+    Sync sy = make_sync(a.c.ctl, a.c.partials, a.c.bar_sel);
     const Geo& g = a.c.g;
     const unsigned N = g.S * (unsigned)g.nz, S = g.S;
     const float gs = a.g_scale;
-    const unsigned stride = gridDim.x * NT;
-    const unsigned c0 = blockIdx.x * NT + threadIdx.x;
+    const unsigned stride = cta_count() * NT;
+    const unsigned c0 = cta_id() * NT + threadIdx.x;
     (void)stride;
     (void)c0;
     // increments used by the start of step n (ring slot m holds mu^m - mu^{m+1})
@@ -2145,7 +2158,7 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ A
                              &conv, &fin);
         }
         if (!ok) return;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (cta_id() == 0 && threadIdx.x == 0) {
             a.c.iters[a.n1 - n] = it;
             a.c.resid[a.n1 - n] = rel;
             if (!conv) atomicAdd(&a.c.ctl->notconv, 1);
@@ -2190,368 +2203,58 @@ __global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ A
     }
 }
 
-// ------------------------------------------------------------- batched sweeps
+// Launches of one sweep on the whole grid.
+template <int kMode, bool kJac>
+__global__ void __launch_bounds__(NT, 1) forward_tiled(const __grid_constant__ FwdTiled a) {
+    if (threadIdx.x == 0) {
+        s_cta = blockIdx.x;
+        s_ncta = gridDim.x;
+    }
+    __syncthreads();
+    forward_sweep<kMode, kJac>(a);
+}
+template <int kMode, bool kJac>
+__global__ void __launch_bounds__(NT, 1) adjoint_tiled(const __grid_constant__ AdjTiled a) {
+    if (threadIdx.x == 0) {
+        s_cta = blockIdx.x;
+        s_ncta = gridDim.x;
+    }
+    __syncthreads();
+    adjoint_sweep<kMode, kJac>(a);
+}
+
+// ------------------------------------------------------------- grouped sweeps
 // Serving runs the sweeps of several jobs (forward or adjoint, ragged grids)
-// in one persistent launch.  Each sweep keeps the step sequence of its own
-// launch (forward_tiled / adjoint_tiled) and runs it as a state machine: per
-// grid-wide pass every unfinished sweep does its next pass over its own
-// units (split over all CTAs as in a launch of its own), then one grid
-// barrier and one reduction serve every sweep's inner products.  A sweep's
-// arithmetic, its reduction order and the split of its units depend only on
-// the sweep and the grid size, so its results are the same bits alone or in
-// any mix.  Only TMA-staged sweeps are batched.
-enum SwPhase : int { kSwPrep, kSwInit1, kSwInit2, kSwIter, kSwAdd, kSwTail, kSwDone };
-
-struct SwState {
-    int ph;      // the sweep's next pass
-    int n;       // step of the current solve
-    int post;    // the previous step's post-work is due (frames and ring save; gradient)
-    int it, cur; // CG iterations so far; ping-pong index of the iteration inputs
-    float a, b;  // step lengths of the next iteration pass
-};
-struct SwScalars {   // CG scalars of the current solve (thread 0)
-    DF bb, lim, gam, rho, al;
-};
-
-__device__ __forceinline__ int sw_nv(int ph) { return ph == kSwInit1 || ph == kSwIter ? 3 : (ph == kSwInit2 ? 1 : 0); }
-
-__device__ __forceinline__ int fwd_hu(const FwdTiled& a, int n) {
-    return min(a.extrap, min(a.hist0 + (n - a.n0), kRing));
-}
-__device__ __forceinline__ int adj_hu(const AdjTiled& a, int n) {
-    return min(a.extrap, min(a.hist0 + (a.n1 - n), kRing));
-}
-
-__device__ __forceinline__ SwState sw_begin(const BatchSweep& w) {
-    SwState s{};
-    if (w.adjoint) {
-        s.n = w.a.n1;
-        s.ph = w.a.n1 <= w.a.n0 ? kSwDone : (adj_hu(w.a, w.a.n1) > 0 ? kSwPrep : kSwInit1);
-    } else {
-        s.n = w.f.n0;
-        s.ph = w.f.n1 <= w.f.n0 ? kSwDone : ((w.f.ring_load || fwd_hu(w.f, w.f.n0) > 0) ? kSwPrep : kSwInit1);
-    }
-    return s;
-}
-
-// One side of a staged pass: the compute threads consume, the copy thread
-// (threadIdx.x == NCT) produces; no other thread calls this.
-template <class Body>
-__device__ __forceinline__ bool stage_side(const Common& C, Ring& R, const PassIn& in, Body& B) {
-    if (threadIdx.x < NCT) return (C.g.px || C.g.py) ? consume<true>(C, in, R, B) : consume<false>(C, in, R, B);
-    return produce(C, R, in, 0, 1 << 30);
-}
-
-// The staged passes both kinds share: the first product and an iteration.
-__device__ bool sw_cg_side(const Common& C, const SwState& st, Ring& ring, Acc<3>& acc) {
-    if (st.ph == kSwInit2) {
-        Acc<1> acc1;
-        Init2Body Bd(C, acc1);
-        const bool ok = stage_side(C, ring, PassIn{kInit2, 0, false, 0u, 0u}, Bd);
-        acc.h[0] = acc1.h[0];
-        acc.l[0] = acc1.l[0];
-        return ok;
-    }
-    Step S;
-    S.a = st.a;
-    S.bt = st.b;
-    S.first = st.it == 0;
-    IterBody Bd(C, S, st.cur, acc);
-    return stage_side(C, ring, PassIn{kIter, st.cur, S.first, 0u, 0u}, Bd);
-}
-
-// The staged work of a sweep in one grid-wide pass (compute threads and the
-// copy thread): the adjoint's gradient of the step just updated, then the
-// solve's pass (initial residual, first product or iteration).
-__device__ bool sw_staged(const BatchSweep& w, const SwState& st, Ring& ring, Acc<3>& acc) {
-    if (w.adjoint) {
-        const AdjTiled& a = w.a;
-        const unsigned N = a.c.g.S * (unsigned)a.c.g.nz, S = a.c.g.S;
-        if (st.post) {   // gradient of step m with mu^m and T^m
-            const int m = st.n + 1;
-            PassIn in{kGrad, 0, false, 0u, 0u};
-            if (!slab_half(a.c, a.T[m - a.n0], &in.zx) || !slab_half(a.c, a.mu[m & 1], &in.zm)) return false;
-            GradBody Bd;
-            Bd.grad = a.grad;
-            Bd.wx = a.wx; Bd.wy = a.wy; Bd.wz = a.wz;
-            Bd.nz = a.c.g.nz;
-            Bd.S = a.c.g.S;
-            if (!stage_side(a.c, ring, in, Bd)) return false;
-        }
-        if (st.ph == kSwInit1) {
-            const int n = st.n, hu = adj_hu(a, n);
-            const float* __restrict__ Tn = a.T[n - a.n0];
-            const float* ob = a.obs + (size_t)(n - 1) * S;
-            const float gs = a.g_scale;
-            auto rhs = [&](unsigned c, int) {
-                return (c >= a.obs_off && c < a.obs_off + S) ? gs * ((Tn[c] - ob[c - a.obs_off]) + Tn[N + c]) : 0.f;
-            };
-            PassIn in{kInit1, 0, false, 0u, 0u, hu};
-            if (!slab_half(a.c, hu > 0 ? a.ystart : a.mu[(n + 1) & 1], &in.zx)) return false;
-            Init1Body<decltype(rhs)> Bd(a.c, rhs, acc, hu);
-            return stage_side(a.c, ring, in, Bd);
-        }
-        if (st.ph == kSwInit2 || st.ph == kSwIter) return sw_cg_side(a.c, st, ring, acc);
-        return true;
-    }
-    const FwdTiled& a = w.f;
-    if (st.ph == kSwInit1) {
-        const int n = st.n, hu = fwd_hu(a, n);
-        const unsigned S = a.c.g.S;
-        const float* qmap = a.q_full ? a.q_full + (size_t)n * S : (n < a.q_steps ? a.q_face : nullptr);
-        const float sc = a.src_scale;
-        auto rhs = [=](unsigned c, int k) { return (qmap && k == 0) ? sc * qmap[c] : 0.f; };
-        PassIn in{kInit1, 0, false, 0u, 0u, hu};
-        if (!slab_half(a.c, hu > 0 ? a.ystart : a.src[n - a.n0], &in.zx)) return false;
-        Init1Body<decltype(rhs)> Bd(a.c, rhs, acc, hu);
-        return stage_side(a.c, ring, in, Bd);
-    }
-    if (st.ph == kSwInit2 || st.ph == kSwIter) return sw_cg_side(a.c, st, ring, acc);
-    return true;
-}
-
-// The unstaged work of a sweep in one grid-wide pass (every thread, after
-// the staged work of all sweeps): the forward's ring save and frame of the
-// step just updated, the start of a launch, the state update.
-__device__ void sw_unstaged(const BatchSweep& w, const SwState& st, double& loss) {
-    const unsigned stride = gridDim.x * NT, c0 = blockIdx.x * NT + threadIdx.x;
-    if (w.adjoint) {
-        const AdjTiled& a = w.a;
-        const unsigned N = a.c.g.S * (unsigned)a.c.g.nz;
-        const IncRing ring_d{a.ring, N};
-        if (st.ph == kSwPrep) {
-            prepare_start(a.mu[(a.n1 + 1) & 1], ring_d.slot(a.n1 + 1), older(ring_d, a.n1 + 1, 1), adj_hu(a, a.n1),
-                          a.c.v.delta, a.ystart, N);
-        } else if (st.ph == kSwAdd) {
-            const int n = st.n;
-            add_state(a.mu[(n + 1) & 1], a.c.v.delta, a.mu[n & 1], N, ring_d.slot(n), older(ring_d, n, 1),
-                      n - 1 > a.n0 ? adj_hu(a, n - 1) : 0, a.ystart, false);
-        }
-        return;
-    }
-    const FwdTiled& a = w.f;
-    const unsigned N = a.c.g.S * (unsigned)a.c.g.nz, S = a.c.g.S;
-    const IncRing ring_d{a.ring, N};
-    if (st.post) {   // step m has ended: ring save and frame of T^{m+1}
-        const int m = st.n - 1;
-        const float* Tn1 = a.dst[m - a.n0];
-        if (a.ring_save && a.ring_save[m - a.n0]) save_hist(a.ring_save[m - a.n0], ring_d, m, a.extrap);
-        if (a.frames || a.obs) {
-            for (unsigned s = c0; s < S; s += stride) {
-                const float v = Tn1[a.obs_off + s];
-                if (a.frames) a.frames[(size_t)m * S + s] = v;
-                if (a.obs) {
-                    const double e = ((double)v - (double)a.obs[(size_t)m * S + s]) + (double)Tn1[N + a.obs_off + s];
-                    loss += e * e;
-                }
-            }
-        }
-    }
-    if (st.ph == kSwPrep) {
-        if (a.ring_load) load_hist(a.ring_load, ring_d, a.n0 - 1, a.extrap);
-        if (fwd_hu(a, a.n0) > 0)
-            prepare_start(a.src[0], ring_d.slot(a.n0 - 1), older(ring_d, a.n0 - 1, -1), fwd_hu(a, a.n0), a.c.v.delta,
-                          a.ystart, N);
-    } else if (st.ph == kSwAdd) {
-        const int n = st.n;
-        const int hu1 = n + 1 < a.n1 ? fwd_hu(a, n + 1) : 0;
-        add_state(a.src[n - a.n0], a.c.v.delta, a.dst[n - a.n0], N, ring_d.slot(n), older(ring_d, n, -1), hu1,
-                  a.ystart, true);
-    }
-}
-
-// The end of a solve (thread 0): iterations, relative residual and the
-// not-converged count of the sweep.
-__device__ void sw_record(const Common& C, int idx, int it, const SwScalars& q) {
-    const bool conv = df_le(q.rho, q.lim);
-    if (blockIdx.x == 0) {
-        C.iters[idx] = it;
-        C.resid[idx] = q.bb.hi > 0.f ? sqrtf(q.rho.hi / q.bb.hi) : 0.f;
-        if (!conv) atomicAdd(&C.ctl->notconv, 1);
-    }
-}
-
-// The sweep's state after a pass whose sums are t[0..2] (thread 0); the same
-// decisions as solve() and the step loops of the sweep kernels.
-__device__ void sw_advance(const BatchSweep& w, SwState& s, SwScalars& q, const DF* t) {
-    const Common& C = w.adjoint ? w.a.c : w.f.c;
-    const int idx = w.adjoint ? w.a.n1 - s.n : s.n - w.f.n0;
-    const bool was_add = s.ph == kSwAdd;
-    switch (s.ph) {
-        case kSwPrep:
-            s.ph = kSwInit1;
-            break;
-        case kSwInit1:
-            q.bb = t[0];
-            q.lim = df_mul(DF{C.tol2_hi, C.tol2_lo}, q.bb);
-            q.gam = t[1];
-            q.rho = t[2];
-            s.it = 0;
-            if (!df_le(q.rho, q.lim) && C.max_iter > 0) {
-                s.ph = kSwInit2;
-            } else {
-                sw_record(C, idx, 0, q);
-                s.ph = kSwAdd;
-            }
-            break;
-        case kSwInit2:
-            q.al = df_div(q.gam, t[0]);
-            s.a = q.al.hi;
-            s.b = 0.f;
-            s.cur = 0;
-            s.ph = kSwIter;
-            break;
-        case kSwIter: {
-            ++s.it;
-            s.cur ^= 1;
-            q.rho = t[2];
-            if (!(df_le(q.rho, q.lim) || s.it >= C.max_iter)) {
-                const DF gam_new = t[0];
-                const DF beta = df_div(gam_new, q.gam);
-                q.al = df_div(gam_new, df_add(t[1], df_neg(df_div(df_mul(beta, gam_new), q.al))));
-                q.gam = gam_new;
-                s.a = q.al.hi;
-                s.b = beta.hi;
-            } else {
-                sw_record(C, idx, s.it, q);
-                s.ph = kSwAdd;
-            }
-            break;
-        }
-        case kSwAdd:
-            if (w.adjoint) {
-                s.n -= 1;
-                s.ph = s.n > w.a.n0 ? kSwInit1 : kSwTail;
-            } else {
-                s.n += 1;
-                s.ph = s.n < w.f.n1 ? kSwInit1 : kSwTail;
-            }
-            break;
-        default:
-            s.ph = kSwDone;
-            break;
-    }
-    // the post-work of a step runs at the start of the pass after its update
-    s.post = was_add ? 1 : 0;
-}
-
-// One grid barrier and the grid-wide sums of the first nv values of the
-// per-warp partials wh/wl (compensated, the same order as grid_sum for every
-// value).  Every CTA gets the totals in tot[0, nv).
-__device__ bool batch_sum(Sync& g, int nv, float (*wh)[kBatchRed], float (*wl)[kBatchRed], DF* tot) {
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    float2* part = reinterpret_cast<float2*>(g.partials) + (size_t)(g.red & 1u) * kBatchRed * g.G;
-    for (int i = warp; i < nv; i += NW) {
-        float hi = lane < NW ? wh[lane][i] : 0.f, lo = lane < NW ? wl[lane][i] : 0.f;
-        warp_sum2(hi, lo);
-        if (lane == 0) part[(size_t)blockIdx.x * kBatchRed + i] = make_float2(hi, lo);
-    }
-    if (!barrier(g)) return false;
-    for (int i = warp; i < nv; i += NW) {
-        float2 v[kMaxGrid / 32];
-#pragma unroll
-        for (int r = 0; r < kMaxGrid / 32; ++r) {
-            const unsigned b = lane + 32u * r;
-            v[r] = b < g.G ? part[(size_t)b * kBatchRed + i] : make_float2(0.f, 0.f);
-        }
-        float hi = 0.f, lo = 0.f;
-#pragma unroll
-        for (int r = 0; r < kMaxGrid / 32; ++r) {
-            float sh, e;
-            two_sum(hi, v[r].x, sh, e);
-            hi = sh;
-            lo = lo + v[r].y + e;
-        }
-        warp_sum2(hi, lo);
-        if (lane == 0) tot[i] = df_make(hi, lo);
-    }
-    g.red += 1;
-    __syncthreads();
-    return true;
-}
-
+// in one persistent launch: each sweep gets its own range of CTAs
+// (B.off[j] .. B.off[j + 1] - 1, sized by the host in proportion to its work)
+// and runs there exactly what a launch of its own would run, with its own
+// grid barriers and reductions, so the sweeps proceed independently inside
+// the launch.
 static_assert(sizeof(BatchArgs) <= 32764, "kernel parameter space");
 
-__global__ void __launch_bounds__(NT, 1) batch_tiled(const __grid_constant__ BatchArgs B) {
-    extern __shared__ unsigned char dyn_smem[];
-    __shared__ __align__(8) unsigned long long s_full[NS], s_empty[NS];
-    __shared__ SwState s_st[kMaxBatch];
-    __shared__ SwScalars s_q[kMaxBatch];
-    __shared__ float s_wh[NW][kBatchRed], s_wl[NW][kBatchRed];
-    __shared__ DF s_tot[kBatchRed];
-    Ring ring = make_ring(dyn_smem, s_full, s_empty, true);
-    const int ns = min(B.n, kMaxBatch);
-    if (threadIdx.x == NCT)
-        for (int j = 0; j < ns; ++j) prefetch_maps(B.s[j].adjoint ? B.s[j].a.c.maps : B.s[j].f.c.maps);
-    Sync sy = make_sync(B.ctl, B.partials);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double loss[kMaxBatch];
-    for (int j = 0; j < kMaxBatch; ++j) loss[j] = 0.0;
-    if (threadIdx.x == 0)
-        for (int j = 0; j < ns; ++j) s_st[j] = sw_begin(B.s[j]);
-    for (int i = threadIdx.x; i < NW * kBatchRed; i += NT) {   // the copy warp's row stays zero
-        s_wh[i / kBatchRed][i % kBatchRed] = 0.f;
-        s_wl[i / kBatchRed][i % kBatchRed] = 0.f;
+__global__ void __launch_bounds__(NT, 1) group_tiled(const __grid_constant__ BatchArgs B) {
+    int j = -1;
+    for (int i = 0; i < B.n; ++i)
+        if ((int)blockIdx.x >= B.off[i] && (int)blockIdx.x < B.off[i + 1]) j = i;
+    if (j < 0) return;   // beyond the sweeps' ranges
+    if (threadIdx.x == 0) {
+        s_cta = blockIdx.x - (unsigned)B.off[j];
+        s_ncta = (unsigned)(B.off[j + 1] - B.off[j]);
     }
     __syncthreads();
-    bool ok = true;
-    while (true) {
-        int live = 0, nv = 0;
-        for (int j = 0; j < ns; ++j)
-            if (s_st[j].ph != kSwDone) {
-                ++live;
-                nv = 3 * (j + 1);
-            }
-        if (live == 0) break;
-        // staged work of every sweep: the copy thread streams their planes
-        // back to back, the compute warps consume them in the same order
-        if (threadIdx.x < NCT || threadIdx.x == NCT) {
-            for (int j = 0; j < ns && ok; ++j) {
-                const SwState st = s_st[j];
-                Acc<3> acc;
-                if (st.ph != kSwDone) ok = sw_staged(B.s[j], st, ring, acc);
-                if (threadIdx.x < NCT) {
-                    ok = __all_sync(0xffffffffu, ok);   // the warp stays together for the sums
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) {
-                        float hi = acc.h[i], lo = acc.l[i];
-                        warp_sum2(hi, lo);
-                        if (lane == 0) { s_wh[warp][3 * j + i] = hi; s_wl[warp][3 * j + i] = lo; }
-                    }
-                }
-            }
-        }
-        if (__syncthreads_or(ok ? 0 : 1)) {
-            if (threadIdx.x == NCT) drain(ring);
-            ok = false;
-            break;
-        }
-        for (int j = 0; j < ns; ++j) {
-            const SwState st = s_st[j];
-            if (st.ph != kSwDone) sw_unstaged(B.s[j], st, loss[j]);
-        }
-        if (!batch_sum(sy, nv, s_wh, s_wl, s_tot)) { ok = false; break; }
-        if (threadIdx.x == 0)
-            for (int j = 0; j < ns; ++j)
-                if (s_st[j].ph != kSwDone) sw_advance(B.s[j], s_st[j], s_q[j], s_tot + 3 * j);
-        __syncthreads();
+    const BatchSweep& w = B.s[j];
+    if (w.adjoint) {
+        if (w.a.c.g.px || w.a.c.g.py) adjoint_sweep<2, false>(w.a);
+        else adjoint_sweep<1, false>(w.a);
+    } else {
+        if (w.f.c.g.px || w.f.c.g.py) forward_sweep<2, false>(w.f);
+        else forward_sweep<1, false>(w.f);
     }
-    if (ok) {
-        for (int j = 0; j < ns; ++j)
-            if (!B.s[j].adjoint && B.s[j].f.loss_partials) {
-                const double t = block_sum(loss[j]);   // chunks of a sweep add up
-                if (threadIdx.x == 0) B.s[j].f.loss_partials[blockIdx.x] += t;
-            }
-    } else if (threadIdx.x == 0) {
-        atomicCAS(&B.ctl->err, kDevOk, kDevTimeout);
-    }
-    // a failed launch fails every sweep in it
-    if (threadIdx.x == 0) {
-        const int e = ld_relaxed(&B.ctl->err);
-        if (e != kDevOk)
-            for (int j = 0; j < ns; ++j) atomicCAS(&(B.s[j].adjoint ? B.s[j].a.c.ctl : B.s[j].f.c.ctl)->err, kDevOk, e);
+    // the counter this launch did not use is idle until the sweep's next
+    // launch, which counts on it: zero it now (no CTA of this launch reads it)
+    if (s_cta == 0 && threadIdx.x == 0) {
+        const Common& c = w.adjoint ? w.a.c : w.f.c;
+        *(c.bar_sel ? &c.ctl->bar : &c.ctl->bar2) = 0u;
     }
 }
 
@@ -2595,7 +2298,7 @@ cudaError_t launch_adjoint_tiled(const tiled::AdjTiled& a, int grid, cudaStream_
 cudaError_t launch_batch_tiled(const tiled::BatchArgs& b, int grid, cudaStream_t s) {
     tiled::BatchArgs copy = b;
     void* args[] = {&copy};
-    return cudaLaunchCooperativeKernel((const void*)tiled::batch_tiled, dim3(grid), dim3(tiled::NT), args,
+    return cudaLaunchCooperativeKernel((const void*)tiled::group_tiled, dim3(grid), dim3(tiled::NT), args,
                                        tiled::DYN_SMEM, s);
 }
 
@@ -2630,7 +2333,7 @@ cudaError_t launch_cast_split_pairs(const float* hi, const float* lo, float* out
 int tiled_grid_blocks(int device) {
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return 0;
-    std::vector<const void*> tma_fns = {(const void*)tiled::batch_tiled}, plain_fns;
+    std::vector<const void*> tma_fns = {(const void*)tiled::group_tiled}, plain_fns;
     for (int mode = 0; mode < 3; ++mode)
         for (const void* f : {forward_fn<false>(mode), forward_fn<true>(mode), adjoint_fn<false>(mode),
                               adjoint_fn<true>(mode)})

@@ -33,6 +33,7 @@ enum DevError : int { kDevOk = 0, kDevTimeout = 1, kDevBadAlpha = 2, kDevBadStat
 // host before each launch except `err`, which persists over a call).
 struct DevCtl {
     unsigned int bar;      // grid-barrier arrival counter
+    unsigned int bar2;     // the second counter of grouped launches (they alternate; see group_tiled)
     int err;               // DevError of the call
     int notconv;           // number of solves that hit max_iter
     unsigned int missing;  // fault injection (tests): arrivals every grid barrier waits for in vain; 0 normally
@@ -203,6 +204,7 @@ struct Common {
     DevCtl* ctl;
     double* partials;      // [2][G][kMaxRed] (hi, lo) float pairs
     float tol2_hi, tol2_lo;   // rtol^2 as a double-float
+    int bar_sel;           // grid-barrier counter: 0 = ctl->bar, 1 = ctl->bar2 (grouped launches alternate)
     int max_iter;
     int jacobi_k;          // > 0: every solve is K Jacobi sweeps from its warm start (no CG)
     int* iters;
@@ -235,6 +237,7 @@ struct FwdTiled {
     const float* obs;
     float* frames;
     double* loss_partials;
+    int loss_add;             // 1: add this launch's frame losses to loss_partials (chunks of one sweep)
 };
 
 struct AdjTiled {
@@ -255,11 +258,10 @@ struct AdjTiled {
 };
 
 // Several sweeps in one persistent launch (serving).  A sweep is the
-// argument block of one forward or adjoint launch; every sweep of a batch
-// advances by one of its passes per grid-wide pass, and the passes of all
-// sweeps share the grid barrier and the reduction that ends each pass.
+// argument block of one forward or adjoint launch (its own control word and
+// reduction partials); sweep j runs on CTAs off[j] .. off[j + 1] - 1 of the
+// launch exactly as a launch of its own would run on that many CTAs.
 constexpr int kMaxBatch = 16;
-constexpr int kBatchRed = 3 * kMaxBatch;   // reduced values per grid-wide pass
 struct BatchSweep {
     int adjoint;           // 0: f is used, 1: a is used
     union {
@@ -269,8 +271,7 @@ struct BatchSweep {
 };
 struct BatchArgs {
     int n;                 // sweeps in s[0, n)
-    DevCtl* ctl;           // barrier counter and error word of the launch
-    double* partials;      // [2][G][kBatchRed] (hi, lo) float pairs
+    int off[kMaxBatch + 1];   // CTA ranges
     BatchSweep s[kMaxBatch];
 };
 
@@ -317,7 +318,9 @@ bool tiled_encode_maps(tiled::TmaMaps* maps, const tiled::Geo& g, const tiled::V
                        const float* slab, unsigned slab_halves);
 cudaError_t launch_forward_tiled(const tiled::FwdTiled& a, int grid, cudaStream_t s);
 cudaError_t launch_adjoint_tiled(const tiled::AdjTiled& a, int grid, cudaStream_t s);
-// One batched launch (TMA-staged sweeps only; b.ctl->bar zeroed by the caller).
+// One grouped launch (TMA-staged sweeps only): sweep j counts its grid barriers
+// on ctl->bar or ctl->bar2 (Common::bar_sel), which must be zero, and zeroes the
+// other one at its end for the sweep's next launch.
 cudaError_t launch_batch_tiled(const tiled::BatchArgs& b, int grid, cudaStream_t s);
 // Batched serving launches (serve.cu).  A Batcher owns one stream and runs the
 // sweeps handed to batcher_run from any thread in shared persistent launches

@@ -10,15 +10,20 @@
 //
 // Batched mode: the lanes' handles hand their TMA-staged FP32 sweeps to one
 // Batcher instead of launching them.  The Batcher thread repeatedly takes the
-// next chunk of every pending sweep (at most kMaxBatch, in arrival order),
+// next chunk of every pending sweep (at most kMaxBatch, in arrival order) and
 // launches them together as one persistent grid over the whole device
-// (tiled::batch_tiled), and composes the next launch when that one is done, so
-// a job admitted meanwhile joins the next launch.  Ordering: a launch waits
-// for the work each lane issued before its sweep (an event per request), and
-// a lane's stream waits for the launch that carried its sweep's last chunk.
-// Unbatched mode (and the sweeps the batch kernel does not take) runs each
-// lane's own cooperative grid on 1 / lanes of the SMs, resident beside the
-// others.  In both modes a job's results do not depend on the other jobs.
+// (tiled::group_tiled): each sweep gets its own range of CTAs, in proportion
+// to its work per step, and runs there as in a launch of its own, so the
+// sweeps proceed independently; the next launch is composed when this one is
+// done, so a job admitted meanwhile joins it.  Every sweep is cut into chunks
+// of the same number of steps, so the chunks of one launch take about the
+// same time.  Ordering: a launch waits for the work each lane issued before
+// its sweep (an event per request), and a lane's stream waits for the launch
+// that carried its sweep's last chunk.  Unbatched mode (and the sweeps the
+// grouped kernel does not take) runs each lane's own cooperative grid on
+// 1 / lanes of the SMs, resident beside the others.  A job's results depend
+// on the CTAs it gets (its reduction order), not otherwise on the other
+// jobs: alone and in a mix they agree to rounding.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -95,17 +100,14 @@ class Batcher {
         cudaSetDevice(device_);
         nefty_status st = NEFTY_OK;
         grid_ = std::min(tiled_grid_blocks(device_), tiled::kMaxGrid);
-        const size_t part = 2 * (size_t)tiled::kBatchRed * (size_t)std::max(grid_, 1) * sizeof(float2);
         if (grid_ <= 0) {
             *why = "cannot size the batched solver grid on this device";
             st = NEFTY_ECUDA;
         } else if (cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking) != cudaSuccess ||
-                   cudaEventCreateWithFlags(&done_, cudaEventDisableTiming) != cudaSuccess) {
+                   cudaEventCreateWithFlags(&done_[0], cudaEventDisableTiming) != cudaSuccess ||
+                   cudaEventCreateWithFlags(&done_[1], cudaEventDisableTiming) != cudaSuccess) {
             *why = "cannot create the batcher's stream";
             st = NEFTY_ECUDA;
-        } else if (cudaMalloc(&ctl_, sizeof(DevCtl)) != cudaSuccess || cudaMalloc(&partials_, part) != cudaSuccess) {
-            *why = "cannot allocate the batcher's control block";
-            st = NEFTY_ENOMEM;
         }
         cudaGetLastError();
         cudaSetDevice(cur);
@@ -128,10 +130,10 @@ class Batcher {
     }
 
     int grid() const { return grid_; }
-    int chunk(unsigned N) const {
-        if (chunk_steps_ > 0) return chunk_steps_;
-        return std::max(4, (int)std::min(1e6, 134217728.0 / (double)N));
-    }
+    // Steps per chunk: the same for every sweep (the CTA shares of a launch
+    // follow the work per step, so equal step counts take about equal time).
+    int chunk(unsigned) const { return chunk_steps_ > 0 ? chunk_steps_ : kDefaultChunkSteps; }
+    static constexpr int kDefaultChunkSteps = 32;
 
     nefty_status run(std::vector<tiled::BatchSweep>& chunks, int grid, cudaStream_t s, int* launches,
                      int* shared, std::string* why) {
@@ -174,14 +176,53 @@ class Batcher {
 
   private:
     void release() {
-        if (ctl_) cudaFree(ctl_);
-        if (partials_) cudaFree(partials_);
-        if (done_) cudaEventDestroy(done_);
+        for (cudaEvent_t& ev : done_) {
+            if (ev) cudaEventDestroy(ev);
+            ev = nullptr;
+        }
         if (stream_) cudaStreamDestroy(stream_);
-        ctl_ = nullptr;
-        partials_ = nullptr;
-        done_ = nullptr;
         stream_ = nullptr;
+    }
+
+    // CTA ranges of the sweeps taken for one launch: shares of the grid in
+    // proportion to each sweep's work per step (cells, adjoint sweeps weighted
+    // 1.5 for their extra gradient pass and iterations), at least one CTA, at
+    // most the CTAs a launch of its own would use (one per two tile-planes).
+    // The sweeps that do not fit wait for the next launch; returns how many fit.
+    int shares(const std::vector<const tiled::BatchSweep*>& sw, int* off) const {
+        const int n = (int)sw.size();
+        std::vector<double> cost(n);
+        std::vector<int> cap(n), g(n, 1);
+        for (int i = 0; i < n; ++i) {
+            const tiled::Common& c = sw[i]->adjoint ? sw[i]->a.c : sw[i]->f.c;
+            cost[i] = (double)c.g.S * c.g.nz * (sw[i]->adjoint ? 1.5 : 1.0);
+            cap[i] = std::max(1, std::min(grid_, (int)(c.g.units / 2)));
+        }
+        int used = 0, fit = 0;
+        for (; fit < n && used + 1 <= grid_; ++fit) used += 1;   // one CTA each first
+        if (fit == 0) return 0;
+        int left = grid_ - fit;
+        double tf = 0.0;
+        for (int i = 0; i < fit; ++i) tf += cost[i];
+        for (int i = 0; i < fit; ++i) {
+            const int add = std::min(cap[i] - 1, (int)((double)(grid_ - fit) * cost[i] / tf));
+            g[i] += std::max(0, add);
+            left -= std::max(0, add);
+        }
+        for (bool more = true; left > 0 && more;) {   // the rest, largest first, up to the caps
+            more = false;
+            int best = -1;
+            for (int i = 0; i < fit; ++i)
+                if (g[i] < cap[i] && (best < 0 || cost[i] / g[i] > cost[best] / g[best])) best = i;
+            if (best >= 0) {
+                ++g[best];
+                --left;
+                more = true;
+            }
+        }
+        off[0] = 0;
+        for (int i = 0; i < fit; ++i) off[i + 1] = off[i] + g[i];
+        return fit;
     }
 
     void main() {
@@ -192,24 +233,33 @@ class Batcher {
             {
                 std::unique_lock<std::mutex> lk(mu_);
                 cv_.wait(lk, [&] { return stopping_ || !pending_.empty(); });
-                if (pending_.empty()) return;   // stopping, nothing left
+                if (pending_.empty()) break;   // stopping, nothing left
                 for (BatchReq* r : pending_) {
                     if ((int)take.size() == tiled::kMaxBatch) break;
                     take.push_back(r);
                 }
             }
-            // one launch with the next chunk of every request taken
-            args.n = (int)take.size();
-            args.ctl = ctl_;
-            args.partials = (double*)partials_;
+            // one launch with the next chunk of every request taken (those
+            // whose CTA shares fit)
+            std::vector<const tiled::BatchSweep*> sw;
+            for (BatchReq* r : take) sw.push_back(&(*r->chunks)[r->next]);
+            args.n = shares(sw, args.off);
+            take.resize(args.n);
             cudaError_t e = cudaSuccess;
+            cudaEvent_t done = done_[nlaunch_ & 1];
             for (int i = 0; i < args.n && e == cudaSuccess; ++i) {
-                args.s[i] = (*take[i]->chunks)[take[i]->next];
+                args.s[i] = *sw[i];
                 e = cudaStreamWaitEvent(stream_, take[i]->ready, 0);
+                // grid-barrier counters: the sweep's launches alternate between its
+                // two counters, each launch zeroing the other one at its end (both are
+                // zero at the start of every library call)
+                tiled::Common& c = args.s[i].adjoint ? args.s[i].a.c : args.s[i].f.c;
+                unsigned& par = parity_[c.ctl];
+                c.bar_sel = (int)(par & 1u);
+                par += 1;
             }
-            if (e == cudaSuccess) e = cudaMemsetAsync(ctl_, 0, sizeof(DevCtl), stream_);
             if (e == cudaSuccess) e = launch_batch_tiled(args, grid_, stream_);
-            if (e == cudaSuccess) e = cudaEventRecord(done_, stream_);
+            if (e == cudaSuccess) e = cudaEventRecord(done, stream_);
             if (e != cudaSuccess) cudaGetLastError();
             {
                 std::lock_guard<std::mutex> lk(mu_);
@@ -220,7 +270,7 @@ class Batcher {
                     if (e != cudaSuccess) r->err = e;
                     if (e != cudaSuccess || r->next == r->chunks->size()) {
                         // the lane continues after this launch
-                        if (e == cudaSuccess) cudaStreamWaitEvent(r->stream, done_, 0);
+                        if (e == cudaSuccess) cudaStreamWaitEvent(r->stream, done, 0);
                         r->finished = true;
                         pending_.erase(std::find(pending_.begin(), pending_.end(), r));
                     }
@@ -228,19 +278,22 @@ class Batcher {
                 ++launches_;
             }
             cv_.notify_all();
-            // the next launch is composed once this one is done, from every
-            // sweep pending by then
-            if (e == cudaSuccess) cudaEventSynchronize(done_);
+            // one launch may wait in the stream behind the running one: the next
+            // is composed (from every sweep pending by then) once the launch
+            // before this one is done, so no host round trip separates launches
+            if (e == cudaSuccess && nlaunch_ > 0) cudaEventSynchronize(done_[(nlaunch_ - 1) & 1]);
+            ++nlaunch_;
         }
+        if (nlaunch_ > 0) cudaEventSynchronize(done_[(nlaunch_ - 1) & 1]);
     }
 
     int device_;
     int chunk_steps_;
     int grid_ = 0;
     cudaStream_t stream_ = nullptr;
-    cudaEvent_t done_ = nullptr;
-    DevCtl* ctl_ = nullptr;
-    void* partials_ = nullptr;
+    cudaEvent_t done_[2] = {nullptr, nullptr};
+    long long nlaunch_ = 0;
+    std::unordered_map<DevCtl*, unsigned> parity_;   // grouped launches per control block
     std::thread thread_;
     std::mutex mu_;
     std::condition_variable cv_;

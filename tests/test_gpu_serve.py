@@ -72,7 +72,12 @@ def test_inversion_job_matches_python_loop(solver, batched):
 
 
 @pytest.mark.parametrize("batched", [True, False])
-def test_same_bits_alone_and_in_the_mix(solver, batched):
+def test_same_result_alone_and_in_the_mix(solver, batched):
+    """A job's frames alone and among other jobs.  On lanes with their own
+    grids the job runs on the same CTAs either way: the same bits.  Batched,
+    the job's share of the launch's CTAs follows the mix, which changes only
+    the order of its reductions: the frames agree to the FP32 surface
+    tolerance (and in fact to rounding)."""
     w, p, alpha, q = _case(64, 64, 16, 60, 3003)
     others = [_case(*shape, seed) for shape, seed in (((96, 64, 24, 80), 3004), ((128, 96, 20, 50), 3005),
                                                       ((32, 32, 8, 200), 3006))]
@@ -90,7 +95,9 @@ def test_same_bits_alone_and_in_the_mix(solver, batched):
     assert all(x["state_name"] == "done" for x in res), res
     if batched:   # 60 steps in chunks of 9: 7 launches, shared with the jobs submitted before it
         assert res[2]["launches"] == 7 and res[2]["shared_launches"] > 0, res[2]
-    assert torch.equal(alone, mixed)
+        assert float((mixed - alone).norm() / alone.norm()) <= 1e-6
+    else:
+        assert torch.equal(alone, mixed)
 
 
 def test_batched_ragged_mix_matches_direct_calls(solver):
