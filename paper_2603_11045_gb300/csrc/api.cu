@@ -327,6 +327,11 @@ struct Call {
     float* ring_f = nullptr;           // increment rings of the forward and adjoint sweeps ([kRing][N] each)
     float* ring_a = nullptr;
     float* ystart = nullptr;           // the next solve's start (a slot of the state slab)
+    float* diag_buf = nullptr;
+    int* cflag = nullptr;
+    // The TMA-staged PCG carries the residual of each solve into the next
+    // (cg_tiled.cu); checkpoints then keep it beside the increments.
+    bool carries() const { return kTiled && tma_grid(P) && P.jacobi_k == 0; }
 
     void place_common(Arena& a, size_t ntables) {
         const size_t N = P.N;
@@ -342,6 +347,12 @@ struct Call {
             tv.delta = tv.p + N;
             ring_f = (float*)a.take(tiled::kRing * N * sizeof(float));
             ring_a = (float*)a.take(tiled::kRing * N * sizeof(float));
+            // the carried residual of the forward and adjoint sweeps, and the
+            // diagonal of A (used by the TMA-staged PCG only: diag stays null
+            // otherwise, which the kernels read as "not carried")
+            tv.sig[0] = (float*)a.take(3 * N * sizeof(float));
+            tv.sig[1] = tv.sig[0] + N;
+            diag_buf = tv.sig[0] + 2 * N;
         } else {
             r = (Real*)a.take(N * sizeof(Real));
             p = (Real*)a.take(N * sizeof(Real));
@@ -351,6 +362,7 @@ struct Call {
         partials = (double*)a.take(2 * kMaxRed * (size_t)G * sizeof(double));
         loss_partials = (double*)a.take((size_t)G * sizeof(double));
         iters = (int*)a.take(3 * (size_t)P.nt * sizeof(int));
+        cflag = (int*)a.take(2 * ((size_t)P.nt + 1) * sizeof(int));   // forward, adjoint (FwdTiled::cflag)
         resid = (double*)a.take(3 * (size_t)P.nt * sizeof(double));
         tables = (Real**)a.take(ntables * sizeof(Real*));
         alpha.place(a); T0.place(a); qf.place(a); qfull.place(a); obs.place(a);
@@ -386,6 +398,7 @@ struct Call {
             if (!tiled_encode_maps(&host_maps, g, tv, (const float*)alpha.dev, (const float*)slab, slab_halves))
                 return NEFTY_OK;
             use_tma = true;
+            if (carries()) tv.diag = diag_buf;
         }
         return NEFTY_OK;
     }
@@ -510,6 +523,7 @@ struct Call {
             w.f.dst = a.dst + (m0 - a.n0);
             w.f.hist0 = std::min(a.hist0 + (m0 - a.n0), tiled::kRing);
             w.f.ring_load = m0 == a.n0 ? a.ring_load : nullptr;
+            w.f.carry = m0 == a.n0 ? a.carry : 1;   // a chunk continues the one before it
             w.f.ring_save = a.ring_save ? a.ring_save + (m0 - a.n0) : nullptr;
             w.f.c.iters = a.c.iters + (m0 - a.n0);
             w.f.c.resid = a.c.resid + (m0 - a.n0);
@@ -528,6 +542,7 @@ struct Call {
             w.a.n0 = std::max(a.n0, m1 - batch_chunk());
             w.a.T = a.T + (w.a.n0 - a.n0);
             w.a.hist0 = std::min(a.hist0 + (a.n1 - m1), tiled::kRing);
+            w.a.carry = m1 == a.n1 ? a.carry : 1;
             w.a.c.iters = a.c.iters + (a.n1 - m1);
             w.a.c.resid = a.c.resid + (a.n1 - m1);
             chunks.push_back(w);
@@ -557,10 +572,12 @@ struct Call {
         return end_timed(t);
     }
     // forward launch over steps [n0, n1) with either kernel family
-    // ring_load / ring_save / hist0: the increment history (FP32 path, see FwdTiled)
+    // ring_load / ring_save / hist0 / carry: the increment history and the
+    // carried residual (FP32 path, see FwdTiled)
     nefty_status forward_steps(int n0, int n1, Real* const* src, Real* const* dst, int* it, double* rs,
                                Real* frames, const Real* obsp, double* lossp, int kind,
-                               const Real* ring_load = nullptr, Real* const* ring_save = nullptr, int hist0 = 0) {
+                               const Real* ring_load = nullptr, Real* const* ring_save = nullptr, int hist0 = 0,
+                               int carry = 0) {
         if constexpr (kTiled) {
             tiled::FwdTiled a{};
             a.c = tiled_common(it, rs);
@@ -571,6 +588,9 @@ struct Call {
             a.hist0 = hist0;
             a.ring_load = ring_load;
             a.ring_save = ring_save;
+            a.carry = carry;
+            a.cflag = cflag;
+            a.n_end = P.nt;
             a.src = src; a.dst = dst;
             a.q_face = (const float*)qf.dev;
             a.q_steps = qf.dev ? q_steps : 0;
@@ -814,9 +834,10 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
     }
     const size_t SB = (Call<Real>::kTiled ? 2 : 1) * N * R;   // one state slot (see run_forward)
     // FP32 checkpoints also keep the increments before them (as many as the
-    // start extrapolates from), so a recomputed segment starts from the same
-    // extrapolation as the first sweep
-    const int ck_hist_if = Call<Real>::kTiled ? P.extrap : 0;
+    // start extrapolates from) and, on the TMA-staged path, the carried
+    // residual, so a recomputed segment starts from the same bits as the
+    // first sweep
+    const int ck_hist_if = Call<Real>::kTiled ? P.extrap + (C.carries() ? 1 : 0) : 0;
     const CkPlan plan = plan_checkpoints(P, fixed, h->budget, SB, (ck_hist_if + 1) / 2);
     const int K = plan.K, gB = plan.gB;
     const int B = (int)std::min((long long)gB * K, (long long)P.nt);   // recomputed steps [0, B)
@@ -966,7 +987,7 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
             if (nefty_status e = C.forward_steps(a0, a1, dR_src + a0, dR_dst + a0, C.iters + nt + rec_steps,
                                                  C.resid + nt + rec_steps, nullptr, nullptr, nullptr, 1,
                                                  ck_ring && g > 0 ? ck[g] + 2 * N : nullptr, nullptr,
-                                                 std::min(a0, tiled::kRing)))
+                                                 std::min(a0, tiled::kRing), ck_ring && g > 0 ? 1 : 0))
                 return e;
             rec_steps += a1 - a0;
         }
@@ -979,6 +1000,8 @@ nefty_status run_adjoint(nefty_handle* h, const Prob& P, const void* alpha, cons
             ta.ystart = C.ystart;
             ta.extrap = P.extrap;
             ta.hist0 = std::min(adj_steps, tiled::kRing);
+            ta.carry = adj_steps > 0 ? 1 : 0;   // the launch before left the residual of step a1
+            ta.cflag = C.cflag + (P.nt + 1);
             ta.T = (float* const*)(dA_T + sg.aoff);
             ta.mu[0] = mu[0];
             ta.mu[1] = mu[1];

@@ -201,6 +201,53 @@ __device__ __forceinline__ DF df_div(DF x, DF y) {
 }
 __device__ __forceinline__ bool df_le(DF x, DF y) { return x.hi < y.hi || (x.hi == y.hi && x.lo <= y.lo); }
 
+// After the grid barrier of a grid sum: compute warp i sums value i of the
+// G CTA partials (every load of the warp first, then the fixed order: the
+// rows of a lane, then the warp tree), so all values take one round trip to
+// L2 at once; values i < NV as compensated pairs, the others (pout) in plain
+// FP32.  The totals reach thread 0 through shared memory.
+template <int NV, int NP>
+__device__ void sum_partials(const Sync& g, const float2* part, DF (&out)[NV], float* pout) {
+    static_assert(NV + NP <= CW && NV + NP <= kMaxRed, "one compute warp per value");
+    __shared__ float s_th[kMaxRed], s_tl[kMaxRed];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp < NV + NP) {
+        float2 v[kMaxGrid / 32];
+#pragma unroll
+        for (int r = 0; r < kMaxGrid / 32; ++r) {
+            const unsigned b = lane + 32u * r;
+            v[r] = b < g.G ? part[(size_t)b * kMaxRed + warp] : make_float2(0.f, 0.f);
+        }
+        float hi = 0.f, lo = 0.f;
+        if (warp < NV) {
+#pragma unroll
+            for (int r = 0; r < kMaxGrid / 32; ++r) {
+                float sh, e;
+                two_sum(hi, v[r].x, sh, e);
+                hi = sh;
+                lo = lo + v[r].y + e;
+            }
+            warp_sum2(hi, lo);
+        } else {
+#pragma unroll
+            for (int r = 0; r < kMaxGrid / 32; ++r) hi += v[r].x;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) hi += __shfl_xor_sync(0xffffffffu, hi, o);
+        }
+        if (lane == 0) {
+            s_th[warp] = hi;
+            s_tl[warp] = lo;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) out[i] = df_make(s_th[i], s_tl[i]);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) pout[i] = s_th[NV + i];
+    }
+}
+
 // Grid sum of NV compensated per-thread pairs.  The sums run on the FP32
 // pipes as (hi, lo) pairs, which keeps about twice the FP32 precision: TwoSum
 // trees over the warp, the CTA and the G CTA partials (fixed order, so every
@@ -210,7 +257,8 @@ __device__ __forceinline__ bool df_le(DF x, DF y) { return x.hi < y.hi || (x.hi 
 // Every pass ends here, so this is also where each thread orders its global
 // stores of the pass before the TMA reads of later passes.  after_barrier()
 // runs in every thread right after the grid barrier, before the partials are
-// summed (the copy thread starts the next pass's copies there).
+// summed (the copy thread starts the next pass's copies there).  Every thread
+// of the CTA takes part (sum_partials ends with a CTA barrier).
 template <int NV, class Hook>
 __device__ bool grid_sum(Sync& g, const Acc<NV>& in, DF (&out)[NV], Hook after_barrier) {
     __shared__ float s_h[NW][kMaxRed], s_l[NW][kMaxRed];
@@ -235,35 +283,7 @@ __device__ bool grid_sum(Sync& g, const Acc<NV>& in, DF (&out)[NV], Hook after_b
     }
     if (!barrier(g)) return false;
     after_barrier();
-    if (warp == 0) {
-        // in groups of up to four values: every load of a group first, then
-        // its compensated sums in a fixed order
-#pragma unroll
-        for (int i0 = 0; i0 < NV; i0 += 4) {
-            float2 v[kMaxGrid / 32][4];
-#pragma unroll
-            for (int r = 0; r < kMaxGrid / 32; ++r) {
-                const unsigned b = lane + 32u * r;
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    v[r][i] = (i0 + i < NV && b < g.G) ? part[(size_t)b * kMaxRed + i0 + i] : make_float2(0.f, 0.f);
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                if (i0 + i >= NV) break;
-                float hi = 0.f, lo = 0.f;
-#pragma unroll
-                for (int r = 0; r < kMaxGrid / 32; ++r) {
-                    float sh, e;
-                    two_sum(hi, v[r][i].x, sh, e);
-                    hi = sh;
-                    lo = lo + v[r][i].y + e;
-                }
-                warp_sum2(hi, lo);
-                out[i0 + i] = df_make(hi, lo);
-            }
-        }
-    }
+    sum_partials<NV, 0>(g, part, out, nullptr);
     g.red += 1;
     return true;
 }
@@ -311,42 +331,7 @@ __device__ bool grid_sum_p(Sync& g, const Acc<NV>& in, const float (&pin)[NP], D
     }
     if (!barrier(g)) return false;
     after_barrier();
-    if (warp == 0) {
-        // every load first, then the sums in a fixed order
-        float2 v[kMaxGrid / 32][NV];
-        float w[kMaxGrid / 32][NP];
-#pragma unroll
-        for (int r = 0; r < kMaxGrid / 32; ++r) {
-            const unsigned b = lane + 32u * r;
-#pragma unroll
-            for (int i = 0; i < NV; ++i)
-                v[r][i] = b < g.G ? part[(size_t)b * kMaxRed + i] : make_float2(0.f, 0.f);
-#pragma unroll
-            for (int i = 0; i < NP; ++i) w[r][i] = b < g.G ? part[(size_t)b * kMaxRed + NV + i].x : 0.f;
-        }
-#pragma unroll
-        for (int i = 0; i < NV; ++i) {
-            float hi = 0.f, lo = 0.f;
-#pragma unroll
-            for (int r = 0; r < kMaxGrid / 32; ++r) {
-                float sh, e;
-                two_sum(hi, v[r][i].x, sh, e);
-                hi = sh;
-                lo = lo + v[r][i].y + e;
-            }
-            warp_sum2(hi, lo);
-            out[i] = df_make(hi, lo);
-        }
-#pragma unroll
-        for (int i = 0; i < NP; ++i) {
-            float t = 0.f;
-#pragma unroll
-            for (int r = 0; r < kMaxGrid / 32; ++r) t += w[r][i];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            pout[i] = t;
-        }
-    }
+    sum_partials<NV, NP>(g, part, out, pout);
     g.red += 1;
     return true;
 }
@@ -495,7 +480,8 @@ enum PassKind : int {
     kInit1,   // 0 start hi, 1 start lo, 3 alpha, 4-5 p and delta (own boxes; delta = d when used)
     kInit2,   // 0 u_0, 3 alpha
     kGrad,    // 0 T hi, 1 T lo, 3 alpha, 4 mu hi, 5 mu lo
-    kJacobi   // 0-2 u, ws, ss of set 0 (u0 and the two sweep buffers), 3 alpha
+    kJacobi,  // 0-2 u, ws, ss of set 0 (u0 and the two sweep buffers), 3 alpha
+    kInitC    // 0 delta (= d), 3 alpha, 4 the carried residual sig[cur] (own box)
 };
 struct PassIn {
     int kind;
@@ -510,6 +496,7 @@ __device__ __forceinline__ unsigned pass_bytes(const PassIn& in) {
         case kInit1: return 3 * SZ_H + (in.hu > 0 ? 2 * SZ_O : 0);
         case kInit2: return 2 * SZ_H;
         case kJacobi: return 4 * SZ_H;
+        case kInitC: return 2 * SZ_H + SZ_O;
         default: return 5 * SZ_H;
     }
 }
@@ -656,6 +643,11 @@ __device__ bool produce(const Common& C, Ring& R, const PassIn& in, int from, in
                     tma_load4(dst, &M->uws[0], xh, yh, k, 0, bar);
                     tma_load3(dst + OFF_A, &M->alpha, xh, yh, k, bar);
                     break;
+                case kInitC:
+                    tma_load3(dst, &M->dh, xh, yh, k, bar);
+                    tma_load3(dst + OFF_A, &M->alpha, xh, yh, k, bar);
+                    tma_load4(dst + OFF_P, &M->sg, x0, y0, k, in.cur, bar);
+                    break;
                 default:
                     tma_load4(dst, &M->states, xh, yh, k, (int)in.zx, bar);
                     tma_load3(dst + OFF_A, &M->alpha, xh, yh, k, bar);
@@ -703,6 +695,7 @@ __device__ __forceinline__ const float* halo_src(const Common& C, const PassIn& 
         case kIter: return j < 3 ? C.v.u[in.cur] + (size_t)j * N : nullptr;
         case kJacobi: return j < 3 ? C.v.u[0] + (size_t)j * N : nullptr;
         case kInit2: return j == 0 ? C.v.u[0] : nullptr;
+        case kInitC: return j == 0 ? C.v.delta : nullptr;
         case kInit1: return j < 2 ? C.slab + (size_t)(in.zx + j) * N : nullptr;
         default:   // kGrad: T (hi, lo) in slots 0-1, mu (hi, lo) in slots 4-5, slot 2 unused
             if (j < 2) return C.slab + (size_t)(in.zx + j) * N;
@@ -1206,6 +1199,70 @@ struct Init2Body {
     }
 };
 
+// ---- init 1 from the carried residual: r0 = s - A d = g - (A - I) d with
+// g = s - d (carried from the solve before, see add_state) and d the
+// predicted increment (in delta, staged with its halo); (A - I) d in plain
+// FP32.  g and (A - I) d are small against d when the prediction is good and
+// the field smooth, and the rounding of r0 is relative to them, not to d.
+// u0 = M^{-1} r0; the sums (r0, u0), (r0, r0) join the carried ||b||^2 of
+// the state update.
+struct InitCBody {
+    const Common& C;
+    Acc<3>& acc;
+    float dm[QX], am[QX], dc[QX], ac[QX], dp[QX], ap[QX], czm[QX], czp[QX];
+    __device__ InitCBody(const Common& c, Acc<3>& a) : C(c), acc(a) {}
+    __device__ __forceinline__ void reset() { setq(dm, 0.f); setq(am, 0.f); setq(czm, 0.f); }
+    __device__ __forceinline__ void below(const unsigned char* st, int hb) {
+        ldq(st, sl(0), hb, dm);
+        ldq(st, sl(3), hb, am);
+    }
+    __device__ __forceinline__ void own(const unsigned char* st, int hb, bool has_below) {
+        ldq(st, sl(0), hb, dc);
+        ldq(st, sl(3), hb, ac);
+        if (has_below) {
+#pragma unroll
+            for (int j = 0; j < QX; ++j) czm[j] = face(ac[j], am[j], C.kz);
+        }
+    }
+    __device__ __forceinline__ void above(const unsigned char* st, int hb) {
+        ldq(st, sl(0), hb, dp);
+        ldq(st, sl(3), hb, ap);
+#pragma unroll
+        for (int j = 0; j < QX; ++j) czp[j] = face(ac[j], ap[j], C.kz);
+    }
+    __device__ __forceinline__ void top() { setq(dp, 0.f); setq(ap, 0.f); setq(czp, 0.f); }
+    __device__ __forceinline__ void plane(int k, unsigned c, bool valid, const unsigned char* st,
+                                          const unsigned char*, int hb, int ob) {
+        if (!valid) return;
+        float dym[QX], dyp[QX], sv[QX], cx[QX + 1], cyp[QX], cym[QX], u[QX], s1 = 0.f, s2 = 0.f;
+        ldq(st, sl(0), hb - HB, dym);
+        ldq(st, sl(0), hb + HB, dyp);
+        ldq(st, OFF_P, ob, sv);
+        const float dxl = lds1(st, sl(0), hb - 1), dxr = lds1(st, sl(0), hb + QX);
+        quad_faces(st, hb, ac, C.kx, C.ky, cx, cyp, cym);
+        const float rob = k + 1 == C.g.nz ? C.robin : 0.f;
+#pragma unroll
+        for (int j = 0; j < QX; ++j) {
+            const float f = dc[j];
+            const float fxm = j > 0 ? dc[j - 1] : dxl, fxp = j < QX - 1 ? dc[j + 1] : dxr;
+            const float cxp = cx[j + 1], cxm = cx[j];
+            const float Ld = cxp * (f - fxp) + cxm * (f - fxm) + cyp[j] * (f - dyp[j]) + cym[j] * (f - dym[j]) +
+                             czp[j] * (f - dp[j]) + czm[j] * (f - dm[j]) + rob * f;   // (A - I) d
+            const float r = sv[j] - Ld;
+            u[j] = rcp_approx(diag(cxp, cxm, cyp[j], cym[j], czp[j], czm[j], rob)) * r;
+            s1 += r * u[j];
+            s2 += r * r;
+        }
+        acc.add(1, s1);
+        acc.add(2, s2);
+        stgq(C.v.u[0] + c, u);
+    }
+    __device__ __forceinline__ void shift() {
+        cpyq(dm, dc); cpyq(czm, czp);
+        cpyq(dc, dp); cpyq(ac, ap);
+    }
+};
+
 // ---- one sweep of the paper's Jacobi inner solver (App. D.2, Eq. jacobi_iter)
 // on the increment delta = T - T^(0): the sweep T <- D^{-1}(b - R T) reads
 // delta' = u0 + D^{-1} sum_f c_f delta_q with u0 = D^{-1} r0 (slot 0) and
@@ -1508,12 +1565,34 @@ struct Start {
 // The last CG iteration of a solve, when its pass is left out: its whole
 // effect on the state is delta += a p with p = u (the first iteration) or
 // p = u + b p_prev, u = u[cur] and p_prev = p, which the state update applies
-// with the same arithmetic as an iteration pass (see solve()).
+// with the same arithmetic as an iteration pass (see solve()).  Without it
+// (apply == 0), cur is the set whose u holds the solve's last M^{-1} r.
 struct Final {
     int apply;
     float a, b;
     int first, cur;
 };
+
+// The start of a solve from the carried residual (on != 0): the residual at
+// a zero increment is in sig[sig], and (bh, bl) is this thread's part of
+// ||b||^2, summed by the state update that carried it.
+struct Carry {
+    int on, sig;
+    float bh, bl;
+};
+// When the next solve may start from the carried residual.  Carrying never
+// recomputes the residual from the state, so rounding made while it is
+// carried stays in it: the recursive residual of a solve drifts from the
+// true one by FP32 rounding relative to the residuals the solve went
+// through, about ||r0|| (measured: a surface pulse left a fixed error of
+// 1e-5 of its start residuals in every later carried step).  The next step
+// therefore forms its residual from the state (the error-free pass) when
+// this step started with ||r0|| > kCarryBound tol ||b|| (a transient: fewer
+// than one step in ten on the inversion workloads), and on every step that
+// is a multiple of kCarryRefresh, which bounds what the smaller roundings
+// add up to.
+constexpr float kCarryBound = 1000.f;
+constexpr int kCarryRefresh = 32;
 
 // ||D u_next||^2 for u_next = u - A (w + (B/A) t') expanded in the sums of the
 // pass that made u, w and t': rho = (r, r), q = (r.e, r.t, e.e, e.t, t.t) with
@@ -1539,7 +1618,8 @@ __device__ __forceinline__ float next_rho(float rho, float A, float B, float q0,
 // the pass's own sum up to rounding.
 template <int kMode, class RhsFn>
 __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, const Start& st0, RhsFn rhs,
-                      int* it_out, float* rel_out, bool* conv_out, Final* fin) {
+                      int* it_out, float* rel_out, bool* conv_out, Final* fin, const Carry& cy = Carry{0, 0, 0.f, 0.f},
+                      bool* big = nullptr) {
     constexpr bool kTma = kMode > 0, kWrap = kMode == 2, kPred = kTma;
     const Geo& g = C.g;
     Pipe pp = pipe_none();
@@ -1547,10 +1627,18 @@ __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, co
     // ---- init 1: r0 = e - d - (A - I) y, u0 = M^{-1} r0 ; bb, (r0,u0), (r0,r0)
     Acc<3> acc3;
     if constexpr (kTma) {
-        PassIn in{kInit1, 0, false, 0u, 0u, st0.hu};
-        if (!slab_half(C, st0.y, &in.zx)) return false;
-        Init1Body<RhsFn> B(C, rhs, acc3, st0.hu);
-        if (!staged<kWrap>(C, ring, in, B, pre.n, pre.ok)) return false;
+        if (cy.on) {   // r0 = s - A d from the carried residual
+            const PassIn in{kInitC, cy.sig, false, 0u, 0u, 0};
+            acc3.h[0] = cy.bh;
+            acc3.l[0] = cy.bl;
+            InitCBody B(C, acc3);
+            if (!staged<kWrap>(C, ring, in, B, pre.n, pre.ok)) return false;
+        } else {
+            PassIn in{kInit1, 0, false, 0u, 0u, st0.hu};
+            if (!slab_half(C, st0.y, &in.zx)) return false;
+            Init1Body<RhsFn> B(C, rhs, acc3, st0.hu);
+            if (!staged<kWrap>(C, ring, in, B, pre.n, pre.ok)) return false;
+        }
     } else {
         const unsigned N = g.S * (unsigned)g.nz;
         const float* __restrict__ yh = st0.y;
@@ -1591,7 +1679,7 @@ __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, co
     // barrier between the two passes (u0 complete, its stores ordered before
     // the copies of the next pass), one reduction after both.
     __shared__ float s_a, s_b;
-    __shared__ int s_go, s_fin;
+    __shared__ int s_go, s_fin, s_big;
     asm volatile("fence.proxy.async.global;" ::: "memory");
     if (!barrier(sy)) return false;
     // ---- init 2: ws0 = M^{-1} A u0 ; (A u0, u0)
@@ -1641,8 +1729,12 @@ __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, co
     const DF bb = t4[0], lim = df_mul(DF{C.tol2_hi, C.tol2_lo}, bb);
     DF gam = t4[1], rho = t4[2];
     int it = 0;
-    if (threadIdx.x == 0) s_go = (!df_le(rho, lim) && C.max_iter > 0) ? 1 : 0;
+    if (threadIdx.x == 0) {
+        s_go = (!df_le(rho, lim) && C.max_iter > 0) ? 1 : 0;
+        s_big = rho.hi > kCarryBound * kCarryBound * lim.hi ? 1 : 0;   // a transient (see kCarryBound)
+    }
     __syncthreads();
+    if (big) *big = s_big != 0;
     if (!s_go) {
         if constexpr (kTma) {
             if (!pipe_cancel(C, ring, pp)) return false;
@@ -1731,6 +1823,8 @@ __device__ bool solve(const Common& C, Sync& sy, Ring& ring, const Pipe& pre, co
                     if (s_fin) {   // the next iteration is the last: its update goes to the state update
                         *fin = Final{1, s_a, s_b, 0, cur};
                         ++it;
+                    } else {
+                        fin->cur = cur;
                     }
                     break;
                 }
@@ -1824,6 +1918,8 @@ __device__ __forceinline__ void prefetch_maps(const TmaMaps& M) {
     tma_prefetch_desc(&M.alpha);
     tma_prefetch_desc(&M.pd);
     tma_prefetch_desc(&M.states);
+    tma_prefetch_desc(&M.dh);
+    tma_prefetch_desc(&M.sg);
 }
 
 __device__ __forceinline__ Sync make_sync(DevCtl* ctl, double* partials, int bar_sel = 0) {
@@ -1872,6 +1968,30 @@ __device__ __forceinline__ float4 ld_older(const float* p, unsigned i, bool use)
     return use ? reinterpret_cast<const float4*>(p)[i] : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// The carried residual (TMA-staged PCG).  With s^m = b^m - A x0^m, the
+// residual of step m's system at a zero increment, and r^m = s^m - A delta^m
+// the residual the solve ends with (r^m = D u, u the CG's last M^{-1} r),
+// the next step's system (x0 <- x0 + delta, b = x0 + e) gives exactly
+//   s^{next} = r^m + delta^m + (e^{next} - e^m)
+// (A is the same for every step of a sweep).  The state update forms, at
+// each cell, g = s^{next} - d^{next} = (r^m + (e^{next} - e^m)) + (delta^m -
+// d^{next}) with d^{next} the next predicted increment, so the next solve
+// needs no error-free pass over the state: its start residual is
+// r0 = g - (A - I) d (InitCBody).  Both parts of g are small (a residual and
+// the error of the prediction, formed from two close numbers), so their
+// rounding is far below that of delta itself; the rounding of r^m (FP32,
+// relative to the residuals of the solve) stays in s, well below the solve's
+// tolerance, which is relative to ||b||.
+// Forcing e of a step at a cell: the source plane of the sweep holds it, every
+// other cell has none.
+struct CarryOut {
+    float* sig;            // g = s^{next} - d^{next} (written)
+    const float* diag;     // D
+    const float* u;        // u of the solve's last set
+    const float* ws;       // ws and ss of that set (a folded last iteration only)
+    const float* ss;
+};
+
 // End of a solve, by every thread of the grid (quads when N % 4 == 0):
 //   y = x + delta as compensated pairs (hi in [0, N), lo in [N, 2N)), the new state;
 //   rd = delta, the ring slot of this step's increment;
@@ -1882,10 +2002,18 @@ __device__ __forceinline__ float4 ld_older(const float* p, unsigned i, bool use)
 // fin (when fin.apply): the solve's last iteration, whose pass was left out,
 // is applied first: delta += a p with p = u[fin.cur] (+ b p_prev), the same
 // fused multiply-adds as an iteration pass.
+// co (quads only): the next solve starts from the carried residual instead:
+// co->sig = g (ecur, enext: the forcing of this step and the next at a cell;
+// d with hu_next increments, which must be the count the next step uses
+// even when another launch runs it), delta = d (0 when it does not
+// predict), no ys; (bh, bl) = this thread's part of ||y + e^{next}||^2, the
+// next solve's ||b||^2, summed quad by quad in the order of the quads
+// (prepare_carried sums the same way).
+template <class EFn>
 __device__ void add_state(const float* __restrict__ x, float* __restrict__ delta, float* __restrict__ y,
                           unsigned N, float* __restrict__ rd, const Older& old, int hu_next,
-                          float* __restrict__ ys, bool stream_y, const Final& fin = Final{0, 0.f, 0.f, 0, 0},
-                          const Vecs* vv = nullptr) {
+                          float* __restrict__ ys, bool stream_y, const Final& fin, const Vecs* vv,
+                          const CarryOut* co, EFn ecur, EFn enext, float& bh, float& bl) {
     const unsigned stride = cta_count() * NT, t0 = cta_id() * NT + threadIdx.x;
     const bool fa = fin.apply && vv;
     const float* __restrict__ fu = fa ? vv->u[fin.cur] : nullptr;
@@ -1893,6 +2021,7 @@ __device__ void add_state(const float* __restrict__ x, float* __restrict__ delta
     auto last = [&](float dv, float uv, float pv) {   // delta + a (u or u + b p)
         return fmaf(fin.a, fin.first ? uv : fmaf(fin.b, pv, uv), dv);
     };
+    bh = bl = 0.f;
     if ((N & 3u) == 0) {
         // Batches of two quads per thread: every load of a batch is issued
         // before its stores.  x (the old state) is not read again soon, so it
@@ -1913,10 +2042,15 @@ __device__ void add_state(const float* __restrict__ x, float* __restrict__ delta
         float4* __restrict__ sh4 = reinterpret_cast<float4*>(ys);
         float4* __restrict__ sl4 = reinterpret_cast<float4*>(ys + N);
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4* __restrict__ fu4 = reinterpret_cast<const float4*>(fu);
+        const float4* __restrict__ fu4 = reinterpret_cast<const float4*>(co ? co->u : fu);
         const float4* __restrict__ fp4 = reinterpret_cast<const float4*>(fp);
+        const float4* __restrict__ cw4 = reinterpret_cast<const float4*>(co && fa ? co->ws : nullptr);
+        const float4* __restrict__ cs4 = reinterpret_cast<const float4*>(co && fa ? co->ss : nullptr);
+        const float4* __restrict__ dg4 = reinterpret_cast<const float4*>(co ? co->diag : nullptr);
+        float4* __restrict__ sg4 = reinterpret_cast<float4*>(co ? co->sig : nullptr);
+        Acc<1> bb;
         for (unsigned i0 = t0; i0 < N4; i0 += B * stride) {
-            float4 h[B], l[B], e[B], o1[B], o2[B], o3[B];
+            float4 h[B], l[B], e[B], o1[B], o2[B], o3[B], uf[B], dg[B];
 #pragma unroll
             for (int u = 0; u < B; ++u) {
                 const unsigned i = i0 + u * stride;
@@ -1927,10 +2061,18 @@ __device__ void add_state(const float* __restrict__ x, float* __restrict__ delta
                 o1[u] = in && hu_next > 1 ? o1p[i] : z4;
                 o2[u] = in && hu_next > 2 ? o2p[i] : z4;
                 o3[u] = in && hu_next > 3 ? o3p[i] : z4;
+                uf[u] = in && (fa || co) ? fu4[i] : z4;
+                dg[u] = in && co ? dg4[i] : z4;
                 if (fa && in) {
-                    const float4 uu = fu4[i], pq = fin.first ? z4 : fp4[i];
+                    const float4 uu = uf[u], pq = fin.first ? z4 : fp4[i];
                     e[u] = make_float4(last(e[u].x, uu.x, pq.x), last(e[u].y, uu.y, pq.y), last(e[u].z, uu.z, pq.z),
                                        last(e[u].w, uu.w, pq.w));
+                    if (co) {   // the last u: u - a (ws + b ss), as an iteration pass forms it
+                        const float4 w = cw4[i], sv = fin.first ? z4 : cs4[i];
+                        const Step S{fin.a, fin.b, fin.first != 0};
+                        uf[u] = make_float4(S.next(uu.x, S.sdir(w.x, sv.x)), S.next(uu.y, S.sdir(w.y, sv.y)),
+                                            S.next(uu.z, S.sdir(w.z, sv.z)), S.next(uu.w, S.sdir(w.w, sv.w)));
+                    }
                 }
             }
 #pragma unroll
@@ -1950,11 +2092,33 @@ __device__ void add_state(const float* __restrict__ x, float* __restrict__ delta
                     yl[i] = ol;
                 }
                 r4[i] = e[u];
-                if (hu_next > 0) {
-                    const float4 dn = make_float4(predict(hu_next, e[u].x, o1[u].x, o2[u].x, o3[u].x),
-                                                  predict(hu_next, e[u].y, o1[u].y, o2[u].y, o3[u].y),
-                                                  predict(hu_next, e[u].z, o1[u].z, o2[u].z, o3[u].z),
-                                                  predict(hu_next, e[u].w, o1[u].w, o2[u].w, o3[u].w));
+                float4 dn = z4;
+                if (hu_next > 0)
+                    dn = make_float4(predict(hu_next, e[u].x, o1[u].x, o2[u].x, o3[u].x),
+                                     predict(hu_next, e[u].y, o1[u].y, o2[u].y, o3[u].y),
+                                     predict(hu_next, e[u].z, o1[u].z, o2[u].z, o3[u].z),
+                                     predict(hu_next, e[u].w, o1[u].w, o2[u].w, o3[u].w));
+                if (co) {
+                    // g = (r + (e^{next} - e)) + (delta - d^{next})
+                    const unsigned c = 4u * i;
+                    const float en[4] = {enext(c), enext(c + 1), enext(c + 2), enext(c + 3)};
+                    const float ec[4] = {ecur(c), ecur(c + 1), ecur(c + 2), ecur(c + 3)};
+                    const float dgv[4] = {dg[u].x, dg[u].y, dg[u].z, dg[u].w};
+                    const float ufv[4] = {uf[u].x, uf[u].y, uf[u].z, uf[u].w};
+                    const float ev[4] = {e[u].x, e[u].y, e[u].z, e[u].w};
+                    const float dnv[4] = {dn.x, dn.y, dn.z, dn.w};
+                    const float ohv[4] = {oh.x, oh.y, oh.z, oh.w}, olv[4] = {ol.x, ol.y, ol.z, ol.w};
+                    float sv[4], q = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        sv[j] = (dgv[j] * ufv[j] + (en[j] - ec[j])) + (ev[j] - dnv[j]);
+                        const float b = (ohv[j] + olv[j]) + en[j];
+                        q += b * b;
+                    }
+                    bb.add(0, q);
+                    sg4[i] = make_float4(sv[0], sv[1], sv[2], sv[3]);
+                    d4[i] = dn;
+                } else if (hu_next > 0) {
                     float4 sh, sl;
                     add_pair(oh.x, ol.x, dn.x, sh.x, sl.x);
                     add_pair(oh.y, ol.y, dn.y, sh.y, sl.y);
@@ -1966,7 +2130,9 @@ __device__ void add_state(const float* __restrict__ x, float* __restrict__ delta
                 }
             }
         }
-    } else {
+        bh = bb.h[0];
+        bl = bb.l[0];
+    } else {   // plain-load path only (the staged path needs nx % 4 == 0)
         for (unsigned c = t0; c < N; c += stride) {
             const float e = fa ? last(delta[c], fu[c], fin.first ? 0.f : fp[c]) : delta[c];
             float oh, ol;
@@ -1983,6 +2149,63 @@ __device__ void add_state(const float* __restrict__ x, float* __restrict__ delta
         }
     }
     asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// The start of a launch's first solve from the carried residual (the
+// previous step ran in another launch): delta = d = predict(rn and the
+// hu - 1 increments before it) or 0, and (bh, bl) = this thread's part of
+// ||x + e||^2, with the loop and arithmetic of add_state's carried path, so a
+// launch resumed here starts from the same bits as one that ran through.
+template <class EFn>
+__device__ void prepare_carried(const float* __restrict__ x, const float* __restrict__ rn, const Older& old, int hu,
+                                float* __restrict__ delta, unsigned N, EFn ecur, float& bh, float& bl) {
+    const unsigned stride = cta_count() * NT, t0 = cta_id() * NT + threadIdx.x;
+    const unsigned N4 = N >> 2;
+    const float4* __restrict__ xh = reinterpret_cast<const float4*>(x);
+    const float4* __restrict__ xl = reinterpret_cast<const float4*>(x + N);
+    const float4* __restrict__ r4 = reinterpret_cast<const float4*>(rn);
+    const float4* __restrict__ o1p = reinterpret_cast<const float4*>(old.r[0]);
+    const float4* __restrict__ o2p = reinterpret_cast<const float4*>(old.r[1]);
+    const float4* __restrict__ o3p = reinterpret_cast<const float4*>(old.r[2]);
+    float4* __restrict__ d4 = reinterpret_cast<float4*>(delta);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    Acc<1> bb;
+    for (unsigned i = t0; i < N4; i += stride) {
+        float4 dn = z4;
+        if (hu > 0) {
+            const float4 e = r4[i], o1 = hu > 1 ? o1p[i] : z4, o2 = hu > 2 ? o2p[i] : z4, o3 = hu > 3 ? o3p[i] : z4;
+            dn = make_float4(predict(hu, e.x, o1.x, o2.x, o3.x), predict(hu, e.y, o1.y, o2.y, o3.y),
+                             predict(hu, e.z, o1.z, o2.z, o3.z), predict(hu, e.w, o1.w, o2.w, o3.w));
+        }
+        d4[i] = dn;
+        const float4 h = xh[i], l = xl[i];
+        const unsigned c = 4u * i;
+        const float hv[4] = {h.x, h.y, h.z, h.w}, lv[4] = {l.x, l.y, l.z, l.w};
+        float q = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float b = (hv[j] + lv[j]) + ecur(c + j);
+            q += b * b;
+        }
+        bb.add(0, q);
+    }
+    bh = bb.h[0];
+    bl = bb.l[0];
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// The diagonal of A at every cell (plain loads, every thread of the grid),
+// for the carried residual: the same face values and sum as the passes.
+__device__ void write_diag(const Common& C) {
+    const Geo& g = C.g;
+    const unsigned stride = cta_count() * NT, t0 = cta_id() * NT + threadIdx.x, N = g.S * (unsigned)g.nz;
+    for (unsigned c = t0; c < N; c += stride) {
+        const int k = (int)(c / g.S), y = (int)((c % g.S) / (unsigned)g.nx), x = (int)(c % (unsigned)g.nx);
+        const Nb n = neighbours(g, c, x, y, k);
+        float cf[6];
+        cell_faces(C, n, C.alpha[c], cf);
+        C.v.diag[c] = diag(cf[0], cf[1], cf[2], cf[3], cf[4], cf[5], k + 1 == g.nz ? C.robin : 0.f);
+    }
 }
 
 // The start of a launch's first solve when it predicts (the previous step ran
@@ -2005,19 +2228,51 @@ __device__ void prepare_start(const float* __restrict__ x, const float* __restri
 // A checkpoint's increment history: dst[i N, (i + 1) N) = the increment of
 // step m - i (forward; m + i adjoint is not needed), i < h; every thread of
 // the grid.  load_hist is the inverse at a launch start.
-__device__ void save_hist(float* __restrict__ dst, const IncRing& R, int m, int h) {
+// sig (or null): the carried residual of step m + 1, kept after the increments.
+__device__ void save_hist(float* __restrict__ dst, const IncRing& R, int m, int h, const float* sig) {
     const unsigned stride = cta_count() * NT, t0 = cta_id() * NT + threadIdx.x, N = R.N;
     for (int k = 0; k < h; ++k) {
         const float* src = R.slot(m - k);
         for (unsigned i = t0; i < N; i += stride) dst[(size_t)k * N + i] = src[i];
     }
+    if (sig)
+        for (unsigned i = t0; i < N; i += stride) dst[(size_t)h * N + i] = sig[i];
 }
-__device__ void load_hist(const float* __restrict__ src, const IncRing& R, int m, int h) {
+__device__ void load_hist(const float* __restrict__ src, const IncRing& R, int m, int h, float* sig) {
     const unsigned stride = cta_count() * NT, t0 = cta_id() * NT + threadIdx.x, N = R.N;
     for (int k = 0; k < h; ++k) {
         float* dst = R.slot(m - k);
         for (unsigned i = t0; i < N; i += stride) dst[i] = src[(size_t)k * N + i];
     }
+    if (sig)
+        for (unsigned i = t0; i < N; i += stride) sig[i] = src[(size_t)h * N + i];
+}
+
+// Forcing of a forward step at a cell: the surface flux of the step on plane 0.
+struct FwdForce {
+    const float* q;        // the step's flux map, or null
+    float sc;
+    unsigned S;
+    __device__ __forceinline__ float operator()(unsigned c) const { return (q && c < S) ? sc * q[c] : 0.f; }
+};
+__device__ __forceinline__ FwdForce fwd_force(const FwdTiled& a, int n) {
+    const unsigned S = a.c.g.S;
+    const float* q = a.q_full ? a.q_full + (size_t)n * S : (n < a.q_steps ? a.q_face : nullptr);
+    return FwdForce{q, a.src_scale, S};
+}
+// Forcing of an adjoint step n at a cell: the surface misfit of T^n.
+struct AdjForce {
+    const float* T;        // T^n (pair), or null
+    const float* ob;       // its target frame
+    unsigned o0, S, N;
+    float gs;
+    __device__ __forceinline__ float operator()(unsigned c) const {
+        return (T && c - o0 < S) ? gs * ((T[c] - ob[c - o0]) + T[N + c]) : 0.f;
+    }
+};
+__device__ __forceinline__ AdjForce adj_force(const AdjTiled& a, int n) {
+    const unsigned S = a.c.g.S, N = S * (unsigned)a.c.g.nz;
+    return AdjForce{a.T[n - a.n0], a.obs + (size_t)(n - 1) * S, a.obs_off, S, N, a.g_scale};
 }
 
 // ------------------------------------------------------------- forward
@@ -2038,13 +2293,28 @@ __device__ __forceinline__ void forward_sweep(const FwdTiled& a) {
     const unsigned c0 = cta_id() * NT + threadIdx.x;
     double loss = 0.0;
     Pipe pre = pipe_none();
+    // the carried residual (TMA-staged PCG, when the workspace has it)
+    const bool carry_on = kTma && !kJac && a.c.v.diag != nullptr;
+    if (carry_on) write_diag(a.c);
     // increments used by the start of step n (ring slot m holds delta^m)
     auto hu_at = [&](int n) { return min(a.extrap, min(a.hist0 + (n - a.n0), kRing)); };
     const IncRing ring_d{a.ring, N};
     // increments of steps n0-1, n0-2, ... from a checkpoint (recompute
-    // launches), copied by the same threads that read them below
-    if (a.ring_load) load_hist(a.ring_load, ring_d, a.n0 - 1, a.extrap);
-    if (hu_at(a.n0) > 0) {
+    // launches), copied by the same threads that read them in prepare_start
+    const bool carried0 = carry_on && a.carry && a.n0 > 0 && a.cflag && a.cflag[a.n0];
+    if (a.ring_load) {
+        load_hist(a.ring_load, ring_d, a.n0 - 1, a.extrap, carried0 ? a.c.v.sig[0] : nullptr);
+        // prepare_carried reads them by quads, other threads than the copy's
+        if (carried0 && !barrier(sy)) return;
+    }
+    float bh = 0.f, bl = 0.f;   // this thread's part of the next solve's ||b||^2 (carried)
+    bool carried = false;
+    if (carried0) {
+        prepare_carried(a.src[0], ring_d.slot(a.n0 - 1), older(ring_d, a.n0 - 1, -1), hu_at(a.n0), a.c.v.delta, N,
+                        fwd_force(a, a.n0), bh, bl);
+        if (!barrier(sy)) return;
+        carried = true;
+    } else if (hu_at(a.n0) > 0) {
         prepare_start(a.src[0], ring_d.slot(a.n0 - 1), older(ring_d, a.n0 - 1, -1), hu_at(a.n0), a.c.v.delta,
                       a.ystart, N);
         if (!barrier(sy)) return;
@@ -2059,6 +2329,7 @@ __device__ __forceinline__ void forward_sweep(const FwdTiled& a) {
         float rel = 0.f;
         bool conv = true;
         Final fin{0, 0.f, 0.f, 0, 0};
+        bool big = true;
         const int hu = hu_at(n);
         auto rhs = [=](unsigned c, int k) { return (qmap && k == 0) ? sc * qmap[c] : 0.f; };
         bool ok;
@@ -2066,7 +2337,8 @@ __device__ __forceinline__ void forward_sweep(const FwdTiled& a) {
             ok = solve_jacobi<kMode>(a.c, sy, ring, pre, Start{Tn, 0}, rhs, a.c.jacobi_k);
             it = a.c.jacobi_k;
         } else {
-            ok = solve<kMode>(a.c, sy, ring, pre, Start{hu > 0 ? a.ystart : Tn, hu}, rhs, &it, &rel, &conv, &fin);
+            ok = solve<kMode>(a.c, sy, ring, pre, Start{hu > 0 ? a.ystart : Tn, hu}, rhs, &it, &rel, &conv, &fin,
+                              Carry{carried ? 1 : 0, 0, bh, bl}, &big);
         }
         if (!ok) return;
         if (cta_id() == 0 && threadIdx.x == 0) {
@@ -2076,18 +2348,28 @@ __device__ __forceinline__ void forward_sweep(const FwdTiled& a) {
             if (fin.apply) atomicAdd(&a.c.ctl->folded, 1);
         }
         // T^{n+1} = T^n + delta as a compensated pair, delta^n into the ring, and
-        // the start of step n+1 when it predicts
-        const int hu1 = n + 1 < a.n1 ? hu_at(n + 1) : 0;
-        add_state(Tn, a.c.v.delta, Tn1, N, ring_d.slot(n), older(ring_d, n, -1), hu1, a.ystart, true, fin, &a.c.v);
+        // the start of step n+1 when it predicts (carried: the residual of step
+        // n+1, also at the end of a launch that another one continues; the
+        // choice is kept per step for launches that resume there)
+        carried = carry_on && n + 1 < a.n_end && !big && (n + 1) % kCarryRefresh != 0;
+        if (carry_on && cta_id() == 0 && threadIdx.x == 0 && n + 1 < a.n_end) a.cflag[n + 1] = carried ? 1 : 0;
+        const int hu1 = n + 1 < (carried ? a.n_end : a.n1) ? hu_at(n + 1) : 0;
+        const CarryOut co{a.c.v.sig[0], a.c.v.diag, a.c.v.u[fin.cur], a.c.v.ws[fin.cur], a.c.v.ss[fin.cur]};
+        add_state(Tn, a.c.v.delta, Tn1, N, ring_d.slot(n), older(ring_d, n, -1), hu1, a.ystart, true, fin, &a.c.v,
+                  carried ? &co : nullptr, fwd_force(a, n), fwd_force(a, carried ? n + 1 : n), bh, bl);
         if (!barrier(sy)) return;
-        if (a.ring_save && a.ring_save[n - a.n0])   // a checkpoint keeps [delta^n; delta^{n-1}; ...]
-            save_hist(a.ring_save[n - a.n0], ring_d, n, a.extrap);
+        if (a.ring_save && a.ring_save[n - a.n0])   // a checkpoint keeps [delta^n; delta^{n-1}; ...] (+ s^{n+1})
+            save_hist(a.ring_save[n - a.n0], ring_d, n, a.extrap, carried ? a.c.v.sig[0] : nullptr);
         pre = pipe_none();
         if constexpr (kTma) {   // the next step's first pass, behind the frame below
             if (n + 1 < a.n1) {
-                PassIn in{kInit1, 0, false, 0u, 0u, hu1};
-                if (!slab_half(a.c, hu1 > 0 ? a.ystart : a.src[n + 1 - a.n0], &in.zx)) return;
-                pre = pipe_start(a.c, ring, in);
+                if (carried) {
+                    pre = pipe_start(a.c, ring, PassIn{kInitC, 0, false, 0u, 0u, 0});
+                } else {
+                    PassIn in{kInit1, 0, false, 0u, 0u, hu1};
+                    if (!slab_half(a.c, hu1 > 0 ? a.ystart : a.src[n + 1 - a.n0], &in.zx)) return;
+                    pre = pipe_start(a.c, ring, in);
+                }
             }
         }
         if (a.frames || a.obs) {
@@ -2127,10 +2409,20 @@ __device__ __forceinline__ void adjoint_sweep(const AdjTiled& a) {
     const unsigned c0 = cta_id() * NT + threadIdx.x;
     (void)stride;
     (void)c0;
+    // the carried residual (TMA-staged PCG, when the workspace has it)
+    const bool carry_on = kTma && !kJac && a.c.v.diag != nullptr;
+    if (carry_on) write_diag(a.c);
     // increments used by the start of step n (ring slot m holds mu^m - mu^{m+1})
     auto hu_at = [&](int n) { return min(a.extrap, min(a.hist0 + (a.n1 - n), kRing)); };
     const IncRing ring_d{a.ring, N};
-    if (hu_at(a.n1) > 0) {
+    float bh = 0.f, bl = 0.f;   // this thread's part of the next solve's ||b||^2 (carried)
+    bool carried = false;
+    if (carry_on && a.carry && a.cflag && a.cflag[a.n1]) {
+        prepare_carried(a.mu[(a.n1 + 1) & 1], ring_d.slot(a.n1 + 1), older(ring_d, a.n1 + 1, 1), hu_at(a.n1),
+                        a.c.v.delta, N, adj_force(a, a.n1), bh, bl);
+        if (!barrier(sy)) return;
+        carried = true;
+    } else if (hu_at(a.n1) > 0) {
         prepare_start(a.mu[(a.n1 + 1) & 1], ring_d.slot(a.n1 + 1), older(ring_d, a.n1 + 1, 1), hu_at(a.n1),
                       a.c.v.delta, a.ystart, N);
         if (!barrier(sy)) return;
@@ -2144,6 +2436,7 @@ __device__ __forceinline__ void adjoint_sweep(const AdjTiled& a) {
         float rel = 0.f;
         bool conv = true;
         Final fin{0, 0.f, 0.f, 0, 0};
+        bool big = true;
         const int hu = hu_at(n);
         const unsigned o0 = a.obs_off;
         auto rhs = [=](unsigned c, int) {
@@ -2155,7 +2448,7 @@ __device__ __forceinline__ void adjoint_sweep(const AdjTiled& a) {
             it = a.c.jacobi_k;
         } else {
             ok = solve<kMode>(a.c, sy, ring, pipe_none(), Start{hu > 0 ? a.ystart : mnext, hu}, rhs, &it, &rel,
-                             &conv, &fin);
+                              &conv, &fin, Carry{carried ? 1 : 0, 1, bh, bl}, &big);
         }
         if (!ok) return;
         if (cta_id() == 0 && threadIdx.x == 0) {
@@ -2164,8 +2457,16 @@ __device__ __forceinline__ void adjoint_sweep(const AdjTiled& a) {
             if (!conv) atomicAdd(&a.c.ctl->notconv, 1);
             if (fin.apply) atomicAdd(&a.c.ctl->folded, 1);
         }
-        add_state(mnext, a.c.v.delta, mu, N, ring_d.slot(n), older(ring_d, n, 1), n - 1 > a.n0 ? hu_at(n - 1) : 0,
-                  a.ystart, false, fin, &a.c.v);
+        // mu^n = mu^{n+1} + delta; carried: the residual of step n - 1 (the
+        // last adjoint step is n = 1), also at the end of a launch that
+        // another one continues
+        carried = carry_on && n - 1 >= 1 && !big && (n - 1) % kCarryRefresh != 0;
+        if (carry_on && cta_id() == 0 && threadIdx.x == 0 && n - 1 >= 1) a.cflag[n - 1] = carried ? 1 : 0;
+        const CarryOut co{a.c.v.sig[1], a.c.v.diag, a.c.v.u[fin.cur], a.c.v.ws[fin.cur], a.c.v.ss[fin.cur]};
+        add_state(mnext, a.c.v.delta, mu, N, ring_d.slot(n), older(ring_d, n, 1),
+                  (carried || n - 1 > a.n0) ? hu_at(n - 1) : 0,
+                  a.ystart, false, fin, &a.c.v, carried ? &co : nullptr, adj_force(a, n),
+                  adj_force(a, carried ? n - 1 : n), bh, bl);
         if (!barrier(sy)) return;
         // gradient of step n with mu^n and T^n (the next step writes only the
         // other mu buffer and the CG vectors, so no barrier is needed after it)
@@ -2387,7 +2688,8 @@ bool tiled_encode_maps(tiled::TmaMaps* M, const tiled::Geo& g, const tiled::Vecs
     bool ok = true;
     for (int i = 0; i < 2; ++i) ok = ok && make(&M->uws[i], v.u[i], HB, HR, 3, 3);
     ok = ok && make(&M->u0, v.u[0], HB, HR, 0, 1) && make(&M->alpha, alpha, HB, HR, 0, 1) &&
-         make(&M->pd, v.p, tiled::TX, tiled::TY, 2, 2) && make(&M->states, slab, HB, HR, slab_halves, 2);
+         make(&M->pd, v.p, tiled::TX, tiled::TY, 2, 2) && make(&M->states, slab, HB, HR, slab_halves, 2) &&
+         make(&M->dh, v.delta, HB, HR, 0, 1) && make(&M->sg, v.sig[0], tiled::TX, tiled::TY, 2, 1);
     return ok;
 }
 

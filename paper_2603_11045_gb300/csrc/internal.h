@@ -172,6 +172,13 @@ struct Vecs {
     float* ss[2];          // M^{-1} A p      (= u[i] + 2N)
     float* p;
     float* delta;          // increment of the current solve (= p + N)
+    // Carried residual (TMA-staged PCG): the residual of each solve at a zero
+    // increment, s = b - A x0, follows from the solve before it (see
+    // cg_tiled.cu); sig[0] carries it through a forward sweep, sig[1] through
+    // an adjoint sweep (contiguous, sig[1] = sig[0] + N).  diag: the diagonal
+    // of A, written at the start of every such launch.
+    float* sig[2];
+    float* diag;
 };
 
 // TMA descriptors of the staged passes (tiled FP32 path).  They travel by
@@ -185,6 +192,8 @@ struct TmaMaps {
     CUtensorMap pd;        // p, delta (2 x N floats, contiguous): 4D, box 32 x 32 x 1 x 2 at (x0, y0, k, 0)
     CUtensorMap states;    // the state slab as 4D (x, y, z, halves): box 40 x 34 x 1 x 2 at
                            //   (x0-4, y0-1, k, h) reads the hi and lo halves of the state at half h
+    CUtensorMap dh;        // delta alone: box 40 x 34 x 1 at (x0-4, y0-1, k)
+    CUtensorMap sg;        // sig[0], sig[1] (2 x N floats, contiguous): 4D, box 32 x 32 x 1 x 1 at (x0, y0, k, i)
 };
 
 struct Common {
@@ -228,7 +237,15 @@ struct FwdTiled {
     int extrap;               // 0 .. kRing
     int hist0;                // increments valid at launch start (steps n0-1, n0-2, ...)
     const float* ring_load;   // [delta^{n0-1}; delta^{n0-2}; ...] (extrap of them) copied in at launch start, or null
+                              //   (+ the carried residual of step n0 after them when carry)
     float* const* ring_save;  // per step n (index n - n0), after T^{n+1}: [delta^n; delta^{n-1}; ...] or null
+                              //   (+ the carried residual of step n + 1 after them when the sweep carries it)
+    int carry;                // 1: the carried residual of step n0 is valid at launch start (in sig[0], or in
+                              //   ring_load when that is given) if cflag[n0] says step n0 uses it; 0: step n0
+                              //   forms its residual from the state
+    int* cflag;               // [n_end] per step n: 1 if step n starts from the carried residual (written by
+                              //   the step before, read by a launch that resumes at n)
+    int n_end;                // steps of the whole sweep (the forcing of step n exists for n < n_end)
     float* const* src;
     float* const* dst;
     const float* q_face; int q_steps; const float* q_full;
@@ -247,6 +264,8 @@ struct AdjTiled {
     float* ystart;            // as FwdTiled::ystart
     int extrap;
     int hist0;                // increments valid at launch start (steps n1+1, n1+2, ...)
+    int carry;                // 1: the carried residual of step n1 is valid in sig[1] at launch start
+    int* cflag;               // as FwdTiled::cflag, per adjoint step (index n)
     float* const* T;
     float* mu[2];
     const float* alpha;
