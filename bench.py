@@ -488,7 +488,8 @@ def run_native(args):
                 "cpu_baseline": cpu, "clocks": clk,
                 "solver_stats": {k: stats[-1][k] for k in ("fwd_iters", "adj_iters", "recompute_iters",
                                                            "max_step_iters", "max_rel_residual",
-                                                           "ckpt_every", "grid_blocks", "workspace_bytes")}}
+                                                           "ckpt_every", "grid_blocks", "workspace_bytes",
+                                                           "folded_last_iters", "carried_solves")}}
         print(json.dumps(line), flush=True)
     solver.close()
     if world > 1:

@@ -98,6 +98,14 @@ typedef struct {
                               sweeps T <- D^-1 (b - R T) per solve from the warm start T^n (the
                               adjoint from mu^(n+1)), with no stopping test and no extrapolation;
                               rtol, max_iter and extrap are then ignored.  At most 100000. */
+    int32_t residual;      /* start residual of each FP32 solve on the TMA-staged kernels: 0 = default
+                              (1); 1 = carried: the state update of each step forms the next step's
+                              residual at a zero increment from the residual its solve ended with
+                              (exact for the fixed A of a sweep), and the next solve starts with one
+                              FP32 stencil pass over the predicted increment; a step after a large
+                              start residual (above 1000 rtol ||b||) and every 32nd step form it from
+                              the state instead; -1 = every solve forms it from the state (the
+                              error-free pass).  Ignored on the other paths. */
 } nefty_problem;
 
 /* Solver statistics of one call. */
@@ -122,6 +130,7 @@ typedef struct {
                                    wall setting); 0: plain global loads (nx % 4 != 0) or the FP64 path */
     int32_t folded_last_iters;  /* solves whose last CG iteration was applied by the state update (its
                                    residual norm known before its pass), so that its pass was left out */
+    int32_t carried_solves;     /* solves that started from the carried residual (nefty_problem.residual) */
 } nefty_stats;
 
 typedef struct nefty_handle nefty_handle;

@@ -26,7 +26,7 @@ class nefty_problem(ctypes.Structure):
                 ("robin_h", ctypes.c_double), ("obs_face", ctypes.c_int32), ("prec", ctypes.c_int32),
                 ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("ckpt_every", ctypes.c_int32),
                 ("loss_scale", ctypes.c_double), ("extrap", ctypes.c_int32),
-                ("jacobi_k", ctypes.c_int32)]
+                ("jacobi_k", ctypes.c_int32), ("residual", ctypes.c_int32)]
 
 
 class nefty_field_desc(ctypes.Structure):
@@ -46,7 +46,8 @@ class nefty_stats(ctypes.Structure):
                 ("max_rel_residual", ctypes.c_double), ("workspace_bytes", ctypes.c_uint64),
                 ("grid_blocks", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
                 ("fwd_ms", ctypes.c_double), ("recompute_ms", ctypes.c_double),
-                ("adj_ms", ctypes.c_double), ("tma_staged", ctypes.c_int32), ("folded_last_iters", ctypes.c_int32)]
+                ("adj_ms", ctypes.c_double), ("tma_staged", ctypes.c_int32), ("folded_last_iters", ctypes.c_int32),
+                ("carried_solves", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -105,7 +105,7 @@ PtrKind ptr_kind(const void* p, int dev) {
 
 // Effective problem with defaults filled in.
 struct Prob {
-    int nx, ny, nz, nt, bc, obs_face, prec, max_iter, ckpt_every, extrap, jacobi_k;
+    int nx, ny, nz, nt, bc, obs_face, prec, max_iter, ckpt_every, extrap, jacobi_k, residual;
     double dx, dy, dz, dt, robin_h, rtol, loss_scale;
     unsigned N, S;
 };
@@ -132,6 +132,7 @@ nefty_status check_problem(const nefty_problem* p, Prob* out, std::string* why) 
     if (p->loss_scale < 0 || !std::isfinite(p->loss_scale)) { *why = "loss_scale must be >= 0"; return NEFTY_EINVAL; }
     if (p->extrap < -1 || p->extrap > tiled::kRing) { *why = "extrap must be -1, 0, 1, 2, 3 or 4"; return NEFTY_EINVAL; }
     if (p->jacobi_k < 0 || p->jacobi_k > 100000) { *why = "jacobi_k must be in [0, 100000]"; return NEFTY_EINVAL; }
+    if (p->residual < -1 || p->residual > 1) { *why = "residual must be -1, 0 or 1"; return NEFTY_EINVAL; }
     if (out) {
         out->nx = p->nx; out->ny = p->ny; out->nz = p->nz; out->nt = p->nt; out->bc = p->bc;
         out->obs_face = p->obs_face; out->prec = p->prec;
@@ -142,6 +143,7 @@ nefty_status check_problem(const nefty_problem* p, Prob* out, std::string* why) 
         // the paper's fixed Jacobi sweeps start from T^n (mu^(n+1)) exactly
         out->jacobi_k = p->jacobi_k;
         if (out->jacobi_k > 0) out->extrap = 0;
+        out->residual = p->residual < 0 ? -1 : 1;
         out->dx = p->dx; out->dy = p->dy; out->dz = p->dz; out->dt = p->dt; out->robin_h = p->robin_h;
         out->rtol = p->rtol > 0 ? p->rtol : (p->prec == NEFTY_FP32 ? kDefaultRtolFp32 : kDefaultRtolFp64);
         out->loss_scale = p->loss_scale > 0 ? p->loss_scale : 1.0 / ((double)p->nt * p->nx * p->ny);
@@ -331,7 +333,7 @@ struct Call {
     int* cflag = nullptr;
     // The TMA-staged PCG carries the residual of each solve into the next
     // (cg_tiled.cu); checkpoints then keep it beside the increments.
-    bool carries() const { return kTiled && tma_grid(P) && P.jacobi_k == 0; }
+    bool carries() const { return kTiled && tma_grid(P) && P.jacobi_k == 0 && P.residual >= 0; }
 
     void place_common(Arena& a, size_t ntables) {
         const size_t N = P.N;
@@ -659,6 +661,7 @@ struct Call {
             st->kernel_launches = launches;
             st->tma_staged = use_tma ? 1 : 0;
             st->folded_last_iters = hc.folded;
+            st->carried_solves = hc.carried;
             double ms[3] = {0.0, 0.0, 0.0};
             for (auto& t : timed) {
                 float v = 0.f;

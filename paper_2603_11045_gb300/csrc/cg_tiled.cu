@@ -2346,6 +2346,7 @@ __device__ __forceinline__ void forward_sweep(const FwdTiled& a) {
             a.c.resid[n - a.n0] = rel;
             if (!conv) atomicAdd(&a.c.ctl->notconv, 1);
             if (fin.apply) atomicAdd(&a.c.ctl->folded, 1);
+            if (carried) atomicAdd(&a.c.ctl->carried, 1);
         }
         // T^{n+1} = T^n + delta as a compensated pair, delta^n into the ring, and
         // the start of step n+1 when it predicts (carried: the residual of step
@@ -2456,6 +2457,7 @@ __device__ __forceinline__ void adjoint_sweep(const AdjTiled& a) {
             a.c.resid[a.n1 - n] = rel;
             if (!conv) atomicAdd(&a.c.ctl->notconv, 1);
             if (fin.apply) atomicAdd(&a.c.ctl->folded, 1);
+            if (carried) atomicAdd(&a.c.ctl->carried, 1);
         }
         // mu^n = mu^{n+1} + delta; carried: the residual of step n - 1 (the
         // last adjoint step is n = 1), also at the end of a launch that

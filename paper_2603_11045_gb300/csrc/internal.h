@@ -39,7 +39,7 @@ struct DevCtl {
     unsigned int missing;  // fault injection (tests): arrivals every grid barrier waits for in vain; 0 normally
     unsigned long long wait_ns;   // grid-barrier wait limit (%globaltimer ns); 0 = kBarrierTimeoutNs
     int folded;            // solves whose last CG iteration was applied by the state update
-    int pad;
+    int carried;           // solves that started from the carried residual
 };
 
 // Grid geometry and the precomputed operator of A(alpha) = I - dt L(alpha).

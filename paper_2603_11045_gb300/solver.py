@@ -41,6 +41,7 @@ class Problem:
     loss_scale: float = 0.0
     extrap: int = 0
     jacobi_k: int = 0
+    residual: int = 0     # 0/1 carried start residual (staged FP32 path), -1 formed from the state
 
     @classmethod
     def from_workload(cls, w, **kw) -> "Problem":

@@ -350,6 +350,40 @@ def test_tv_matches_oracle(solver, orc, prec, bc, shape):
     assert np.abs(got - ref_g).max() <= (1e-12 if prec == "fp64" else 1e-5) * np.abs(ref_g).max()
 
 
+@pytest.mark.parametrize("bc", [0, 1])
+def test_carried_residual_matches_recomputed(solver, bc):
+    """Start residuals carried from step to step against every one formed
+    from the state (nefty_problem.residual = -1), zero-flux and periodic
+    walls: the same frames and final state within the solver tolerance, the
+    same gradient direction, none carried when switched off; a checkpointed
+    run still reproduces the first sweep bit for bit.  (This short case is
+    mostly the pulse's transient, during which the start residuals are large
+    and formed from the state: a sixth of its solves are carried.)"""
+    from paper_2603_11045_gb300.solver import Problem
+    w = S.inclusion_case(nx=64, ny=48, nz=16, nt=90, seed=1013)
+    w.bc = bc
+    a, q = dev(w.alpha, "fp32"), dev(w.q_face, "fp32")
+    base = Problem.from_workload(w, prec="fp32")
+    obs = solver.forward(base, dev(w.alpha_target, "fp32"), q_face=q, q_steps=3)["frames"]
+    out = {}
+    for res in (1, -1):
+        prob = base.with_(residual=res)
+        f = solver.forward(prob, a, q_face=q, q_steps=3, T_final=True)
+        g = solver.adjoint_grad(prob, a, obs, q_face=q, q_steps=3)
+        out[res] = (f, g)
+    (fc, gc), (fx, gx) = out[1], out[-1]
+    assert fc["stats"]["tma_staged"] == 1
+    solves = gc["stats"]["fwd_steps"] + gc["stats"]["adj_steps"]
+    assert 20 <= gc["stats"]["carried_solves"] <= solves, gc["stats"]
+    assert gx["stats"]["carried_solves"] == 0 and fx["stats"]["carried_solves"] == 0
+    assert rel_l2(fc["frames"].cpu(), fx["frames"].cpu()) <= 1e-6
+    assert rel_l2(fc["T_final"].cpu(), fx["T_final"].cpu()) <= 1e-6
+    assert cosine(gc["grad_alpha"].cpu(), gx["grad_alpha"].cpu()) >= 0.9999
+    k7 = solver.adjoint_grad(base.with_(ckpt_every=7), a, obs, q_face=q, q_steps=3)
+    assert torch.equal(k7["grad_alpha"], gc["grad_alpha"]) and k7["loss"] == gc["loss"]
+    assert k7["stats"]["carried_solves"] > 0
+
+
 def test_increment_extrapolation(solver):
     """The CG start of each step extrapolates the last increments: fewer
     iterations and the same states within the solver tolerance, and the

@@ -56,6 +56,38 @@ def test_robin_sink_margin(orc):
     assert np.allclose(margin[-1], 1.0 + 0.3 * 0.7 / 0.5, atol=1e-13)
 
 
+def test_step_structure_for_carried_residual(orc):
+    """The staged FP32 path carries the residual of each step's system at a
+    zero increment to the next step (s' = r + delta + e' - e).  That holds
+    when every implicit-Euler step solves A T^{n+1} = T^n + e^n with one A for
+    the whole sweep and a forcing e^n that is dt/dz times the flux on the
+    heated plane k = 0 and zero elsewhere (App. A.5).  Pinned on the oracle's
+    converged states; a step-dependent A or a forcing on the wrong plane
+    breaks it."""
+    nx, ny, nz, nt, qs = 5, 4, 3, 5, 2
+    p = orc.problem(nx, ny, nz, dx=0.9, dy=1.1, dz=0.6, dt=0.4, nt=nt, bc=1, robin_h=0.2)
+    g = S.rng(91)
+    alpha = g.uniform(0.1, 2.0, (nz, ny, nx))
+    T0 = g.uniform(0.0, 0.5, (nz, ny, nx))
+    q = g.uniform(0.0, 1.0, (ny, nx))
+    X = orc.forward(p, alpha, T0=T0, q_face=q, q_steps=qs, keep_states=True, tol=1e-15)["states"]
+    X = X.reshape(nt + 1, -1)
+    A = orc.assemble_A(p, alpha)
+    S_ = nx * ny
+    E = np.zeros((nt, nx * ny * nz))
+    E[:qs, :S_] = p.dt / p.dz * q.ravel()
+    scale = np.abs(X).max()
+    for n in range(nt):
+        assert np.allclose(A @ X[n + 1] - X[n], E[n], rtol=0, atol=1e-12 * scale)
+    s = X[0] + E[0] - A @ X[0]
+    for n in range(nt - 1):
+        delta = X[n + 1] - X[n]
+        r = s - A @ delta                      # the residual the solve ends with
+        s = r + delta + (E[n + 1] - E[n])      # carried
+        direct = X[n + 1] + E[n + 1] - A @ X[n + 1]
+        assert np.allclose(s, direct, rtol=0, atol=1e-12 * scale)
+
+
 def test_uniform_alpha_face_equals_alpha(orc):
     """Prop. 1 / App. A.3: for uniform alpha the face value equals alpha, so
     L is the standard 7-point Laplacian times alpha."""
