@@ -192,12 +192,19 @@ __device__ __forceinline__ DF df_mul(DF x, DF y) {
     const float cl2 = fmaf(x.lo, y.hi, fmaf(x.hi, y.lo, x.lo * y.lo));
     return df_norm(ch, cl1 + cl2);
 }
+// q1 from the hardware reciprocal (about 1 ulp): the remainder x - q1 y is
+// formed exactly (TwoProd through fmaf, and x.hi - p is exact for q1 that
+// close), so the quotient keeps the precision of the pair whatever q1's last
+// bit; a correctly rounded division would only add latency to the chain of
+// CG scalars every iteration waits on.
 __device__ __forceinline__ DF df_div(DF x, DF y) {
-    const float q1 = __fdiv_rn(x.hi, y.hi);
+    float ry;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(ry) : "f"(y.hi));
+    const float q1 = x.hi * ry;
     const float p = q1 * y.hi;
     const float pe = fmaf(q1, y.hi, -p);
     const float r = (((x.hi - p) - pe) + x.lo) - q1 * y.lo;   // x - q1 y
-    return df_norm(q1, __fdiv_rn(r, y.hi));
+    return df_norm(q1, r * ry);
 }
 __device__ __forceinline__ bool df_le(DF x, DF y) { return x.hi < y.hi || (x.hi == y.hi && x.lo <= y.lo); }
 
@@ -2023,12 +2030,13 @@ __device__ void add_state(const float* __restrict__ x, float* __restrict__ delta
     };
     bh = bl = 0.f;
     if ((N & 3u) == 0) {
-        // Batches of two quads per thread: every load of a batch is issued
-        // before its stores.  x (the old state) is not read again soon, so it
+        // One quad per thread and loop step, every load of the quad issued
+        // before its stores (batches of two quads cost the adjoint kernel
+        // 110 more bytes of spills and were slower).  x (the old state) is not read again soon, so it
         // streams past L2 (evict-first), and so does the new state y when
         // stream_y (a forward state, read again only a step later); delta,
         // the ring and the next start stay there for the passes that follow.
-        constexpr int B = 2;
+        constexpr int B = 1;
         const unsigned N4 = N >> 2;
         const float4* __restrict__ xh = reinterpret_cast<const float4*>(x);
         const float4* __restrict__ xl = reinterpret_cast<const float4*>(x + N);
