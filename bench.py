@@ -47,18 +47,17 @@ UNIT = "Gcell-steps/s"
 ALG_BYTES_ITER = {"fp32": 28, "fp64": 80}
 ALG_BYTES_STEP = {"fp32": 8, "fp64": 16}
 ALG_BYTES_GRAD = {"fp32": 20, "fp64": 24}
-# DRAM bytes per cell per solver pass of the FP32 CG kernels, from one ncu
-# capture of each sweep on the 256x256x48 grid (20 steps): the forward sweep
-# and the reverse sweep with the gradient, with the fixed passes per solve of
-# those kernels.  bench.py scales them to the timed launches by their pass
-# counts (CG iterations plus the fixed passes) as an ESTIMATE of the timed
-# traffic, and only while the kernel source still hashes to the captured one:
-# once the kernels change the figure is stale and `traffic` is null.
+# DRAM bytes per cell-step of the FP32 CG launches, measured by ncu on this
+# workload at full size (256x256x48, 1000 steps; dram__bytes_read.sum +
+# dram__bytes_write.sum, one-pass metrics, every launch of a bench run): the
+# forward sweep and the reverse sweep with the gradient.  bench.py multiplies
+# them by the timed step's solved steps for `traffic`, and only while the
+# kernel source still hashes to the captured one: once the kernels change the
+# figure is stale and `traffic` is null.
 DRAM_CAPTURE = {
-    "fp32": {"fwd": 25.3, "adj": 26.1, "fixed_passes_fwd": 3, "fixed_passes_adj": 4,
-             "kernel_source": "paper_2603_11045_gb300/csrc/cg_tiled.cu", "kernel_sha16": "69255fe70b939e5e",
-             "profiles": ["profiles/forward_tiled_256x256x48_nt20_ncu.md",
-                          "profiles/adjoint_tiled_256x256x48_nt20_ncu.md"]},
+    "fp32": {"fwd": 109.6, "adj": 181.6, "grid": [256, 256, 48], "nt": 1000,
+             "kernel_source": "paper_2603_11045_gb300/csrc/cg_tiled.cu", "kernel_sha16": "a1ae9f09d5f157d0",
+             "profiles": ["profiles/inversion_step_256x256x48_nt1000_launches.md"]},
     "fp64": None,
 }
 KERNELS = {"fp32": "tiled::forward_tiled + tiled::adjoint_tiled (persistent single-reduction Jacobi-PCG, TMA-staged)",
@@ -383,19 +382,18 @@ def run_native(args):
     pk = peaks()
     peak = pk["hbm_gbs"] if pk else 6800.0
     achieved = alg_bytes / (cg_ms / 1000.0) / 1e9
-    fwd_iters = sum(s["fwd_iters"] + s["recompute_iters"] for s in stats) / len(stats)
-    adj_iters = sum(s["adj_iters"] for s in stats) / len(stats)
     cap = DRAM_CAPTURE[R]
     traffic, traffic_note = None, "no ncu capture of these kernels"
     if cap is not None:
         if source_sha16(cap["kernel_source"]) != cap["kernel_sha16"]:
             traffic_note = "stale: the kernel source changed since the ncu capture"
         else:
-            fwd_passes = fwd_iters + cap["fixed_passes_fwd"] * (st0["fwd_steps"] + st0["recompute_steps"])
-            adj_passes = adj_iters + cap["fixed_passes_adj"] * st0["adj_steps"]
-            traffic = w.n_cells * (cap["fwd"] * fwd_passes + cap["adj"] * adj_passes)
-            traffic_note = ("estimate: DRAM bytes per cell-pass of one ncu capture per sweep (" +
-                            ", ".join(cap["profiles"]) + "), scaled by the timed step's solver passes")
+            traffic = w.n_cells * (cap["fwd"] * (st0["fwd_steps"] + st0["recompute_steps"])
+                                   + cap["adj"] * st0["adj_steps"])
+            same = [w.nx, w.ny, w.nz] == cap["grid"] and w.nt == cap["nt"]
+            traffic_note = ("DRAM bytes per cell-step of the forward and reverse launches measured by ncu on "
+                            + ("this workload" if same else "the 256x256x48x1000 workload (scaled here)")
+                            + " (" + ", ".join(cap["profiles"]) + ")")
     dram_gbs = None if traffic is None else traffic / (cg_ms / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_note": traffic_note,
