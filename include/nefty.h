@@ -304,9 +304,10 @@ nefty_status nefty_forward_static(int device, const nefty_problem *p, const void
  * nx % 4 == 0 (either wall setting) run together in ONE persistent launch over
  * the whole device, whatever their grid sizes and step counts: each sweep runs
  * on its own range of the launch's CTAs, sized in proportion to its work per
- * step, with its own grid barriers.  Each sweep is cut into chunks of
- * chunk_steps steps, and a launch carries the next chunk of every running
- * job, so a newly admitted job joins the launch that follows.  Other sweeps
+ * step, with its own grid barriers.  A launch lasts about launch_us of device
+ * time: every sweep in it runs its next time steps until that time has
+ * passed, and the next launch continues each from where it stopped, so a
+ * newly admitted job joins the launch that follows.  Other sweeps
  * (FP64, nx % 4 != 0, Jacobi-K) and unbatched servers (batched = -1) run each
  * lane's own persistent grid on 1 / lanes of the SMs, resident beside the
  * others.  On lanes a job's results are the same bits alone or among other
@@ -365,8 +366,13 @@ typedef struct {
     int32_t max_queue;          /* queued-job limit for NEFTY_EBUSY (0 = 4096) */
     uint64_t mem_budget_bytes;  /* device memory shared by the lanes (0 = 80% of free memory) */
     int32_t batched;            /* 0 or 1: batched launches (see above); -1: each lane its own grid */
-    int32_t chunk_steps;        /* batched: time steps of a sweep per launch (0 = 32); smaller chunks
-                                   admit new jobs sooner */
+    int32_t chunk_steps;        /* batched: at most this many time steps of a sweep per launch (0 = no
+                                   cap beyond launch_us) */
+    int32_t launch_us;          /* batched: device time of one launch in microseconds (0 = 20000):
+                                   each sweep of a launch runs time steps until that much time has
+                                   passed since the launch began (at least one step), so the sweeps
+                                   of a launch end together; a job submitted meanwhile joins the
+                                   next launch */
 } nefty_serve_config;
 
 /* Start serving on h's device (cfg may be NULL for the defaults).

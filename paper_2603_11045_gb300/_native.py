@@ -76,7 +76,7 @@ class nefty_job_result(ctypes.Structure):
 
 class nefty_serve_config(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_int32), ("max_queue", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_uint64),
-                ("batched", ctypes.c_int32), ("chunk_steps", ctypes.c_int32)]
+                ("batched", ctypes.c_int32), ("chunk_steps", ctypes.c_int32), ("launch_us", ctypes.c_int32)]
 
 
 class NeftyError(RuntimeError):

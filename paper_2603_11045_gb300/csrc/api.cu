@@ -496,60 +496,34 @@ struct Call {
         c.resid = rs;
         return c;
     }
-    // Batched sweeps (serving): a sweep is cut into chunks of a few time
-    // steps, so that a launch of the batcher stays short and newly admitted
-    // jobs join the next one; the chunks of a sweep ride consecutive launches,
-    // and the call's stream continues after the last.
-    int batch_chunk() const { return batcher_chunk(h->batch, P.N); }
-    nefty_status run_batched(std::vector<tiled::BatchSweep>& chunks) {
+    // Batched sweeps (serving): the whole sweep goes to the batcher, whose
+    // launches each run a part of it (until their device-time budget is
+    // spent) beside the other running jobs' sweeps; the call's stream
+    // continues after the launch that ran its last step.
+    nefty_status run_batched(const tiled::BatchSweep& whole) {
         int launched = 0, shared = 0;
         std::string why;
-        const nefty_status e = batcher_run(h->batch, chunks, G, s, &launched, &shared, &why);
+        const nefty_status e = batcher_run(h->batch, whole, G, s, &launched, &shared, &why);
         h->batch_launches += launched;
         h->batch_shared += shared;
-        launches += (int)chunks.size() - 1;
+        launches += std::max(0, launched - 1);
         if (e != NEFTY_OK) return fail(h, e, why);
         return NEFTY_OK;
     }
     nefty_status batched_fwd(const tiled::FwdTiled& a) {
-        // the chunks add their frame losses into loss_partials
+        // the parts add their frame losses into loss_partials
         if (a.loss_partials) NEFTY_CUDA(h, cudaMemsetAsync(a.loss_partials, 0, (size_t)G * sizeof(double), s));
-        std::vector<tiled::BatchSweep> chunks;
-        for (int m0 = a.n0; m0 < a.n1; m0 += batch_chunk()) {
-            tiled::BatchSweep w{};
-            w.adjoint = 0;
-            w.f = a;
-            w.f.n0 = m0;
-            w.f.n1 = std::min(a.n1, m0 + batch_chunk());
-            w.f.src = a.src + (m0 - a.n0);
-            w.f.dst = a.dst + (m0 - a.n0);
-            w.f.hist0 = std::min(a.hist0 + (m0 - a.n0), tiled::kRing);
-            w.f.ring_load = m0 == a.n0 ? a.ring_load : nullptr;
-            w.f.carry = m0 == a.n0 ? a.carry : 1;   // a chunk continues the one before it
-            w.f.ring_save = a.ring_save ? a.ring_save + (m0 - a.n0) : nullptr;
-            w.f.c.iters = a.c.iters + (m0 - a.n0);
-            w.f.c.resid = a.c.resid + (m0 - a.n0);
-            w.f.loss_add = 1;
-            chunks.push_back(w);
-        }
-        return run_batched(chunks);
+        tiled::BatchSweep w{};
+        w.adjoint = 0;
+        w.f = a;
+        w.f.loss_add = 1;
+        return run_batched(w);
     }
     nefty_status batched_adj(const tiled::AdjTiled& a) {
-        std::vector<tiled::BatchSweep> chunks;
-        for (int m1 = a.n1; m1 > a.n0; m1 -= batch_chunk()) {
-            tiled::BatchSweep w{};
-            w.adjoint = 1;
-            w.a = a;
-            w.a.n1 = m1;
-            w.a.n0 = std::max(a.n0, m1 - batch_chunk());
-            w.a.T = a.T + (w.a.n0 - a.n0);
-            w.a.hist0 = std::min(a.hist0 + (a.n1 - m1), tiled::kRing);
-            w.a.carry = m1 == a.n1 ? a.carry : 1;
-            w.a.c.iters = a.c.iters + (a.n1 - m1);
-            w.a.c.resid = a.c.resid + (a.n1 - m1);
-            chunks.push_back(w);
-        }
-        return run_batched(chunks);
+        tiled::BatchSweep w{};
+        w.adjoint = 1;
+        w.a = a;
+        return run_batched(w);
     }
     nefty_status launch_fwd_tiled(const tiled::FwdTiled& a, int kind) {
         NEFTY_CUDA(h, cudaMemsetAsync(&ctl->bar, 0, 2 * sizeof(unsigned), s));

@@ -2301,6 +2301,8 @@ __device__ __forceinline__ void forward_sweep(const FwdTiled& a) {
     const unsigned c0 = cta_id() * NT + threadIdx.x;
     double loss = 0.0;
     Pipe pre = pipe_none();
+    const unsigned long long t_start = a.budget_ns ? now_ns() : 0ull;   // used by CTA 0 only
+    int n_next = a.n1;   // the next step to run after this launch
     // the carried residual (TMA-staged PCG, when the workspace has it)
     const bool carry_on = kTma && !kJac && a.c.v.diag != nullptr;
     if (carry_on) write_diag(a.c);
@@ -2366,12 +2368,15 @@ __device__ __forceinline__ void forward_sweep(const FwdTiled& a) {
         const CarryOut co{a.c.v.sig[0], a.c.v.diag, a.c.v.u[fin.cur], a.c.v.ws[fin.cur], a.c.v.ss[fin.cur]};
         add_state(Tn, a.c.v.delta, Tn1, N, ring_d.slot(n), older(ring_d, n, -1), hu1, a.ystart, true, fin, &a.c.v,
                   carried ? &co : nullptr, fwd_force(a, n), fwd_force(a, carried ? n + 1 : n), bh, bl);
+        if (a.budget_ns && cta_id() == 0 && threadIdx.x == 0)   // the launch's last step? (read after the barrier)
+            *(volatile int*)&a.c.ctl->stop = (n + 1 < a.n1 && now_ns() - t_start >= a.budget_ns) ? 1 : 0;
         if (!barrier(sy)) return;
+        const bool stop = a.budget_ns && *(volatile int*)&a.c.ctl->stop != 0;
         if (a.ring_save && a.ring_save[n - a.n0])   // a checkpoint keeps [delta^n; delta^{n-1}; ...] (+ s^{n+1})
             save_hist(a.ring_save[n - a.n0], ring_d, n, a.extrap, carried ? a.c.v.sig[0] : nullptr);
         pre = pipe_none();
         if constexpr (kTma) {   // the next step's first pass, behind the frame below
-            if (n + 1 < a.n1) {
+            if (n + 1 < a.n1 && !stop) {
                 if (carried) {
                     pre = pipe_start(a.c, ring, PassIn{kInitC, 0, false, 0u, 0u, 0});
                 } else {
@@ -2391,7 +2396,12 @@ __device__ __forceinline__ void forward_sweep(const FwdTiled& a) {
                 }
             }
         }
+        if (stop) {   // the budget of this launch is spent; a later one continues at n + 1
+            n_next = n + 1;
+            break;
+        }
     }
+    if (a.progress && cta_id() == 0 && threadIdx.x == 0) *a.progress = n_next;
     if (a.loss_partials) {
         const double t = block_sum(loss);
         if (threadIdx.x == 0) {
@@ -2426,6 +2436,8 @@ __device__ __forceinline__ void adjoint_sweep(const AdjTiled& a) {
     const IncRing ring_d{a.ring, N};
     float bh = 0.f, bl = 0.f;   // this thread's part of the next solve's ||b||^2 (carried)
     bool carried = false;
+    const unsigned long long t_start = a.budget_ns ? now_ns() : 0ull;   // used by CTA 0 only
+    int n_next = a.n0;   // the next step to run after this launch (downwards)
     if (carry_on && a.carry && a.cflag && a.cflag[a.n1]) {
         prepare_carried(a.mu[(a.n1 + 1) & 1], ring_d.slot(a.n1 + 1), older(ring_d, a.n1 + 1, 1), hu_at(a.n1),
                         a.c.v.delta, N, adj_force(a, a.n1), bh, bl);
@@ -2477,7 +2489,10 @@ __device__ __forceinline__ void adjoint_sweep(const AdjTiled& a) {
                   (carried || n - 1 > a.n0) ? hu_at(n - 1) : 0,
                   a.ystart, false, fin, &a.c.v, carried ? &co : nullptr, adj_force(a, n),
                   adj_force(a, carried ? n - 1 : n), bh, bl);
+        if (a.budget_ns && cta_id() == 0 && threadIdx.x == 0)   // the launch's last step? (read after the barrier)
+            *(volatile int*)&a.c.ctl->stop = (n - 1 > a.n0 && now_ns() - t_start >= a.budget_ns) ? 1 : 0;
         if (!barrier(sy)) return;
+        const bool stop = a.budget_ns && *(volatile int*)&a.c.ctl->stop != 0;
         // gradient of step n with mu^n and T^n (the next step writes only the
         // other mu buffer and the CG vectors, so no barrier is needed after it)
         if constexpr (kTma) {
@@ -2511,7 +2526,12 @@ __device__ __forceinline__ void adjoint_sweep(const AdjTiled& a) {
                 a.grad[c] = make_float2(gh, gl);
             });
         }
+        if (stop) {   // the budget of this launch is spent; a later one continues at n - 1
+            n_next = n - 1;
+            break;
+        }
     }
+    if (a.progress && cta_id() == 0 && threadIdx.x == 0) *a.progress = n_next;
 }
 
 // Launches of one sweep on the whole grid.

@@ -40,6 +40,8 @@ struct DevCtl {
     unsigned long long wait_ns;   // grid-barrier wait limit (%globaltimer ns); 0 = kBarrierTimeoutNs
     int folded;            // solves whose last CG iteration was applied by the state update
     int carried;           // solves that started from the carried residual
+    int stop;              // time-budgeted launches: this step is the launch's last (set by CTA 0)
+    int pad;
 };
 
 // Grid geometry and the precomputed operator of A(alpha) = I - dt L(alpha).
@@ -246,6 +248,9 @@ struct FwdTiled {
     int* cflag;               // [n_end] per step n: 1 if step n starts from the carried residual (written by
                               //   the step before, read by a launch that resumes at n)
     int n_end;                // steps of the whole sweep (the forcing of step n exists for n < n_end)
+    unsigned long long budget_ns;   // > 0: stop after the step during which this much device time has
+                                    //   passed since the launch began (at least one step)
+    int* progress;            // with budget_ns: the next step to run is written here (n1 when all ran)
     float* const* src;
     float* const* dst;
     const float* q_face; int q_steps; const float* q_full;
@@ -266,6 +271,8 @@ struct AdjTiled {
     int hist0;                // increments valid at launch start (steps n1+1, n1+2, ...)
     int carry;                // 1: the carried residual of step n1 is valid in sig[1] at launch start
     int* cflag;               // as FwdTiled::cflag, per adjoint step (index n)
+    unsigned long long budget_ns;   // as FwdTiled::budget_ns
+    int* progress;            // with budget_ns: the next step to run (downwards; n0 when all ran)
     float* const* T;
     float* mu[2];
     const float* alpha;
@@ -343,19 +350,20 @@ cudaError_t launch_adjoint_tiled(const tiled::AdjTiled& a, int grid, cudaStream_
 cudaError_t launch_batch_tiled(const tiled::BatchArgs& b, int grid, cudaStream_t s);
 // Batched serving launches (serve.cu).  A Batcher owns one stream and runs the
 // sweeps handed to batcher_run from any thread in shared persistent launches
-// (tiled::batch_tiled) on the whole device.
+// (tiled::group_tiled) on the whole device.
 // api.cu: h's TMA-staged sweeps go to b (null: h launches its own grids);
 // the launches that carried h's sweeps so far, and those shared with others.
 void set_batcher(nefty_handle* h, Batcher* b);
 void batch_counts(nefty_handle* h, int* launches, int* shared);
 int batcher_grid(Batcher* b);
-int batcher_chunk(Batcher* b, unsigned N);   // time steps per chunk of a sweep on N cells
-// Runs the chunks (consecutive parts of one sweep, in order) in launches of b
-// after the work issued on s so far; returns once the last chunk is launched,
-// with s ordered after that launch.  *launches / *shared: launches used, and
-// those that carried other sweeps too.  grid must be batcher_grid(b).
-nefty_status batcher_run(Batcher* b, std::vector<tiled::BatchSweep>& chunks, int grid, cudaStream_t s,
-                         int* launches, int* shared, std::string* why);
+// Runs the whole sweep (one forward or adjoint launch's descriptor) in
+// launches of b after the work issued on s so far, each launch running the
+// next part of it beside the other pending sweeps; returns once the last part
+// is launched, with s ordered after that launch.  *launches / *shared:
+// launches used, and those that carried other sweeps too.  grid must be
+// batcher_grid(b).
+nefty_status batcher_run(Batcher* b, const tiled::BatchSweep& whole, int grid, cudaStream_t s, int* launches,
+                         int* shared, std::string* why);
 // out[i] = (in[i].x + in[i].y) * scale (the tiled gradient accumulator to FP32);
 // the split form reads a state's hi and lo halves.
 cudaError_t launch_cast_pairs(const float2* in, float* out, unsigned n, float scale, cudaStream_t s);

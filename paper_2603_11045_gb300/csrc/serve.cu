@@ -9,17 +9,19 @@
 // NEFTY_ENOMEM, a job whose smallest workspace does not fit a share.
 //
 // Batched mode: the lanes' handles hand their TMA-staged FP32 sweeps to one
-// Batcher instead of launching them.  The Batcher thread repeatedly takes the
-// next chunk of every pending sweep (at most kMaxBatch, in arrival order) and
-// launches them together as one persistent grid over the whole device
+// Batcher instead of launching them.  The Batcher thread repeatedly takes
+// every pending sweep (at most kMaxBatch, in arrival order) and launches them
+// together as one persistent grid over the whole device
 // (tiled::group_tiled): each sweep gets its own range of CTAs, in proportion
 // to its work per step, and runs there as in a launch of its own, so the
-// sweeps proceed independently; the next launch is composed when this one is
-// done, so a job admitted meanwhile joins it.  Every sweep is cut into chunks
-// of the same number of steps, so the chunks of one launch take about the
-// same time.  Ordering: a launch waits for the work each lane issued before
+// sweeps proceed independently.  Each sweep runs time steps until the
+// launch's device-time budget has passed and reports the step it reached;
+// the sweeps of a launch thus end together whatever their speeds (no CTA
+// waits for a slower sweep), and the next launch, composed once this one is
+// done, continues each from where it stopped and takes the jobs admitted
+// meanwhile.  Ordering: a launch waits for the work each lane issued before
 // its sweep (an event per request), and a lane's stream waits for the launch
-// that carried its sweep's last chunk.  Unbatched mode (and the sweeps the
+// that ran its sweep's last step.  Unbatched mode (and the sweeps the
 // grouped kernel does not take) runs each lane's own cooperative grid on
 // 1 / lanes of the SMs, resident beside the others.  A job's results depend
 // on the CTAs it gets (its reduction order), not otherwise on the other
@@ -76,22 +78,64 @@ struct Job {
     std::atomic<bool> cancel{false};
 };
 
-// One sweep handed to the Batcher: its chunks, launched in order.
+// One sweep handed to the Batcher: the whole sweep and where it stands.
 struct BatchReq {
-    std::vector<tiled::BatchSweep>* chunks = nullptr;
-    size_t next = 0;               // first chunk not launched yet
+    tiled::BatchSweep whole{};     // the sweep's full descriptor (all its steps)
+    int cursor = 0;                // forward: the next step; adjoint: the next step downwards
     cudaEvent_t ready = nullptr;   // the lane's work before the sweep
-    cudaStream_t stream = nullptr; // the lane's stream, ordered after the last chunk
+    cudaStream_t stream = nullptr; // the lane's stream, ordered after the last launch
     int launches = 0, shared = 0;
     cudaError_t err = cudaSuccess;
     bool finished = false;
+    int end() const { return whole.adjoint ? whole.a.n0 : whole.f.n1; }
 };
+
+// The part of a sweep that a launch runs: from `cursor` on, at most `cap`
+// steps (0: to the end), stopping early once `budget_ns` of device time has
+// passed, with the step it reached written to `progress`.  The same
+// arithmetic as a launch of its own from that step: increments, the carried
+// residual and the per-step choices continue from the workspace.
+tiled::BatchSweep resume(const BatchReq& r, int cap, unsigned long long budget_ns, int* progress) {
+    tiled::BatchSweep c = r.whole;
+    const int m = r.cursor;
+    if (!r.whole.adjoint) {
+        const tiled::FwdTiled& a = r.whole.f;
+        tiled::FwdTiled& f = c.f;
+        f.n0 = m;
+        f.n1 = cap > 0 ? std::min(a.n1, m + cap) : a.n1;
+        f.src = a.src + (m - a.n0);
+        f.dst = a.dst + (m - a.n0);
+        f.hist0 = std::min(a.hist0 + (m - a.n0), tiled::kRing);
+        f.ring_load = m == a.n0 ? a.ring_load : nullptr;
+        f.ring_save = a.ring_save ? a.ring_save + (m - a.n0) : nullptr;
+        f.carry = m == a.n0 ? a.carry : 1;
+        f.c.iters = a.c.iters + (m - a.n0);
+        f.c.resid = a.c.resid + (m - a.n0);
+        f.loss_add = 1;
+        f.budget_ns = budget_ns;
+        f.progress = progress;
+    } else {
+        const tiled::AdjTiled& a = r.whole.a;
+        tiled::AdjTiled& b = c.a;
+        b.n1 = m;
+        b.n0 = cap > 0 ? std::max(a.n0, m - cap) : a.n0;
+        b.T = a.T + (b.n0 - a.n0);   // T^n at index n - n0
+        b.hist0 = std::min(a.hist0 + (a.n1 - m), tiled::kRing);
+        b.carry = m == a.n1 ? a.carry : 1;
+        b.c.iters = a.c.iters + (a.n1 - m);
+        b.c.resid = a.c.resid + (a.n1 - m);
+        b.budget_ns = budget_ns;
+        b.progress = progress;
+    }
+    return c;
+}
 
 }  // namespace
 
 class Batcher {
   public:
-    Batcher(int device, int chunk_steps) : device_(device), chunk_steps_(chunk_steps) {}
+    Batcher(int device, int chunk_steps, int launch_us)
+        : device_(device), chunk_steps_(chunk_steps), launch_us_(launch_us) {}
     ~Batcher() { stop(); }
 
     nefty_status start(std::string* why) {
@@ -104,9 +148,11 @@ class Batcher {
             *why = "cannot size the batched solver grid on this device";
             st = NEFTY_ECUDA;
         } else if (cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking) != cudaSuccess ||
-                   cudaEventCreateWithFlags(&done_[0], cudaEventDisableTiming) != cudaSuccess ||
-                   cudaEventCreateWithFlags(&done_[1], cudaEventDisableTiming) != cudaSuccess) {
-            *why = "cannot create the batcher's stream";
+                   cudaEventCreateWithFlags(&done_, cudaEventDisableTiming) != cudaSuccess ||
+                   cudaMalloc((void**)&progress_dev_, tiled::kMaxBatch * sizeof(int)) != cudaSuccess ||
+                   cudaHostAlloc((void**)&progress_host_, tiled::kMaxBatch * sizeof(int), cudaHostAllocDefault) !=
+                       cudaSuccess) {
+            *why = "cannot create the batcher's stream and progress slots";
             st = NEFTY_ECUDA;
         }
         cudaGetLastError();
@@ -130,22 +176,28 @@ class Batcher {
     }
 
     int grid() const { return grid_; }
-    // Steps per chunk: the same for every sweep (the CTA shares of a launch
-    // follow the work per step, so equal step counts take about equal time).
-    int chunk(unsigned) const { return chunk_steps_ > 0 ? chunk_steps_ : kDefaultChunkSteps; }
-    static constexpr int kDefaultChunkSteps = 32;
+    // Device time of a launch: each of its sweeps runs steps until this much
+    // has passed since the launch began (at least one step), so the sweeps of
+    // a launch end together whatever their speeds, and a job admitted
+    // meanwhile joins within this time.  chunk_steps > 0 also caps the steps
+    // of every sweep per launch.
+    static constexpr int kDefaultLaunchUs = 20000;
+    unsigned long long budget_ns() const {
+        return (unsigned long long)(launch_us_ > 0 ? launch_us_ : kDefaultLaunchUs) * 1000ull;
+    }
 
-    nefty_status run(std::vector<tiled::BatchSweep>& chunks, int grid, cudaStream_t s, int* launches,
-                     int* shared, std::string* why) {
+    nefty_status run(const tiled::BatchSweep& whole, int grid, cudaStream_t s, int* launches, int* shared,
+                     std::string* why) {
         *launches = *shared = 0;
-        if (chunks.empty()) return NEFTY_OK;
         if (grid != grid_) {
             *why = "internal error: a batched sweep was sized for another grid";
             return NEFTY_ECUDA;
         }
         BatchReq r;
-        r.chunks = &chunks;
+        r.whole = whole;
+        r.cursor = whole.adjoint ? whole.a.n1 : whole.f.n0;
         r.stream = s;
+        if (r.cursor == r.end()) return NEFTY_OK;
         if (cudaEventCreateWithFlags(&r.ready, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventRecord(r.ready, s) != cudaSuccess) {
             cudaGetLastError();
@@ -176,10 +228,12 @@ class Batcher {
 
   private:
     void release() {
-        for (cudaEvent_t& ev : done_) {
-            if (ev) cudaEventDestroy(ev);
-            ev = nullptr;
-        }
+        if (done_) cudaEventDestroy(done_);
+        done_ = nullptr;
+        if (progress_dev_) cudaFree(progress_dev_);
+        progress_dev_ = nullptr;
+        if (progress_host_) cudaFreeHost(progress_host_);
+        progress_host_ = nullptr;
         if (stream_) cudaStreamDestroy(stream_);
         stream_ = nullptr;
     }
@@ -189,13 +243,13 @@ class Batcher {
     // 1.5 for their extra gradient pass and iterations), at least one CTA, at
     // most the CTAs a launch of its own would use (one per two tile-planes).
     // The sweeps that do not fit wait for the next launch; returns how many fit.
-    int shares(const std::vector<const tiled::BatchSweep*>& sw, int* off) const {
+    int shares(const std::vector<tiled::BatchSweep>& sw, int* off) const {
         const int n = (int)sw.size();
         std::vector<double> cost(n);
         std::vector<int> cap(n), g(n, 1);
         for (int i = 0; i < n; ++i) {
-            const tiled::Common& c = sw[i]->adjoint ? sw[i]->a.c : sw[i]->f.c;
-            cost[i] = (double)c.g.S * c.g.nz * (sw[i]->adjoint ? 1.5 : 1.0);
+            const tiled::Common& c = sw[i].adjoint ? sw[i].a.c : sw[i].f.c;
+            cost[i] = (double)c.g.S * c.g.nz * (sw[i].adjoint ? 1.5 : 1.0);
             cap[i] = std::max(1, std::min(grid_, (int)(c.g.units / 2)));
         }
         int used = 0, fit = 0;
@@ -239,16 +293,16 @@ class Batcher {
                     take.push_back(r);
                 }
             }
-            // one launch with the next chunk of every request taken (those
+            // one launch with the next part of every request taken (those
             // whose CTA shares fit)
-            std::vector<const tiled::BatchSweep*> sw;
-            for (BatchReq* r : take) sw.push_back(&(*r->chunks)[r->next]);
+            std::vector<tiled::BatchSweep> sw;
+            for (size_t i = 0; i < take.size(); ++i)
+                sw.push_back(resume(*take[i], chunk_steps_, budget_ns(), progress_dev_ + i));
             args.n = shares(sw, args.off);
             take.resize(args.n);
             cudaError_t e = cudaSuccess;
-            cudaEvent_t done = done_[nlaunch_ & 1];
             for (int i = 0; i < args.n && e == cudaSuccess; ++i) {
-                args.s[i] = *sw[i];
+                args.s[i] = sw[i];
                 e = cudaStreamWaitEvent(stream_, take[i]->ready, 0);
                 // grid-barrier counters: the sweep's launches alternate between its
                 // two counters, each launch zeroing the other one at its end (both are
@@ -259,18 +313,23 @@ class Batcher {
                 par += 1;
             }
             if (e == cudaSuccess) e = launch_batch_tiled(args, grid_, stream_);
-            if (e == cudaSuccess) e = cudaEventRecord(done, stream_);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(progress_host_, progress_dev_, (size_t)args.n * sizeof(int),
+                                    cudaMemcpyDeviceToHost, stream_);
+            if (e == cudaSuccess) e = cudaEventRecord(done_, stream_);
+            if (e == cudaSuccess) e = cudaEventSynchronize(done_);   // where each sweep stopped
             if (e != cudaSuccess) cudaGetLastError();
             {
                 std::lock_guard<std::mutex> lk(mu_);
-                for (BatchReq* r : take) {
-                    r->next += 1;
+                for (int i = 0; i < args.n; ++i) {
+                    BatchReq* r = take[i];
                     r->launches += 1;
                     if (args.n > 1) r->shared += 1;
                     if (e != cudaSuccess) r->err = e;
-                    if (e != cudaSuccess || r->next == r->chunks->size()) {
+                    else r->cursor = progress_host_[i];
+                    if (e != cudaSuccess || r->cursor == r->end()) {
                         // the lane continues after this launch
-                        if (e == cudaSuccess) cudaStreamWaitEvent(r->stream, done, 0);
+                        if (e == cudaSuccess) cudaStreamWaitEvent(r->stream, done_, 0);
                         r->finished = true;
                         pending_.erase(std::find(pending_.begin(), pending_.end(), r));
                     }
@@ -278,21 +337,17 @@ class Batcher {
                 ++launches_;
             }
             cv_.notify_all();
-            // one launch may wait in the stream behind the running one: the next
-            // is composed (from every sweep pending by then) once the launch
-            // before this one is done, so no host round trip separates launches
-            if (e == cudaSuccess && nlaunch_ > 0) cudaEventSynchronize(done_[(nlaunch_ - 1) & 1]);
-            ++nlaunch_;
         }
-        if (nlaunch_ > 0) cudaEventSynchronize(done_[(nlaunch_ - 1) & 1]);
     }
 
     int device_;
     int chunk_steps_;
+    int launch_us_;
     int grid_ = 0;
     cudaStream_t stream_ = nullptr;
-    cudaEvent_t done_[2] = {nullptr, nullptr};
-    long long nlaunch_ = 0;
+    cudaEvent_t done_ = nullptr;
+    int* progress_dev_ = nullptr;    // [kMaxBatch] where each sweep of the last launch stopped
+    int* progress_host_ = nullptr;   // pinned copy
     std::unordered_map<DevCtl*, unsigned> parity_;   // grouped launches per control block
     std::thread thread_;
     std::mutex mu_;
@@ -303,10 +358,9 @@ class Batcher {
 };
 
 int batcher_grid(Batcher* b) { return b->grid(); }
-int batcher_chunk(Batcher* b, unsigned N) { return b->chunk(N); }
-nefty_status batcher_run(Batcher* b, std::vector<tiled::BatchSweep>& chunks, int grid, cudaStream_t s,
-                         int* launches, int* shared, std::string* why) {
-    return b->run(chunks, grid, s, launches, shared, why);
+nefty_status batcher_run(Batcher* b, const tiled::BatchSweep& whole, int grid, cudaStream_t s, int* launches,
+                         int* shared, std::string* why) {
+    return b->run(whole, grid, s, launches, shared, why);
 }
 
 class Server {
@@ -322,7 +376,7 @@ class Server {
         nefty_status st = NEFTY_OK;
         const uint64_t share = cfg_.mem_budget_bytes / (uint64_t)cfg_.lanes;
         if (cfg_.batched >= 0) {
-            batcher_ = std::make_unique<Batcher>(device_, cfg_.chunk_steps);
+            batcher_ = std::make_unique<Batcher>(device_, cfg_.chunk_steps, cfg_.launch_us);
             st = batcher_->start(why);
             if (st != NEFTY_OK) {
                 batcher_.reset();
@@ -616,8 +670,9 @@ Server* server_start(int device, const nefty_serve_config* cfg, nefty_status* st
     if (c.lanes == 0) c.lanes = 2;
     if (c.max_queue == 0) c.max_queue = 4096;
     if (c.lanes < 1 || c.lanes > tiled::kMaxBatch || c.max_queue < 1 || c.batched < -1 || c.batched > 1 ||
-        c.chunk_steps < 0) {
-        *why = "need 1 <= lanes <= 16, max_queue >= 1, batched in {-1, 0, 1} and chunk_steps >= 0";
+        c.chunk_steps < 0 || c.launch_us < 0 || c.launch_us > 10000000) {
+        *why = "need 1 <= lanes <= 16, max_queue >= 1, batched in {-1, 0, 1}, chunk_steps >= 0 and "
+               "0 <= launch_us <= 10000000";
         *st = NEFTY_EINVAL;
         return nullptr;
     }

@@ -26,11 +26,11 @@ _FINAL = (N.NEFTY_JOB_DONE, N.NEFTY_JOB_FAILED, N.NEFTY_JOB_CANCELLED)
 
 class Server:
     def __init__(self, solver: Solver, lanes: int = 2, max_queue: int = 0, mem_budget_bytes: int = 0,
-                 batched: bool = True, chunk_steps: int = 0):
+                 batched: bool = True, chunk_steps: int = 0, launch_us: int = 0):
         self.solver = solver
         self._lib = solver._lib
         cfg = N.nefty_serve_config(int(lanes), int(max_queue), int(mem_budget_bytes), 1 if batched else -1,
-                                   int(chunk_steps))
+                                   int(chunk_steps), int(launch_us))
         N.check(self._lib.nefty_serve_start(solver._h, ctypes.byref(cfg)), solver._h)
         self._keep = {}
 
