@@ -100,6 +100,37 @@ def test_same_result_alone_and_in_the_mix(solver, batched):
         assert torch.equal(alone, mixed)
 
 
+def test_launches_by_device_time(solver):
+    """A tiny device-time budget per launch (300 us) makes every batched sweep
+    stop part-way by time and resume in the next launch from the step it
+    reached: a forward job's frames and loss and an inversion's alpha match
+    the direct calls, and each job took many launches."""
+    w, p, alpha, q = _case(96, 64, 24, 80, 3201)
+    obs = solver.forward(p, torch.tensor(w.alpha_target, dtype=torch.float32, device="cuda"), q_face=q,
+                         q_steps=w.q_steps)["frames"]
+    direct = solver.forward(p, alpha, q_face=q, q_steps=w.q_steps, obs=obs)
+    wi, pi, ai, qi = _case(64, 48, 16, 40, 3202)
+    obs_i = solver.forward(pi, torch.tensor(wi.alpha_target, dtype=torch.float32, device="cuda"), q_face=qi,
+                           q_steps=wi.q_steps)["frames"]
+    lr, floor, iters = 2.0, 0.05, 2
+    ref = ai.clone()
+    for _ in range(iters):
+        out = solver.adjoint_grad(pi, ref, obs_i, q_face=qi, q_steps=wi.q_steps)
+        ref = torch.clamp(ref - lr * out["grad_alpha"], min=floor)
+    with Server(solver, lanes=2, launch_us=300) as srv:
+        fr = torch.empty_like(direct["frames"])
+        j1 = srv.submit(p, alpha, q_face=q, q_steps=w.q_steps, obs=obs, frames_out=fr)
+        a_inv = ai.clone()
+        j2 = srv.submit(pi, a_inv, kind="inversion", iters=iters, lr=lr, alpha_floor=floor, q_face=qi,
+                        q_steps=wi.q_steps, obs=obs_i)
+        r1, r2 = srv.wait(j1), srv.wait(j2)
+    assert r1["state_name"] == "done" and r2["state_name"] == "done", (r1, r2)
+    assert r1["launches"] >= 5 and r2["launches"] >= 5, (r1, r2)
+    assert float((fr - direct["frames"]).norm() / direct["frames"].norm()) <= 1e-6
+    assert abs(r1["loss"] - direct["loss"]) <= 1e-6 * abs(direct["loss"])
+    assert float((a_inv - ref).norm() / ref.norm()) <= 1e-5
+
+
 def test_batched_ragged_mix_matches_direct_calls(solver):
     """Forward jobs with a loss, an inversion and a grid the batch kernel does
     not take (nx % 4 != 0) served together, their sweeps cut into 7-step
