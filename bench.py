@@ -122,7 +122,9 @@ def workload(args):
 
 def field_spec(w):
     from paper_2603_11045_gb300.field import FieldSpec
-    return FieldSpec(w.nx, w.ny, w.nz)   # 64 bands pi..128 pi, 4 x 256, alpha in [0.01, 2]
+    # 64 bands pi..128 pi, 4 x 256, alpha in [0.01, 2]; the backward at the
+    # evaluated theta takes the evaluation's activations
+    return FieldSpec(w.nx, w.ny, w.nz, keep_activations=True)
 
 
 def mlp_flops(spec):
@@ -264,14 +266,19 @@ def peaks():
         return None
 
 
-def field_launches(spec):
-    """Kernels of one nefty_field_eval + nefty_field_backward + nefty_tv call."""
-    L = spec.depth
-    ev = 3 + 1 + L + L + 1          # axis tables, features, BF16 weights, layer GEMMs, head
-    # backward: the forward layers again, head backward, 2 x 2 output-layer sums,
-    # L weight transposes, per layer (2 bias sums, 2 transposes, weight-gradient
-    # GEMM, split-K reduce) and L - 1 input-gradient GEMMs
-    bw = (ev - 1) + 1 + 4 + L + 6 * L + (L - 1)
+def field_launches(spec, reuse):
+    """Kernels of one nefty_field_eval + nefty_field_backward + nefty_tv call
+    (no band weights).  reuse: the backward took the evaluation's kept
+    activations (one parameter comparison instead of the forward layers)."""
+    L, ns = spec.depth, 3 if spec.precision == 1 else 1
+    # axis tables, features (+ the skip layer's feature copies), BF16 weights, layer GEMMs
+    fwd = 3 + 1 + (ns if spec.skip_layer else 0) + L + L
+    ev = fwd + 1                    # + head
+    # backward: the forward layers again (or the comparison), head backward,
+    # 2 x 2 output-layer sums, L weight transposes, h_0^T, the top delta's
+    # transpose (ns blocks), per layer 2 bias sums + weight-gradient GEMM +
+    # split-K reduce, and L - 1 input-gradient GEMMs
+    bw = (1 if reuse else fwd) + 1 + 4 + L + 1 + ns + 4 * L + (L - 1)
     return ev + bw + 1              # + TV
 
 
@@ -354,6 +361,7 @@ def run_native(args):
     torch.cuda.synchronize(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     stats = []
+    reuses0 = int(solver._lib.nefty_field_activation_reuses(solver._h))
     for k in range(args.steps):
         flush.fill_(float(k))
         ev[k][0].record(stream)
@@ -364,6 +372,8 @@ def run_native(args):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
+    # every timed backward took the evaluation's kept activations
+    reused = int(solver._lib.nefty_field_activation_reuses(solver._h)) - reuses0 == args.steps
     step_ms = [a.elapsed_time(b) for a, b in ev]
     f_fwd = [e[0].elapsed_time(e[1]) for e, _ in field_ms[-args.steps:]]
     f_bwd = [e[2].elapsed_time(e[3]) for e, _ in field_ms[-args.steps:]]
@@ -415,6 +425,7 @@ def run_native(args):
                     "traffic": None, "kernel": "tcgen05 BF16 GEMMs of the field (eval + backward calls)",
                     "peak_source": "measured sustained bf16 (MEASURED_PEAKS.json)" if pk else "fallback",
                     "field_eval_ms": f_fwd_ms, "field_backward_ms": f_bwd_ms,
+                    "backward_reused_activations": reused,
                     "flops_per_step": fwd_fl + bwd_fl}
 
     # error of the timed configuration against the FP64 GPU path, outside the
@@ -478,7 +489,7 @@ def run_native(args):
                 "warmup": max(3, args.warmup), "ms_per_step": max_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if R == "fp32" else "f64",
                 "data": "synthetic", "config": config_dict(args, w), "parallelism": f"replicas x{world}",
-                "gpu_launches": launches * args.steps + field_launches(spec) * args.steps, "e2e": e2e,
+                "gpu_launches": launches * args.steps + field_launches(spec, reused) * args.steps, "e2e": e2e,
                 "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                                "max": float(max(step_ms)), "per": "inversion step (device time, CUDA events)"},
                 "error": error,
@@ -680,6 +691,7 @@ def run_paper_inversion(args):
     from paper_2603_11045_gb300.solver import Problem, Solver
     w = S.paper_grid_case(seed=5000, nt=100)
     spec = FieldSpec.paper(w.nx, w.ny, w.nz)
+    spec.keep_activations = True   # each backward runs at the evaluated theta
     prob = Problem.from_workload(w, prec="fp32", jacobi_k=args.paper_jacobi_k)
     solver = Solver(0)
     dev = torch.device("cuda", 0)

@@ -220,6 +220,17 @@ typedef struct {
                                lo = bf16(v - hi) (about 16 significant bits) and every product
                                takes the three tensor-core products hi*hi + hi*lo + lo*hi into the
                                same FP32 accumulator: 3x the tensor work and activation memory */
+    int32_t keep_activations; /* 0 = off (default).  1: nefty_field_eval also writes what the
+                               backward needs (activations and their transposes) into a second
+                               device buffer of the handle, the size of a backward's field
+                               workspace, kept between calls; a following nefty_field_backward
+                               with the same descriptor, bitwise-equal theta and band weights
+                               (compared on the device) takes them from there instead of
+                               running the forward layers again.  Any other call leaves the
+                               result unchanged: the backward recomputes, bit for bit the same
+                               gradient.  The buffer counts against the memory budget; when a
+                               workspace needs the room it is freed (the next backward then
+                               recomputes), and when it does not fit the call runs as with 0. */
 } nefty_field_desc;
 
 /* Number of FP32 parameters of the packed vector for `d` (0 if d is invalid). */
@@ -235,6 +246,10 @@ nefty_status nefty_field_eval(nefty_handle *h, const nefty_field_desc *d, const 
 nefty_status nefty_field_backward(nefty_handle *h, const nefty_field_desc *d, const float *theta,
                                   const float *band_weights, const float *grad_alpha, float *grad_theta,
                                   void *stream);
+
+/* Number of nefty_field_backward calls on h that took the activations of a
+ * keep_activations evaluation instead of recomputing them (0 for NULL). */
+uint64_t nefty_field_activation_reuses(const nefty_handle *h);
 
 /* The field's tensor-core GEMM on its own: C[M x N] (FP32, row-major, ld N) =
  * A[M x K] B[N x K]^T with A, B BF16 row-major (lda, ldb in elements, multiples of 8)

@@ -34,7 +34,8 @@ class nefty_field_desc(ctypes.Structure):
                 ("n_freq", ctypes.c_int32), ("width", ctypes.c_int32), ("depth", ctypes.c_int32),
                 ("freq_lo", ctypes.c_double), ("freq_hi", ctypes.c_double),
                 ("alpha_min", ctypes.c_double), ("alpha_max", ctypes.c_double),
-                ("skip_layer", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("skip_layer", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("keep_activations", ctypes.c_int32)]
 
 
 class nefty_stats(ctypes.Structure):
@@ -103,6 +104,7 @@ _SIGNATURES = {
     "nefty_adjoint_grad": ([_vp, _P, _vp, _vp, _vp, ctypes.c_int32, _vp, _vp,
                             ctypes.POINTER(ctypes.c_double), _vp, _vp, _ST, _vp], ctypes.c_int),
     "nefty_field_param_count": ([ctypes.c_void_p], ctypes.c_uint64),
+    "nefty_field_activation_reuses": ([_vp], ctypes.c_uint64),
     "nefty_field_eval": ([_vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "nefty_field_backward": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "nefty_gemm_bf16": ([_vp, _vp, ctypes.c_int32, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,

@@ -32,6 +32,14 @@ struct nefty_handle {
     // fault injection of the solver launches (nefty_debug_barrier_fault)
     uint32_t fault_missing = 0;
     uint64_t fault_wait_ns = 0;
+    // keep_activations field buffer: a backward-layout field workspace, then
+    // the theta and band-weight copies of the evaluation it holds, then a flag
+    void* keep = nullptr;
+    size_t keep_bytes = 0;
+    bool keep_valid = false;     // the buffer holds the evaluation of keep_dims at the copied parameters
+    bool keep_bw = false;        // ... with band weights (else none)
+    nefty::FieldDims keep_dims{};
+    uint64_t field_reuses = 0;
 };
 
 void nefty::set_grid_share(nefty_handle* h, int share) { h->grid_share = share > 1 ? share : 1; }
@@ -166,7 +174,16 @@ struct Arena {
     }
 };
 
+void drop_keep(nefty_handle* h) {
+    if (h->keep) cudaFree(h->keep);
+    h->keep = nullptr;
+    h->keep_bytes = 0;
+    h->keep_valid = false;
+}
+
 nefty_status ensure_workspace(nefty_handle* h, size_t bytes) {
+    // the kept field activations give way to a workspace that needs their room
+    if (h->keep && bytes > h->ws_bytes && bytes + h->keep_bytes > h->budget) drop_keep(h);
     if (bytes > h->budget) {
         char buf[160];
         snprintf(buf, sizeof buf, "workspace of %zu bytes exceeds the memory budget of %llu bytes", bytes,
@@ -1108,6 +1125,7 @@ nefty_status nefty_destroy(nefty_handle* h) {
     {
         DeviceGuard guard(h->device);
         if (h->ws) cudaFree(h->ws);
+        drop_keep(h);
     }
     delete h;
     return NEFTY_OK;
@@ -1215,6 +1233,7 @@ bool field_dims(const nefty_field_desc* d, FieldDims* out, std::string* why) {
         return false;
     }
     if (d->precision != 0 && d->precision != 1) { *why = "precision must be 0 (BF16) or 1 (split BF16)"; return false; }
+    if (d->keep_activations != 0 && d->keep_activations != 1) { *why = "keep_activations must be 0 or 1"; return false; }
     if (!(d->freq_lo > 0) || !(d->freq_hi >= d->freq_lo) || !std::isfinite(d->freq_hi)) {
         *why = "need 0 < freq_lo <= freq_hi";
         return false;
@@ -1242,6 +1261,13 @@ bool field_dims(const nefty_field_desc* d, FieldDims* out, std::string* why) {
         out->colsum_blocks = (int)std::min<unsigned>(1024u, std::max(1u, out->Mp / 256u));
     }
     return true;
+}
+
+// Descriptors that give the same activations and head.
+bool same_field(const FieldDims& a, const FieldDims& b) {
+    return a.nx == b.nx && a.ny == b.ny && a.nz == b.nz && a.F == b.F && a.W == b.W && a.depth == b.depth &&
+           a.skip == b.skip && a.ns == b.ns && a.freq_lo == b.freq_lo && a.freq_hi == b.freq_hi &&
+           a.alpha_min == b.alpha_min && a.alpha_max == b.alpha_max;
 }
 
 }  // namespace
@@ -1283,31 +1309,80 @@ static nefty_status field_call(nefty_handle* h, const nefty_field_desc* d, const
     Output o;
     o.plan(out, (backward ? P : (size_t)fd.M) * 4, h->device);
     if (nefty_status e = reject_foreign(h, th, bw, ga, o)) return e;
+    // keep_activations: the field workspace is the handle's kept buffer (the
+    // backward layout, then copies of theta and the band weights, then a flag)
+    const size_t bwd_bytes = field_workspace_bytes(fd, true);
+    const size_t snap_th = (bwd_bytes + 255) & ~(size_t)255, snap_bw = snap_th + ((P * 4 + 255) & ~(size_t)255);
+    const size_t snap_flag = snap_bw + (((size_t)fd.F * 4 + 255) & ~(size_t)255), keep_need = snap_flag + 256;
+    bool keep = d->keep_activations == 1;
     char* fws = nullptr;
-    const size_t fbytes = field_workspace_bytes(fd, backward);
     auto layout = [&](Arena& a) {
         th.place(a); bw.place(a); ga.place(a); o.place(a);
-        fws = (char*)a.take(fbytes);
+        if (!keep) fws = (char*)a.take(field_workspace_bytes(fd, backward));
     };
     Arena probe;
+    if (keep) {   // the staging workspace first, then the kept buffer in the room left
+        layout(probe);
+        if (nefty_status e = ensure_workspace(h, probe.off)) return e;
+        if (h->keep_bytes < keep_need) {
+            drop_keep(h);
+            if (keep_need + h->ws_bytes <= h->budget && cudaMalloc(&h->keep, keep_need) == cudaSuccess)
+                h->keep_bytes = keep_need;
+            else {
+                cudaGetLastError();
+                h->keep = nullptr;
+                keep = false;   // no room: run as without keep_activations
+            }
+        }
+        probe = Arena();
+    }
     layout(probe);
     if (nefty_status e = ensure_workspace(h, probe.off)) return e;
+    if (keep && !h->keep) keep = false;   // the workspace took the kept buffer's room
     Arena arena;
     arena.base = (char*)h->ws;
     layout(arena);
+    if (keep) fws = (char*)h->keep;
     for (Input* in : {&th, &bw, &ga})
         if (in->user && in->stage) NEFTY_CUDA(h, cudaMemcpyAsync(in->dev, in->user, in->bytes, cudaMemcpyHostToDevice, s));
+    float* const kth = keep ? (float*)(fws + snap_th) : nullptr;
+    float* const kbw = keep ? (float*)(fws + snap_bw) : nullptr;
+    bool reuse = false;
+    if (keep && backward && h->keep_valid && same_field(h->keep_dims, fd) && h->keep_bw == (bw.dev != nullptr)) {
+        // the kept evaluation is reused only at bitwise-equal parameters
+        int* flag = (int*)(fws + snap_flag);
+        NEFTY_CUDA(h, cudaMemsetAsync(flag, 1, sizeof(int), s));
+        NEFTY_CUDA(h, field_params_equal((const float*)th.dev, kth, P, flag, s));
+        if (bw.dev) NEFTY_CUDA(h, field_params_equal((const float*)bw.dev, kbw, (size_t)fd.F, flag, s));
+        int same = 0;
+        NEFTY_CUDA(h, cudaMemcpyAsync(&same, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        NEFTY_CUDA(h, cudaStreamSynchronize(s));
+        reuse = same != 0;
+    }
+    if (keep) h->keep_valid = false;   // until this call has finished writing the buffer
     if (backward)
         NEFTY_CUDA(h, field_backward(fd, (const float*)th.dev, (const float*)bw.dev, (const float*)ga.dev,
-                                     (float*)o.dev, fws, s));
+                                     (float*)o.dev, fws, s, reuse));
     else
-        NEFTY_CUDA(h, field_eval(fd, (const float*)th.dev, (const float*)bw.dev, (float*)o.dev, fws, s));
+        NEFTY_CUDA(h, field_eval(fd, (const float*)th.dev, (const float*)bw.dev, (float*)o.dev, fws, s, keep));
+    if (keep && !reuse) {   // the buffer now holds the evaluation at these parameters
+        NEFTY_CUDA(h, cudaMemcpyAsync(kth, th.dev, P * 4, cudaMemcpyDeviceToDevice, s));
+        if (bw.dev) NEFTY_CUDA(h, cudaMemcpyAsync(kbw, bw.dev, (size_t)fd.F * 4, cudaMemcpyDeviceToDevice, s));
+    }
     if (o.stage) NEFTY_CUDA(h, cudaMemcpyAsync(o.user, o.dev, o.bytes, cudaMemcpyDeviceToHost, s));
-    const int err = field_error(fd, fws, s, backward);
+    const int err = field_error(fd, fws, s, backward || keep);
     if (err < 0) return fail(h, NEFTY_ECUDA, "field: stream synchronisation failed");
     if (err > 0) return fail(h, NEFTY_ETIMEOUT, "field: a tensor-core pipeline wait timed out");
+    if (keep) {
+        h->keep_valid = true;
+        h->keep_bw = bw.dev != nullptr;
+        h->keep_dims = fd;
+    }
+    if (reuse) ++h->field_reuses;
     return NEFTY_OK;
 }
+
+uint64_t nefty_field_activation_reuses(const nefty_handle* h) { return h ? h->field_reuses : 0; }
 
 nefty_status nefty_field_eval(nefty_handle* h, const nefty_field_desc* d, const float* theta,
                               const float* band_weights, float* alpha_out, void* stream) {

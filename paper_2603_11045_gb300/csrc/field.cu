@@ -125,6 +125,54 @@ __global__ void features_kernel(__nv_bfloat16* h0, unsigned M, unsigned Mp, int 
     }
 }
 
+// h_0^T [Dp x ns Mp] straight from the axis tables, as the B side of the
+// first layer's weight-gradient product: row f holds feature f of every cell,
+// the split blocks in B-side order [hi | lo | hi] at column offsets 0, Mp,
+// 2 Mp (zeros for padded cells and features).  The same BF16 values as
+// features_kernel writes, transposed; each thread writes 8 consecutive cells
+// (16 bytes per block; Mp is a multiple of 128).
+__global__ void features_t_kernel(__nv_bfloat16* hT, unsigned M, unsigned Mp, int nx, int ny, int F, int Dp, int ns,
+                                  const float* tx, const float* ty, const float* tz) {
+    const int D = 6 * F, F2 = 2 * F;
+    const unsigned per = Mp / 8;   // 8-cell chunks per feature row
+    const size_t ldt = (size_t)ns * Mp;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)Dp * per;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int f = (int)(e / per);
+        const unsigned c0 = (unsigned)(e - (size_t)f * per) * 8;
+        float v[8];
+        const int d = f / F2, r = f - d * F2;
+        unsigned cy = c0 / (unsigned)nx, i = c0 - cy * (unsigned)nx;
+        unsigned k = cy / (unsigned)ny, j = cy - k * (unsigned)ny;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const unsigned c = c0 + t;
+            float x = 0.f;
+            if (c < M && f < D)
+                x = d == 0 ? tx[(size_t)i * F2 + r] : (d == 1 ? ty[(size_t)j * F2 + r] : tz[(size_t)k * F2 + r]);
+            v[t] = x;
+            if (++i == (unsigned)nx) {
+                i = 0;
+                if (++j == (unsigned)ny) { j = 0; ++k; }
+            }
+        }
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * t], v[2 * t + 1]);
+            const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[2 * t] - __low2float(h2), v[2 * t + 1] - __high2float(h2));
+            hi[t] = *reinterpret_cast<const uint32_t*>(&h2);
+            lo[t] = *reinterpret_cast<const uint32_t*>(&l2);
+        }
+        __nv_bfloat16* out = hT + (size_t)f * ldt + c0;
+        *reinterpret_cast<uint4*>(out) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        if (ns == 3) {
+            *reinterpret_cast<uint4*>(out + Mp) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            *reinterpret_cast<uint4*>(out + 2 * (size_t)Mp) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        }
+    }
+}
+
 // dst [R x Cp] = bf16(src [R x C]) with zero columns C .. Cp-1; with ns = 3
 // rows of 3 Cp values, the split blocks in B-side order [hi | lo | hi].
 __global__ void to_bf16_kernel(const float* src, __nv_bfloat16* dst, int R, int C, int Cp, int ns) {
@@ -263,6 +311,19 @@ template <typename T>
 __global__ void colsum_partial_kernel(const T* A, size_t lda, int lo_off, const float* v, unsigned M, int C,
                                       unsigned rows_per_block, double* part) {
     const unsigned r0 = blockIdx.x * rows_per_block, r1 = min(M, r0 + rows_per_block);
+    if (C == 1) {   // one column: every thread takes a stride of rows, then a fixed tree over the block
+        __shared__ float red[1024];
+        float s = 0.f;
+        for (unsigned m = r0 + threadIdx.x; m < r1; m += blockDim.x) s += ld<T>(A, (size_t)m * lda, lo_off) * (v ? v[m] : 1.f);
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (unsigned h = blockDim.x / 2; h > 0; h >>= 1) {
+            if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[blockIdx.x] = (double)red[0];
+        return;
+    }
     for (int j = threadIdx.x; j < C; j += blockDim.x) {
         float s = 0.f;   // FP32 within a block of rows, FP64 across blocks
         for (unsigned m = r0; m < r1; ++m) s += ld<T>(A, (size_t)m * lda + j, lo_off) * (v ? v[m] : 1.f);
@@ -270,11 +331,16 @@ __global__ void colsum_partial_kernel(const T* A, size_t lda, int lo_off, const 
     }
 }
 
+// One warp per column: lane t sums partials t, t + 32, ..., then a fixed
+// butterfly over the lanes (the same order on every run).
 __global__ void colsum_final_kernel(const double* part, int nblk, int C, float* out) {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < C; j += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < C; j += (gridDim.x * blockDim.x) >> 5) {
         double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += part[(size_t)b * C + j];
-        out[j] = (float)s;
+        for (int b = lane; b < nblk; b += 32) s += part[(size_t)b * C + j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[j] = (float)s;
     }
 }
 
@@ -289,6 +355,14 @@ __global__ void split_reduce_kernel(const float* part, int splits, int R, int Cp
         for (int z = 0; z < splits; ++z) s += part[(size_t)z * n + i];
         out[e] = s;
     }
+}
+
+// *flag = 0 when a and b differ in any bit (the caller sets it nonzero first)
+__global__ void same_bits_kernel(const uint32_t* a, const uint32_t* b, size_t n, int* flag) {
+    bool differ = false;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        differ |= a[e] != b[e];
+    if (__any_sync(0xffffffffu, differ) && (threadIdx.x & 31) == 0) *flag = 0;
 }
 
 inline unsigned blocks_for(size_t n, unsigned t = kT) {
@@ -412,8 +486,9 @@ static cudaError_t forward_layers(const FieldDims& d, const float* theta, const 
     axis_table_kernel<<<blocks_for((size_t)d.nx * F), kT, 0, s>>>(w.tx, d.nx, F, lo, ratio_log, band_w);
     axis_table_kernel<<<blocks_for((size_t)d.ny * F), kT, 0, s>>>(w.ty, d.ny, F, lo, ratio_log, band_w);
     axis_table_kernel<<<blocks_for((size_t)d.nz * F), kT, 0, s>>>(w.tz, d.nz, F, lo, ratio_log, band_w);
-    features_kernel<<<blocks_for((size_t)d.Mp * d.Dp), kT, 0, s>>>(w.h[0], d.M, d.Mp, d.nx, d.ny, F, d.Dp, ns, w.tx,
-                                                                   w.ty, w.tz);
+    // one thread per 16-byte chunk of a cell's features (F % 4 == 0), else per feature
+    const size_t fwork = (size_t)d.Mp * (F % 4 == 0 ? d.Dp / 8 : d.Dp);
+    features_kernel<<<blocks_for(fwork), kT, 0, s>>>(w.h[0], d.M, d.Mp, d.nx, d.ny, F, d.Dp, ns, w.tx, w.ty, w.tz);
     if (d.skip > 0)   // the encoding beside h_s in each block of the skip layer's input
         for (int b = 0; b < ns; ++b)
             copy_cols_kernel<<<blocks_for((size_t)d.Mp * d.Dp / 8), kT, 0, s>>>(
@@ -448,11 +523,11 @@ static cudaError_t forward_layers(const FieldDims& d, const float* theta, const 
 }
 
 cudaError_t field_eval(const FieldDims& d, const float* theta, const float* band_w, float* alpha, char* ws,
-                       cudaStream_t s) {
-    FieldWs w = carve(ws, d, false);
+                       cudaStream_t s, bool keep) {
+    FieldWs w = carve(ws, d, keep);
     cudaError_t e = cudaMemsetAsync(w.err, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    if ((e = forward_layers(d, theta, band_w, w, s, false)) != cudaSuccess) return e;
+    if ((e = forward_layers(d, theta, band_w, w, s, keep)) != cudaSuccess) return e;
     const float* w_out = theta + field_param_count(d.F, d.W, d.depth, d.skip) - d.W - 1;
     head_kernel<<<blocks_for((size_t)d.M * 32), kT, 0, s>>>(w.h[d.depth], (size_t)h_ld(d, d.depth),
                                                             d.ns == 3 ? 2 * d.W : 0, d.W, w_out, w_out + d.W, d.M,
@@ -461,13 +536,15 @@ cudaError_t field_eval(const FieldDims& d, const float* theta, const float* band
 }
 
 cudaError_t field_backward(const FieldDims& d, const float* theta, const float* band_w, const float* g_alpha,
-                           float* g_theta, char* ws, cudaStream_t s) {
+                           float* g_theta, char* ws, cudaStream_t s, bool reuse) {
     FieldWs w = carve(ws, d, true);
     const int W = d.W, ns = d.ns;
     const int lo_w = ns == 3 ? 2 * W : 0;   // column offset of the lo block of a W-wide split row
     cudaError_t e = cudaMemsetAsync(w.err, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    if ((e = forward_layers(d, theta, band_w, w, s, true)) != cudaSuccess) return e;
+    // reuse: ws already holds the activations, their transposes and the axis
+    // tables of a keep-mode evaluation at these same parameters
+    if (!reuse && (e = forward_layers(d, theta, band_w, w, s, true)) != cudaSuccess) return e;
     // parameter offsets (packed) and weight-copy offsets (stored, in units of one block)
     size_t poff[16], woff[16];
     {
@@ -490,7 +567,7 @@ cudaError_t field_backward(const FieldDims& d, const float* theta, const float* 
     const unsigned rpb = (d.Mp + d.colsum_blocks - 1) / d.colsum_blocks;
     colsum_partial_kernel<__nv_bfloat16><<<d.colsum_blocks, kT, 0, s>>>(w.h[d.depth], (size_t)h_ld(d, d.depth), lo_w,
                                                                       w.gf, d.Mp, W, rpb, w.colpart);
-    colsum_final_kernel<<<blocks_for(W), kT, 0, s>>>(w.colpart, d.colsum_blocks, W, g_wout);
+    colsum_final_kernel<<<blocks_for((size_t)W * 32), kT, 0, s>>>(w.colpart, d.colsum_blocks, W, g_wout);
     colsum_partial_kernel<float><<<d.colsum_blocks, kT, 0, s>>>(w.gf, 1, 0, nullptr, d.Mp, 1, rpb, w.colpart);
     colsum_final_kernel<<<1, 32, 0, s>>>(w.colpart, d.colsum_blocks, 1, g_wout + W);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -505,7 +582,8 @@ cudaError_t field_backward(const FieldDims& d, const float* theta, const float* 
         }
     }
     // h_0^T (B side), also the encoding rows of the skip layer's h^T
-    transpose_operand(w.h[0], (size_t)ns * d.Dp, w.tB, d.Mp, d.Dp, ns, true, s);
+    features_t_kernel<<<blocks_for((size_t)d.Dp * (d.Mp / 8)), kT, 0, s>>>(w.tB, d.M, d.Mp, d.nx, d.ny, d.F, d.Dp,
+                                                                          ns, w.tx, w.ty, w.tz);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (d.skip > 0 && d.skip < d.depth) {
         e = cudaMemcpyAsync(w.hT[d.skip] + (size_t)W * ns * d.Mp, w.tB, (size_t)d.Dp * ns * d.Mp * 2,
@@ -519,7 +597,7 @@ cudaError_t field_backward(const FieldDims& d, const float* theta, const float* 
         // db_l = column sums of delta
         colsum_partial_kernel<__nv_bfloat16><<<d.colsum_blocks, kT, 0, s>>>(w.dl[cur], (size_t)ns * W, lo_w, nullptr,
                                                                           d.Mp, W, rpb, w.colpart);
-        colsum_final_kernel<<<blocks_for(W), kT, 0, s>>>(w.colpart, d.colsum_blocks, W,
+        colsum_final_kernel<<<blocks_for((size_t)W * 32), kT, 0, s>>>(w.colpart, d.colsum_blocks, W,
                                                          g_theta + poff[l] + (size_t)W * in);
         // dW_l = delta^T h_l: K-major operands are the transposes [W x ns Mp] (A
         // side) and [ins x ns Mp] (B side).  delta^T comes from the previous
@@ -545,6 +623,13 @@ cudaError_t field_backward(const FieldDims& d, const float* theta, const float* 
             cur ^= 1;
         }
     }
+    return cudaGetLastError();
+}
+
+cudaError_t field_params_equal(const float* a, const float* b, size_t n, int* flag, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    same_bits_kernel<<<blocks_for(n), kT, 0, s>>>(reinterpret_cast<const uint32_t*>(a),
+                                                  reinterpret_cast<const uint32_t*>(b), n, flag);
     return cudaGetLastError();
 }
 

@@ -318,10 +318,15 @@ struct FieldDims {
 };
 size_t field_param_count(int F, int W, int depth, int skip);
 size_t field_workspace_bytes(const FieldDims& d, bool backward);
+// keep: ws has the backward layout and the evaluation also leaves there what
+// field_backward needs (activations, their transposes, the axis tables);
+// reuse: field_backward takes them from ws instead of recomputing them.
 cudaError_t field_eval(const FieldDims& d, const float* theta, const float* band_w, float* alpha, char* ws,
-                       cudaStream_t s);
+                       cudaStream_t s, bool keep = false);
 cudaError_t field_backward(const FieldDims& d, const float* theta, const float* band_w, const float* g_alpha,
-                           float* g_theta, char* ws, cudaStream_t s);
+                           float* g_theta, char* ws, cudaStream_t s, bool reuse = false);
+// *flag = 0 if the n floats at a and b differ in any bit (left as is otherwise)
+cudaError_t field_params_equal(const float* a, const float* b, size_t n, int* flag, cudaStream_t s);
 int field_error(const FieldDims& d, char* ws, cudaStream_t s, bool backward);
 // tcgen05 BF16 GEMM (umma_gemm.cu): D = A B^T, epi 0 bias+relu->bf16, 1 mask->bf16, 2 fp32 split partials;
 // the BF16 epilogues can also write D^T [N x ldt] (out_t); the mask has leading

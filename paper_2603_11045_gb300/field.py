@@ -37,6 +37,7 @@ class FieldSpec:
     alpha_max: float = 2.0
     skip_layer: int = 0
     precision: int = 0      # 0: BF16 operands; 1: split BF16 (hi + lo, three products each)
+    keep_activations: bool = False   # the evaluation keeps what a backward at the same theta needs
 
     @classmethod
     def paper(cls, nx: int, ny: int, nz: int, alpha_min: float = 0.003, alpha_max: float = 0.25,
@@ -48,7 +49,7 @@ class FieldSpec:
     def to_c(self) -> N.nefty_field_desc:
         return N.nefty_field_desc(self.nx, self.ny, self.nz, self.n_freq, self.width, self.depth,
                                   self.freq_lo, self.freq_hi, self.alpha_min, self.alpha_max, self.skip_layer,
-                                  self.precision)
+                                  self.precision, int(self.keep_activations))
 
     @property
     def n_params(self) -> int:

@@ -185,3 +185,135 @@ def test_inversion_chain_finite_differences(solver, orc):
     got = grad[idx]
     assert np.linalg.norm(got - fd) <= 5e-2 * np.linalg.norm(fd)
     assert float(got @ fd / (np.linalg.norm(got) * np.linalg.norm(fd))) >= 0.99
+
+
+def _field_calls(solver, spec, theta, bw, g_a):
+    """alpha and grad_theta through the C ABI with spec's descriptor."""
+    import ctypes
+    d = spec.to_c()
+    sp = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    p = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+    a = torch.empty(spec.nz, spec.ny, spec.nx, device="cuda")
+    g = torch.empty_like(theta)
+    st = solver._lib.nefty_field_eval(solver._h, ctypes.byref(d), p(theta), p(bw), p(a), sp)
+    assert st == 0, solver._lib.nefty_last_error(solver._h)
+    return a, g, d, sp, p
+
+
+def _backward(solver, d, sp, p, theta, bw, g_a, g):
+    import ctypes
+    st = solver._lib.nefty_field_backward(solver._h, ctypes.byref(d), p(theta), p(bw), p(g_a), p(g), sp)
+    assert st == 0, solver._lib.nefty_last_error(solver._h)
+    return g.clone()
+
+
+KEEP_CASES = [dict(nx=20, ny=16, nz=8, n_freq=64, width=256, depth=4),
+              dict(nx=14, ny=9, nz=5, n_freq=5, width=128, depth=3, skip_layer=2, precision=1)]
+
+
+@pytest.mark.parametrize("c", KEEP_CASES)
+def test_keep_activations_reuse_is_bitwise(solver, c):
+    """keep_activations: a backward at the evaluated theta takes the kept
+    activations (the reuse counter moves) and gives bit for bit the gradient
+    of a recomputing backward; alpha is unchanged by the mode."""
+    from dataclasses import replace
+    from paper_2603_11045_gb300.field import annealing_weights
+    spec = _spec(c)
+    keep = replace(spec, keep_activations=True)
+    th = S.xavier_theta(spec.n_freq, spec.width, spec.depth, 31, skip=spec.skip_layer)
+    theta = torch.tensor(th, dtype=torch.float32, device="cuda")
+    bw = torch.tensor(annealing_weights(spec.n_freq, spec.n_freq * 0.7), dtype=torch.float32, device="cuda")
+    g_a = torch.tensor(S.rng(32).standard_normal((spec.nz, spec.ny, spec.nx)), dtype=torch.float32, device="cuda")
+    lib = solver._lib
+    a0, g, d0, sp, p = _field_calls(solver, spec, theta, bw, g_a)
+    ref = _backward(solver, d0, sp, p, theta, bw, g_a, g)
+    n0 = lib.nefty_field_activation_reuses(solver._h)
+    a1, g, d1, sp, p = _field_calls(solver, keep, theta, bw, g_a)
+    got = _backward(solver, d1, sp, p, theta, bw, g_a, g)
+    assert lib.nefty_field_activation_reuses(solver._h) == n0 + 1
+    assert torch.equal(a0, a1)
+    assert torch.equal(got, ref)
+    # a second backward at the same theta (another g_alpha) reuses again
+    g_b = g_a.flip(0).contiguous()
+    got_b = _backward(solver, d1, sp, p, theta, bw, g_b, g)
+    assert lib.nefty_field_activation_reuses(solver._h) == n0 + 2
+    assert torch.equal(got_b, _backward(solver, d0, sp, p, theta, bw, g_b, g))
+
+
+def test_keep_activations_recomputes_on_any_change(solver):
+    """theta changed in place (same pointer), other band weights, none where
+    the evaluation had some, another descriptor: each backward recomputes
+    and matches the plain backward bit for bit."""
+    from dataclasses import replace
+    from paper_2603_11045_gb300.field import annealing_weights
+    spec = _spec(dict(nx=20, ny=16, nz=8, n_freq=64, width=256, depth=4))
+    keep = replace(spec, keep_activations=True)
+    th = S.xavier_theta(spec.n_freq, spec.width, spec.depth, 33)
+    theta = torch.tensor(th, dtype=torch.float32, device="cuda")
+    bw = torch.tensor(annealing_weights(spec.n_freq, spec.n_freq * 0.4), dtype=torch.float32, device="cuda")
+    g_a = torch.tensor(S.rng(34).standard_normal((spec.nz, spec.ny, spec.nx)), dtype=torch.float32, device="cuda")
+    lib = solver._lib
+    _, g, d0, sp, p = _field_calls(solver, spec, theta, bw, g_a)
+    d1 = keep.to_c()
+    n0 = lib.nefty_field_activation_reuses(solver._h)
+
+    def check(th_b, bw_b, d_b=d1):
+        got = _backward(solver, d_b, sp, p, th_b, bw_b, g_a, g)
+        ref = _backward(solver, d0 if d_b is d1 else d_b, sp, p, th_b, bw_b, g_a, g)
+        assert torch.equal(got, ref)
+
+    _field_calls(solver, keep, theta, bw, g_a)
+    theta[5] += 1e-3                       # one weight, in place
+    check(theta, bw)
+    _field_calls(solver, keep, theta, bw, g_a)
+    check(theta, bw * 0.5)                 # other band weights
+    _field_calls(solver, keep, theta, bw, g_a)
+    check(theta, None)                     # none
+    _field_calls(solver, keep, theta, bw, g_a)
+    other = replace(keep, alpha_max=3.0).to_c()
+    got = _backward(solver, other, sp, p, theta, bw, g_a, g)
+    assert torch.equal(got, _backward(solver, replace(spec, alpha_max=3.0).to_c(), sp, p, theta, bw, g_a, g))
+    assert lib.nefty_field_activation_reuses(solver._h) == n0
+
+
+def test_keep_activations_without_room_runs_plain():
+    """A budget that holds a plain backward's workspace but not the kept
+    buffer: the calls run as without keep_activations (no reuse) and give
+    the same results bit for bit."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import ctypes
+    import re
+    from dataclasses import replace
+    from paper_2603_11045_gb300.solver import Solver
+    spec = _spec(dict(nx=20, ny=16, nz=8, n_freq=64, width=256, depth=4))
+    keep = replace(spec, keep_activations=True)
+    th = S.xavier_theta(spec.n_freq, spec.width, spec.depth, 35)
+    theta = torch.tensor(th, dtype=torch.float32, device="cuda")
+    g_a = torch.tensor(S.rng(36).standard_normal((spec.nz, spec.ny, spec.nx)), dtype=torch.float32, device="cuda")
+    g = torch.empty_like(theta)
+    # the plain backward's workspace size, from the budget error of a 1 MiB handle
+    tiny = Solver(0, mem_budget_bytes=1 << 20)
+    try:
+        d = spec.to_c()
+        st = tiny._lib.nefty_field_backward(tiny._h, ctypes.byref(d), ctypes.c_void_p(theta.data_ptr()), None,
+                                            ctypes.c_void_p(g_a.data_ptr()), ctypes.c_void_p(g.data_ptr()), None)
+        assert st == 2   # NEFTY_ENOMEM
+        msg = tiny._lib.nefty_last_error(tiny._h).decode()
+        need = int(re.search(r"workspace of (\d+) bytes", msg).group(1))
+    finally:
+        tiny.close()
+    big = Solver(0)
+    try:
+        a0, g, d0, sp, p = _field_calls(big, spec, theta, None, g_a)
+        ref = _backward(big, d0, sp, p, theta, None, g_a, g)
+    finally:
+        big.close()
+    small = Solver(0, mem_budget_bytes=need)
+    try:
+        a1, g, d1, sp, p = _field_calls(small, keep, theta, None, g_a)
+        got = _backward(small, d1, sp, p, theta, None, g_a, g)
+        assert small._lib.nefty_field_activation_reuses(small._h) == 0
+        assert torch.equal(a0, a1) and torch.equal(got, ref)
+    finally:
+        small.close()
