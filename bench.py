@@ -274,11 +274,18 @@ def field_launches(spec, reuse):
     # axis tables, features (+ the skip layer's feature copies), BF16 weights, layer GEMMs
     fwd = 3 + 1 + (ns if spec.skip_layer else 0) + L + L
     ev = fwd + 1                    # + head
-    # backward: the forward layers again (or the comparison), head backward,
-    # 2 x 2 output-layer sums, L weight transposes, h_0^T, the top delta's
-    # transpose (ns blocks), per layer 2 bias sums + weight-gradient GEMM +
-    # split-K reduce, and L - 1 input-gradient GEMMs
-    bw = (1 if reuse else fwd) + 1 + 4 + L + 1 + ns + 4 * L + (L - 1)
+    # backward: the forward layers again (or the comparison); the head pass
+    # (fused: g_f, top delta and its transpose, three partial sums, then their
+    # three final sums; with a head too wide for its shared-memory tile, head
+    # backward, 2 x 2 output-layer sums and the top delta's transpose in ns
+    # blocks); L weight transposes, h_0^T; per layer 2 bias sums (the top
+    # layer's in the fused pass), weight-gradient GEMM, split-K reduce; and
+    # L - 1 input-gradient GEMMs
+    W = spec.width
+    fused = max((2 if ns == 3 else 1) * W * 16, 8 * (2 * W + 1)) * 4 <= 200 * 1024 and (W // 8 + 31) // 32 in (1, 2, 4)
+    head = 1 + 3 if fused else 1 + 4 + ns
+    bias = 2 * (L - 1) if fused else 2 * L
+    bw = (1 if reuse else fwd) + head + L + 1 + bias + 2 * L + (L - 1)
     return ev + bw + 1              # + TV
 
 

@@ -52,55 +52,68 @@ constexpr int kT = 256;
 // reaches thousands of radians for the paper's top band (2^11 pi), where a
 // single-precision product or frequency would already be off by about 1e-3
 // rad, so the n F table entries are formed in double and rounded once.
-__global__ void axis_table_kernel(float* tab, int n, int F, double lo, double ratio_log, const float* band_w) {
+// tabT [2F][n] gets the same values feature-major (for h_0^T).
+__global__ void axis_table_kernel(float* tab, float* tabT, int n, int F, double lo, double ratio_log,
+                                  const float* band_w) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * F; e += gridDim.x * blockDim.x) {
         const int i = e / F, b = e % F;
         const double x = 2.0 * ((double)i + 0.5) / (double)n - 1.0;
         const double w = F > 1 ? lo * exp(ratio_log * (double)b / (double)(F - 1)) : lo;
         const double wt = band_w ? (double)band_w[b] : 1.0;
-        tab[(size_t)i * 2 * F + 2 * b] = (float)(wt * sin(w * x));
-        tab[(size_t)i * 2 * F + 2 * b + 1] = (float)(wt * cos(w * x));
+        const float sv = (float)(wt * sin(w * x)), cv = (float)(wt * cos(w * x));
+        tab[(size_t)i * 2 * F + 2 * b] = sv;
+        tab[(size_t)i * 2 * F + 2 * b + 1] = cv;
+        tabT[(size_t)(2 * b) * n + i] = sv;
+        tabT[(size_t)(2 * b + 1) * n + i] = cv;
+    }
+}
+
+// Split of 8 FP32 values into BF16 hi words and lo = bf16(v - hi) words.
+__device__ __forceinline__ void split8(const float* v, uint32_t* hi, uint32_t* lo) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * t], v[2 * t + 1]);
+        const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[2 * t] - __low2float(h2), v[2 * t + 1] - __high2float(h2));
+        hi[t] = *reinterpret_cast<const uint32_t*>(&h2);
+        lo[t] = *reinterpret_cast<const uint32_t*>(&l2);
     }
 }
 
 // h0[c][d*2F + j] = tab_d[index_d(c)][j], as BF16, rows padded to Mp and
 // columns to Dp (zeros); rows of ns * Dp values, the split blocks [hi | hi | lo]
-// at offsets 0, Dp, 2 Dp when ns = 3.  With F % 4 == 0 each thread writes 8
-// features (16 bytes) of one cell per block, which never straddle two axes;
-// otherwise one feature at a time.
+// at offsets 0, Dp, 2 Dp when ns = 3.  With F % 4 == 0 a warp writes one
+// cell's row at a time, lane l its 16-byte chunks l, l + 32, ... (8 features,
+// never straddling two axes; the cell's axis indices are warp-uniform);
+// otherwise one feature per thread.
 __global__ void features_kernel(__nv_bfloat16* h0, unsigned M, unsigned Mp, int nx, int ny, int F, int Dp, int ns,
                                 const float* tx, const float* ty, const float* tz) {
     const int D = 6 * F, F2 = 2 * F;
     const size_t ld = (size_t)ns * Dp;
     if ((F & 3) == 0) {
-        const unsigned per = (unsigned)Dp / 8;   // 16-byte chunks per cell
-        for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)Mp * per;
-             e += (size_t)gridDim.x * blockDim.x) {
-            const unsigned c = (unsigned)(e / per);
-            const int f = (int)(e - (size_t)c * per) * 8;
-            float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (c < M && f < D) {
-                const unsigned cy = c / (unsigned)nx, i = c - cy * (unsigned)nx;
-                const unsigned k = cy / (unsigned)ny, j = cy - k * (unsigned)ny;
-                const int d = f / F2, r = f - d * F2;
-                const float* row = d == 0 ? tx + (size_t)i * F2 : (d == 1 ? ty + (size_t)j * F2 : tz + (size_t)k * F2);
-                const float4 p = *reinterpret_cast<const float4*>(row + r);
-                const float4 q = *reinterpret_cast<const float4*>(row + r + 4);
-                v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w; v[4] = q.x; v[5] = q.y; v[6] = q.z; v[7] = q.w;
-            }
-            uint32_t hi[4], lo[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * t], v[2 * t + 1]);
-                const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[2 * t] - __low2float(h2), v[2 * t + 1] - __high2float(h2));
-                hi[t] = *reinterpret_cast<const uint32_t*>(&h2);
-                lo[t] = *reinterpret_cast<const uint32_t*>(&l2);
-            }
-            __nv_bfloat16* out = h0 + (size_t)c * ld + f;
-            *reinterpret_cast<uint4*>(out) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-            if (ns == 3) {
-                *reinterpret_cast<uint4*>(out + Dp) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                *reinterpret_cast<uint4*>(out + 2 * Dp) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        const int per = Dp / 8, lane = threadIdx.x & 31;   // 16-byte chunks per cell
+        const unsigned warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+        for (unsigned c = warp0; c < Mp; c += nwarps) {
+            const unsigned cy = c / (unsigned)nx, i = c - cy * (unsigned)nx;
+            const unsigned k = cy / (unsigned)ny, j = cy - k * (unsigned)ny;
+            for (int q = lane; q < per; q += 32) {
+                const int f = 8 * q;
+                float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (c < M && f < D) {
+                    const int d = f / F2, r = f - d * F2;
+                    const float* row = d == 0 ? tx + (size_t)i * F2 : (d == 1 ? ty + (size_t)j * F2 : tz + (size_t)k * F2);
+                    const float4 p = *reinterpret_cast<const float4*>(row + r);
+                    const float4 p2 = *reinterpret_cast<const float4*>(row + r + 4);
+                    v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w; v[4] = p2.x; v[5] = p2.y; v[6] = p2.z; v[7] = p2.w;
+                }
+                uint32_t hi[4], lo[4];
+                split8(v, hi, lo);
+                __nv_bfloat16* out = h0 + (size_t)c * ld + f;
+                *reinterpret_cast<uint4*>(out) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                if (ns == 3) {
+                    *reinterpret_cast<uint4*>(out + Dp) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                    *reinterpret_cast<uint4*>(out + 2 * Dp) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                }
             }
         }
         return;
@@ -125,46 +138,52 @@ __global__ void features_kernel(__nv_bfloat16* h0, unsigned M, unsigned Mp, int 
     }
 }
 
-// h_0^T [Dp x ns Mp] straight from the axis tables, as the B side of the
-// first layer's weight-gradient product: row f holds feature f of every cell,
-// the split blocks in B-side order [hi | lo | hi] at column offsets 0, Mp,
-// 2 Mp (zeros for padded cells and features).  The same BF16 values as
-// features_kernel writes, transposed; each thread writes 8 consecutive cells
-// (16 bytes per block; Mp is a multiple of 128).
-__global__ void features_t_kernel(__nv_bfloat16* hT, unsigned M, unsigned Mp, int nx, int ny, int F, int Dp, int ns,
-                                  const float* tx, const float* ty, const float* tz) {
-    const int D = 6 * F, F2 = 2 * F;
+// h_0^T [Dp x ns Mp] straight from the feature-major axis tables txT [2F][nx],
+// tyT [2F][ny], tzT [2F][nz], as the B side of the first layer's
+// weight-gradient product: row f holds feature f of every cell, the split
+// blocks in B-side order [hi | lo | hi] at column offsets 0, Mp, 2 Mp (zeros
+// for padded cells and features).  The same BF16 values as features_kernel
+// writes, transposed.  Row f = blockIdx.y; each thread writes 8 consecutive
+// cells (16 bytes per block; Mp is a multiple of 128), reading consecutive
+// table entries (x features) or one entry (y, z features) when nx % 8 == 0.
+__global__ void features_t_kernel(__nv_bfloat16* hT, unsigned M, unsigned Mp, int nx, int ny, int nz, int F, int Dp,
+                                  int ns, const float* tx, const float* ty, const float* tz) {
+    const int D = 6 * F, F2 = 2 * F, f = blockIdx.y;
+    const int d = f / F2, r = f - d * F2;
     const unsigned per = Mp / 8;   // 8-cell chunks per feature row
-    const size_t ldt = (size_t)ns * Mp;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)Dp * per;
-         e += (size_t)gridDim.x * blockDim.x) {
-        const int f = (int)(e / per);
-        const unsigned c0 = (unsigned)(e - (size_t)f * per) * 8;
-        float v[8];
-        const int d = f / F2, r = f - d * F2;
-        unsigned cy = c0 / (unsigned)nx, i = c0 - cy * (unsigned)nx;
-        unsigned k = cy / (unsigned)ny, j = cy - k * (unsigned)ny;
+    __nv_bfloat16* rowT = hT + (size_t)f * ns * Mp;
+    const bool fast = (nx & 7) == 0;
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < per; q += gridDim.x * blockDim.x) {
+        const unsigned c0 = q * 8;
+        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (f < D && c0 < M) {
+            unsigned cy = c0 / (unsigned)nx, i = c0 - cy * (unsigned)nx;
+            unsigned k = cy / (unsigned)ny, j = cy - k * (unsigned)ny;
+            if (fast && c0 + 8 <= M) {   // the 8 cells share j and k
+                if (d == 0) {
+                    const float4 p = *reinterpret_cast<const float4*>(tx + (size_t)r * nx + i);
+                    const float4 p2 = *reinterpret_cast<const float4*>(tx + (size_t)r * nx + i + 4);
+                    v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w; v[4] = p2.x; v[5] = p2.y; v[6] = p2.z; v[7] = p2.w;
+                } else {
+                    const float x = d == 1 ? ty[(size_t)r * ny + j] : tz[(size_t)r * nz + k];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const unsigned c = c0 + t;
-            float x = 0.f;
-            if (c < M && f < D)
-                x = d == 0 ? tx[(size_t)i * F2 + r] : (d == 1 ? ty[(size_t)j * F2 + r] : tz[(size_t)k * F2 + r]);
-            v[t] = x;
-            if (++i == (unsigned)nx) {
-                i = 0;
-                if (++j == (unsigned)ny) { j = 0; ++k; }
+                    for (int t = 0; t < 8; ++t) v[t] = x;
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    if (c0 + t < M)
+                        v[t] = d == 0 ? tx[(size_t)r * nx + i] : (d == 1 ? ty[(size_t)r * ny + j] : tz[(size_t)r * nz + k]);
+                    if (++i == (unsigned)nx) {
+                        i = 0;
+                        if (++j == (unsigned)ny) { j = 0; ++k; }
+                    }
+                }
             }
         }
         uint32_t hi[4], lo[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * t], v[2 * t + 1]);
-            const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[2 * t] - __low2float(h2), v[2 * t + 1] - __high2float(h2));
-            hi[t] = *reinterpret_cast<const uint32_t*>(&h2);
-            lo[t] = *reinterpret_cast<const uint32_t*>(&l2);
-        }
-        __nv_bfloat16* out = hT + (size_t)f * ldt + c0;
+        split8(v, hi, lo);
+        __nv_bfloat16* out = rowT + c0;
         *reinterpret_cast<uint4*>(out) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
         if (ns == 3) {
             *reinterpret_cast<uint4*>(out + Mp) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
@@ -294,6 +313,207 @@ __global__ void head_back_kernel(const __nv_bfloat16* h, size_t ld, int lo_off, 
     }
 }
 
+// The head's backward in one pass over h = h_depth, in tiles of kHR = 32
+// rows: per row g_f (as head_back_kernel) and the top layer's delta, written
+// row-major (rows of ns W, blocks [hi | hi | lo]) and transposed as the A side
+// of its weight-gradient product (deltaT [W x ns Mp], blocks [hi | hi | lo] at
+// column offsets 0, Mp, 2 Mp); and, per block of rows, the partial sums of
+// dw_out[j] = sum_m g_f[m] h[m][j], db_out = sum_m g_f[m] and db_top[j] =
+// sum_m delta[m][j] (the stored value: hi, + lo when split) at part
+// [blk][W], [nblk][W] + blk and [nblk][W + 1] + blk * W + j, for
+// colsum_final_kernel.  Warp w takes rows 4w .. 4w+3 of a tile, lane l the
+// 16-byte column chunks l, l + 32, ... (VC of them): a row's dot product is a
+// warp reduction and its delta is written from registers; only the transpose
+// goes through shared memory, as words holding two consecutive rows of one
+// column (kHQ words per column, the word index XOR-swizzled by the column's
+// chunk so that both the writes and the column reads spread over the banks).
+// Sums are FP32 per thread in row order, then over the block's warps in warp
+// order.
+constexpr int kHR = 32, kHQ = kHR / 2;
+__device__ __forceinline__ size_t hq_index(int col, int pair) {
+    return (size_t)col * kHQ + (pair ^ ((col >> 3) & (kHQ - 1)));
+}
+inline int head_vc(int W) { return (W / 8 + 31) / 32; }
+inline size_t head_fused_smem(int W, int ns) {
+    const size_t tiles = (size_t)(ns == 3 ? 2 : 1) * W * kHQ * 4;   // hi (and lo) transposed tiles
+    const size_t sums = (size_t)(kT / 32) * (2 * W + 1) * 4;         // per-warp partial sums, at the end
+    return std::max(tiles, sums);
+}
+constexpr size_t kHeadSmemMax = 200 * 1024;   // wider heads take the unfused kernels
+
+template <int VC, int NS>
+__global__ void __launch_bounds__(kT, (VC == 1 && NS == 1) ? 2 : 1) head_back_fused_kernel(
+    const __nv_bfloat16* h, size_t ld, int lo_off, int W, const float* w_out, const float* b_out, unsigned M,
+    unsigned Mp, float a_lo, float a_hi, const float* g_alpha, float* gf, __nv_bfloat16* delta,
+    __nv_bfloat16* deltaT, unsigned rows_per_block, double* part) {
+    extern __shared__ uint32_t hsm[];
+    uint32_t* thi = hsm;                          // [W][kHQ] transposed hi pairs
+    uint32_t* tlo = hsm + (size_t)W * kHQ;        // [W][kHQ] transposed lo pairs (NS = 3)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = kT / 32;
+    const int cpr = W / 8;                        // 16-byte chunks per row
+    const unsigned r0 = blockIdx.x * rows_per_block, r1 = min(Mp, r0 + rows_per_block);
+    const size_t ldd = (size_t)NS * W, ldt = (size_t)NS * Mp;
+    const float bo = b_out[0], span = a_hi - a_lo;
+    float sw[VC][8], sd[VC][8], sb = 0.f;
+#pragma unroll
+    for (int v = 0; v < VC; ++v)
+#pragma unroll
+        for (int t = 0; t < 8; ++t) sw[v][t] = sd[v][t] = 0.f;
+    // the value of column t of a raw 16-byte chunk (hi, + lo when split)
+    auto val = [&](const uint4& a, const uint4& b, int t) {
+        const uint32_t wa = t < 2 ? a.x : (t < 4 ? a.y : (t < 6 ? a.z : a.w));
+        const float hv = __uint_as_float((t & 1) ? (wa & 0xFFFF0000u) : (wa << 16));
+        if (NS == 1) return hv;
+        const uint32_t wb = t < 2 ? b.x : (t < 4 ? b.y : (t < 6 ? b.z : b.w));
+        return hv + __uint_as_float((t & 1) ? (wb & 0xFFFF0000u) : (wb << 16));
+    };
+    // the warp's rows of the tile at m0: raw hi (and lo) chunks and g_alpha
+    auto load_rows = [&](unsigned m0, uint4 (&xa)[4][VC], uint4 (&xb)[4][VC], float (&xg)[4]) {
+        const unsigned mw = m0 + 4 * warp;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) xg[i] = mw + i < M ? g_alpha[mw + i] : 0.f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int v = 0; v < VC; ++v) {
+                const int q = lane + 32 * v;
+                xa[i][v] = xb[i][v] = make_uint4(0u, 0u, 0u, 0u);
+                if (q < cpr) {
+                    const __nv_bfloat16* src = h + (size_t)(mw + i) * ld + 8 * q;
+                    xa[i][v] = *reinterpret_cast<const uint4*>(src);
+                    if (NS == 3) xb[i][v] = *reinterpret_cast<const uint4*>(src + lo_off);
+                }
+            }
+    };
+    // narrow rows: the next tile's rows are loaded while this one is processed
+    constexpr bool kPrefetch = VC == 1 && NS == 1;
+    uint4 ra[4][VC], rb[4][VC], na[4][VC], nb[4][VC];   // this tile's rows and the next tile's
+    float ga[4], nga[4];
+    if (kPrefetch && r0 < r1) load_rows(r0, ra, rb, ga);
+    for (unsigned m0 = r0; m0 < r1; m0 += kHR) {   // Mp and rows_per_block are multiples of kHR
+        const unsigned mw = m0 + 4 * warp;          // this warp's first row
+        if constexpr (kPrefetch) {
+            if (m0 + kHR < r1) load_rows(m0 + kHR, na, nb, nga);
+        } else {
+            load_rows(m0, ra, rb, ga);
+        }
+        float g[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float sacc = 0.f;
+#pragma unroll
+            for (int v = 0; v < VC; ++v) {
+                const int q = lane + 32 * v;
+                if (q < cpr)
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) sacc += val(ra[i][v], rb[i][v], t) * w_out[8 * q + t];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+            const float sg = 1.f / (1.f + expf(-(sacc + bo)));
+            g[i] = mw + i < M ? ga[i] * span * sg * (1.f - sg) : 0.f;
+        }
+        if (lane < 4) gf[mw + lane] = lane == 0 ? g[0] : (lane == 1 ? g[1] : (lane == 2 ? g[2] : g[3]));
+        sb += g[0] + g[1] + g[2] + g[3];
+        __syncthreads();                            // the previous tile's transposed reads are done
+#pragma unroll
+        for (int v = 0; v < VC; ++v) {
+            const int q = lane + 32 * v;
+            if (q >= cpr) continue;
+#pragma unroll
+            for (int pr = 0; pr < 2; ++pr) {        // rows 4w + 2pr, 4w + 2pr + 1
+                uint32_t hp[8], lp[8];              // one word per column: the pair's two rows
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int i = 2 * pr + e;
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        const float hv = val(ra[i][v], rb[i][v], t);
+                        const float wj = w_out[8 * q + t];
+                        const float dv = hv > 0.f ? g[i] * wj : 0.f;
+                        const __nv_bfloat16 dh = __float2bfloat16_rn(dv);
+                        const uint32_t hb = __bfloat16_as_ushort(dh);
+                        sw[v][t] += g[i] * hv;
+                        uint32_t lb = 0u;
+                        if (NS == 3) {
+                            const __nv_bfloat16 dl = __float2bfloat16_rn(dv - __bfloat162float(dh));
+                            lb = __bfloat16_as_ushort(dl);
+                            sd[v][t] += __bfloat162float(dh) + __bfloat162float(dl);
+                        } else {
+                            sd[v][t] += __bfloat162float(dh);
+                        }
+                        if (e == 0) { hp[t] = hb; lp[t] = lb; }
+                        else { hp[t] |= hb << 16; lp[t] |= lb << 16; }
+                        if (t & 1) { hw[t >> 1] |= hb << 16; lw[t >> 1] |= lb << 16; }
+                        else { hw[t >> 1] = hb; lw[t >> 1] = lb; }
+                    }
+                    __nv_bfloat16* out = delta + (size_t)(mw + i) * ldd + 8 * q;
+                    *reinterpret_cast<uint4*>(out) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    if (NS == 3) {
+                        *reinterpret_cast<uint4*>(out + W) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        *reinterpret_cast<uint4*>(out + 2 * W) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const size_t o = hq_index(8 * q + t, 2 * warp + pr);
+                    thi[o] = hp[t];
+                    if (NS == 3) tlo[o] = lp[t];
+                }
+            }
+        }
+        __syncthreads();
+        // deltaT: lanes 0-15 write column j, lanes 16-31 column j + 1, 64 bytes each
+        for (int j = 2 * warp + (lane >> 4); j < W; j += 2 * nw) {
+            const int pr = lane & 15;
+            const size_t o = hq_index(j, pr);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(deltaT + (size_t)j * ldt + m0) + pr;
+            const uint32_t wv = thi[o];
+            *dst = wv;
+            if (NS == 3) {
+                dst[Mp / 2] = wv;
+                dst[Mp] = tlo[o];
+            }
+        }
+        if constexpr (kPrefetch) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                ga[i] = nga[i];
+#pragma unroll
+                for (int v = 0; v < VC; ++v) {
+                    ra[i][v] = na[i][v];
+                    rb[i][v] = nb[i][v];
+                }
+            }
+        }
+    }
+    // block sums: per-warp partials through shared memory, summed in warp order
+    __syncthreads();
+    float* red = reinterpret_cast<float*>(hsm);   // [nw][2 W + 1]
+    const int rw = 2 * W + 1;
+#pragma unroll
+    for (int v = 0; v < VC; ++v) {
+        const int q = lane + 32 * v;
+        if (q >= cpr) continue;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            red[(size_t)warp * rw + 8 * q + t] = sw[v][t];
+            red[(size_t)warp * rw + W + 8 * q + t] = sd[v][t];
+        }
+    }
+    if (lane == 0) red[(size_t)warp * rw + 2 * W] = sb;
+    __syncthreads();
+    const unsigned nblk = gridDim.x;
+    for (int c = threadIdx.x; c < rw; c += kT) {
+        float s = 0.f;
+        for (int w2 = 0; w2 < nw; ++w2) s += red[(size_t)w2 * rw + c];
+        if (c < W) part[(size_t)blockIdx.x * W + c] = (double)s;
+        else if (c < 2 * W) part[(size_t)nblk * (W + 1) + (size_t)blockIdx.x * W + (c - W)] = (double)s;
+        else part[(size_t)nblk * W + blockIdx.x] = (double)s;
+    }
+}
+
 // out[j] = sum_m A[m][j] * (v ? v[m] : 1) over rows, in fixed order:
 // per-block partial sums, then a second pass.  A is BF16 (rows of pitch lda;
 // a split row adds its lo block at column offset lo_off) or FP32.
@@ -400,7 +620,7 @@ size_t field_workspace_bytes(const FieldDims& d, bool backward) {
         maxin = std::max(maxin, (size_t)in_store(d, l));
     }
     auto add = [&](size_t x) { b += (x + 255) & ~(size_t)255; };
-    add((size_t)(d.nx + d.ny + d.nz) * 2 * d.F * 4);   // axis tables
+    add((size_t)(d.nx + d.ny + d.nz) * 2 * d.F * 4 * 2 + 16);   // axis tables, cell-major and feature-major
     for (int l = 0; l <= d.depth; ++l) add(Mp * (size_t)h_ld(d, l) * 2);   // h_0 .. h_depth
     add(wsum * ns * 2);                                 // BF16 weights
     add(sizeof(int));
@@ -412,14 +632,15 @@ size_t field_workspace_bytes(const FieldDims& d, bool backward) {
         add(Mp * ns * W * 2);                           // delta^T
         add(Mp * ns * (size_t)d.Dp * 2);                // h_0^T
         add((size_t)d.splits * W * maxin * 4);          // split-K partials
-        add((size_t)d.colsum_blocks * W * 8);           // column-sum partials
+        add((size_t)d.colsum_blocks * (2 * W + 1) * 8); // column-sum partials (the fused head: 2 W + 1 per block)
     }
     return b;
 }
 
 // Carves the workspace identically to field_workspace_bytes.
 struct FieldWs {
-    float *tx, *ty, *tz;
+    float *tx, *ty, *tz;          // axis tables [n][2F]
+    float *txT, *tyT, *tzT;       // the same, [2F][n]
     __nv_bfloat16* h[16];
     __nv_bfloat16* wb;      // BF16 weights, layer l at offset ns * woff[l]
     __nv_bfloat16* wt;      // BF16 transposed weights
@@ -442,10 +663,13 @@ static FieldWs carve(char* base, const FieldDims& d, bool backward) {
     FieldWs w{};
     size_t off = 0;
     auto take = [&](size_t x) { char* p = base + off; off += (x + 255) & ~(size_t)255; return p; };
-    char* tab = take((size_t)(d.nx + d.ny + d.nz) * 2 * d.F * 4);
+    char* tab = take((size_t)(d.nx + d.ny + d.nz) * 2 * d.F * 4 * 2 + 16);
     w.tx = (float*)tab;
     w.ty = w.tx + (size_t)d.nx * 2 * d.F;
     w.tz = w.ty + (size_t)d.ny * 2 * d.F;
+    w.txT = w.tx + ((size_t)(d.nx + d.ny + d.nz) * 2 * d.F + 3) / 4 * 4;   // 16-byte aligned
+    w.tyT = w.txT + (size_t)d.nx * 2 * d.F;
+    w.tzT = w.tyT + (size_t)d.ny * 2 * d.F;
     for (int l = 0; l <= d.depth; ++l) w.h[l] = (__nv_bfloat16*)take(Mp * (size_t)h_ld(d, l) * 2);
     w.wb = (__nv_bfloat16*)take(wsum * ns * 2);
     w.err = (int*)take(sizeof(int));
@@ -459,7 +683,7 @@ static FieldWs carve(char* base, const FieldDims& d, bool backward) {
         w.tA = (__nv_bfloat16*)take(Mp * ns * W * 2);
         w.tB = (__nv_bfloat16*)take(Mp * ns * (size_t)d.Dp * 2);
         w.split = (float*)take((size_t)d.splits * W * maxin * 4);
-        w.colpart = (double*)take((size_t)d.colsum_blocks * W * 8);
+        w.colpart = (double*)take((size_t)d.colsum_blocks * (2 * W + 1) * 8);
     }
     return w;
 }
@@ -483,12 +707,13 @@ static cudaError_t forward_layers(const FieldDims& d, const float* theta, const 
                                   cudaStream_t s, bool with_t) {
     const int F = d.F, W = d.W, ns = d.ns;
     const double lo = d.freq_lo, ratio_log = log(d.freq_hi / d.freq_lo);
-    axis_table_kernel<<<blocks_for((size_t)d.nx * F), kT, 0, s>>>(w.tx, d.nx, F, lo, ratio_log, band_w);
-    axis_table_kernel<<<blocks_for((size_t)d.ny * F), kT, 0, s>>>(w.ty, d.ny, F, lo, ratio_log, band_w);
-    axis_table_kernel<<<blocks_for((size_t)d.nz * F), kT, 0, s>>>(w.tz, d.nz, F, lo, ratio_log, band_w);
+    axis_table_kernel<<<blocks_for((size_t)d.nx * F), kT, 0, s>>>(w.tx, w.txT, d.nx, F, lo, ratio_log, band_w);
+    axis_table_kernel<<<blocks_for((size_t)d.ny * F), kT, 0, s>>>(w.ty, w.tyT, d.ny, F, lo, ratio_log, band_w);
+    axis_table_kernel<<<blocks_for((size_t)d.nz * F), kT, 0, s>>>(w.tz, w.tzT, d.nz, F, lo, ratio_log, band_w);
     // one thread per 16-byte chunk of a cell's features (F % 4 == 0), else per feature
-    const size_t fwork = (size_t)d.Mp * (F % 4 == 0 ? d.Dp / 8 : d.Dp);
-    features_kernel<<<blocks_for(fwork), kT, 0, s>>>(w.h[0], d.M, d.Mp, d.nx, d.ny, F, d.Dp, ns, w.tx, w.ty, w.tz);
+    const size_t fwork = F % 4 == 0 ? (size_t)d.Mp * 32 : (size_t)d.Mp * d.Dp;   // one warp per cell, else per feature
+    const unsigned fblocks = F % 4 == 0 ? std::min(blocks_for(fwork), (unsigned)(16 * d.sms)) : blocks_for(fwork);
+    features_kernel<<<fblocks, kT, 0, s>>>(w.h[0], d.M, d.Mp, d.nx, d.ny, F, d.Dp, ns, w.tx, w.ty, w.tz);
     if (d.skip > 0)   // the encoding beside h_s in each block of the skip layer's input
         for (int b = 0; b < ns; ++b)
             copy_cols_kernel<<<blocks_for((size_t)d.Mp * d.Dp / 8), kT, 0, s>>>(
@@ -559,17 +784,44 @@ cudaError_t field_backward(const FieldDims& d, const float* theta, const float* 
     }
     const float* w_out = theta + poff[d.depth];
     float* g_wout = g_theta + poff[d.depth];
-    // head
-    head_back_kernel<<<blocks_for((size_t)d.Mp * 32), kT, 0, s>>>(w.h[d.depth], (size_t)h_ld(d, d.depth), lo_w, W,
-                                                                  w_out, w_out + W, d.M, d.Mp, (float)d.alpha_min,
-                                                                  (float)d.alpha_max, g_alpha, w.gf, w.dl[0], ns);
-    // dw_out[j] = sum_m gf[m] h[m][j];  db_out = sum_m gf[m]
     const unsigned rpb = (d.Mp + d.colsum_blocks - 1) / d.colsum_blocks;
-    colsum_partial_kernel<__nv_bfloat16><<<d.colsum_blocks, kT, 0, s>>>(w.h[d.depth], (size_t)h_ld(d, d.depth), lo_w,
-                                                                      w.gf, d.Mp, W, rpb, w.colpart);
-    colsum_final_kernel<<<blocks_for((size_t)W * 32), kT, 0, s>>>(w.colpart, d.colsum_blocks, W, g_wout);
-    colsum_partial_kernel<float><<<d.colsum_blocks, kT, 0, s>>>(w.gf, 1, 0, nullptr, d.Mp, 1, rpb, w.colpart);
-    colsum_final_kernel<<<1, 32, 0, s>>>(w.colpart, d.colsum_blocks, 1, g_wout + W);
+    // head: g_f, the top delta and its transpose, dw_out, db_out and the top
+    // layer's db in one pass when its row tile fits in shared memory
+    const size_t hsm = head_fused_smem(W, ns);
+    const int vc = head_vc(W);
+    const bool fused = hsm <= kHeadSmemMax && (vc == 1 || vc == 2 || vc == 4);
+    if (fused) {
+        auto kern = ns == 1 ? (vc == 1 ? head_back_fused_kernel<1, 1>
+                                       : (vc == 2 ? head_back_fused_kernel<2, 1> : head_back_fused_kernel<4, 1>))
+                            : (vc == 1 ? head_back_fused_kernel<1, 3>
+                                       : (vc == 2 ? head_back_fused_kernel<2, 3> : head_back_fused_kernel<4, 3>));
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHeadSmemMax)) !=
+            cudaSuccess)
+            return e;
+        int occ = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kT, hsm)) != cudaSuccess) return e;
+        // blocks: the resident ones, at most the partial buffer's colsum_blocks
+        const unsigned nblk = (unsigned)std::max(1, std::min(d.colsum_blocks, std::max(1, occ) * d.sms));
+        const unsigned hrpb = ((d.Mp + nblk - 1) / nblk + kHR - 1) / kHR * kHR;
+        kern<<<nblk, kT, hsm, s>>>(w.h[d.depth], (size_t)h_ld(d, d.depth), lo_w, W, w_out, w_out + W, d.M, d.Mp,
+                                   (float)d.alpha_min, (float)d.alpha_max, g_alpha, w.gf, w.dl[0], w.tA, hrpb,
+                                   w.colpart);
+        const double* part = w.colpart;
+        colsum_final_kernel<<<blocks_for((size_t)W * 32), kT, 0, s>>>(part, (int)nblk, W, g_wout);
+        colsum_final_kernel<<<1, 32, 0, s>>>(part + (size_t)nblk * W, (int)nblk, 1, g_wout + W);
+        colsum_final_kernel<<<blocks_for((size_t)W * 32), kT, 0, s>>>(
+            part + (size_t)nblk * (W + 1), (int)nblk, W, g_theta + poff[d.depth - 1] + (size_t)W * in_packed(d, d.depth - 1));
+    } else {
+        head_back_kernel<<<blocks_for((size_t)d.Mp * 32), kT, 0, s>>>(w.h[d.depth], (size_t)h_ld(d, d.depth), lo_w, W,
+                                                                      w_out, w_out + W, d.M, d.Mp, (float)d.alpha_min,
+                                                                      (float)d.alpha_max, g_alpha, w.gf, w.dl[0], ns);
+        // dw_out[j] = sum_m gf[m] h[m][j];  db_out = sum_m gf[m]
+        colsum_partial_kernel<__nv_bfloat16><<<d.colsum_blocks, kT, 0, s>>>(
+            w.h[d.depth], (size_t)h_ld(d, d.depth), lo_w, w.gf, d.Mp, W, rpb, w.colpart);
+        colsum_final_kernel<<<blocks_for((size_t)W * 32), kT, 0, s>>>(w.colpart, d.colsum_blocks, W, g_wout);
+        colsum_partial_kernel<float><<<d.colsum_blocks, kT, 0, s>>>(w.gf, 1, 0, nullptr, d.Mp, 1, rpb, w.colpart);
+        colsum_final_kernel<<<1, 32, 0, s>>>(w.colpart, d.colsum_blocks, 1, g_wout + W);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // transposed BF16 weights W_l^T [in_store x ns W] (B side) for the input-gradient GEMMs
     {
@@ -582,8 +834,11 @@ cudaError_t field_backward(const FieldDims& d, const float* theta, const float* 
         }
     }
     // h_0^T (B side), also the encoding rows of the skip layer's h^T
-    features_t_kernel<<<blocks_for((size_t)d.Dp * (d.Mp / 8)), kT, 0, s>>>(w.tB, d.M, d.Mp, d.nx, d.ny, d.F, d.Dp,
-                                                                          ns, w.tx, w.ty, w.tz);
+    {
+        const unsigned gx = std::min(blocks_for(d.Mp / 8), (unsigned)std::max(1, 8 * d.sms / std::max(1, d.Dp / 8)));
+        features_t_kernel<<<dim3(gx, d.Dp), kT, 0, s>>>(w.tB, d.M, d.Mp, d.nx, d.ny, d.nz, d.F, d.Dp, ns, w.txT, w.tyT,
+                                                         w.tzT);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (d.skip > 0 && d.skip < d.depth) {
         e = cudaMemcpyAsync(w.hT[d.skip] + (size_t)W * ns * d.Mp, w.tB, (size_t)d.Dp * ns * d.Mp * 2,
@@ -594,16 +849,18 @@ cudaError_t field_backward(const FieldDims& d, const float* theta, const float* 
     int cur = 0;
     for (int l = d.depth - 1; l >= 0; --l) {
         const int in = in_packed(d, l), ins = in_store(d, l);
-        // db_l = column sums of delta
-        colsum_partial_kernel<__nv_bfloat16><<<d.colsum_blocks, kT, 0, s>>>(w.dl[cur], (size_t)ns * W, lo_w, nullptr,
-                                                                          d.Mp, W, rpb, w.colpart);
-        colsum_final_kernel<<<blocks_for((size_t)W * 32), kT, 0, s>>>(w.colpart, d.colsum_blocks, W,
-                                                         g_theta + poff[l] + (size_t)W * in);
+        // db_l = column sums of delta (the top layer's: in the fused head pass)
+        if (!(fused && l == d.depth - 1)) {
+            colsum_partial_kernel<__nv_bfloat16><<<d.colsum_blocks, kT, 0, s>>>(w.dl[cur], (size_t)ns * W, lo_w,
+                                                                              nullptr, d.Mp, W, rpb, w.colpart);
+            colsum_final_kernel<<<blocks_for((size_t)W * 32), kT, 0, s>>>(w.colpart, d.colsum_blocks, W,
+                                                                         g_theta + poff[l] + (size_t)W * in);
+        }
         // dW_l = delta^T h_l: K-major operands are the transposes [W x ns Mp] (A
         // side) and [ins x ns Mp] (B side).  delta^T comes from the previous
         // masked product's epilogue (top layer: transposed here); h_l^T from the
         // forward epilogues (l = 0: h_0^T).
-        if (l == d.depth - 1) transpose_operand(w.dl[cur], (size_t)ns * W, w.tA, d.Mp, W, ns, false, s);
+        if (l == d.depth - 1 && !fused) transpose_operand(w.dl[cur], (size_t)ns * W, w.tA, d.Mp, W, ns, false, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // split-K: one CTA per SM over the layer's output tiles
         const int tiles = ((W + 127) / 128) * ((ins + 127) / 128);
