@@ -282,7 +282,7 @@ def field_launches(spec, reuse):
     # layer's in the fused pass), weight-gradient GEMM, split-K reduce; and
     # L - 1 input-gradient GEMMs
     W = spec.width
-    fused = max((2 if ns == 3 else 1) * W * 16, 8 * (2 * W + 1)) * 4 <= 200 * 1024 and (W // 8 + 31) // 32 in (1, 2, 4)
+    fused = max((2 if ns == 3 else 1) * W * 32, 8 * (2 * W + 1)) * 4 <= 200 * 1024 and (W // 8 + 31) // 32 in ((1, 2, 4) if ns == 1 else (1, 2))
     head = 1 + 3 if fused else 1 + 4 + ns
     bias = 2 * (L - 1) if fused else 2 * L
     bw = (1 if reuse else fwd) + head + L + 1 + bias + 2 * L + (L - 1)

@@ -313,7 +313,7 @@ __global__ void head_back_kernel(const __nv_bfloat16* h, size_t ld, int lo_off, 
     }
 }
 
-// The head's backward in one pass over h = h_depth, in tiles of kHR = 32
+// The head's backward in one pass over h = h_depth, in tiles of kHR = 64
 // rows: per row g_f (as head_back_kernel) and the top layer's delta, written
 // row-major (rows of ns W, blocks [hi | hi | lo]) and transposed as the A side
 // of its weight-gradient product (deltaT [W x ns Mp], blocks [hi | hi | lo] at
@@ -321,15 +321,15 @@ __global__ void head_back_kernel(const __nv_bfloat16* h, size_t ld, int lo_off, 
 // dw_out[j] = sum_m g_f[m] h[m][j], db_out = sum_m g_f[m] and db_top[j] =
 // sum_m delta[m][j] (the stored value: hi, + lo when split) at part
 // [blk][W], [nblk][W] + blk and [nblk][W + 1] + blk * W + j, for
-// colsum_final_kernel.  Warp w takes rows 4w .. 4w+3 of a tile, lane l the
-// 16-byte column chunks l, l + 32, ... (VC of them): a row's dot product is a
-// warp reduction and its delta is written from registers; only the transpose
-// goes through shared memory, as words holding two consecutive rows of one
-// column (kHQ words per column, the word index XOR-swizzled by the column's
-// chunk so that both the writes and the column reads spread over the banks).
-// Sums are FP32 per thread in row order, then over the block's warps in warp
-// order.
-constexpr int kHR = 32, kHQ = kHR / 2;
+// colsum_final_kernel.  Warp w takes rows kRW w .. kRW w + kRW - 1 of a tile,
+// lane l the 16-byte column chunks l, l + 32, ... (VC of them): a row's dot
+// product is a warp reduction and its delta is written from registers; only
+// the transpose goes through shared memory, as words holding two consecutive
+// rows of one column (kHQ = 32 words per column, the word index XOR-swizzled
+// by the column's chunk so that the writes and the column reads each cover
+// the 32 banks), and leaves it 128 contiguous bytes per column.  Sums are
+// FP32 per thread in row order, then over the block's warps in warp order.
+constexpr int kHR = 64, kRW = kHR / (kT / 32), kHQ = kHR / 2;
 __device__ __forceinline__ size_t hq_index(int col, int pair) {
     return (size_t)col * kHQ + (pair ^ ((col >> 3) & (kHQ - 1)));
 }
@@ -367,39 +367,27 @@ __global__ void __launch_bounds__(kT, (VC == 1 && NS == 1) ? 2 : 1) head_back_fu
         const uint32_t wb = t < 2 ? b.x : (t < 4 ? b.y : (t < 6 ? b.z : b.w));
         return hv + __uint_as_float((t & 1) ? (wb & 0xFFFF0000u) : (wb << 16));
     };
-    // the warp's rows of the tile at m0: raw hi (and lo) chunks and g_alpha
-    auto load_rows = [&](unsigned m0, uint4 (&xa)[4][VC], uint4 (&xb)[4][VC], float (&xg)[4]) {
-        const unsigned mw = m0 + 4 * warp;
+    for (unsigned m0 = r0; m0 < r1; m0 += kHR) {   // Mp and rows_per_block are multiples of kHR
+        const unsigned mw = m0 + kRW * warp;        // this warp's first row
+        float ga[kRW];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) xg[i] = mw + i < M ? g_alpha[mw + i] : 0.f;
+        for (int i = 0; i < kRW; ++i) ga[i] = mw + i < M ? g_alpha[mw + i] : 0.f;
+        uint4 ra[kRW][VC], rb[kRW][VC];             // raw hi (and lo) chunks of the warp's rows
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < kRW; ++i)
 #pragma unroll
             for (int v = 0; v < VC; ++v) {
                 const int q = lane + 32 * v;
-                xa[i][v] = xb[i][v] = make_uint4(0u, 0u, 0u, 0u);
+                ra[i][v] = rb[i][v] = make_uint4(0u, 0u, 0u, 0u);
                 if (q < cpr) {
                     const __nv_bfloat16* src = h + (size_t)(mw + i) * ld + 8 * q;
-                    xa[i][v] = *reinterpret_cast<const uint4*>(src);
-                    if (NS == 3) xb[i][v] = *reinterpret_cast<const uint4*>(src + lo_off);
+                    ra[i][v] = *reinterpret_cast<const uint4*>(src);
+                    if (NS == 3) rb[i][v] = *reinterpret_cast<const uint4*>(src + lo_off);
                 }
             }
-    };
-    // narrow rows: the next tile's rows are loaded while this one is processed
-    constexpr bool kPrefetch = VC == 1 && NS == 1;
-    uint4 ra[4][VC], rb[4][VC], na[4][VC], nb[4][VC];   // this tile's rows and the next tile's
-    float ga[4], nga[4];
-    if (kPrefetch && r0 < r1) load_rows(r0, ra, rb, ga);
-    for (unsigned m0 = r0; m0 < r1; m0 += kHR) {   // Mp and rows_per_block are multiples of kHR
-        const unsigned mw = m0 + 4 * warp;          // this warp's first row
-        if constexpr (kPrefetch) {
-            if (m0 + kHR < r1) load_rows(m0 + kHR, na, nb, nga);
-        } else {
-            load_rows(m0, ra, rb, ga);
-        }
-        float g[4];
+        float g[kRW];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < kRW; ++i) {
             float sacc = 0.f;
 #pragma unroll
             for (int v = 0; v < VC; ++v) {
@@ -412,16 +400,21 @@ __global__ void __launch_bounds__(kT, (VC == 1 && NS == 1) ? 2 : 1) head_back_fu
             for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
             const float sg = 1.f / (1.f + expf(-(sacc + bo)));
             g[i] = mw + i < M ? ga[i] * span * sg * (1.f - sg) : 0.f;
+            sb += g[i];
         }
-        if (lane < 4) gf[mw + lane] = lane == 0 ? g[0] : (lane == 1 ? g[1] : (lane == 2 ? g[2] : g[3]));
-        sb += g[0] + g[1] + g[2] + g[3];
+        if (lane < kRW) {
+            float gl = g[0];
+#pragma unroll
+            for (int i = 1; i < kRW; ++i) gl = lane == i ? g[i] : gl;
+            gf[mw + lane] = gl;
+        }
         __syncthreads();                            // the previous tile's transposed reads are done
 #pragma unroll
         for (int v = 0; v < VC; ++v) {
             const int q = lane + 32 * v;
             if (q >= cpr) continue;
 #pragma unroll
-            for (int pr = 0; pr < 2; ++pr) {        // rows 4w + 2pr, 4w + 2pr + 1
+            for (int pr = 0; pr < kRW / 2; ++pr) {  // rows kRW w + 2 pr, + 1
                 uint32_t hp[8], lp[8];              // one word per column: the pair's two rows
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
@@ -457,34 +450,22 @@ __global__ void __launch_bounds__(kT, (VC == 1 && NS == 1) ? 2 : 1) head_back_fu
                 }
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
-                    const size_t o = hq_index(8 * q + t, 2 * warp + pr);
+                    const size_t o = hq_index(8 * q + t, (kRW / 2) * warp + pr);
                     thi[o] = hp[t];
                     if (NS == 3) tlo[o] = lp[t];
                 }
             }
         }
         __syncthreads();
-        // deltaT: lanes 0-15 write column j, lanes 16-31 column j + 1, 64 bytes each
-        for (int j = 2 * warp + (lane >> 4); j < W; j += 2 * nw) {
-            const int pr = lane & 15;
-            const size_t o = hq_index(j, pr);
-            uint32_t* dst = reinterpret_cast<uint32_t*>(deltaT + (size_t)j * ldt + m0) + pr;
+        // deltaT: a warp writes one column's 64 rows, 128 contiguous bytes per block
+        for (int j = warp; j < W; j += nw) {
+            const size_t o = hq_index(j, lane);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(deltaT + (size_t)j * ldt + m0) + lane;
             const uint32_t wv = thi[o];
             *dst = wv;
             if (NS == 3) {
                 dst[Mp / 2] = wv;
                 dst[Mp] = tlo[o];
-            }
-        }
-        if constexpr (kPrefetch) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                ga[i] = nga[i];
-#pragma unroll
-                for (int v = 0; v < VC; ++v) {
-                    ra[i][v] = na[i][v];
-                    rb[i][v] = nb[i][v];
-                }
             }
         }
     }
@@ -789,12 +770,12 @@ cudaError_t field_backward(const FieldDims& d, const float* theta, const float* 
     // layer's db in one pass when its row tile fits in shared memory
     const size_t hsm = head_fused_smem(W, ns);
     const int vc = head_vc(W);
-    const bool fused = hsm <= kHeadSmemMax && (vc == 1 || vc == 2 || vc == 4);
+    // up to 1024 columns per row (512 split) in registers; wider heads take the unfused kernels
+    const bool fused = hsm <= kHeadSmemMax && (vc == 1 || vc == 2 || (vc == 4 && ns == 1));
     if (fused) {
         auto kern = ns == 1 ? (vc == 1 ? head_back_fused_kernel<1, 1>
                                        : (vc == 2 ? head_back_fused_kernel<2, 1> : head_back_fused_kernel<4, 1>))
-                            : (vc == 1 ? head_back_fused_kernel<1, 3>
-                                       : (vc == 2 ? head_back_fused_kernel<2, 3> : head_back_fused_kernel<4, 3>));
+                            : (vc == 1 ? head_back_fused_kernel<1, 3> : head_back_fused_kernel<2, 3>);
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHeadSmemMax)) !=
             cudaSuccess)
             return e;
