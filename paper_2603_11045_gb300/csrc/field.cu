@@ -138,7 +138,7 @@ __global__ void features_kernel(__nv_bfloat16* h0, unsigned M, unsigned Mp, int 
     }
 }
 
-// h_0^T [Dp x ns Mp] straight from the feature-major axis tables txT [2F][nx],
+// h_0^T [Dp x ns Mp], K-blocked, straight from the feature-major axis tables txT [2F][nx],
 // tyT [2F][ny], tzT [2F][nz], as the B side of the first layer's
 // weight-gradient product: row f holds feature f of every cell, the split
 // blocks in B-side order [hi | lo | hi] at column offsets 0, Mp, 2 Mp (zeros
@@ -151,7 +151,7 @@ __global__ void features_t_kernel(__nv_bfloat16* hT, unsigned M, unsigned Mp, in
     const int D = 6 * F, F2 = 2 * F, f = blockIdx.y;
     const int d = f / F2, r = f - d * F2;
     const unsigned per = Mp / 8;   // 8-cell chunks per feature row
-    __nv_bfloat16* rowT = hT + (size_t)f * ns * Mp;
+    __nv_bfloat16* rowT = hT + (size_t)f * 64;   // K-blocked: (k / 64) Dp 64 + f 64 + k % 64
     const bool fast = (nx & 7) == 0;
     for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < per; q += gridDim.x * blockDim.x) {
         const unsigned c0 = q * 8;
@@ -183,11 +183,11 @@ __global__ void features_t_kernel(__nv_bfloat16* hT, unsigned M, unsigned Mp, in
         }
         uint32_t hi[4], lo[4];
         split8(v, hi, lo);
-        __nv_bfloat16* out = rowT + c0;
+        __nv_bfloat16* out = rowT + (size_t)(c0 >> 6) * Dp * 64 + (c0 & 63);
         *reinterpret_cast<uint4*>(out) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        if (ns == 3) {
-            *reinterpret_cast<uint4*>(out + Mp) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-            *reinterpret_cast<uint4*>(out + 2 * (size_t)Mp) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        if (ns == 3) {   // the split blocks start Mp and 2 Mp along k: Mp Dp and 2 Mp Dp elements on
+            *reinterpret_cast<uint4*>(out + (size_t)Mp * Dp) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            *reinterpret_cast<uint4*>(out + 2 * (size_t)Mp * Dp) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
         }
     }
 }
@@ -242,7 +242,7 @@ __global__ void copy_cols_kernel(const __nv_bfloat16* src, int lds, __nv_bfloat1
 // dst[c][r] = src[r][c] for a BF16 [R x C] matrix (R rows = points, row
 // pitch lds), into rows of pitch ldd; tiled.
 __global__ void transpose_bf16_kernel(const __nv_bfloat16* src, size_t lds, __nv_bfloat16* dst, size_t ldd,
-                                      unsigned R, int C) {
+                                      unsigned R, int C, int rt) {
     __shared__ __nv_bfloat16 t[32][33];
     const unsigned r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
     for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
@@ -252,7 +252,8 @@ __global__ void transpose_bf16_kernel(const __nv_bfloat16* src, size_t lds, __nv
     __syncthreads();
     for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
         const unsigned c = c0 + yy, r = r0 + threadIdx.x;
-        if (c < (unsigned)C && r < R) dst[(size_t)c * ldd + r] = t[threadIdx.x][yy];
+        if (c < (unsigned)C && r < R)
+            dst[rt ? (size_t)(r >> 6) * rt * 64 + (size_t)c * 64 + (r & 63) : (size_t)c * ldd + r] = t[threadIdx.x][yy];
     }
 }
 
@@ -316,8 +317,8 @@ __global__ void head_back_kernel(const __nv_bfloat16* h, size_t ld, int lo_off, 
 // The head's backward in one pass over h = h_depth, in tiles of kHR = 64
 // rows: per row g_f (as head_back_kernel) and the top layer's delta, written
 // row-major (rows of ns W, blocks [hi | hi | lo]) and transposed as the A side
-// of its weight-gradient product (deltaT [W x ns Mp], blocks [hi | hi | lo] at
-// column offsets 0, Mp, 2 Mp); and, per block of rows, the partial sums of
+// of its weight-gradient product (deltaT [W x ns Mp] K-blocked, blocks
+// [hi | hi | lo] at k offsets 0, Mp, 2 Mp); and, per block of rows, the partial sums of
 // dw_out[j] = sum_m g_f[m] h[m][j], db_out = sum_m g_f[m] and db_top[j] =
 // sum_m delta[m][j] (the stored value: hi, + lo when split) at part
 // [blk][W], [nblk][W] + blk and [nblk][W + 1] + blk * W + j, for
@@ -352,7 +353,7 @@ __global__ void __launch_bounds__(kT, (VC == 1 && NS == 1) ? 2 : 1) head_back_fu
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = kT / 32;
     const int cpr = W / 8;                        // 16-byte chunks per row
     const unsigned r0 = blockIdx.x * rows_per_block, r1 = min(Mp, r0 + rows_per_block);
-    const size_t ldd = (size_t)NS * W, ldt = (size_t)NS * Mp;
+    const size_t ldd = (size_t)NS * W;
     const float bo = b_out[0], span = a_hi - a_lo;
     float sw[VC][8], sd[VC][8], sb = 0.f;
 #pragma unroll
@@ -457,15 +458,17 @@ __global__ void __launch_bounds__(kT, (VC == 1 && NS == 1) ? 2 : 1) head_back_fu
             }
         }
         __syncthreads();
-        // deltaT: a warp writes one column's 64 rows, 128 contiguous bytes per block
+        // deltaT, K-blocked (element (j, k) at (k / 64) W 64 + j 64 + k % 64; the
+        // tile is one 64-wide k-block): a warp writes one column's 64 rows,
+        // 128 contiguous bytes per block
         for (int j = warp; j < W; j += nw) {
             const size_t o = hq_index(j, lane);
-            uint32_t* dst = reinterpret_cast<uint32_t*>(deltaT + (size_t)j * ldt + m0) + lane;
+            uint32_t* dst = reinterpret_cast<uint32_t*>(deltaT + (size_t)(m0 >> 6) * W * 64 + (size_t)j * 64) + lane;
             const uint32_t wv = thi[o];
             *dst = wv;
             if (NS == 3) {
-                dst[Mp / 2] = wv;
-                dst[Mp] = tlo[o];
+                dst[(size_t)Mp * W / 2] = wv;
+                dst[(size_t)Mp * W] = tlo[o];
             }
         }
     }
@@ -627,6 +630,9 @@ struct FieldWs {
     __nv_bfloat16* wt;      // BF16 transposed weights
     __nv_bfloat16* dl[2];
     float* gf;
+    // transposes for the weight-gradient products, K-blocked: element (r, k) of
+    // R rows at (k / 64) R 64 + r 64 + k % 64 (one 64-wide k-block of 128
+    // rows is 16 contiguous KB, a single TMA box)
     __nv_bfloat16* hT[16];  // h_l^T [in_store(l) x ns Mp], l = 1 .. depth-1
     __nv_bfloat16 *tA, *tB; // delta^T [W x ns Mp], h_0^T [Dp x ns Mp]
     float* split;
@@ -673,13 +679,15 @@ static FieldWs carve(char* base, const FieldDims& d, bool backward) {
 // split blocks [hi | hi | lo] at column offsets 0, C, 2 C when ns = 3), each
 // block transposed into its place in the requested order: A-side [hi | hi | lo]
 // (b_side = false) or B-side [hi | lo | hi].
+// dst is written K-blocked (element (c, k) of C rows at (k / 64) C 64 + c 64 +
+// k % 64, k = block * R + r; R is a multiple of 64), the layout the
+// weight-gradient products read.
 static void transpose_operand(const __nv_bfloat16* src, size_t lds, __nv_bfloat16* dst, unsigned R, int C, int ns,
                               bool b_side, cudaStream_t s) {
     const dim3 tb(32, 8), grid((R + 31) / 32, (C + 31) / 32);
-    const size_t ldd = (size_t)ns * R;
     for (int b = 0; b < ns; ++b) {
         const int from = ns == 1 ? 0 : (b_side ? (b == 1 ? 2 : 0) : b);   // source block of output block b
-        transpose_bf16_kernel<<<grid, tb, 0, s>>>(src + (size_t)from * C, lds, dst + (size_t)b * R, ldd, R, C);
+        transpose_bf16_kernel<<<grid, tb, 0, s>>>(src + (size_t)from * C, lds, dst + (size_t)b * R * C, 0, R, C, C);
     }
 }
 
@@ -720,7 +728,8 @@ static cudaError_t forward_layers(const FieldDims& d, const float* theta, const 
         const int so = ns == 3 ? h_w(d, l + 1) : 0;
         e = umma_gemm(w.h[l], ns * ins, w.wb + ns * woff, ns * ins, (int)d.Mp, W, ns * ins, 0 /*bias+relu*/, bias,
                       nullptr, w.h[l + 1], nullptr, h_ld(d, l + 1), 1, w.err, s, t ? w.hT[l + 1] : nullptr,
-                      t ? ns * (int)d.Mp : 0, 0, so, (t && ns == 3) ? (int)d.Mp : 0, 1 /*B-side transposes*/);
+                      t ? ns * (int)d.Mp : 0, 0, so, (t && ns == 3) ? (int)d.Mp : 0, 1 /*B-side transposes*/, 0, 0,
+                      t ? in_store(d, l + 1) : 0 /*K-blocked*/);
         if (e != cudaSuccess) return e;
         p += (size_t)W * in + W;
         woff += (size_t)W * ins;
@@ -822,8 +831,10 @@ cudaError_t field_backward(const FieldDims& d, const float* theta, const float* 
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (d.skip > 0 && d.skip < d.depth) {
-        e = cudaMemcpyAsync(w.hT[d.skip] + (size_t)W * ns * d.Mp, w.tB, (size_t)d.Dp * ns * d.Mp * 2,
-                            cudaMemcpyDeviceToDevice, s);
+        // K-blocked: per 64-wide k-block, rows W .. W + Dp of the skip layer's input
+        e = cudaMemcpy2DAsync(w.hT[d.skip] + (size_t)W * 64, (size_t)(W + d.Dp) * 64 * 2, w.tB,
+                              (size_t)d.Dp * 64 * 2, (size_t)d.Dp * 64 * 2, (size_t)ns * d.Mp / 64,
+                              cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return e;
     }
     // layers, top to bottom: delta_l = dJ/dz_{l+1} [Mp x ns W] lives in dl[cur]
@@ -838,7 +849,7 @@ cudaError_t field_backward(const FieldDims& d, const float* theta, const float* 
                                                                          g_theta + poff[l] + (size_t)W * in);
         }
         // dW_l = delta^T h_l: K-major operands are the transposes [W x ns Mp] (A
-        // side) and [ins x ns Mp] (B side).  delta^T comes from the previous
+        // side) and [ins x ns Mp] (B side), both K-blocked.  delta^T comes from the previous
         // masked product's epilogue (top layer: transposed here); h_l^T from the
         // forward epilogues (l = 0: h_0^T).
         if (l == d.depth - 1 && !fused) transpose_operand(w.dl[cur], (size_t)ns * W, w.tA, d.Mp, W, ns, false, s);
@@ -847,7 +858,8 @@ cudaError_t field_backward(const FieldDims& d, const float* theta, const float* 
         const int tiles = ((W + 127) / 128) * ((ins + 127) / 128);
         const int splits = std::min(d.splits, std::max(1, d.sms / tiles));
         e = umma_gemm(w.tA, ns * (int)d.Mp, l == 0 ? w.tB : w.hT[l], ns * (int)d.Mp, W, ins, ns * (int)d.Mp,
-                      2 /*f32 partials*/, nullptr, nullptr, nullptr, w.split, ins, splits, w.err, s);
+                      2 /*f32 partials*/, nullptr, nullptr, nullptr, w.split, ins, splits, w.err, s, nullptr, 0, 0,
+                      0, 0, 0, 1, 1 /*K-blocked A and B*/);
         if (e != cudaSuccess) return e;
         split_reduce_kernel<<<blocks_for((size_t)W * in), kT, 0, s>>>(w.split, splits, W, ins, in,
                                                                       g_theta + poff[l]);
@@ -856,7 +868,7 @@ cudaError_t field_backward(const FieldDims& d, const float* theta, const float* 
         if (l > 0) {
             e = umma_gemm(w.dl[cur], ns * W, w.wt + ns * woff[l], ns * W, (int)d.Mp, W, ns * W, 1 /*mask*/, nullptr,
                           w.h[l], w.dl[cur ^ 1], nullptr, ns * W, 1, w.err, s, w.tA, ns * (int)d.Mp, h_ld(d, l),
-                          ns == 3 ? W : 0, ns == 3 ? (int)d.Mp : 0, 0 /*A-side transposes*/);
+                          ns == 3 ? W : 0, ns == 3 ? (int)d.Mp : 0, 0 /*A-side transposes*/, 0, 0, W /*K-blocked*/);
             if (e != cudaSuccess) return e;
             cur ^= 1;
         }

@@ -68,6 +68,11 @@ __device__ __forceinline__ void tma2(uint32_t dst, const CUtensorMap* map, int x
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
         ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(b) : "memory");
 }
+__device__ __forceinline__ void tma3(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t b) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(z), "r"(b) : "memory");
+}
 
 // Shared-memory matrix descriptor of a K-major tile in the 128-byte swizzle
 // layout: 8-row atoms of 1024 bytes stacked along M/N (stride 1024), start
@@ -118,6 +123,11 @@ struct Args {
     // so, 2 so; out_t gets three blocks at column offsets 0, tso, 2 tso in the
     // order [hi | hi | lo] (t_order 0) or [hi | lo | hi] (t_order 1).
     int so, tso, t_order;
+    // K-blocked operands and transposed output (0 = row-major): element
+    // (r, k) of a matrix with R rows sits at (k / 64) R 64 + r 64 + k % 64,
+    // so one 64-wide k-block of 128 rows is 16 contiguous KB
+    int a_blk, b_blk;            // A, B in that layout (TMA through a 3D map)
+    int t_rows;                  // out_t in that layout with t_rows rows
 };
 
 template <int STAGES>
@@ -161,8 +171,10 @@ gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
         auto load = [&](int i) {   // k-block kb0 + i into stage i % STAGES
             const int s = i % STAGES;
             bar_expect_tx(s_u32(&full[s]), STAGE_BYTES);
-            tma2(sa(s), &mapA, (kb0 + i) * BK, m0, s_u32(&full[s]));
-            tma2(sb(s), &mapB, (kb0 + i) * BK, n0, s_u32(&full[s]));
+            if (a.a_blk) tma3(sa(s), &mapA, 0, m0, kb0 + i, s_u32(&full[s]));
+            else tma2(sa(s), &mapA, (kb0 + i) * BK, m0, s_u32(&full[s]));
+            if (a.b_blk) tma3(sb(s), &mapB, 0, n0, kb0 + i, s_u32(&full[s]));
+            else tma2(sb(s), &mapB, (kb0 + i) * BK, n0, s_u32(&full[s]));
         };
         int issued = 0;
         for (; issued < nk && issued < STAGES; ++issued) load(issued);
@@ -284,12 +296,13 @@ gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
                         for (int b = 0; b < nb; ++b) {
                             const bool lo = b == (a.t_order == 0 ? 2 : 1);
                             const uint32_t* src = lo ? pl : pk;
-                            unsigned short* dt = reinterpret_cast<unsigned short*>(a.out_t) + (size_t)cb * a.ldt +
-                                                 (size_t)b * a.tso + row;
+                            const size_t k = (size_t)b * a.tso + row, cs = a.t_rows ? 64 : (size_t)a.ldt;
+                            const size_t ko = a.t_rows ? (k >> 6) * (size_t)a.t_rows * 64 + (k & 63) : k;
+                            unsigned short* dt = reinterpret_cast<unsigned short*>(a.out_t) + ko + (size_t)cb * cs;
 #pragma unroll
                             for (int t = 0; t < 16; ++t) {
-                                dt[(size_t)(2 * t) * a.ldt] = (unsigned short)(src[t] & 0xFFFFu);
-                                dt[(size_t)(2 * t + 1) * a.ldt] = (unsigned short)(src[t] >> 16);
+                                dt[(size_t)(2 * t) * cs] = (unsigned short)(src[t] & 0xFFFFu);
+                                dt[(size_t)(2 * t + 1) * cs] = (unsigned short)(src[t] >> 16);
                             }
                         }
                     }
@@ -320,7 +333,10 @@ gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
                             const int nb = a.tso ? 3 : 1;
                             for (int b = 0; b < nb; ++b) {
                                 const bool lo = b == (a.t_order == 0 ? 2 : 1);
-                                a.out_t[(size_t)col * a.ldt + (size_t)b * a.tso + row] = lo ? rl : r;
+                                const size_t k = (size_t)b * a.tso + row;
+                                const size_t o = a.t_rows ? (k >> 6) * (size_t)a.t_rows * 64 + (size_t)col * 64 + (k & 63)
+                                                          : (size_t)col * a.ldt + k;
+                                a.out_t[o] = lo ? rl : r;
                             }
                         }
                     } else {
@@ -359,10 +375,21 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
 }
 
 // 2D BF16 map over [rows x cols] (cols contiguous, pitch ld elements), box
-// 64 x 128 with the 128-byte swizzle.
-bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld) {
+// 64 x 128 with the 128-byte swizzle; with blk, a 3D map over the K-blocked
+// layout [cols / 64][rows][64], box 64 x 128 x 1 (16 contiguous KB), which
+// lands in shared memory exactly as the 2D box does.
+bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, bool blk = false) {
     auto enc = encoder();
     if (!enc) return false;
+    if (blk) {
+        const cuuint64_t dims[3] = {(cuuint64_t)umma::BK, (cuuint64_t)rows, (cuuint64_t)(cols / umma::BK)};
+        const cuuint64_t strides[2] = {(cuuint64_t)umma::BK * 2, (cuuint64_t)rows * umma::BK * 2};
+        const cuuint32_t box[3] = {(cuuint32_t)umma::BK, (cuuint32_t)umma::BM, 1};
+        const cuuint32_t es[3] = {1, 1, 1};
+        return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
     const cuuint32_t box[2] = {(cuuint32_t)umma::BK, (cuuint32_t)umma::BM};
@@ -379,7 +406,7 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld) {
 cudaError_t umma_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
                       int epi, const float* bias, const __nv_bfloat16* mask, __nv_bfloat16* out_bf16,
                       float* out_f32, int ldo, int splits, int* err, cudaStream_t s, __nv_bfloat16* out_t, int ldt,
-                      int ldm, int so, int tso, int t_order) {
+                      int ldm, int so, int tso, int t_order, int a_blk, int b_blk, int t_rows) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(umma::gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -391,11 +418,14 @@ cudaError_t umma_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, i
         attr_set = true;
     }
     if (K % umma::BK != 0 || lda % 8 != 0 || ldb % 8 != 0 || splits < 1) return cudaErrorInvalidValue;
-    if (out_t && (epi == umma::kEpiF32 || ldt < M)) return cudaErrorInvalidValue;
+    if (out_t && (epi == umma::kEpiF32 || (t_rows ? t_rows < N : ldt < M))) return cudaErrorInvalidValue;
+    if (t_rows && ((tso ? 3 * (size_t)tso : (size_t)M) % umma::BK != 0 || (tso && tso % umma::BK != 0)))
+        return cudaErrorInvalidValue;   // K-blocked D^T: whole 64-wide k-blocks
     if ((so || tso) && epi == umma::kEpiF32) return cudaErrorInvalidValue;
     if (so < 0 || so % 8 != 0 || tso < 0 || (tso && (tso < M || ldt < 2 * tso + M))) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, A, M, K, lda) || !make_map(&mb, B, N, K, ldb)) return cudaErrorInvalidValue;
+    if (!make_map(&ma, A, M, K, lda, a_blk != 0) || !make_map(&mb, B, N, K, ldb, b_blk != 0))
+        return cudaErrorInvalidValue;
     umma::Args a;
     a.M = M; a.N = N; a.K = K;
     const int kb = K / umma::BK;
@@ -408,6 +438,9 @@ cudaError_t umma_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, i
     a.so = so;
     a.tso = out_t ? tso : 0;
     a.t_order = t_order;
+    a.a_blk = a_blk;
+    a.b_blk = b_blk;
+    a.t_rows = out_t ? t_rows : 0;
     auto al16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
     a.vec = (epi == umma::kEpiF32 ? (ldo % 4 == 0 && al16(out_f32))
                                   : (ldo % 8 == 0 && al16(out_bf16) &&
