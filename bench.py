@@ -55,7 +55,7 @@ ALG_BYTES_GRAD = {"fp32": 20, "fp64": 24}
 # kernel source still hashes to the captured one: once the kernels change the
 # figure is stale and `traffic` is null.
 DRAM_CAPTURE = {
-    "fp32": {"fwd": 110.7, "adj": 184.6, "grid": [256, 256, 48], "nt": 1000,
+    "fp32": {"fwd": 112.4, "adj": 186.8, "grid": [256, 256, 48], "nt": 1000,
              "kernel_source": "paper_2603_11045_gb300/csrc/cg_tiled.cu", "kernel_sha16": "225deb44661310b3",
              "profiles": ["profiles/inversion_step_256x256x48_nt1000_launches.md"]},
     "fp64": None,
