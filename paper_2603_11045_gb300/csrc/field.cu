@@ -194,34 +194,38 @@ __global__ void features_t_kernel(__nv_bfloat16* hT, unsigned M, unsigned Mp, in
 
 // dst [R x Cp] = bf16(src [R x C]) with zero columns C .. Cp-1; with ns = 3
 // rows of 3 Cp values, the split blocks in B-side order [hi | lo | hi].
+// K-blocked (the B operand of a layer product): element (r, k) of the [R x ns
+// Cp] matrix at (k / 64) R 64 + r 64 + k % 64; Cp is a multiple of 64.
 __global__ void to_bf16_kernel(const float* src, __nv_bfloat16* dst, int R, int C, int Cp, int ns) {
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)R * Cp;
          e += (size_t)gridDim.x * blockDim.x) {
         const int r = (int)(e / Cp), c = (int)(e % Cp);
         const float v = c < C ? src[(size_t)r * C + c] : 0.f;
         const __nv_bfloat16 hv = __float2bfloat16_rn(v);
-        __nv_bfloat16* out = dst + (size_t)r * ns * Cp + c;
+        __nv_bfloat16* out = dst + (size_t)(c >> 6) * R * 64 + (size_t)r * 64 + (c & 63);
         out[0] = hv;
-        if (ns == 3) {
-            out[Cp] = __float2bfloat16_rn(v - __bfloat162float(hv));
-            out[2 * Cp] = hv;
+        if (ns == 3) {   // blocks at k = Cp and 2 Cp: Cp R and 2 Cp R elements on
+            out[(size_t)Cp * R] = __float2bfloat16_rn(v - __bfloat162float(hv));
+            out[2 * (size_t)Cp * R] = hv;
         }
     }
 }
 
 // dst [Cp x R] = bf16(src [R x C])^T with zero rows C .. Cp-1; with ns = 3
-// rows of 3 R values in B-side order [hi | lo | hi].
+// rows of 3 R values in B-side order [hi | lo | hi].  K-blocked: element
+// (c, k) of the [Cp x ns R] matrix at (k / 64) Cp 64 + c 64 + k % 64; R is a
+// multiple of 64.
 __global__ void transpose_f32_bf16_kernel(const float* src, __nv_bfloat16* dst, int R, int C, int Cp, int ns) {
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)R * Cp;
          e += (size_t)gridDim.x * blockDim.x) {
         const int c = (int)(e / R), r = (int)(e % R);
         const float v = c < C ? src[(size_t)r * C + c] : 0.f;
         const __nv_bfloat16 hv = __float2bfloat16_rn(v);
-        __nv_bfloat16* out = dst + (size_t)c * ns * R + r;
+        __nv_bfloat16* out = dst + (size_t)(r >> 6) * Cp * 64 + (size_t)c * 64 + (r & 63);
         out[0] = hv;
-        if (ns == 3) {
-            out[R] = __float2bfloat16_rn(v - __bfloat162float(hv));
-            out[2 * R] = hv;
+        if (ns == 3) {   // blocks at k = R and 2 R: R Cp and 2 R Cp elements on
+            out[(size_t)R * Cp] = __float2bfloat16_rn(v - __bfloat162float(hv));
+            out[2 * (size_t)R * Cp] = hv;
         }
     }
 }
@@ -626,8 +630,8 @@ struct FieldWs {
     float *tx, *ty, *tz;          // axis tables [n][2F]
     float *txT, *tyT, *tzT;       // the same, [2F][n]
     __nv_bfloat16* h[16];
-    __nv_bfloat16* wb;      // BF16 weights, layer l at offset ns * woff[l]
-    __nv_bfloat16* wt;      // BF16 transposed weights
+    __nv_bfloat16* wb;      // BF16 weights [W x ns in_store], K-blocked, layer l at offset ns * woff[l]
+    __nv_bfloat16* wt;      // BF16 transposed weights [in_store x ns W], K-blocked
     __nv_bfloat16* dl[2];
     float* gf;
     // transposes for the weight-gradient products, K-blocked: element (r, k) of
@@ -728,8 +732,8 @@ static cudaError_t forward_layers(const FieldDims& d, const float* theta, const 
         const int so = ns == 3 ? h_w(d, l + 1) : 0;
         e = umma_gemm(w.h[l], ns * ins, w.wb + ns * woff, ns * ins, (int)d.Mp, W, ns * ins, 0 /*bias+relu*/, bias,
                       nullptr, w.h[l + 1], nullptr, h_ld(d, l + 1), 1, w.err, s, t ? w.hT[l + 1] : nullptr,
-                      t ? ns * (int)d.Mp : 0, 0, so, (t && ns == 3) ? (int)d.Mp : 0, 1 /*B-side transposes*/, 0, 0,
-                      t ? in_store(d, l + 1) : 0 /*K-blocked*/);
+                      t ? ns * (int)d.Mp : 0, 0, so, (t && ns == 3) ? (int)d.Mp : 0, 1 /*B-side transposes*/, 0,
+                      W /*K-blocked weights*/, t ? in_store(d, l + 1) : 0 /*K-blocked transposes*/);
         if (e != cudaSuccess) return e;
         p += (size_t)W * in + W;
         woff += (size_t)W * ins;
@@ -859,7 +863,7 @@ cudaError_t field_backward(const FieldDims& d, const float* theta, const float* 
         const int splits = std::min(d.splits, std::max(1, d.sms / tiles));
         e = umma_gemm(w.tA, ns * (int)d.Mp, l == 0 ? w.tB : w.hT[l], ns * (int)d.Mp, W, ins, ns * (int)d.Mp,
                       2 /*f32 partials*/, nullptr, nullptr, nullptr, w.split, ins, splits, w.err, s, nullptr, 0, 0,
-                      0, 0, 0, 1, 1 /*K-blocked A and B*/);
+                      0, 0, 0, W, ins /*K-blocked A and B*/);
         if (e != cudaSuccess) return e;
         split_reduce_kernel<<<blocks_for((size_t)W * in), kT, 0, s>>>(w.split, splits, W, ins, in,
                                                                       g_theta + poff[l]);
@@ -868,7 +872,8 @@ cudaError_t field_backward(const FieldDims& d, const float* theta, const float* 
         if (l > 0) {
             e = umma_gemm(w.dl[cur], ns * W, w.wt + ns * woff[l], ns * W, (int)d.Mp, W, ns * W, 1 /*mask*/, nullptr,
                           w.h[l], w.dl[cur ^ 1], nullptr, ns * W, 1, w.err, s, w.tA, ns * (int)d.Mp, h_ld(d, l),
-                          ns == 3 ? W : 0, ns == 3 ? (int)d.Mp : 0, 0 /*A-side transposes*/, 0, 0, W /*K-blocked*/);
+                          ns == 3 ? W : 0, ns == 3 ? (int)d.Mp : 0, 0 /*A-side transposes*/, 0,
+                          ins /*K-blocked weights*/, W /*K-blocked transposes*/);
             if (e != cudaSuccess) return e;
             cur ^= 1;
         }

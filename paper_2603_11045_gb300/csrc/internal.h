@@ -340,8 +340,8 @@ cudaError_t umma_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, i
                       float* out_f32, int ldo, int splits, int* err, cudaStream_t s,
                       __nv_bfloat16* out_t = nullptr, int ldt = 0, int ldm = 0, int so = 0, int tso = 0,
                       int t_order = 0, int a_blk = 0, int b_blk = 0, int t_rows = 0);
-// a_blk / b_blk: A / B are K-blocked (element (r, k) of R rows at
-// (k / 64) R 64 + r 64 + k % 64; R = M for A, N for B; lda / ldb unused);
+// a_blk / b_blk = R > 0: A / B are K-blocked with R rows (element (r, k) at
+// (k / 64) R 64 + r 64 + k % 64; R >= M for A, >= N for B; lda / ldb unused);
 // t_rows > 0: out_t is written K-blocked with t_rows rows (ldt unused).
 
 int tiled_grid_blocks(int device);

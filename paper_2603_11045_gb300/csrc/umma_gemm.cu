@@ -126,7 +126,7 @@ struct Args {
     // K-blocked operands and transposed output (0 = row-major): element
     // (r, k) of a matrix with R rows sits at (k / 64) R 64 + r 64 + k % 64,
     // so one 64-wide k-block of 128 rows is 16 contiguous KB
-    int a_blk, b_blk;            // A, B in that layout (TMA through a 3D map)
+    int a_blk, b_blk;            // A, B in that layout (TMA through a 3D map): its row count R, 0 = row-major
     int t_rows;                  // out_t in that layout with t_rows rows
 };
 
@@ -424,7 +424,8 @@ cudaError_t umma_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, i
     if ((so || tso) && epi == umma::kEpiF32) return cudaErrorInvalidValue;
     if (so < 0 || so % 8 != 0 || tso < 0 || (tso && (tso < M || ldt < 2 * tso + M))) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, A, M, K, lda, a_blk != 0) || !make_map(&mb, B, N, K, ldb, b_blk != 0))
+    if ((a_blk && a_blk < M) || (b_blk && b_blk < N)) return cudaErrorInvalidValue;
+    if (!make_map(&ma, A, a_blk ? a_blk : M, K, lda, a_blk != 0) || !make_map(&mb, B, b_blk ? b_blk : N, K, ldb, b_blk != 0))
         return cudaErrorInvalidValue;
     umma::Args a;
     a.M = M; a.N = N; a.K = K;
