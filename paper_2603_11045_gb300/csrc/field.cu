@@ -621,6 +621,7 @@ size_t field_workspace_bytes(const FieldDims& d, bool backward) {
         add(Mp * ns * (size_t)d.Dp * 2);                // h_0^T
         add((size_t)d.splits * W * maxin * 4);          // split-K partials
         add((size_t)d.colsum_blocks * (2 * W + 1) * 8); // column-sum partials (the fused head: 2 W + 1 per block)
+        add(Mp / 32 * W * 4);                           // per-32-row delta column sums of the masked products
     }
     return b;
 }
@@ -641,6 +642,7 @@ struct FieldWs {
     __nv_bfloat16 *tA, *tB; // delta^T [W x ns Mp], h_0^T [Dp x ns Mp]
     float* split;
     double* colpart;
+    float* cs32;            // [Mp / 32][W] column sums of a masked product's delta over each 32 rows
     int* err;
 };
 
@@ -675,6 +677,7 @@ static FieldWs carve(char* base, const FieldDims& d, bool backward) {
         w.tB = (__nv_bfloat16*)take(Mp * ns * (size_t)d.Dp * 2);
         w.split = (float*)take((size_t)d.splits * W * maxin * 4);
         w.colpart = (double*)take((size_t)d.colsum_blocks * (2 * W + 1) * 8);
+        w.cs32 = (float*)take(Mp / 32 * W * 4);
     }
     return w;
 }
@@ -845,10 +848,17 @@ cudaError_t field_backward(const FieldDims& d, const float* theta, const float* 
     int cur = 0;
     for (int l = d.depth - 1; l >= 0; --l) {
         const int in = in_packed(d, l), ins = in_store(d, l);
-        // db_l = column sums of delta (the top layer's: in the fused head pass)
-        if (!(fused && l == d.depth - 1)) {
+        // db_l = column sums of delta: the top layer's in the fused head pass,
+        // the others from the 32-row sums the masked product's epilogue left
+        if (l == d.depth - 1 && !fused) {
             colsum_partial_kernel<__nv_bfloat16><<<d.colsum_blocks, kT, 0, s>>>(w.dl[cur], (size_t)ns * W, lo_w,
                                                                               nullptr, d.Mp, W, rpb, w.colpart);
+            colsum_final_kernel<<<blocks_for((size_t)W * 32), kT, 0, s>>>(w.colpart, d.colsum_blocks, W,
+                                                                         g_theta + poff[l] + (size_t)W * in);
+        } else if (l < d.depth - 1) {
+            const unsigned rows = d.Mp / 32, rpb32 = (rows + d.colsum_blocks - 1) / d.colsum_blocks;
+            colsum_partial_kernel<float><<<d.colsum_blocks, kT, 0, s>>>(w.cs32, W, 0, nullptr, rows, W, rpb32,
+                                                                      w.colpart);
             colsum_final_kernel<<<blocks_for((size_t)W * 32), kT, 0, s>>>(w.colpart, d.colsum_blocks, W,
                                                                          g_theta + poff[l] + (size_t)W * in);
         }
@@ -873,7 +883,7 @@ cudaError_t field_backward(const FieldDims& d, const float* theta, const float* 
             e = umma_gemm(w.dl[cur], ns * W, w.wt + ns * woff[l], ns * W, (int)d.Mp, W, ns * W, 1 /*mask*/, nullptr,
                           w.h[l], w.dl[cur ^ 1], nullptr, ns * W, 1, w.err, s, w.tA, ns * (int)d.Mp, h_ld(d, l),
                           ns == 3 ? W : 0, ns == 3 ? (int)d.Mp : 0, 0 /*A-side transposes*/, 0,
-                          ins /*K-blocked weights*/, W /*K-blocked transposes*/);
+                          ins /*K-blocked weights*/, W /*K-blocked transposes*/, w.cs32 /*db_{l-1} partials*/);
             if (e != cudaSuccess) return e;
             cur ^= 1;
         }

@@ -339,10 +339,12 @@ cudaError_t umma_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, i
                       int epi, const float* bias, const __nv_bfloat16* mask, __nv_bfloat16* out_bf16,
                       float* out_f32, int ldo, int splits, int* err, cudaStream_t s,
                       __nv_bfloat16* out_t = nullptr, int ldt = 0, int ldm = 0, int so = 0, int tso = 0,
-                      int t_order = 0, int a_blk = 0, int b_blk = 0, int t_rows = 0);
+                      int t_order = 0, int a_blk = 0, int b_blk = 0, int t_rows = 0, float* colsum = nullptr);
 // a_blk / b_blk = R > 0: A / B are K-blocked with R rows (element (r, k) at
 // (k / 64) R 64 + r 64 + k % 64; R >= M for A, >= N for B; lda / ldb unused);
 // t_rows > 0: out_t is written K-blocked with t_rows rows (ldt unused).
+// colsum (BF16 epilogues, M and N multiples of 128): column sums of the stored
+// output over each 32 rows, colsum[(row / 32) N + col] (FP32, fixed order).
 
 int tiled_grid_blocks(int device);
 // Shared memory (bytes) the tiled kernels request dynamically.

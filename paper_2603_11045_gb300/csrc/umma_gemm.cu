@@ -128,9 +128,13 @@ struct Args {
     // so one 64-wide k-block of 128 rows is 16 contiguous KB
     int a_blk, b_blk;            // A, B in that layout (TMA through a 3D map): its row count R, 0 = row-major
     int t_rows;                  // out_t in that layout with t_rows rows
+    // BF16 epilogues, whole tiles only: column sums of the stored output (hi,
+    // + lo when split) over each warp's 32 rows, at colsum[(row / 32) N + col]
+    float* colsum;
 };
 
-template <int STAGES>
+// COLSUM: the variant with the epilogue's column sums (Args::colsum)
+template <int STAGES, bool COLSUM>
 __global__ void __launch_bounds__(THREADS, ctas_per_sm(STAGES))
 gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, Args a) {
     extern __shared__ unsigned char smem_raw[];
@@ -282,6 +286,34 @@ gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
                     uint4* dst = reinterpret_cast<uint4*>(a.out_bf16 + o);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+                    if (COLSUM) {   // every lane is here: whole tiles (checked on the host)
+                        // butterfly reduce-scatter over the warp's 32 rows: after the
+                        // round with offset o a lane holds o partial column sums, the
+                        // upper half of its 2o when lane & o; at the end column lane
+                        float cs[32];
+#pragma unroll
+                        for (int t = 0; t < 16; ++t) {
+                            const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&pk[t]);
+                            cs[2 * t] = __low2float(h2);
+                            cs[2 * t + 1] = __high2float(h2);
+                            if (a.so || a.tso) {
+                                const __nv_bfloat162 l2 = *reinterpret_cast<const __nv_bfloat162*>(&pl[t]);
+                                cs[2 * t] += __low2float(l2);
+                                cs[2 * t + 1] += __high2float(l2);
+                            }
+                        }
+#pragma unroll
+                        for (int off = 16; off >= 1; off >>= 1) {
+                            const bool up = (lane & off) != 0;
+#pragma unroll
+                            for (int j = 0; j < off; ++j) {
+                                const float send = up ? cs[j] : cs[j + off];
+                                const float keep = up ? cs[j + off] : cs[j];
+                                cs[j] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+                            }
+                        }
+                        a.colsum[(size_t)(row >> 5) * a.N + cb + lane] = cs[0];
+                    }
                     if (a.so) {
                         uint4* d1 = reinterpret_cast<uint4*>(a.out_bf16 + o + a.so);
                         uint4* d2 = reinterpret_cast<uint4*>(a.out_bf16 + o + 2 * (size_t)a.so);
@@ -406,13 +438,19 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, bool
 cudaError_t umma_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
                       int epi, const float* bias, const __nv_bfloat16* mask, __nv_bfloat16* out_bf16,
                       float* out_f32, int ldo, int splits, int* err, cudaStream_t s, __nv_bfloat16* out_t, int ldt,
-                      int ldm, int so, int tso, int t_order, int a_blk, int b_blk, int t_rows) {
+                      int ldm, int so, int tso, int t_order, int a_blk, int b_blk, int t_rows, float* colsum) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(umma::gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(umma::gemm_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              umma::smem_bytes(2));
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(umma::gemm_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(umma::gemm_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     umma::smem_bytes(2));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(umma::gemm_kernel<6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     umma::smem_bytes(6));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(umma::gemm_kernel<6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      umma::smem_bytes(6));
         if (e != cudaSuccess) return e;
         attr_set = true;
@@ -442,20 +480,26 @@ cudaError_t umma_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, i
     a.a_blk = a_blk;
     a.b_blk = b_blk;
     a.t_rows = out_t ? t_rows : 0;
+    a.colsum = colsum;
     auto al16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
     a.vec = (epi == umma::kEpiF32 ? (ldo % 4 == 0 && al16(out_f32))
                                   : (ldo % 8 == 0 && al16(out_bf16) &&
                                      (epi != umma::kEpiMaskBf16 || (al16(mask) && a.ldm % 8 == 0))))
                 ? 1 : 0;
     a.err = err;
+    if (colsum && (epi == umma::kEpiF32 || M % umma::BM || N % umma::BN || !a.vec)) return cudaErrorInvalidValue;
     a.n_tiles = (N + umma::BN - 1) / umma::BN;
     const long long tiles = (long long)((M + umma::BM - 1) / umma::BM) * a.n_tiles;
     if (tiles < 1 || tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     dim3 grid((unsigned)tiles, 1, splits);
-    if (a.k_blocks_per_split <= 8)
-        umma::gemm_kernel<2><<<grid, umma::THREADS, umma::smem_bytes(2), s>>>(ma, mb, a);
+    if (colsum && a.k_blocks_per_split <= 8)
+        umma::gemm_kernel<2, true><<<grid, umma::THREADS, umma::smem_bytes(2), s>>>(ma, mb, a);
+    else if (colsum)
+        umma::gemm_kernel<6, true><<<grid, umma::THREADS, umma::smem_bytes(6), s>>>(ma, mb, a);
+    else if (a.k_blocks_per_split <= 8)
+        umma::gemm_kernel<2, false><<<grid, umma::THREADS, umma::smem_bytes(2), s>>>(ma, mb, a);
     else
-        umma::gemm_kernel<6><<<grid, umma::THREADS, umma::smem_bytes(6), s>>>(ma, mb, a);
+        umma::gemm_kernel<6, false><<<grid, umma::THREADS, umma::smem_bytes(6), s>>>(ma, mb, a);
     return cudaGetLastError();
 }
 
