@@ -35,7 +35,8 @@ def test_struct_fields_match_header():
     from paper_2603_11045_gb300 import _native as N
     src = open(HEADER).read()
     structs = (("nefty_problem", N.nefty_problem), ("nefty_stats", N.nefty_stats), ("nefty_job", N.nefty_job),
-               ("nefty_job_result", N.nefty_job_result), ("nefty_serve_config", N.nefty_serve_config))
+               ("nefty_job_result", N.nefty_job_result), ("nefty_serve_config", N.nefty_serve_config),
+               ("nefty_field_desc", N.nefty_field_desc))
     sizes = {"int32_t": 4, "double": 8, "int64_t": 8, "uint64_t": 8,
              "nefty_problem": ctypes.sizeof(N.nefty_problem)}
     for struct, cls in structs:
@@ -99,3 +100,32 @@ def test_debug_barrier_fault_needs_a_handle(lib):
     """The fault-injection hook validates its handle on the host (no device work)."""
     assert lib.nefty_debug_barrier_fault(None, 1, 0) == 1   # NEFTY_EINVAL
     assert b"handle" in lib.nefty_last_error(None)
+
+
+def _field(**kw):
+    from paper_2603_11045_gb300.field import FieldSpec
+    args = dict(nx=8, ny=6, nz=4, n_freq=5, width=128, depth=3, skip_layer=2)
+    args.update(kw)
+    return FieldSpec(**args).to_c()
+
+
+def test_field_param_count_and_validation(lib):
+    """nefty_field_param_count follows the packed layout of nefty.h (W_0 [W x 6F],
+    b_0, W_l [W x in_l], b_l, w_out, b_out) and returns 0 for an invalid
+    descriptor; keep_activations is a 0/1 switch that leaves the layout alone."""
+    F, W, L, s = 5, 128, 3, 2
+    want = W * 6 * F + W + sum(W * (W + 6 * F if l == s else W) + W for l in range(1, L)) + W + 1
+    for keep in (0, 1):
+        d = _field(keep_activations=bool(keep))
+        assert d.keep_activations == keep
+        assert lib.nefty_field_param_count(ctypes.byref(d)) == want
+    d = _field()
+    d.keep_activations = 2
+    assert lib.nefty_field_param_count(ctypes.byref(d)) == 0
+    for bad in (dict(width=100), dict(depth=0), dict(precision=2), dict(skip_layer=3), dict(n_freq=0),
+                dict(freq_lo=0.0), dict(alpha_min=2.0, alpha_max=1.0)):
+        assert lib.nefty_field_param_count(ctypes.byref(_field(**bad))) == 0, bad
+
+
+def test_field_activation_reuses_of_null_handle(lib):
+    assert lib.nefty_field_activation_reuses(None) == 0
