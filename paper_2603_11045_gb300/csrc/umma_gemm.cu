@@ -13,9 +13,18 @@
 // with the FP32 accumulator in tensor memory and releases each stage with
 // tcgen05.commit onto that stage's "empty" mbarrier.  After the last k-block the
 // four warps read their 32 accumulator lanes with tcgen05.ld and apply the
-// epilogue, each thread writing 16-byte pieces of its row.  Every wait is bounded: on timeout the kernel records an error,
-// waits (bounded) for its own copies and MMAs, frees its tensor memory and
-// returns.
+// epilogue, each thread writing 16-byte pieces of its row (and, where asked,
+// the transposed output and per-warp column sums).
+//
+// An operand is either row-major (a 2D tensor map, box 64 x 128) or K-blocked:
+// element (r, k) of R rows at (k / 64) R 64 + r 64 + k % 64, read through a 3D
+// map whose box {64, 128, 1} is 16 contiguous KB and lands in shared memory
+// exactly as the 2D box does.  The long-K weight-gradient products read their
+// transposed operands that way; a row-major box there would fetch 128 rows a
+// whole K apart.
+//
+// Every wait is bounded: on timeout the kernel records an error, waits
+// (bounded) for its own copies and MMAs, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
